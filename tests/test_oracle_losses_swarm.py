@@ -1,0 +1,137 @@
+"""T5/T8/T6 pins of the oracle: exact charge conservation, determinism and
+checkpoint/resume; paired random removal (Sec. II) keeps N constant with
+victims uniform over slots; radial losses are binomial; and the exact
+Maxwell-model swarm (constant collision frequency): drift w = eE/(m nu) and
+mean energy from the energy balance e E w = nu (2m/M) <eps>."""
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_2202_03215_gb300 import workloads as w
+from tests.helpers import QE, ME, AMU, beam_state, maxwell_model_xsec, n_gas
+
+
+def _small(seed=1, **kw):
+    return w.config_argon_small(seed=seed, n_e0=20000, n_i0=20000, **kw)
+
+
+def test_charge_is_exact_and_runs_are_deterministic():
+    a, b = oracle.Oracle(_small()), oracle.Oracle(_small())
+    a.step(23); b.step(23)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("cell_e", "off_e", "vx_e", "id_e", "cell_i", "vx_i", "E", "Q_e", "Q_i"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert sa["Q_e"].sum() == sa["n_e"] * 2**32
+    assert sa["Q_i"].sum() == sa["n_i"] * 2**32
+    assert len(np.unique(np.concatenate([sa["id_e"], sa["id_i"]]))) == sa["n_e"] + sa["n_i"]
+    assert np.all(sa["id_e"] < sa["next_id"])
+
+
+@pytest.mark.parametrize("split", [10, 7])
+def test_checkpoint_resume_is_bit_identical(split):
+    ref = oracle.Oracle(_small(seed=3))
+    ref.step(25)
+    a = oracle.Oracle(_small(seed=3))
+    a.step(split)
+    st = a.get_state()
+    b = oracle.Oracle(_small(seed=3))  # its own init is overwritten by the checkpoint
+    b.set_state(st)
+    b.step(25 - split)
+    sr, sb = ref.get_state(), b.get_state()
+    for k in ("cell_e", "off_e", "vx_e", "vy_e", "vz_e", "id_e", "cell_i", "off_i", "vx_i", "id_i",
+              "E", "Q_e", "Q_i"):
+        assert np.array_equal(sr[k], sb[k]), k
+    assert sr["next_id"] == sb["next_id"]
+
+
+def test_pair_removal_keeps_n_and_draws_uniform_victims():
+    n, eps0 = 2000, 60.0
+    p = w.Params(L_m=0.05, n_cells=100, dt_s=2e-11, field_mode=w.FIELD_APPLIED, drive=w.DRIVE_E0,
+                 E0_Vpm=0.0, n_e0=n, n_i0=n, ion_subcycle=0, loss_mode=w.LOSS_PAIR)
+    o = oracle.Oracle(p)
+    speed = np.sqrt(2 * QE * eps0 / ME)
+    hits_e = np.zeros(n)
+    hits_i = np.zeros(n)
+    tot = 0
+    for rep in range(60):
+        st = beam_state(n, p.n_cells, speed, np.random.default_rng(100 + rep), n_i=n, step=rep)
+        o.set_state(st)
+        o.step(1)
+        s = o.get_state()
+        codes = o.codes(0, n)
+        nb = int((codes == 2).sum())
+        assert s["n_e"] == n and s["n_i"] == n
+        new_e = s["id_e"] >= 2 * n
+        new_i = s["id_i"] >= 2 * n
+        assert new_e.sum() == nb and new_i.sum() == nb   # victims distinct within a step
+        assert s["Q_e"].sum() == n * 2**32 and s["Q_i"].sum() == n * 2**32
+        hits_e += new_e
+        hits_i += new_i
+        tot += nb
+    assert tot > 5000
+    for h in (hits_e, hits_i):
+        chi2 = ((h - tot / n) ** 2 / (tot / n)).sum()
+        assert stats.chi2.sf(chi2, n - 1) > 1e-4
+
+
+def test_radial_loss_survivors_are_binomial_and_compacted():
+    n, nu_w, dt = 100_000, 2e9, 2e-11
+    p = w.Params(L_m=0.05, n_cells=100, dt_s=dt, xsec=[], field_mode=w.FIELD_APPLIED, drive=w.DRIVE_E0,
+                 E0_Vpm=0.0, n_e0=n, n_i0=n, ion_subcycle=1, loss_mode=w.LOSS_RADIAL, nu_w=nu_w)
+    o = oracle.Oracle(p)
+    before = o.get_state()
+    o.step(1)
+    s = o.get_state()
+    P = 1 - np.exp(-nu_w * dt)
+    for sp in ("e", "i"):
+        surv = s[f"n_{sp}"]
+        assert abs(surv - n * (1 - P)) < 4.5 * np.sqrt(n * P * (1 - P))
+        ids = s[f"id_{sp}"]
+        assert len(np.unique(ids)) == surv and np.all(np.isin(ids, before[f"id_{sp}"]))
+        # compaction: survivors below N_new keep their slots, tail survivors fill holes ascending
+        keep = np.isin(before[f"id_{sp}"], ids)
+        dead = np.nonzero(~keep)[0]
+        holes = dead[dead < surv]
+        tail = np.nonzero(keep[surv:])[0] + surv
+        expect = before[f"id_{sp}"][:surv].copy()
+        expect[holes] = before[f"id_{sp}"][tail]
+        assert np.array_equal(ids, expect)
+    assert s["Q_e"].sum() == s["n_e"] * 2**32
+
+
+def test_maxwell_model_swarm_drift_and_energy():
+    """Constant collision frequency nu, isotropic elastic scattering with the
+    (2m/M)(1 - cos chi) energy loss, uniform field.  Exact expectations of the
+    discrete-time model (kick a dt, then a collision with probability
+    P = 1 - exp(-nu dt)):
+      post-collision drift   w = a dt q / (P (1 - em/6)),  q = 1 - P (1 - em/6)
+      post-collision <v^2>   = (1 - P em)(2 a dt w + (a dt)^2) / (P em)
+    (em/6: the mean x-velocity an isotropic scatter keeps through the
+    cos-chi dependent speed).  Their continuous-time limits are Maxwell's
+    w = eE/(m nu) and the energy balance e E w = nu em <eps>."""
+    nu, E0, M_amu, dt = 5e9, 2784.0, 0.1, 2e-11
+    ng = n_gas()
+    xs = [maxwell_model_xsec(nu, ng, 100.0, 8193)]
+    n = 4000
+    em = 2 * ME / (M_amu * AMU)
+    a = QE * E0 / ME
+    P = 1 - np.exp(-nu * dt)
+    q = 1 - P * (1 - em / 6)
+    w_th = a * dt * q / (P * (1 - em / 6))
+    v2_th = (1 - P * em) * (2 * a * dt * w_th + (a * dt) ** 2) / (P * em)
+    eps_th = 0.5 * ME / QE * v2_th
+    assert abs(w_th / (a / nu) - 1) < 0.06          # continuous-time limits, for orientation
+    p = w.Params(gas_mass_amu=M_amu, L_m=0.01, n_cells=100, dt_s=dt, xsec=xs, eps_max_e_eV=100.0,
+                 field_mode=w.FIELD_APPLIED, drive=w.DRIVE_E0, E0_Vpm=E0, n_e0=n, n_i0=0, ion_subcycle=0,
+                 loss_mode=w.LOSS_SWARM, Te0_eV=2 / 3 * eps_th, seed=5)
+    o = oracle.Oracle(p)
+    o.step(5000)
+    ws, es = [], []
+    for _ in range(400):
+        o.step(50)
+        s = o.get_state()
+        ws.append(s["vx_e"].mean())
+        es.append((0.5 * ME / QE * (s["vx_e"] ** 2 + s["vy_e"] ** 2 + s["vz_e"] ** 2)).mean())
+    assert abs(np.mean(ws) / w_th - 1) < 0.02
+    assert abs(np.mean(es) / eps_th - 1) < 0.01

@@ -1,0 +1,144 @@
+"""T4/T7 pins of the oracle's null-collision Monte Carlo collisions: real
+collision counts per process against the analytic collision frequencies,
+the constant-frequency (Maxwell) model, and the scattering kinematics."""
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_2202_03215_gb300 import workloads as w
+from tests.helpers import QE, ME, AMU, KB, beam_state, maxwell_model_xsec, n_gas
+
+
+def _sigma(x, eps):
+    s = np.interp(eps, x.energy_eV, x.sigma_m2)
+    if x.kind in (w.EXCITATION, w.IONIZATION) and eps < x.threshold_eV:
+        return 0.0
+    return float(s)
+
+
+def _beam_params(n, **kw):
+    base = dict(L_m=0.05, n_cells=500, dt_s=2e-11, field_mode=w.FIELD_APPLIED, drive=w.DRIVE_E0,
+                E0_Vpm=0.0, n_e0=n, n_i0=0, ion_subcycle=0, loss_mode=w.LOSS_NONE, Te0_eV=1.0,
+                capacity=2 * n + 10)
+    base.update(kw)
+    return w.Params(**base)
+
+
+@pytest.mark.parametrize("eps0", [10.0, 30.0, 120.0])
+def test_real_collision_counts_match_analytic_rates(eps0):
+    n = 200_000
+    p = _beam_params(n)
+    o = oracle.Oracle(p)
+    speed = np.sqrt(2 * QE * eps0 / ME)
+    o.set_state(beam_state(n, p.n_cells, speed, np.random.default_rng(1)))
+    o.step(1)
+    codes = o.codes(0, n)
+    d = o.derived()
+    ng = n_gas()
+    nus = d["nu_star_e"]
+    Pn = 1 - np.exp(-nus * p.dt_s)
+    for k, x in enumerate(p.xsec[:3]):
+        nu = ng * _sigma(x, eps0) * speed
+        pk = Pn * nu / nus
+        cnt = np.count_nonzero(codes == k)
+        if pk == 0:
+            assert cnt == 0
+        else:
+            assert abs(cnt - n * pk) < 4.5 * np.sqrt(n * pk * (1 - pk)), (k, cnt, n * pk)
+    # nu* bounds the total frequency on the whole table range
+    e = np.linspace(0, p.eps_max_e_eV, 20001)
+    tot = sum(np.array([_sigma(x, ee) for ee in e]) for x in p.xsec[:3]) * ng * np.sqrt(2 * QE * e / ME)
+    assert nus >= tot.max() * (1 - 1e-4)
+
+
+def test_maxwell_model_has_no_energy_dependence():
+    n, nu = 200_000, 4e9
+    xs = [maxwell_model_xsec(nu, n_gas(), 100.0, 8193)]
+    p = _beam_params(n, xsec=xs, eps_max_e_eV=100.0, Te0_eV=3.0)
+    o = oracle.Oracle(p)
+    o.step(1)
+    codes = o.codes(0, n)
+    P = 1 - np.exp(-nu * p.dt_s)
+    cnt = np.count_nonzero(codes == 0)
+    assert abs(cnt - n * P) < 4.5 * np.sqrt(n * P * (1 - P))
+    assert abs(o.derived()["nu_star_e"] / nu - 1) < 1e-9
+
+
+def test_elastic_kinematics_isotropic_with_mass_ratio_loss():
+    n, eps0 = 200_000, 10.0
+    M_amu = 0.01   # light gas so that 2m/M is resolved
+    p = _beam_params(n, gas_mass_amu=M_amu)
+    o = oracle.Oracle(p)
+    speed = np.sqrt(2 * QE * eps0 / ME)
+    o.set_state(beam_state(n, p.n_cells, speed, np.random.default_rng(2)))
+    o.step(1)
+    codes = o.codes(0, n)
+    s = o.get_state()
+    sel = codes == 0
+    v = np.stack([s["vx_e"][sel], s["vy_e"][sel], s["vz_e"][sel]])
+    eps = 0.5 * ME / QE * (v * v).sum(0)
+    em = 2 * ME / (M_amu * AMU)
+    r = eps / eps0                       # = 1 - em (1 - cos chi), cos chi ~ U(-1, 1)
+    assert stats.kstest((r - (1 - 2 * em)) / (2 * em), "uniform").pvalue > 1e-4
+    nvec = v / np.sqrt((v * v).sum(0))
+    m = nvec.shape[1]
+    assert np.all(np.abs(nvec.mean(1)) < 5 / np.sqrt(3 * m))
+    assert np.all(np.abs((nvec ** 2).mean(1) - 1 / 3) < 5 * np.sqrt(4 / 45 / m))
+    # cos chi against the beam direction (+x) is uniform
+    assert stats.kstest((nvec[0] + 1) / 2, "uniform").pvalue > 1e-4
+
+
+def test_excitation_and_ionization_energy_balance():
+    n, eps0 = 200_000, 60.0
+    p = _beam_params(n)
+    o = oracle.Oracle(p)
+    speed = np.sqrt(2 * QE * eps0 / ME)
+    o.set_state(beam_state(n, p.n_cells, speed, np.random.default_rng(3)))
+    o.step(1)
+    codes = o.codes(0, n)
+    s = o.get_state()
+    K = 0.5 * ME / QE
+    eps = K * (s["vx_e"] ** 2 + s["vy_e"] ** 2 + s["vz_e"] ** 2)
+    exc = codes == 1
+    assert np.allclose(eps[:n][exc], eps0 - 11.5, rtol=1e-12)
+    iz = np.nonzero(codes == 2)[0]
+    nb = len(iz)
+    assert s["n_e"] == n + nb and s["n_i"] == nb
+    ej = eps[n:n + nb]                   # newborns appended in parent-slot order
+    assert np.allclose(eps[iz] + ej, eps0 - 15.76, rtol=1e-11)
+    assert stats.kstest(ej / (eps0 - 15.76), "uniform").pvalue > 1e-4
+    # newborn electron sits at its parent's position, the ion too
+    assert np.array_equal(s["cell_e"][n:], s["cell_e"][iz]) and np.array_equal(s["off_e"][n:], s["off_e"][iz])
+    assert np.array_equal(s["cell_i"], s["cell_e"][iz])
+    # newborn ion velocity: gas Maxwellian
+    M = p.gas_mass_amu * AMU
+    vt = np.sqrt(KB * p.T_gas_K / M)
+    vi = np.concatenate([s["vx_i"], s["vy_i"], s["vz_i"]]) / vt
+    assert stats.kstest(vi, "norm").pvalue > 1e-4
+
+
+def test_ion_charge_exchange_takes_the_neutral_velocity():
+    n = 100_000
+    p = _beam_params(0, n_i0=n, ion_subcycle=1, capacity=n + 10, xsec=w.argon_xsecs(sigma_iso=0.0))
+    o = oracle.Oracle(p)
+    M = p.gas_mass_amu * AMU
+    g = 3000.0
+    st = beam_state(0, p.n_cells, 0.0, np.random.default_rng(4), n_i=n, ion_speed=g)
+    o.set_state(st)
+    o.step(1)
+    codes = o.codes(1, n)
+    s = o.get_state()
+    cx = codes == 3
+    ng = n_gas()
+    d = o.derived()
+    # the relative speed varies with the neutral draw: compare with the mean of sigma g over the gas
+    vt = np.sqrt(KB * p.T_gas_K / M)
+    rng = np.random.default_rng(9)
+    vn = rng.standard_normal((3, 400000)) * vt
+    gr = np.sqrt((g - vn[0]) ** 2 + vn[1] ** 2 + vn[2] ** 2)
+    nu_mean = ng * 5e-19 * gr.mean()
+    P = (1 - np.exp(-d["nu_star_i"] * p.dt_s)) * nu_mean / d["nu_star_i"]
+    assert abs(cx.sum() - n * P) < 4.5 * np.sqrt(n * P)
+    vi = np.concatenate([s["vx_i"][cx], s["vy_i"][cx], s["vz_i"][cx]]) / vt
+    assert stats.kstest(vi, "norm").pvalue > 1e-4
