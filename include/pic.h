@@ -1,0 +1,220 @@
+/* pic.h -- C ABI of the GB300 (sm_103a) PIC-MCC positive-column library.
+ *
+ * The library advances the 1D3V electrostatic Particle-In-Cell Monte Carlo
+ * Collisions model of a rare-gas positive column of Boeuf, "Ionization waves
+ * (striations) in a low-current plasma column revisited with kinetic and
+ * fluid models", Sec. II: electrons and ions move in the self-consistent
+ * field E = -E0 + E_sp of a periodic column of length L; the field comes from
+ * Poisson's equation on a uniform grid; collisions with the neutral gas are
+ * Monte Carlo events drawn from cross sections; every ionization creates an
+ * electron-ion pair and, in the paper's model, removes one randomly chosen
+ * electron and one randomly chosen ion so that the particle number stays
+ * constant.  Sec. V's alternative (an imposed loss frequency) is the RADIAL
+ * loss mode.
+ *
+ * Every step runs in CUDA kernels on one GPU; there is no CPU fallback.  All
+ * calls return 0 or a negative PIC_E* code; pic_last_error() gives a message.
+ *
+ * Conventions
+ *  - Pointers in structs passed IN are caller-owned host memory, read during
+ *    the call only; nothing is retained after the call returns.
+ *  - Pointers in structs passed OUT are caller-owned host buffers of the
+ *    documented length; a NULL pointer skips that output.
+ *  - A handle owns its device memory and one CUDA stream; it is not
+ *    thread-safe.  Errors raised on the device (capacity, non-finite field)
+ *    latch in the handle and are returned by the call that detects them.
+ *  - Units are SI except energies (eV) and pressure (Torr).
+ */
+#ifndef PIC_H
+#define PIC_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_ABI_VERSION 1
+
+/* error codes */
+#define PIC_OK 0
+#define PIC_EINVAL (-1)     /* bad argument */
+#define PIC_ENOMEM (-2)     /* device or host allocation failed */
+#define PIC_ECUDA (-3)      /* a CUDA runtime call failed */
+#define PIC_ECAPACITY (-4)  /* particle capacity or per-step staging capacity exceeded */
+#define PIC_ENONFINITE (-5) /* the field became non-finite */
+#define PIC_ETIMEOUT (-6)   /* a bounded device wait gave up */
+#define PIC_EPARAM (-7)     /* stability limit violated (nu* dt > 0.3) without PIC_FLAG_ALLOW_LARGE_NULL */
+
+/* collision process kinds (Sec. II: electron-neutral elastic, excitation,
+ * ionization; ion-neutral charge exchange ("backward") and isotropic) */
+#define PIC_ELASTIC 0
+#define PIC_EXCITATION 1
+#define PIC_IONIZATION 2
+#define PIC_ION_CX 3
+#define PIC_ION_ISO 4
+
+/* how the applied field E0 is set */
+#define PIC_DRIVE_E0 0       /* E0 = E0_Vpm (the paper's control parameter) */
+#define PIC_DRIVE_V 1        /* E0 = V_applied / L */
+#define PIC_DRIVE_CIRCUIT 2  /* reserved: external resistor circuit (Sec. V) */
+
+/* field: self-consistent (Sec. II) or the applied field alone (uniform-field swarm) */
+#define PIC_FIELD_POISSON 0
+#define PIC_FIELD_APPLIED 1
+
+/* particle losses */
+#define PIC_LOSS_PAIR 0    /* Sec. II: one random electron and ion removed per ionization */
+#define PIC_LOSS_RADIAL 1  /* Sec. V: every particle removed with probability 1 - exp(-nu_w dt) */
+#define PIC_LOSS_NONE 2    /* births kept, nothing removed */
+#define PIC_LOSS_SWARM 3   /* ionizations counted but no particle created or removed */
+
+/* particle storage form */
+#define PIC_FP64 0   /* FP64 offset and velocity */
+#define PIC_MIXED 1  /* int32 cell + FP32 offset/velocity (float4); FP64 field */
+
+/* flags */
+#define PIC_FLAG_RECORD_CODES 1u        /* keep each particle's process code of the last step */
+#define PIC_FLAG_NO_GRAPH 2u            /* launch kernels one by one instead of CUDA graphs */
+#define PIC_FLAG_ALLOW_LARGE_NULL 4u    /* accept nu* dt > 0.3 */
+
+/* One collision process (Sec. II, "scattering cross-sections"): sigma(eps)
+ * on an ascending energy grid.  Electron processes use the electron energy;
+ * ion processes use 0.5 M g^2 / e, g the ion-neutral relative speed.  Linear
+ * interpolation between points, end values held outside; excitation and
+ * ionization are zero below threshold_eV. */
+typedef struct pic_xsec {
+  int32_t kind;            /* PIC_ELASTIC .. PIC_ION_ISO */
+  int32_t n;               /* number of points, >= 1 */
+  double threshold_eV;     /* excitation / ionization threshold; ignored otherwise */
+  const double *energy_eV; /* n ascending energies */
+  const double *sigma_m2;  /* n cross sections */
+} pic_xsec;
+
+/* The problem statement of one periodic column (Sec. II). */
+typedef struct pic_params {
+  double gas_mass_amu;     /* neutral (= ion) mass */
+  double pressure_torr;    /* gas pressure p */
+  double T_gas_K;          /* gas temperature */
+  double L_m;              /* column length L */
+  double R_m;              /* column radius R (used by radius-based drives) */
+  int32_t drive;           /* PIC_DRIVE_* */
+  int32_t field_mode;      /* PIC_FIELD_* */
+  double E0_Vpm;           /* |applied field| for PIC_DRIVE_E0; the applied field is -E0 */
+  double V_applied;        /* voltage across L for PIC_DRIVE_V */
+  double I_A, U_src, R_ext_ohm_m2;  /* current / source / resistor (reserved drives) */
+  int32_t n_xsec, pad0;
+  const pic_xsec *xsec;    /* n_xsec processes; at most 8 per species */
+  int32_t n_cells;         /* grid cells = nodes (periodic), >= 3 */
+  int32_t ion_subcycle;    /* ions advance every ion_subcycle steps with dt_i = ion_subcycle dt; 0 = frozen */
+  double dt_s;             /* electron time step dt (Sec. II: dt < 0.2/w_pe) */
+  int64_t n_e0, n_i0;      /* initial macroparticles per species */
+  int64_t capacity;        /* particle slots per species; 0 = 1.25 max(n_e0, n_i0) + 1024 */
+  double n0_m3;            /* initial density n0: macro weight w = n0 L / n_e0 (per m^2) */
+  double Te0_eV, Ti0_eV;   /* initial Maxwellian temperatures */
+  int32_t loss_mode;       /* PIC_LOSS_* */
+  int32_t precision;       /* PIC_FP64 or PIC_MIXED */
+  double nu_w;             /* loss frequency of PIC_LOSS_RADIAL (s^-1) */
+  uint64_t seed;           /* Philox4x32-10 key */
+  int32_t diag_every;      /* accumulate moments every diag_every steps (0 = never); must be a
+                              multiple of ion_subcycle when ions move */
+  int32_t sort_every;      /* counting sort of particles by cell every sort_every steps (0 = never) */
+  int32_t n_table;         /* points of the uniform-energy collision-frequency tables, >= 3 */
+  uint32_t flags;          /* PIC_FLAG_* */
+  double eps_max_e_eV;     /* electron table range [0, eps_max_e]; higher energies hold the last value */
+  double eps_max_i_eV;     /* ion table range */
+  int32_t column, pad1;    /* column index mixed into the random-number counters (batched runs) */
+} pic_params;
+
+/* Particle state and field, host arrays.  pic_get_state fills the non-NULL
+ * arrays (lengths >= n_e, n_i, n_cells); pic_set_state reads them.  For
+ * PIC_MIXED the offsets/velocities are rounded to FP32 on set and widened on get.
+ * Offsets lie in [0, 1): position x = (cell + off) L / n_cells. */
+typedef struct pic_state {
+  int64_t n_e, n_i;        /* live particles */
+  int64_t step;            /* steps taken (the random-number counter of the next step) */
+  int64_t next_id;         /* id of the next newborn particle */
+  double E0;               /* current |applied field| */
+  int32_t *cell_e; double *off_e, *vx_e, *vy_e, *vz_e; uint64_t *id_e;
+  int32_t *cell_i; double *off_i, *vx_i, *vy_i, *vz_i; uint64_t *id_i;
+  double *E;               /* node field E^n (V/m), n_cells; set: NULL = recompute from the charges */
+  int64_t *Q_e;            /* electron node charge, fixed point 2^32 per particle (get only) */
+  int64_t *Q_i;            /* ion node charge, fixed point (set: NULL = re-deposit the ions) */
+} pic_state;
+
+/* Counters since pic_init. */
+typedef struct pic_stats {
+  int64_t step, n_e, n_i, next_id;
+  int64_t n_coll_e[8];     /* real electron collisions per electron process (in xsec order) */
+  int64_t n_coll_i[8];     /* real ion collisions per ion process */
+  int64_t births;          /* ionization events (pairs created) */
+  int64_t losses_e, losses_i;
+  int64_t overflow_e, overflow_i;  /* collisions evaluated above the table range */
+  double E0;
+  int64_t n_diag;          /* diagnostic samples taken */
+} pic_stats;
+
+/* Time-averaged moments over the current window (the profiles of Fig. 4).
+ * Every non-NULL array has n_cells entries (node values). */
+typedef struct pic_moments_out {
+  int64_t n_samples, n_steps;   /* diagnostic samples / steps in the window (out) */
+  double *n_e, *n_i;            /* densities (m^-3) */
+  double *gamma_e;              /* electron flux (m^-2 s^-1) */
+  double *mean_eps_e;           /* electron mean energy (eV) */
+  double *heat_e;               /* electron energy flux (eV m^-2 s^-1) */
+  double *iz_rate;              /* ionizations (m^-3 s^-1), every step counted */
+  double *gamma_i;              /* ion flux (m^-2 s^-1) */
+  double *E;                    /* field (V/m) */
+  double *phi;                  /* space-charge potential (V), phi_0 = 0 */
+  int32_t reset, pad;           /* in: reset the window after reading */
+} pic_moments_out;
+
+typedef struct pic_handle pic_handle;
+
+/* Validate params, build the collision tables, allocate device memory,
+ * place n_e0 electrons and n_i0 ions uniformly with Maxwellian velocities,
+ * solve the initial field and pull velocities back half a step (leapfrog).
+ * *out receives the handle (owned by the caller until pic_free). */
+int pic_init(const pic_params *params, pic_handle **out);
+
+/* Advance n >= 0 steps.  Each step: electron gather/push/collisions/deposit,
+ * ion step on every ion_subcycle-th step, births and removals, periodic sort
+ * every sort_every steps, field solve.  Stream-ordered; synchronises once at
+ * the end to read the device status word. */
+int pic_step(pic_handle *h, int64_t n);
+
+/* Copy the moment window (host arrays of n_cells, NULL to skip). */
+int pic_moments(pic_handle *h, pic_moments_out *out);
+
+int pic_get_state(pic_handle *h, pic_state *out);
+/* Replace the state; the next step uses state->step as its counter. */
+int pic_set_state(pic_handle *h, const pic_state *in);
+int pic_get_stats(pic_handle *h, pic_stats *out);
+
+/* Per-particle process code of the last step (needs PIC_FLAG_RECORD_CODES):
+ * -1 no collision, -2 removed by the radial loss, else the xsec index.
+ * Indexed by the slot the particle had during that step; n <= capacity. */
+int pic_last_codes(pic_handle *h, int species, int32_t *out, int64_t n);
+
+/* Derived scalars: [n_g, nu*_e, P_null_e, nu*_i, P_null_i, w, dx]. */
+int pic_derived(pic_handle *h, double out[7]);
+
+/* The CUDA stream the handle launches on (a cudaStream_t). */
+void *pic_stream(pic_handle *h);
+
+void pic_free(pic_handle *h);
+
+/* Message of the last error on this handle (NULL: the last global error). */
+const char *pic_last_error(pic_handle *h);
+
+/* Self-test hook: int128 -> double conversion used by the field solve, run
+ * on the device: v_k = hi[k] 2^64 + lo[k]; out[k] = double nearest to v_k
+ * (ties to even).  Host arrays of n. */
+int pic_test_i128_to_double(const int64_t *hi, const uint64_t *lo, double *out, int n);
+
+int pic_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

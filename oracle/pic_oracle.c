@@ -378,7 +378,7 @@ static void push(const ora_t *h, real a, real d, real E, int32_t *cell, real *of
 /* table position of eps: i, fraction fr; above the table the last value is held */
 static int tab_pos(real eps, real inv_de, int ntab, real *fr, int *ovf) {
   real x = eps * inv_de;
-  if (x >= (real)(ntab - 1)) { *fr = (real)1; *ovf = 1; return ntab - 2; }
+  if (!(x < (real)(ntab - 1))) { *fr = (real)1; *ovf = 1; return ntab - 2; }  /* also NaN */
   int i = (int)x;
   *fr = x - (real)i;
   *ovf = 0;

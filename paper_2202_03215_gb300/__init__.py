@@ -1,0 +1,243 @@
+"""Python binding of the GB300 PIC-MCC library (include/pic.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of libpic.so.  There is no CPU fallback; importing the binding
+without the compiled library, or creating a column without a GPU, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+from typing import Optional
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+LIBPATH = HERE / "libpic.so"
+
+PIC_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ECAPACITY", -5: "ENONFINITE",
+              -6: "ETIMEOUT", -7: "EPARAM"}
+FLAG_RECORD_CODES = 1
+FLAG_NO_GRAPH = 2
+FLAG_ALLOW_LARGE_NULL = 4
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{PIC_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Xsec(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("threshold_eV", C.c_double),
+                ("energy_eV", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double))]
+
+
+class Params(C.Structure):
+    _fields_ = [("gas_mass_amu", C.c_double), ("pressure_torr", C.c_double), ("T_gas_K", C.c_double),
+                ("L_m", C.c_double), ("R_m", C.c_double),
+                ("drive", C.c_int32), ("field_mode", C.c_int32),
+                ("E0_Vpm", C.c_double), ("V_applied", C.c_double), ("I_A", C.c_double),
+                ("U_src", C.c_double), ("R_ext_ohm_m2", C.c_double),
+                ("n_xsec", C.c_int32), ("pad0", C.c_int32), ("xsec", C.POINTER(Xsec)),
+                ("n_cells", C.c_int32), ("ion_subcycle", C.c_int32), ("dt_s", C.c_double),
+                ("n_e0", C.c_int64), ("n_i0", C.c_int64), ("capacity", C.c_int64),
+                ("n0_m3", C.c_double), ("Te0_eV", C.c_double), ("Ti0_eV", C.c_double),
+                ("loss_mode", C.c_int32), ("precision", C.c_int32), ("nu_w", C.c_double),
+                ("seed", C.c_uint64),
+                ("diag_every", C.c_int32), ("sort_every", C.c_int32), ("n_table", C.c_int32),
+                ("flags", C.c_uint32),
+                ("eps_max_e_eV", C.c_double), ("eps_max_i_eV", C.c_double),
+                ("column", C.c_int32), ("pad1", C.c_int32)]
+
+
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+_U64 = C.POINTER(C.c_uint64)
+
+
+class State(C.Structure):
+    _fields_ = [("n_e", C.c_int64), ("n_i", C.c_int64), ("step", C.c_int64), ("next_id", C.c_int64),
+                ("E0", C.c_double),
+                ("cell_e", _I32), ("off_e", _D), ("vx_e", _D), ("vy_e", _D), ("vz_e", _D), ("id_e", _U64),
+                ("cell_i", _I32), ("off_i", _D), ("vx_i", _D), ("vy_i", _D), ("vz_i", _D), ("id_i", _U64),
+                ("E", _D), ("Q_e", _I64), ("Q_i", _I64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("n_e", C.c_int64), ("n_i", C.c_int64), ("next_id", C.c_int64),
+                ("n_coll_e", C.c_int64 * 8), ("n_coll_i", C.c_int64 * 8),
+                ("births", C.c_int64), ("losses_e", C.c_int64), ("losses_i", C.c_int64),
+                ("overflow_e", C.c_int64), ("overflow_i", C.c_int64),
+                ("E0", C.c_double), ("n_diag", C.c_int64)]
+
+
+MOMENT_NAMES = ("n_e", "n_i", "gamma_e", "mean_eps_e", "heat_e", "iz_rate", "gamma_i", "E", "phi")
+
+
+class MomentsOut(C.Structure):
+    _fields_ = [("n_samples", C.c_int64), ("n_steps", C.c_int64)] + \
+               [(k, _D) for k in MOMENT_NAMES] + [("reset", C.c_int32), ("pad", C.c_int32)]
+
+
+_lib: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    """Load libpic.so (built by build.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not LIBPATH.exists():
+            raise ImportError(f"{LIBPATH} is missing: run paper_2202_03215_gb300.build.build() (nvcc, sm_103a)")
+        L = C.CDLL(str(LIBPATH))
+        L.pic_init.argtypes = [C.POINTER(Params), C.POINTER(C.c_void_p)]
+        L.pic_step.argtypes = [C.c_void_p, C.c_int64]
+        L.pic_moments.argtypes = [C.c_void_p, C.POINTER(MomentsOut)]
+        L.pic_get_state.argtypes = [C.c_void_p, C.POINTER(State)]
+        L.pic_set_state.argtypes = [C.c_void_p, C.POINTER(State)]
+        L.pic_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+        L.pic_last_codes.argtypes = [C.c_void_p, C.c_int, _I32, C.c_int64]
+        L.pic_derived.argtypes = [C.c_void_p, _D]
+        L.pic_stream.argtypes = [C.c_void_p]
+        L.pic_stream.restype = C.c_void_p
+        L.pic_free.argtypes = [C.c_void_p]
+        L.pic_free.restype = None
+        L.pic_last_error.argtypes = [C.c_void_p]
+        L.pic_last_error.restype = C.c_char_p
+        L.pic_test_i128_to_double.argtypes = [_I64, _U64, _D, C.c_int]
+        L.pic_abi_version.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+def _check(rc: int, h=None) -> None:
+    if rc:
+        msg = lib().pic_last_error(h)
+        raise PicError(rc, msg.decode() if msg else "")
+
+
+def make_params(p):
+    """Marshal a workloads.Params into pic_params; returns (struct, keepalive)."""
+    keep = []
+    xs = (Xsec * max(1, len(p.xsec)))()
+    for k, x in enumerate(p.xsec):
+        e = np.ascontiguousarray(x.energy_eV, dtype=np.float64)
+        s = np.ascontiguousarray(x.sigma_m2, dtype=np.float64)
+        keep += [e, s]
+        xs[k].kind, xs[k].n, xs[k].threshold_eV = x.kind, len(e), x.threshold_eV
+        xs[k].energy_eV, xs[k].sigma_m2 = _ptr(e, _D), _ptr(s, _D)
+    keep.append(xs)
+    st = Params()
+    for name, _ in Params._fields_:
+        if name in ("xsec", "n_xsec") or name.startswith("pad"):
+            continue
+        setattr(st, name, getattr(p, name))
+    st.n_xsec = len(p.xsec)
+    st.xsec = C.cast(xs, C.POINTER(Xsec))
+    return st, keep
+
+
+def i128_to_double(values) -> np.ndarray:
+    """Run the device int128 -> double conversion of the field solve on a list of Python ints."""
+    vals = [int(v) for v in values]
+    hi = np.array([v >> 64 for v in vals], dtype=np.int64)
+    lo = np.array([v & ((1 << 64) - 1) for v in vals], dtype=np.uint64)
+    out = np.zeros(len(vals))
+    _check(lib().pic_test_i128_to_double(_ptr(hi, _I64), _ptr(lo, _U64), _ptr(out, _D), len(vals)))
+    return out
+
+
+class Column:
+    """One periodic positive column on the GPU (pic_init / pic_step / pic_moments / pic_free)."""
+
+    def __init__(self, params, flags: int = 0):
+        self.L = lib()
+        self.params = params
+        st, keep = make_params(params)
+        st.flags = params.flags | flags
+        h = C.c_void_p()
+        rc = self.L.pic_init(C.byref(st), C.byref(h))
+        _check(rc)
+        self.h = h
+        self.N = params.n_cells
+        self.cap = params.capacity or (max(params.n_e0, params.n_i0) * 5 // 4 + 1024)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.L.pic_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, n: int = 1) -> None:
+        _check(self.L.pic_step(self.h, n), self.h)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self.L.pic_get_stats(self.h, C.byref(s)), self.h)
+        d = {k: getattr(s, k) for k, _ in Stats._fields_}
+        d["n_coll_e"], d["n_coll_i"] = list(s.n_coll_e), list(s.n_coll_i)
+        return d
+
+    def derived(self) -> dict:
+        o = np.zeros(7)
+        _check(self.L.pic_derived(self.h, _ptr(o, _D)), self.h)
+        return dict(zip(["n_g", "nu_star_e", "P_null_e", "nu_star_i", "P_null_i", "w", "dx"], o))
+
+    def stream(self) -> int:
+        return self.L.pic_stream(self.h) or 0
+
+    def get_state(self) -> dict:
+        st = self.stats()
+        ne, ni = st["n_e"], st["n_i"]
+        d = {"cell_e": np.zeros(ne, np.int32), "off_e": np.zeros(ne), "vx_e": np.zeros(ne),
+             "vy_e": np.zeros(ne), "vz_e": np.zeros(ne), "id_e": np.zeros(ne, np.uint64),
+             "cell_i": np.zeros(ni, np.int32), "off_i": np.zeros(ni), "vx_i": np.zeros(ni),
+             "vy_i": np.zeros(ni), "vz_i": np.zeros(ni), "id_i": np.zeros(ni, np.uint64),
+             "E": np.zeros(self.N), "Q_e": np.zeros(self.N, np.int64), "Q_i": np.zeros(self.N, np.int64)}
+        s = State()
+        for k, t in (("cell", _I32), ("off", _D), ("vx", _D), ("vy", _D), ("vz", _D), ("id", _U64)):
+            for sp in ("e", "i"):
+                setattr(s, f"{k}_{sp}", _ptr(d[f"{k}_{sp}"], t))
+        s.E, s.Q_e, s.Q_i = _ptr(d["E"], _D), _ptr(d["Q_e"], _I64), _ptr(d["Q_i"], _I64)
+        _check(self.L.pic_get_state(self.h, C.byref(s)), self.h)
+        d.update(n_e=s.n_e, n_i=s.n_i, step=s.step, next_id=s.next_id, E0=s.E0)
+        return d
+
+    def set_state(self, d: dict, with_E: bool = True, with_Qi: bool = True) -> None:
+        s = State()
+        s.n_e, s.n_i = len(d["cell_e"]), len(d["cell_i"])
+        s.step, s.next_id, s.E0 = int(d["step"]), int(d["next_id"]), float(d["E0"])
+        keep = []
+        for k, dt, t in (("cell", np.int32, _I32), ("off", np.float64, _D), ("vx", np.float64, _D),
+                         ("vy", np.float64, _D), ("vz", np.float64, _D), ("id", np.uint64, _U64)):
+            for sp in ("e", "i"):
+                a = np.ascontiguousarray(d[f"{k}_{sp}"], dtype=dt)
+                keep.append(a)
+                setattr(s, f"{k}_{sp}", _ptr(a, t))
+        if with_E and d.get("E") is not None:
+            a = np.ascontiguousarray(d["E"], dtype=np.float64); keep.append(a); s.E = _ptr(a, _D)
+        if with_Qi and d.get("Q_i") is not None:
+            a = np.ascontiguousarray(d["Q_i"], dtype=np.int64); keep.append(a); s.Q_i = _ptr(a, _I64)
+        _check(self.L.pic_set_state(self.h, C.byref(s)), self.h)
+
+    def codes(self, species: int, n: int) -> np.ndarray:
+        out = np.zeros(n, np.int32)
+        _check(self.L.pic_last_codes(self.h, species, _ptr(out, _I32), n), self.h)
+        return out
+
+    def moments(self, reset: bool = False) -> dict:
+        d = {k: np.zeros(self.N) for k in MOMENT_NAMES}
+        m = MomentsOut()
+        for k in MOMENT_NAMES:
+            setattr(m, k, _ptr(d[k], _D))
+        m.reset = int(reset)
+        _check(self.L.pic_moments(self.h, C.byref(m)), self.h)
+        d["n_samples"], d["n_steps"] = m.n_samples, m.n_steps
+        return d

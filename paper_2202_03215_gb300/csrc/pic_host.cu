@@ -1,0 +1,686 @@
+// Host driver and C ABI (include/pic.h) of the PIC-MCC library.
+//
+// Owns the device memory of one periodic column, builds the uniform-energy
+// collision-frequency tables from the caller's cross sections (Sec. II), and
+// launches the step kernels on the handle's stream.  No step is computed on
+// the host; the host only prepares tables, launches, and copies state.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+namespace {
+
+// CODATA 2018
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kKb = 1.380649e-23;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kTorr = 133.32236842105263;
+constexpr double kTwo32 = 4294967296.0;
+
+thread_local std::string g_err;
+
+}  // namespace
+
+struct pic_handle {
+  pic_params p{};
+  int N = 0;
+  int ntab = 0;
+  int nsm = 0;
+  bool mixed = false;
+  cudaStream_t stream = nullptr;
+  // derived
+  double ng = 0, dx = 0, w = 0, M = 0, Cfield = 0, E0 = 0, dt_i = 0;
+  double nustar[2] = {0, 0}, Pnull[2] = {0, 0};
+  // device memory
+  pic::Ctl *ctl = nullptr;
+  pic::SpeciesDev sp[2]{};
+  double *E = nullptr, *Eh = nullptr;
+  void *Ef = nullptr;                 // R[N+1]
+  void *tab[2] = {nullptr, nullptr};  // R[np * ntab]
+  float *gauss = nullptr;
+  void *bb_mem = nullptr;
+  uint32_t *k3_mem = nullptr;
+  double *mom = nullptr;              // 8 * N doubles
+  unsigned long long *mom_iz = nullptr;
+  // kernel parameter blocks
+  pic::StepK<double> kd{};
+  pic::StepK<float> kf{};
+  pic::BirthBuf<double> bbd{};
+  pic::BirthBuf<float> bbf{};
+  pic::K3Scratch sc{};
+  pic::Moments m{};
+  pic::FieldK fk{};
+  long long host_step = 0;
+  std::string err;
+  int latched = 0;
+};
+
+namespace {
+
+int set_err(pic_handle *h, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  if (h) h->err = buf;
+  return code;
+}
+
+#define CU(h, x)                                                                                        \
+  do {                                                                                                  \
+    cudaError_t e_ = (x);                                                                               \
+    if (e_ != cudaSuccess) return set_err(h, PIC_ECUDA, "%s: %s", #x, cudaGetErrorString(e_));       \
+  } while (0)
+
+bool is_e_kind(int k) { return k == PIC_ELASTIC || k == PIC_EXCITATION || k == PIC_IONIZATION; }
+
+// sigma at eps: linear interpolation of the caller's table, end values held,
+// zero below an excitation / ionization threshold
+double xs_at(const pic_xsec &x, double eps) {
+  if ((x.kind == PIC_EXCITATION || x.kind == PIC_IONIZATION) && eps < x.threshold_eV) return 0.0;
+  const double *E = x.energy_eV, *S = x.sigma_m2;
+  const int n = x.n;
+  if (eps <= E[0]) return S[0];
+  if (eps >= E[n - 1]) return S[n - 1];
+  int lo = 0, hi = n - 1;  // largest a with E[a] <= eps: E[lo] <= eps < E[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (E[mid] <= eps) lo = mid; else hi = mid;
+  }
+  const double t = (eps - E[lo]) / (E[lo + 1] - E[lo]);
+  return S[lo] + t * (S[lo + 1] - S[lo]);
+}
+
+// nu_k(eps_i) = n_g sigma_k(eps_i) sqrt(eps_i 2e/m), eps_i = i eps_max/(n-1)
+void nu_table(const pic_xsec &x, double ng, double eps_max, int n, double Vq, double *out) {
+  const double de = eps_max / (double)(n - 1);
+  for (int i = 0; i < n; ++i) {
+    const double eps = (double)i * de;
+    const double v = std::sqrt(eps * Vq);
+    out[i] = ng * xs_at(x, eps) * v;
+  }
+}
+
+// Phi^-1(p) for p <= 1/2 by Newton's method from 0 on Phi(x) = erfc(-x/sqrt2)/2
+// (Phi is convex for x < 0, so the iterates decrease monotonically to the root).
+double inv_phi_newton(double p) {
+  double x = 0.0;
+  for (int it = 0; it < 200; ++it) {
+    const double F = 0.5 * std::erfc(-x / std::sqrt(2.0));
+    const double f = std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI);
+    const double dxn = (F - p) / f;
+    const double xn = x - dxn;
+    if (xn == x || std::fabs(dxn) <= 1e-17 * std::fabs(xn)) { x = xn; break; }
+    x = xn;
+  }
+  return x;
+}
+
+// Gaussian inverse-CDF table, 4096 intervals, FP32 entries: T[k] = Phi^-1(k/4096),
+// end entries with the exact conditional mean of the normal tail over the end interval.
+void gauss_table(float *T) {
+  const int n = pic::kGaussN;
+  for (int k = 1; k <= n / 2; ++k) {
+    const double z = inv_phi_newton((double)k / n);
+    T[k] = (float)z;
+    T[n - k] = (float)(-z);
+  }
+  T[n / 2] = 0.0f;
+  const double z1 = inv_phi_newton(1.0 / n);
+  const double m0 = -(double)n * std::exp(-0.5 * z1 * z1) / std::sqrt(2.0 * M_PI);
+  T[0] = (float)(2.0 * m0 - z1);
+  T[n] = -T[0];
+}
+
+template <class R> pic::StepK<R> &kparams(pic_handle *h);
+template <> pic::StepK<double> &kparams<double>(pic_handle *h) { return h->kd; }
+template <> pic::StepK<float> &kparams<float>(pic_handle *h) { return h->kf; }
+template <class R> pic::BirthBuf<R> &bbuf(pic_handle *h);
+template <> pic::BirthBuf<double> &bbuf<double>(pic_handle *h) { return h->bbd; }
+template <> pic::BirthBuf<float> &bbuf<float>(pic_handle *h) { return h->bbf; }
+
+int check_status(pic_handle *h) {
+  pic::Ctl c;
+  CU(h, cudaMemcpyAsync(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (c.status) {
+    if (c.status & pic::kStNonFinite) h->latched = set_err(h, PIC_ENONFINITE, "the field became non-finite");
+    else if (c.status & pic::kStVictim) h->latched = set_err(h, PIC_ECAPACITY, "more births than particles to remove");
+    else h->latched = set_err(h, PIC_ECAPACITY, "capacity exceeded (status 0x%x)", c.status);
+  }
+  return h->latched;
+}
+
+template <class R> int setup_tables(pic_handle *h) {
+  pic::StepK<R> &k = kparams<R>(h);
+  const pic_params &p = h->p;
+  const int n = h->ntab;
+  k.N = h->N;
+  k.ntab = n;
+  k.loss_mode = p.loss_mode;
+  k.field_mode = p.field_mode;
+  k.flags = p.flags;
+  k.diag_every = p.diag_every;
+  k.sub = p.ion_subcycle;
+  k.column = (uint32_t)p.column;
+  k.seed = p.seed;
+  const double M = h->M;
+  k.V_e = (R)(2.0 * kQe / kMe);
+  k.em = (R)(2.0 * kMe / M);
+  k.sig_n = (R)std::sqrt(kKb * p.T_gas_K / M);
+  k.gauss = h->gauss;
+  const double Vq[2] = {2.0 * kQe / kMe, 2.0 * kQe / M};
+  const double emax[2] = {p.eps_max_e_eV, p.eps_max_i_eV};
+  const double dts[2] = {p.dt_s, h->dt_i};
+  std::vector<std::vector<double>> t64[2];
+  std::vector<double> sum[2] = {std::vector<double>(n, 0.0), std::vector<double>(n, 0.0)};
+  for (int q = 0; q < 2; ++q) { k.sp[q].np = 0; }
+  for (int x = 0; x < p.n_xsec; ++x) {
+    const pic_xsec &xs = p.xsec[x];
+    const int q = is_e_kind(xs.kind) ? 0 : 1;
+    pic::SpecK<R> &s = k.sp[q];
+    const int j = s.np++;
+    s.kind[j] = xs.kind;
+    s.xs[j] = x;
+    s.thr[j] = (R)xs.threshold_eV;
+    t64[q].emplace_back(n);
+    nu_table(xs, h->ng, emax[q], n, Vq[q], t64[q].back().data());
+    for (int i = 0; i < n; ++i) sum[q][i] = sum[q][i] + t64[q].back()[i];
+  }
+  for (int q = 0; q < 2; ++q) {
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i)
+      if (sum[q][i] > mx) mx = sum[q][i];
+    h->nustar[q] = mx;
+    h->Pnull[q] = -std::expm1(-mx * dts[q]);
+    pic::SpecK<R> &s = k.sp[q];
+    s.P = (R)h->Pnull[q];
+    s.nus = (R)mx;
+    s.inv_de = (R)((double)(n - 1) / emax[q]);
+    s.K = (R)(0.5 * (q == 0 ? kMe : M) / kQe);
+    if (p.loss_mode == PIC_LOSS_RADIAL) {
+      const double Pw = -std::expm1(-p.nu_w * dts[q]);
+      s.Pw = (uint32_t)(Pw * kTwo32);
+    } else {
+      s.Pw = 0u;
+    }
+    std::vector<R> flat((size_t)s.np * n + 1);
+    for (int j = 0; j < s.np; ++j)
+      for (int i = 0; i < n; ++i) flat[(size_t)j * n + i] = (R)t64[q][j][i];
+    CU(h, cudaMalloc(&h->tab[q], flat.size() * sizeof(R)));
+    CU(h, cudaMemcpy(h->tab[q], flat.data(), flat.size() * sizeof(R), cudaMemcpyHostToDevice));
+    s.tab = reinterpret_cast<const R *>(h->tab[q]);
+  }
+  k.sp[0].a = (R)(-kQe / kMe * p.dt_s);
+  k.sp[0].d = (R)(p.dt_s / h->dx);
+  k.sp[1].a = (R)(kQe / M * h->dt_i);
+  k.sp[1].d = (R)(h->dt_i / h->dx);
+  if (h->nustar[0] * p.dt_s > 0.3 && !(p.flags & PIC_FLAG_ALLOW_LARGE_NULL))
+    return set_err(h, PIC_EPARAM, "nu*_e dt = %.3f > 0.3", h->nustar[0] * p.dt_s);
+  return 0;
+}
+
+template <class R> int alloc_species(pic_handle *h) {
+  const int64_t cap = h->sp[0].cap;
+  for (int q = 0; q < 2; ++q) {
+    pic::SpeciesDev &s = h->sp[q];
+    CU(h, cudaMalloc(&s.cell, (size_t)cap * 4));
+    CU(h, cudaMalloc(&s.rec, (size_t)cap * sizeof(typename pic::Rec<R>::T)));
+    CU(h, cudaMalloc(&s.id, (size_t)cap * 8));
+    CU(h, cudaMalloc(&s.Q, (size_t)h->N * 8));
+    CU(h, cudaMalloc(&s.dead, (size_t)pic::kStageCap * 4));
+    CU(h, cudaMemset(s.Q, 0, (size_t)h->N * 8));
+    if (h->p.flags & PIC_FLAG_RECORD_CODES) {
+      CU(h, cudaMalloc(&s.code, (size_t)cap * 4));
+      CU(h, cudaMemset(s.code, 0xff, (size_t)cap * 4));
+    }
+  }
+  CU(h, cudaMalloc(&h->Ef, ((size_t)h->N + 1) * sizeof(R)));
+  // birth staging: parent, cell (int32), off + 3 ve + 3 vi (R)
+  const size_t sc = pic::kStageCap;
+  CU(h, cudaMalloc(&h->bb_mem, sc * 8 + sc * 7 * sizeof(R)));
+  pic::BirthBuf<R> &bb = bbuf<R>(h);
+  char *b = reinterpret_cast<char *>(h->bb_mem);
+  bb.parent = reinterpret_cast<int32_t *>(b);
+  bb.cell = reinterpret_cast<int32_t *>(b + sc * 4);
+  bb.off = reinterpret_cast<R *>(b + sc * 8);
+  bb.ve = bb.off + sc;
+  bb.vi = bb.ve + 3 * sc;
+  return 0;
+}
+
+template <class R> int run_init(pic_handle *h) {
+  pic::StepK<R> &k = kparams<R>(h);
+  const pic_params &p = h->p;
+  const R sig_e = (R)std::sqrt(kQe * p.Te0_eV / kMe);
+  const R sig_i = (R)std::sqrt(kQe * p.Ti0_eV / h->M);
+  pic::launch_init<R>(k, h->sp[0], 0, p.n_e0, 0, sig_e, h->stream);
+  pic::launch_init<R>(k, h->sp[1], 1, p.n_i0, (uint64_t)p.n_e0, sig_i, h->stream);
+  pic::launch_deposit<R>(k, h->sp[0], h->ctl, 0, h->stream);
+  pic::launch_deposit<R>(k, h->sp[1], h->ctl, 1, h->stream);
+  pic::launch_field<R>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<R *>(h->Ef), h->m,
+                       h->stream);
+  pic::launch_halfstep<R>(k, h->sp[0], h->ctl, reinterpret_cast<R *>(h->Ef), 0, h->stream);
+  pic::launch_halfstep<R>(k, h->sp[1], h->ctl, reinterpret_cast<R *>(h->Ef), 1, h->stream);
+  CU(h, cudaGetLastError());
+  return 0;
+}
+
+template <class R> int enqueue_step(pic_handle *h) {
+  pic::StepK<R> &k = kparams<R>(h);
+  const int sub = h->p.ion_subcycle;
+  const bool ion_push = sub > 0 && (h->host_step % sub) == 0;
+  const R *Ef = reinterpret_cast<const R *>(h->Ef);
+  CU(h, cudaMemsetAsync(h->sp[0].Q, 0, (size_t)h->N * 8, h->stream));
+  pic::launch_push<R>(k, h->sp[0], h->ctl, Ef, bbuf<R>(h), h->m, 0, h->nsm, h->stream);
+  if (ion_push) {
+    CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->N * 8, h->stream));
+    pic::launch_push<R>(k, h->sp[1], h->ctl, Ef, bbuf<R>(h), h->m, 1, h->nsm, h->stream);
+  }
+  pic::launch_births<R>(k, h->sp[0], h->sp[1], h->ctl, bbuf<R>(h), h->sc, ion_push ? 1 : 0, h->stream);
+  pic::launch_field<R>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<R *>(h->Ef), h->m,
+                       h->stream);
+  CU(h, cudaGetLastError());
+  h->host_step++;
+  return 0;
+}
+
+void free_all(pic_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int q = 0; q < 2; ++q) {
+    cudaFree(h->sp[q].cell); cudaFree(h->sp[q].rec); cudaFree(h->sp[q].id); cudaFree(h->sp[q].code);
+    cudaFree(h->sp[q].Q); cudaFree(h->sp[q].dead); cudaFree(h->tab[q]);
+  }
+  cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->Ef); cudaFree(h->gauss);
+  cudaFree(h->bb_mem); cudaFree(h->k3_mem); cudaFree(h->mom); cudaFree(h->mom_iz);
+  if (h->stream) cudaStreamDestroy(h->stream);
+}
+
+int validate(const pic_params *p) {
+  if (!p) return set_err(nullptr, PIC_EINVAL, "params is NULL");
+  if (p->n_cells < 3) return set_err(nullptr, PIC_EINVAL, "n_cells must be >= 3");
+  if (!(p->dt_s > 0) || !(p->L_m > 0)) return set_err(nullptr, PIC_EINVAL, "dt and L must be > 0");
+  if (p->n_e0 < 0 || p->n_i0 < 0) return set_err(nullptr, PIC_EINVAL, "negative particle count");
+  if (p->n_table < 3) return set_err(nullptr, PIC_EINVAL, "n_table must be >= 3");
+  if (p->precision != PIC_FP64 && p->precision != PIC_MIXED) return set_err(nullptr, PIC_EINVAL, "bad precision");
+  if (p->loss_mode < PIC_LOSS_PAIR || p->loss_mode > PIC_LOSS_SWARM) return set_err(nullptr, PIC_EINVAL, "bad loss mode");
+  if (p->drive != PIC_DRIVE_E0 && p->drive != PIC_DRIVE_V)
+    return set_err(nullptr, PIC_EINVAL, "drive %d not supported", p->drive);
+  if (p->field_mode != PIC_FIELD_POISSON && p->field_mode != PIC_FIELD_APPLIED)
+    return set_err(nullptr, PIC_EINVAL, "bad field mode");
+  if (p->ion_subcycle < 0) return set_err(nullptr, PIC_EINVAL, "ion_subcycle < 0");
+  if (p->diag_every < 0) return set_err(nullptr, PIC_EINVAL, "diag_every < 0");
+  if (p->diag_every > 0 && p->ion_subcycle > 0 && p->diag_every % p->ion_subcycle != 0)
+    return set_err(nullptr, PIC_EINVAL, "diag_every must be a multiple of ion_subcycle");
+  if (p->n_xsec < 0 || (p->n_xsec > 0 && !p->xsec)) return set_err(nullptr, PIC_EINVAL, "bad xsec list");
+  int ne = 0, ni = 0;
+  for (int x = 0; x < p->n_xsec; ++x) {
+    const pic_xsec &xs = p->xsec[x];
+    if (xs.kind < PIC_ELASTIC || xs.kind > PIC_ION_ISO || xs.n < 1 || !xs.energy_eV || !xs.sigma_m2)
+      return set_err(nullptr, PIC_EINVAL, "bad cross section %d", x);
+    for (int i = 1; i < xs.n; ++i)
+      if (!(xs.energy_eV[i] >= xs.energy_eV[i - 1])) return set_err(nullptr, PIC_EINVAL, "xsec %d not ascending", x);
+    (is_e_kind(xs.kind) ? ne : ni)++;
+  }
+  if (ne > pic::kMaxProc || ni > pic::kMaxProc) return set_err(nullptr, PIC_EINVAL, "at most 8 processes per species");
+  if (p->n_e0 > 0 && !(p->n0_m3 > 0) && p->field_mode == PIC_FIELD_POISSON)
+    return set_err(nullptr, PIC_EINVAL, "n0 must be > 0");
+  if (!(p->eps_max_e_eV > 0) || !(p->eps_max_i_eV > 0)) return set_err(nullptr, PIC_EINVAL, "eps_max must be > 0");
+  if (p->column < 0 || p->column > 4095) return set_err(nullptr, PIC_EINVAL, "column must be in [0, 4095]");
+  return 0;
+}
+
+template <class R> int init_typed(pic_handle *h) {
+  int rc = setup_tables<R>(h);
+  if (rc) return rc;
+  rc = alloc_species<R>(h);
+  if (rc) return rc;
+  h->m.ge = h->mom; h->m.ee = h->mom + h->N; h->m.he = h->mom + 2 * h->N; h->m.gi = h->mom + 3 * h->N;
+  h->m.ne = h->mom + 4 * h->N; h->m.ni = h->mom + 5 * h->N; h->m.E = h->mom + 6 * h->N; h->m.phi = h->mom + 7 * h->N;
+  h->m.iz = h->mom_iz;
+  return run_init<R>(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_abi_version(void) { return PIC_ABI_VERSION; }
+
+const char *pic_last_error(pic_handle *h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int pic_init(const pic_params *params, pic_handle **out) {
+  if (!out) return set_err(nullptr, PIC_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(params);
+  if (rc) return rc;
+  pic_handle *h = new (std::nothrow) pic_handle();
+  if (!h) return set_err(nullptr, PIC_ENOMEM, "host allocation failed");
+  h->p = *params;  // p.xsec is caller-owned: used during pic_init only, cleared below
+  const pic_params &p = *params;
+  h->N = p.n_cells;
+  h->ntab = p.n_table;
+  h->mixed = p.precision == PIC_MIXED;
+  h->M = p.gas_mass_amu * kAmu;
+  h->ng = p.pressure_torr * kTorr / (kKb * p.T_gas_K);
+  h->dx = p.L_m / (double)p.n_cells;
+  h->w = p.n_e0 > 0 ? p.n0_m3 * p.L_m / (double)p.n_e0 : 0.0;
+  h->Cfield = (kQe * h->w) / (kEps0 * kTwo32);
+  h->E0 = p.drive == PIC_DRIVE_V ? p.V_applied / p.L_m : p.E0_Vpm;
+  h->dt_i = (double)(p.ion_subcycle > 0 ? p.ion_subcycle : 1) * p.dt_s;
+  const int64_t nmax = p.n_e0 > p.n_i0 ? p.n_e0 : p.n_i0;
+  int64_t cap = p.capacity > 0 ? p.capacity : nmax + nmax / 4 + 1024;
+  if (cap < nmax || cap > (int64_t)INT32_MAX) {
+    delete h;
+    return set_err(nullptr, PIC_EINVAL, "capacity out of range");
+  }
+  h->sp[0].cap = h->sp[1].cap = cap;
+  int dev = 0;
+  auto fail = [&](int code) {
+    free_all(h);
+    g_err = h->err.empty() ? g_err : h->err;
+    delete h;
+    return code;
+  };
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(set_err(h, PIC_ECUDA, "no CUDA device"));
+  if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(set_err(h, PIC_ECUDA, "device query failed"));
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(set_err(h, PIC_ECUDA, "stream creation failed"));
+  if (cudaMalloc(&h->ctl, sizeof(pic::Ctl)) != cudaSuccess || cudaMalloc(&h->E, (size_t)h->N * 8) != cudaSuccess ||
+      cudaMalloc(&h->Eh, (size_t)h->N * 8) != cudaSuccess ||
+      cudaMalloc(&h->gauss, (pic::kGaussN + 1) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&h->k3_mem, (size_t)pic::kStageCap * 7 * 4) != cudaSuccess ||
+      cudaMalloc(&h->mom, (size_t)h->N * 8 * 8) != cudaSuccess ||
+      cudaMalloc(&h->mom_iz, (size_t)h->N * 8) != cudaSuccess)
+    return fail(set_err(h, PIC_ENOMEM, "device allocation failed"));
+  cudaMemset(h->mom, 0, (size_t)h->N * 8 * 8);
+  cudaMemset(h->mom_iz, 0, (size_t)h->N * 8);
+  h->sc.order = h->k3_mem;
+  h->sc.cand = h->k3_mem + pic::kStageCap;
+  h->sc.att = h->k3_mem + 2 * pic::kStageCap;
+  h->sc.settled = h->k3_mem + 3 * pic::kStageCap;
+  h->sc.win = h->k3_mem + 4 * pic::kStageCap;
+  h->sc.vic = h->k3_mem + 5 * pic::kStageCap;
+  std::vector<float> T(pic::kGaussN + 1);
+  gauss_table(T.data());
+  cudaMemcpy(h->gauss, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice);
+  pic::Ctl c{};
+  c.n[0] = p.n_e0;
+  c.n[1] = p.n_i0;
+  c.step = 0;
+  c.next_id = p.n_e0 + p.n_i0;
+  c.E0 = h->E0;
+  if (cudaMemcpy(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(set_err(h, PIC_ECUDA, "control block upload failed"));
+  h->fk.N = h->N;
+  h->fk.field_mode = p.field_mode;
+  h->fk.sub = p.ion_subcycle;
+  h->fk.diag_every = 0;  // the initial solve takes no diagnostic sample
+  h->fk.Cf = h->Cfield / ((double)h->N * (double)h->N);
+  h->fk.dx = h->dx;
+  int rc2 = h->mixed ? init_typed<float>(h) : init_typed<double>(h);
+  h->p.xsec = nullptr;
+  h->p.n_xsec = 0;
+  if (rc2) return fail(rc2);
+  // the initial field solve advanced the device step counter: put it back to 0
+  c.step = 0;
+  if (cudaMemcpyAsync(&h->ctl->step, &c.step, sizeof c.step, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return fail(set_err(h, PIC_ECUDA, "reset step failed"));
+  long long zero = 0;
+  cudaMemcpyAsync(&h->ctl->m_steps, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream);
+  h->fk.diag_every = p.diag_every;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(set_err(h, PIC_ECUDA, "init failed"));
+  if (check_status(h)) return fail(h->latched);
+  *out = h;
+  return 0;
+}
+
+int pic_step(pic_handle *h, int64_t n) {
+  if (!h || n < 0) return set_err(h, PIC_EINVAL, "bad arguments");
+  if (h->latched) return h->latched;
+  for (int64_t s = 0; s < n; ++s) {
+    const int rc = h->mixed ? enqueue_step<float>(h) : enqueue_step<double>(h);
+    if (rc) return rc;
+  }
+  return check_status(h);
+}
+
+int pic_get_stats(pic_handle *h, pic_stats *out) {
+  if (!h || !out) return set_err(h, PIC_EINVAL, "bad arguments");
+  pic::Ctl c;
+  CU(h, cudaMemcpyAsync(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  memset(out, 0, sizeof *out);
+  out->step = c.step; out->n_e = c.n[0]; out->n_i = c.n[1]; out->next_id = c.next_id;
+  for (int j = 0; j < pic::kMaxProc; ++j) { out->n_coll_e[j] = (int64_t)c.n_coll[0][j]; out->n_coll_i[j] = (int64_t)c.n_coll[1][j]; }
+  out->births = (int64_t)c.births;
+  out->losses_e = (int64_t)c.losses[0]; out->losses_i = (int64_t)c.losses[1];
+  out->overflow_e = (int64_t)c.overflow[0]; out->overflow_i = (int64_t)c.overflow[1];
+  out->E0 = c.E0;
+  out->n_diag = c.n_diag;
+  return 0;
+}
+
+int pic_get_state(pic_handle *h, pic_state *o) {
+  if (!h || !o) return set_err(h, PIC_EINVAL, "bad arguments");
+  pic::Ctl c;
+  CU(h, cudaMemcpyAsync(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  o->n_e = c.n[0]; o->n_i = c.n[1]; o->step = c.step; o->next_id = c.next_id; o->E0 = c.E0;
+  int32_t *cells[2] = {o->cell_e, o->cell_i};
+  double *offs[2] = {o->off_e, o->off_i}, *vxs[2] = {o->vx_e, o->vx_i}, *vys[2] = {o->vy_e, o->vy_i},
+         *vzs[2] = {o->vz_e, o->vz_i};
+  uint64_t *ids[2] = {o->id_e, o->id_i};
+  for (int q = 0; q < 2; ++q) {
+    const int64_t n = c.n[q];
+    if (n == 0) continue;
+    if (cells[q]) CU(h, cudaMemcpy(cells[q], h->sp[q].cell, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    if (ids[q]) CU(h, cudaMemcpy(ids[q], h->sp[q].id, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    if (offs[q] || vxs[q] || vys[q] || vzs[q]) {
+      if (h->mixed) {
+        std::vector<float4> r((size_t)n);
+        CU(h, cudaMemcpy(r.data(), h->sp[q].rec, (size_t)n * 16, cudaMemcpyDeviceToHost));
+        for (int64_t p = 0; p < n; ++p) {
+          if (offs[q]) offs[q][p] = r[p].x;
+          if (vxs[q]) vxs[q][p] = r[p].y;
+          if (vys[q]) vys[q][p] = r[p].z;
+          if (vzs[q]) vzs[q][p] = r[p].w;
+        }
+      } else {
+        std::vector<pic::D4> r((size_t)n);
+        CU(h, cudaMemcpy(r.data(), h->sp[q].rec, (size_t)n * 32, cudaMemcpyDeviceToHost));
+        for (int64_t p = 0; p < n; ++p) {
+          if (offs[q]) offs[q][p] = r[p].off;
+          if (vxs[q]) vxs[q][p] = r[p].vx;
+          if (vys[q]) vys[q][p] = r[p].vy;
+          if (vzs[q]) vzs[q][p] = r[p].vz;
+        }
+      }
+    }
+  }
+  if (o->E) CU(h, cudaMemcpy(o->E, h->E, (size_t)h->N * 8, cudaMemcpyDeviceToHost));
+  if (o->Q_e) CU(h, cudaMemcpy(o->Q_e, h->sp[0].Q, (size_t)h->N * 8, cudaMemcpyDeviceToHost));
+  if (o->Q_i) CU(h, cudaMemcpy(o->Q_i, h->sp[1].Q, (size_t)h->N * 8, cudaMemcpyDeviceToHost));
+  return 0;
+}
+
+int pic_set_state(pic_handle *h, const pic_state *in) {
+  if (!h || !in) return set_err(h, PIC_EINVAL, "bad arguments");
+  if (in->n_e < 0 || in->n_i < 0 || in->n_e > h->sp[0].cap || in->n_i > h->sp[1].cap)
+    return set_err(h, PIC_EINVAL, "particle count out of range");
+  if (in->step < 0) return set_err(h, PIC_EINVAL, "step < 0");
+  CU(h, cudaStreamSynchronize(h->stream));
+  const int32_t *cells[2] = {in->cell_e, in->cell_i};
+  const double *offs[2] = {in->off_e, in->off_i}, *vxs[2] = {in->vx_e, in->vx_i}, *vys[2] = {in->vy_e, in->vy_i},
+               *vzs[2] = {in->vz_e, in->vz_i};
+  const uint64_t *ids[2] = {in->id_e, in->id_i};
+  const int64_t ns[2] = {in->n_e, in->n_i};
+  for (int q = 0; q < 2; ++q) {
+    const int64_t n = ns[q];
+    if (n == 0) continue;
+    if (!cells[q] || !offs[q] || !vxs[q] || !vys[q] || !vzs[q] || !ids[q])
+      return set_err(h, PIC_EINVAL, "missing state array");
+    for (int64_t p = 0; p < n; ++p) {
+      const double o = offs[q][p];
+      if (cells[q][p] < 0 || cells[q][p] >= h->N || !(o >= 0.0 && o < 1.0) || (h->mixed && !((float)o < 1.0f)))
+        return set_err(h, PIC_EINVAL, "particle %lld of species %d outside the grid", (long long)p, q);
+    }
+    CU(h, cudaMemcpy(h->sp[q].cell, cells[q], (size_t)n * 4, cudaMemcpyHostToDevice));
+    CU(h, cudaMemcpy(h->sp[q].id, ids[q], (size_t)n * 8, cudaMemcpyHostToDevice));
+    if (h->mixed) {
+      std::vector<float4> r((size_t)n);
+      for (int64_t p = 0; p < n; ++p)
+        r[p] = make_float4((float)offs[q][p], (float)vxs[q][p], (float)vys[q][p], (float)vzs[q][p]);
+      CU(h, cudaMemcpy(h->sp[q].rec, r.data(), (size_t)n * 16, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<pic::D4> r((size_t)n);
+      for (int64_t p = 0; p < n; ++p) r[p] = pic::D4{offs[q][p], vxs[q][p], vys[q][p], vzs[q][p]};
+      CU(h, cudaMemcpy(h->sp[q].rec, r.data(), (size_t)n * 32, cudaMemcpyHostToDevice));
+    }
+  }
+  pic::Ctl c;
+  CU(h, cudaMemcpy(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost));
+  c.n[0] = in->n_e; c.n[1] = in->n_i; c.step = in->step; c.next_id = in->next_id; c.E0 = in->E0;
+  c.status = 0; c.n_birth = 0; c.n_dead[0] = c.n_dead[1] = 0;
+  CU(h, cudaMemcpy(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+  h->latched = 0;
+  h->host_step = in->step;
+  CU(h, cudaMemset(h->sp[0].Q, 0, (size_t)h->N * 8));
+  if (h->mixed) pic::launch_deposit<float>(h->kf, h->sp[0], h->ctl, 0, h->stream);
+  else pic::launch_deposit<double>(h->kd, h->sp[0], h->ctl, 0, h->stream);
+  if (in->Q_i) {
+    CU(h, cudaMemcpyAsync(h->sp[1].Q, in->Q_i, (size_t)h->N * 8, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->N * 8, h->stream));
+    if (h->mixed) pic::launch_deposit<float>(h->kf, h->sp[1], h->ctl, 1, h->stream);
+    else pic::launch_deposit<double>(h->kd, h->sp[1], h->ctl, 1, h->stream);
+  }
+  if (in->E) {
+    CU(h, cudaMemcpyAsync(h->E, in->E, (size_t)h->N * 8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (h->mixed) {
+      std::vector<float> f((size_t)h->N + 1);
+      for (int j = 0; j < h->N; ++j) f[j] = (float)in->E[j];
+      f[h->N] = f[0];
+      CU(h, cudaMemcpy(h->Ef, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<double> f((size_t)h->N + 1);
+      for (int j = 0; j < h->N; ++j) f[j] = in->E[j];
+      f[h->N] = f[0];
+      CU(h, cudaMemcpy(h->Ef, f.data(), f.size() * 8, cudaMemcpyHostToDevice));
+    }
+  } else {
+    // solve the field of the new charges without advancing the step counter
+    pic::FieldK fk = h->fk;
+    fk.diag_every = 0;
+    if (h->mixed)
+      pic::launch_field<float>(fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<float *>(h->Ef), h->m,
+                               h->stream);
+    else
+      pic::launch_field<double>(fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<double *>(h->Ef),
+                                h->m, h->stream);
+    long long st = in->step, ms = 0;
+    CU(h, cudaMemcpyAsync(&h->ctl->step, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(&h->ctl->m_steps, &ms, sizeof ms, cudaMemcpyHostToDevice, h->stream));
+  }
+  CU(h, cudaStreamSynchronize(h->stream));
+  CU(h, cudaGetLastError());
+  return check_status(h);
+}
+
+int pic_moments(pic_handle *h, pic_moments_out *o) {
+  if (!h || !o) return set_err(h, PIC_EINVAL, "bad arguments");
+  const int N = h->N;
+  std::vector<double> acc((size_t)N * 8);
+  std::vector<unsigned long long> iz((size_t)N);
+  pic::Ctl c;
+  CU(h, cudaMemcpyAsync(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaMemcpyAsync(acc.data(), h->mom, acc.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaMemcpyAsync(iz.data(), h->mom_iz, iz.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  const double *ge = acc.data(), *ee = ge + N, *he = ge + 2 * N, *gi = ge + 3 * N, *ne = ge + 4 * N, *ni = ge + 5 * N,
+               *E = ge + 6 * N, *phi = ge + 7 * N;
+  const double ns = c.m_samples > 0 ? (double)c.m_samples : 1.0;
+  const double dens = h->w / h->dx;
+  const double tsteps = (double)(c.m_steps > 0 ? c.m_steps : 1) * h->p.dt_s;
+  o->n_samples = c.m_samples;
+  o->n_steps = c.m_steps;
+  for (int j = 0; j < N; ++j) {
+    if (o->n_e) o->n_e[j] = ne[j] / ns * dens;
+    if (o->n_i) o->n_i[j] = ni[j] / ns * dens;
+    if (o->gamma_e) o->gamma_e[j] = ge[j] / ns * dens;
+    if (o->mean_eps_e) o->mean_eps_e[j] = ne[j] > 0 ? ee[j] / ne[j] : 0.0;
+    if (o->heat_e) o->heat_e[j] = he[j] / ns * dens;
+    if (o->iz_rate) o->iz_rate[j] = (double)(long long)iz[j] * (1.0 / kTwo32) * dens / tsteps;
+    if (o->gamma_i) o->gamma_i[j] = gi[j] / ns * dens;
+    if (o->E) o->E[j] = E[j] / ns;
+    if (o->phi) o->phi[j] = phi[j] / ns;
+  }
+  if (o->reset) {
+    CU(h, cudaMemsetAsync(h->mom, 0, (size_t)N * 8 * 8, h->stream));
+    CU(h, cudaMemsetAsync(h->mom_iz, 0, (size_t)N * 8, h->stream));
+    long long z[3] = {0, 0, 0};  // m_samples, m_steps (n_diag kept)
+    CU(h, cudaMemcpyAsync(&h->ctl->m_samples, &z[0], 8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(&h->ctl->m_steps, &z[1], 8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+  }
+  return 0;
+}
+
+int pic_last_codes(pic_handle *h, int species, int32_t *out, int64_t n) {
+  if (!h || !out || species < 0 || species > 1 || n < 0 || n > h->sp[species].cap)
+    return set_err(h, PIC_EINVAL, "bad arguments");
+  if (!h->sp[species].code) return set_err(h, PIC_EINVAL, "codes need PIC_FLAG_RECORD_CODES");
+  CU(h, cudaStreamSynchronize(h->stream));
+  CU(h, cudaMemcpy(out, h->sp[species].code, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  return 0;
+}
+
+int pic_derived(pic_handle *h, double out[7]) {
+  if (!h || !out) return set_err(h, PIC_EINVAL, "bad arguments");
+  out[0] = h->ng; out[1] = h->nustar[0]; out[2] = h->Pnull[0]; out[3] = h->nustar[1]; out[4] = h->Pnull[1];
+  out[5] = h->w; out[6] = h->dx;
+  return 0;
+}
+
+void *pic_stream(pic_handle *h) { return h ? (void *)h->stream : nullptr; }
+
+void pic_free(pic_handle *h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+int pic_test_i128_to_double(const int64_t *hi, const uint64_t *lo, double *out, int n) {
+  if (!hi || !lo || !out || n < 0) return set_err(nullptr, PIC_EINVAL, "bad arguments");
+  if (n == 0) return 0;
+  int64_t *dh = nullptr;
+  uint64_t *dl = nullptr;
+  double *dout = nullptr;
+  if (cudaMalloc(&dh, (size_t)n * 8) != cudaSuccess || cudaMalloc(&dl, (size_t)n * 8) != cudaSuccess ||
+      cudaMalloc(&dout, (size_t)n * 8) != cudaSuccess) {
+    cudaFree(dh); cudaFree(dl); cudaFree(dout);
+    return set_err(nullptr, PIC_ENOMEM, "device allocation failed");
+  }
+  cudaMemcpy(dh, hi, (size_t)n * 8, cudaMemcpyHostToDevice);
+  cudaMemcpy(dl, lo, (size_t)n * 8, cudaMemcpyHostToDevice);
+  pic::launch_i128_test(dh, dl, dout, n, nullptr);
+  const cudaError_t e = cudaMemcpy(out, dout, (size_t)n * 8, cudaMemcpyDeviceToHost);
+  cudaFree(dh); cudaFree(dl); cudaFree(dout);
+  if (e != cudaSuccess) return set_err(nullptr, PIC_ECUDA, "%s", cudaGetErrorString(e));
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// Internal types shared by the host driver (pic_host.cu) and the kernels
+// (pic_kernels.cu) of the PIC-MCC library.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pic.h"
+
+namespace pic {
+
+constexpr int kMaxProc = 8;
+constexpr int kGaussN = 4096;          // Gaussian inverse-CDF intervals
+constexpr int kStageCap = 8192;        // births / radial losses staged per step and species
+constexpr int kFieldThreads = 1024;
+constexpr int kStepThreads = 1024;
+
+// device status bits
+constexpr unsigned kStBirthOverflow = 1u;
+constexpr unsigned kStCapacity = 2u;
+constexpr unsigned kStNonFinite = 4u;
+constexpr unsigned kStDeadOverflow = 8u;
+constexpr unsigned kStVictim = 16u;
+
+// random-number streams (counter word 3 = stream<<28 | column<<16 | block)
+enum Stream : uint32_t { kStE = 0, kStI = 1, kStInitE = 2, kStInitI = 3, kStVicE = 4, kStVicI = 5 };
+
+// FP64 particle record (offset in cell, velocity); MIXED uses float4 with the same order
+struct alignas(32) D4 { double off, vx, vy, vz; };
+
+template <class R> struct Rec;
+template <> struct Rec<double> { using T = D4; };
+template <> struct Rec<float> { using T = float4; };
+
+// device control block
+struct Ctl {
+  long long n[2];          // live particles per species
+  long long step;          // steps taken
+  long long next_id;
+  double E0;
+  unsigned int status;
+  int n_birth;             // staged births of the current step
+  int n_dead[2];           // staged radial losses
+  int pad;
+  unsigned long long n_coll[2][kMaxProc];
+  unsigned long long births, losses[2], overflow[2];
+  long long n_diag, m_samples, m_steps;
+};
+
+struct SpeciesDev {
+  int32_t *cell;
+  void *rec;               // D4 or float4 records
+  uint64_t *id;
+  int32_t *code;           // optional per-particle process code
+  unsigned long long *Q;   // node charge (fixed point, two's complement)
+  int32_t *dead;           // staged radial losses (kStageCap)
+  int64_t cap;
+};
+
+template <class R> struct SpecK {
+  R a, d, K, inv_de, P, nus;      // kick q dt/m, drift dt/dx, energy m/2e, 1/deps, P_null, nu*
+  uint32_t Pw;                    // radial loss threshold on a 32-bit word
+  int np;
+  int kind[kMaxProc];
+  int xs[kMaxProc];               // index of the process in the caller's xsec list
+  R thr[kMaxProc];
+  const R *tab;                   // np x ntab collision frequencies
+};
+
+template <class R> struct StepK {
+  int N, ntab, loss_mode, field_mode;
+  unsigned flags;
+  int diag_every, sub;
+  uint32_t column;
+  uint64_t seed;
+  R V_e, em, sig_n;               // 2e/m, 2m/M, sqrt(kT_g/M)
+  const float *gauss;             // kGaussN+1 entries
+  SpecK<R> sp[2];
+};
+
+template <class R> struct BirthBuf {
+  int32_t *parent, *cell;
+  R *off, *ve, *vi;               // ve, vi: 3 * kStageCap (component-major)
+};
+
+struct Moments {
+  double *ge, *ee, *he, *gi, *ne, *ni, *E, *phi;
+  unsigned long long *iz;
+};
+
+struct K3Scratch {
+  uint32_t *order;   // births sorted by parent slot -> staging index
+  uint32_t *cand, *att, *settled, *win;
+  uint32_t *vic;     // 2 * kStageCap victim slots (electrons, ions)
+};
+
+struct FieldK {
+  int N, field_mode, sub, diag_every;
+  double Cf;          // e w / (eps0 2^32 N^2)
+  double dx;
+};
+
+// launchers (pic_kernels.cu)
+template <class R>
+void launch_init(const StepK<R> &k, SpeciesDev s, int species, int64_t n, uint64_t id0, R sig, cudaStream_t st);
+template <class R>
+void launch_deposit(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, int species, cudaStream_t st);
+template <class R>
+void launch_halfstep(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, const R *Ef, int species, cudaStream_t st);
+template <class R>
+void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBuf<R> bb, Moments m,
+                 int species, int nsm, cudaStream_t st);
+template <class R>
+void launch_births(const StepK<R> &k, SpeciesDev e, SpeciesDev i, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
+                   int ion_pushed, cudaStream_t st);
+template <class R>
+void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned long long *Qi, Ctl *ctl,
+                  double *E, double *Eh, R *Ef, Moments m, cudaStream_t st);
+void launch_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n, cudaStream_t st);
+template <class R> int push_smem_bytes(int N);
+
+}  // namespace pic

@@ -1,0 +1,804 @@
+// CUDA kernels of the 1D3V electrostatic PIC-MCC positive-column step
+// (Boeuf, Sec. II), written for sm_103a.
+//
+//   k_push      field gather, leapfrog push, periodic wrap, null-collision MCC,
+//               radial-loss flag, birth staging, cloud-in-cell deposit into
+//               shared-memory 64-bit fixed-point bins (one persistent CTA per SM)
+//   k_births    ionization births and the paired random removal (or radial
+//               losses with compaction); one CTA
+//   k_field     periodic Poisson solve by the exact integer route; one CTA
+//   k_init / k_deposit / k_halfstep   initial state
+#include <cstdint>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <class R> __device__ __forceinline__ void rec_load(const void *base, long long p, R &off, R &vx, R &vy, R &vz) {
+  if constexpr (std::is_same<R, float>::value) {
+    const float4 r = __ldcs(reinterpret_cast<const float4 *>(base) + p);
+    off = r.x; vx = r.y; vy = r.z; vz = r.w;
+  } else {
+    const double2 *q = reinterpret_cast<const double2 *>(reinterpret_cast<const D4 *>(base) + p);
+    const double2 a = __ldcs(q), b = __ldcs(q + 1);
+    off = a.x; vx = a.y; vy = b.x; vz = b.y;
+  }
+}
+template <class R> __device__ __forceinline__ void rec_store(void *base, long long p, R off, R vx, R vy, R vz) {
+  if constexpr (std::is_same<R, float>::value) {
+    __stcs(reinterpret_cast<float4 *>(base) + p, make_float4(off, vx, vy, vz));
+  } else {
+    double2 *q = reinterpret_cast<double2 *>(reinterpret_cast<D4 *>(base) + p);
+    __stcs(q, make_double2(off, vx));
+    __stcs(q + 1, make_double2(vy, vz));
+  }
+}
+template <class R> __device__ __forceinline__ R rec_get_off(const void *base, long long p) {
+  if constexpr (std::is_same<R, float>::value) return reinterpret_cast<const float4 *>(base)[p].x;
+  else return reinterpret_cast<const D4 *>(base)[p].off;
+}
+
+// signed fixed-point deposit straight to global memory (births, removals, init)
+template <class R>
+__device__ __forceinline__ void dep_global(unsigned long long *Q, int N, int32_t cell, R off, bool add) {
+  const unsigned long long k = wfix(off);
+  unsigned long long a = (1ull << 32) - k, b = k;
+  if (!add) { a = 0ull - a; b = 0ull - b; }
+  const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+  atomicAdd(Q + cell, a);
+  atomicAdd(Q + c1, b);
+}
+
+template <class R> __device__ __forceinline__ int64_t pow2ceil(int64_t n) {
+  int64_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+__device__ void bitonic_sort(unsigned long long *a, int n2) {
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const unsigned long long x = a[i], y = a[ixj];
+          if ((x > y) == up) { a[i] = y; a[ixj] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Particle step.  One persistent CTA per SM walks a contiguous slot range.
+// Shared memory: the node field (N+1 values) and 64-bit fixed-point charge
+// bins over a cell window (the whole grid when it fits).
+template <class R, int SP>
+__global__ void __launch_bounds__(kStepThreads, 1)
+k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef, BirthBuf<R> bb,
+       Moments m, int W, int smemE) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int s_cnt[kMaxProc + 1];
+  const int N = k.N;
+  const SpecK<R> &sp = k.sp[SP];
+  const size_t eb = smemE ? ((((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15) : 0;
+  R *sE = reinterpret_cast<R *>(smem);
+  unsigned long long *bins = reinterpret_cast<unsigned long long *>(smem + eb);
+  const long long n = ctl->n[SP];
+  const long long stepll = ctl->step;
+  const uint32_t step = (uint32_t)stepll;
+  const bool diag = k.diag_every > 0 && (stepll % k.diag_every) == 0;
+  const uint2 key = seed_key(k.seed);
+  const uint32_t c3 = ((SP == 0 ? (uint32_t)kStE : (uint32_t)kStI) << 28) | (k.column << 16);
+  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  const long long p0 = (long long)blockIdx.x * chunk;
+  const long long p1 = min(n, p0 + chunk);
+  int c0 = 0;
+  if (W < N && p0 < p1) {
+    c0 = s.cell[p0] - W / 16;
+    if (c0 < 0) c0 += N;
+  }
+  if (smemE)
+    for (int j = threadIdx.x; j <= N; j += blockDim.x) sE[j] = Ef[j];
+  for (int j = threadIdx.x; j < W; j += blockDim.x) bins[j] = 0ull;
+  if (threadIdx.x <= kMaxProc) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  const R *E = smemE ? sE : Ef;
+  const int lane = threadIdx.x & 31;
+  const bool radial = k.loss_mode == PIC_LOSS_RADIAL;
+  const bool record = (k.flags & PIC_FLAG_RECORD_CODES) != 0;
+
+  for (long long base = p0; base < p1; base += blockDim.x) {
+    const long long p = base + threadIdx.x;
+    const bool valid = p < p1;
+    int sel = -1;
+    bool ovf = false;
+    if (valid) {
+      int32_t cell = s.cell[p];
+      R off, vx, vy, vz;
+      rec_load<R>(s.rec, p, off, vx, vy, vz);
+      const uint64_t id = s.id[p];
+      const R Ep = gather(E, cell, off);
+      push<R>(N, sp.a, sp.d, Ep, cell, off, vx);
+      const uint4 w0 = philox10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, c3), key);
+      int code = -1;
+      const bool dead = radial && (w0.z < sp.Pw);
+      if (!dead) {
+        const R u0 = u_dec<R>(w0.x), u1 = u_dec<R>(w0.y);
+        if (u0 < sp.P) {
+          UStream<R> us(key, id, step, c3);
+          if constexpr (SP == 0) {
+            // electron-neutral: elastic, excitation levels, ionization (Sec. II)
+            const R eps = sp.K * (vx * vx + vy * vy + vz * vz);
+            R fr;
+            const int it = tab_pos(eps, sp.inv_de, k.ntab, fr, ovf);
+            const R r = u1 * sp.nus;
+            R cum = 0;
+            for (int q = 0; q < sp.np; ++q) {
+              R nu;
+              if (sp.kind[q] != PIC_ELASTIC && eps < sp.thr[q]) nu = 0;
+              else nu = tab_at(sp.tab + (size_t)q * k.ntab, it, fr);
+              cum = cum + nu;
+              if (r < cum) { sel = q; break; }
+            }
+            if (sel >= 0) {
+              const int kind = sp.kind[sel];
+              code = sp.xs[sel];
+              R nx, ny, nz;
+              if (kind == PIC_ELASTIC) {
+                iso_dir(us, nx, ny, nz);
+                const R vm = sqrt(vx * vx + vy * vy + vz * vz);
+                const R cosx = (vm > (R)0) ? (nx * vx + ny * vy + nz * vz) / vm : (R)0;
+                const R e2 = eps * ((R)1 - k.em * ((R)1 - cosx));
+                const R spd = sqrt(e2 * k.V_e);
+                vx = spd * nx; vy = spd * ny; vz = spd * nz;
+              } else if (kind == PIC_EXCITATION) {
+                const R e2 = eps - sp.thr[sel];
+                iso_dir(us, nx, ny, nz);
+                const R spd = sqrt(e2 * k.V_e);
+                vx = spd * nx; vy = spd * ny; vz = spd * nz;
+              } else {
+                const R er = eps - sp.thr[sel];
+                const R ush = us.next();
+                const R e_ej = ush * er;
+                const R e_sc = er - e_ej;
+                iso_dir(us, nx, ny, nz);
+                const R spd = sqrt(e_sc * k.V_e);
+                vx = spd * nx; vy = spd * ny; vz = spd * nz;
+                R mx, my, mz;
+                iso_dir(us, mx, my, mz);
+                const R sq = sqrt(e_ej * k.V_e);
+                const R g0 = gauss<R>(k.gauss, us.next());
+                const R g1 = gauss<R>(k.gauss, us.next());
+                const R g2 = gauss<R>(k.gauss, us.next());
+                if (k.loss_mode != PIC_LOSS_SWARM) {
+                  const int idx = atomicAdd(&ctl->n_birth, 1);
+                  if (idx < kStageCap) {
+                    bb.parent[idx] = (int32_t)p;
+                    bb.cell[idx] = cell;
+                    bb.off[idx] = off;
+                    bb.ve[idx] = sq * mx; bb.ve[kStageCap + idx] = sq * my; bb.ve[2 * kStageCap + idx] = sq * mz;
+                    bb.vi[idx] = k.sig_n * g0; bb.vi[kStageCap + idx] = k.sig_n * g1;
+                    bb.vi[2 * kStageCap + idx] = k.sig_n * g2;
+                  } else {
+                    atomicOr(&ctl->status, kStBirthOverflow);
+                  }
+                } else {
+                  atomicAdd(&ctl->births, 1ull);
+                }
+                const unsigned long long kk = wfix(off);
+                const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+                atomicAdd(m.iz + cell, (1ull << 32) - kk);
+                atomicAdd(m.iz + c1, kk);
+              }
+            }
+          } else {
+            // ion-neutral: neutral velocity from the gas Maxwellian, relative speed g,
+            // charge exchange or isotropic elastic in the centre-of-mass frame
+            const R g0 = gauss<R>(k.gauss, us.next());
+            const R g1 = gauss<R>(k.gauss, us.next());
+            const R g2 = gauss<R>(k.gauss, us.next());
+            const R nvx = k.sig_n * g0, nvy = k.sig_n * g1, nvz = k.sig_n * g2;
+            const R gx = vx - nvx, gy = vy - nvy, gz = vz - nvz;
+            const R eg = sp.K * (gx * gx + gy * gy + gz * gz);
+            R fr;
+            const int it = tab_pos(eg, sp.inv_de, k.ntab, fr, ovf);
+            const R r = u1 * sp.nus;
+            R cum = 0;
+            for (int q = 0; q < sp.np; ++q) {
+              cum = cum + tab_at(sp.tab + (size_t)q * k.ntab, it, fr);
+              if (r < cum) { sel = q; break; }
+            }
+            if (sel >= 0) {
+              code = sp.xs[sel];
+              if (sp.kind[sel] == PIC_ION_CX) {
+                vx = nvx; vy = nvy; vz = nvz;
+              } else {
+                R nx, ny, nz;
+                iso_dir(us, nx, ny, nz);
+                const R gm = sqrt(gx * gx + gy * gy + gz * gz);
+                const R hg = (R)0.5 * gm;
+                vx = (R)0.5 * (vx + nvx) + hg * nx;
+                vy = (R)0.5 * (vy + nvy) + hg * ny;
+                vz = (R)0.5 * (vz + nvz) + hg * nz;
+              }
+            }
+          }
+        }
+      } else {
+        code = -2;
+      }
+      s.cell[p] = cell;
+      rec_store<R>(s.rec, p, off, vx, vy, vz);
+      if (record) s.code[p] = code;
+      if (dead) {
+        const int idx = atomicAdd(&ctl->n_dead[SP], 1);
+        if (idx < kStageCap) s.dead[idx] = (int32_t)p;
+        else atomicOr(&ctl->status, kStDeadOverflow);
+      } else {
+        const unsigned long long kk = wfix(off);
+        const unsigned long long a = (1ull << 32) - kk;
+        const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+        if (W == N) {
+          atomicAdd(bins + cell, a);
+          atomicAdd(bins + c1, kk);
+        } else {
+          int li = cell - c0;
+          if (li < 0) li += N;
+          if (li < W - 1) {
+            atomicAdd(bins + li, a);
+            atomicAdd(bins + li + 1, kk);
+          } else {
+            atomicAdd(s.Q + cell, a);
+            atomicAdd(s.Q + c1, kk);
+          }
+        }
+        if (diag) {
+          const double w1 = (double)kk * (1.0 / 4294967296.0), w0 = 1.0 - w1;
+          const double vxd = (double)vx;
+          if constexpr (SP == 0) {
+            const double eps = (double)(sp.K * (vx * vx + vy * vy + vz * vz));
+            atomicAdd(m.ge + cell, w0 * vxd); atomicAdd(m.ge + c1, w1 * vxd);
+            atomicAdd(m.ee + cell, w0 * eps); atomicAdd(m.ee + c1, w1 * eps);
+            const double h = eps * vxd;
+            atomicAdd(m.he + cell, w0 * h); atomicAdd(m.he + c1, w1 * h);
+          } else {
+            atomicAdd(m.gi + cell, w0 * vxd); atomicAdd(m.gi + c1, w1 * vxd);
+          }
+        }
+      }
+    }
+    // warp-aggregated collision counters
+    for (int q = 0; q < sp.np; ++q) {
+      const unsigned b = __ballot_sync(kFull, sel == q);
+      if (lane == 0 && b) atomicAdd(&s_cnt[q], (unsigned)__popc(b));
+    }
+    const unsigned bo = __ballot_sync(kFull, ovf);
+    if (lane == 0 && bo) atomicAdd(&s_cnt[kMaxProc], (unsigned)__popc(bo));
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < W; j += blockDim.x) {
+    const unsigned long long v = bins[j];
+    if (v) {
+      int node = j;
+      if (W < N) { node = c0 + j; if (node >= N) node -= N; }
+      atomicAdd(s.Q + node, v);
+    }
+  }
+  if (threadIdx.x < sp.np && s_cnt[threadIdx.x])
+    atomicAdd(&ctl->n_coll[SP][threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+  if (threadIdx.x == 0 && s_cnt[kMaxProc]) atomicAdd(&ctl->overflow[SP], (unsigned long long)s_cnt[kMaxProc]);
+}
+
+template <class R> int push_smem_bytes(int N) {
+  const size_t e = (((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15;
+  return (int)e;
+}
+
+template <class R>
+void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBuf<R> bb, Moments m, int species,
+                 int nsm, cudaStream_t st) {
+  const size_t budget = 200 * 1024;
+  size_t eb = (((size_t)k.N + 1) * sizeof(R) + 15) & ~(size_t)15;
+  int smemE = eb <= 128 * 1024 ? 1 : 0;
+  if (!smemE) eb = 0;
+  size_t wmax = (budget - eb) / 8;
+  int W = (int)((size_t)k.N < wmax ? (size_t)k.N : wmax);
+  if (W < (int)k.N) W &= ~63;
+  const size_t bytes = eb + (size_t)W * 8;
+  if (species == 0) {
+    cudaFuncSetAttribute(k_push<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_push<R, 0><<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
+  } else {
+    cudaFuncSetAttribute(k_push<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    k_push<R, 1><<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Births and losses (one CTA).  Births are ordered by parent slot; event k
+// gets ids next_id + 2k (electron) and next_id + 2k + 1 (ion).
+
+__device__ __forceinline__ uint32_t victim_draw(uint2 key, uint32_t k, uint32_t att, uint32_t step, uint32_t c3,
+                                                unsigned long long npre) {
+  const uint4 w = philox10(make_uint4(k, att, step, c3), key);
+  const unsigned long long r = ((unsigned long long)w.y << 32) | (unsigned long long)w.x;
+  return (uint32_t)__umul64hi(r, npre);
+}
+
+// Victims without replacement, in rounds: an unsettled event settles iff no
+// settled event holds its candidate and no lower unsettled event shares it.
+__device__ bool draw_victims(uint2 key, uint32_t step, uint32_t c3, int nb, long long npre, unsigned long long *keys,
+                             K3Scratch sc, uint32_t *out) {
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    sc.att[t] = 0u;
+    sc.settled[t] = 0u;
+    sc.cand[t] = victim_draw(key, (uint32_t)t, 0u, step, c3, (unsigned long long)npre);
+  }
+  __syncthreads();
+  const int n2 = (int)pow2ceil<float>(nb);
+  for (int round = 0; round < 64; ++round) {
+    for (int t = threadIdx.x; t < n2; t += blockDim.x)
+      keys[t] = t < nb ? (((unsigned long long)sc.cand[t] << 32) | ((sc.settled[t] ? 0ull : 1ull) << 31) |
+                          (unsigned long long)t)
+                       : ~0ull;
+    __syncthreads();
+    bitonic_sort(keys, n2);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      const unsigned long long kk = keys[i];
+      if ((kk >> 31) & 1ull) {
+        const uint32_t ev = (uint32_t)(kk & 0x7fffffffull);
+        sc.win[ev] = (i == 0 || (keys[i - 1] >> 32) != (kk >> 32)) ? 1u : 0u;
+      }
+    }
+    __syncthreads();
+    int any = 0;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      if (!sc.settled[t]) {
+        if (sc.win[t]) sc.settled[t] = 1u;
+        else {
+          sc.att[t] += 1u;
+          sc.cand[t] = victim_draw(key, (uint32_t)t, sc.att[t], step, c3, (unsigned long long)npre);
+          any = 1;
+        }
+      }
+    }
+    if (!__syncthreads_or(any)) {
+      for (int t = threadIdx.x; t < nb; t += blockDim.x) out[t] = sc.cand[t];
+      __syncthreads();
+      return true;
+    }
+  }
+  return false;
+}
+
+template <class R>
+__device__ void write_newborn(SpeciesDev s, long long slot, int32_t cell, R off, R vx, R vy, R vz, uint64_t id, int N) {
+  s.cell[slot] = cell;
+  rec_store<R>(s.rec, slot, off, vx, vy, vz);
+  s.id[slot] = id;
+  dep_global<R>(s.Q, N, cell, off, true);
+}
+
+template <class R>
+__device__ void copy_particle(SpeciesDev s, long long dst, long long src) {
+  s.cell[dst] = s.cell[src];
+  using T = typename Rec<R>::T;
+  reinterpret_cast<T *>(s.rec)[dst] = reinterpret_cast<const T *>(s.rec)[src];
+  s.id[dst] = s.id[src];
+}
+
+// radial mode: births fill the dead slots (ascending); extra births are
+// appended; extra holes below N_new take the live tail particles in order
+template <class R>
+__device__ void fill_compact(const StepK<R> &k, SpeciesDev s, Ctl *ctl, int SP, BirthBuf<R> bb, K3Scratch sc, int nb,
+                             int nd, long long next_id, unsigned long long *keys, int *s_scan) {
+  const int N = k.N;
+  const long long Nold = ctl->n[SP];
+  const int n2 = (int)pow2ceil<float>(nd);
+  for (int t = threadIdx.x; t < n2; t += blockDim.x)
+    keys[t] = t < nd ? (unsigned long long)(uint32_t)s.dead[t] : ~0ull;
+  __syncthreads();
+  if (nd > 1) bitonic_sort(keys, n2);
+  const int m = nb < nd ? nb : nd;
+  const R *bv = SP == 0 ? bb.ve : bb.vi;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    const uint32_t b = sc.order[t];
+    write_newborn<R>(s, (long long)keys[t], bb.cell[b], bb.off[b], bv[b], bv[kStageCap + b], bv[2 * kStageCap + b],
+                     (uint64_t)next_id + 2ull * (uint64_t)t + (uint64_t)SP, N);
+  }
+  long long Nnew = Nold;
+  if (nb > nd) {
+    Nnew = Nold + (nb - nd);
+    if (Nnew > s.cap) {
+      if (threadIdx.x == 0) atomicOr(&ctl->status, kStCapacity);
+      Nnew = Nold;
+    } else {
+      for (int t = m + threadIdx.x; t < nb; t += blockDim.x) {
+        const uint32_t b = sc.order[t];
+        write_newborn<R>(s, Nold + (t - m), bb.cell[b], bb.off[b], bv[b], bv[kStageCap + b], bv[2 * kStageCap + b],
+                         (uint64_t)next_id + 2ull * (uint64_t)t + (uint64_t)SP, N);
+      }
+    }
+  } else if (nd > nb) {
+    Nnew = Nold - (nd - nb);
+    // q = number of remaining holes below Nnew (keys[nb..nd) ascending)
+    __shared__ int s_q;
+    if (threadIdx.x == 0) {
+      int lo = nb, hi = nd;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)keys[mid] < Nnew) lo = mid + 1; else hi = mid;
+      }
+      s_q = lo - nb;
+    }
+    __syncthreads();
+    const int q = s_q;
+    const int T = nd - nb;
+    int carry = 0;
+    for (int c0 = 0; c0 < T; c0 += blockDim.x) {
+      const int i = c0 + threadIdx.x;
+      int live = 0;
+      long long t = Nnew + i;
+      if (i < T) {
+        int lo = nb + q, hi = nd;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if ((long long)keys[mid] < t) lo = mid + 1; else hi = mid;
+        }
+        live = !(lo < nd && (long long)keys[lo] == t);
+      }
+      s_scan[threadIdx.x] = live;
+      __syncthreads();
+      for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const int v = threadIdx.x >= (unsigned)off ? s_scan[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_scan[threadIdx.x] += v;
+        __syncthreads();
+      }
+      const int incl = s_scan[threadIdx.x];
+      if (live) copy_particle<R>(s, (long long)keys[nb + carry + incl - 1], t);
+      const int tot = s_scan[blockDim.x - 1];
+      __syncthreads();
+      carry += tot;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ctl->n[SP] = Nnew;
+}
+
+template <class R>
+__global__ void __launch_bounds__(1024, 1)
+k_births(const __grid_constant__ StepK<R> k, SpeciesDev e, SpeciesDev ion, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
+         int ion_pushed) {
+  extern __shared__ __align__(16) unsigned long long keys[];   // kStageCap
+  __shared__ int s_scan[1024];
+  const int N = k.N;
+  int nb = ctl->n_birth;
+  if (nb > kStageCap) nb = kStageCap;
+  int nde = ctl->n_dead[0], ndi = ion_pushed ? ctl->n_dead[1] : 0;
+  if (nde > kStageCap) nde = kStageCap;
+  if (ndi > kStageCap) ndi = kStageCap;
+  const long long next_id = ctl->next_id;
+  const uint32_t step = (uint32_t)ctl->step;
+  const uint2 key = seed_key(k.seed);
+  // births in parent-slot order
+  if (nb > 0) {
+    const int n2 = (int)pow2ceil<float>(nb);
+    for (int t = threadIdx.x; t < n2; t += blockDim.x)
+      keys[t] = t < nb ? (((unsigned long long)(uint32_t)bb.parent[t] << 32) | (unsigned long long)t) : ~0ull;
+    __syncthreads();
+    bitonic_sort(keys, n2);
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) sc.order[t] = (uint32_t)keys[t];
+    __syncthreads();
+  }
+  if (k.loss_mode == PIC_LOSS_PAIR) {
+    if (nb > 0) {
+      const long long npe = ctl->n[0], npi = ctl->n[1];
+      bool ok = nb <= npe && nb <= npi;
+      if (ok) ok = draw_victims(key, step, ((uint32_t)kStVicE << 28) | (k.column << 16), nb, npe, keys, sc, sc.vic);
+      if (ok)
+        ok = draw_victims(key, step, ((uint32_t)kStVicI << 28) | (k.column << 16), nb, npi, keys, sc,
+                          sc.vic + kStageCap);
+      if (!ok) {
+        if (threadIdx.x == 0) atomicOr(&ctl->status, kStVictim);
+      } else {
+        for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+          const uint32_t b = sc.order[t];
+          const long long ve = sc.vic[t], vi = sc.vic[kStageCap + t];
+          dep_global<R>(e.Q, N, e.cell[ve], rec_get_off<R>(e.rec, ve), false);
+          write_newborn<R>(e, ve, bb.cell[b], bb.off[b], bb.ve[b], bb.ve[kStageCap + b], bb.ve[2 * kStageCap + b],
+                           (uint64_t)next_id + 2ull * (uint64_t)t, N);
+          dep_global<R>(ion.Q, N, ion.cell[vi], rec_get_off<R>(ion.rec, vi), false);
+          write_newborn<R>(ion, vi, bb.cell[b], bb.off[b], bb.vi[b], bb.vi[kStageCap + b], bb.vi[2 * kStageCap + b],
+                           (uint64_t)next_id + 2ull * (uint64_t)t + 1ull, N);
+        }
+        if (threadIdx.x == 0) { ctl->losses[0] += nb; ctl->losses[1] += nb; }
+      }
+    }
+  } else if (k.loss_mode == PIC_LOSS_RADIAL) {
+    fill_compact<R>(k, e, ctl, 0, bb, sc, nb, nde, next_id, keys, s_scan);
+    __syncthreads();
+    fill_compact<R>(k, ion, ctl, 1, bb, sc, nb, ndi, next_id, keys, s_scan);
+    if (threadIdx.x == 0) { ctl->losses[0] += nde; ctl->losses[1] += ndi; }
+  } else if (k.loss_mode == PIC_LOSS_NONE) {
+    const long long ne = ctl->n[0], ni = ctl->n[1];
+    if (ne + nb > e.cap || ni + nb > ion.cap) {
+      if (threadIdx.x == 0) atomicOr(&ctl->status, kStCapacity);
+    } else {
+      for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        const uint32_t b = sc.order[t];
+        write_newborn<R>(e, ne + t, bb.cell[b], bb.off[b], bb.ve[b], bb.ve[kStageCap + b], bb.ve[2 * kStageCap + b],
+                         (uint64_t)next_id + 2ull * (uint64_t)t, N);
+        write_newborn<R>(ion, ni + t, bb.cell[b], bb.off[b], bb.vi[b], bb.vi[kStageCap + b], bb.vi[2 * kStageCap + b],
+                         (uint64_t)next_id + 2ull * (uint64_t)t + 1ull, N);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) { ctl->n[0] = ne + nb; ctl->n[1] = ni + nb; }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (k.loss_mode != PIC_LOSS_SWARM) {
+      ctl->next_id = next_id + 2 * (long long)nb;
+      ctl->births += (unsigned long long)nb;
+    }
+    ctl->n_birth = 0;
+    ctl->n_dead[0] = 0;
+    ctl->n_dead[1] = 0;
+  }
+}
+
+template <class R>
+void launch_births(const StepK<R> &k, SpeciesDev e, SpeciesDev i, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
+                   int ion_pushed, cudaStream_t st) {
+  const int bytes = kStageCap * 8;
+  cudaFuncSetAttribute(k_births<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  k_births<R><<<1, 1024, bytes, st>>>(k, e, i, ctl, bb, sc, ion_pushed);
+}
+
+// ---------------------------------------------------------------------------
+// Field (one CTA).  Gauss's law on the grid with zero-mean space-charge field
+// and the uniform background removed (Sec. II, E = -E0 + E_sp):
+//   D_j = Q_i,j - Q_e,j,  T = sum D,  S'_j = N sum_{k<=j} D_k - (j+1) T,
+//   M = sum S'_j,  E_{j+1/2} = (N S'_j - M) Cf,  Cf = e w / (eps0 2^32 N^2),
+//   E_j = (E_{j-1/2} + E_{j+1/2}) / 2 - E0.
+// The numerator is an exact 128-bit integer, rounded once to double.
+
+__device__ double i128_to_double(__int128 v) {
+  if (v == 0) return 0.0;
+  const bool neg = v < 0;
+  const unsigned __int128 u = neg ? (unsigned __int128)0 - (unsigned __int128)v : (unsigned __int128)v;
+  const unsigned long long hi = (unsigned long long)(u >> 64);
+  double d;
+  if (hi == 0) {
+    d = __ull2double_rn((unsigned long long)u);
+  } else {
+    const int sh = 64 - __clzll((long long)hi);          // bits dropped below the top 64
+    const unsigned long long top = (unsigned long long)(u >> sh);
+    const unsigned __int128 rest = u - ((unsigned __int128)top << sh);
+    const unsigned long long t = top | (rest != 0 ? 1ull : 0ull);   // sticky bit below the rounding point
+    d = __ull2double_rn(t) * __longlong_as_double((long long)(1023 + sh) << 52);
+  }
+  return neg ? -d : d;
+}
+
+__device__ __int128 block_excl_scan_i128(__int128 v, __int128 *sh, __int128 &total) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const __int128 x = t >= off ? sh[t - off] : (__int128)0;
+    __syncthreads();
+    sh[t] += x;
+    __syncthreads();
+  }
+  const __int128 incl = sh[t];
+  total = sh[blockDim.x - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+__device__ double block_excl_scan_f64(double v, double *sh, double &total) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const double x = t >= off ? sh[t - off] : 0.0;
+    __syncthreads();
+    sh[t] += x;
+    __syncthreads();
+  }
+  const double incl = sh[t];
+  total = sh[blockDim.x - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kFieldThreads, 1)
+k_field(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi, Ctl *ctl,
+        double *E, double *Eh, R *Ef, Moments m) {
+  __shared__ __int128 sh[kFieldThreads];
+  const int N = f.N;
+  const int t = threadIdx.x;
+  const int seg = (N + blockDim.x - 1) / blockDim.x;
+  const int j0 = min(N, t * seg), j1 = min(N, j0 + seg);
+  const long long stepll = ctl->step;
+  const bool diag = f.diag_every > 0 && (stepll % f.diag_every) == 0;
+  const double E0 = ctl->E0;
+  bool bad = false;
+  if (f.field_mode == PIC_FIELD_APPLIED) {
+    for (int j = j0; j < j1; ++j) { Eh[j] = 0.0; E[j] = -E0; }
+  } else {
+    __int128 loc = 0;
+    for (int j = j0; j < j1; ++j) loc += (__int128)((long long)Qi[j] - (long long)Qe[j]);
+    __int128 T;
+    const __int128 pre = block_excl_scan_i128(loc, sh, T);
+    const __int128 Nn = (__int128)N;
+    __int128 run = pre, Mloc = 0;
+    for (int j = j0; j < j1; ++j) {
+      run += (__int128)((long long)Qi[j] - (long long)Qe[j]);
+      Mloc += Nn * run - (__int128)(j + 1) * T;
+    }
+    __int128 M;
+    (void)block_excl_scan_i128(Mloc, sh, M);
+    run = pre;
+    for (int j = j0; j < j1; ++j) {
+      run += (__int128)((long long)Qi[j] - (long long)Qe[j]);
+      const __int128 Sp = Nn * run - (__int128)(j + 1) * T;
+      Eh[j] = i128_to_double(Nn * Sp - M) * f.Cf;
+    }
+    __syncthreads();
+    const double Eapp = -E0;
+    for (int j = j0; j < j1; ++j) {
+      const double left = Eh[j == 0 ? N - 1 : j - 1];
+      E[j] = 0.5 * (left + Eh[j]) + Eapp;
+    }
+  }
+  for (int j = j0; j < j1; ++j) {
+    if (!isfinite(E[j])) bad = true;
+    Ef[j] = (R)E[j];
+  }
+  __syncthreads();
+  if (t == 0) Ef[N] = Ef[0];
+  if (__syncthreads_or(bad) && t == 0) atomicOr(&ctl->status, kStNonFinite);
+  if (diag) {
+    // phi_j = -dx sum_{k<j} E_{k+1/2} (space-charge potential, phi_0 = 0)
+    double loc = 0.0;
+    for (int j = j0; j < j1; ++j) loc += Eh[j];
+    double tot;
+    double *shd = reinterpret_cast<double *>(sh);
+    const double pre = block_excl_scan_f64(loc, shd, tot);
+    double run = pre;
+    for (int j = j0; j < j1; ++j) {
+      m.phi[j] += -f.dx * run;
+      run += Eh[j];
+      m.ne[j] += (double)(long long)Qe[j] * (1.0 / 4294967296.0);
+      m.ni[j] += (double)(long long)Qi[j] * (1.0 / 4294967296.0);
+      m.E[j] += E[j];
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    ctl->step = stepll + 1;
+    ctl->m_steps += 1;
+    if (diag) { ctl->m_samples += 1; ctl->n_diag += 1; }
+  }
+}
+
+template <class R>
+void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned long long *Qi, Ctl *ctl, double *E,
+                  double *Eh, R *Ef, Moments m, cudaStream_t st) {
+  k_field<R><<<1, kFieldThreads, 0, st>>>(f, Qe, Qi, ctl, E, Eh, Ef, m);
+}
+
+__global__ void k_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const __int128 v = (__int128)(((unsigned __int128)(uint64_t)hi[i] << 64) | (unsigned __int128)lo[i]);
+    out[i] = i128_to_double(v);
+  }
+}
+
+void launch_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n, cudaStream_t st) {
+  k_i128_test<<<(n + 255) / 256, 256, 0, st>>>(hi, lo, out, n);
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: uniform positions, Maxwellian velocities (Sec. II).
+template <class R>
+__global__ void k_init(const __grid_constant__ StepK<R> k, SpeciesDev s, int species, long long n, uint64_t id0, R sig) {
+  const uint2 key = seed_key(k.seed);
+  const uint32_t c3 = ((species == 0 ? (uint32_t)kStInitE : (uint32_t)kStInitI) << 28) | (k.column << 16);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    const uint64_t id = id0 + (uint64_t)p;
+    const uint32_t a = (uint32_t)id, b = (uint32_t)(id >> 32);
+    const uint4 w = philox10(make_uint4(a, b, 0u, c3 | 0u), key);
+    const uint4 x = philox10(make_uint4(a, b, 0u, c3 | 1u), key);
+    const int32_t cell = (int32_t)(((unsigned long long)w.x * (unsigned long long)(uint32_t)k.N) >> 32);
+    R off, vx, vy, vz;
+    if constexpr (std::is_same<R, float>::value) {
+      off = u24(w.y);
+      vx = sig * gauss<float>(k.gauss, u24(w.z));
+      vy = sig * gauss<float>(k.gauss, u24(w.w));
+      vz = sig * gauss<float>(k.gauss, u24(x.x));
+    } else {
+      const uint4 y = philox10(make_uint4(a, b, 0u, c3 | 2u), key);
+      off = u53(w.y, w.z);
+      vx = sig * gauss<double>(k.gauss, u53(x.x, x.y));
+      vy = sig * gauss<double>(k.gauss, u53(x.z, x.w));
+      vz = sig * gauss<double>(k.gauss, u53(y.x, y.y));
+    }
+    s.cell[p] = cell;
+    rec_store<R>(s.rec, p, off, vx, vy, vz);
+    s.id[p] = id;
+  }
+}
+
+template <class R>
+void launch_init(const StepK<R> &k, SpeciesDev s, int species, int64_t n, uint64_t id0, R sig, cudaStream_t st) {
+  if (n <= 0) return;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_init<R><<<blocks, 256, 0, st>>>(k, s, species, (long long)n, id0, sig);
+}
+
+template <class R>
+__global__ void k_deposit(SpeciesDev s, const Ctl *ctl, int species, int N) {
+  const long long n = ctl->n[species];
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+    dep_global<R>(s.Q, N, s.cell[p], rec_get_off<R>(s.rec, p), true);
+}
+
+template <class R>
+void launch_deposit(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, int species, cudaStream_t st) {
+  k_deposit<R><<<152 * 8, 256, 0, st>>>(s, ctl, species, k.N);
+}
+
+// leapfrog start: v^{-1/2} = v^0 - (q dt / 2m) E^0(x^0)
+template <class R>
+__global__ void k_halfstep(SpeciesDev s, const Ctl *ctl, const R *Ef, int species, R a) {
+  const long long n = ctl->n[species];
+  const R ha = (R)0.5 * a;
+  using T = typename Rec<R>::T;
+  T *rec = reinterpret_cast<T *>(s.rec);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    R off, vx, vy, vz;
+    rec_load<R>(s.rec, p, off, vx, vy, vz);
+    const R Ep = gather(Ef, s.cell[p], off);
+    vx = vx - ha * Ep;
+    rec_store<R>(s.rec, p, off, vx, vy, vz);
+  }
+  (void)rec;
+}
+
+template <class R>
+void launch_halfstep(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, const R *Ef, int species, cudaStream_t st) {
+  k_halfstep<R><<<152 * 8, 256, 0, st>>>(s, ctl, Ef, species, k.sp[species].a);
+}
+
+// explicit instantiations
+#define PIC_INST(R)                                                                                                  \
+  template void launch_init<R>(const StepK<R> &, SpeciesDev, int, int64_t, uint64_t, R, cudaStream_t);              \
+  template void launch_deposit<R>(const StepK<R> &, SpeciesDev, const Ctl *, int, cudaStream_t);                    \
+  template void launch_halfstep<R>(const StepK<R> &, SpeciesDev, const Ctl *, const R *, int, cudaStream_t);        \
+  template void launch_push<R>(const StepK<R> &, SpeciesDev, Ctl *, const R *, BirthBuf<R>, Moments, int, int,      \
+                               cudaStream_t);                                                                        \
+  template void launch_births<R>(const StepK<R> &, SpeciesDev, SpeciesDev, Ctl *, BirthBuf<R>, K3Scratch, int,      \
+                                 cudaStream_t);                                                                      \
+  template void launch_field<R>(const FieldK &, const unsigned long long *, const unsigned long long *, Ctl *,       \
+                                double *, double *, R *, Moments, cudaStream_t);                                    \
+  template int push_smem_bytes<R>(int);
+PIC_INST(double)
+PIC_INST(float)
+
+}  // namespace pic
