@@ -1,0 +1,283 @@
+#!/usr/bin/env python
+"""Throughput of the PIC-MCC step on GB300: pushed particle-steps per second.
+
+Workload: the periodic neon column, 1 Torr, 300 K, L = 0.30 m, 16384 cells,
+2e7 electrons + 2e7 ions, dt = 4e-11 s, ions subcycled x10, particle state
+int32 cell + FP32 offset/velocity (float4), FP64 field; synthetic analytic
+neon-like cross sections stand in for the LXCat data.  A step is one pass of
+the whole hot path: electron gather/push/collisions/deposit, the ion step on
+every 10th step, births and paired removals, and the Poisson solve.  A pushed
+particle-step counts every electron every step and every ion on its push steps.
+
+python bench.py [--gpus N --steps K --warmup W] prints one JSON line.
+--impl reference times the CPU oracle (the reference arm) instead.
+Multi-GPU runs are independent replicas, one column per rank (no collective
+in the data path); value = particle-steps of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "particle-steps/s and % HBM roofline on 1 GB300 vs CPU oracle; batched vs serial"
+UNIT = "particle-steps/s"
+BYTES_PER_PUSH = 48  # float4 state read + write (32 B) + id read (8 B) + int32 cell read + write (8 B)
+WORKLOAD = ("neon periodic column, 1 Torr 300 K, L=0.30 m, R=0.01 m, 16384 cells, 2e7 electrons + 2e7 ions, "
+            "dt=4e-11 s, ions subcycled x10, E0=600 V/m, PAIR losses, int32 cell + FP32 offset/velocity, "
+            "FP64 Poisson")
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pic_kernels.cu", "pic_device.cuh", "pic_internal.cuh"):
+        h.update((ROOT / "paper_2202_03215_gb300" / "csrc" / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n_e: int):
+    """DRAM bytes per launch of the electron step from the committed ncu summary,
+    scaled to n_e electrons; None if the kernel changed since it was taken."""
+    f = ROOT / "profiles" / "k_push_electron_neon_traffic.json"
+    if not f.exists():
+        return None
+    d = json.loads(f.read_text())
+    if d.get("source_sha") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_electron"]) * n_e
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in Path(self.f.name).read_text().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def pushed_steps(s0: int, k: int, n_e: int, n_i: int, sub: int) -> int:
+    ion_steps = sum(1 for s in range(s0, s0 + k) if sub > 0 and s % sub == 0)
+    return k * n_e + ion_steps * n_i
+
+
+def oracle_rate(n_per_species: int, steps: int, warmup: int = 1):
+    """The CPU oracle as it stands (FP32-storage build, one thread) on a sample of the workload."""
+    import oracle
+    from paper_2202_03215_gb300 import workloads as w
+    p = w.config_neon_column(n_per_species=n_per_species)
+    o = oracle.Oracle(p)
+    o.step(warmup)
+    s0 = o.stats()["step"]
+    t = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t
+    return pushed_steps(s0, steps, n_per_species, n_per_species, p.ion_subcycle) / dt, dt
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # each step one oracle step of a sample of the workload, sized so K steps take about two minutes
+    n = int(min(2_000_000, max(100_000, 120.0 * 2.5e7 / max(1, args.steps) / 1.1)))
+    rate, dt = oracle_rate(n, args.steps, warmup=min(args.warmup, 3))
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{n} electrons + {n} ions per step (same cells, dt, gas)"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps of {n}+{n} particles, {dt:.1f} s"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=20_000_000, help="particles per species")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import paper_2202_03215_gb300 as pb
+    from paper_2202_03215_gb300 import build as pbuild
+    from paper_2202_03215_gb300 import workloads as w
+    pbuild.build()
+    # the CPU baseline runs before the first GPU call of this process (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s = 2_000_000
+        steps_s = 60
+        rate, dt = oracle_rate(n_s, steps_s)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{steps_s} oracle steps (FP32-storage build) of {n_s} electrons + {n_s} ions on the "
+                         f"same column, {dt:.1f} s of single-thread CPU"}
+
+    p = w.config_neon_column(n_per_species=args.n, seed=1 + rank, column=rank)
+    col = pb.Column(p)
+    col.step(args.warmup)
+    st0 = col.stats()
+    ext = torch.cuda.ExternalStream(col.stream())
+    col.set_timing(True)
+    col.kernel_times()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    e0.record(ext)
+    col.step(args.steps)
+    e1.record(ext)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop() if clk else None
+    ms = e0.elapsed_time(e1)
+    kt = col.kernel_times()
+    col.set_timing(False)
+    st1 = col.stats()
+    units = pushed_steps(st0["step"], args.steps, st0["n_e"], st0["n_i"], p.ion_subcycle)
+    assert st1["n_e"] == st0["n_e"] and st1["step"] == st0["step"] + args.steps
+    launches = sum(v[1] for v in kt.values())
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        u = torch.tensor([float(units)], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(t.item()), int(u.item())
+    value = units / (ms / 1e3)
+
+    # roofline of the dominant kernel (electron step), live from the timed region
+    push_ms, push_n = kt["push_e"]
+    n_e = st0["n_e"]
+    avg_s = push_ms / max(1, push_n) / 1e3
+    achieved = BYTES_PER_PUSH * n_e / avg_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = ncu_traffic(n_e)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_push<float,electrons>", "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": BYTES_PER_PUSH * n_e, "avg_launch_us": avg_s * 1e6,
+            "share_of_step": push_ms / ms}
+
+    # end to end through the public API with host buffers: upload the state, step, read moments
+    e2e = None
+    if not args.no_e2e:
+        host = col.get_state()
+        pinned = {}
+        for k, v in host.items():
+            if isinstance(v, np.ndarray):
+                t = torch.empty(v.shape, dtype=getattr(torch, str(v.dtype)) if v.dtype != np.uint64 else torch.int64,
+                                pin_memory=True)
+                a = t.numpy().view(v.dtype)
+                a[...] = v
+                pinned[k] = (t, a)
+        hstate = {k: (pinned[k][1] if k in pinned else v) for k, v in host.items()}
+        col.close()
+        col2 = pb.Column(p)
+        local_units = pushed_steps(host["step"], args.steps, host["n_e"], host["n_i"], p.ion_subcycle)
+        h2d = sum(a.nbytes for k, (t, a) in pinned.items() if k not in ("Q_e",))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        col2.set_state(hstate)
+        col2.step(args.steps)
+        mom = col2.moments()
+        stx = col2.stats()
+        t1 = time.perf_counter()
+        d2h = sum(v.nbytes for v in mom.values() if isinstance(v, np.ndarray)) + 8 * 40
+        secs = t1 - t0
+        if dist:
+            t = torch.tensor([secs], device="cuda")
+            u = torch.tensor([float(local_units)], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(u, op=dist.ReduceOp.SUM)
+            secs, local_units = float(t.item()), int(u.item())
+        e2e = {"value": local_units / secs, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": secs, "api": "pic_set_state (host arrays) + pic_step(K) + pic_moments + pic_get_stats"}
+        assert stx["step"] == host["step"] + args.steps
+        col2.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "particles_per_species": args.n, "n_cells": p.n_cells,
+                           "l2": "inputs larger than L2 (state 1.1 GB)", "parallelism": f"replicas x{world}",
+                           "pushed_particle_steps": units},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernel_ms": {k: v[0] for k, v in kt.items()}, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

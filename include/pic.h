@@ -199,6 +199,23 @@ int pic_last_codes(pic_handle *h, int species, int32_t *out, int64_t n);
 /* Derived scalars: [n_g, nu*_e, P_null_e, nu*_i, P_null_i, w, dx]. */
 int pic_derived(pic_handle *h, double out[7]);
 
+/* Kernel classes of pic_kernel_times. */
+#define PIC_K_PUSH_E 0   /* electron step (gather, push, collisions, deposit) */
+#define PIC_K_PUSH_I 1   /* ion step */
+#define PIC_K_BIRTHS 2   /* births and removals */
+#define PIC_K_FIELD 3    /* field solve */
+#define PIC_K_SORT 4     /* counting sort by cell */
+#define PIC_K_OTHER 5
+#define PIC_K_CLASSES 8
+
+/* Per-kernel timing.  With timing on, pic_step records a CUDA event pair on
+ * the handle's stream around every kernel it launches.  pic_kernel_times
+ * returns, per class, the summed event milliseconds and the launch count
+ * since the last call (launches are counted with timing off too), then
+ * resets both.  ms and launches are host arrays of PIC_K_CLASSES. */
+int pic_set_timing(pic_handle *h, int enable);
+int pic_kernel_times(pic_handle *h, double *ms, int64_t *launches);
+
 /* The CUDA stream the handle launches on (a cudaStream_t). */
 void *pic_stream(pic_handle *h);
 

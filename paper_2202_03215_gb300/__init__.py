@@ -107,6 +107,8 @@ def lib() -> C.CDLL:
         L.pic_last_error.restype = C.c_char_p
         L.pic_test_i128_to_double.argtypes = [_I64, _U64, _D, C.c_int]
         L.pic_abi_version.restype = C.c_int
+        L.pic_set_timing.argtypes = [C.c_void_p, C.c_int]
+        L.pic_kernel_times.argtypes = [C.c_void_p, _D, _I64]
         _lib = L
     return _lib
 
@@ -226,6 +228,17 @@ class Column:
         if with_Qi and d.get("Q_i") is not None:
             a = np.ascontiguousarray(d["Q_i"], dtype=np.int64); keep.append(a); s.Q_i = _ptr(a, _I64)
         _check(self.L.pic_set_state(self.h, C.byref(s)), self.h)
+
+    def set_timing(self, enable: bool) -> None:
+        _check(self.L.pic_set_timing(self.h, int(enable)), self.h)
+
+    def kernel_times(self) -> dict:
+        """Summed event milliseconds and launch counts per kernel class since the last call."""
+        ms = np.zeros(8)
+        n = np.zeros(8, np.int64)
+        _check(self.L.pic_kernel_times(self.h, _ptr(ms, _D), _ptr(n, _I64)), self.h)
+        names = ("push_e", "push_i", "births", "field", "sort", "other")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(names)}
 
     def codes(self, species: int, n: int) -> np.ndarray:
         out = np.zeros(n, np.int32)

@@ -43,6 +43,8 @@ struct pic_handle {
   pic::Ctl *ctl = nullptr;
   pic::SpeciesDev sp[2]{};
   double *E = nullptr, *Eh = nullptr;
+  long long *Dg = nullptr;            // field scratch when the nodes exceed shared memory
+  pic::FieldScan *fs = nullptr;       // exact prefix data between the two field kernels
   void *Ef = nullptr;                 // R[N+1]
   void *tab[2] = {nullptr, nullptr};  // R[np * ntab]
   float *gauss = nullptr;
@@ -61,6 +63,13 @@ struct pic_handle {
   long long host_step = 0;
   std::string err;
   int latched = 0;
+  // kernel timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;        // event pool, used in pairs
+  std::vector<int> ev_cls;            // class of each recorded pair
+  size_t ev_used = 0;
+  double kms[PIC_K_CLASSES] = {0};
+  int64_t klaunch[PIC_K_CLASSES] = {0};
 };
 
 namespace {
@@ -148,6 +157,35 @@ template <> pic::StepK<float> &kparams<float>(pic_handle *h) { return h->kf; }
 template <class R> pic::BirthBuf<R> &bbuf(pic_handle *h);
 template <> pic::BirthBuf<double> &bbuf<double>(pic_handle *h) { return h->bbd; }
 template <> pic::BirthBuf<float> &bbuf<float>(pic_handle *h) { return h->bbf; }
+
+// event pair around one launch (timing on), launch counting (always)
+void t_begin(pic_handle *h) {
+  if (!h->timing) return;
+  if (h->ev_used + 2 > h->ev.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      h->ev.push_back(e);
+    }
+  }
+  cudaEventRecord(h->ev[h->ev_used], h->stream);
+}
+void t_end(pic_handle *h, int cls) {
+  h->klaunch[cls]++;
+  if (!h->timing) return;
+  cudaEventRecord(h->ev[h->ev_used + 1], h->stream);
+  h->ev_cls.push_back(cls);
+  h->ev_used += 2;
+}
+// after a synchronisation: fold the recorded pairs into the per-class sums
+void t_collect(pic_handle *h) {
+  for (size_t i = 0; i < h->ev_cls.size(); ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess) h->kms[h->ev_cls[i]] += ms;
+  }
+  h->ev_cls.clear();
+  h->ev_used = 0;
+}
 
 int check_status(pic_handle *h) {
   pic::Ctl c;
@@ -269,7 +307,7 @@ template <class R> int run_init(pic_handle *h) {
   pic::launch_deposit<R>(k, h->sp[0], h->ctl, 0, h->stream);
   pic::launch_deposit<R>(k, h->sp[1], h->ctl, 1, h->stream);
   pic::launch_field<R>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<R *>(h->Ef), h->m,
-                       h->stream);
+                       h->Dg, h->fs, false, false, h->stream);
   pic::launch_halfstep<R>(k, h->sp[0], h->ctl, reinterpret_cast<R *>(h->Ef), 0, h->stream);
   pic::launch_halfstep<R>(k, h->sp[1], h->ctl, reinterpret_cast<R *>(h->Ef), 1, h->stream);
   CU(h, cudaGetLastError());
@@ -282,14 +320,23 @@ template <class R> int enqueue_step(pic_handle *h) {
   const bool ion_push = sub > 0 && (h->host_step % sub) == 0;
   const R *Ef = reinterpret_cast<const R *>(h->Ef);
   CU(h, cudaMemsetAsync(h->sp[0].Q, 0, (size_t)h->N * 8, h->stream));
+  t_begin(h);
   pic::launch_push<R>(k, h->sp[0], h->ctl, Ef, bbuf<R>(h), h->m, 0, h->nsm, h->stream);
+  t_end(h, PIC_K_PUSH_E);
   if (ion_push) {
     CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->N * 8, h->stream));
+    t_begin(h);
     pic::launch_push<R>(k, h->sp[1], h->ctl, Ef, bbuf<R>(h), h->m, 1, h->nsm, h->stream);
+    t_end(h, PIC_K_PUSH_I);
   }
+  t_begin(h);
   pic::launch_births<R>(k, h->sp[0], h->sp[1], h->ctl, bbuf<R>(h), h->sc, ion_push ? 1 : 0, h->stream);
+  t_end(h, PIC_K_BIRTHS);
+  const bool diag = h->p.diag_every > 0 && (h->host_step % h->p.diag_every) == 0;
+  t_begin(h);
   pic::launch_field<R>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<R *>(h->Ef), h->m,
-                       h->stream);
+                       h->Dg, h->fs, diag, true, h->stream);
+  t_end(h, PIC_K_FIELD);
   CU(h, cudaGetLastError());
   h->host_step++;
   return 0;
@@ -302,8 +349,9 @@ void free_all(pic_handle *h) {
     cudaFree(h->sp[q].cell); cudaFree(h->sp[q].rec); cudaFree(h->sp[q].id); cudaFree(h->sp[q].code);
     cudaFree(h->sp[q].Q); cudaFree(h->sp[q].dead); cudaFree(h->tab[q]);
   }
-  cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->Ef); cudaFree(h->gauss);
+  cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->Dg); cudaFree(h->fs); cudaFree(h->Ef); cudaFree(h->gauss);
   cudaFree(h->bb_mem); cudaFree(h->k3_mem); cudaFree(h->mom); cudaFree(h->mom_iz);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -399,7 +447,8 @@ int pic_init(const pic_params *params, pic_handle **out) {
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(set_err(h, PIC_ECUDA, "stream creation failed"));
   if (cudaMalloc(&h->ctl, sizeof(pic::Ctl)) != cudaSuccess || cudaMalloc(&h->E, (size_t)h->N * 8) != cudaSuccess ||
-      cudaMalloc(&h->Eh, (size_t)h->N * 8) != cudaSuccess ||
+      cudaMalloc(&h->Eh, (size_t)h->N * 8) != cudaSuccess || cudaMalloc(&h->Dg, ((size_t)h->N + h->N / 16 + 1) * 8) != cudaSuccess ||
+      cudaMalloc(&h->fs, sizeof(pic::FieldScan)) != cudaSuccess ||
       cudaMalloc(&h->gauss, (pic::kGaussN + 1) * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&h->k3_mem, (size_t)pic::kStageCap * 7 * 4) != cudaSuccess ||
       cudaMalloc(&h->mom, (size_t)h->N * 8 * 8) != cudaSuccess ||
@@ -430,16 +479,12 @@ int pic_init(const pic_params *params, pic_handle **out) {
   h->fk.diag_every = 0;  // the initial solve takes no diagnostic sample
   h->fk.Cf = h->Cfield / ((double)h->N * (double)h->N);
   h->fk.dx = h->dx;
+  h->fk.smem = h->N <= pic::kFieldSmemMax ? 1 : 0;
+  h->fk.seg = (h->N + pic::kFieldThreads - 1) / pic::kFieldThreads;
   int rc2 = h->mixed ? init_typed<float>(h) : init_typed<double>(h);
   h->p.xsec = nullptr;
   h->p.n_xsec = 0;
   if (rc2) return fail(rc2);
-  // the initial field solve advanced the device step counter: put it back to 0
-  c.step = 0;
-  if (cudaMemcpyAsync(&h->ctl->step, &c.step, sizeof c.step, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-    return fail(set_err(h, PIC_ECUDA, "reset step failed"));
-  long long zero = 0;
-  cudaMemcpyAsync(&h->ctl->m_steps, &zero, sizeof zero, cudaMemcpyHostToDevice, h->stream);
   h->fk.diag_every = p.diag_every;
   if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(set_err(h, PIC_ECUDA, "init failed"));
   if (check_status(h)) return fail(h->latched);
@@ -453,8 +498,36 @@ int pic_step(pic_handle *h, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     const int rc = h->mixed ? enqueue_step<float>(h) : enqueue_step<double>(h);
     if (rc) return rc;
+    // keep the event pool bounded: fold recorded pairs every 256 steps
+    if (h->timing && h->ev_cls.size() > 1024) {
+      CU(h, cudaStreamSynchronize(h->stream));
+      t_collect(h);
+    }
   }
-  return check_status(h);
+  const int rc = check_status(h);
+  t_collect(h);
+  return rc;
+}
+
+int pic_set_timing(pic_handle *h, int enable) {
+  if (!h) return set_err(h, PIC_EINVAL, "bad arguments");
+  CU(h, cudaStreamSynchronize(h->stream));
+  t_collect(h);
+  h->timing = enable != 0;
+  return 0;
+}
+
+int pic_kernel_times(pic_handle *h, double *ms, int64_t *launches) {
+  if (!h) return set_err(h, PIC_EINVAL, "bad arguments");
+  CU(h, cudaStreamSynchronize(h->stream));
+  t_collect(h);
+  for (int c = 0; c < PIC_K_CLASSES; ++c) {
+    if (ms) ms[c] = h->kms[c];
+    if (launches) launches[c] = h->klaunch[c];
+    h->kms[c] = 0.0;
+    h->klaunch[c] = 0;
+  }
+  return 0;
 }
 
 int pic_get_stats(pic_handle *h, pic_stats *out) {
@@ -583,17 +656,12 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
     }
   } else {
     // solve the field of the new charges without advancing the step counter
-    pic::FieldK fk = h->fk;
-    fk.diag_every = 0;
     if (h->mixed)
-      pic::launch_field<float>(fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<float *>(h->Ef), h->m,
-                               h->stream);
+      pic::launch_field<float>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<float *>(h->Ef),
+                               h->m, h->Dg, h->fs, false, false, h->stream);
     else
-      pic::launch_field<double>(fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<double *>(h->Ef),
-                                h->m, h->stream);
-    long long st = in->step, ms = 0;
-    CU(h, cudaMemcpyAsync(&h->ctl->step, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
-    CU(h, cudaMemcpyAsync(&h->ctl->m_steps, &ms, sizeof ms, cudaMemcpyHostToDevice, h->stream));
+      pic::launch_field<double>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh,
+                                reinterpret_cast<double *>(h->Ef), h->m, h->Dg, h->fs, false, false, h->stream);
   }
   CU(h, cudaStreamSynchronize(h->stream));
   CU(h, cudaGetLastError());

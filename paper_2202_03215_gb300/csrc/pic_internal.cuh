@@ -13,6 +13,7 @@ constexpr int kGaussN = 4096;          // Gaussian inverse-CDF intervals
 constexpr int kStageCap = 8192;        // births / radial losses staged per step and species
 constexpr int kFieldThreads = 1024;
 constexpr int kStepThreads = 1024;
+constexpr int kFieldSmemMax = 24576;   // nodes whose int64 charges fit in shared memory
 
 // device status bits
 constexpr unsigned kStBirthOverflow = 1u;
@@ -93,8 +94,16 @@ struct K3Scratch {
   uint32_t *vic;     // 2 * kStageCap victim slots (electrons, ions)
 };
 
+// exact integer prefix data handed from the scan kernel to the evaluation kernel
+struct FieldScan {
+  __int128 Sp0[kFieldThreads];   // S'_{j0-1} at the start of each thread segment
+  __int128 T, M;
+};
+
 struct FieldK {
   int N, field_mode, sub, diag_every;
+  int smem;           // node arrays staged in shared memory (N <= kFieldSmemMax)
+  int seg;            // nodes per thread segment: ceil(N / kFieldThreads)
   double Cf;          // e w / (eps0 2^32 N^2)
   double dx;
 };
@@ -112,9 +121,11 @@ void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBu
 template <class R>
 void launch_births(const StepK<R> &k, SpeciesDev e, SpeciesDev i, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
                    int ion_pushed, cudaStream_t st);
+// field solve; diag: take a diagnostic sample; advance: count the step
 template <class R>
 void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned long long *Qi, Ctl *ctl,
-                  double *E, double *Eh, R *Ef, Moments m, cudaStream_t st);
+                  double *E, double *Eh, R *Ef, Moments m, long long *Dg, FieldScan *fs, bool diag, bool advance,
+                  cudaStream_t st);
 void launch_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n, cudaStream_t st);
 template <class R> int push_smem_bytes(int N);
 

@@ -17,6 +17,8 @@ namespace pic {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kDirectMax = 1024;   // births handled by O(n^2) ranking instead of a sort
+constexpr int kBirthThreads = 512;
 
 template <class R> __device__ __forceinline__ void rec_load(const void *base, long long p, R &off, R &vx, R &vy, R &vz) {
   if constexpr (std::is_same<R, float>::value) {
@@ -345,18 +347,31 @@ __device__ bool draw_victims(uint2 key, uint32_t step, uint32_t c3, int nb, long
   }
   __syncthreads();
   const int n2 = (int)pow2ceil<float>(nb);
+  const bool direct = nb <= kDirectMax;
   for (int round = 0; round < 64; ++round) {
-    for (int t = threadIdx.x; t < n2; t += blockDim.x)
-      keys[t] = t < nb ? (((unsigned long long)sc.cand[t] << 32) | ((sc.settled[t] ? 0ull : 1ull) << 31) |
-                          (unsigned long long)t)
-                       : ~0ull;
-    __syncthreads();
-    bitonic_sort(keys, n2);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-      const unsigned long long kk = keys[i];
-      if ((kk >> 31) & 1ull) {
-        const uint32_t ev = (uint32_t)(kk & 0x7fffffffull);
-        sc.win[ev] = (i == 0 || (keys[i - 1] >> 32) != (kk >> 32)) ? 1u : 0u;
+    if (direct) {
+      // O(nb^2) conflict test: no sort for the usual few hundred events
+      for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        if (sc.settled[t]) continue;
+        const uint32_t c = sc.cand[t];
+        uint32_t ok = 1u;
+        for (int j = 0; j < nb && ok; ++j)
+          if (j != t && sc.cand[j] == c && (sc.settled[j] || j < t)) ok = 0u;
+        sc.win[t] = ok;
+      }
+    } else {
+      for (int t = threadIdx.x; t < n2; t += blockDim.x)
+        keys[t] = t < nb ? (((unsigned long long)sc.cand[t] << 32) | ((sc.settled[t] ? 0ull : 1ull) << 31) |
+                            (unsigned long long)t)
+                         : ~0ull;
+      __syncthreads();
+      bitonic_sort(keys, n2);
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const unsigned long long kk = keys[i];
+        if ((kk >> 31) & 1ull) {
+          const uint32_t ev = (uint32_t)(kk & 0x7fffffffull);
+          sc.win[ev] = (i == 0 || (keys[i - 1] >> 32) != (kk >> 32)) ? 1u : 0u;
+        }
       }
     }
     __syncthreads();
@@ -476,14 +491,24 @@ __device__ void fill_compact(const StepK<R> &k, SpeciesDev s, Ctl *ctl, int SP, 
 }
 
 template <class R>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(kBirthThreads, 1)
 k_births(const __grid_constant__ StepK<R> k, SpeciesDev e, SpeciesDev ion, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
          int ion_pushed) {
   extern __shared__ __align__(16) unsigned long long keys[];   // kStageCap
-  __shared__ int s_scan[1024];
+  __shared__ int s_scan[kBirthThreads];
+  __shared__ uint32_t s_scr[7 * kDirectMax];
   const int N = k.N;
   int nb = ctl->n_birth;
   if (nb > kStageCap) nb = kStageCap;
+  if (nb <= kDirectMax) {
+    // the usual few hundred events: scratch in shared memory instead of global memory
+    sc.order = s_scr;
+    sc.cand = s_scr + kDirectMax;
+    sc.att = s_scr + 2 * kDirectMax;
+    sc.settled = s_scr + 3 * kDirectMax;
+    sc.win = s_scr + 4 * kDirectMax;
+    sc.vic = s_scr + 5 * kDirectMax;
+  }
   int nde = ctl->n_dead[0], ndi = ion_pushed ? ctl->n_dead[1] : 0;
   if (nde > kStageCap) nde = kStageCap;
   if (ndi > kStageCap) ndi = kStageCap;
@@ -491,7 +516,16 @@ k_births(const __grid_constant__ StepK<R> k, SpeciesDev e, SpeciesDev ion, Ctl *
   const uint32_t step = (uint32_t)ctl->step;
   const uint2 key = seed_key(k.seed);
   // births in parent-slot order
-  if (nb > 0) {
+  if (nb > 0 && nb <= kDirectMax) {
+    // rank of each birth by parent slot (parents are distinct)
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      const int32_t pt = bb.parent[t];
+      int r = 0;
+      for (int j = 0; j < nb; ++j) r += bb.parent[j] < pt;
+      sc.order[r] = (uint32_t)t;
+    }
+    __syncthreads();
+  } else if (nb > 0) {
     const int n2 = (int)pow2ceil<float>(nb);
     for (int t = threadIdx.x; t < n2; t += blockDim.x)
       keys[t] = t < nb ? (((unsigned long long)(uint32_t)bb.parent[t] << 32) | (unsigned long long)t) : ~0ull;
@@ -500,6 +534,7 @@ k_births(const __grid_constant__ StepK<R> k, SpeciesDev e, SpeciesDev ion, Ctl *
     for (int t = threadIdx.x; t < nb; t += blockDim.x) sc.order[t] = (uint32_t)keys[t];
     __syncthreads();
   }
+  const int vstride = nb <= kDirectMax ? kDirectMax : kStageCap;
   if (k.loss_mode == PIC_LOSS_PAIR) {
     if (nb > 0) {
       const long long npe = ctl->n[0], npi = ctl->n[1];
@@ -507,13 +542,13 @@ k_births(const __grid_constant__ StepK<R> k, SpeciesDev e, SpeciesDev ion, Ctl *
       if (ok) ok = draw_victims(key, step, ((uint32_t)kStVicE << 28) | (k.column << 16), nb, npe, keys, sc, sc.vic);
       if (ok)
         ok = draw_victims(key, step, ((uint32_t)kStVicI << 28) | (k.column << 16), nb, npi, keys, sc,
-                          sc.vic + kStageCap);
+                          sc.vic + vstride);
       if (!ok) {
         if (threadIdx.x == 0) atomicOr(&ctl->status, kStVictim);
       } else {
         for (int t = threadIdx.x; t < nb; t += blockDim.x) {
           const uint32_t b = sc.order[t];
-          const long long ve = sc.vic[t], vi = sc.vic[kStageCap + t];
+          const long long ve = sc.vic[t], vi = sc.vic[vstride + t];
           dep_global<R>(e.Q, N, e.cell[ve], rec_get_off<R>(e.rec, ve), false);
           write_newborn<R>(e, ve, bb.cell[b], bb.off[b], bb.ve[b], bb.ve[kStageCap + b], bb.ve[2 * kStageCap + b],
                            (uint64_t)next_id + 2ull * (uint64_t)t, N);
@@ -562,7 +597,7 @@ void launch_births(const StepK<R> &k, SpeciesDev e, SpeciesDev i, Ctl *ctl, Birt
                    int ion_pushed, cudaStream_t st) {
   const int bytes = kStageCap * 8;
   cudaFuncSetAttribute(k_births<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  k_births<R><<<1, 1024, bytes, st>>>(k, e, i, ctl, bb, sc, ion_pushed);
+  k_births<R><<<1, kBirthThreads, bytes, st>>>(k, e, i, ctl, bb, sc, ion_pushed);
 }
 
 // ---------------------------------------------------------------------------
@@ -589,6 +624,15 @@ __device__ double i128_to_double(__int128 v) {
     d = __ull2double_rn(t) * __longlong_as_double((long long)(1023 + sh) << 52);
   }
   return neg ? -d : d;
+}
+
+// x * n modulo 2^128 (two's complement), n < 2^32
+__device__ __forceinline__ __int128 mul_u32(__int128 x, uint32_t n) {
+  const unsigned __int128 ux = (unsigned __int128)x;
+  const unsigned long long lo = (unsigned long long)ux, hi = (unsigned long long)(ux >> 64);
+  const unsigned long long plo = lo * (unsigned long long)n;
+  const unsigned long long phi = hi * (unsigned long long)n + __umul64hi(lo, (unsigned long long)n);
+  return (__int128)(((unsigned __int128)phi << 64) | (unsigned __int128)plo);
 }
 
 __device__ __int128 block_excl_scan_i128(__int128 v, __int128 *sh, __int128 &total) {
@@ -623,82 +667,132 @@ __device__ double block_excl_scan_f64(double v, double *sh, double &total) {
   return incl - v;
 }
 
+// padded shared-memory index: one spare slot per 16 nodes keeps the per-thread
+// contiguous segments on distinct banks
+__device__ __forceinline__ int fpad(int j) { return j + (j >> 4); }
+
+// Integer part of the field solve (one CTA, no floating point): the exact
+// prefix values S'_{j0-1} at the start of every thread segment, T and M.
 template <class R>
 __global__ void __launch_bounds__(kFieldThreads, 1)
-k_field(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi, Ctl *ctl,
-        double *E, double *Eh, R *Ef, Moments m) {
+k_field_scan(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi,
+             long long *Dg, FieldScan *fs) {
+  extern __shared__ __align__(16) long long sD[];
   __shared__ __int128 sh[kFieldThreads];
   const int N = f.N;
   const int t = threadIdx.x;
-  const int seg = (N + blockDim.x - 1) / blockDim.x;
+  long long *D = f.smem ? sD : Dg;   // indexed through fpad()
+  const int seg = f.seg;
   const int j0 = min(N, t * seg), j1 = min(N, j0 + seg);
-  const long long stepll = ctl->step;
-  const bool diag = f.diag_every > 0 && (stepll % f.diag_every) == 0;
+  for (int j = t; j < N; j += blockDim.x) D[fpad(j)] = (long long)Qi[j] - (long long)Qe[j];
+  __syncthreads();
+  __int128 loc = 0;
+  for (int j = j0; j < j1; ++j) loc += (__int128)D[fpad(j)];
+  __int128 T;
+  const __int128 pre = block_excl_scan_i128(loc, sh, T);
+  const uint32_t Nu = (uint32_t)N;
+  // S'_j = N run_j - (j+1) T obeys S'_j = S'_{j-1} + (N D_j - T)
+  const __int128 Sp0 = mul_u32(pre, Nu) - (__int128)j0 * T;
+  __int128 Sp = Sp0, Mloc = 0;
+  for (int j = j0; j < j1; ++j) {
+    Sp += mul_u32((__int128)D[fpad(j)], Nu) - T;
+    Mloc += Sp;
+  }
+  __int128 M;
+  (void)block_excl_scan_i128(Mloc, sh, M);
+  fs->Sp0[t] = Sp0;
+  if (t == 0) { fs->T = T; fs->M = M; }
+}
+
+// Floating-point part (many CTAs, one thread per segment):
+//   E_{j+1/2} = (N S'_j - M) Cf,  E_j = (E_{j-1/2} + E_{j+1/2}) / 2 - E0.
+// S'_{-1} = 0 = S'_{N-1}, so the segment start formula also gives E_{-1/2} = E_{N-1/2}.
+template <class R>
+__global__ void k_field_eval(FieldK f, const unsigned long long *__restrict__ Qe,
+                             const unsigned long long *__restrict__ Qi, Ctl *ctl, const FieldScan *fs, double *E,
+                             double *Eh, R *Ef, int advance) {
+  const int N = f.N;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int seg = f.seg;
+  const int j0 = min(N, t * seg), j1 = min(N, j0 + seg);
   const double E0 = ctl->E0;
   bool bad = false;
-  if (f.field_mode == PIC_FIELD_APPLIED) {
-    for (int j = j0; j < j1; ++j) { Eh[j] = 0.0; E[j] = -E0; }
-  } else {
-    __int128 loc = 0;
-    for (int j = j0; j < j1; ++j) loc += (__int128)((long long)Qi[j] - (long long)Qe[j]);
-    __int128 T;
-    const __int128 pre = block_excl_scan_i128(loc, sh, T);
-    const __int128 Nn = (__int128)N;
-    __int128 run = pre, Mloc = 0;
-    for (int j = j0; j < j1; ++j) {
-      run += (__int128)((long long)Qi[j] - (long long)Qe[j]);
-      Mloc += Nn * run - (__int128)(j + 1) * T;
+  if (t < kFieldThreads && j0 < j1) {
+    if (f.field_mode == PIC_FIELD_APPLIED) {
+      for (int j = j0; j < j1; ++j) {
+        Eh[j] = 0.0;
+        E[j] = -E0;
+        Ef[j] = (R)(-E0);
+      }
+    } else {
+      const uint32_t Nu = (uint32_t)N;
+      const __int128 T = fs->T, M = fs->M;
+      __int128 Sp = fs->Sp0[t];
+      double prev = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;
+      const double Eapp = -E0;
+      for (int j = j0; j < j1; ++j) {
+        Sp += mul_u32((__int128)((long long)Qi[j] - (long long)Qe[j]), Nu) - T;
+        const double eh = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;
+        const double e = 0.5 * (prev + eh) + Eapp;
+        Eh[j] = eh;
+        E[j] = e;
+        Ef[j] = (R)e;
+        if (!isfinite(e)) bad = true;
+        prev = eh;
+      }
     }
-    __int128 M;
-    (void)block_excl_scan_i128(Mloc, sh, M);
-    run = pre;
-    for (int j = j0; j < j1; ++j) {
-      run += (__int128)((long long)Qi[j] - (long long)Qe[j]);
-      const __int128 Sp = Nn * run - (__int128)(j + 1) * T;
-      Eh[j] = i128_to_double(Nn * Sp - M) * f.Cf;
-    }
-    __syncthreads();
-    const double Eapp = -E0;
-    for (int j = j0; j < j1; ++j) {
-      const double left = Eh[j == 0 ? N - 1 : j - 1];
-      E[j] = 0.5 * (left + Eh[j]) + Eapp;
-    }
+    if (j0 == 0) Ef[N] = (R)E[0];
   }
+  if (bad) atomicOr(&ctl->status, kStNonFinite);
+  if (advance && t == 0) {
+    ctl->step += 1;
+    ctl->m_steps += 1;
+  }
+}
+
+// Diagnostic sample of the field step (one CTA, diagnostic steps only):
+// phi_j = -dx sum_{k<j} E_{k+1/2} (space-charge potential, phi_0 = 0), densities, E.
+template <class R>
+__global__ void __launch_bounds__(kFieldThreads, 1)
+k_field_diag(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi,
+             Ctl *ctl, const double *E, const double *Eh, Moments m) {
+  __shared__ double shd[kFieldThreads];
+  const int N = f.N;
+  const int t = threadIdx.x;
+  const int seg = f.seg;
+  const int j0 = min(N, t * seg), j1 = min(N, j0 + seg);
+  double loc = 0.0;
+  for (int j = j0; j < j1; ++j) loc += Eh[j];
+  double tot;
+  const double pre = block_excl_scan_f64(loc, shd, tot);
+  double run = pre;
   for (int j = j0; j < j1; ++j) {
-    if (!isfinite(E[j])) bad = true;
-    Ef[j] = (R)E[j];
+    m.phi[j] += -f.dx * run;
+    run += Eh[j];
   }
-  __syncthreads();
-  if (t == 0) Ef[N] = Ef[0];
-  if (__syncthreads_or(bad) && t == 0) atomicOr(&ctl->status, kStNonFinite);
-  if (diag) {
-    // phi_j = -dx sum_{k<j} E_{k+1/2} (space-charge potential, phi_0 = 0)
-    double loc = 0.0;
-    for (int j = j0; j < j1; ++j) loc += Eh[j];
-    double tot;
-    double *shd = reinterpret_cast<double *>(sh);
-    const double pre = block_excl_scan_f64(loc, shd, tot);
-    double run = pre;
-    for (int j = j0; j < j1; ++j) {
-      m.phi[j] += -f.dx * run;
-      run += Eh[j];
-      m.ne[j] += (double)(long long)Qe[j] * (1.0 / 4294967296.0);
-      m.ni[j] += (double)(long long)Qi[j] * (1.0 / 4294967296.0);
-      m.E[j] += E[j];
-    }
+  for (int j = t; j < N; j += blockDim.x) {
+    m.ne[j] += (double)(long long)Qe[j] * (1.0 / 4294967296.0);
+    m.ni[j] += (double)(long long)Qi[j] * (1.0 / 4294967296.0);
+    m.E[j] += E[j];
   }
   __syncthreads();
   if (t == 0) {
-    ctl->step = stepll + 1;
-    ctl->m_steps += 1;
-    if (diag) { ctl->m_samples += 1; ctl->n_diag += 1; }
+    ctl->m_samples += 1;
+    ctl->n_diag += 1;
   }
 }
 
 template <class R>
 void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned long long *Qi, Ctl *ctl, double *E,
-                  double *Eh, R *Ef, Moments m, cudaStream_t st) {
-  k_field<R><<<1, kFieldThreads, 0, st>>>(f, Qe, Qi, ctl, E, Eh, Ef, m);
+                  double *Eh, R *Ef, Moments m, long long *Dg, FieldScan *fs, bool diag, bool advance,
+                  cudaStream_t st) {
+  if (f.field_mode == PIC_FIELD_POISSON) {
+    const int bytes = f.smem ? (f.N + f.N / 16 + 1) * 8 : 0;
+    if (f.smem) cudaFuncSetAttribute(k_field_scan<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    k_field_scan<R><<<1, kFieldThreads, bytes, st>>>(f, Qe, Qi, Dg, fs);
+  }
+  k_field_eval<R><<<kFieldThreads / 32, 32, 0, st>>>(f, Qe, Qi, ctl, fs, E, Eh, Ef, advance ? 1 : 0);
+  if (diag) k_field_diag<R><<<1, kFieldThreads, 0, st>>>(f, Qe, Qi, ctl, E, Eh, m);
 }
 
 __global__ void k_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n) {
@@ -796,7 +890,8 @@ void launch_halfstep(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, const R *E
   template void launch_births<R>(const StepK<R> &, SpeciesDev, SpeciesDev, Ctl *, BirthBuf<R>, K3Scratch, int,      \
                                  cudaStream_t);                                                                      \
   template void launch_field<R>(const FieldK &, const unsigned long long *, const unsigned long long *, Ctl *,       \
-                                double *, double *, R *, Moments, cudaStream_t);                                    \
+                                double *, double *, R *, Moments, long long *, FieldScan *, bool, bool,             \
+                                cudaStream_t);                                                                      \
   template int push_smem_bytes<R>(int);
 PIC_INST(double)
 PIC_INST(float)
