@@ -224,6 +224,25 @@ void pic_free(pic_handle *h);
 /* Message of the last error on this handle (NULL: the last global error). */
 const char *pic_last_error(pic_handle *h);
 
+/* Periodic Poisson solve of Sec. II on caller device memory: the field step
+ * that pic_step runs every step ("two tridiagonal systems" in the paper; here
+ * the algebraically identical exact route).  From fixed-point node charges
+ * (2^32 per particle) it computes the half-node space-charge field
+ *   E_{j+1/2} = C (N S'_j - M) / N^2,  S'_j = N sum_{k<=j} D_k - (j+1) T,
+ *   D = Q_i - Q_e, T = sum D, M = sum S'   (zero-mean field, uniform
+ *   background T/N removed; integers exact, one rounding to double)
+ * and the node field E_j = (E_{j-1/2} + E_{j+1/2}) / 2 - E0.
+ *   Q_i, Q_e  device int64[n_cells], 3 <= n_cells <= 65536
+ *   C         e w / (eps0 2^32): field of one fixed-point unit (V/m)
+ *   E0        |applied field| (V/m)
+ *   E, E_half device double[n_cells], written
+ *   stream    cudaStream_t to run on (NULL: the legacy default stream)
+ * Allocates its scratch with cudaMalloc, frees it, and synchronises the
+ * stream before returning.  Errors: PIC_EINVAL (bad size or NULL pointer),
+ * PIC_ENOMEM, PIC_ECUDA, PIC_ENONFINITE (a field value is not finite). */
+int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, double C, double E0, double *E,
+                       double *E_half, void *stream);
+
 /* Self-test hook: int128 -> double conversion used by the field solve, run
  * on the device: v_k = hi[k] 2^64 + lo[k]; out[k] = double nearest to v_k
  * (ties to even).  Host arrays of n. */

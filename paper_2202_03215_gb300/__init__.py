@@ -107,6 +107,8 @@ def lib() -> C.CDLL:
         L.pic_last_error.restype = C.c_char_p
         L.pic_test_i128_to_double.argtypes = [_I64, _U64, _D, C.c_int]
         L.pic_abi_version.restype = C.c_int
+        L.pic_field_periodic.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]
         L.pic_set_timing.argtypes = [C.c_void_p, C.c_int]
         L.pic_kernel_times.argtypes = [C.c_void_p, _D, _I64]
         _lib = L
@@ -152,6 +154,18 @@ def i128_to_double(values) -> np.ndarray:
     out = np.zeros(len(vals))
     _check(lib().pic_test_i128_to_double(_ptr(hi, _I64), _ptr(lo, _U64), _ptr(out, _D), len(vals)))
     return out
+
+
+def field_periodic(Q_i, Q_e, C_unit: float, E0: float, stream: int = 0):
+    """Periodic Poisson solve on device tensors (int64 node charges, 2^32 per particle).
+    Returns (E, E_half) as float64 device tensors of the same length."""
+    import torch
+    n = Q_i.numel()
+    E = torch.empty(n, dtype=torch.float64, device=Q_i.device)
+    Eh = torch.empty_like(E)
+    _check(lib().pic_field_periodic(Q_i.data_ptr(), Q_e.data_ptr(), n, C_unit, E0, E.data_ptr(), Eh.data_ptr(),
+                                    stream or None))
+    return E, Eh
 
 
 class Column:

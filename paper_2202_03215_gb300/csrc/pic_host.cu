@@ -731,6 +731,47 @@ void pic_free(pic_handle *h) {
   delete h;
 }
 
+int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, double C, double E0, double *E,
+                       double *E_half, void *stream) {
+  if (!Q_i || !Q_e || !E || !E_half || n_cells < 3 || n_cells > 65536)
+    return set_err(nullptr, PIC_EINVAL, "bad arguments");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int N = n_cells;
+  pic::Ctl *ctl = nullptr;
+  pic::FieldScan *fs = nullptr;
+  long long *Dg = nullptr;
+  double *Ef = nullptr;
+  int rc = 0;
+  if (cudaMalloc(&ctl, sizeof(pic::Ctl)) != cudaSuccess || cudaMalloc(&fs, sizeof(pic::FieldScan)) != cudaSuccess ||
+      cudaMalloc(&Dg, ((size_t)N + N / 16 + 1) * 8) != cudaSuccess ||
+      cudaMalloc(&Ef, ((size_t)N + 1) * 8) != cudaSuccess) {
+    rc = set_err(nullptr, PIC_ENOMEM, "device allocation failed");
+  } else {
+    pic::Ctl c{};
+    c.E0 = E0;
+    pic::FieldK f{};
+    f.N = N;
+    f.field_mode = PIC_FIELD_POISSON;
+    f.smem = N <= pic::kFieldSmemMax ? 1 : 0;
+    f.seg = (N + pic::kFieldThreads - 1) / pic::kFieldThreads;
+    f.Cf = C / ((double)N * (double)N);
+    if (cudaMemcpyAsync(ctl, &c, sizeof c, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = set_err(nullptr, PIC_ECUDA, "upload failed");
+    } else {
+      pic::launch_field<double>(f, reinterpret_cast<const unsigned long long *>(Q_e),
+                                reinterpret_cast<const unsigned long long *>(Q_i), ctl, E, E_half, Ef, pic::Moments{},
+                                Dg, fs, false, false, st);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&c, ctl, sizeof c, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) rc = set_err(nullptr, PIC_ECUDA, "%s", cudaGetErrorString(e));
+      else if (c.status & pic::kStNonFinite) rc = set_err(nullptr, PIC_ENONFINITE, "the field became non-finite");
+    }
+  }
+  cudaFree(ctl); cudaFree(fs); cudaFree(Dg); cudaFree(Ef);
+  return rc;
+}
+
 int pic_test_i128_to_double(const int64_t *hi, const uint64_t *lo, double *out, int n) {
   if (!hi || !lo || !out || n < 0) return set_err(nullptr, PIC_EINVAL, "bad arguments");
   if (n == 0) return 0;
