@@ -243,6 +243,25 @@ const char *pic_last_error(pic_handle *h);
 int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, double C, double E0, double *E,
                        double *E_half, void *stream);
 
+/* pic_field_periodic for callers that must not allocate device memory during
+ * a call.  (The paper has no counterpart: this is a deployment variant.)
+ * pic_field_periodic gets its scratch with cudaMalloc and returns it with
+ * cudaFree, and cudaFree waits for the whole device to go idle, stalling the
+ * caller's other streams; callers that manage device memory through their own
+ * pool may not allocate behind it at all.  This variant takes the same
+ * arguments and computes the same result (bit for bit), but keeps its scratch
+ * in a fixed array built into the library: about 1.1 MB that every GPU which
+ * loads the library holds until the process exits.  It calls no allocator.
+ *   n_cells    3 <= n_cells <= 65536; larger sizes return PIC_EINVAL
+ *   the first call on a device looks up the array's device address (once per
+ *   device, with that device current): make it before any stream capture
+ *   every call shares and overwrites the one array: calls that overlap on the
+ *   GPU (other streams, other host threads on the same device) race; order them
+ * Synchronises the stream before returning.  Errors are returned as codes only
+ * (PIC_EINVAL, PIC_ECUDA, PIC_ENONFINITE); pic_last_error does not see them. */
+int pic_field_periodic_noalloc(const int64_t *Q_i, const int64_t *Q_e, int n_cells, double C, double E0, double *E,
+                               double *E_half, void *stream);
+
 /* Self-test hook: int128 -> double conversion used by the field solve, run
  * on the device: v_k = hi[k] 2^64 + lo[k]; out[k] = double nearest to v_k
  * (ties to even).  Host arrays of n. */

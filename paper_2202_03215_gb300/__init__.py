@@ -109,6 +109,8 @@ def lib() -> C.CDLL:
         L.pic_abi_version.restype = C.c_int
         L.pic_field_periodic.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
                                          C.c_void_p, C.c_void_p, C.c_void_p]
+        L.pic_field_periodic_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                                 C.c_void_p, C.c_void_p, C.c_void_p]
         L.pic_set_timing.argtypes = [C.c_void_p, C.c_int]
         L.pic_kernel_times.argtypes = [C.c_void_p, _D, _I64]
         _lib = L
@@ -166,6 +168,15 @@ def field_periodic(Q_i, Q_e, C_unit: float, E0: float, stream: int = 0):
     _check(lib().pic_field_periodic(Q_i.data_ptr(), Q_e.data_ptr(), n, C_unit, E0, E.data_ptr(), Eh.data_ptr(),
                                     stream or None))
     return E, Eh
+
+
+def field_periodic_noalloc(Q_i, Q_e, C_unit: float, E0: float, E, E_half, stream: int = 0) -> None:
+    """pic_field_periodic_noalloc: the same solve with caller-provided outputs E, E_half
+    (float64 device tensors) and no device allocation inside the call."""
+    rc = lib().pic_field_periodic_noalloc(Q_i.data_ptr(), Q_e.data_ptr(), Q_i.numel(), C_unit, E0,
+                                          E.data_ptr(), E_half.data_ptr(), stream or None)
+    if rc:
+        raise PicError(rc, "pic_field_periodic_noalloc failed")
 
 
 class Column:
