@@ -105,7 +105,7 @@ typedef struct pic_params {
   double I_A, U_src, R_ext_ohm_m2;  /* current / source / resistor (reserved drives) */
   int32_t n_xsec, pad0;
   const pic_xsec *xsec;    /* n_xsec processes; at most 8 per species */
-  int32_t n_cells;         /* grid cells = nodes (periodic), >= 3 */
+  int32_t n_cells;         /* grid cells = nodes (periodic), 3 <= n_cells <= 65536 */
   int32_t ion_subcycle;    /* ions advance every ion_subcycle steps with dt_i = ion_subcycle dt; 0 = frozen */
   double dt_s;             /* electron time step dt (Sec. II: dt < 0.2/w_pe) */
   int64_t n_e0, n_i0;      /* initial macroparticles per species */

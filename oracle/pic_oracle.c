@@ -724,12 +724,43 @@ static int births_and_losses(ora_t *h, int ion_pushed) {
   return 0;
 }
 
+/* Stable counting sort of one species by cell (build reading: particles are
+ * reordered periodically so that each GPU thread block works on a narrow
+ * cell window; slots, and hence victim draws, depend on the order, so the
+ * sort is part of the step's definition).  Equal cells keep slot order. */
+static void sort_species(ora_t *h, species *s) {
+  int N = h->N;
+  int64_t n = s->n;
+  int64_t *start = (int64_t *)xcalloc((size_t)N + 1, 8);
+  for (int64_t p = 0; p < n; ++p) start[s->cell[p] + 1]++;
+  for (int c = 0; c < N; ++c) start[c + 1] += start[c];
+  species t;
+  t.cell = (int32_t *)xcalloc((size_t)n, 4); t.off = (real *)xcalloc((size_t)n, sizeof(real));
+  t.vx = (real *)xcalloc((size_t)n, sizeof(real)); t.vy = (real *)xcalloc((size_t)n, sizeof(real));
+  t.vz = (real *)xcalloc((size_t)n, sizeof(real)); t.id = (uint64_t *)xcalloc((size_t)n, 8);
+  for (int64_t p = 0; p < n; ++p) {
+    int64_t q = start[s->cell[p]]++;
+    t.cell[q] = s->cell[p]; t.off[q] = s->off[p]; t.vx[q] = s->vx[p]; t.vy[q] = s->vy[p]; t.vz[q] = s->vz[p];
+    t.id[q] = s->id[p];
+  }
+  memcpy(s->cell, t.cell, (size_t)n * 4); memcpy(s->off, t.off, (size_t)n * sizeof(real));
+  memcpy(s->vx, t.vx, (size_t)n * sizeof(real)); memcpy(s->vy, t.vy, (size_t)n * sizeof(real));
+  memcpy(s->vz, t.vz, (size_t)n * sizeof(real)); memcpy(s->id, t.id, (size_t)n * 8);
+  free(t.cell); free(t.off); free(t.vx); free(t.vy); free(t.vz); free(t.id); free(start);
+}
+
 /* one full step s -> s+1 */
 static int step_once(ora_t *h) {
   int sub = h->p.ion_subcycle;
   int ion_push = (sub > 0) && (h->step % sub == 0);
   int diag = (h->p.diag_every > 0) && (h->step % h->p.diag_every == 0);
   h->nde = 0; h->ndi = 0; h->nb = 0;
+  /* electrons are sorted every sort_every steps, ions every sort_every * ion_subcycle steps */
+  if (h->p.sort_every > 0 && h->step % h->p.sort_every == 0) {
+    sort_species(h, &h->e);
+    int64_t pi = (int64_t)h->p.sort_every * (sub > 0 ? sub : 1);
+    if (h->step % pi == 0) sort_species(h, &h->i);
+  }
   memset(h->e.Q, 0, sizeof(int64_t) * (size_t)h->N);
   for (int64_t p = 0; p < h->e.n; ++p) electron_step(h, p, diag);
   if (ion_push) {

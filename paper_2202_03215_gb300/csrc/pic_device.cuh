@@ -18,9 +18,9 @@ namespace pic {
 __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;   // one 32x32->64 multiply each
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
     if (r < 9) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
   }
   return c;
@@ -104,8 +104,12 @@ __device__ __forceinline__ void push(int N, R a, R d, R E, int32_t &cell, R &off
   f = f - c;
   int32_t cl = cell + (int32_t)c;
   if (f >= (R)1) { f = (R)0; cl += 1; }
-  cl %= N;
-  if (cl < 0) cl += N;
+  // cl mod N, without a division when the particle moved less than a column length
+  if (cl >= N) cl = cl < 2 * N ? cl - N : cl % N;
+  else if (cl < 0) {
+    cl = cl >= -N ? cl + N : cl % N;
+    if (cl < 0) cl += N;
+  }
   cell = cl;
   off = f;
 }

@@ -45,6 +45,7 @@ struct pic_handle {
   double *E = nullptr, *Eh = nullptr;
   long long *Dg = nullptr;            // field scratch when the nodes exceed shared memory
   pic::FieldScan *fs = nullptr;       // exact prefix data between the two field kernels
+  pic::SortBuf sb[2]{};               // sort buffers per species (sort_every > 0)
   void *Ef = nullptr;                 // R[N+1]
   void *tab[2] = {nullptr, nullptr};  // R[np * ntab]
   float *gauss = nullptr;
@@ -284,6 +285,15 @@ template <class R> int alloc_species(pic_handle *h) {
     }
   }
   CU(h, cudaMalloc(&h->Ef, ((size_t)h->N + 1) * sizeof(R)));
+  if (h->p.sort_every > 0) {
+    for (int q = 0; q < 2; ++q) {
+      pic::SortBuf &b = h->sb[q];
+      CU(h, cudaMalloc(&b.cell, (size_t)cap * 4));
+      CU(h, cudaMalloc(&b.rec, (size_t)cap * sizeof(typename pic::Rec<R>::T)));
+      CU(h, cudaMalloc(&b.id, (size_t)cap * 8));
+      CU(h, cudaMalloc(&b.hist, pic::sort_hist_words(cap) * 4));
+    }
+  }
   // birth staging: parent, cell (int32), off + 3 ve + 3 vi (R)
   const size_t sc = pic::kStageCap;
   CU(h, cudaMalloc(&h->bb_mem, sc * 8 + sc * 7 * sizeof(R)));
@@ -319,6 +329,16 @@ template <class R> int enqueue_step(pic_handle *h) {
   const int sub = h->p.ion_subcycle;
   const bool ion_push = sub > 0 && (h->host_step % sub) == 0;
   const R *Ef = reinterpret_cast<const R *>(h->Ef);
+  // electrons sorted every sort_every steps, ions every sort_every * ion_subcycle steps
+  const int se = h->p.sort_every;
+  if (se > 0 && h->host_step % se == 0) {
+    t_begin(h);
+    pic::launch_sort<R>(h->sp[0], h->sb[0], &h->ctl->n[0], h->sp[0].cap, h->N, h->nsm, h->stream);
+    const long long pi = (long long)se * (sub > 0 ? sub : 1);
+    if (h->host_step % pi == 0)
+      pic::launch_sort<R>(h->sp[1], h->sb[1], &h->ctl->n[1], h->sp[1].cap, h->N, h->nsm, h->stream);
+    t_end(h, PIC_K_SORT);
+  }
   CU(h, cudaMemsetAsync(h->sp[0].Q, 0, (size_t)h->N * 8, h->stream));
   t_begin(h);
   pic::launch_push<R>(k, h->sp[0], h->ctl, Ef, bbuf<R>(h), h->m, 0, h->nsm, h->stream);
@@ -348,6 +368,7 @@ void free_all(pic_handle *h) {
   for (int q = 0; q < 2; ++q) {
     cudaFree(h->sp[q].cell); cudaFree(h->sp[q].rec); cudaFree(h->sp[q].id); cudaFree(h->sp[q].code);
     cudaFree(h->sp[q].Q); cudaFree(h->sp[q].dead); cudaFree(h->tab[q]);
+    cudaFree(h->sb[q].cell); cudaFree(h->sb[q].rec); cudaFree(h->sb[q].id); cudaFree(h->sb[q].hist);
   }
   cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->Dg); cudaFree(h->fs); cudaFree(h->Ef); cudaFree(h->gauss);
   cudaFree(h->bb_mem); cudaFree(h->k3_mem); cudaFree(h->mom); cudaFree(h->mom_iz);
@@ -357,7 +378,7 @@ void free_all(pic_handle *h) {
 
 int validate(const pic_params *p) {
   if (!p) return set_err(nullptr, PIC_EINVAL, "params is NULL");
-  if (p->n_cells < 3) return set_err(nullptr, PIC_EINVAL, "n_cells must be >= 3");
+  if (p->n_cells < 3 || p->n_cells > 65536) return set_err(nullptr, PIC_EINVAL, "n_cells must be in [3, 65536]");
   if (!(p->dt_s > 0) || !(p->L_m > 0)) return set_err(nullptr, PIC_EINVAL, "dt and L must be > 0");
   if (p->n_e0 < 0 || p->n_i0 < 0) return set_err(nullptr, PIC_EINVAL, "negative particle count");
   if (p->n_table < 3) return set_err(nullptr, PIC_EINVAL, "n_table must be >= 3");

@@ -108,6 +108,21 @@ struct FieldK {
   double dx;
 };
 
+// second set of particle buffers and digit histograms for the sort
+struct SortBuf {
+  int32_t *cell;
+  void *rec;
+  uint64_t *id;
+  unsigned *hist;
+};
+
+// sort (pic_sort.cu)
+int sort_passes(int n_cells);
+size_t sort_hist_words(int64_t cap);
+template <class R>
+void launch_sort(SpeciesDev s, SortBuf alt, const long long *n_dev, long long cap, int n_cells, int nsm,
+                 cudaStream_t st);
+
 // launchers (pic_kernels.cu)
 template <class R>
 void launch_init(const StepK<R> &k, SpeciesDev s, int species, int64_t n, uint64_t id0, R sig, cudaStream_t st);

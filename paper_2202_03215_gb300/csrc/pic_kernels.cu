@@ -80,9 +80,229 @@ __device__ void bitonic_sort(unsigned long long *a, int n2) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Particle step.  One persistent CTA per SM walks a contiguous slot range.
-// Shared memory: the node field (N+1 values) and 64-bit fixed-point charge
-// bins over a cell window (the whole grid when it fits).
+// Particle step.  One persistent CTA per SM walks a contiguous slot range in
+// tiles of blockDim particles.
+//   phase A (every particle): gather, leapfrog push, wrap, the Philox block
+//     that decides collision candidacy (u0 < P_null) and radial loss, the
+//     cloud-in-cell deposit (warp-aggregated over equal cells into 64-bit
+//     fixed-point bins in shared memory over a cell window), and the store of
+//     every non-candidate; candidates go to a shared-memory queue;
+//   phase B (whenever a warp has queued 32 candidates, and at the end): the
+//     collision path for 32 queued candidates, one per lane, so that a warp
+//     runs it densely instead of whenever any of its lanes collides.
+// Every warp owns its queue (64 entries): no block-wide barrier in the loop,
+// so the warps' memory latencies overlap freely.  Collisions change
+// velocities only, so the deposit in phase A is final.
+
+constexpr int kWarpQ = 64;                               // queue entries per warp
+constexpr int kQcap = (kStepThreads / 32) * kWarpQ;      // queue entries per CTA
+
+template <class R> struct Queue {
+  uint64_t *id;
+  R *off, *vx, *vy, *vz, *u1;
+  int32_t *slot, *cell;
+};
+
+template <class R> __device__ __forceinline__ Queue<R> queue_at(unsigned char *q) {
+  Queue<R> Q;
+  Q.id = reinterpret_cast<uint64_t *>(q);
+  Q.off = reinterpret_cast<R *>(Q.id + kQcap);
+  Q.vx = Q.off + kQcap;
+  Q.vy = Q.vx + kQcap;
+  Q.vz = Q.vy + kQcap;
+  Q.u1 = Q.vz + kQcap;
+  Q.slot = reinterpret_cast<int32_t *>(Q.u1 + kQcap);
+  Q.cell = Q.slot + kQcap;
+  return Q;
+}
+template <class R> constexpr size_t queue_bytes() { return (size_t)kQcap * (8 + 5 * sizeof(R) + 8); }
+
+// diagnostic moments of one particle (FP64, cloud-in-cell weights)
+template <class R, int SP>
+__device__ __forceinline__ void add_moments(const SpecK<R> &sp, const Moments &m, int N, int32_t cell, R off, R vx,
+                                            R vy, R vz) {
+  const unsigned long long kk = wfix(off);
+  const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+  const double w1 = (double)kk * (1.0 / 4294967296.0), w0 = 1.0 - w1;
+  const double vxd = (double)vx;
+  if constexpr (SP == 0) {
+    const double eps = (double)(sp.K * (vx * vx + vy * vy + vz * vz));
+    atomicAdd(m.ge + cell, w0 * vxd); atomicAdd(m.ge + c1, w1 * vxd);
+    atomicAdd(m.ee + cell, w0 * eps); atomicAdd(m.ee + c1, w1 * eps);
+    const double h = eps * vxd;
+    atomicAdd(m.he + cell, w0 * h); atomicAdd(m.he + c1, w1 * h);
+  } else {
+    atomicAdd(m.gi + cell, w0 * vxd); atomicAdd(m.gi + c1, w1 * vxd);
+  }
+}
+
+// Collision of one candidate (u0 < P_null already drawn): process choice by
+// u1 nu* against the cumulative collision frequencies, then the scattering.
+// Returns the process index within the species, or -1 for a null collision.
+template <class R, int SP>
+__device__ __forceinline__ int collide(const StepK<R> &k, const SpecK<R> &sp, Ctl *ctl, const BirthBuf<R> &bb,
+                                       const Moments &m, uint64_t id, uint32_t step, uint32_t c3, int32_t p,
+                                       int32_t cell, R off, R u1, R &vx, R &vy, R &vz, bool &ovf) {
+  const int N = k.N;
+  UStream<R> us(seed_key(k.seed), id, step, c3);
+  int sel = -1;
+  if constexpr (SP == 0) {
+    // electron-neutral: elastic, excitation levels, ionization (Sec. II)
+    const R eps = sp.K * (vx * vx + vy * vy + vz * vz);
+    R fr;
+    const int it = tab_pos(eps, sp.inv_de, k.ntab, fr, ovf);
+    const R r = u1 * sp.nus;
+    R cum = 0;
+    for (int q = 0; q < sp.np; ++q) {
+      R nu;
+      if (sp.kind[q] != PIC_ELASTIC && eps < sp.thr[q]) nu = 0;
+      else nu = tab_at(sp.tab + (size_t)q * k.ntab, it, fr);
+      cum = cum + nu;
+      if (r < cum) { sel = q; break; }
+    }
+    if (sel >= 0) {
+      const int kind = sp.kind[sel];
+      R nx, ny, nz;
+      if (kind == PIC_ELASTIC) {
+        iso_dir(us, nx, ny, nz);
+        const R vm = sqrt(vx * vx + vy * vy + vz * vz);
+        const R cosx = (vm > (R)0) ? (nx * vx + ny * vy + nz * vz) / vm : (R)0;
+        const R e2 = eps * ((R)1 - k.em * ((R)1 - cosx));
+        const R spd = sqrt(e2 * k.V_e);
+        vx = spd * nx; vy = spd * ny; vz = spd * nz;
+      } else if (kind == PIC_EXCITATION) {
+        const R e2 = eps - sp.thr[sel];
+        iso_dir(us, nx, ny, nz);
+        const R spd = sqrt(e2 * k.V_e);
+        vx = spd * nx; vy = spd * ny; vz = spd * nz;
+      } else {
+        const R er = eps - sp.thr[sel];
+        const R ush = us.next();
+        const R e_ej = ush * er;
+        const R e_sc = er - e_ej;
+        iso_dir(us, nx, ny, nz);
+        const R spd = sqrt(e_sc * k.V_e);
+        vx = spd * nx; vy = spd * ny; vz = spd * nz;
+        R mx, my, mz;
+        iso_dir(us, mx, my, mz);
+        const R sq = sqrt(e_ej * k.V_e);
+        const R g0 = gauss<R>(k.gauss, us.next());
+        const R g1 = gauss<R>(k.gauss, us.next());
+        const R g2 = gauss<R>(k.gauss, us.next());
+        if (k.loss_mode != PIC_LOSS_SWARM) {
+          const int idx = atomicAdd(&ctl->n_birth, 1);
+          if (idx < kStageCap) {
+            bb.parent[idx] = p;
+            bb.cell[idx] = cell;
+            bb.off[idx] = off;
+            bb.ve[idx] = sq * mx; bb.ve[kStageCap + idx] = sq * my; bb.ve[2 * kStageCap + idx] = sq * mz;
+            bb.vi[idx] = k.sig_n * g0; bb.vi[kStageCap + idx] = k.sig_n * g1; bb.vi[2 * kStageCap + idx] = k.sig_n * g2;
+          } else {
+            atomicOr(&ctl->status, kStBirthOverflow);
+          }
+        } else {
+          atomicAdd(&ctl->births, 1ull);
+        }
+        const unsigned long long kk = wfix(off);
+        const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+        atomicAdd(m.iz + cell, (1ull << 32) - kk);
+        atomicAdd(m.iz + c1, kk);
+      }
+    }
+  } else {
+    // ion-neutral: neutral velocity from the gas Maxwellian, relative speed g,
+    // charge exchange or isotropic elastic in the centre-of-mass frame
+    const R g0 = gauss<R>(k.gauss, us.next());
+    const R g1 = gauss<R>(k.gauss, us.next());
+    const R g2 = gauss<R>(k.gauss, us.next());
+    const R nvx = k.sig_n * g0, nvy = k.sig_n * g1, nvz = k.sig_n * g2;
+    const R gx = vx - nvx, gy = vy - nvy, gz = vz - nvz;
+    const R eg = sp.K * (gx * gx + gy * gy + gz * gz);
+    R fr;
+    const int it = tab_pos(eg, sp.inv_de, k.ntab, fr, ovf);
+    const R r = u1 * sp.nus;
+    R cum = 0;
+    for (int q = 0; q < sp.np; ++q) {
+      cum = cum + tab_at(sp.tab + (size_t)q * k.ntab, it, fr);
+      if (r < cum) { sel = q; break; }
+    }
+    if (sel >= 0) {
+      if (sp.kind[sel] == PIC_ION_CX) {
+        vx = nvx; vy = nvy; vz = nvz;
+      } else {
+        R nx, ny, nz;
+        iso_dir(us, nx, ny, nz);
+        const R gm = sqrt(gx * gx + gy * gy + gz * gz);
+        const R hg = (R)0.5 * gm;
+        vx = (R)0.5 * (vx + nvx) + hg * nx;
+        vy = (R)0.5 * (vy + nvy) + hg * ny;
+        vz = (R)0.5 * (vz + nvz) + hg * nz;
+      }
+    }
+  }
+  return sel;
+}
+
+// 64-bit fixed-point add into a shared-memory bin held as two 32-bit words:
+// native 32-bit atomics, the carry of the low word propagated exactly
+__device__ __forceinline__ void bin_add(unsigned *lo, unsigned *hi, unsigned long long v) {
+  const unsigned vlo = (unsigned)v;
+  const unsigned vhi = (unsigned)(v >> 32);
+  const unsigned old = atomicAdd(lo, vlo);
+  const unsigned c = vhi + ((old + vlo < old) ? 1u : 0u);
+  if (c) atomicAdd(hi, c);
+}
+
+// Deposit of one warp, summed over runs of neighbouring lanes that share a
+// cell (sorted particles come in long runs): a segmented scan of the
+// fixed-point weights with shuffles, then the last lane of each run adds
+// node cell += n 2^32 - sum k and node cell+1 += sum k (exact integers).
+// Lanes with in == false contribute nothing.  All 32 lanes must call it.
+__device__ __forceinline__ void deposit_runs(bool in, int lane, int32_t cell, unsigned long long kk, int N, int W,
+                                             int c0, unsigned *blo, unsigned *bhi, unsigned long long *Q) {
+  const unsigned mask = __ballot_sync(kFull, in);
+  const int32_t pc = __shfl_up_sync(kFull, cell, 1);
+  const int32_t nc = __shfl_down_sync(kFull, cell, 1);
+  const bool pin = lane > 0 && ((mask >> (lane - 1)) & 1u);
+  const bool nin = lane < 31 && ((mask >> (lane + 1)) & 1u);
+  const bool head = !in || !pin || pc != cell;
+  const bool tail = in && (!nin || nc != cell);
+  int start = head ? lane : 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, start, o);
+    if (lane >= o) start = max(start, t);
+  }
+  // low 16 bits of k plus a count in bits 21..; high 16 bits separately (no overflow over 32 lanes)
+  unsigned a = in ? (((unsigned)kk & 0xffffu) | (1u << 21)) : 0u;
+  unsigned b = in ? (unsigned)(kk >> 16) : 0u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned ta = __shfl_up_sync(kFull, a, o), tb = __shfl_up_sync(kFull, b, o);
+    if (lane - o >= start) { a += ta; b += tb; }
+  }
+  if (tail) {
+    const unsigned long long sk = ((unsigned long long)b << 16) + (unsigned long long)(a & 0x1fffffu);
+    const unsigned long long A = ((unsigned long long)(a >> 21) << 32) - sk;
+    const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+    int li = cell;
+    if (W < N) {
+      li = cell - c0;
+      if (li < 0) li += N;
+    }
+    if (W == N) {
+      bin_add(blo + cell, bhi + cell, A);
+      bin_add(blo + c1, bhi + c1, sk);
+    } else if (li < W - 1) {
+      bin_add(blo + li, bhi + li, A);
+      bin_add(blo + li + 1, bhi + li + 1, sk);
+    } else {
+      atomicAdd(Q + cell, A);
+      atomicAdd(Q + c1, sk);
+    }
+  }
+}
+
 template <class R, int SP>
 __global__ void __launch_bounds__(kStepThreads, 1)
 k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef, BirthBuf<R> bb,
@@ -93,7 +313,9 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
   const SpecK<R> &sp = k.sp[SP];
   const size_t eb = smemE ? ((((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15) : 0;
   R *sE = reinterpret_cast<R *>(smem);
-  unsigned long long *bins = reinterpret_cast<unsigned long long *>(smem + eb);
+  unsigned *blo = reinterpret_cast<unsigned *>(smem + eb);   // bins: low and high 32-bit words
+  unsigned *bhi = blo + W;
+  const Queue<R> Qd = queue_at<R>(smem + eb + (size_t)W * 8);
   const long long n = ctl->n[SP];
   const long long stepll = ctl->step;
   const uint32_t step = (uint32_t)stepll;
@@ -105,190 +327,121 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
   const long long p1 = min(n, p0 + chunk);
   int c0 = 0;
   if (W < N && p0 < p1) {
-    c0 = s.cell[p0] - W / 16;
+    c0 = s.cell[p0] - W / 8;
     if (c0 < 0) c0 += N;
   }
   if (smemE)
     for (int j = threadIdx.x; j <= N; j += blockDim.x) sE[j] = Ef[j];
-  for (int j = threadIdx.x; j < W; j += blockDim.x) bins[j] = 0ull;
+  for (int j = threadIdx.x; j < W; j += blockDim.x) { blo[j] = 0u; bhi[j] = 0u; }
   if (threadIdx.x <= kMaxProc) s_cnt[threadIdx.x] = 0u;
   __syncthreads();
   const R *E = smemE ? sE : Ef;
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
   const bool radial = k.loss_mode == PIC_LOSS_RADIAL;
   const bool record = (k.flags & PIC_FLAG_RECORD_CODES) != 0;
+  const int qoff = (threadIdx.x >> 5) * kWarpQ;   // this warp's queue slice
+  int wq = 0;                                     // its length (warp-uniform)
 
-  for (long long base = p0; base < p1; base += blockDim.x) {
-    const long long p = base + threadIdx.x;
-    const bool valid = p < p1;
+  // collision path for the warp's first nq (<= 32) queued candidates, one per lane
+  auto flush = [&](int nq) {
     int sel = -1;
     bool ovf = false;
-    if (valid) {
-      int32_t cell = s.cell[p];
-      R off, vx, vy, vz;
-      rec_load<R>(s.rec, p, off, vx, vy, vz);
-      const uint64_t id = s.id[p];
-      const R Ep = gather(E, cell, off);
-      push<R>(N, sp.a, sp.d, Ep, cell, off, vx);
-      const uint4 w0 = philox10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, c3), key);
-      int code = -1;
-      const bool dead = radial && (w0.z < sp.Pw);
-      if (!dead) {
-        const R u0 = u_dec<R>(w0.x), u1 = u_dec<R>(w0.y);
-        if (u0 < sp.P) {
-          UStream<R> us(key, id, step, c3);
-          if constexpr (SP == 0) {
-            // electron-neutral: elastic, excitation levels, ionization (Sec. II)
-            const R eps = sp.K * (vx * vx + vy * vy + vz * vz);
-            R fr;
-            const int it = tab_pos(eps, sp.inv_de, k.ntab, fr, ovf);
-            const R r = u1 * sp.nus;
-            R cum = 0;
-            for (int q = 0; q < sp.np; ++q) {
-              R nu;
-              if (sp.kind[q] != PIC_ELASTIC && eps < sp.thr[q]) nu = 0;
-              else nu = tab_at(sp.tab + (size_t)q * k.ntab, it, fr);
-              cum = cum + nu;
-              if (r < cum) { sel = q; break; }
-            }
-            if (sel >= 0) {
-              const int kind = sp.kind[sel];
-              code = sp.xs[sel];
-              R nx, ny, nz;
-              if (kind == PIC_ELASTIC) {
-                iso_dir(us, nx, ny, nz);
-                const R vm = sqrt(vx * vx + vy * vy + vz * vz);
-                const R cosx = (vm > (R)0) ? (nx * vx + ny * vy + nz * vz) / vm : (R)0;
-                const R e2 = eps * ((R)1 - k.em * ((R)1 - cosx));
-                const R spd = sqrt(e2 * k.V_e);
-                vx = spd * nx; vy = spd * ny; vz = spd * nz;
-              } else if (kind == PIC_EXCITATION) {
-                const R e2 = eps - sp.thr[sel];
-                iso_dir(us, nx, ny, nz);
-                const R spd = sqrt(e2 * k.V_e);
-                vx = spd * nx; vy = spd * ny; vz = spd * nz;
-              } else {
-                const R er = eps - sp.thr[sel];
-                const R ush = us.next();
-                const R e_ej = ush * er;
-                const R e_sc = er - e_ej;
-                iso_dir(us, nx, ny, nz);
-                const R spd = sqrt(e_sc * k.V_e);
-                vx = spd * nx; vy = spd * ny; vz = spd * nz;
-                R mx, my, mz;
-                iso_dir(us, mx, my, mz);
-                const R sq = sqrt(e_ej * k.V_e);
-                const R g0 = gauss<R>(k.gauss, us.next());
-                const R g1 = gauss<R>(k.gauss, us.next());
-                const R g2 = gauss<R>(k.gauss, us.next());
-                if (k.loss_mode != PIC_LOSS_SWARM) {
-                  const int idx = atomicAdd(&ctl->n_birth, 1);
-                  if (idx < kStageCap) {
-                    bb.parent[idx] = (int32_t)p;
-                    bb.cell[idx] = cell;
-                    bb.off[idx] = off;
-                    bb.ve[idx] = sq * mx; bb.ve[kStageCap + idx] = sq * my; bb.ve[2 * kStageCap + idx] = sq * mz;
-                    bb.vi[idx] = k.sig_n * g0; bb.vi[kStageCap + idx] = k.sig_n * g1;
-                    bb.vi[2 * kStageCap + idx] = k.sig_n * g2;
-                  } else {
-                    atomicOr(&ctl->status, kStBirthOverflow);
-                  }
-                } else {
-                  atomicAdd(&ctl->births, 1ull);
-                }
-                const unsigned long long kk = wfix(off);
-                const int c1 = (cell + 1 == N) ? 0 : cell + 1;
-                atomicAdd(m.iz + cell, (1ull << 32) - kk);
-                atomicAdd(m.iz + c1, kk);
-              }
-            }
-          } else {
-            // ion-neutral: neutral velocity from the gas Maxwellian, relative speed g,
-            // charge exchange or isotropic elastic in the centre-of-mass frame
-            const R g0 = gauss<R>(k.gauss, us.next());
-            const R g1 = gauss<R>(k.gauss, us.next());
-            const R g2 = gauss<R>(k.gauss, us.next());
-            const R nvx = k.sig_n * g0, nvy = k.sig_n * g1, nvz = k.sig_n * g2;
-            const R gx = vx - nvx, gy = vy - nvy, gz = vz - nvz;
-            const R eg = sp.K * (gx * gx + gy * gy + gz * gz);
-            R fr;
-            const int it = tab_pos(eg, sp.inv_de, k.ntab, fr, ovf);
-            const R r = u1 * sp.nus;
-            R cum = 0;
-            for (int q = 0; q < sp.np; ++q) {
-              cum = cum + tab_at(sp.tab + (size_t)q * k.ntab, it, fr);
-              if (r < cum) { sel = q; break; }
-            }
-            if (sel >= 0) {
-              code = sp.xs[sel];
-              if (sp.kind[sel] == PIC_ION_CX) {
-                vx = nvx; vy = nvy; vz = nvz;
-              } else {
-                R nx, ny, nz;
-                iso_dir(us, nx, ny, nz);
-                const R gm = sqrt(gx * gx + gy * gy + gz * gz);
-                const R hg = (R)0.5 * gm;
-                vx = (R)0.5 * (vx + nvx) + hg * nx;
-                vy = (R)0.5 * (vy + nvy) + hg * ny;
-                vz = (R)0.5 * (vz + nvz) + hg * nz;
-              }
-            }
-          }
-        }
-      } else {
-        code = -2;
-      }
-      s.cell[p] = cell;
-      rec_store<R>(s.rec, p, off, vx, vy, vz);
-      if (record) s.code[p] = code;
-      if (dead) {
-        const int idx = atomicAdd(&ctl->n_dead[SP], 1);
-        if (idx < kStageCap) s.dead[idx] = (int32_t)p;
-        else atomicOr(&ctl->status, kStDeadOverflow);
-      } else {
-        const unsigned long long kk = wfix(off);
-        const unsigned long long a = (1ull << 32) - kk;
-        const int c1 = (cell + 1 == N) ? 0 : cell + 1;
-        if (W == N) {
-          atomicAdd(bins + cell, a);
-          atomicAdd(bins + c1, kk);
-        } else {
-          int li = cell - c0;
-          if (li < 0) li += N;
-          if (li < W - 1) {
-            atomicAdd(bins + li, a);
-            atomicAdd(bins + li + 1, kk);
-          } else {
-            atomicAdd(s.Q + cell, a);
-            atomicAdd(s.Q + c1, kk);
-          }
-        }
-        if (diag) {
-          const double w1 = (double)kk * (1.0 / 4294967296.0), w0 = 1.0 - w1;
-          const double vxd = (double)vx;
-          if constexpr (SP == 0) {
-            const double eps = (double)(sp.K * (vx * vx + vy * vy + vz * vz));
-            atomicAdd(m.ge + cell, w0 * vxd); atomicAdd(m.ge + c1, w1 * vxd);
-            atomicAdd(m.ee + cell, w0 * eps); atomicAdd(m.ee + c1, w1 * eps);
-            const double h = eps * vxd;
-            atomicAdd(m.he + cell, w0 * h); atomicAdd(m.he + c1, w1 * h);
-          } else {
-            atomicAdd(m.gi + cell, w0 * vxd); atomicAdd(m.gi + c1, w1 * vxd);
-          }
-        }
-      }
+    if (lane < nq) {
+      const int i = qoff + lane;
+      const int32_t qp = Qd.slot[i], qcell = Qd.cell[i];
+      const R qoff_ = Qd.off[i];
+      R qx = Qd.vx[i], qy = Qd.vy[i], qz = Qd.vz[i];
+      sel = collide<R, SP>(k, sp, ctl, bb, m, Qd.id[i], step, c3, qp, qcell, qoff_, Qd.u1[i], qx, qy, qz, ovf);
+      rec_store<R>(s.rec, qp, qoff_, qx, qy, qz);
+      if (record) s.code[qp] = sel >= 0 ? sp.xs[sel] : -1;
+      if (diag) add_moments<R, SP>(sp, m, N, qcell, qoff_, qx, qy, qz);
     }
-    // warp-aggregated collision counters
     for (int q = 0; q < sp.np; ++q) {
       const unsigned b = __ballot_sync(kFull, sel == q);
       if (lane == 0 && b) atomicAdd(&s_cnt[q], (unsigned)__popc(b));
     }
     const unsigned bo = __ballot_sync(kFull, ovf);
     if (lane == 0 && bo) atomicAdd(&s_cnt[kMaxProc], (unsigned)__popc(bo));
+    __syncwarp();
+  };
+
+  // software pipeline: the next tile's particle is loaded while this one is processed
+  int32_t n_cell = 0;
+  R n_off = 0, n_vx = 0, n_vy = 0, n_vz = 0;
+  uint64_t n_id = 0;
+  {
+    const int p = (int)p0 + threadIdx.x;
+    if (p < (int)p1) {
+      n_cell = s.cell[p];
+      rec_load<R>(s.rec, p, n_off, n_vx, n_vy, n_vz);
+      n_id = s.id[p];
+    }
   }
+  for (int base = (int)p0; base < (int)p1; base += blockDim.x) {
+    const int p = base + threadIdx.x;
+    const bool valid = p < (int)p1;
+    bool cand = false, dead = false;
+    int32_t cell = n_cell;
+    R off = n_off, vx = n_vx, vy = n_vy, vz = n_vz, u1 = 0;
+    uint64_t id = n_id;
+    {
+      const int pn = p + blockDim.x;
+      if (pn < (int)p1) {
+        n_cell = s.cell[pn];
+        rec_load<R>(s.rec, pn, n_off, n_vx, n_vy, n_vz);
+        n_id = s.id[pn];
+      }
+    }
+    if (valid) {
+      const R Ep = gather(E, cell, off);
+      push<R>(N, sp.a, sp.d, Ep, cell, off, vx);
+      const uint4 w0 = philox10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, c3), key);
+      dead = radial && (w0.z < sp.Pw);
+      if (!dead) {
+        u1 = u_dec<R>(w0.y);
+        cand = u_dec<R>(w0.x) < sp.P;
+      }
+      s.cell[p] = cell;
+      if (!cand) {
+        rec_store<R>(s.rec, p, off, vx, vy, vz);
+        if (record) s.code[p] = dead ? -2 : -1;
+        if (!dead && diag) add_moments<R, SP>(sp, m, N, cell, off, vx, vy, vz);
+      }
+      if (dead) {
+        const int idx = atomicAdd(&ctl->n_dead[SP], 1);
+        if (idx < kStageCap) s.dead[idx] = p;
+        else atomicOr(&ctl->status, kStDeadOverflow);
+      }
+    }
+    // queue the candidates in this warp's slice
+    const unsigned bal = __ballot_sync(kFull, cand);
+    if (cand) {
+      const int qi = qoff + wq + __popc(bal & lt);
+      Qd.id[qi] = id; Qd.off[qi] = off; Qd.vx[qi] = vx; Qd.vy[qi] = vy; Qd.vz[qi] = vz; Qd.u1[qi] = u1;
+      Qd.slot[qi] = p; Qd.cell[qi] = cell;
+    }
+    wq += __popc(bal);
+    // charge deposit, summed over runs of lanes in the same cell
+    deposit_runs(valid && !dead, lane, cell, wfix(off), N, W, c0, blo, bhi, s.Q);
+    __syncwarp();
+    if (wq >= 32) {
+      flush(32);
+      // move the remaining entries to the front of the slice
+      const int rest = wq - 32;
+      if (lane < rest) {
+        const int a = qoff + 32 + lane, b = qoff + lane;
+        Qd.id[b] = Qd.id[a]; Qd.off[b] = Qd.off[a]; Qd.vx[b] = Qd.vx[a]; Qd.vy[b] = Qd.vy[a];
+        Qd.vz[b] = Qd.vz[a]; Qd.u1[b] = Qd.u1[a]; Qd.slot[b] = Qd.slot[a]; Qd.cell[b] = Qd.cell[a];
+      }
+      __syncwarp();
+      wq = rest;
+    }
+  }
+  if (wq > 0) flush(wq);
   __syncthreads();
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
-    const unsigned long long v = bins[j];
+    const unsigned long long v = ((unsigned long long)bhi[j] << 32) | (unsigned long long)blo[j];
     if (v) {
       int node = j;
       if (W < N) { node = c0 + j; if (node >= N) node -= N; }
@@ -308,14 +461,16 @@ template <class R> int push_smem_bytes(int N) {
 template <class R>
 void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBuf<R> bb, Moments m, int species,
                  int nsm, cudaStream_t st) {
-  const size_t budget = 200 * 1024;
+  const size_t budget = 220 * 1024;
+  const size_t qb = queue_bytes<R>();
   size_t eb = (((size_t)k.N + 1) * sizeof(R) + 15) & ~(size_t)15;
-  int smemE = eb <= 128 * 1024 ? 1 : 0;
+  // the node field goes to shared memory when it leaves room for a 4096-node bin window
+  int smemE = eb + qb + 4096 * 8 <= budget ? 1 : 0;
   if (!smemE) eb = 0;
-  size_t wmax = (budget - eb) / 8;
+  const size_t wmax = (budget - eb - qb) / 8;
   int W = (int)((size_t)k.N < wmax ? (size_t)k.N : wmax);
-  if (W < (int)k.N) W &= ~63;
-  const size_t bytes = eb + (size_t)W * 8;
+  if (W < k.N) W = W < 8192 ? (W & ~63) : 8192;
+  const size_t bytes = eb + (size_t)W * 8 + qb;
   if (species == 0) {
     cudaFuncSetAttribute(k_push<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     k_push<R, 0><<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
@@ -635,20 +790,47 @@ __device__ __forceinline__ __int128 mul_u32(__int128 x, uint32_t n) {
   return (__int128)(((unsigned __int128)phi << 64) | (unsigned __int128)plo);
 }
 
+__device__ __forceinline__ __int128 shfl_up_i128(__int128 v, int o) {
+  const unsigned __int128 u = (unsigned __int128)v;
+  const unsigned long long lo = __shfl_up_sync(0xffffffffu, (unsigned long long)u, o);
+  const unsigned long long hi = __shfl_up_sync(0xffffffffu, (unsigned long long)(u >> 64), o);
+  return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+__device__ __forceinline__ __int128 shfl_i128(__int128 v, int src) {
+  const unsigned __int128 u = (unsigned __int128)v;
+  const unsigned long long lo = __shfl_sync(0xffffffffu, (unsigned long long)u, src);
+  const unsigned long long hi = __shfl_sync(0xffffffffu, (unsigned long long)(u >> 64), src);
+  return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+
+// exclusive block scan of 128-bit integers (warp shuffles, one pass through
+// shared memory for the warp totals); total receives the block sum
 __device__ __int128 block_excl_scan_i128(__int128 v, __int128 *sh, __int128 &total) {
-  const int t = threadIdx.x;
-  sh[t] = v;
-  __syncthreads();
-  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-    const __int128 x = t >= off ? sh[t - off] : (__int128)0;
-    __syncthreads();
-    sh[t] += x;
-    __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __int128 incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const __int128 t = shfl_up_i128(incl, o);
+    if (lane >= o) incl += t;
   }
-  const __int128 incl = sh[t];
-  total = sh[blockDim.x - 1];
+  if (lane == 31) sh[w] = incl;
   __syncthreads();
-  return incl - v;
+  if (w == 0) {
+    __int128 x = lane < nw ? sh[lane] : (__int128)0;
+    __int128 xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const __int128 t = shfl_up_i128(xi, o);
+      if (lane >= o) xi += t;
+    }
+    sh[32 + lane] = xi - x;                      // exclusive prefix of warp totals
+    if (lane == 31) sh[64] = xi;                 // block total
+  }
+  __syncthreads();
+  const __int128 res = sh[32 + w] + incl - v;
+  total = sh[64];
+  __syncthreads();
+  return res;
 }
 
 __device__ double block_excl_scan_f64(double v, double *sh, double &total) {
@@ -684,7 +866,8 @@ k_field_scan(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned
   long long *D = f.smem ? sD : Dg;   // indexed through fpad()
   const int seg = f.seg;
   const int j0 = min(N, t * seg), j1 = min(N, j0 + seg);
-  for (int j = t; j < N; j += blockDim.x) D[fpad(j)] = (long long)Qi[j] - (long long)Qe[j];
+#pragma unroll 8
+  for (int j = t; j < N; j += blockDim.x) D[fpad(j)] = (long long)__ldcg(Qi + j) - (long long)__ldcg(Qe + j);
   __syncthreads();
   __int128 loc = 0;
   for (int j = j0; j < j1; ++j) loc += (__int128)D[fpad(j)];
@@ -704,47 +887,53 @@ k_field_scan(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned
   if (t == 0) { fs->T = T; fs->M = M; }
 }
 
-// Floating-point part (many CTAs, one thread per segment):
-//   E_{j+1/2} = (N S'_j - M) Cf,  E_j = (E_{j-1/2} + E_{j+1/2}) / 2 - E0.
-// S'_{-1} = 0 = S'_{N-1}, so the segment start formula also gives E_{-1/2} = E_{N-1/2}.
+// Floating-point part (many CTAs, one thread per node):
+//   E_{j+1/2} = (N S'_j - M) Cf,  E_j = (E_{j-1/2} + E_{j+1/2}) / 2 - E0,
+// with S'_j rebuilt from the segment start S'_{j0-1} and the charges of the
+// segment (staged in shared memory).  S'_{-1} = 0 = S'_{N-1}, so node 0 gets
+// E_{-1/2} = E_{N-1/2} from the same formula.
+constexpr int kEvalThreads = 256;
+
 template <class R>
-__global__ void k_field_eval(FieldK f, const unsigned long long *__restrict__ Qe,
-                             const unsigned long long *__restrict__ Qi, Ctl *ctl, const FieldScan *fs, double *E,
-                             double *Eh, R *Ef, int advance) {
+__global__ void __launch_bounds__(kEvalThreads)
+k_field_eval(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi, Ctl *ctl,
+             const FieldScan *fs, double *E, double *Eh, R *Ef, int advance) {
+  __shared__ long long sD[kEvalThreads + 64];
   const int N = f.N;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int seg = f.seg;
-  const int j0 = min(N, t * seg), j1 = min(N, j0 + seg);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const double E0 = ctl->E0;
+  // nodes of this block and the part of the first segment before it
+  const int jb = blockIdx.x * blockDim.x;
+  const int sb = (jb / seg) * seg;               // start of the segment holding the block's first node
+  const int lo = sb, hi = min(N, jb + (int)blockDim.x);
+  for (int q = lo + threadIdx.x; q < hi; q += blockDim.x) sD[q - lo] = (long long)Qi[q] - (long long)Qe[q];
+  __syncthreads();
   bool bad = false;
-  if (t < kFieldThreads && j0 < j1) {
+  if (j < N) {
+    double e;
     if (f.field_mode == PIC_FIELD_APPLIED) {
-      for (int j = j0; j < j1; ++j) {
-        Eh[j] = 0.0;
-        E[j] = -E0;
-        Ef[j] = (R)(-E0);
-      }
+      Eh[j] = 0.0;
+      e = -E0;
     } else {
       const uint32_t Nu = (uint32_t)N;
       const __int128 T = fs->T, M = fs->M;
-      __int128 Sp = fs->Sp0[t];
-      double prev = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;
-      const double Eapp = -E0;
-      for (int j = j0; j < j1; ++j) {
-        Sp += mul_u32((__int128)((long long)Qi[j] - (long long)Qe[j]), Nu) - T;
-        const double eh = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;
-        const double e = 0.5 * (prev + eh) + Eapp;
-        Eh[j] = eh;
-        E[j] = e;
-        Ef[j] = (R)e;
-        if (!isfinite(e)) bad = true;
-        prev = eh;
-      }
+      const int g = j / seg, j0 = g * seg;
+      __int128 Sp = fs->Sp0[g];                  // S'_{j0-1}
+      for (int q = j0; q < j; ++q) Sp += mul_u32((__int128)sD[q - lo], Nu) - T;
+      const double prev = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;      // E_{j-1/2}
+      Sp += mul_u32((__int128)sD[j - lo], Nu) - T;
+      const double eh = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;        // E_{j+1/2}
+      Eh[j] = eh;
+      e = 0.5 * (prev + eh) + (-E0);
     }
-    if (j0 == 0) Ef[N] = (R)E[0];
+    E[j] = e;
+    Ef[j] = (R)e;
+    if (j == 0) Ef[N] = (R)e;
+    if (!isfinite(e)) bad = true;
   }
   if (bad) atomicOr(&ctl->status, kStNonFinite);
-  if (advance && t == 0) {
+  if (advance && j == 0) {
     ctl->step += 1;
     ctl->m_steps += 1;
   }
@@ -791,7 +980,8 @@ void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned 
     if (f.smem) cudaFuncSetAttribute(k_field_scan<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     k_field_scan<R><<<1, kFieldThreads, bytes, st>>>(f, Qe, Qi, Dg, fs);
   }
-  k_field_eval<R><<<kFieldThreads / 32, 32, 0, st>>>(f, Qe, Qi, ctl, fs, E, Eh, Ef, advance ? 1 : 0);
+  k_field_eval<R><<<(f.N + kEvalThreads - 1) / kEvalThreads, kEvalThreads, 0, st>>>(f, Qe, Qi, ctl, fs, E, Eh, Ef,
+                                                                                   advance ? 1 : 0);
   if (diag) k_field_diag<R><<<1, kFieldThreads, 0, st>>>(f, Qe, Qi, ctl, E, Eh, m);
 }
 

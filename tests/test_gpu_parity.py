@@ -53,11 +53,12 @@ def test_initial_state_matches(precision):
         assert gd[k] == od[k], k
 
 
+@pytest.mark.parametrize("sort_every", [0, 5])
 @pytest.mark.parametrize("precision", [w.FP64, w.MIXED])
 @pytest.mark.parametrize("loss", [w.LOSS_PAIR, w.LOSS_RADIAL, w.LOSS_NONE])
-def test_steps_match_bit_exact(precision, loss):
+def test_steps_match_bit_exact(precision, loss, sort_every):
     p = small(precision, loss_mode=loss, nu_w=2e8 if loss == w.LOSS_RADIAL else 0.0,
-              capacity=40000)
+              capacity=40000, sort_every=sort_every)
     g = pb.Column(p, flags=pb.FLAG_RECORD_CODES)
     o = oracle.Oracle(p)
     for n in (1, 9, 1, 10, 4):
@@ -102,8 +103,10 @@ def test_single_step_from_set_state_with_codes(precision):
         assert len(np.unique(co)) >= 3
 
 
-def test_ragged_sizes_and_frozen_ions():
-    p = small(n_e0=12345, n_i0=12345, n_cells=97, ion_subcycle=0, capacity=20000)
+@pytest.mark.parametrize("n_cells", [97, 30000])
+def test_ragged_sizes_and_frozen_ions(n_cells):
+    # 97 cells: one radix pass (odd, copied back); 30000 cells: three passes, field scratch in global memory
+    p = small(n_e0=12345, n_i0=12345, n_cells=n_cells, ion_subcycle=0, capacity=20000, sort_every=3)
     g, o = pb.Column(p), oracle.Oracle(p)
     g.step(7)
     o.step(7)

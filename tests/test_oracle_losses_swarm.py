@@ -135,3 +135,34 @@ def test_maxwell_model_swarm_drift_and_energy():
         es.append((0.5 * ME / QE * (s["vx_e"] ** 2 + s["vy_e"] ** 2 + s["vz_e"] ** 2)).mean())
     assert abs(np.mean(ws) / w_th - 1) < 0.02
     assert abs(np.mean(es) / eps_th - 1) < 0.01
+
+
+def test_sort_is_the_stable_order_by_cell():
+    n, N = 5000, 64
+    p = w.Params(L_m=0.01, n_cells=N, dt_s=2e-11, xsec=[], field_mode=w.FIELD_APPLIED, drive=w.DRIVE_E0,
+                 E0_Vpm=0.0, n_e0=n, n_i0=n, ion_subcycle=1, loss_mode=w.LOSS_NONE, sort_every=1)
+    o = oracle.Oracle(p)
+    rng = np.random.default_rng(4)
+    st = beam_state(n, N, 0.0, rng, n_i=n)
+    o.set_state(st)
+    o.step(1)   # nothing moves: the step only reorders
+    s = o.get_state()
+    for sp in ("e", "i"):
+        order = np.argsort(st[f"cell_{sp}"], kind="stable")
+        assert np.array_equal(s[f"id_{sp}"], st[f"id_{sp}"][order])
+        assert np.array_equal(s[f"off_{sp}"], st[f"off_{sp}"][order])
+
+
+def test_sorting_does_not_change_any_particle():
+    """With no slot-dependent randomness (no births, no removals) each particle's
+    trajectory depends only on its id: sorted and unsorted runs agree per id."""
+    a = oracle.Oracle(_small(seed=8, loss_mode=w.LOSS_SWARM))
+    b = oracle.Oracle(_small(seed=8, loss_mode=w.LOSS_SWARM, sort_every=7))
+    a.step(22); b.step(22)
+    sa, sb = a.get_state(), b.get_state()
+    for sp in ("e", "i"):
+        ia, ib = np.argsort(sa[f"id_{sp}"]), np.argsort(sb[f"id_{sp}"])
+        for k in ("cell", "off", "vx", "vy", "vz", "id"):
+            assert np.array_equal(sa[f"{k}_{sp}"][ia], sb[f"{k}_{sp}"][ib]), (sp, k)
+    assert np.array_equal(sa["E"], sb["E"]) and np.array_equal(sa["Q_i"], sb["Q_i"])
+    assert not np.array_equal(sa["id_e"], sb["id_e"])   # the order did change
