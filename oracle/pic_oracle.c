@@ -262,6 +262,7 @@ struct ora_t {
   real thr_e[MAXPROC];
   double *tab_e[MAXPROC], *tab_i[MAXPROC];   /* nu_k(eps_i), FP64 */
   real *rt_e[MAXPROC], *rt_i[MAXPROC];       /* tables in the storage precision */
+  real *nub_e, *Pb_e;                        /* electrons: per-bin majorant and its null-collision probability */
   double nustar_e, nustar_i, Pnull_e, Pnull_i;
   float gauss[NGAUSS + 1];
   species e, i;
@@ -446,12 +447,12 @@ static void electron_step(ora_t *h, int64_t p, int diag) {
   if (h->p.loss_mode == ORA_LOSS_RADIAL && w[2] < h->Pw_e) dead = 1;
   if (!dead) {
     real u0 = u_dec(w[0]), u1 = u_dec(w[1]);
-    if (u0 < h->P_e) {
-      real eps = h->K_e * (vx * vx + vy * vy + vz * vz);
-      real fr; int ovf;
-      int it = tab_pos(eps, h->inv_de_e, h->ntab, &fr, &ovf);
+    real eps = h->K_e * (vx * vx + vy * vy + vz * vz);
+    real fr; int ovf;
+    int it = tab_pos(eps, h->inv_de_e, h->ntab, &fr, &ovf);
+    if (u0 < h->Pb_e[it]) {
       if (ovf) h->st.overflow_e++;
-      real r = u1 * h->nus_e, cum = 0;
+      real r = u1 * h->nub_e[it], cum = 0;
       int sel = -1;
       for (int k = 0; k < h->np_e; ++k) {
         real nu;
@@ -897,6 +898,16 @@ int ora_create(const ora_params *pp, ora_t **out) {
     if (sum_e[i] > sum_e_max) sum_e_max = sum_e[i];
     if (sum_i[i] > sum_i_max) sum_i_max = sum_i[i];
   }
+  /* Electron majorant per energy bin [eps_i, eps_i+1]: the interpolated frequencies in a bin never
+   * exceed the larger of the summed frequencies at its two ends (build reading: an energy-binned
+   * null-collision majorant; the electron energy is known before the collision test). */
+  h->nub_e = (real *)xcalloc((size_t)n, sizeof(real));
+  h->Pb_e = (real *)xcalloc((size_t)n, sizeof(real));
+  for (int i = 0; i + 1 < n; ++i) {
+    double mx = sum_e[i] > sum_e[i + 1] ? sum_e[i] : sum_e[i + 1];
+    h->nub_e[i] = (real)mx;
+    h->Pb_e[i] = (real)(-expm1(-mx * pp->dt_s));
+  }
   free(sum_e); free(sum_i);
   h->nustar_e = sum_e_max; h->nustar_i = sum_i_max;
   h->Pnull_e = -expm1(-sum_e_max * pp->dt_s);
@@ -945,6 +956,7 @@ int ora_create(const ora_params *pp, ora_t **out) {
 void ora_destroy(ora_t *h) {
   if (!h) return;
   for (int j = 0; j < MAXPROC; ++j) { free(h->tab_e[j]); free(h->tab_i[j]); free(h->rt_e[j]); free(h->rt_i[j]); }
+  free(h->nub_e); free(h->Pb_e);
   species_free(&h->e); species_free(&h->i);
   free(h->E); free(h->Eh); free(h->Ef); free(h->births); free(h->dead_e); free(h->dead_i);
   moments_free(h);

@@ -48,6 +48,7 @@ struct pic_handle {
   pic::SortBuf sb[2]{};               // sort buffers per species (sort_every > 0)
   void *Ef = nullptr;                 // R[N+1]
   void *tab[2] = {nullptr, nullptr};  // R[np * ntab]
+  void *tabb = nullptr;               // electron per-bin majorant and null-collision probability, R[2 ntab]
   float *gauss = nullptr;
   void *bb_mem = nullptr;
   uint32_t *k3_mem = nullptr;
@@ -240,6 +241,19 @@ template <class R> int setup_tables(pic_handle *h) {
     double mx = 0.0;
     for (int i = 0; i < n; ++i)
       if (sum[q][i] > mx) mx = sum[q][i];
+    if (q == 0) {
+      // majorant per energy bin [eps_i, eps_i+1]: the larger end value of the summed frequencies
+      std::vector<R> bins(2 * (size_t)n, (R)0);
+      for (int i = 0; i + 1 < n; ++i) {
+        const double b = sum[0][i] > sum[0][i + 1] ? sum[0][i] : sum[0][i + 1];
+        bins[i] = (R)b;
+        bins[n + i] = (R)(-std::expm1(-b * dts[0]));
+      }
+      CU(h, cudaMalloc(&h->tabb, bins.size() * sizeof(R)));
+      CU(h, cudaMemcpy(h->tabb, bins.data(), bins.size() * sizeof(R), cudaMemcpyHostToDevice));
+      k.sp[0].nub = reinterpret_cast<const R *>(h->tabb);
+      k.sp[0].Pb = reinterpret_cast<const R *>(h->tabb) + n;
+    }
     h->nustar[q] = mx;
     h->Pnull[q] = -std::expm1(-mx * dts[q]);
     pic::SpecK<R> &s = k.sp[q];
@@ -370,6 +384,7 @@ void free_all(pic_handle *h) {
     cudaFree(h->sp[q].Q); cudaFree(h->sp[q].dead); cudaFree(h->tab[q]);
     cudaFree(h->sb[q].cell); cudaFree(h->sb[q].rec); cudaFree(h->sb[q].id); cudaFree(h->sb[q].hist);
   }
+  cudaFree(h->tabb);
   cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->Dg); cudaFree(h->fs); cudaFree(h->Ef); cudaFree(h->gauss);
   cudaFree(h->bb_mem); cudaFree(h->k3_mem); cudaFree(h->mom); cudaFree(h->mom_iz);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);

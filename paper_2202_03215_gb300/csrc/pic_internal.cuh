@@ -65,6 +65,7 @@ template <class R> struct SpecK {
   int xs[kMaxProc];               // index of the process in the caller's xsec list
   R thr[kMaxProc];
   const R *tab;                   // np x ntab collision frequencies
+  const R *nub, *Pb;              // electrons: per energy bin majorant and its null-collision probability
 };
 
 template <class R> struct StepK {

@@ -151,7 +151,7 @@ __device__ __forceinline__ int collide(const StepK<R> &k, const SpecK<R> &sp, Ct
     const R eps = sp.K * (vx * vx + vy * vy + vz * vz);
     R fr;
     const int it = tab_pos(eps, sp.inv_de, k.ntab, fr, ovf);
-    const R r = u1 * sp.nus;
+    const R r = u1 * __ldg(sp.nub + it);
     R cum = 0;
     for (int q = 0; q < sp.np; ++q) {
       R nu;
@@ -243,9 +243,9 @@ __device__ __forceinline__ int collide(const StepK<R> &k, const SpecK<R> &sp, Ct
   return sel;
 }
 
-// 64-bit fixed-point add into a shared-memory bin held as two 32-bit words:
-// native 32-bit atomics, the carry of the low word propagated exactly
-__device__ __forceinline__ void bin_add(unsigned *lo, unsigned *hi, unsigned long long v) {
+// 64-bit fixed-point add into a shared-memory word pair: native 32-bit
+// atomics, the carry of the low word propagated exactly
+__device__ __forceinline__ void add64(unsigned *lo, unsigned *hi, unsigned long long v) {
   const unsigned vlo = (unsigned)v;
   const unsigned vhi = (unsigned)(v >> 32);
   const unsigned old = atomicAdd(lo, vlo);
@@ -253,19 +253,52 @@ __device__ __forceinline__ void bin_add(unsigned *lo, unsigned *hi, unsigned lon
   if (c) atomicAdd(hi, c);
 }
 
-// Deposit of one warp, summed over runs of neighbouring lanes that share a
-// cell (sorted particles come in long runs): a segmented scan of the
-// fixed-point weights with shuffles, then the last lane of each run adds
-// node cell += n 2^32 - sum k and node cell+1 += sum k (exact integers).
-// Lanes with in == false contribute nothing.  All 32 lanes must call it.
-__device__ __forceinline__ void deposit_runs(bool in, int lane, int32_t cell, unsigned long long kk, int N, int W,
-                                             int c0, unsigned *blo, unsigned *bhi, unsigned long long *Q) {
+// bytes of the shared-memory bins of W cells, rounded so that what follows stays 16-byte aligned
+__host__ __device__ constexpr size_t bins_bytes(int W) { return ((size_t)W * 12 + 15) & ~(size_t)15; }
+
+// Shared-memory charge bins per cell of a window [c0, c0 + W): particle count
+// and the sum of the cloud-in-cell weights k (64-bit).  Cell c's particles
+// give node c: n 2^32 - sum k and node c+1: sum k, applied at the flush.
+struct CellBins {
+  unsigned *cnt, *klo, *khi;
+  int W, c0;
+};
+
+// n particles of cell `cell` with summed weight sk
+__device__ __forceinline__ void cell_add(const CellBins &b, int N, int32_t cell, unsigned n, unsigned long long sk,
+                                         unsigned long long *Q) {
+  int li = cell;
+  if (b.W < N) {
+    li = cell - b.c0;
+    if (li < 0) li += N;
+  }
+  if (li < b.W) {
+    atomicAdd(b.cnt + li, n);
+    add64(b.klo + li, b.khi + li, sk);
+  } else {
+    const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+    atomicAdd(Q + cell, ((unsigned long long)n << 32) - sk);
+    atomicAdd(Q + c1, sk);
+  }
+}
+
+// Deposit of one warp.  Sorted particles come in runs of neighbouring lanes
+// in one cell: those are summed by a segmented warp scan and added once by
+// the run's last lane; when no two neighbouring lanes share a cell every
+// lane adds its own particle.  Lanes with in == false contribute nothing.
+// All 32 lanes must call it.
+__device__ __forceinline__ void deposit_runs(bool in, int lane, int32_t cell, unsigned long long kk, int N,
+                                             const CellBins &b, unsigned long long *Q) {
   const unsigned mask = __ballot_sync(kFull, in);
   const int32_t pc = __shfl_up_sync(kFull, cell, 1);
-  const int32_t nc = __shfl_down_sync(kFull, cell, 1);
   const bool pin = lane > 0 && ((mask >> (lane - 1)) & 1u);
-  const bool nin = lane < 31 && ((mask >> (lane + 1)) & 1u);
   const bool head = !in || !pin || pc != cell;
+  if (__ballot_sync(kFull, !head) == 0) {
+    if (in) cell_add(b, N, cell, 1u, kk, Q);
+    return;
+  }
+  const int32_t nc = __shfl_down_sync(kFull, cell, 1);
+  const bool nin = lane < 31 && ((mask >> (lane + 1)) & 1u);
   const bool tail = in && (!nin || nc != cell);
   int start = head ? lane : 0;
 #pragma unroll
@@ -275,31 +308,15 @@ __device__ __forceinline__ void deposit_runs(bool in, int lane, int32_t cell, un
   }
   // low 16 bits of k plus a count in bits 21..; high 16 bits separately (no overflow over 32 lanes)
   unsigned a = in ? (((unsigned)kk & 0xffffu) | (1u << 21)) : 0u;
-  unsigned b = in ? (unsigned)(kk >> 16) : 0u;
+  unsigned c = in ? (unsigned)(kk >> 16) : 0u;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const unsigned ta = __shfl_up_sync(kFull, a, o), tb = __shfl_up_sync(kFull, b, o);
-    if (lane - o >= start) { a += ta; b += tb; }
+    const unsigned ta = __shfl_up_sync(kFull, a, o), tc = __shfl_up_sync(kFull, c, o);
+    if (lane - o >= start) { a += ta; c += tc; }
   }
   if (tail) {
-    const unsigned long long sk = ((unsigned long long)b << 16) + (unsigned long long)(a & 0x1fffffu);
-    const unsigned long long A = ((unsigned long long)(a >> 21) << 32) - sk;
-    const int c1 = (cell + 1 == N) ? 0 : cell + 1;
-    int li = cell;
-    if (W < N) {
-      li = cell - c0;
-      if (li < 0) li += N;
-    }
-    if (W == N) {
-      bin_add(blo + cell, bhi + cell, A);
-      bin_add(blo + c1, bhi + c1, sk);
-    } else if (li < W - 1) {
-      bin_add(blo + li, bhi + li, A);
-      bin_add(blo + li + 1, bhi + li + 1, sk);
-    } else {
-      atomicAdd(Q + cell, A);
-      atomicAdd(Q + c1, sk);
-    }
+    const unsigned long long sk = ((unsigned long long)c << 16) + (unsigned long long)(a & 0x1fffffu);
+    cell_add(b, N, cell, a >> 21, sk, Q);
   }
 }
 
@@ -313,9 +330,12 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
   const SpecK<R> &sp = k.sp[SP];
   const size_t eb = smemE ? ((((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15) : 0;
   R *sE = reinterpret_cast<R *>(smem);
-  unsigned *blo = reinterpret_cast<unsigned *>(smem + eb);   // bins: low and high 32-bit words
-  unsigned *bhi = blo + W;
-  const Queue<R> Qd = queue_at<R>(smem + eb + (size_t)W * 8);
+  CellBins bins;
+  bins.cnt = reinterpret_cast<unsigned *>(smem + eb);
+  bins.klo = bins.cnt + W;
+  bins.khi = bins.klo + W;
+  bins.W = W;
+  const Queue<R> Qd = queue_at<R>(smem + eb + bins_bytes(W));
   const long long n = ctl->n[SP];
   const long long stepll = ctl->step;
   const uint32_t step = (uint32_t)stepll;
@@ -330,9 +350,10 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
     c0 = s.cell[p0] - W / 8;
     if (c0 < 0) c0 += N;
   }
+  bins.c0 = c0;
   if (smemE)
     for (int j = threadIdx.x; j <= N; j += blockDim.x) sE[j] = Ef[j];
-  for (int j = threadIdx.x; j < W; j += blockDim.x) { blo[j] = 0u; bhi[j] = 0u; }
+  for (int j = threadIdx.x; j < W; j += blockDim.x) { bins.cnt[j] = 0u; bins.klo[j] = 0u; bins.khi[j] = 0u; }
   if (threadIdx.x <= kMaxProc) s_cnt[threadIdx.x] = 0u;
   __syncthreads();
   const R *E = smemE ? sE : Ef;
@@ -400,7 +421,16 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
       dead = radial && (w0.z < sp.Pw);
       if (!dead) {
         u1 = u_dec<R>(w0.y);
-        cand = u_dec<R>(w0.x) < sp.P;
+        if constexpr (SP == 0) {
+          // electrons: null-collision probability of the energy bin of the particle
+          const R eps = sp.K * (vx * vx + vy * vy + vz * vz);
+          R fr;
+          bool ovf;
+          const int it = tab_pos(eps, sp.inv_de, k.ntab, fr, ovf);
+          cand = u_dec<R>(w0.x) < __ldg(sp.Pb + it);
+        } else {
+          cand = u_dec<R>(w0.x) < sp.P;
+        }
       }
       s.cell[p] = cell;
       if (!cand) {
@@ -423,7 +453,7 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
     }
     wq += __popc(bal);
     // charge deposit, summed over runs of lanes in the same cell
-    deposit_runs(valid && !dead, lane, cell, wfix(off), N, W, c0, blo, bhi, s.Q);
+    deposit_runs(valid && !dead, lane, cell, wfix(off), N, bins, s.Q);
     __syncwarp();
     if (wq >= 32) {
       flush(32);
@@ -441,11 +471,14 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
   if (wq > 0) flush(wq);
   __syncthreads();
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
-    const unsigned long long v = ((unsigned long long)bhi[j] << 32) | (unsigned long long)blo[j];
-    if (v) {
-      int node = j;
-      if (W < N) { node = c0 + j; if (node >= N) node -= N; }
-      atomicAdd(s.Q + node, v);
+    const unsigned nq = bins.cnt[j];
+    const unsigned long long sk = ((unsigned long long)bins.khi[j] << 32) | (unsigned long long)bins.klo[j];
+    if (nq || sk) {
+      int cell = j;
+      if (W < N) { cell = c0 + j; if (cell >= N) cell -= N; }
+      const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+      atomicAdd(s.Q + cell, ((unsigned long long)nq << 32) - sk);
+      atomicAdd(s.Q + c1, sk);
     }
   }
   if (threadIdx.x < sp.np && s_cnt[threadIdx.x])
@@ -465,12 +498,12 @@ void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBu
   const size_t qb = queue_bytes<R>();
   size_t eb = (((size_t)k.N + 1) * sizeof(R) + 15) & ~(size_t)15;
   // the node field goes to shared memory when it leaves room for a 4096-node bin window
-  int smemE = eb + qb + 4096 * 8 <= budget ? 1 : 0;
+  int smemE = eb + qb + 4096 * 12 <= budget ? 1 : 0;
   if (!smemE) eb = 0;
-  const size_t wmax = (budget - eb - qb) / 8;
+  const size_t wmax = (budget - eb - qb) / 12;
   int W = (int)((size_t)k.N < wmax ? (size_t)k.N : wmax);
-  if (W < k.N) W = W < 8192 ? (W & ~63) : 8192;
-  const size_t bytes = eb + (size_t)W * 8 + qb;
+  if (W < k.N) W = W < 4096 ? (W & ~63) : 4096;
+  const size_t bytes = eb + bins_bytes(W) + qb;
   if (species == 0) {
     cudaFuncSetAttribute(k_push<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     k_push<R, 0><<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);

@@ -34,18 +34,25 @@ def test_real_collision_counts_match_analytic_rates(eps0):
     o.set_state(beam_state(n, p.n_cells, speed, np.random.default_rng(1)))
     o.step(1)
     codes = o.codes(0, n)
-    d = o.derived()
     ng = n_gas()
-    nus = d["nu_star_e"]
-    Pn = 1 - np.exp(-nus * p.dt_s)
+    # energy-binned majorant: the larger summed frequency at the two ends of the table bin holding eps0
+    de = p.eps_max_e_eV / (p.n_table - 1)
+    i = int(eps0 / de)
+    ends = [(i * de), ((i + 1) * de)]
+    S = [sum(_sigma(x, e) for x in p.xsec[:3]) * ng * np.sqrt(2 * QE * e / ME) for e in ends]
+    nub = max(S)
+    Pn = 1 - np.exp(-nub * p.dt_s)
     for k, x in enumerate(p.xsec[:3]):
         nu = ng * _sigma(x, eps0) * speed
-        pk = Pn * nu / nus
+        pk = Pn * nu / nub
         cnt = np.count_nonzero(codes == k)
         if pk == 0:
             assert cnt == 0
         else:
             assert abs(cnt - n * pk) < 4.5 * np.sqrt(n * pk * (1 - pk)), (k, cnt, n * pk)
+    # the candidates are the particles of the bin with probability P_null(bin): real + null
+    d = o.derived()
+    nus = d["nu_star_e"]
     # nu* bounds the total frequency on the whole table range
     e = np.linspace(0, p.eps_max_e_eV, 20001)
     tot = sum(np.array([_sigma(x, ee) for ee in e]) for x in p.xsec[:3]) * ng * np.sqrt(2 * QE * e / ME)
