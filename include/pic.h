@@ -191,6 +191,24 @@ int pic_get_state(pic_handle *h, pic_state *out);
 int pic_set_state(pic_handle *h, const pic_state *in);
 int pic_get_stats(pic_handle *h, pic_stats *out);
 
+/* Batched columns: n independent periodic columns (uneven lengths, cell counts,
+ * pressures, particle counts, gases) advanced together, one kernel launch per
+ * phase of the step for all columns, on a CTA schedule in proportion to each
+ * column's particles (the first pic_step_batch steps time several schedules
+ * and keep the fastest; the schedule never changes results), with the
+ * plain ion cycles replayed from a captured CUDA graph.  Column i keys its
+ * random numbers with column index i (params[i].column is overridden), so
+ * column i of a batch evolves bit for bit like a lone handle created with
+ * column = i.  All columns need equal dt, ion_subcycle, precision,
+ * diag_every, sort_every and field_mode (PIC_EINVAL otherwise). */
+int pic_init_batch(const pic_params *params, int n, pic_handle **out);
+/* Advance every column of the batch n steps (pic_step on a batch handle does the same). */
+int pic_step_batch(pic_handle *batch, int64_t n);
+/* Column i of a batch (owned by the batch: use it for get_state, stats,
+ * moments; it cannot be stepped or freed on its own).  NULL if out of range. */
+pic_handle *pic_batch_column(pic_handle *batch, int i);
+int pic_batch_size(pic_handle *batch);
+
 /* Per-particle process code of the last step (needs PIC_FLAG_RECORD_CODES):
  * -1 no collision, -2 removed by the radial loss, else the xsec index.
  * Indexed by the slot the particle had during that step; n <= capacity. */

@@ -111,6 +111,11 @@ def lib() -> C.CDLL:
                                          C.c_void_p, C.c_void_p, C.c_void_p]
         L.pic_field_periodic_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_double,
                                                  C.c_void_p, C.c_void_p, C.c_void_p]
+        L.pic_init_batch.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_void_p)]
+        L.pic_step_batch.argtypes = [C.c_void_p, C.c_int64]
+        L.pic_batch_column.argtypes = [C.c_void_p, C.c_int]
+        L.pic_batch_column.restype = C.c_void_p
+        L.pic_batch_size.argtypes = [C.c_void_p]
         L.pic_set_timing.argtypes = [C.c_void_p, C.c_int]
         L.pic_kernel_times.argtypes = [C.c_void_p, _D, _I64]
         _lib = L
@@ -182,21 +187,26 @@ def field_periodic_noalloc(Q_i, Q_e, C_unit: float, E0: float, E, E_half, stream
 class Column:
     """One periodic positive column on the GPU (pic_init / pic_step / pic_moments / pic_free)."""
 
-    def __init__(self, params, flags: int = 0):
+    def __init__(self, params, flags: int = 0, _handle=None):
         self.L = lib()
         self.params = params
+        self.N = params.n_cells
+        self.cap = params.capacity or (max(params.n_e0, params.n_i0) * 5 // 4 + 1024)
+        self._owned = _handle is None
+        if _handle is not None:
+            self.h = C.c_void_p(_handle)
+            return
         st, keep = make_params(params)
         st.flags = params.flags | flags
         h = C.c_void_p()
         rc = self.L.pic_init(C.byref(st), C.byref(h))
         _check(rc)
         self.h = h
-        self.N = params.n_cells
-        self.cap = params.capacity or (max(params.n_e0, params.n_i0) * 5 // 4 + 1024)
 
     def close(self) -> None:
         if getattr(self, "h", None):
-            self.L.pic_free(self.h)
+            if self._owned:
+                self.L.pic_free(self.h)
             self.h = None
 
     def __del__(self):
@@ -279,3 +289,51 @@ class Column:
         _check(self.L.pic_moments(self.h, C.byref(m)), self.h)
         d["n_samples"], d["n_steps"] = m.n_samples, m.n_steps
         return d
+
+
+class Batch:
+    """Many independent columns advanced together (pic_init_batch / pic_step_batch)."""
+
+    def __init__(self, params_list, flags: int = 0):
+        self.L = lib()
+        self.params = list(params_list)
+        n = len(self.params)
+        arr = (Params * n)()
+        self._keep = []
+        for i, p in enumerate(self.params):
+            st, keep = make_params(p)
+            st.flags = p.flags | flags
+            arr[i] = st
+            self._keep.append(keep)
+        h = C.c_void_p()
+        _check(self.L.pic_init_batch(arr, n, C.byref(h)))
+        self.h = h
+        self.columns = [Column(p.with_(column=i), _handle=self.L.pic_batch_column(h, i))
+                        for i, p in enumerate(self.params)]
+
+    def step(self, n: int = 1) -> None:
+        _check(self.L.pic_step_batch(self.h, n), self.h)
+
+    def stream(self) -> int:
+        return self.L.pic_stream(self.h) or 0
+
+    def set_timing(self, enable: bool) -> None:
+        _check(self.L.pic_set_timing(self.h, int(enable)), self.h)
+
+    def kernel_times(self) -> dict:
+        ms = np.zeros(8)
+        n = np.zeros(8, np.int64)
+        _check(self.L.pic_kernel_times(self.h, _ptr(ms, _D), _ptr(n, _I64)), self.h)
+        names = ("push_e", "push_i", "births", "field", "sort", "other")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(names)}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            for c in self.columns:
+                c.h = None
+            self.L.pic_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+

@@ -72,6 +72,20 @@ struct pic_handle {
   size_t ev_used = 0;
   double kms[PIC_K_CLASSES] = {0};
   int64_t klaunch[PIC_K_CLASSES] = {0};
+  // batch of columns (pic_init_batch): the columns are full handles sharing this handle's stream
+  bool is_batch = false;
+  pic_handle *owner = nullptr;        // set on the columns of a batch
+  std::vector<pic_handle *> cols;
+  void *coldev = nullptr;             // ColDev<R>[ncol] on the device
+  int4 *sched = nullptr;              // CTA schedules: electrons at [0, nsched[0]), ions after
+  int nsched[2] = {0, 0};
+  std::vector<int> mults;             // CTAs per SM multipliers tried by the autotuner
+  std::vector<double> tune_ms;        // measured step time per multiplier
+  int tune_next = 0, mult = 1;
+  size_t push_smem = 0;
+  int maxN = 0;
+  cudaGraphExec_t cycle = nullptr;    // captured cycle of ion_subcycle steps (no sort, no diagnostics)
+  int64_t cycle_launch[PIC_K_CLASSES] = {0};   // kernel launches per replay of the cycle
 };
 
 namespace {
@@ -379,6 +393,15 @@ template <class R> int enqueue_step(pic_handle *h) {
 void free_all(pic_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (pic_handle *c : h->cols) {
+    c->stream = nullptr;  // shared with the batch
+    free_all(c);
+    delete c;
+  }
+  h->cols.clear();
+  cudaFree(h->coldev);
+  cudaFree(h->sched);
+  if (h->cycle) cudaGraphExecDestroy(h->cycle);
   for (int q = 0; q < 2; ++q) {
     cudaFree(h->sp[q].cell); cudaFree(h->sp[q].rec); cudaFree(h->sp[q].id); cudaFree(h->sp[q].code);
     cudaFree(h->sp[q].Q); cudaFree(h->sp[q].dead); cudaFree(h->tab[q]);
@@ -434,6 +457,210 @@ template <class R> int init_typed(pic_handle *h) {
   h->m.ne = h->mom + 4 * h->N; h->m.ni = h->mom + 5 * h->N; h->m.E = h->mom + 6 * h->N; h->m.phi = h->mom + 7 * h->N;
   h->m.iz = h->mom_iz;
   return run_init<R>(h);
+}
+
+// ---------------------------------------------------------------------------
+// batches
+
+template <class R> pic::ColDev<R> coldev_of(pic_handle *c) {
+  pic::ColDev<R> d{};
+  d.k = kparams<R>(c);
+  d.sp[0] = c->sp[0];
+  d.sp[1] = c->sp[1];
+  d.ctl = c->ctl;
+  d.Ef = c->Ef;
+  d.E = c->E;
+  d.Eh = c->Eh;
+  d.bb = bbuf<R>(c);
+  d.sc = c->sc;
+  d.m = c->m;
+  d.fk = c->fk;
+  d.fs = c->fs;
+  d.Dg = c->Dg;
+  d.N = c->N;
+  pic::push_layout<R>(c->N, d.W, d.smemE);
+  return d;
+}
+
+// CTA schedule of one species: CTAs in proportion to the live particles of each column (at least one)
+void build_schedule(pic_handle *b, int species, int mult, std::vector<int4> &out) {
+  long long tot = 0;
+  std::vector<long long> n(b->cols.size());
+  for (size_t c = 0; c < b->cols.size(); ++c) {
+    const pic_params &p = b->cols[c]->p;
+    n[c] = species == 0 ? p.n_e0 : p.n_i0;
+    tot += n[c];
+  }
+  const long long G = (long long)b->nsm * mult;
+  for (size_t c = 0; c < b->cols.size(); ++c) {
+    if (n[c] == 0) continue;
+    long long k = tot > 0 ? (G * n[c] + tot - 1) / tot : 1;
+    if (k < 1) k = 1;
+    const long long per = (n[c] + k - 1) / k;
+    if (per < 1024) k = (n[c] + 1023) / 1024;  // at least a full CTA of particles each
+    for (long long i = 0; i < k; ++i) out.push_back(make_int4((int)c, (int)i, (int)k, 0));
+  }
+}
+
+template <class R> int batch_schedules(pic_handle *b, int mult) {
+  std::vector<int4> se, si;
+  build_schedule(b, 0, mult, se);
+  build_schedule(b, 1, mult, si);
+  b->nsched[0] = (int)se.size();
+  b->nsched[1] = (int)si.size();
+  cudaFree(b->sched);
+  b->sched = nullptr;
+  std::vector<int4> all(se);
+  all.insert(all.end(), si.begin(), si.end());
+  if (all.empty()) all.push_back(make_int4(0, 0, 1, 0));
+  CU(b, cudaMalloc(&b->sched, all.size() * sizeof(int4)));
+  CU(b, cudaMemcpy(b->sched, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (b->cycle) { cudaGraphExecDestroy(b->cycle); b->cycle = nullptr; }
+  return 0;
+}
+
+template <class R> int enqueue_batch_step(pic_handle *b) {
+  pic_handle *c0 = b->cols[0];
+  const int ncol = (int)b->cols.size();
+  const int sub = c0->p.ion_subcycle;
+  const bool ion_push = sub > 0 && (b->host_step % sub) == 0;
+  const pic::ColDev<R> *cd = reinterpret_cast<const pic::ColDev<R> *>(b->coldev);
+  const int se = c0->p.sort_every;
+  if (se > 0 && b->host_step % se == 0) {
+    t_begin(b);
+    const long long pi = (long long)se * (sub > 0 ? sub : 1);
+    for (pic_handle *c : b->cols) {
+      pic::launch_sort<R>(c->sp[0], c->sb[0], &c->ctl->n[0], c->sp[0].cap, c->N, b->nsm, b->stream);
+      if (b->host_step % pi == 0)
+        pic::launch_sort<R>(c->sp[1], c->sb[1], &c->ctl->n[1], c->sp[1].cap, c->N, b->nsm, b->stream);
+    }
+    t_end(b, PIC_K_SORT);
+  }
+  t_begin(b);
+  pic::launch_zero_q_batch<R>(cd, ncol, 0, b->maxN, b->stream);
+  pic::launch_push_batch<R>(cd, b->sched, b->nsched[0], 0, b->push_smem, b->stream);
+  t_end(b, PIC_K_PUSH_E);
+  if (ion_push && b->nsched[1] > 0) {
+    t_begin(b);
+    pic::launch_zero_q_batch<R>(cd, ncol, 1, b->maxN, b->stream);
+    pic::launch_push_batch<R>(cd, b->sched + b->nsched[0], b->nsched[1], 1, b->push_smem, b->stream);
+    t_end(b, PIC_K_PUSH_I);
+  }
+  t_begin(b);
+  pic::launch_births_batch<R>(cd, ncol, ion_push ? 1 : 0, b->stream);
+  t_end(b, PIC_K_BIRTHS);
+  const bool diag = c0->p.diag_every > 0 && (b->host_step % c0->p.diag_every) == 0;
+  t_begin(b);
+  pic::launch_field_batch<R>(cd, ncol, b->maxN, c0->p.field_mode == PIC_FIELD_POISSON, diag, b->stream);
+  t_end(b, PIC_K_FIELD);
+  CU(b, cudaGetLastError());
+  b->host_step++;
+  for (pic_handle *c : b->cols) c->host_step = b->host_step;
+  return 0;
+}
+
+// steps s .. s+sub-1 hold no sort and no diagnostic sample
+bool plain_cycle(pic_handle *b, long long s, int sub) {
+  const pic_params &p = b->cols[0]->p;
+  for (long long q = s; q < s + sub; ++q) {
+    if (p.sort_every > 0 && q % p.sort_every == 0) return false;
+    if (p.diag_every > 0 && q % p.diag_every == 0) return false;
+  }
+  return true;
+}
+
+template <class R> int step_batch(pic_handle *b, int64_t n) {
+  const int sub = b->cols[0]->p.ion_subcycle > 0 ? b->cols[0]->p.ion_subcycle : 1;
+  const bool graphs = !(b->p.flags & PIC_FLAG_NO_GRAPH) && !b->timing;
+  int64_t done = 0;
+  while (done < n) {
+    // autotuner: the first steps try each CTA multiplier once (the schedule does not change results)
+    if (b->tune_next < (int)b->mults.size()) {
+      const int m = b->mults[b->tune_next];
+      int rc = batch_schedules<R>(b, m);
+      if (rc) return rc;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, b->stream);
+      rc = enqueue_batch_step<R>(b);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (rc) return rc;
+      b->tune_ms.push_back(ms);
+      if (++b->tune_next == (int)b->mults.size()) {
+        size_t best = 0;
+        for (size_t i = 1; i < b->tune_ms.size(); ++i)
+          if (b->tune_ms[i] < b->tune_ms[best]) best = i;
+        b->mult = b->mults[best];
+        rc = batch_schedules<R>(b, b->mult);
+        if (rc) return rc;
+      }
+      ++done;
+      continue;
+    }
+    if (graphs && n - done >= sub && b->host_step % sub == 0 && plain_cycle(b, b->host_step, sub)) {
+      if (!b->cycle) {
+        // capture one ion cycle; the kernels read the step counter on the device, so it replays
+        const long long s0 = b->host_step;
+        int64_t before[PIC_K_CLASSES];
+        for (int q = 0; q < PIC_K_CLASSES; ++q) before[q] = b->klaunch[q];
+        cudaGraph_t g;
+        CU(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = 0;
+        for (int q = 0; q < sub && !rc; ++q) rc = enqueue_batch_step<R>(b);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        b->host_step = s0;
+        for (pic_handle *c : b->cols) c->host_step = s0;
+        if (rc) return rc;
+        if (e != cudaSuccess) return set_err(b, PIC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->cycle, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_err(b, PIC_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
+        for (int q = 0; q < PIC_K_CLASSES; ++q) {   // the capture only recorded the launches
+          b->cycle_launch[q] = b->klaunch[q] - before[q];
+          b->klaunch[q] = before[q];
+        }
+      }
+      CU(b, cudaGraphLaunch(b->cycle, b->stream));
+      for (int q = 0; q < PIC_K_CLASSES; ++q) b->klaunch[q] += b->cycle_launch[q];
+      b->host_step += sub;
+      for (pic_handle *c : b->cols) c->host_step = b->host_step;
+      done += sub;
+      continue;
+    }
+    const int rc = enqueue_batch_step<R>(b);
+    if (rc) return rc;
+    ++done;
+    if (b->timing && b->ev_cls.size() > 1024) {
+      CU(b, cudaStreamSynchronize(b->stream));
+      t_collect(b);
+    }
+  }
+  return 0;
+}
+
+template <class R> int init_batch_typed(pic_handle *b) {
+  std::vector<pic::ColDev<R>> d;
+  size_t smem = 0;
+  for (pic_handle *c : b->cols) {
+    d.push_back(coldev_of<R>(c));
+    int W = 0, se = 0;
+    const size_t by = pic::push_layout<R>(c->N, W, se);
+    if (by > smem) smem = by;
+    if (c->N > b->maxN) b->maxN = c->N;
+  }
+  b->push_smem = smem;
+  // the batched field scan stages nodes in shared memory only when the largest column fits
+  for (auto &x : d)
+    if (b->maxN > pic::kFieldSmemMax) x.fk.smem = 0;
+  CU(b, cudaMalloc(&b->coldev, d.size() * sizeof(pic::ColDev<R>)));
+  CU(b, cudaMemcpy(b->coldev, d.data(), d.size() * sizeof(pic::ColDev<R>), cudaMemcpyHostToDevice));
+  return batch_schedules<R>(b, b->mult);
 }
 
 }  // namespace
@@ -530,6 +757,8 @@ int pic_init(const pic_params *params, pic_handle **out) {
 
 int pic_step(pic_handle *h, int64_t n) {
   if (!h || n < 0) return set_err(h, PIC_EINVAL, "bad arguments");
+  if (h->is_batch) return pic_step_batch(h, n);
+  if (h->owner) return set_err(h, PIC_EINVAL, "a column of a batch advances with pic_step_batch");
   if (h->latched) return h->latched;
   for (int64_t s = 0; s < n; ++s) {
     const int rc = h->mixed ? enqueue_step<float>(h) : enqueue_step<double>(h);
@@ -565,6 +794,82 @@ int pic_kernel_times(pic_handle *h, double *ms, int64_t *launches) {
   }
   return 0;
 }
+
+int pic_init_batch(const pic_params *params, int n, pic_handle **out) {
+  if (!out || !params || n < 1 || n > 4096) return set_err(nullptr, PIC_EINVAL, "bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    const int rc = validate(&params[i]);
+    if (rc) return rc;
+    if (params[i].dt_s != params[0].dt_s || params[i].ion_subcycle != params[0].ion_subcycle ||
+        params[i].precision != params[0].precision || params[i].diag_every != params[0].diag_every ||
+        params[i].sort_every != params[0].sort_every || params[i].field_mode != params[0].field_mode)
+      return set_err(nullptr, PIC_EINVAL, "batched columns need equal dt, ion_subcycle, precision, diag_every, "
+                                          "sort_every and field_mode");
+  }
+  pic_handle *b = new (std::nothrow) pic_handle();
+  if (!b) return set_err(nullptr, PIC_ENOMEM, "host allocation failed");
+  b->is_batch = true;
+  b->p = params[0];
+  b->p.xsec = nullptr;
+  b->mixed = params[0].precision == PIC_MIXED;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return set_err(nullptr, PIC_ECUDA, "stream creation failed");
+  }
+  for (int i = 0; i < n; ++i) {
+    pic_params pi = params[i];
+    pi.column = i;  // the column index keys the column's random numbers
+    pic_handle *c = nullptr;
+    const int rc = pic_init(&pi, &c);
+    if (rc) {
+      free_all(b);
+      delete b;
+      return rc;
+    }
+    cudaStreamDestroy(c->stream);
+    c->stream = b->stream;
+    c->owner = b;
+    b->cols.push_back(c);
+  }
+  b->mults = {1, 2, 4};
+  const int rc = b->mixed ? init_batch_typed<float>(b) : init_batch_typed<double>(b);
+  if (rc) {
+    free_all(b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return 0;
+}
+
+int pic_step_batch(pic_handle *b, int64_t n) {
+  if (!b || !b->is_batch || n < 0) return set_err(b, PIC_EINVAL, "not a batch handle");
+  if (b->latched) return b->latched;
+  const int rc = b->mixed ? step_batch<float>(b, n) : step_batch<double>(b, n);
+  if (rc) return rc;
+  int worst = 0;
+  for (pic_handle *c : b->cols) {
+    const int r = check_status(c);
+    if (r && !worst) {
+      worst = r;
+      b->err = c->err;
+    }
+  }
+  t_collect(b);
+  b->latched = worst;
+  return worst;
+}
+
+pic_handle *pic_batch_column(pic_handle *b, int i) {
+  if (!b || !b->is_batch || i < 0 || i >= (int)b->cols.size()) return nullptr;
+  return b->cols[i];
+}
+
+int pic_batch_size(pic_handle *b) { return (b && b->is_batch) ? (int)b->cols.size() : 0; }
 
 int pic_get_stats(pic_handle *h, pic_stats *out) {
   if (!h || !out) return set_err(h, PIC_EINVAL, "bad arguments");
@@ -630,6 +935,9 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
   if (in->n_e < 0 || in->n_i < 0 || in->n_e > h->sp[0].cap || in->n_i > h->sp[1].cap)
     return set_err(h, PIC_EINVAL, "particle count out of range");
   if (in->step < 0) return set_err(h, PIC_EINVAL, "step < 0");
+  if (h->is_batch) return set_err(h, PIC_EINVAL, "set the state of the batch's columns");
+  if (h->owner && in->step != h->owner->host_step)
+    return set_err(h, PIC_EINVAL, "a column of a batch keeps the batch's step counter");
   CU(h, cudaStreamSynchronize(h->stream));
   const int32_t *cells[2] = {in->cell_e, in->cell_i};
   const double *offs[2] = {in->off_e, in->off_i}, *vxs[2] = {in->vx_e, in->vx_i}, *vys[2] = {in->vy_e, in->vy_i},
@@ -762,7 +1070,7 @@ int pic_derived(pic_handle *h, double out[7]) {
 void *pic_stream(pic_handle *h) { return h ? (void *)h->stream : nullptr; }
 
 void pic_free(pic_handle *h) {
-  if (!h) return;
+  if (!h || h->owner) return;  // columns of a batch are freed with the batch
   free_all(h);
   delete h;
 }

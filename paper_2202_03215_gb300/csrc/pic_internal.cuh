@@ -109,6 +109,23 @@ struct FieldK {
   double dx;
 };
 
+// device descriptor of one column of a batch (everything the step kernels need)
+template <class R> struct ColDev {
+  StepK<R> k;
+  SpeciesDev sp[2];
+  Ctl *ctl;
+  void *Ef;
+  double *E, *Eh;
+  BirthBuf<R> bb;
+  K3Scratch sc;
+  Moments m;
+  FieldK fk;
+  FieldScan *fs;
+  long long *Dg;
+  int W, smemE;   // shared-memory layout of the particle step for this column
+  int N;
+};
+
 // second set of particle buffers and digit histograms for the sort
 struct SortBuf {
   int32_t *cell;
@@ -144,5 +161,16 @@ void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned 
                   cudaStream_t st);
 void launch_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n, cudaStream_t st);
 template <class R> int push_smem_bytes(int N);
+// shared-memory layout of the particle step for n_cells: bin window W, node field in shared memory
+template <class R> size_t push_layout(int n_cells, int &W, int &smemE);
+
+// batched columns (one launch per phase for all columns)
+template <class R> void launch_zero_q_batch(const ColDev<R> *cols, int ncol, int species, int maxN, cudaStream_t st);
+template <class R>
+void launch_push_batch(const ColDev<R> *cols, const int4 *sched, int nblocks, int species, size_t smem,
+                       cudaStream_t st);
+template <class R> void launch_births_batch(const ColDev<R> *cols, int ncol, int ion_pushed, cudaStream_t st);
+template <class R>
+void launch_field_batch(const ColDev<R> *cols, int ncol, int maxN, bool poisson, bool diag, cudaStream_t st);
 
 }  // namespace pic

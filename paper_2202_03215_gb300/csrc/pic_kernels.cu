@@ -320,11 +320,11 @@ __device__ __forceinline__ void deposit_runs(bool in, int lane, int32_t cell, un
   }
 }
 
+// one CTA's share (cta of ncta) of the particle step of one column
 template <class R, int SP>
-__global__ void __launch_bounds__(kStepThreads, 1)
-k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef, BirthBuf<R> bb,
-       Moments m, int W, int smemE) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef,
+                                          BirthBuf<R> bb, Moments m, int W, int smemE, int cta, int ncta,
+                                          unsigned char *smem) {
   __shared__ unsigned int s_cnt[kMaxProc + 1];
   const int N = k.N;
   const SpecK<R> &sp = k.sp[SP];
@@ -342,8 +342,8 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
   const bool diag = k.diag_every > 0 && (stepll % k.diag_every) == 0;
   const uint2 key = seed_key(k.seed);
   const uint32_t c3 = ((SP == 0 ? (uint32_t)kStE : (uint32_t)kStI) << 28) | (k.column << 16);
-  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
-  const long long p0 = (long long)blockIdx.x * chunk;
+  const long long chunk = (n + ncta - 1) / ncta;
+  const long long p0 = (long long)cta * chunk;
   const long long p1 = min(n, p0 + chunk);
   int c0 = 0;
   if (W < N && p0 < p1) {
@@ -486,24 +486,54 @@ k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__re
   if (threadIdx.x == 0 && s_cnt[kMaxProc]) atomicAdd(&ctl->overflow[SP], (unsigned long long)s_cnt[kMaxProc]);
 }
 
+template <class R, int SP>
+__global__ void __launch_bounds__(kStepThreads, 1)
+k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef, BirthBuf<R> bb,
+       Moments m, int W, int smemE) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  push_body<R, SP>(k, s, ctl, Ef, bb, m, W, smemE, blockIdx.x, gridDim.x, smem);
+}
+
+// batched columns: CTA b runs share sched[b].y of sched[b].z of column sched[b].x
+template <class R, int SP>
+__global__ void __launch_bounds__(kStepThreads, 1) k_push_batch(const ColDev<R> *cols, const int4 *sched) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) StepK<R> sk;
+  const int4 sc = sched[blockIdx.x];
+  const ColDev<R> *cd = cols + sc.x;
+  {
+    const int *src = reinterpret_cast<const int *>(&cd->k);
+    int *dst = reinterpret_cast<int *>(&sk);
+    for (int q = threadIdx.x; q < (int)(sizeof(StepK<R>) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+  }
+  __syncthreads();
+  push_body<R, SP>(sk, cd->sp[SP], cd->ctl, reinterpret_cast<const R *>(cd->Ef), cd->bb, cd->m, cd->W, cd->smemE,
+                   sc.y, sc.z, smem);
+}
+
 template <class R> int push_smem_bytes(int N) {
   const size_t e = (((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15;
   return (int)e;
 }
 
+template <class R> size_t push_layout(int n_cells, int &W, int &smemE) {
+  const size_t budget = 220 * 1024;
+  const size_t qb = queue_bytes<R>();
+  size_t eb = (((size_t)n_cells + 1) * sizeof(R) + 15) & ~(size_t)15;
+  // the node field goes to shared memory when it leaves room for a 4096-cell bin window
+  smemE = eb + qb + bins_bytes(4096) <= budget ? 1 : 0;
+  if (!smemE) eb = 0;
+  const size_t wmax = (budget - eb - qb) / 12;
+  W = (int)((size_t)n_cells < wmax ? (size_t)n_cells : wmax);
+  if (W < n_cells) W = W < 4096 ? (W & ~63) : 4096;
+  return eb + bins_bytes(W) + qb;
+}
+
 template <class R>
 void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBuf<R> bb, Moments m, int species,
                  int nsm, cudaStream_t st) {
-  const size_t budget = 220 * 1024;
-  const size_t qb = queue_bytes<R>();
-  size_t eb = (((size_t)k.N + 1) * sizeof(R) + 15) & ~(size_t)15;
-  // the node field goes to shared memory when it leaves room for a 4096-node bin window
-  int smemE = eb + qb + 4096 * 12 <= budget ? 1 : 0;
-  if (!smemE) eb = 0;
-  const size_t wmax = (budget - eb - qb) / 12;
-  int W = (int)((size_t)k.N < wmax ? (size_t)k.N : wmax);
-  if (W < k.N) W = W < 4096 ? (W & ~63) : 4096;
-  const size_t bytes = eb + bins_bytes(W) + qb;
+  int W = 0, smemE = 0;
+  const size_t bytes = push_layout<R>(k.N, W, smemE);
   if (species == 0) {
     cudaFuncSetAttribute(k_push<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     k_push<R, 0><<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
@@ -511,6 +541,29 @@ void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBu
     cudaFuncSetAttribute(k_push<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     k_push<R, 1><<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
   }
+}
+
+template <class R>
+void launch_push_batch(const ColDev<R> *cols, const int4 *sched, int nblocks, int species, size_t smem,
+                       cudaStream_t st) {
+  if (species == 0) {
+    cudaFuncSetAttribute(k_push_batch<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_push_batch<R, 0><<<nblocks, kStepThreads, smem, st>>>(cols, sched);
+  } else {
+    cudaFuncSetAttribute(k_push_batch<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_push_batch<R, 1><<<nblocks, kStepThreads, smem, st>>>(cols, sched);
+  }
+}
+
+template <class R> __global__ void k_zero_q_batch(const ColDev<R> *cols, int species) {
+  const ColDev<R> *cd = cols + blockIdx.y;
+  unsigned long long *Q = cd->sp[species].Q;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cd->N; j += gridDim.x * blockDim.x) Q[j] = 0ull;
+}
+
+template <class R> void launch_zero_q_batch(const ColDev<R> *cols, int ncol, int species, int maxN, cudaStream_t st) {
+  const int bx = (maxN + 255) / 256 < 16 ? (maxN + 255) / 256 : 16;
+  k_zero_q_batch<R><<<dim3(bx, ncol), 256, 0, st>>>(cols, species);
 }
 
 // ---------------------------------------------------------------------------
@@ -679,10 +732,8 @@ __device__ void fill_compact(const StepK<R> &k, SpeciesDev s, Ctl *ctl, int SP, 
 }
 
 template <class R>
-__global__ void __launch_bounds__(kBirthThreads, 1)
-k_births(const __grid_constant__ StepK<R> k, SpeciesDev e, SpeciesDev ion, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
-         int ion_pushed) {
-  extern __shared__ __align__(16) unsigned long long keys[];   // kStageCap
+__device__ __forceinline__ void births_body(const StepK<R> &k, SpeciesDev e, SpeciesDev ion, Ctl *ctl,
+                                            BirthBuf<R> bb, K3Scratch sc, int ion_pushed, unsigned long long *keys) {
   __shared__ int s_scan[kBirthThreads];
   __shared__ uint32_t s_scr[7 * kDirectMax];
   const int N = k.N;
@@ -781,11 +832,40 @@ k_births(const __grid_constant__ StepK<R> k, SpeciesDev e, SpeciesDev ion, Ctl *
 }
 
 template <class R>
+__global__ void __launch_bounds__(kBirthThreads, 1)
+k_births(const __grid_constant__ StepK<R> k, SpeciesDev e, SpeciesDev ion, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
+         int ion_pushed) {
+  extern __shared__ __align__(16) unsigned long long keys[];   // kStageCap
+  births_body<R>(k, e, ion, ctl, bb, sc, ion_pushed, keys);
+}
+
+// batched columns: one CTA per column
+template <class R>
+__global__ void __launch_bounds__(kBirthThreads, 1) k_births_batch(const ColDev<R> *cols, int ion_pushed) {
+  extern __shared__ __align__(16) unsigned long long keys[];
+  __shared__ __align__(16) StepK<R> sk;
+  const ColDev<R> *cd = cols + blockIdx.x;
+  {
+    const int *src = reinterpret_cast<const int *>(&cd->k);
+    int *dst = reinterpret_cast<int *>(&sk);
+    for (int q = threadIdx.x; q < (int)(sizeof(StepK<R>) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+  }
+  __syncthreads();
+  births_body<R>(sk, cd->sp[0], cd->sp[1], cd->ctl, cd->bb, cd->sc, ion_pushed, keys);
+}
+
+template <class R>
 void launch_births(const StepK<R> &k, SpeciesDev e, SpeciesDev i, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
                    int ion_pushed, cudaStream_t st) {
   const int bytes = kStageCap * 8;
   cudaFuncSetAttribute(k_births<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   k_births<R><<<1, kBirthThreads, bytes, st>>>(k, e, i, ctl, bb, sc, ion_pushed);
+}
+
+template <class R> void launch_births_batch(const ColDev<R> *cols, int ncol, int ion_pushed, cudaStream_t st) {
+  const int bytes = kStageCap * 8;
+  cudaFuncSetAttribute(k_births_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  k_births_batch<R><<<ncol, kBirthThreads, bytes, st>>>(cols, ion_pushed);
 }
 
 // ---------------------------------------------------------------------------
@@ -888,11 +968,9 @@ __device__ __forceinline__ int fpad(int j) { return j + (j >> 4); }
 
 // Integer part of the field solve (one CTA, no floating point): the exact
 // prefix values S'_{j0-1} at the start of every thread segment, T and M.
-template <class R>
-__global__ void __launch_bounds__(kFieldThreads, 1)
-k_field_scan(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi,
-             long long *Dg, FieldScan *fs) {
-  extern __shared__ __align__(16) long long sD[];
+__device__ __forceinline__ void field_scan_body(const FieldK &f, const unsigned long long *__restrict__ Qe,
+                                                const unsigned long long *__restrict__ Qi, long long *Dg,
+                                                FieldScan *fs, long long *sD) {
   __shared__ __int128 sh[kFieldThreads];
   const int N = f.N;
   const int t = threadIdx.x;
@@ -920,6 +998,22 @@ k_field_scan(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned
   if (t == 0) { fs->T = T; fs->M = M; }
 }
 
+template <class R>
+__global__ void __launch_bounds__(kFieldThreads, 1)
+k_field_scan(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi,
+             long long *Dg, FieldScan *fs) {
+  extern __shared__ __align__(16) long long sD[];
+  field_scan_body(f, Qe, Qi, Dg, fs, sD);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kFieldThreads, 1) k_field_scan_batch(const ColDev<R> *cols) {
+  extern __shared__ __align__(16) long long sD[];
+  const ColDev<R> *cd = cols + blockIdx.x;
+  const FieldK f = cd->fk;
+  if (f.field_mode == PIC_FIELD_POISSON) field_scan_body(f, cd->sp[0].Q, cd->sp[1].Q, cd->Dg, cd->fs, sD);
+}
+
 // Floating-point part (many CTAs, one thread per node):
 //   E_{j+1/2} = (N S'_j - M) Cf,  E_j = (E_{j-1/2} + E_{j+1/2}) / 2 - E0,
 // with S'_j rebuilt from the segment start S'_{j0-1} and the charges of the
@@ -928,16 +1022,17 @@ k_field_scan(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned
 constexpr int kEvalThreads = 256;
 
 template <class R>
-__global__ void __launch_bounds__(kEvalThreads)
-k_field_eval(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi, Ctl *ctl,
-             const FieldScan *fs, double *E, double *Eh, R *Ef, int advance) {
+__device__ __forceinline__ void field_eval_body(const FieldK &f, const unsigned long long *__restrict__ Qe,
+                                                const unsigned long long *__restrict__ Qi, Ctl *ctl,
+                                                const FieldScan *fs, double *E, double *Eh, R *Ef, int advance,
+                                                int blk) {
   __shared__ long long sD[kEvalThreads + 64];
   const int N = f.N;
   const int seg = f.seg;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blk * blockDim.x + threadIdx.x;
   const double E0 = ctl->E0;
   // nodes of this block and the part of the first segment before it
-  const int jb = blockIdx.x * blockDim.x;
+  const int jb = blk * blockDim.x;
   const int sb = (jb / seg) * seg;               // start of the segment holding the block's first node
   const int lo = sb, hi = min(N, jb + (int)blockDim.x);
   for (int q = lo + threadIdx.x; q < hi; q += blockDim.x) sD[q - lo] = (long long)Qi[q] - (long long)Qe[q];
@@ -972,12 +1067,28 @@ k_field_eval(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned
   }
 }
 
+template <class R>
+__global__ void __launch_bounds__(kEvalThreads)
+k_field_eval(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi, Ctl *ctl,
+             const FieldScan *fs, double *E, double *Eh, R *Ef, int advance) {
+  field_eval_body<R>(f, Qe, Qi, ctl, fs, E, Eh, Ef, advance, blockIdx.x);
+}
+
+// batched columns: blockIdx.y = column, blockIdx.x = block of nodes
+template <class R>
+__global__ void __launch_bounds__(kEvalThreads) k_field_eval_batch(const ColDev<R> *cols, int advance) {
+  const ColDev<R> *cd = cols + blockIdx.y;
+  const FieldK f = cd->fk;
+  if ((int)(blockIdx.x * blockDim.x) >= f.N) return;
+  field_eval_body<R>(f, cd->sp[0].Q, cd->sp[1].Q, cd->ctl, cd->fs, cd->E, cd->Eh, reinterpret_cast<R *>(cd->Ef),
+                     advance, blockIdx.x);
+}
+
 // Diagnostic sample of the field step (one CTA, diagnostic steps only):
 // phi_j = -dx sum_{k<j} E_{k+1/2} (space-charge potential, phi_0 = 0), densities, E.
-template <class R>
-__global__ void __launch_bounds__(kFieldThreads, 1)
-k_field_diag(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi,
-             Ctl *ctl, const double *E, const double *Eh, Moments m) {
+__device__ __forceinline__ void field_diag_body(const FieldK &f, const unsigned long long *__restrict__ Qe,
+                                                const unsigned long long *__restrict__ Qi, Ctl *ctl, const double *E,
+                                                const double *Eh, const Moments &m) {
   __shared__ double shd[kFieldThreads];
   const int N = f.N;
   const int t = threadIdx.x;
@@ -1005,6 +1116,20 @@ k_field_diag(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned
 }
 
 template <class R>
+__global__ void __launch_bounds__(kFieldThreads, 1)
+k_field_diag(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi,
+             Ctl *ctl, const double *E, const double *Eh, Moments m) {
+  field_diag_body(f, Qe, Qi, ctl, E, Eh, m);
+}
+
+template <class R>
+__global__ void __launch_bounds__(kFieldThreads, 1) k_field_diag_batch(const ColDev<R> *cols) {
+  const ColDev<R> *cd = cols + blockIdx.x;
+  const FieldK f = cd->fk;
+  field_diag_body(f, cd->sp[0].Q, cd->sp[1].Q, cd->ctl, cd->E, cd->Eh, cd->m);
+}
+
+template <class R>
 void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned long long *Qi, Ctl *ctl, double *E,
                   double *Eh, R *Ef, Moments m, long long *Dg, FieldScan *fs, bool diag, bool advance,
                   cudaStream_t st) {
@@ -1016,6 +1141,17 @@ void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned 
   k_field_eval<R><<<(f.N + kEvalThreads - 1) / kEvalThreads, kEvalThreads, 0, st>>>(f, Qe, Qi, ctl, fs, E, Eh, Ef,
                                                                                    advance ? 1 : 0);
   if (diag) k_field_diag<R><<<1, kFieldThreads, 0, st>>>(f, Qe, Qi, ctl, E, Eh, m);
+}
+
+template <class R>
+void launch_field_batch(const ColDev<R> *cols, int ncol, int maxN, bool poisson, bool diag, cudaStream_t st) {
+  if (poisson) {
+    const int bytes = maxN <= kFieldSmemMax ? (maxN + maxN / 16 + 1) * 8 : 0;
+    if (bytes) cudaFuncSetAttribute(k_field_scan_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    k_field_scan_batch<R><<<ncol, kFieldThreads, bytes, st>>>(cols);
+  }
+  k_field_eval_batch<R><<<dim3((maxN + kEvalThreads - 1) / kEvalThreads, ncol), kEvalThreads, 0, st>>>(cols, 1);
+  if (diag) k_field_diag_batch<R><<<ncol, kFieldThreads, 0, st>>>(cols);
 }
 
 __global__ void k_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n) {
@@ -1115,7 +1251,12 @@ void launch_halfstep(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, const R *E
   template void launch_field<R>(const FieldK &, const unsigned long long *, const unsigned long long *, Ctl *,       \
                                 double *, double *, R *, Moments, long long *, FieldScan *, bool, bool,             \
                                 cudaStream_t);                                                                      \
-  template int push_smem_bytes<R>(int);
+  template int push_smem_bytes<R>(int);                                                                             \
+  template size_t push_layout<R>(int, int &, int &);                                                                \
+  template void launch_zero_q_batch<R>(const ColDev<R> *, int, int, int, cudaStream_t);                             \
+  template void launch_push_batch<R>(const ColDev<R> *, const int4 *, int, int, size_t, cudaStream_t);              \
+  template void launch_births_batch<R>(const ColDev<R> *, int, int, cudaStream_t);                                  \
+  template void launch_field_batch<R>(const ColDev<R> *, int, int, bool, bool, cudaStream_t);
 PIC_INST(double)
 PIC_INST(float)
 

@@ -172,3 +172,32 @@ def random_state(n: int, n_cells: int, rng: np.random.Generator, v_scale: float,
         v = v.astype(np.float32).astype(np.float64)
     ids = np.arange(id0, id0 + n, dtype=np.uint64)
     return cell, off, v[0].copy(), v[1].copy(), v[2].copy(), ids
+
+
+def config_batch_sweep(n_columns: int = 64, seed: int = 42, particle_scale: float = 1.0,
+                       precision: int = MIXED) -> List[Params]:
+    """Batched sweep of uneven columns: log-uniform draws from `seed` of
+    L in [0.05, 0.40] m, p in [0.3, 3] Torr, I in [0.1, 5] mA and 1e5..5e6 particles
+    per species; cells = round(L / 0.05 m * 2048) clamped to [2048, 16384]; gases
+    alternate argon / neon.  Readings (no drive from current is built): E0/p = 12 V/cm/Torr
+    for argon and 6 V/cm/Torr for neon (near the paper's striation onsets); n0 = 1e15 m^-3
+    x (I / 1 mA) (the model is linear in density); dt = 5e-12 s for every column (the
+    batch shares one time step; nu* dt <= 0.3 up to 3 Torr with 200 eV tables)."""
+    rng = np.random.default_rng(seed)
+
+    def logu(a, b):
+        return float(np.exp(rng.uniform(np.log(a), np.log(b))))
+
+    out = []
+    for c in range(n_columns):
+        L, p, I, n = logu(0.05, 0.40), logu(0.3, 3.0), logu(1e-4, 5e-3), logu(1e5, 5e6)
+        n = max(1000, int(n * particle_scale))
+        cells = int(min(16384, max(2048, round(L / 0.05 * 2048))))
+        argon = c % 2 == 0
+        xs = argon_xsecs(eps_max_e=200.0) if argon else neon_xsecs()
+        out.append(Params(gas_mass_amu=AMU_AR if argon else AMU_NE, pressure_torr=p, L_m=L, R_m=0.01,
+                          drive=DRIVE_E0, E0_Vpm=(1200.0 if argon else 600.0) * p, V_applied=0.0, I_A=I,
+                          xsec=xs, n_cells=cells, dt_s=5e-12, ion_subcycle=10, n_e0=n, n_i0=n,
+                          n0_m3=1e15 * (I / 1e-3), precision=precision, seed=seed, sort_every=1000,
+                          eps_max_e_eV=200.0, column=c))
+    return out
