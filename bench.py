@@ -121,6 +121,47 @@ def oracle_rate(n_per_species: int, steps: int, warmup: int = 1):
     return pushed_steps(s0, steps, n_per_species, n_per_species, p.ion_subcycle) / dt, dt
 
 
+def batched_vs_serial(pb, w, torch, steps: int, warmup: int, n_columns: int = 64):
+    """The 64-column sweep (uneven L, p, I, particles; argon and neon) advanced as one
+    batch (one launch per phase for all columns, graph-replayed ion cycles) and as 64
+    lone columns stepped one after another on the same GPU."""
+    cols = w.config_batch_sweep(n_columns=n_columns)
+    sub = cols[0].ion_subcycle
+    b = pb.Batch(cols)
+    b.step(warmup + 3)                      # three autotuning steps, then warm-up
+    s0 = b.columns[0].stats()["step"]
+    units = sum(pushed_steps(s0, steps, c.n_e0, c.n_i0, sub) for c in cols)
+    ext = torch.cuda.ExternalStream(b.stream())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ext)
+    b.step(steps)
+    e1.record(ext)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    b.set_timing(True)
+    b.step(sub)
+    launches = sum(v[1] for v in b.kernel_times().values())
+    b.set_timing(False)
+    b.close()
+    lone = [pb.Column(c) for c in cols]
+    for c in lone:
+        c.step(warmup + 3)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for c in lone:
+        c.step(steps)
+    torch.cuda.synchronize()
+    t_serial = time.perf_counter() - t
+    for c in lone:
+        c.close()
+    return {"columns": n_columns, "steps": steps, "pushed_particle_steps": units,
+            "batched": units / t_batch, "serial": units / t_serial, "unit": UNIT,
+            "speedup": t_serial / t_batch, "launches_per_ion_cycle": launches,
+            "workload": "64 columns, seed 42: L 0.05-0.40 m, p 0.3-3 Torr, I 0.1-5 mA, 1e5-5e6 particles "
+                        "per species, 2048-16384 cells, Ar/Ne alternating, dt 5e-12 s, MIXED"}
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -154,6 +195,7 @@ def main():
     ap.add_argument("--n", type=int, default=20_000_000, help="particles per species")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -264,6 +306,10 @@ def main():
         assert stx["step"] == host["step"] + args.steps
         col2.close()
 
+    batch = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch = batched_vs_serial(pb, w, torch, steps=200, warmup=min(args.warmup, 10))
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -271,7 +317,8 @@ def main():
                 "config": {"workload": WORKLOAD, "particles_per_species": args.n, "n_cells": p.n_cells,
                            "l2": "inputs larger than L2 (state 1.1 GB)", "parallelism": f"replicas x{world}",
                            "pushed_particle_steps": units},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_vs_serial": batch,
+                "gpu_launches": launches,
                 "kernel_ms": {k: v[0] for k, v in kt.items()}, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:

@@ -718,6 +718,7 @@ int pic_init(const pic_params *params, pic_handle **out) {
       cudaMalloc(&h->mom_iz, (size_t)h->N * 8) != cudaSuccess)
     return fail(set_err(h, PIC_ENOMEM, "device allocation failed"));
   cudaMemset(h->mom, 0, (size_t)h->N * 8 * 8);
+  cudaMemset(h->fs, 0, sizeof(pic::FieldScan));
   cudaMemset(h->mom_iz, 0, (size_t)h->N * 8);
   h->sc.order = h->k3_mem;
   h->sc.cand = h->k3_mem + pic::kStageCap;
@@ -1093,6 +1094,7 @@ int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, doub
   } else {
     pic::Ctl c{};
     c.E0 = E0;
+    cudaMemsetAsync(fs, 0, sizeof(pic::FieldScan), st);
     pic::FieldK f{};
     f.N = N;
     f.field_mode = PIC_FIELD_POISSON;

@@ -95,10 +95,15 @@ struct K3Scratch {
   uint32_t *vic;     // 2 * kStageCap victim slots (electrons, ions)
 };
 
-// exact integer prefix data handed from the scan kernel to the evaluation kernel
+// exact integer data handed from the reduction kernel to the evaluation kernel
+constexpr int kEvalThreads = 256;                         // nodes per block of the field kernels
+constexpr int kFieldBlocksMax = 65536 / kEvalThreads;     // n_cells <= 65536
 struct FieldScan {
-  __int128 Sp0[kFieldThreads];   // S'_{j0-1} at the start of each thread segment
+  __int128 R[kFieldBlocksMax];     // per node block: sum of D
+  __int128 U[kFieldBlocksMax];     // per node block: sum of (N - k) D_k
+  __int128 Sp0[kFieldBlocksMax];   // S'_{j0 - 1} at the start of each node block
   __int128 T, M;
+  unsigned int ticket;             // blocks done (the last one finishes, then resets it)
 };
 
 struct FieldK {

@@ -916,6 +916,13 @@ __device__ __forceinline__ __int128 shfl_i128(__int128 v, int src) {
   return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
 }
 
+__device__ __forceinline__ __int128 shfl_i128_down(__int128 v, int o) {
+  const unsigned __int128 u = (unsigned __int128)v;
+  const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)u, o);
+  const unsigned long long hi = __shfl_down_sync(0xffffffffu, (unsigned long long)(u >> 64), o);
+  return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+
 // exclusive block scan of 128-bit integers (warp shuffles, one pass through
 // shared memory for the warp totals); total receives the block sum
 __device__ __int128 block_excl_scan_i128(__int128 v, __int128 *sh, __int128 &total) {
@@ -962,98 +969,121 @@ __device__ double block_excl_scan_f64(double v, double *sh, double &total) {
   return incl - v;
 }
 
-// padded shared-memory index: one spare slot per 16 nodes keeps the per-thread
-// contiguous segments on distinct banks
-__device__ __forceinline__ int fpad(int j) { return j + (j >> 4); }
 
-// Integer part of the field solve (one CTA, no floating point): the exact
-// prefix values S'_{j0-1} at the start of every thread segment, T and M.
-__device__ __forceinline__ void field_scan_body(const FieldK &f, const unsigned long long *__restrict__ Qe,
-                                                const unsigned long long *__restrict__ Qi, long long *Dg,
-                                                FieldScan *fs, long long *sD) {
-  __shared__ __int128 sh[kFieldThreads];
+// Field solve in two launches over blocks of kEvalThreads nodes.
+// Reduction: each block sums R_b = sum D_k and U_b = sum (N - k) D_k over its
+// nodes (D = Q_i - Q_e); the last block to finish (atomic ticket, no waiting)
+// forms T = sum R_b, M = N U - T N (N+1)/2 (U = sum U_b) and the exact
+// block-start values S'_{jb-1} = N (R_0 + .. + R_{b-1}) - jb T.
+__device__ __forceinline__ void field_reduce_body(const FieldK &f, const unsigned long long *__restrict__ Qe,
+                                                  const unsigned long long *__restrict__ Qi, FieldScan *fs,
+                                                  int blk, int nblk) {
+  __shared__ __int128 sh[2 * 32 + 2];   // also the block scans of the last block (65 entries)
+  __shared__ bool last;
   const int N = f.N;
-  const int t = threadIdx.x;
-  long long *D = f.smem ? sD : Dg;   // indexed through fpad()
-  const int seg = f.seg;
-  const int j0 = min(N, t * seg), j1 = min(N, j0 + seg);
-#pragma unroll 8
-  for (int j = t; j < N; j += blockDim.x) D[fpad(j)] = (long long)__ldcg(Qi + j) - (long long)__ldcg(Qe + j);
-  __syncthreads();
-  __int128 loc = 0;
-  for (int j = j0; j < j1; ++j) loc += (__int128)D[fpad(j)];
-  __int128 T;
-  const __int128 pre = block_excl_scan_i128(loc, sh, T);
-  const uint32_t Nu = (uint32_t)N;
-  // S'_j = N run_j - (j+1) T obeys S'_j = S'_{j-1} + (N D_j - T)
-  const __int128 Sp0 = mul_u32(pre, Nu) - (__int128)j0 * T;
-  __int128 Sp = Sp0, Mloc = 0;
-  for (int j = j0; j < j1; ++j) {
-    Sp += mul_u32((__int128)D[fpad(j)], Nu) - T;
-    Mloc += Sp;
+  const int j = blk * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __int128 r = 0, u = 0;
+  if (j < N) {
+    const long long d = (long long)__ldcg(Qi + j) - (long long)__ldcg(Qe + j);
+    r = (__int128)d;
+    u = mul_u32(r, (uint32_t)(N - j));
   }
-  __int128 M;
-  (void)block_excl_scan_i128(Mloc, sh, M);
-  fs->Sp0[t] = Sp0;
-  if (t == 0) { fs->T = T; fs->M = M; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r += shfl_i128_down(r, o);
+    u += shfl_i128_down(u, o);
+  }
+  if (lane == 0) { sh[w] = r; sh[32 + w] = u; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __int128 R = 0, U = 0;
+    for (int q = 0; q < nw; ++q) { R += sh[q]; U += sh[32 + q]; }
+    fs->R[blk] = R;
+    fs->U[blk] = U;
+    __threadfence();
+    last = atomicAdd(&fs->ticket, 1u) == (unsigned)(nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // the last block: one thread per node block (nblk <= blockDim)
+  const uint32_t Nu = (uint32_t)N;
+  __int128 Rb = 0, Ub = 0;
+  if ((int)threadIdx.x < nblk) {
+    // L2 reads (the other blocks' writes are not in this SM's L1)
+    const longlong2 r2 = __ldcg(reinterpret_cast<const longlong2 *>(&fs->R[threadIdx.x]));
+    const longlong2 u2 = __ldcg(reinterpret_cast<const longlong2 *>(&fs->U[threadIdx.x]));
+    Rb = (__int128)(((unsigned __int128)(unsigned long long)r2.y << 64) | (unsigned __int128)(unsigned long long)r2.x);
+    Ub = (__int128)(((unsigned __int128)(unsigned long long)u2.y << 64) | (unsigned __int128)(unsigned long long)u2.x);
+  }
+  __int128 T, U;
+  const __int128 run = block_excl_scan_i128(Rb, sh, T);    // sum of D before this thread's block
+  (void)block_excl_scan_i128(Ub, sh, U);
+  if ((int)threadIdx.x < nblk) fs->Sp0[threadIdx.x] = mul_u32(run, Nu) - (__int128)(threadIdx.x * blockDim.x) * T;
+  if (threadIdx.x == 0) {
+    const __int128 half = (__int128)((unsigned long long)N * (unsigned long long)(N + 1) / 2ull);
+    fs->T = T;
+    fs->M = mul_u32(U, Nu) - half * T;
+    fs->ticket = 0u;
+  }
 }
 
 template <class R>
-__global__ void __launch_bounds__(kFieldThreads, 1)
-k_field_scan(FieldK f, const unsigned long long *__restrict__ Qe, const unsigned long long *__restrict__ Qi,
-             long long *Dg, FieldScan *fs) {
-  extern __shared__ __align__(16) long long sD[];
-  field_scan_body(f, Qe, Qi, Dg, fs, sD);
+__global__ void __launch_bounds__(kEvalThreads) k_field_reduce(FieldK f, const unsigned long long *__restrict__ Qe,
+                                                               const unsigned long long *__restrict__ Qi,
+                                                               FieldScan *fs) {
+  field_reduce_body(f, Qe, Qi, fs, blockIdx.x, gridDim.x);
 }
 
 template <class R>
-__global__ void __launch_bounds__(kFieldThreads, 1) k_field_scan_batch(const ColDev<R> *cols) {
-  extern __shared__ __align__(16) long long sD[];
-  const ColDev<R> *cd = cols + blockIdx.x;
+__global__ void __launch_bounds__(kEvalThreads) k_field_reduce_batch(const ColDev<R> *cols) {
+  const ColDev<R> *cd = cols + blockIdx.y;
   const FieldK f = cd->fk;
-  if (f.field_mode == PIC_FIELD_POISSON) field_scan_body(f, cd->sp[0].Q, cd->sp[1].Q, cd->Dg, cd->fs, sD);
+  const int nblk = (f.N + kEvalThreads - 1) / kEvalThreads;
+  if ((int)blockIdx.x >= nblk || f.field_mode != PIC_FIELD_POISSON) return;
+  field_reduce_body(f, cd->sp[0].Q, cd->sp[1].Q, cd->fs, blockIdx.x, nblk);
 }
 
-// Floating-point part (many CTAs, one thread per node):
-//   E_{j+1/2} = (N S'_j - M) Cf,  E_j = (E_{j-1/2} + E_{j+1/2}) / 2 - E0,
-// with S'_j rebuilt from the segment start S'_{j0-1} and the charges of the
-// segment (staged in shared memory).  S'_{-1} = 0 = S'_{N-1}, so node 0 gets
-// E_{-1/2} = E_{N-1/2} from the same formula.
-constexpr int kEvalThreads = 256;
-
+// Evaluation (one thread per node): S'_j = S'_{jb-1} + sum over the block up
+// to j of (N D_k - T) by a block scan;
+//   E_{j+1/2} = (N S'_j - M) Cf,  E_j = (E_{j-1/2} + E_{j+1/2}) / 2 - E0.
+// S'_{-1} = 0 = S'_{N-1}, so node 0 gets E_{-1/2} = E_{N-1/2} from the same formula.
 template <class R>
 __device__ __forceinline__ void field_eval_body(const FieldK &f, const unsigned long long *__restrict__ Qe,
                                                 const unsigned long long *__restrict__ Qi, Ctl *ctl,
                                                 const FieldScan *fs, double *E, double *Eh, R *Ef, int advance,
                                                 int blk) {
-  __shared__ long long sD[kEvalThreads + 64];
+  __shared__ __int128 sh[32 + 32 + 1];
+  __shared__ double sEh[kEvalThreads + 1];
   const int N = f.N;
-  const int seg = f.seg;
   const int j = blk * blockDim.x + threadIdx.x;
   const double E0 = ctl->E0;
-  // nodes of this block and the part of the first segment before it
-  const int jb = blk * blockDim.x;
-  const int sb = (jb / seg) * seg;               // start of the segment holding the block's first node
-  const int lo = sb, hi = min(N, jb + (int)blockDim.x);
-  for (int q = lo + threadIdx.x; q < hi; q += blockDim.x) sD[q - lo] = (long long)Qi[q] - (long long)Qe[q];
+  const bool poisson = f.field_mode == PIC_FIELD_POISSON;
+  double eh = 0.0;
+  if (poisson) {
+    const uint32_t Nu = (uint32_t)N;
+    const __int128 T = fs->T, M = fs->M;
+    __int128 v = 0;
+    if (j < N) v = mul_u32((__int128)((long long)Qi[j] - (long long)Qe[j]), Nu) - T;
+    __int128 tot;
+    const __int128 ex = block_excl_scan_i128(v, sh, tot);
+    const __int128 Sp0 = fs->Sp0[blk];
+    const __int128 Sp = Sp0 + ex + v;                                         // S'_j
+    eh = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;                          // E_{j+1/2}
+    if (threadIdx.x == 0) sEh[0] = i128_to_double(mul_u32(Sp0, Nu) - M) * f.Cf;   // E_{jb-1/2}
+  }
+  sEh[threadIdx.x + 1] = eh;
   __syncthreads();
   bool bad = false;
   if (j < N) {
     double e;
-    if (f.field_mode == PIC_FIELD_APPLIED) {
+    if (poisson) {
+      Eh[j] = eh;
+      e = 0.5 * (sEh[threadIdx.x] + eh) + (-E0);
+    } else {
       Eh[j] = 0.0;
       e = -E0;
-    } else {
-      const uint32_t Nu = (uint32_t)N;
-      const __int128 T = fs->T, M = fs->M;
-      const int g = j / seg, j0 = g * seg;
-      __int128 Sp = fs->Sp0[g];                  // S'_{j0-1}
-      for (int q = j0; q < j; ++q) Sp += mul_u32((__int128)sD[q - lo], Nu) - T;
-      const double prev = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;      // E_{j-1/2}
-      Sp += mul_u32((__int128)sD[j - lo], Nu) - T;
-      const double eh = i128_to_double(mul_u32(Sp, Nu) - M) * f.Cf;        // E_{j+1/2}
-      Eh[j] = eh;
-      e = 0.5 * (prev + eh) + (-E0);
     }
     E[j] = e;
     Ef[j] = (R)e;
@@ -1133,24 +1163,18 @@ template <class R>
 void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned long long *Qi, Ctl *ctl, double *E,
                   double *Eh, R *Ef, Moments m, long long *Dg, FieldScan *fs, bool diag, bool advance,
                   cudaStream_t st) {
-  if (f.field_mode == PIC_FIELD_POISSON) {
-    const int bytes = f.smem ? (f.N + f.N / 16 + 1) * 8 : 0;
-    if (f.smem) cudaFuncSetAttribute(k_field_scan<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_field_scan<R><<<1, kFieldThreads, bytes, st>>>(f, Qe, Qi, Dg, fs);
-  }
-  k_field_eval<R><<<(f.N + kEvalThreads - 1) / kEvalThreads, kEvalThreads, 0, st>>>(f, Qe, Qi, ctl, fs, E, Eh, Ef,
-                                                                                   advance ? 1 : 0);
+  (void)Dg;
+  const int nblk = (f.N + kEvalThreads - 1) / kEvalThreads;
+  if (f.field_mode == PIC_FIELD_POISSON) k_field_reduce<R><<<nblk, kEvalThreads, 0, st>>>(f, Qe, Qi, fs);
+  k_field_eval<R><<<nblk, kEvalThreads, 0, st>>>(f, Qe, Qi, ctl, fs, E, Eh, Ef, advance ? 1 : 0);
   if (diag) k_field_diag<R><<<1, kFieldThreads, 0, st>>>(f, Qe, Qi, ctl, E, Eh, m);
 }
 
 template <class R>
 void launch_field_batch(const ColDev<R> *cols, int ncol, int maxN, bool poisson, bool diag, cudaStream_t st) {
-  if (poisson) {
-    const int bytes = maxN <= kFieldSmemMax ? (maxN + maxN / 16 + 1) * 8 : 0;
-    if (bytes) cudaFuncSetAttribute(k_field_scan_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_field_scan_batch<R><<<ncol, kFieldThreads, bytes, st>>>(cols);
-  }
-  k_field_eval_batch<R><<<dim3((maxN + kEvalThreads - 1) / kEvalThreads, ncol), kEvalThreads, 0, st>>>(cols, 1);
+  const dim3 grid((maxN + kEvalThreads - 1) / kEvalThreads, ncol);
+  if (poisson) k_field_reduce_batch<R><<<grid, kEvalThreads, 0, st>>>(cols);
+  k_field_eval_batch<R><<<grid, kEvalThreads, 0, st>>>(cols, 1);
   if (diag) k_field_diag_batch<R><<<ncol, kFieldThreads, 0, st>>>(cols);
 }
 

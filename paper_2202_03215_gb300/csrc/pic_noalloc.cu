@@ -78,6 +78,9 @@ int pic_field_periodic_noalloc(const int64_t *Q_i, const int64_t *Q_e, int n_cel
   c.E0 = E0;
   e = cudaMemcpyAsync(ctl, &c, sizeof c, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return PIC_ECUDA;
+  // the reduction's completion ticket must start at zero
+  e = cudaMemsetAsync(&fs->ticket, 0, sizeof fs->ticket, st);
+  if (e != cudaSuccess) return PIC_ECUDA;
   pic::FieldK f{};
   f.N = n_cells;
   f.field_mode = PIC_FIELD_POISSON;
