@@ -57,7 +57,9 @@ extern "C" {
 /* how the applied field E0 is set */
 #define PIC_DRIVE_E0 0       /* E0 = E0_Vpm (the paper's control parameter) */
 #define PIC_DRIVE_V 1        /* E0 = V_applied / L */
-#define PIC_DRIVE_CIRCUIT 2  /* reserved: external resistor circuit (Sec. V) */
+#define PIC_DRIVE_CIRCUIT 2  /* Sec. V: external circuit, E0 = (U_src - R_ext J) / L after every step,
+                                J = e w (sum v_x,ions - sum v_x,electrons) / L over the pushed particles
+                                (ions at their last push; velocities summed as round(256 v_x), exact) */
 
 /* field: self-consistent (Sec. II) or the applied field alone (uniform-field swarm) */
 #define PIC_FIELD_POISSON 0
@@ -102,7 +104,8 @@ typedef struct pic_params {
   int32_t field_mode;      /* PIC_FIELD_* */
   double E0_Vpm;           /* |applied field| for PIC_DRIVE_E0; the applied field is -E0 */
   double V_applied;        /* voltage across L for PIC_DRIVE_V */
-  double I_A, U_src, R_ext_ohm_m2;  /* current / source / resistor (reserved drives) */
+  double I_A, U_src, R_ext_ohm_m2;  /* discharge current (workload label); circuit source voltage (V) and
+                                       resistor (Ohm m^2) of PIC_DRIVE_CIRCUIT */
   int32_t n_xsec, pad0;
   const pic_xsec *xsec;    /* n_xsec processes; at most 8 per species */
   int32_t n_cells;         /* grid cells = nodes (periodic), 3 <= n_cells <= 65536 */

@@ -250,7 +250,7 @@ struct ora_t {
   ora_params p;
   int N;
   /* derived (Sec. II) */
-  double ng, dx, w, M, C_field, E0;
+  double ng, dx, w, M, C_field, E0, Cj;
   double dt_i;
   real a_e, d_e, a_i, d_i, K_e, K_i, V_e, em, sig_n, sig_e0, sig_i0;
   real inv_de_e, inv_de_i;
@@ -270,6 +270,7 @@ struct ora_t {
   double *Eh;     /* half-node space-charge field */
   real *Ef;       /* gather copy, N+1 */
   int64_t step, next_id;
+  int64_t sumv[2];          /* circuit drive: sum of round(256 vx) over electrons (this step) and ions (last push) */
   birth *births; int64_t nb, bcap;
   int64_t *dead_e, *dead_i; int64_t nde, ndi;
   ora_stats st;
@@ -517,6 +518,7 @@ static void electron_step(ora_t *h, int64_t p, int diag) {
   s->code[p] = code;
   if (dead) { h->dead_e[h->nde++] = p; return; }
   deposit(s->Q, h->N, cell, off, +1);
+  if (h->p.drive == ORA_DRIVE_CIRCUIT) h->sumv[0] += (int64_t)llrint((double)(vx * (real)256));
   if (diag) {
     double eps = (double)(h->K_e * (vx * vx + vy * vy + vz * vz));
     moment_add(h->m_ge, h->N, cell, off, (double)vx);
@@ -586,6 +588,7 @@ static void ion_step(ora_t *h, int64_t p, int diag) {
   s->code[p] = code;
   if (dead) { h->dead_i[h->ndi++] = p; return; }
   deposit(s->Q, h->N, cell, off, +1);
+  if (h->p.drive == ORA_DRIVE_CIRCUIT) h->sumv[1] += (int64_t)llrint((double)(vx * (real)256));
   if (diag) moment_add(h->m_gi, h->N, cell, off, (double)vx);
 }
 
@@ -763,9 +766,11 @@ static int step_once(ora_t *h) {
     if (h->step % pi == 0) sort_species(h, &h->i);
   }
   memset(h->e.Q, 0, sizeof(int64_t) * (size_t)h->N);
+  h->sumv[0] = 0;
   for (int64_t p = 0; p < h->e.n; ++p) electron_step(h, p, diag);
   if (ion_push) {
     memset(h->i.Q, 0, sizeof(int64_t) * (size_t)h->N);
+    h->sumv[1] = 0;
     for (int64_t p = 0; p < h->i.n; ++p) ion_step(h, p, diag);
   }
   if (h->err) return h->err;
@@ -773,6 +778,14 @@ static int step_once(ora_t *h) {
   if (rc) return rc;
   h->step++;
   h->m_steps++;
+  /* Sec. V: an external circuit with a resistor sets the applied field,
+   * E0 = (U - R_ext J) / L, J = e w (sum v_i - sum v_e) / L over the pushed
+   * particles (ions at their last push) -- build reading of "adding an
+   * external circuit with a resistor to adjust the applied field E0". */
+  if (h->p.drive == ORA_DRIVE_CIRCUIT) {
+    double J = h->Cj * (double)(h->sumv[1] - h->sumv[0]);
+    h->E0 = (h->p.U_src - h->p.R_ext_ohm_m2 * J) / h->p.L_m;
+  }
   solve_field(h);
   if (diag) {
     double phi = 0.0;
@@ -856,6 +869,7 @@ int ora_create(const ora_params *pp, ora_t **out) {
   h->w = (pp->n_e0 > 0) ? pp->n0_m3 * pp->L_m / (double)pp->n_e0 : 0.0;
   h->C_field = (QE * h->w) / (EPS0 * TWO32);
   h->E0 = (pp->drive == ORA_DRIVE_V) ? pp->V_applied / pp->L_m : pp->E0_Vpm;
+  h->Cj = QE * h->w / (pp->L_m * 256.0);
   int sub = pp->ion_subcycle > 0 ? pp->ion_subcycle : 1;
   h->dt_i = (double)sub * pp->dt_s;
   h->a_e = (real)(-QE / ME * pp->dt_s);
@@ -949,6 +963,7 @@ int ora_create(const ora_params *pp, ora_t **out) {
   solve_field(h);
   half_step_back(h, &h->e, h->a_e);
   half_step_back(h, &h->i, h->a_i);
+  for (int64_t p = 0; p < h->i.n; ++p) h->sumv[1] += (int64_t)llrint((double)(h->i.vx[p] * (real)256));
   *out = h;
   return 0;
 }
@@ -1009,6 +1024,8 @@ int ora_set_state(ora_t *h, const ora_state *s) {
     sp[q]->n = ns[q];
   }
   h->step = s->step; h->next_id = s->next_id; h->E0 = s->E0;
+  h->sumv[1] = 0;
+  for (int64_t p = 0; p < h->i.n; ++p) h->sumv[1] += (int64_t)llrint((double)(h->i.vx[p] * (real)256));
   redeposit(h, &h->e);
   if (s->Q_i) memcpy(h->i.Q, s->Q_i, sizeof(int64_t) * (size_t)h->N);
   else redeposit(h, &h->i);

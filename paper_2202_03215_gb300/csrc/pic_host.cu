@@ -186,8 +186,8 @@ void t_begin(pic_handle *h) {
   }
   cudaEventRecord(h->ev[h->ev_used], h->stream);
 }
-void t_end(pic_handle *h, int cls) {
-  h->klaunch[cls]++;
+void t_end(pic_handle *h, int cls, int nkernels = 1) {
+  h->klaunch[cls] += nkernels;
   if (!h->timing) return;
   cudaEventRecord(h->ev[h->ev_used + 1], h->stream);
   h->ev_cls.push_back(cls);
@@ -223,6 +223,7 @@ template <class R> int setup_tables(pic_handle *h) {
   k.ntab = n;
   k.loss_mode = p.loss_mode;
   k.field_mode = p.field_mode;
+  k.drive = p.drive;
   k.flags = p.flags;
   k.diag_every = p.diag_every;
   k.sub = p.ion_subcycle;
@@ -348,6 +349,7 @@ template <class R> int run_init(pic_handle *h) {
                        h->Dg, h->fs, false, false, h->stream);
   pic::launch_halfstep<R>(k, h->sp[0], h->ctl, reinterpret_cast<R *>(h->Ef), 0, h->stream);
   pic::launch_halfstep<R>(k, h->sp[1], h->ctl, reinterpret_cast<R *>(h->Ef), 1, h->stream);
+  if (p.drive == PIC_DRIVE_CIRCUIT) pic::launch_sumv<R>(h->sp[1], h->ctl, 1, h->stream);
   CU(h, cudaGetLastError());
   return 0;
 }
@@ -359,20 +361,27 @@ template <class R> int enqueue_step(pic_handle *h) {
   const R *Ef = reinterpret_cast<const R *>(h->Ef);
   // electrons sorted every sort_every steps, ions every sort_every * ion_subcycle steps
   const int se = h->p.sort_every;
+  const int sort_kernels = 3 * pic::sort_passes(h->N) + (pic::sort_passes(h->N) & 1);
   if (se > 0 && h->host_step % se == 0) {
     t_begin(h);
+    int nk = sort_kernels;
     pic::launch_sort<R>(h->sp[0], h->sb[0], &h->ctl->n[0], h->sp[0].cap, h->N, h->nsm, h->stream);
     const long long pi = (long long)se * (sub > 0 ? sub : 1);
-    if (h->host_step % pi == 0)
+    if (h->host_step % pi == 0) {
       pic::launch_sort<R>(h->sp[1], h->sb[1], &h->ctl->n[1], h->sp[1].cap, h->N, h->nsm, h->stream);
-    t_end(h, PIC_K_SORT);
+      nk += sort_kernels;
+    }
+    t_end(h, PIC_K_SORT, nk);
   }
+  const bool circuit = h->p.drive == PIC_DRIVE_CIRCUIT;
+  if (circuit) CU(h, cudaMemsetAsync(&h->ctl->sumv[0], 0, 8, h->stream));
   CU(h, cudaMemsetAsync(h->sp[0].Q, 0, (size_t)h->N * 8, h->stream));
   t_begin(h);
   pic::launch_push<R>(k, h->sp[0], h->ctl, Ef, bbuf<R>(h), h->m, 0, h->nsm, h->stream);
   t_end(h, PIC_K_PUSH_E);
   if (ion_push) {
     CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->N * 8, h->stream));
+    if (circuit) CU(h, cudaMemsetAsync(&h->ctl->sumv[1], 0, 8, h->stream));
     t_begin(h);
     pic::launch_push<R>(k, h->sp[1], h->ctl, Ef, bbuf<R>(h), h->m, 1, h->nsm, h->stream);
     t_end(h, PIC_K_PUSH_I);
@@ -384,7 +393,7 @@ template <class R> int enqueue_step(pic_handle *h) {
   t_begin(h);
   pic::launch_field<R>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<R *>(h->Ef), h->m,
                        h->Dg, h->fs, diag, true, h->stream);
-  t_end(h, PIC_K_FIELD);
+  t_end(h, PIC_K_FIELD, (h->p.field_mode == PIC_FIELD_POISSON ? 2 : 1) + (diag ? 1 : 0));
   CU(h, cudaGetLastError());
   h->host_step++;
   return 0;
@@ -422,8 +431,10 @@ int validate(const pic_params *p) {
   if (p->n_table < 3) return set_err(nullptr, PIC_EINVAL, "n_table must be >= 3");
   if (p->precision != PIC_FP64 && p->precision != PIC_MIXED) return set_err(nullptr, PIC_EINVAL, "bad precision");
   if (p->loss_mode < PIC_LOSS_PAIR || p->loss_mode > PIC_LOSS_SWARM) return set_err(nullptr, PIC_EINVAL, "bad loss mode");
-  if (p->drive != PIC_DRIVE_E0 && p->drive != PIC_DRIVE_V)
+  if (p->drive != PIC_DRIVE_E0 && p->drive != PIC_DRIVE_V && p->drive != PIC_DRIVE_CIRCUIT)
     return set_err(nullptr, PIC_EINVAL, "drive %d not supported", p->drive);
+  if (p->drive == PIC_DRIVE_CIRCUIT && p->field_mode != PIC_FIELD_POISSON)
+    return set_err(nullptr, PIC_EINVAL, "the circuit drive needs the self-consistent field");
   if (p->field_mode != PIC_FIELD_POISSON && p->field_mode != PIC_FIELD_APPLIED)
     return set_err(nullptr, PIC_EINVAL, "bad field mode");
   if (p->ion_subcycle < 0) return set_err(nullptr, PIC_EINVAL, "ion_subcycle < 0");
@@ -529,22 +540,27 @@ template <class R> int enqueue_batch_step(pic_handle *b) {
   if (se > 0 && b->host_step % se == 0) {
     t_begin(b);
     const long long pi = (long long)se * (sub > 0 ? sub : 1);
+    int nk = 0;
     for (pic_handle *c : b->cols) {
+      const int sk = 3 * pic::sort_passes(c->N) + (pic::sort_passes(c->N) & 1);
       pic::launch_sort<R>(c->sp[0], c->sb[0], &c->ctl->n[0], c->sp[0].cap, c->N, b->nsm, b->stream);
-      if (b->host_step % pi == 0)
+      nk += sk;
+      if (b->host_step % pi == 0) {
         pic::launch_sort<R>(c->sp[1], c->sb[1], &c->ctl->n[1], c->sp[1].cap, c->N, b->nsm, b->stream);
+        nk += sk;
+      }
     }
-    t_end(b, PIC_K_SORT);
+    t_end(b, PIC_K_SORT, nk);
   }
   t_begin(b);
   pic::launch_zero_q_batch<R>(cd, ncol, 0, b->maxN, b->stream);
   pic::launch_push_batch<R>(cd, b->sched, b->nsched[0], 0, b->push_smem, b->stream);
-  t_end(b, PIC_K_PUSH_E);
+  t_end(b, PIC_K_PUSH_E, 2);
   if (ion_push && b->nsched[1] > 0) {
     t_begin(b);
     pic::launch_zero_q_batch<R>(cd, ncol, 1, b->maxN, b->stream);
     pic::launch_push_batch<R>(cd, b->sched + b->nsched[0], b->nsched[1], 1, b->push_smem, b->stream);
-    t_end(b, PIC_K_PUSH_I);
+    t_end(b, PIC_K_PUSH_I, 2);
   }
   t_begin(b);
   pic::launch_births_batch<R>(cd, ncol, ion_push ? 1 : 0, b->stream);
@@ -552,7 +568,7 @@ template <class R> int enqueue_batch_step(pic_handle *b) {
   const bool diag = c0->p.diag_every > 0 && (b->host_step % c0->p.diag_every) == 0;
   t_begin(b);
   pic::launch_field_batch<R>(cd, ncol, b->maxN, c0->p.field_mode == PIC_FIELD_POISSON, diag, b->stream);
-  t_end(b, PIC_K_FIELD);
+  t_end(b, PIC_K_FIELD, (c0->p.field_mode == PIC_FIELD_POISSON ? 2 : 1) + (diag ? 1 : 0));
   CU(b, cudaGetLastError());
   b->host_step++;
   for (pic_handle *c : b->cols) c->host_step = b->host_step;
@@ -745,6 +761,11 @@ int pic_init(const pic_params *params, pic_handle **out) {
   h->fk.dx = h->dx;
   h->fk.smem = h->N <= pic::kFieldSmemMax ? 1 : 0;
   h->fk.seg = (h->N + pic::kFieldThreads - 1) / pic::kFieldThreads;
+  h->fk.circuit = p.drive == PIC_DRIVE_CIRCUIT ? 1 : 0;
+  h->fk.Cj = kQe * h->w / (p.L_m * 256.0);
+  h->fk.U = p.U_src;
+  h->fk.Rext = p.R_ext_ohm_m2;
+  h->fk.L = p.L_m;
   int rc2 = h->mixed ? init_typed<float>(h) : init_typed<double>(h);
   h->p.xsec = nullptr;
   h->p.n_xsec = 0;
@@ -972,7 +993,12 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
   CU(h, cudaMemcpy(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost));
   c.n[0] = in->n_e; c.n[1] = in->n_i; c.step = in->step; c.next_id = in->next_id; c.E0 = in->E0;
   c.status = 0; c.n_birth = 0; c.n_dead[0] = c.n_dead[1] = 0;
+  c.sumv[0] = c.sumv[1] = 0;
   CU(h, cudaMemcpy(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
+  if (h->p.drive == PIC_DRIVE_CIRCUIT) {
+    if (h->mixed) pic::launch_sumv<float>(h->sp[1], h->ctl, 1, h->stream);
+    else pic::launch_sumv<double>(h->sp[1], h->ctl, 1, h->stream);
+  }
   h->latched = 0;
   h->host_step = in->step;
   CU(h, cudaMemset(h->sp[0].Q, 0, (size_t)h->N * 8));

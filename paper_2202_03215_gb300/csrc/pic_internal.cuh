@@ -45,6 +45,7 @@ struct Ctl {
   unsigned long long n_coll[2][kMaxProc];
   unsigned long long births, losses[2], overflow[2];
   long long n_diag, m_samples, m_steps;
+  long long sumv[2];       // circuit drive: sum of round(256 vx), electrons of this step, ions of their last push
 };
 
 struct SpeciesDev {
@@ -70,6 +71,7 @@ template <class R> struct SpecK {
 
 template <class R> struct StepK {
   int N, ntab, loss_mode, field_mode;
+  int drive, pad_;
   unsigned flags;
   int diag_every, sub;
   uint32_t column;
@@ -110,6 +112,8 @@ struct FieldK {
   int N, field_mode, sub, diag_every;
   int smem;           // node arrays staged in shared memory (N <= kFieldSmemMax)
   int seg;            // nodes per thread segment: ceil(N / kFieldThreads)
+  int circuit;        // E0 = (U - R_ext J) / L after every step (Sec. V)
+  double Cj, U, Rext, L;   // J = Cj (sum_i - sum_e); source voltage; resistor (Ohm m^2); length
   double Cf;          // e w / (eps0 2^32 N^2)
   double dx;
 };
@@ -153,6 +157,8 @@ template <class R>
 void launch_deposit(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, int species, cudaStream_t st);
 template <class R>
 void launch_halfstep(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, const R *Ef, int species, cudaStream_t st);
+// ctl->sumv[species] += sum of round(256 vx) over the species (circuit drive start)
+template <class R> void launch_sumv(SpeciesDev s, Ctl *ctl, int species, cudaStream_t st);
 template <class R>
 void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBuf<R> bb, Moments m,
                  int species, int nsm, cudaStream_t st);

@@ -117,6 +117,10 @@ template <class R> __device__ __forceinline__ Queue<R> queue_at(unsigned char *q
 }
 template <class R> constexpr size_t queue_bytes() { return (size_t)kQcap * (8 + 5 * sizeof(R) + 8); }
 
+// round(256 vx) to nearest even, as an integer (exact, order independent sums)
+__device__ __forceinline__ long long vfix(float v) { return __float2ll_rn(v * 256.0f); }
+__device__ __forceinline__ long long vfix(double v) { return __double2ll_rn(v * 256.0); }
+
 // diagnostic moments of one particle (FP64, cloud-in-cell weights)
 template <class R, int SP>
 __device__ __forceinline__ void add_moments(const SpecK<R> &sp, const Moments &m, int N, int32_t cell, R off, R vx,
@@ -363,6 +367,8 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
   const bool record = (k.flags & PIC_FLAG_RECORD_CODES) != 0;
   const int qoff = (threadIdx.x >> 5) * kWarpQ;   // this warp's queue slice
   int wq = 0;                                     // its length (warp-uniform)
+  const bool circuit = k.drive == PIC_DRIVE_CIRCUIT;
+  long long vsum = 0;                             // circuit drive: this thread's sum of round(256 vx)
 
   // collision path for the warp's first nq (<= 32) queued candidates, one per lane
   auto flush = [&](int nq) {
@@ -377,6 +383,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
       rec_store<R>(s.rec, qp, qoff_, qx, qy, qz);
       if (record) s.code[qp] = sel >= 0 ? sp.xs[sel] : -1;
       if (diag) add_moments<R, SP>(sp, m, N, qcell, qoff_, qx, qy, qz);
+      if (circuit) vsum += vfix(qx);
     }
     for (int q = 0; q < sp.np; ++q) {
       const unsigned b = __ballot_sync(kFull, sel == q);
@@ -437,6 +444,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
         rec_store<R>(s.rec, p, off, vx, vy, vz);
         if (record) s.code[p] = dead ? -2 : -1;
         if (!dead && diag) add_moments<R, SP>(sp, m, N, cell, off, vx, vy, vz);
+        if (!dead && circuit) vsum += vfix(vx);
       }
       if (dead) {
         const int idx = atomicAdd(&ctl->n_dead[SP], 1);
@@ -469,6 +477,12 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     }
   }
   if (wq > 0) flush(wq);
+  if (circuit) {
+    unsigned long long u = (unsigned long long)vsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(kFull, u, o);
+    if (lane == 0 && u) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->sumv[SP]), u);
+  }
   __syncthreads();
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
     const unsigned nq = bins.cnt[j];
@@ -558,6 +572,7 @@ void launch_push_batch(const ColDev<R> *cols, const int4 *sched, int nblocks, in
 template <class R> __global__ void k_zero_q_batch(const ColDev<R> *cols, int species) {
   const ColDev<R> *cd = cols + blockIdx.y;
   unsigned long long *Q = cd->sp[species].Q;
+  if (blockIdx.x == 0 && threadIdx.x == 0) cd->ctl->sumv[species] = 0;   // circuit-drive sum of this push
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cd->N; j += gridDim.x * blockDim.x) Q[j] = 0ull;
 }
 
@@ -976,8 +991,8 @@ __device__ double block_excl_scan_f64(double v, double *sh, double &total) {
 // forms T = sum R_b, M = N U - T N (N+1)/2 (U = sum U_b) and the exact
 // block-start values S'_{jb-1} = N (R_0 + .. + R_{b-1}) - jb T.
 __device__ __forceinline__ void field_reduce_body(const FieldK &f, const unsigned long long *__restrict__ Qe,
-                                                  const unsigned long long *__restrict__ Qi, FieldScan *fs,
-                                                  int blk, int nblk) {
+                                                  const unsigned long long *__restrict__ Qi, FieldScan *fs, Ctl *ctl,
+                                                  int blk, int nblk, int advance) {
   __shared__ __int128 sh[2 * 32 + 2];   // also the block scans of the last block (65 entries)
   __shared__ bool last;
   const int N = f.N;
@@ -1026,14 +1041,19 @@ __device__ __forceinline__ void field_reduce_body(const FieldK &f, const unsigne
     fs->T = T;
     fs->M = mul_u32(U, Nu) - half * T;
     fs->ticket = 0u;
+    if (f.circuit && advance) {
+      // Sec. V: the external circuit sets the applied field for the next step
+      const double J = f.Cj * (double)(ctl->sumv[1] - ctl->sumv[0]);
+      ctl->E0 = (f.U - f.Rext * J) / f.L;
+    }
   }
 }
 
 template <class R>
 __global__ void __launch_bounds__(kEvalThreads) k_field_reduce(FieldK f, const unsigned long long *__restrict__ Qe,
                                                                const unsigned long long *__restrict__ Qi,
-                                                               FieldScan *fs) {
-  field_reduce_body(f, Qe, Qi, fs, blockIdx.x, gridDim.x);
+                                                               FieldScan *fs, Ctl *ctl, int advance) {
+  field_reduce_body(f, Qe, Qi, fs, ctl, blockIdx.x, gridDim.x, advance);
 }
 
 template <class R>
@@ -1042,7 +1062,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_field_reduce_batch(const ColDe
   const FieldK f = cd->fk;
   const int nblk = (f.N + kEvalThreads - 1) / kEvalThreads;
   if ((int)blockIdx.x >= nblk || f.field_mode != PIC_FIELD_POISSON) return;
-  field_reduce_body(f, cd->sp[0].Q, cd->sp[1].Q, cd->fs, blockIdx.x, nblk);
+  field_reduce_body(f, cd->sp[0].Q, cd->sp[1].Q, cd->fs, cd->ctl, blockIdx.x, nblk, 1);
 }
 
 // Evaluation (one thread per node): S'_j = S'_{jb-1} + sum over the block up
@@ -1165,7 +1185,8 @@ void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned 
                   cudaStream_t st) {
   (void)Dg;
   const int nblk = (f.N + kEvalThreads - 1) / kEvalThreads;
-  if (f.field_mode == PIC_FIELD_POISSON) k_field_reduce<R><<<nblk, kEvalThreads, 0, st>>>(f, Qe, Qi, fs);
+  if (f.field_mode == PIC_FIELD_POISSON)
+    k_field_reduce<R><<<nblk, kEvalThreads, 0, st>>>(f, Qe, Qi, fs, ctl, advance ? 1 : 0);
   k_field_eval<R><<<nblk, kEvalThreads, 0, st>>>(f, Qe, Qi, ctl, fs, E, Eh, Ef, advance ? 1 : 0);
   if (diag) k_field_diag<R><<<1, kFieldThreads, 0, st>>>(f, Qe, Qi, ctl, E, Eh, m);
 }
@@ -1263,6 +1284,23 @@ void launch_halfstep(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, const R *E
   k_halfstep<R><<<152 * 8, 256, 0, st>>>(s, ctl, Ef, species, k.sp[species].a);
 }
 
+template <class R> __global__ void k_sumv(SpeciesDev s, Ctl *ctl, int species) {
+  const long long n = ctl->n[species];
+  long long acc = 0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    R off, vx, vy, vz;
+    rec_load<R>(s.rec, p, off, vx, vy, vz);
+    acc += vfix(vx);
+  }
+  unsigned long long u = (unsigned long long)acc;
+  for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+  if ((threadIdx.x & 31) == 0 && u) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->sumv[species]), u);
+}
+
+template <class R> void launch_sumv(SpeciesDev s, Ctl *ctl, int species, cudaStream_t st) {
+  k_sumv<R><<<152 * 4, 256, 0, st>>>(s, ctl, species);
+}
+
 // explicit instantiations
 #define PIC_INST(R)                                                                                                  \
   template void launch_init<R>(const StepK<R> &, SpeciesDev, int, int64_t, uint64_t, R, cudaStream_t);              \
@@ -1276,6 +1314,7 @@ void launch_halfstep(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, const R *E
                                 double *, double *, R *, Moments, long long *, FieldScan *, bool, bool,             \
                                 cudaStream_t);                                                                      \
   template int push_smem_bytes<R>(int);                                                                             \
+  template void launch_sumv<R>(SpeciesDev, Ctl *, int, cudaStream_t);                                               \
   template size_t push_layout<R>(int, int &, int &);                                                                \
   template void launch_zero_q_batch<R>(const ColDev<R> *, int, int, int, cudaStream_t);                             \
   template void launch_push_batch<R>(const ColDev<R> *, const int4 *, int, int, size_t, cudaStream_t);              \

@@ -113,6 +113,18 @@ def test_ragged_sizes_and_frozen_ions(n_cells):
     assert_same(g.get_state(), o.get_state(), "ragged")
 
 
+@pytest.mark.parametrize("precision", [w.FP64, w.MIXED])
+def test_circuit_drive_matches(precision):
+    p = small(precision, drive=w.DRIVE_CIRCUIT, U_src=150.0, R_ext_ohm_m2=2.0, E0_Vpm=1000.0)
+    g, o = pb.Column(p), oracle.Oracle(p)
+    for n in (1, 10, 12):
+        g.step(n)
+        o.step(n)
+        sg, so = g.get_state(), o.get_state()
+        assert sg["E0"] == so["E0"] and sg["E0"] != 1000.0
+        assert_same(sg, so, "circuit")
+
+
 def test_uniform_field_swarm_mode():
     p = small(field_mode=w.FIELD_APPLIED, drive=w.DRIVE_E0, E0_Vpm=5e4, loss_mode=w.LOSS_SWARM,
               n_i0=0, ion_subcycle=0)
