@@ -283,6 +283,34 @@ int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, doub
 int pic_field_periodic_noalloc(const int64_t *Q_i, const int64_t *Q_e, int n_cells, double C, double E0, double *E,
                                double *E_half, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned closure network (the extension that closes the paper's three-moment
+ * quasi-neutral fluid model, Sec. IV.A): an MLP 15 -> 128 -> 128 -> 3 with
+ * GELU (tanh form) on the hidden layers, trained by mean-squared error with
+ * Adam (beta 0.9, 0.999, eps 1e-8).  BF16 operands on the tensor cores with
+ * FP32 accumulation; FP32 master weights; deterministic gradient sums.
+ * Inputs: 15 features per sample (5-point stencil of density, mean energy and
+ * field, normalised by the caller); outputs: 3 (electron flux, energy flux,
+ * ionization rate, normalised).  Parameter layout (FP32, flat, 18947 values):
+ * W1[128][15], b1[128], W2[128][128], b2[128], W3[3][128], b3[3]. */
+typedef struct pic_mlp pic_mlp;
+int pic_mlp_nparam(void);
+/* weights and biases uniform in +-1/sqrt(fan_in) from a seeded generator */
+int pic_mlp_create(uint64_t seed, pic_mlp **out);
+void pic_mlp_free(pic_mlp *m);
+/* host arrays of pic_mlp_nparam() floats; set resets the Adam state */
+int pic_mlp_set_params(pic_mlp *m, const float *host, int n);
+int pic_mlp_get_params(pic_mlp *m, float *host, int n);
+/* Y (device, n x 3) = network(X (device, n x 15)); synchronises the stream */
+int pic_mlp_forward(pic_mlp *m, const float *X, int n, float *Y, void *stream);
+/* gradient of the loss mean((Y - T)^2) over the n samples (host array of nparam, may be NULL)
+ * and the loss; X, T device arrays (n x 15, n x 3); no update */
+int pic_mlp_grad(pic_mlp *m, const float *X, const float *T, int n, float *grad_host, double *loss, void *stream);
+/* `steps` Adam steps on consecutive batches of `batch` samples cycling through the n samples;
+ * last_loss receives the loss of the last batch (before its update) */
+int pic_mlp_train(pic_mlp *m, const float *X, const float *T, int n, int batch, int steps, float lr,
+                  double *last_loss, void *stream);
+
 /* Self-test hook: int128 -> double conversion used by the field solve, run
  * on the device: v_k = hi[k] 2^64 + lo[k]; out[k] = double nearest to v_k
  * (ties to even).  Host arrays of n. */

@@ -19,11 +19,16 @@ import numpy as np
 HERE = Path(__file__).resolve().parent
 SRC = HERE / "pic_oracle.c"
 LIBS = {False: HERE / "liboracle_f64.so", True: HERE / "liboracle_f32.so"}
+MLP_SRC = HERE / "mlp_oracle.c"
+MLP_LIB = HERE / "libmlp_oracle.so"
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall"]
 
 
 def build(force: bool = False) -> None:
     """Compile both oracle builds with gcc (no CUDA)."""
+    if force or not MLP_LIB.exists() or MLP_LIB.stat().st_mtime < MLP_SRC.stat().st_mtime:
+        subprocess.run(["gcc", *CFLAGS, "-o", str(MLP_LIB) + ".tmp", str(MLP_SRC), "-lm"], check=True)
+        os.replace(str(MLP_LIB) + ".tmp", MLP_LIB)
     for f32, out in LIBS.items():
         if not force and out.exists() and out.stat().st_mtime > max(SRC.stat().st_mtime,
                                                                    (HERE / "pic_oracle.h").stat().st_mtime):
@@ -288,3 +293,43 @@ class Oracle:
         self.L.ora_moments_get(self.h, C.byref(m))
         d["n_samples"], d["n_steps"] = m.n_samples, m.n_steps
         return d
+
+
+_mlp = None
+
+
+def mlp_lib():
+    global _mlp
+    if _mlp is None:
+        if not MLP_LIB.exists():
+            build()
+        L = C.CDLL(str(MLP_LIB))
+        L.mlp_nparam.restype = C.c_int
+        L.mlp_forward_backward.argtypes = [_D, _D, _D, C.c_int, C.c_int, _D, _D]
+        L.mlp_forward_backward.restype = C.c_double
+        L.mlp_adam.argtypes = [_D, _D, _D, _D, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+        _mlp = L
+    return _mlp
+
+
+MLP_NPARAM = 128 * 15 + 128 + 128 * 128 + 128 + 3 * 128 + 3
+
+
+def mlp_forward_backward(P, X, T, bf16=False, want_grad=True):
+    """loss, outputs (n x 3), gradient (flat) of the oracle network."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    n = X.shape[0]
+    y = np.zeros((n, 3))
+    g = np.zeros(MLP_NPARAM) if want_grad else None
+    loss = mlp_lib().mlp_forward_backward(_ptr(P, _D), _ptr(X, _D), _ptr(T, _D), n, int(bf16), _ptr(y, _D),
+                                          _ptr(g, _D) if g is not None else None)
+    return loss, y, g
+
+
+def mlp_adam(P, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays."""
+    mlp_lib().mlp_adam(_ptr(P, _D), _ptr(np.ascontiguousarray(g, dtype=np.float64), _D), _ptr(m, _D),
+                       _ptr(v, _D), t, lr, b1, b2, eps)
+

@@ -116,6 +116,17 @@ def lib() -> C.CDLL:
         L.pic_batch_column.argtypes = [C.c_void_p, C.c_int]
         L.pic_batch_column.restype = C.c_void_p
         L.pic_batch_size.argtypes = [C.c_void_p]
+        L.pic_mlp_nparam.restype = C.c_int
+        L.pic_mlp_create.argtypes = [C.c_uint64, C.POINTER(C.c_void_p)]
+        L.pic_mlp_free.argtypes = [C.c_void_p]
+        L.pic_mlp_free.restype = None
+        L.pic_mlp_set_params.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
+        L.pic_mlp_get_params.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int]
+        L.pic_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+        L.pic_mlp_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_float), _D,
+                                   C.c_void_p]
+        L.pic_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_float,
+                                    _D, C.c_void_p]
         L.pic_set_timing.argtypes = [C.c_void_p, C.c_int]
         L.pic_kernel_times.argtypes = [C.c_void_p, _D, _I64]
         _lib = L
@@ -336,4 +347,51 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+class Mlp:
+    """The closure network on the GPU (pic_mlp_*); data as float32 device tensors."""
+
+    def __init__(self, seed: int = 7):
+        self.L = lib()
+        h = C.c_void_p()
+        _check(self.L.pic_mlp_create(seed, C.byref(h)))
+        self.h = h
+        self.nparam = self.L.pic_mlp_nparam()
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.L.pic_mlp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.nparam, np.float32)
+        _check(self.L.pic_mlp_get_params(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), self.nparam))
+        return out
+
+    def set_params(self, P) -> None:
+        P = np.ascontiguousarray(P, dtype=np.float32)
+        _check(self.L.pic_mlp_set_params(self.h, P.ctypes.data_as(C.POINTER(C.c_float)), len(P)))
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty((X.shape[0], 3), dtype=torch.float32, device=X.device)
+        _check(self.L.pic_mlp_forward(self.h, X.data_ptr(), X.shape[0], Y.data_ptr(), None))
+        return Y
+
+    def grad(self, X, T):
+        g = np.zeros(self.nparam, np.float32)
+        loss = C.c_double()
+        _check(self.L.pic_mlp_grad(self.h, X.data_ptr(), T.data_ptr(), X.shape[0],
+                                   g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss), None))
+        return loss.value, g
+
+    def train(self, X, T, batch: int = 8192, steps: int = 1, lr: float = 1e-3) -> float:
+        loss = C.c_double()
+        _check(self.L.pic_mlp_train(self.h, X.data_ptr(), T.data_ptr(), X.shape[0], batch, steps, lr,
+                                    C.byref(loss), None))
+        return loss.value
 
