@@ -311,6 +311,36 @@ int pic_mlp_grad(pic_mlp *m, const float *X, const float *T, int n, float *grad_
 int pic_mlp_train(pic_mlp *m, const float *X, const float *T, int n, int batch, int steps, float lr,
                   double *last_loss, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Electron transport of a uniform-field swarm from the two-term Boltzmann
+ * equation (steady state, homogeneous): the closure the paper tabulates for
+ * its fluid model (Sec. IV.A, eqs. 6-9, "solutions of the 0D Boltzmann
+ * equation").  Isotropic scattering for every process (momentum transfer =
+ * sum of all electron cross sections), elastic recoil loss 2m/M with the gas
+ * at rest, excitation loss u_k, ionization leaving the scattered electron a
+ * uniform share of eps - u_iz and no new electron (population held fixed, as
+ * in the particle model's swarm mode).  Host code, FP64.
+ * All rates are per gas density N (multiply by N, or divide for mobility and
+ * diffusion, to get SI values at a given pressure). */
+typedef struct pic_transport {
+  double EN_Td;       /* reduced field, Td (1e-21 V m^2) */
+  double mean_eps_eV; /* mean energy; Te = 2/3 of it */
+  double muN;         /* mobility x N, 1/(V m s) */
+  double DN;          /* diffusion x N, 1/(m s) */
+  double mueN;        /* energy mobility x N */
+  double DeN;         /* energy diffusion x N */
+  double nu_izN;      /* ionization frequency / N, m^3/s */
+  double lossN;       /* energy loss frequency / N (elastic + sum of thresholds x rates), eV m^3/s */
+  double powerN;      /* power gained from the field / N = muN (E/N)^2, eV m^3/s */
+  double alphaN;      /* ionization coefficient / N = nu_izN / drift, m^2 */
+} pic_transport;
+/* xs: the cross sections of pic_params (ion processes are ignored); EN_Td: n_EN
+ * reduced fields (> 0); eps_max_eV: top of the energy grid (F must be
+ * negligible there); n_grid: energy cells (64 .. 8192).  out: n_EN records.
+ * Errors: PIC_EINVAL (bad argument), PIC_ENOMEM. */
+int pic_two_term(const pic_xsec *xs, int n_xsec, double gas_mass_amu, const double *EN_Td, int n_EN,
+                 double eps_max_eV, int n_grid, pic_transport *out);
+
 /* Self-test hook: int128 -> double conversion used by the field solve, run
  * on the device: v_k = hi[k] 2^64 + lo[k]; out[k] = double nearest to v_k
  * (ties to even).  Host arrays of n. */

@@ -127,6 +127,8 @@ def lib() -> C.CDLL:
                                    C.c_void_p]
         L.pic_mlp_train.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_float,
                                     _D, C.c_void_p]
+        L.pic_two_term.argtypes = [C.POINTER(Xsec), C.c_int, C.c_double, _D, C.c_int, C.c_double, C.c_int,
+                                   C.POINTER(Transport)]
         L.pic_set_timing.argtypes = [C.c_void_p, C.c_int]
         L.pic_kernel_times.argtypes = [C.c_void_p, _D, _I64]
         _lib = L
@@ -143,17 +145,36 @@ def _check(rc: int, h=None) -> None:
         raise PicError(rc, msg.decode() if msg else "")
 
 
-def make_params(p):
-    """Marshal a workloads.Params into pic_params; returns (struct, keepalive)."""
+class Transport(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("EN_Td", "mean_eps_eV", "muN", "DN", "mueN", "DeN", "nu_izN", "lossN",
+                                           "powerN", "alphaN")]
+
+
+def _xsec_array(xsec):
     keep = []
-    xs = (Xsec * max(1, len(p.xsec)))()
-    for k, x in enumerate(p.xsec):
+    xs = (Xsec * max(1, len(xsec)))()
+    for k, x in enumerate(xsec):
         e = np.ascontiguousarray(x.energy_eV, dtype=np.float64)
         s = np.ascontiguousarray(x.sigma_m2, dtype=np.float64)
         keep += [e, s]
         xs[k].kind, xs[k].n, xs[k].threshold_eV = x.kind, len(e), x.threshold_eV
         xs[k].energy_eV, xs[k].sigma_m2 = _ptr(e, _D), _ptr(s, _D)
     keep.append(xs)
+    return xs, keep
+
+
+def two_term(xsec, gas_mass_amu: float, EN_Td, eps_max_eV: float = 100.0, n_grid: int = 1000) -> list:
+    """pic_two_term: two-term Boltzmann transport at each reduced field (list of dicts)."""
+    xs, keep = _xsec_array(xsec)
+    en = np.ascontiguousarray(np.atleast_1d(EN_Td), dtype=np.float64)
+    out = (Transport * len(en))()
+    _check(lib().pic_two_term(xs, len(xsec), gas_mass_amu, _ptr(en, _D), len(en), eps_max_eV, n_grid, out))
+    return [{n: getattr(o, n) for n, _ in Transport._fields_} for o in out]
+
+
+def make_params(p):
+    """Marshal a workloads.Params into pic_params; returns (struct, keepalive)."""
+    xs, keep = _xsec_array(p.xsec)
     st = Params()
     for name, _ in Params._fields_:
         if name in ("xsec", "n_xsec") or name.startswith("pad"):
