@@ -341,6 +341,73 @@ typedef struct pic_transport {
 int pic_two_term(const pic_xsec *xs, int n_xsec, double gas_mass_amu, const double *EN_Td, int n_EN,
                  double eps_max_eV, int n_grid, pic_transport *out);
 
+/* ------------------------------------------------------------------------
+ * Quasi-neutral three-moment fluid model of the column (Sec. IV.A, eqs. 3-5,
+ * 8-9, 11, 17) for many independent periodic columns at once: the fast screen
+ * of discharge conditions.  State per cell: electron density n (= ion
+ * density) and temperature Te, FP32 on the device.  Closure: mu_e, D_e,
+ * mu_eps, D_eps, nu_i and L_eps as functions of Te from transport records
+ * (pic_two_term), optionally corrected per cell by the closure network.
+ *
+ * One step (dt, faces j+1/2 between cells j and j+1, face values averages of
+ * the two cells, coefficients at the step's starting Te):
+ *  1. continuity, backward Euler in the ambipolar diffusion:
+ *       n'_j - dt/dx^2 [a_{j+1/2}((nD_e)'_{j+1} - (nD_e)'_j) - a_{j-1/2}((nD_e)'_j - (nD_e)'_{j-1})]
+ *         = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i + dnu - nu_w) - dt/dx (dG_{j+1/2} - dG_{j-1/2}),
+ *     a = mu_i/(mu_e + mu_i), b = 1 - a (eq. 11);
+ *  2. Gamma_{j+1/2} (eq. 11, plus dG) and E_{j+1/2} (eq. 17) from n';
+ *  3. energy, backward Euler in Te' for conduction, energy drift and the
+ *     linearised loss, with H = -3/2 mu_eps E n Te - d_x(3/2 n D_eps Te) + dH
+ *     (eqs. 8-9 with beta = 3/2 Te mu_eps, G = 3/2 Te D_eps) and the heating
+ *     P_j = -(Gamma E)_{j+1/2, j-1/2} averaged (eq. 5);
+ *  4. Te' clamped to the table's range.
+ * dG, dH, dnu: closure corrections (flux per electron, energy flux per
+ * electron, ionization frequency) at cells, put on faces as
+ * (n_j d_j + n_{j+1} d_{j+1})/2 with the step's starting n.
+ * Each tridiagonal system is cyclic and is solved by parallel cyclic
+ * reduction in shared memory (one thread block per column). */
+typedef struct pic_fluid_column {
+  double L_m;      /* column length */
+  double N_gas_m3; /* gas density */
+  double mu_iN;    /* ion mobility x N, 1/(V m s) */
+  double Gamma_T;  /* total particle flux J/e (ions minus electrons), 1/(m^2 s); > 0 gives E along +x */
+  double nu_w;     /* wall-loss frequency (eq. 2), 1/s */
+  int32_t n_cells; /* a power of two, 64 .. 4096 */
+  int32_t pad;
+} pic_fluid_column;
+typedef struct pic_fluid pic_fluid;
+/* tr: n_tr >= 2 transport records in increasing Te = 2/3 mean energy, resampled
+ * (linear in Te) onto n_T (2 .. 256) uniform Te points; dt_s > 0; the spectral
+ * record c_m = (1/N) sum_j n_j exp(-2 pi i m j/N), m = 1..n_modes (0 .. 64),
+ * and the mean density are taken after every diag_every-th step (0: never).
+ * Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
+int pic_fluid_init(const pic_fluid_column *cols, int n_cols, const pic_transport *tr, int n_tr, int n_T,
+                   double dt_s, int diag_every, int n_modes, pic_fluid **out);
+/* host arrays of the column's n_cells values (FP64 in, stored as FP32) */
+int pic_fluid_set_state(pic_fluid *f, int col, const double *n_m3, const double *Te_eV);
+int pic_fluid_get_state(pic_fluid *f, int col, double *n_m3, double *Te_eV);
+/* advance every column by n_steps; synchronises the handle's stream */
+int pic_fluid_step(pic_fluid *f, int64_t n_steps);
+/* copy out and clear the spectral record: out holds max_snaps x n_cols x
+ * (n_modes + 1) complex values (re, im as floats), entry 0 of each = (mean n, 0);
+ * *n_snaps receives the number written (PIC_ECAPACITY if more were recorded) */
+int pic_fluid_modes(pic_fluid *f, float *out, int max_snaps, int *n_snaps);
+/* attach (net != NULL) or detach the closure network: every `period` steps the
+ * features of every cell (15: 5-point stencils of n/<n>, 3/2 Te in eV and
+ * E/N in Td with E at cells the mean of its faces; each divided by
+ * feat_scale[k]) go through the network, whose 3 outputs times targ_scale
+ * become dG, dH, dnu for the next `period` steps.  The network is not owned. */
+int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *feat_scale, const float *targ_scale);
+/* fixed corrections (device array, total cells x 3, already scaled to SI; NULL clears) */
+int pic_fluid_set_corrections(pic_fluid *f, const float *corr_dev);
+/* features of the current state (device array, total cells x 15, divided by feat_scale of
+ * the attached closure, or unscaled without one); cells are numbered column after column */
+int pic_fluid_features(pic_fluid *f, float *X_dev);
+/* device time of the last pic_fluid_step and the kernels it launched */
+int pic_fluid_elapsed(pic_fluid *f, double *ms, int64_t *launches);
+void *pic_fluid_stream(pic_fluid *f);
+void pic_fluid_free(pic_fluid *f);
+
 /* Self-test hook: int128 -> double conversion used by the field solve, run
  * on the device: v_k = hi[k] 2^64 + lo[k]; out[k] = double nearest to v_k
  * (ties to even).  Host arrays of n. */

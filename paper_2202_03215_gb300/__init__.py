@@ -129,6 +129,21 @@ def lib() -> C.CDLL:
                                     _D, C.c_void_p]
         L.pic_two_term.argtypes = [C.POINTER(Xsec), C.c_int, C.c_double, _D, C.c_int, C.c_double, C.c_int,
                                    C.POINTER(Transport)]
+        L.pic_fluid_init.argtypes = [C.POINTER(FluidColumn), C.c_int, C.POINTER(Transport), C.c_int, C.c_int,
+                                     C.c_double, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+        L.pic_fluid_set_state.argtypes = [C.c_void_p, C.c_int, _D, _D]
+        L.pic_fluid_get_state.argtypes = [C.c_void_p, C.c_int, _D, _D]
+        L.pic_fluid_step.argtypes = [C.c_void_p, C.c_int64]
+        L.pic_fluid_modes.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
+        L.pic_fluid_set_closure.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_float),
+                                            C.POINTER(C.c_float)]
+        L.pic_fluid_set_corrections.argtypes = [C.c_void_p, C.c_void_p]
+        L.pic_fluid_features.argtypes = [C.c_void_p, C.c_void_p]
+        L.pic_fluid_elapsed.argtypes = [C.c_void_p, _D, _I64]
+        L.pic_fluid_stream.argtypes = [C.c_void_p]
+        L.pic_fluid_stream.restype = C.c_void_p
+        L.pic_fluid_free.argtypes = [C.c_void_p]
+        L.pic_fluid_free.restype = None
         L.pic_set_timing.argtypes = [C.c_void_p, C.c_int]
         L.pic_kernel_times.argtypes = [C.c_void_p, _D, _I64]
         _lib = L
@@ -148,6 +163,11 @@ def _check(rc: int, h=None) -> None:
 class Transport(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("EN_Td", "mean_eps_eV", "muN", "DN", "mueN", "DeN", "nu_izN", "lossN",
                                            "powerN", "alphaN")]
+
+
+class FluidColumn(C.Structure):
+    _fields_ = [("L_m", C.c_double), ("N_gas_m3", C.c_double), ("mu_iN", C.c_double), ("Gamma_T", C.c_double),
+                ("nu_w", C.c_double), ("n_cells", C.c_int32), ("pad", C.c_int32)]
 
 
 def _xsec_array(xsec):
@@ -416,3 +436,87 @@ class Mlp:
                                     C.byref(loss), None))
         return loss.value
 
+
+
+class Fluid:
+    """Many periodic columns of the quasi-neutral fluid model (pic_fluid_*).
+
+    columns: dicts with L_m, N_gas_m3, mu_iN, Gamma_T, nu_w, n_cells;
+    transport: records of two_term() in increasing Te."""
+
+    def __init__(self, columns, transport, n_T: int = 128, dt_s: float = 2e-8, diag_every: int = 0,
+                 n_modes: int = 0):
+        self.L = lib()
+        self.columns = [dict(c) for c in columns]
+        cols = (FluidColumn * len(columns))()
+        for k, c in enumerate(columns):
+            for name in ("L_m", "N_gas_m3", "mu_iN", "Gamma_T", "nu_w", "n_cells"):
+                setattr(cols[k], name, c[name])
+        tr = (Transport * len(transport))()
+        for k, r in enumerate(transport):
+            for name, _ in Transport._fields_:
+                setattr(tr[k], name, r[name])
+        h = C.c_void_p()
+        _check(self.L.pic_fluid_init(cols, len(columns), tr, len(transport), n_T, dt_s, diag_every, n_modes,
+                                     C.byref(h)))
+        self.h = h
+        self.n_modes = n_modes
+        self.offsets = np.cumsum([0] + [c["n_cells"] for c in columns])
+        self._net = None
+        self._corr = None
+
+    def set_state(self, col: int, n, T) -> None:
+        n = np.ascontiguousarray(n, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        _check(self.L.pic_fluid_set_state(self.h, col, _ptr(n, _D), _ptr(T, _D)))
+
+    def get_state(self, col: int):
+        N = self.columns[col]["n_cells"]
+        n, T = np.zeros(N), np.zeros(N)
+        _check(self.L.pic_fluid_get_state(self.h, col, _ptr(n, _D), _ptr(T, _D)))
+        return n, T
+
+    def step(self, n: int = 1) -> None:
+        _check(self.L.pic_fluid_step(self.h, n))
+
+    def modes(self, max_snaps: int = 100000) -> np.ndarray:
+        """Spectral record since the last call: complex array [snap, column, n_modes + 1]
+        (entry 0 = mean density)."""
+        out = np.zeros((max_snaps, len(self.columns), self.n_modes + 1, 2), dtype=np.float32)
+        k = C.c_int()
+        _check(self.L.pic_fluid_modes(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), max_snaps, C.byref(k)))
+        o = out[:k.value].astype(np.float64)
+        return o[..., 0] + 1j * o[..., 1]
+
+    def set_closure(self, net, period: int, feat_scale, targ_scale) -> None:
+        fs = np.ascontiguousarray(feat_scale, dtype=np.float32)
+        ts = np.ascontiguousarray(targ_scale, dtype=np.float32)
+        _check(self.L.pic_fluid_set_closure(self.h, net.h if net is not None else None, period,
+                                            fs.ctypes.data_as(C.POINTER(C.c_float)),
+                                            ts.ctypes.data_as(C.POINTER(C.c_float))))
+        self._net = net
+
+    def set_corrections(self, corr) -> None:
+        """corr: device float32 tensor (total cells x 3) in SI units, or None."""
+        self._corr = corr
+        _check(self.L.pic_fluid_set_corrections(self.h, None if corr is None else corr.data_ptr()))
+
+    def features(self):
+        import torch
+        X = torch.empty((int(self.offsets[-1]), 15), dtype=torch.float32, device="cuda")
+        _check(self.L.pic_fluid_features(self.h, X.data_ptr()))
+        return X
+
+    def elapsed(self):
+        ms = np.zeros(1)
+        k = np.zeros(1, dtype=np.int64)
+        _check(self.L.pic_fluid_elapsed(self.h, _ptr(ms, _D), _ptr(k, _I64)))
+        return float(ms[0]), int(k[0])
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.L.pic_fluid_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -24,7 +24,7 @@ BUILD = HERE / "_build"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-prec-div=true", "-prec-sqrt=true",
          "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math", f"-I{INCLUDE}", f"-I{CSRC}"]
-SOURCES = ["pic_kernels.cu", "pic_host.cu", "pic_sort.cu", "pic_mlp.cu", "pic_noalloc.cu", "pic_transport.cu"]
+SOURCES = ["pic_kernels.cu", "pic_host.cu", "pic_sort.cu", "pic_mlp.cu", "pic_noalloc.cu", "pic_transport.cu", "pic_fluid.cu"]
 
 
 def nvcc() -> str:

@@ -346,8 +346,10 @@ int ensure(pic_mlp *h, int n) {
 
 int run_tiles(pic_mlp *h, const float *X, const float *T, int n, float *Y, int mode, cudaStream_t st) {
   if (n <= 0) return PIC_EINVAL;
-  int rc = ensure(h, n);
-  if (rc) return rc;
+  if (mode == 0) {   // per-tile partial gradients only when training
+    const int rc = ensure(h, n);
+    if (rc) return rc;
+  }
   const int tiles = (n + S - 1) / S;
   const float inv_n3 = 1.0f / (3.0f * (float)n);
   cudaFuncSetAttribute(k_mlp_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
@@ -365,6 +367,12 @@ uint64_t splitmix(uint64_t &x) {
 }
 
 }  // namespace
+
+// forward pass enqueued on st without synchronising (used by the fluid closure)
+int mlp_forward_async(pic_mlp *h, const float *X, int n, float *Y, cudaStream_t st) {
+  if (!h || !X || !Y) return PIC_EINVAL;
+  return run_tiles(h, X, X, n, Y, 1, st);
+}
 
 extern "C" {
 
