@@ -351,9 +351,10 @@ int pic_two_term(const pic_xsec *xs, int n_xsec, double gas_mass_amu, const doub
  *
  * One step (dt, faces j+1/2 between cells j and j+1, face values averages of
  * the two cells, coefficients at the step's starting Te):
- *  1. continuity, backward Euler in the ambipolar diffusion:
- *       n'_j - dt/dx^2 [a_{j+1/2}((nD_e)'_{j+1} - (nD_e)'_j) - a_{j-1/2}((nD_e)'_j - (nD_e)'_{j-1})]
- *         = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i + dnu - nu_w) - dt/dx (dG_{j+1/2} - dG_{j-1/2}),
+ *  0. nu_i + dnu at every cell; nu_w fixed, or <n (nu_i + dnu)>/<n> with pair losses;
+ *  1. continuity, backward Euler in the ambipolar diffusion and the losses:
+ *       n'_j (1 + dt nu_w) - dt/dx^2 [a_{j+1/2}((nD_e)'_{j+1} - (nD_e)'_j) - a_{j-1/2}((nD_e)'_j - (nD_e)'_{j-1})]
+ *         = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i + dnu) - dt/dx (dG_{j+1/2} - dG_{j-1/2}),
  *     a = mu_i/(mu_e + mu_i), b = 1 - a (eq. 11);
  *  2. Gamma_{j+1/2} (eq. 11, plus dG) and E_{j+1/2} (eq. 17) from n';
  *  3. energy, backward Euler in Te' for conduction, energy drift and the
@@ -371,10 +372,14 @@ typedef struct pic_fluid_column {
   double N_gas_m3; /* gas density */
   double mu_iN;    /* ion mobility x N, 1/(V m s) */
   double Gamma_T;  /* total particle flux J/e (ions minus electrons), 1/(m^2 s); > 0 gives E along +x */
-  double nu_w;     /* wall-loss frequency (eq. 2), 1/s */
+  double nu_w;     /* wall-loss frequency (eq. 2), 1/s; unused with PIC_FLUID_LOSS_PAIR */
   int32_t n_cells; /* a power of two, 64 .. 4096 */
-  int32_t pad;
+  int32_t loss;    /* PIC_FLUID_LOSS_FIXED: nu_w as given; PIC_FLUID_LOSS_PAIR: nu_w = <n nu_i>/<n>
+                      each step (the continuum form of the particle model's pair losses: as many
+                      electrons leave as are created, uniformly per electron) */
 } pic_fluid_column;
+#define PIC_FLUID_LOSS_FIXED 0
+#define PIC_FLUID_LOSS_PAIR 1
 typedef struct pic_fluid pic_fluid;
 /* tr: n_tr >= 2 transport records in increasing Te = 2/3 mean energy, resampled
  * (linear in Te) onto n_T (2 .. 256) uniform Te points; dt_s > 0; the spectral
@@ -396,8 +401,12 @@ int pic_fluid_modes(pic_fluid *f, float *out, int max_snaps, int *n_snaps);
  * features of every cell (15: 5-point stencils of n/<n>, 3/2 Te in eV and
  * E/N in Td with E at cells the mean of its faces; each divided by
  * feat_scale[k]) go through the network, whose 3 outputs times targ_scale
- * become dG, dH, dnu for the next `period` steps.  The network is not owned. */
-int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *feat_scale, const float *targ_scale);
+ * become dG, dH, dnu for the next `period` steps (a zero scale switches a
+ * correction off).  nu_bound > 0 limits the learned ionization correction to
+ * |dnu| <= nu_bound nu_i(Te) of the cell (a trust region for states unlike
+ * the training data); <= 0: unbounded.  The network is not owned. */
+int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *feat_scale, const float *targ_scale,
+                          float nu_bound);
 /* fixed corrections (device array, total cells x 3, already scaled to SI; NULL clears) */
 int pic_fluid_set_corrections(pic_fluid *f, const float *corr_dev);
 /* features of the current state (device array, total cells x 15, divided by feat_scale of

@@ -20,9 +20,10 @@ Gamma_T = J/e is the constant total particle flux.
 Discretisation (periodic, N cells, dx = L/N, faces j+1/2 between j and j+1;
 face values of a, b, mu_eps, mu_e + mu_i and n are averages of the two
 cells; coefficients from the table at the step's starting T):
- 1. continuity, backward Euler in the diffusion, explicit in the rest:
-      n'_j - dt/dx^2 [a_{j+1/2} ((nD)'_{j+1} - (nD)'_j) - a_{j-1/2} ((nD)'_j - (nD)'_{j-1})]
-        = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i,j + dnu_j - nu_w)
+ 1. continuity, backward Euler in the diffusion and the losses, explicit in the
+    rest (ionization explicit, losses implicit: n' stays positive):
+      n'_j (1 + dt nu_w) - dt/dx^2 [a_{j+1/2} ((nD)'_{j+1} - (nD)'_j) - a_{j-1/2} ((nD)'_j - (nD)'_{j-1})]
+        = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i,j + dnu_j)
           - dt/dx (dG_{j+1/2} - dG_{j-1/2})
     a = mu_i/(mu_e + mu_i), b = mu_e/(mu_e + mu_i) at cells, D = D_e;
  2. Gamma_{j+1/2} from n' (eq. 11) plus dG_{j+1/2}; E_{j+1/2} from n' (eq. 17);
@@ -37,6 +38,8 @@ cells; coefficients from the table at the step's starting T):
 dG, dH, dnu are optional closure corrections per cell (flux per electron,
 energy flux per electron, ionization frequency), put on faces as
 (n_j d_j + n_{j+1} d_{j+1}) / 2 with the step's starting n.
+With pair losses (col["pair"] true) nu_w = sum(n (nu_i + dnu)) / sum(n) at the
+step's start: the continuum form of the particle model's pair losses.
 Table lookup: x = (T - T0)/dT clamped to [0, nT - 1], i = min(floor x, nT - 2),
 q = q_i + (x - i)(q_{i+1} - q_i), L' = (L_{i+1} - L_i)/dT.
 """
@@ -123,16 +126,18 @@ def step(col, tab, n, T, dt, corr=None):
         dG = face(n * corr[0])
         dH = face(n * corr[1])
         nu_i = nu_i + corr[2]
+    if col.get("pair"):      # as many electrons leave as are created, uniformly per electron
+        nu_w = np.sum(n * nu_i) / np.sum(n)
     # 1. continuity
     r = dt / dx ** 2
     af = face(c["a"])            # a_{j+1/2}
     am = np.roll(af, 1)          # a_{j-1/2}
     D = c["D_e"]
     lo = -r * am * np.roll(D, 1)
-    dg = 1.0 + r * (af + am) * D
+    dg = 1.0 + r * (af + am) * D + dt * nu_w
     up = -r * af * np.roll(D, -1)
     bf = face(c["b"])
-    rhs = n + dt / dx * (bf - np.roll(bf, 1)) * GT + dt * n * (nu_i - nu_w)
+    rhs = n + dt / dx * (bf - np.roll(bf, 1)) * GT + dt * n * nu_i
     if dG is not None:
         rhs = rhs - dt / dx * (dG - np.roll(dG, 1))
     n1 = cyclic_solve(lo, dg, up, rhs)

@@ -136,7 +136,7 @@ def lib() -> C.CDLL:
         L.pic_fluid_step.argtypes = [C.c_void_p, C.c_int64]
         L.pic_fluid_modes.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
         L.pic_fluid_set_closure.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_float),
-                                            C.POINTER(C.c_float)]
+                                            C.POINTER(C.c_float), C.c_float]
         L.pic_fluid_set_corrections.argtypes = [C.c_void_p, C.c_void_p]
         L.pic_fluid_features.argtypes = [C.c_void_p, C.c_void_p]
         L.pic_fluid_elapsed.argtypes = [C.c_void_p, _D, _I64]
@@ -165,9 +165,12 @@ class Transport(C.Structure):
                                            "powerN", "alphaN")]
 
 
+FLUID_LOSS_FIXED, FLUID_LOSS_PAIR = 0, 1
+
+
 class FluidColumn(C.Structure):
     _fields_ = [("L_m", C.c_double), ("N_gas_m3", C.c_double), ("mu_iN", C.c_double), ("Gamma_T", C.c_double),
-                ("nu_w", C.c_double), ("n_cells", C.c_int32), ("pad", C.c_int32)]
+                ("nu_w", C.c_double), ("n_cells", C.c_int32), ("loss", C.c_int32)]
 
 
 def _xsec_array(xsec):
@@ -441,7 +444,8 @@ class Mlp:
 class Fluid:
     """Many periodic columns of the quasi-neutral fluid model (pic_fluid_*).
 
-    columns: dicts with L_m, N_gas_m3, mu_iN, Gamma_T, nu_w, n_cells;
+    columns: dicts with L_m, N_gas_m3, mu_iN, Gamma_T, nu_w, n_cells and optionally
+    loss (FLUID_LOSS_FIXED or FLUID_LOSS_PAIR);
     transport: records of two_term() in increasing Te."""
 
     def __init__(self, columns, transport, n_T: int = 128, dt_s: float = 2e-8, diag_every: int = 0,
@@ -452,6 +456,7 @@ class Fluid:
         for k, c in enumerate(columns):
             for name in ("L_m", "N_gas_m3", "mu_iN", "Gamma_T", "nu_w", "n_cells"):
                 setattr(cols[k], name, c[name])
+            cols[k].loss = c.get("loss", FLUID_LOSS_FIXED)
         tr = (Transport * len(transport))()
         for k, r in enumerate(transport):
             for name, _ in Transport._fields_:
@@ -488,12 +493,12 @@ class Fluid:
         o = out[:k.value].astype(np.float64)
         return o[..., 0] + 1j * o[..., 1]
 
-    def set_closure(self, net, period: int, feat_scale, targ_scale) -> None:
+    def set_closure(self, net, period: int, feat_scale, targ_scale, nu_bound: float = 0.0) -> None:
         fs = np.ascontiguousarray(feat_scale, dtype=np.float32)
         ts = np.ascontiguousarray(targ_scale, dtype=np.float32)
         _check(self.L.pic_fluid_set_closure(self.h, net.h if net is not None else None, period,
                                             fs.ctypes.data_as(C.POINTER(C.c_float)),
-                                            ts.ctypes.data_as(C.POINTER(C.c_float))))
+                                            ts.ctypes.data_as(C.POINTER(C.c_float)), nu_bound))
         self._net = net
 
     def set_corrections(self, corr) -> None:

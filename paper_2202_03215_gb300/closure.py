@@ -140,3 +140,67 @@ def swarm_samples(ps: Sequence[w.Params], mom) -> tuple[np.ndarray, np.ndarray]:
 
 def normalise(X: np.ndarray, T: np.ndarray):
     return X / FEATURE_SCALE, T / TARGET_SCALE
+
+
+# ---------------------------------------------------------------------------
+# Residual targets for the fluid screen: the network learns what the particle
+# model's moments add to the tabulated closure of the fluid model, in the
+# fluid model's frame (applied field along +x; the particle model's points
+# along -x, so its windows are mirrored first).
+
+def mirror(m: dict) -> dict:
+    """x -> -x of a periodic moment window: node j -> node (-j) mod N; fluxes and the
+    field change sign."""
+    out = {}
+    for k, v in m.items():
+        if not isinstance(v, np.ndarray):
+            out[k] = v
+            continue
+        r = np.roll(v[::-1], 1)
+        out[k] = -r if k in ("gamma_e", "heat_e", "gamma_i", "E") else r
+    return out
+
+
+def _face(v):
+    return 0.5 * (v + np.roll(v, -1))
+
+
+def table_closure(n, T, Gamma_T, L_m, N_gas, mu_iN, tab):
+    """The fluid model's tabulated closure evaluated on a given state (the same
+    formulas as the fluid step): electron flux (eq. 11), field (eq. 17) and energy
+    flux (eqs. 8-9) at cells as averages of their faces, and nu_i(T)."""
+    dx = L_m / len(n)
+    mu_e = tab.at("muN", T) / N_gas
+    D_e = tab.at("DN", T) / N_gas
+    mu_eps = tab.at("mueN", T) / N_gas
+    D_eps = tab.at("DeN", T) / N_gas
+    mu_i = mu_iN / N_gas
+    a = mu_i / (mu_e + mu_i)
+    af = _face(a)
+    nD = n * D_e
+    G = -af * (np.roll(nD, -1) - nD) / dx - (1.0 - af) * Gamma_T
+    nDm = n * D_e / mu_e
+    nf = _face(n)
+    E = -(np.roll(nDm, -1) - nDm) / (dx * nf) + Gamma_T / (nf * _face(mu_e + mu_i))
+    nT = n * T
+    H = -0.75 * _face(mu_eps) * E * (nT + np.roll(nT, -1)) - 1.5 * (np.roll(n * D_eps * T, -1) - n * D_eps * T) / dx
+    cell = lambda f: 0.5 * (f + np.roll(f, 1))
+    return cell(G), cell(H), tab.at("nu_izN", T) * N_gas, cell(E)
+
+
+def residual_samples(m: dict, p: w.Params, tab, mu_iN: float, T_range=None):
+    """(features, residual targets) of every cell of one particle-model window, in the
+    fluid frame: features as the fluid screen computes them (n/<n>, mean energy, E/N
+    from eq. 17), targets = (Gamma_e - Gamma_tab)/n, (H_e - H_tab)/n, nu_iz - nu_tab."""
+    f = mirror(m)
+    N_gas = n_gas(p)
+    n = np.maximum(f["n_e"], 1e-30 + 1e-6 * f["n_e"].mean())
+    T = 2.0 / 3.0 * f["mean_eps_e"]
+    if T_range is not None:
+        T = np.clip(T, *T_range)
+    Gamma_T = float(np.mean(f["gamma_i"] - f["gamma_e"]))
+    G, H, nu, E = table_closure(n, T, Gamma_T, p.L_m, N_gas, mu_iN, tab)
+    j = np.arange(len(n))
+    X = np.concatenate([_stencil(n / n.mean(), j), _stencil(1.5 * T, j), _stencil(E / (N_gas * TD), j)], 1)
+    Y = np.stack([(f["gamma_e"] - G) / n, (f["heat_e"] - H) / n, f["iz_rate"] / n - nu], 1)
+    return X.astype(np.float32), Y.astype(np.float32)

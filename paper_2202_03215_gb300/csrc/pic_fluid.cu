@@ -34,6 +34,7 @@ struct ColK {
   long long off;       // first cell in the state arrays
   float dx, r, s, k;   // dx, dt/dx^2, dt/dx, 3/(2 dx)
   float GT, nu_w, mu_i, Ng, invNg;
+  int pair;            // nu_w = <n nu>/<n> every step
 };
 
 struct FluidK {
@@ -50,6 +51,7 @@ struct FluidK {
   const float *corr;            // cells x 3 (scaled) or null
   const float *netY;            // cells x 3 (network outputs) or null
   float cs0, cs1, cs2;          // network output scales
+  float nu_bound;               // |dnu| <= nu_bound nu_i (network corrections; <= 0: unbounded)
   float *feat;                  // cells x 15 or null: written after the last step
   float fs[15];                 // feature scales (divisors)
 };
@@ -132,18 +134,34 @@ __device__ void field(const Sm &S, const ColK &c) {
   }
 }
 
+__device__ float block_sum(float v, float *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.0f;
+  for (int k = 0; k < kThreads / 32; ++k) s += red[k];
+  return s;
+}
+
 // One step.  Both implicit systems are solved for the increment (n' = n + dn,
 // T' = T + dT) with the residual of the starting state on the right-hand side,
 // formed from flux differences: FP32 then rounds relative to the per-step
 // change rather than to the state, which matters where the conduction term
 // dt D_eps/dx^2 is in the thousands.
-__device__ void step(const Sm &S, const FluidK &K, const ColK &c) {
+__device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
   const int N = c.N, t = threadIdx.x;
   const bool has_corr = K.netY || K.corr;
-  // 1. coefficients at the starting T; starting n kept in u; correction fluxes on faces (starting n)
+  // 1. coefficients at the starting T; starting n kept in u; correction fluxes on faces (starting n);
+  //    ionization frequency per cell in E (free until the field is formed)
   coeffs(S, K, c);
+  float sn = 0.0f, snu = 0.0f;
   for (int j = t; j < N; j += kThreads) {
     S.u[j] = S.n[j];
+    int i; float f;
+    tpos(K, S.T[j], i, f);
+    float nu = tq(S, K, 4, i, f) * c.Ng;
     if (has_corr) {
       const int jp = (j + 1) & (N - 1);
       float g0, h0, n0, g1, h1, n1;
@@ -151,31 +169,36 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c) {
       corr_at(K, c.off + jp, g1, h1, n1);
       S.G[j] = 0.5f * (S.n[j] * g0 + S.n[jp] * g1);
       S.H[j] = 0.5f * (S.n[j] * h0 + S.n[jp] * h1);
+      if (K.netY && K.nu_bound > 0.0f) n0 = fminf(fmaxf(n0, -K.nu_bound * nu), K.nu_bound * nu);
+      nu += n0;
     }
+    S.E[j] = nu;
+    sn += S.n[j];
+    snu += S.n[j] * nu;
+  }
+  float nu_w = c.nu_w;
+  if (c.pair) {
+    const float a = block_sum(sn, red), b = block_sum(snu, red);
+    nu_w = b / a;
   }
   __syncthreads();
   // 2. continuity: A dn = rhs - A n
   for (int j = t; j < N; j += kThreads) {
     const int jm = (j - 1) & (N - 1), jp = (j + 1) & (N - 1);
     const float af = 0.5f * (S.A[j] + S.A[jp]), am = 0.5f * (S.A[jm] + S.A[j]);
-    int i; float f;
-    tpos(K, S.T[j], i, f);
-    float nu = tq(S, K, 4, i, f) * c.Ng;
+    const float nu = S.E[j];
     float dGf = 0.0f, dGm = 0.0f;
     if (has_corr) {
-      float cg, ch, cn;
-      corr_at(K, c.off + j, cg, ch, cn);
-      nu += cn;
       dGf = S.G[j];
       dGm = S.G[jm];
     }
     const float Dn = S.D[j] * S.n[j];
     S.pa[j] = -c.r * am * S.D[jm];
-    S.pb[j] = 1.0f + c.r * (af + am) * S.D[j];
+    S.pb[j] = 1.0f + c.r * (af + am) * S.D[j] + K.dt * nu_w;    // losses implicit: n' stays positive
     S.pc[j] = -c.r * af * S.D[jp];
     // b_{j+1/2} - b_{j-1/2} = -(a_{j+1/2} - a_{j-1/2}): taken from a, which is small, to keep its digits
     S.pd[j] = c.r * (af * (S.D[jp] * S.n[jp] - Dn) - am * (Dn - S.D[jm] * S.n[jm])) -
-              c.s * (af - am) * c.GT + K.dt * S.n[j] * (nu - c.nu_w) - c.s * (dGf - dGm);
+              c.s * (af - am) * c.GT + K.dt * S.n[j] * (nu - nu_w) - c.s * (dGf - dGm);
   }
   __syncthreads();
   pcr(S, N);
@@ -243,17 +266,6 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c) {
     S.T[j] = fminf(fmaxf(T1, K.T0), K.Tmax);
   }
   __syncthreads();
-}
-
-__device__ float block_sum(float v, float *red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  float s = 0.0f;
-  for (int k = 0; k < kThreads / 32; ++k) s += red[k];
-  return s;
 }
 
 // spectral record of n: mean and c_m, m = 1..M (one warp per mode, modes strided over warps)
@@ -326,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fluid(FluidK K, int n_steps, in
   if (!feat_only) {
     const long long first = K.diag_every > 0 ? K.step0 / K.diag_every : 0;
     for (int s = 0; s < n_steps; ++s) {
-      step(S, K, c);
+      step(S, K, c, red);
       const long long g = K.step0 + s;
       if (K.diag_every > 0 && K.n_modes >= 0 && (g + 1) % K.diag_every == 0)
         record(S, K, c, K.snap_base + (int)((g + 1) / K.diag_every - 1 - first), red);
@@ -358,6 +370,7 @@ struct pic_fluid {
   pic_mlp *net = nullptr;
   int period = 0;
   float fs[15], cs[3];
+  float nu_bound = 0.0f;
   float *X = nullptr, *Y = nullptr;
   bool y_valid = false;
   cudaStream_t st = nullptr;
@@ -389,6 +402,7 @@ FluidK make_k(pic_fluid *f) {
   K.corr = f->corr;
   for (int k = 0; k < 15; ++k) K.fs[k] = f->fs[k];
   K.cs0 = f->cs[0]; K.cs1 = f->cs[1]; K.cs2 = f->cs[2];
+  K.nu_bound = f->nu_bound;
   return K;
 }
 
@@ -493,7 +507,8 @@ int pic_fluid_init(const pic_fluid_column *cols, int n_cols, const pic_transport
   for (int c = 0; c < n_cols; ++c) {
     const pic_fluid_column &p = cols[c];
     if (!pow2(p.n_cells) || p.n_cells < 64 || p.n_cells > kMaxCells || !(p.L_m > 0.0) || !(p.N_gas_m3 > 0.0) ||
-        !(p.mu_iN > 0.0) || !std::isfinite(p.Gamma_T) || !std::isfinite(p.nu_w)) {
+        !(p.mu_iN > 0.0) || !std::isfinite(p.Gamma_T) || !std::isfinite(p.nu_w) ||
+        (p.loss != PIC_FLUID_LOSS_FIXED && p.loss != PIC_FLUID_LOSS_PAIR)) {
       delete f;
       return PIC_EINVAL;
     }
@@ -512,6 +527,7 @@ int pic_fluid_init(const pic_fluid_column *cols, int n_cols, const pic_transport
     k.mu_i = (float)(p.mu_iN / p.N_gas_m3);
     k.Ng = (float)p.N_gas_m3;
     k.invNg = (float)(1.0 / p.N_gas_m3);
+    k.pair = p.loss == PIC_FLUID_LOSS_PAIR;
     off += p.n_cells;
     f->maxN = std::max(f->maxN, p.n_cells);
   }
@@ -595,7 +611,8 @@ int pic_fluid_modes(pic_fluid *f, float *out, int max_snaps, int *n_snaps) {
   return lost > 0 ? PIC_ECAPACITY : 0;
 }
 
-int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *feat_scale, const float *targ_scale) {
+int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *feat_scale, const float *targ_scale,
+                          float nu_bound) {
   if (!f) return PIC_EINVAL;
   if (!net) {
     f->net = nullptr;
@@ -612,6 +629,7 @@ int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *f
   std::memcpy(f->cs, targ_scale, sizeof(f->cs));
   f->net = net;
   f->period = period;
+  f->nu_bound = nu_bound;
   f->y_valid = false;
   return 0;
 }

@@ -1,0 +1,456 @@
+"""Screen of discharge conditions with the fluid model, and the striation
+observables used to judge it against the particle model (Sec. IV).
+
+  * transport(): the closure tables -- two-term transport records at reduced
+    fields on a log grid (pic_two_term, eqs. 6-9);
+  * homogeneous_E0() / homogeneous_R(): the uniform steady state of eqs. 3-4
+    (Sec. IV.A: nu_i(T0) = nu_w, P0 = n0 L_eps(T0)), either for an imposed
+    field E0 with the wall loss equal to the ionization frequency (the
+    particle model's pair-loss column) or for a tube of radius R with
+    nu_w = D_a (2.405/R)^2 (eq. 2) and a current I;
+  * linear(): growth rate, wave number and phase velocity of the fastest
+    mode from the linearised fluid model, eqs. (19)-(22), and the instability
+    criterion eq. (23);
+  * observables(): wavelength, phase velocity and growth rate from a record
+    of spatial Fourier modes of n_e(x, t): lambda = L/m* with m* the mode of
+    largest time-averaged power over the saturated half of the record,
+    v_ph = -(d phase/dt)/k from the unwrapped phase of m*, gamma = slope of
+    ln|n_m*| while its amplitude lies between 10x its initial level and
+    1/10 of its saturated level;
+  * fluid_screen(): many columns of the fluid model in one batch on the GPU.
+
+Every density is handled per unit density: the fluid model is linear in n
+(Sec. II), so the current only scales n0.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import List, Sequence
+
+import numpy as np
+
+from . import Fluid, two_term
+from . import workloads as w
+
+KB = 1.380649e-23
+QE = 1.602176634e-19
+TORR = 133.32236842105263
+# Ne+ in Ne with the constant charge-exchange cross section of the particle model
+# (3e-19 m^2): low-field hard-sphere mobility 3/(8 N sigma) sqrt(pi/(mu_r k T)),
+# mu_r = M/2, at 300 K; field-independent in the fluid model
+MU_I_N_NEON = 3.0e22
+
+
+def n_gas(p_torr: float, T_gas: float = 300.0) -> float:
+    return p_torr * TORR / (KB * T_gas)
+
+
+def transport(gas: str = "neon", EN_Td: Sequence[float] | None = None, eps_max_eV: float = 250.0,
+              n_grid: int = 1000) -> List[dict]:
+    """Two-term transport records on a log grid of reduced fields (increasing Te)."""
+    ens = np.geomspace(2.0, 300.0, 64) if EN_Td is None else np.asarray(EN_Td, float)
+    xs = w.neon_xsecs() if gas == "neon" else w.argon_xsecs()
+    mass = w.AMU_NE if gas == "neon" else w.AMU_AR
+    recs = two_term(xs, mass, ens, eps_max_eV, n_grid)
+    te = [2.0 / 3.0 * r["mean_eps_eV"] for r in recs]
+    keep = [k for k in range(len(recs)) if k == 0 or te[k] > max(te[:k])]
+    return [recs[k] for k in keep]
+
+
+class Table:
+    """Linear interpolation of the transport records in Te (as in the fluid kernel)."""
+
+    def __init__(self, records):
+        self.Te = np.array([2.0 / 3.0 * r["mean_eps_eV"] for r in records])
+        self.q = {k: np.array([r[k] for r in records]) for k in records[0]}
+
+    def at(self, key, T):
+        return np.interp(T, self.Te, self.q[key])
+
+    def slope(self, key, T, h=1e-3):
+        return (self.at(key, T + h) - self.at(key, T - h)) / (2 * h)
+
+    def root(self, f):
+        """Smallest Te of the table where f changes sign (linear interpolation)."""
+        v = np.array([f(t) for t in self.Te])
+        k = np.nonzero(np.sign(v[:-1]) != np.sign(v[1:]))[0]
+        if len(k) == 0:
+            return math.nan
+        k = k[0]
+        lo, hi = self.Te[k], self.Te[k + 1]
+        for _ in range(60):
+            mid = 0.5 * (lo + hi)
+            if np.sign(f(mid)) == np.sign(f(lo)):
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+
+@dataclass
+class Homogeneous:
+    p_torr: float
+    N_gas: float
+    T0: float
+    E0: float
+    nu_w: float
+    n0: float
+    Gamma_T: float
+    mu_e: float
+    mu_i: float
+    D_e: float
+    R_m: float = math.nan
+    I_A: float = math.nan
+
+
+def homogeneous_E0(tab: Table, E0_over_p: float, p_torr: float = 1.0, n0: float = 1e15,
+                   mu_iN: float = MU_I_N_NEON, T_gas: float = 300.0) -> Homogeneous:
+    """Imposed field E0 (V/cm/Torr x p): power balance mu_e(T0) E0^2 = L(T0) fixes T0;
+    the wall loss equals the ionization frequency (pair-loss column)."""
+    N = n_gas(p_torr, T_gas)
+    E0 = E0_over_p * 100.0 * p_torr
+    T0 = tab.root(lambda T: tab.at("muN", T) / N * E0 * E0 - tab.at("lossN", T) * N)
+    mu_e = tab.at("muN", T0) / N
+    mu_i = mu_iN / N
+    nu_w = tab.at("nu_izN", T0) * N
+    return Homogeneous(p_torr, N, T0, E0, nu_w, n0, n0 * (mu_e + mu_i) * E0, mu_e, mu_i, tab.at("DN", T0) / N)
+
+
+def homogeneous_R(tab: Table, pR_torr_cm: float, I_over_R: float, R_m: float = 0.01,
+                  mu_iN: float = MU_I_N_NEON, T_gas: float = 300.0) -> Homogeneous:
+    """Tube of radius R, current I: nu_i(T0) = D_a(T0) (2.405/R)^2 (eq. 2) fixes T0, the power
+    balance fixes E0, the current density J = I/(pi R^2) fixes n0 = (J/e)/((mu_e + mu_i) E0)."""
+    p = pR_torr_cm / (R_m * 100.0)
+    N = n_gas(p, T_gas)
+    mu_i = mu_iN / N
+    g = (2.405 / R_m) ** 2
+
+    def f(T):
+        Da = mu_i * tab.at("DN", T) / tab.at("muN", T)
+        return tab.at("nu_izN", T) * N - Da * g
+
+    T0 = tab.root(f)
+    mu_e = tab.at("muN", T0) / N
+    E0 = math.sqrt(tab.at("lossN", T0) * N / mu_e)
+    nu_w = tab.at("nu_izN", T0) * N
+    I = I_over_R * R_m
+    GT = I / (math.pi * R_m * R_m) / QE
+    n0 = GT / ((mu_e + mu_i) * E0)
+    return Homogeneous(p, N, T0, E0, nu_w, n0, GT, mu_e, mu_i, tab.at("DN", T0) / N, R_m, I)
+
+
+def linear(tab: Table, h: Homogeneous) -> dict:
+    """Eqs. (19)-(23) at the homogeneous state h."""
+    N, T0 = h.N_gas, h.T0
+    De = lambda T: tab.at("DN", T) / N
+    mue = lambda T: tab.at("muN", T) / N
+    G = lambda T: 1.5 * T * tab.at("DeN", T) / N
+    beta_e = lambda T: 1.5 * T * tab.at("mueN", T) / N
+    d = 1e-3
+    dG = (G(T0 + d) - G(T0 - d)) / (2 * d)
+    dDe = (De(T0 + d) - De(T0 - d)) / (2 * d)
+    K = dG - beta_e(T0) / mue(T0) * dDe                   # kappa_e0 / n0 (eq. 15)
+    chi = G(T0) - beta_e(T0) / mue(T0) * De(T0)           # eq. 16
+    nup = tab.slope("nu_izN", T0) * N
+    L0 = tab.at("lossN", T0) * N
+    Lp = tab.slope("lossN", T0) * N
+    Da = h.mu_i * De(T0) / mue(T0)
+    al, be, de = chi * nup / (Da * K), Lp / K, 2 * L0 * nup / (Da * K)
+    disc = de - al * be
+    out = dict(chi=chi, K=K, nu_p=nup, L0=L0, L_p=Lp, D_a=Da,
+               chi_crit=-(Da * Lp + math.sqrt(max(8 * Da * K * L0 * nup, 0.0))) / nup)
+    if disc <= 0 or -be + math.sqrt(disc) <= 0:
+        out.update(gamma_max=math.nan, k_max=math.nan, lam=math.nan, v_ph=math.nan, unstable=False)
+        return out
+    k2 = -be + math.sqrt(disc)
+    k = math.sqrt(k2)
+    om = k * nup * h.E0 * De(T0) / (k2 * K + Lp)
+    gmax = Da * (be - al - 2 * math.sqrt(disc))
+    out.update(gamma_max=gmax, k_max=k, lam=2 * math.pi / k, v_ph=om / k, unstable=gmax > 0)
+    return out
+
+
+def gamma_k(tab: Table, h: Homogeneous, k: float) -> tuple[float, float]:
+    """(gamma, omega) of wave number k from eqs. (19)-(20)."""
+    lin = linear(tab, h)
+    K, nup, Lp, L0, Da, chi = lin["K"], lin["nu_p"], lin["L_p"], lin["L0"], lin["D_a"], lin["chi"]
+    den = k * k * K + Lp
+    om = k * nup * h.E0 * h.D_e / den
+    g = -Da * k * k - nup * (2 * L0 + chi * k * k) / den
+    return g, om
+
+
+def observables(t: np.ndarray, modes: np.ndarray, L: float) -> dict:
+    """Striation observables from a record of modes: t (snapshot times, increasing),
+    modes [snap, 1 + M] complex with entry 0 the mean density."""
+    mean = modes[:, 0].real
+    A = np.abs(modes[:, 1:]) / mean[:, None]
+    sat = t >= 0.5 * t[-1]
+    power = (A[sat] ** 2).mean(0)
+    m = int(np.argmax(power)) + 1
+    k = 2 * math.pi * m / L
+    ts = t[sat]
+    ph = np.unwrap(np.angle(modes[sat, m]))
+    v_ph = -np.polyfit(ts, ph, 1)[0] / k if len(ts) >= 3 else math.nan
+    a = A[:, m - 1]
+    a_sat = math.sqrt(power[m - 1])
+    a0 = max(a[0], 1e-30)
+    grow = np.nonzero((a > 10 * a0) & (a < 0.1 * a_sat))[0]
+    gamma = math.nan
+    if len(grow) >= 3:
+        i0, i1 = grow[0], grow[-1]
+        if i1 - i0 >= 2:
+            gamma = np.polyfit(t[i0:i1 + 1], np.log(a[i0:i1 + 1]), 1)[0]
+    return dict(m=m, lam=L / m, v_ph=v_ph, gamma=gamma, amp_sat=a_sat, amp0=a[0])
+
+
+def initial_state(N: int, h: Homogeneous, seed: int, amp: float = 1e-3):
+    """Homogeneous state with a seeded white perturbation of relative amplitude amp."""
+    rng = np.random.default_rng(seed)
+    n = h.n0 * (1.0 + amp * rng.standard_normal(N))
+    T = np.full(N, h.T0)
+    return n, T
+
+
+def fluid_columns(states: Sequence[Homogeneous], L_m: float, n_cells: int, pair: bool | None = None) -> List[dict]:
+    """Fluid columns of the homogeneous states: pair losses for imposed-field states (the
+    particle model's pair-loss column), the wall loss of eq. 2 for tube states (pair=None)."""
+    from . import FLUID_LOSS_FIXED, FLUID_LOSS_PAIR
+    out = []
+    for h in states:
+        pr = (math.isnan(h.R_m)) if pair is None else pair
+        out.append(dict(L_m=L_m, N_gas_m3=h.N_gas, mu_iN=h.mu_i * h.N_gas, Gamma_T=h.Gamma_T, nu_w=h.nu_w,
+                        n_cells=n_cells, loss=FLUID_LOSS_PAIR if pr else FLUID_LOSS_FIXED))
+    return out
+
+
+def fluid_screen(records, states: Sequence[Homogeneous], L_m: float = 0.30, n_cells: int = 4096,
+                 dt: float = 2e-8, steps: int = 20000, diag_every: int = 100, n_modes: int = 64,
+                 seed: int = 11, n_T: int = 128, closure=None) -> dict:
+    """Advance one fluid column per state for `steps` steps; return the observables per
+    column, the device time and the number of kernel launches."""
+    f = Fluid(fluid_columns(states, L_m, n_cells), records, n_T=n_T, dt_s=dt, diag_every=diag_every,
+              n_modes=n_modes)
+    if closure is not None:
+        f.set_closure(*closure)
+    for k, h in enumerate(states):
+        f.set_state(k, *initial_state(n_cells, h, seed + k))
+    f.step(steps)
+    ms, launches = f.elapsed()
+    rec = f.modes()
+    t = (np.arange(rec.shape[0]) + 1) * diag_every * dt
+    obs = [observables(t, rec[:, k], L_m) for k in range(len(states))]
+    f.close()
+    return dict(obs=obs, ms=ms, launches=launches, t=t, modes=rec)
+
+
+def pic_columns(E0_over_p: Sequence[float], p_torr: float = 1.0, L_m: float = 0.10, n_cells: int = 2048,
+                particles: int = 1_000_000, n0: float = 1e15, seed: int = 21, gas: str = "neon"):
+    """Particle-model columns (pair losses, imposed field) at the given reduced fields."""
+    base = w.config_neon_column(n_per_species=particles) if gas == "neon" else w.config_argon_small()
+    return [base.with_(pressure_torr=p_torr, L_m=L_m, n_cells=n_cells, E0_Vpm=e * 100.0 * p_torr,
+                       drive=w.DRIVE_E0, n0_m3=n0, n_e0=particles, n_i0=particles, loss_mode=w.LOSS_PAIR,
+                       diag_every=50, sort_every=1000, seed=seed + k, column=k)
+            for k, e in enumerate(E0_over_p)]
+
+
+def pic_record(params, windows: int, window: int):
+    """Run the columns as one GPU batch; per window and column: the density modes (FFT of
+    the window-averaged n_e), the ion mobility x N from the window's ion flux, and the
+    device time of the whole run."""
+    from . import Batch
+    b = Batch(params)
+    for c in b.columns:
+        c.moments(reset=True)
+    M = 64
+    rec = np.zeros((windows, len(params), M + 1), complex)
+    mob = np.zeros((windows, len(params)))
+    import time
+    t0 = time.perf_counter()
+    for s in range(windows):
+        b.step(window)
+        for k, (c, p) in enumerate(zip(b.columns, params)):
+            m = c.moments(reset=True)
+            ne = m["n_e"]
+            F = np.fft.fft(ne) / len(ne)
+            rec[s, k, 0] = ne.mean()
+            rec[s, k, 1:] = F[1:M + 1]
+            # the applied field points along -x in the particle model: ions drift towards -x
+            mob[s, k] = abs(m["gamma_i"].sum()) / max(m["n_i"].sum(), 1e-30) / p.E0_Vpm * n_gas(p.pressure_torr)
+    wall = time.perf_counter() - t0
+    b.close()
+    return rec, mob, wall
+
+
+def compare(E0_over_p: Sequence[float], p_torr: float = 1.0, L_m: float = 0.10, pic_cells: int = 2048,
+            fluid_cells: int = 2048, particles: int = 1_000_000, windows: int = 50, window: int = 20000,
+            fluid_dt: float = 2e-8, fluid_diag: int = 40, mu_iN: float | None = None, records=None,
+            closure=None, on_pic=None) -> dict:
+    """Particle model and fluid model at the same imposed reduced fields: striation
+    observables of both and the time each took per condition."""
+    records = records or transport()
+    tab = Table(records)
+    params = pic_columns(E0_over_p, p_torr, L_m, pic_cells, particles)
+    rec, mob, wall = pic_record(params, windows, window)
+    if on_pic is not None:
+        on_pic(rec, mob, wall)
+    dt_pic = params[0].dt_s
+    t_pic = (np.arange(windows) + 0.5) * window * dt_pic
+    pic_obs = [observables(t_pic, rec[:, k], L_m) for k in range(len(params))]
+    mu_meas = float(np.median(mob[windows // 2:])) if mu_iN is None else mu_iN
+    states = [homogeneous_E0(tab, e, p_torr, mu_iN=mu_meas) for e in E0_over_p]
+    T_total = windows * window * dt_pic
+    steps = int(round(T_total / fluid_dt))
+    fl = fluid_screen(records, states, L_m=L_m, n_cells=fluid_cells, dt=fluid_dt, steps=steps,
+                      diag_every=fluid_diag, closure=closure)
+    lin = [linear(tab, h) for h in states]
+    return dict(E0_over_p=list(E0_over_p), pic=pic_obs, fluid=fl["obs"], linear=lin, mu_iN=mu_meas,
+                pic_seconds=wall, fluid_ms=fl["ms"], simulated_s=T_total, fluid_steps=steps,
+                pic_steps=windows * window, pic_modes=rec, fluid_modes=fl["modes"], t_pic=t_pic, t_fluid=fl["t"])
+
+
+def _cathode_v(v_ph: float, frame: str) -> float:
+    """Phase velocity counted positive towards the cathode: the particle model's field
+    points along -x (cathode at -x), the fluid model's along +x."""
+    return -v_ph if frame == "pic" else v_ph
+
+
+def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 1.0, L_m: float = 0.10,
+          n_cells: int = 2048, particles: int = 1_000_000, windows: int = 200, window: int = 4000,
+          early: int = 100, early_window: int = 1000, agg: int = 4, fluid_dt: float = 2e-8, fluid_diag: int = 2,
+          train_steps: int = 3000, batch: int = 8192, lr: float = 1e-3, period: int = 10,
+          components=(0.0, 0.0, 1.0), nu_bound: float = 1.0, seed: int = 7, log=print) -> dict:
+    """Particle model (one GPU batch: comparison and training fields), closure training on
+    its moment windows, fluid model with and without the trained closure at the comparison
+    fields; striation observables, closure gain and times.  The particle record takes
+    `early` windows of `early_window` steps (growth phase), then `windows` windows of
+    `window` steps; closure data come from the long windows, `agg` at a time.
+    components: which network outputs the fluid screen applies (flux, energy flux,
+    ionization); the flux corrections enter the step explicitly, so they are only
+    stable while dt |dGamma/n| / dx and the energy change they carry per step stay small."""
+    import time
+    import torch
+    from . import Batch, Mlp
+    from . import closure as cl
+    records = transport()
+    tab = Table(records)
+    Es = list(E_compare) + list(E_train)
+    params = pic_columns(Es, p_torr, L_m, n_cells, particles)
+    ncmp = len(E_compare)
+    b = Batch(params)
+    for c in b.columns:
+        c.moments(reset=True)
+    M = 64
+    plan = [early_window] * early + [window] * windows
+    nw = len(plan)
+    rec = np.zeros((nw, len(Es), M + 1), complex)
+    mob = np.zeros((nw, len(Es)))
+    acc = [dict() for _ in Es]
+    train_windows = [[] for _ in Es]
+    keys = ("n_e", "mean_eps_e", "gamma_e", "heat_e", "iz_rate", "gamma_i", "E")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pic_run = 0.0
+    for s, steps_s in enumerate(plan):
+        ta = time.perf_counter()
+        b.step(steps_s)
+        pic_run += time.perf_counter() - ta
+        for k, (c, p) in enumerate(zip(b.columns, params)):
+            m = c.moments(reset=True)
+            rec[s, k, 0] = m["n_e"].mean()
+            rec[s, k, 1:] = (np.fft.fft(m["n_e"]) / n_cells)[1:M + 1]
+            mob[s, k] = abs(m["gamma_i"].sum()) / max(m["n_i"].sum(), 1e-30) / p.E0_Vpm * n_gas(p_torr)
+            if k >= ncmp and s >= early:
+                for q in keys:
+                    acc[k][q] = acc[k].get(q, 0.0) + m[q] / agg
+                if (s - early + 1) % agg == 0:
+                    train_windows[k].append(acc[k])
+                    acc[k] = dict()
+    wall = time.perf_counter() - t0
+    b.close()
+    total_steps = int(sum(plan))
+    log(f"particle batch: {len(Es)} columns, {total_steps} steps, {pic_run:.1f} s stepping, {wall:.1f} s total")
+    dt_pic = params[0].dt_s
+    ends = np.cumsum(plan)
+    t_pic = (ends - 0.5 * np.array(plan)) * dt_pic
+    amp = np.abs(rec[:, :, 1:]).max(2) / rec[:, :, 0].real
+    mu = []
+    for k in range(len(Es)):
+        # ion mobility of the uniform column: windows after the first 0.2 us, before striations
+        sel = [s for s in range(nw) if t_pic[s] > 2e-7 and amp[s, k] < 0.05][:8] or [min(nw - 1, early)]
+        mu.append(float(np.median(mob[sel, k])))
+    # closure data from the training columns: residuals of the tabulated closure
+    T_range = (tab.Te[0], tab.Te[-1])
+    Xs, Ys, col_of = [], [], []
+    for k in range(ncmp, len(Es)):
+        for m in train_windows[k][2:]:
+            X, Y = cl.residual_samples(m, params[k], tab, mu[k], T_range)
+            Xs.append(X)
+            Ys.append(Y)
+            col_of.append(np.full(len(X), k))
+    X = np.concatenate(Xs)
+    Y = np.concatenate(Ys)
+    col_of = np.concatenate(col_of)
+    fs = cl.FEATURE_SCALE
+    ts = np.maximum(np.std(Y, 0), 1e-30).astype(np.float32)
+    held = ncmp + (len(E_train) // 2)                  # one training column held out (split by run)
+    tr, te = col_of != held, col_of == held
+    Xn, Yn = (X / fs).astype(np.float32), (Y / ts).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(np.nonzero(tr)[0])
+    Xd = torch.from_numpy(Xn[perm]).cuda()
+    Yd = torch.from_numpy(Yn[perm]).cuda()
+    net = Mlp(seed=seed)
+    torch.cuda.synchronize()
+    ta = time.perf_counter()
+    last = net.train(Xd, Yd, batch=batch, steps=train_steps, lr=lr)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - ta
+    Yh = net.forward(torch.from_numpy(Xn[te]).cuda()).cpu().numpy()
+    mse_net = ((Yh - Yn[te]) ** 2).mean(0)
+    mse_tab = (Yn[te] ** 2).mean(0)             # the tabulated closure alone predicts zero residual
+    log(f"closure: {len(X)} samples, held-out column E0/p = {Es[held]}, mse net {mse_net} vs table {mse_tab}")
+    # fluid model at the comparison fields, same simulated time, noise of the particle model
+    states = [homogeneous_E0(tab, e, p_torr, mu_iN=mu[k]) for k, e in enumerate(E_compare)]
+    steps = int(round(total_steps * dt_pic / fluid_dt))
+    diag = fluid_diag
+    noise = 1.0 / math.sqrt(particles / n_cells)
+    mask = np.asarray(components, np.float32)
+    out = {}
+    clo_args = (net, period, fs, ts * mask, nu_bound)
+    variants = (("fluid", True, None), ("fluid_closure", True, clo_args),
+                ("fluid_fixed", False, None), ("fluid_fixed_closure", False, clo_args))
+    for name, pair, clo in variants:
+        f = Fluid(fluid_columns(states, L_m, n_cells, pair=pair), records, n_T=128, dt_s=fluid_dt,
+                  diag_every=diag, n_modes=M)
+        if clo is not None:
+            f.set_closure(*clo)
+        for k, h in enumerate(states):
+            f.set_state(k, *initial_state(n_cells, h, seed + 100 + k, amp=noise))
+        f.step(steps)
+        ms, launches = f.elapsed()
+        r = f.modes()
+        f.close()
+        t = (np.arange(r.shape[0]) + 1) * diag * fluid_dt
+        obs = [observables(t, r[:, k], L_m) for k in range(ncmp)]
+        for o in obs:
+            o["v_ph"] = _cathode_v(o["v_ph"], "fluid")
+        out[name] = dict(obs=obs, ms=ms, launches=launches, modes=r, t=t)
+        log(f"{name}: {steps} steps of {ncmp} columns in {ms:.1f} ms ({launches} launches)")
+    pic_obs = [observables(t_pic, rec[:, k], L_m) for k in range(ncmp)]
+    for o in pic_obs:
+        o["v_ph"] = _cathode_v(o["v_ph"], "pic")
+    lin = [linear(tab, h) for h in states]
+    pic_per_col = pic_run / len(Es)
+    return dict(E_compare=list(E_compare), E_train=list(E_train), mu_iN=mu, pic=pic_obs,
+                fluid=out["fluid"]["obs"], fluid_closure=out["fluid_closure"]["obs"],
+                fluid_fixed=out["fluid_fixed"]["obs"], fluid_fixed_closure=out["fluid_fixed_closure"]["obs"], linear=lin,
+                pic_seconds_per_column=pic_per_col,
+                fluid_seconds_per_column=out["fluid"]["ms"] / 1e3 / ncmp,
+                fluid_closure_seconds_per_column=out["fluid_closure"]["ms"] / 1e3 / ncmp,
+                simulated_s=total_steps * dt_pic, train_seconds=train_s, train_loss=last, components=list(components),
+                n_samples=int(len(X)), held_out_E=Es[held], mse_net=mse_net.tolist(), mse_table=mse_tab.tolist(),
+                target_scale=ts.tolist(), pic_modes=rec, t_pic=t_pic,
+                fluid_modes=out["fluid"]["modes"], fluid_closure_modes=out["fluid_closure"]["modes"],
+                t_fluid=out["fluid"]["t"])

@@ -37,7 +37,8 @@ def records():
 def columns():
     return [dict(L_m=0.05, N_gas_m3=N_GAS, mu_iN=1.1e22, Gamma_T=1.5e20, nu_w=2e4, n_cells=64),
             dict(L_m=0.30, N_gas_m3=0.5 * N_GAS, mu_iN=1.1e22, Gamma_T=3e20, nu_w=5e4, n_cells=512),
-            dict(L_m=0.30, N_gas_m3=2 * N_GAS, mu_iN=1.1e22, Gamma_T=2e20, nu_w=1e4, n_cells=4096)]
+            dict(L_m=0.30, N_gas_m3=2 * N_GAS, mu_iN=1.1e22, Gamma_T=2e20, nu_w=1e4, n_cells=4096),
+            dict(L_m=0.10, N_gas_m3=N_GAS, mu_iN=1.3e22, Gamma_T=2e20, nu_w=0.0, n_cells=1024, loss=pb.FLUID_LOSS_PAIR)]
 
 
 def initial(N, seed):
@@ -49,7 +50,8 @@ def initial(N, seed):
 
 
 def oracle_col(c):
-    return dict(L_m=c["L_m"], N_gas=c["N_gas_m3"], mu_iN=c["mu_iN"], Gamma_T=c["Gamma_T"], nu_w=c["nu_w"])
+    return dict(L_m=c["L_m"], N_gas=c["N_gas_m3"], mu_iN=c["mu_iN"], Gamma_T=c["Gamma_T"], nu_w=c["nu_w"],
+                pair=c.get("loss", 0) == pb.FLUID_LOSS_PAIR)
 
 
 @pytest.mark.parametrize("steps,tol", [(1, 1e-5), (40, 1e-4)])
@@ -120,21 +122,24 @@ def test_fluid_corrections_match_oracle(records):
         for _ in range(5):
             n, T = fl.step(oracle_col(c), tab, n, T, dt, corr=ck)
         gn, gT = f.get_state(k)
-        assert np.max(np.abs(gn / n - 1)) < 3e-5, k
-        assert np.max(np.abs(gT / T - 1)) < 3e-5, k
+        # white-noise corrections make the explicit flux differences the largest right-hand-side
+        # terms; FP32 rounds relative to them: the multi-step tolerance applies
+        assert np.max(np.abs(gn / n - 1)) < 1e-4, k
+        assert np.max(np.abs(gT / T - 1)) < 1e-4, k
     f.close()
 
 
 def test_fluid_network_closure_matches_oracle(records):
     import torch
     from oracle import mlp_forward_backward
-    cols = columns()[:2]
+    cols = columns()[:2] + columns()[3:]
     dt, period = 2e-8, 4
     fs = np.array([1.0] * 5 + [10.0] * 5 + [50.0] * 5, dtype=np.float32)
     ts = np.array([1e3, 1e4, 1e3], dtype=np.float32)
     net = pb.Mlp(seed=5)
     f = pb.Fluid(cols, records, n_T=128, dt_s=dt)
-    f.set_closure(net, period, fs, ts)
+    bound = 0.05                       # active: the random network's dnu exceeds 5% of nu_i in places
+    f.set_closure(net, period, fs, ts, nu_bound=bound)
     for k, c in enumerate(cols):
         f.set_state(k, *initial(c["n_cells"], k + 30))
     f.step(2 * period)
@@ -147,7 +152,10 @@ def test_fluid_network_closure_matches_oracle(records):
             Y = mlp_forward_backward(P, X, np.zeros((len(X), 3)), bf16=True, want_grad=False)[1]
             ck = (Y * ts).T
             for _ in range(period):
-                n, T = fl.step(oracle_col(c), tab, n, T, dt, corr=ck)
+                nu = fl.coefficients(oracle_col(c), tab, T)["nu_i"]
+                cb = ck.copy()
+                cb[2] = np.clip(cb[2], -bound * nu, bound * nu)
+                n, T = fl.step(oracle_col(c), tab, n, T, dt, corr=cb)
         gn, gT = f.get_state(k)
         assert np.max(np.abs(gn / n - 1)) < 1e-4, k
         assert np.max(np.abs(gT / T - 1)) < 1e-4, k

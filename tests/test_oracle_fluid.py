@@ -46,7 +46,7 @@ def test_homogeneous_steady_state_is_stationary():
 @pytest.mark.parametrize("m", [1, 7, 40])
 def test_continuity_symbol(m):
     # uniform T: one step multiplies a density mode by
-    # (1 + dt (nu_i - nu_w)) / (1 + 4 dt D_a sin^2(k dx/2) / dx^2), D_a = mu_i D_e/(mu_e + mu_i)
+    # (1 + dt nu_i) / (1 + dt nu_w + 4 dt D_a sin^2(k dx/2) / dx^2), D_a = mu_i D_e/(mu_e + mu_i)
     tab = const_table()
     N, L, dt = 512, 0.3, 2e-8
     col = column(L=L, tab=tab, nu_w=1e4)
@@ -57,12 +57,12 @@ def test_continuity_symbol(m):
     x = np.arange(N)
     n = 1e16 * (1 + 1e-3 * np.cos(2 * np.pi * m * x / N))
     n1, _ = fl.step(col, tab, n, np.full(N, 4.0), dt)
-    g = (1 + dt * (nu_i - 1e4)) / (1 + 4 * dt * Da * np.sin(np.pi * m / N) ** 2 / dx ** 2)
+    g = (1 + dt * nu_i) / (1 + dt * 1e4 + 4 * dt * Da * np.sin(np.pi * m / N) ** 2 / dx ** 2)
     c0, c1 = fl.modes(n, m)[-1], fl.modes(n1, m)[-1]
     assert c1 / c0 == pytest.approx(g, rel=1e-9)
     if m != 1:     # no other mode is excited
         assert abs(fl.modes(n1, 1)[0]) < 1e-12 * n1.mean()
-    assert n1.mean() == pytest.approx(1e16 * (1 + dt * (nu_i - 1e4)), rel=1e-12)
+    assert n1.mean() == pytest.approx(1e16 * (1 + dt * nu_i) / (1 + dt * 1e4), rel=1e-12)
 
 
 @pytest.mark.parametrize("m,GT,dloss", [(3, 0.0, 0.0), (3, 2e20, 0.0), (25, 2e20, 6e-15)])
@@ -99,7 +99,7 @@ def neon_table():
 
 
 def test_particle_and_energy_balance():
-    # fluxes telescope: sum n' - sum n = dt sum n (nu_i - nu_w); the energy changes by
+    # fluxes telescope: sum n' (1 + dt nu_w) - sum n = dt sum n nu_i; the energy changes by
     # dt sum (P - n' (L + L'(T' - T))) exactly (periodic column)
     tab = neon_table()
     rng = np.random.default_rng(5)
@@ -109,13 +109,28 @@ def test_particle_and_energy_balance():
     T = 5.0 + 0.3 * rng.standard_normal(N)
     c = fl.coefficients(col, tab, T)
     n1, T1 = fl.step(col, tab, n, T, dt)
-    assert n1.sum() - n.sum() == pytest.approx(dt * np.sum(n * (c["nu_i"] - col["nu_w"])), rel=1e-9)
+    assert n1.sum() * (1 + dt * col["nu_w"]) - n.sum() == pytest.approx(dt * np.sum(n * c["nu_i"]), rel=1e-9)
     Gam, E = fl.flux_and_field(col, c, n1)
     P = -0.5 * (Gam * E + np.roll(Gam * E, 1))
     if np.all((T1 > tab["T0"]) & (T1 < tab["T0"] + (tab["nT"] - 1) * tab["dT"])):
         lhs = 1.5 * (np.sum(n1 * T1) - np.sum(n * T))
         rhs = dt * np.sum(P - n1 * (c["L"] + c["dL"] * (T1 - T)))
         assert lhs == pytest.approx(rhs, rel=1e-8)
+
+
+def test_pair_losses_conserve_the_particle_number():
+    # with pair losses the column loses exactly what it ionizes: sum n' = sum n
+    tab = neon_table()
+    rng = np.random.default_rng(6)
+    N, dt = 256, 2e-8
+    col = column(L=0.1, Gamma_T=2e20, tab=tab, nu_w=0.0)
+    col["pair"] = True
+    n = 1e16 * (1 + 0.1 * rng.standard_normal(N))
+    T = 5.5 + 0.5 * rng.standard_normal(N)
+    corr = np.stack([np.zeros(N), np.zeros(N), 1e5 * rng.standard_normal(N)])
+    for c in (None, corr):
+        n1, _ = fl.step(col, tab, n, T, dt, corr=c)
+        assert n1.sum() == pytest.approx(n.sum(), rel=1e-12)
 
 
 def test_cyclic_solve_against_dense():
