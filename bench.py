@@ -162,6 +162,85 @@ def batched_vs_serial(pb, w, torch, steps: int, warmup: int, n_columns: int = 64
                         "per species, 2048-16384 cells, Ar/Ne alternating, dt 5e-12 s, MIXED"}
 
 
+def bf16_peak():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return float(json.loads(p.read_text())["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
+MLP_FWD_FLOP = 2 * (15 * 128 + 128 * 128 + 128 * 3)   # 37,376 per sample
+
+
+def fluid_screen_leg(pb, torch, steps: int = 1000, warmup: int = 20, closure_steps: int = 200):
+    """The fluid screen of a 32 x 32 grid of (pR, I/R) for neon columns (R = 1 cm, L = 0.30 m,
+    4096 cells, FP32): homogeneous states from eq. 2 with seeded 1e-3 noise, one batch on the GPU.
+    Timed with the handle's CUDA events; then the same screen with the closure network attached
+    (random weights, ionization correction bounded to +-50 %, features -> network every 10 steps)."""
+    from paper_2202_03215_gb300 import screen as sc
+    recs = sc.transport()
+    tab = sc.Table(recs)
+    states = [sc.homogeneous_R(tab, pr, ir) for pr in np.geomspace(0.3, 3.0, 32) for ir in np.geomspace(0.01, 1.0, 32)]
+    states = [h for h in states if np.isfinite(h.T0)]
+    cols = sc.fluid_columns(states, 0.30, 4096)
+    f = pb.Fluid(cols, recs, n_T=128, dt_s=2e-8, diag_every=50, n_modes=64)
+    for k, h in enumerate(states):
+        f.set_state(k, *sc.initial_state(4096, h, 100 + k))
+    f.step(warmup)
+    f.step(steps)
+    ms, launches = f.elapsed()
+    rec = f.modes()
+    cells = len(cols) * 4096
+    lin = [sc.linear(tab, h) for h in states]
+    net = pb.Mlp(seed=3)
+    ts = np.array([0.0, 0.0, 1e5], np.float32)
+    f.set_closure(net, 10, np.array([1.0] * 5 + [10.0] * 5 + [50.0] * 5, np.float32), ts, 0.5)
+    f.step(closure_steps)
+    ms_c, launches_c = f.elapsed()
+    f.close()
+    net.close()
+    inf_samples = cells * (closure_steps // 10 + 1)
+    return {"columns": len(cols), "cells_per_column": 4096, "steps": steps,
+            "column_steps_per_s": len(cols) * steps / (ms / 1e3), "cell_steps_per_s": cells * steps / (ms / 1e3),
+            "ms_per_step": ms / steps, "launches": launches, "records": int(rec.shape[0]),
+            "unstable_by_linear_theory": int(sum(1 for l in lin if l["unstable"])),
+            "closure": {"steps": closure_steps, "period": 10, "ms_per_step": ms_c / closure_steps,
+                        "launches": launches_c, "network_samples": inf_samples},
+            "workload": "neon, R=1 cm, L=0.30 m, 4096 cells, pR 0.3-3 Torr cm x I/R 0.01-1 A/m (32x32 log grid), "
+                        "eq. 2 wall loss, dt=2e-8 s, FP32, spectral record every 50 steps"}
+
+
+def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: int = 300, warmup: int = 20):
+    """Adam training of the closure network on the GPU (BF16 operands, FP32 accumulation):
+    forward + backward + deterministic gradient reduction + Adam per batch."""
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn((n, 15), device="cuda", generator=g)
+    T = torch.randn((n, 3), device="cuda", generator=g)
+    net = pb.Mlp(seed=9)
+    net.train(X, T, batch=batch, steps=warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net.train(X, T, batch=batch, steps=steps)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    sps = batch * steps / s
+    tflops = 3 * MLP_FWD_FLOP * sps / 1e12
+    peak, kind = bf16_peak()
+    net.forward(X[:batch])
+    torch.cuda.synchronize()
+    e0.record()
+    Yf = net.forward(X)
+    e1.record()
+    torch.cuda.synchronize()
+    sf = e0.elapsed_time(e1) / 1e3
+    return {"batch": batch, "steps": steps, "samples_per_s": sps, "tflops": tflops,
+            "frac_of_bf16_peak": tflops / peak, "peak_tflops": peak, "peak_kind": kind,
+            "flop_per_sample": 3 * MLP_FWD_FLOP,
+            "forward": {"samples": n, "samples_per_s": n / sf, "tflops": MLP_FWD_FLOP * n / sf / 1e12}}
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -196,6 +275,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-screen", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -310,6 +391,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_batch:
         batch = batched_vs_serial(pb, w, torch, steps=200, warmup=min(args.warmup, 10))
 
+    screen = train = None
+    if rank == 0 and world == 1 and not args.no_screen:
+        screen = fluid_screen_leg(pb, torch)
+    if rank == 0 and world == 1 and not args.no_train:
+        train = closure_training_leg(pb, torch)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -318,6 +405,7 @@ def main():
                            "l2": "inputs larger than L2 (state 1.1 GB)", "parallelism": f"replicas x{world}",
                            "pushed_particle_steps": units},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_vs_serial": batch,
+                "fluid_screen": screen, "closure_training": train,
                 "gpu_launches": launches,
                 "kernel_ms": {k: v[0] for k, v in kt.items()}, "clocks": clocks}
         print(json.dumps(line), flush=True)
