@@ -174,7 +174,7 @@ MLP_FWD_FLOP = 2 * (15 * 128 + 128 * 128 + 128 * 3)   # 37,376 per sample
 
 def fluid_screen_leg(pb, torch, steps: int = 1000, warmup: int = 20, closure_steps: int = 200):
     """The fluid screen of a 32 x 32 grid of (pR, I/R) for neon columns (R = 1 cm, L = 0.30 m,
-    4096 cells, FP32): homogeneous states from eq. 2 with seeded 1e-3 noise, one batch on the GPU.
+    4096 cells, FP32): homogeneous states from eq. 2 with seeded 1e-3 noise, pair losses, one batch.
     Timed with the handle's CUDA events; then the same screen with the closure network attached
     (random weights, ionization correction bounded to +-50 %, features -> network every 10 steps)."""
     from paper_2202_03215_gb300 import screen as sc
@@ -183,7 +183,7 @@ def fluid_screen_leg(pb, torch, steps: int = 1000, warmup: int = 20, closure_ste
     states = [sc.homogeneous_R(tab, pr, ir) for pr in np.geomspace(0.3, 3.0, 32) for ir in np.geomspace(0.01, 1.0, 32)]
     states = [h for h in states if np.isfinite(h.T0)]
     cols = sc.fluid_columns(states, 0.30, 4096)
-    f = pb.Fluid(cols, recs, n_T=128, dt_s=2e-8, diag_every=50, n_modes=64)
+    f = pb.Fluid(cols, recs, n_T=128, dt_s=2e-9, diag_every=50, n_modes=64)
     for k, h in enumerate(states):
         f.set_state(k, *sc.initial_state(4096, h, 100 + k))
     f.step(warmup)
@@ -207,7 +207,8 @@ def fluid_screen_leg(pb, torch, steps: int = 1000, warmup: int = 20, closure_ste
             "closure": {"steps": closure_steps, "period": 10, "ms_per_step": ms_c / closure_steps,
                         "launches": launches_c, "network_samples": inf_samples},
             "workload": "neon, R=1 cm, L=0.30 m, 4096 cells, pR 0.3-3 Torr cm x I/R 0.01-1 A/m (32x32 log grid), "
-                        "eq. 2 wall loss, dt=2e-8 s, FP32, spectral record every 50 steps"}
+                        "homogeneous states from eq. 2, pair losses, dt=2e-9 s, FP32 (state as FP32 pairs), "
+                        "spectral record every 50 steps"}
 
 
 def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: int = 300, warmup: int = 20):

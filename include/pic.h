@@ -343,7 +343,7 @@ int pic_two_term(const pic_xsec *xs, int n_xsec, double gas_mass_amu, const doub
 
 /* ------------------------------------------------------------------------
  * Quasi-neutral three-moment fluid model of the column (Sec. IV.A, eqs. 3-5,
- * 8-9, 11, 17) for many independent periodic columns at once: the fast screen
+ * 8-12, 17) for many independent periodic columns at once: the fast screen
  * of discharge conditions.  State per cell: electron density n (= ion
  * density) and temperature Te, FP32 on the device.  Closure: mu_e, D_e,
  * mu_eps, D_eps, nu_i and L_eps as functions of Te from transport records
@@ -356,7 +356,9 @@ int pic_two_term(const pic_xsec *xs, int n_xsec, double gas_mass_amu, const doub
  *       n'_j (1 + dt nu_w) - dt/dx^2 [a_{j+1/2}((nD_e)'_{j+1} - (nD_e)'_j) - a_{j-1/2}((nD_e)'_j - (nD_e)'_{j-1})]
  *         = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i + dnu) - dt/dx (dG_{j+1/2} - dG_{j-1/2}),
  *     a = mu_i/(mu_e + mu_i), b = 1 - a (eq. 11);
- *  2. Gamma_{j+1/2} (eq. 11, plus dG) and E_{j+1/2} (eq. 17) from n';
+ *  2. Gamma_{j+1/2} (eq. 11, plus dG) and E_{j+1/2} from n', with
+ *     E = -d_x(n D_e)/(n mu_e) + Gamma_T/(n (mu_e + mu_i)) (eq. 10 combined with eq. 12,
+ *     the derivation of eq. 17; mu_e face-averaged);
  *  3. energy, backward Euler in Te' for conduction, energy drift and the
  *     linearised loss, with H = -3/2 mu_eps E n Te - d_x(3/2 n D_eps Te) + dH
  *     (eqs. 8-9 with beta = 3/2 Te mu_eps, G = 3/2 Te D_eps) and the heating

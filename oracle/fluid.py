@@ -9,8 +9,11 @@ Model (Sec. IV.A): electron continuity and energy, eqs. (3)-(4),
     d_t (3/2 n T) + d_x H = P - n L_eps,       P = -Gamma E       (eq. 5)
 with the flux of eq. (11) (eq. 7 with E eliminated through eq. 10)
     Gamma = -mu_i/(mu_e + mu_i) d_x(n D_e) - mu_e/(mu_e + mu_i) Gamma_T,
-the field of eq. (17)
-    E = -d_x(n D_e/mu_e)/n + Gamma_T / (n (mu_e + mu_i)),
+the field of eq. (10) combined with the flux of eq. (12), which is how eq. (17)
+is obtained (read with mu_e outside the gradient, as that combination gives;
+the printed eq. 17 moves it inside, which with a Te-dependent mobility adds a
+negative effective heat conduction and makes the model ill-posed at high Te)
+    E = -d_x(n D_e)/(n mu_e) + Gamma_T / (n (mu_e + mu_i)),
 and the energy flux of eq. (8), H = -n beta E - d_x(n G), with eq. (9) read
 as beta = 3/2 T mu_eps, G = 3/2 T D_eps (the form eq. 16's second line
 requires).  mu_e, D_e, mu_eps, D_eps, nu_i and L_eps are functions of T
@@ -103,14 +106,13 @@ def face(v):
 
 
 def flux_and_field(col, c, n):
-    """Gamma and E at faces j+1/2 for density n (eqs. 11 and 17)."""
+    """Gamma and E at faces j+1/2 for density n (eqs. 11 and 10 + 12)."""
     dx = col["L_m"] / len(n)
     GT = col["Gamma_T"]
     nD = n * c["D_e"]
     Gam = -face(c["a"]) * (np.roll(nD, -1) - nD) / dx - face(c["b"]) * GT
-    nDm = n * c["D_e"] / c["mu_e"]
     nf = face(n)
-    E = -(np.roll(nDm, -1) - nDm) / (dx * nf) + GT / (nf * face(c["mu_e"] + c["mu_i"]))
+    E = -(np.roll(nD, -1) - nD) / (dx * nf * face(c["mu_e"])) + GT / (nf * face(c["mu_e"] + c["mu_i"]))
     return Gam, E
 
 

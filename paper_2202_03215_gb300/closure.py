@@ -167,7 +167,7 @@ def _face(v):
 
 def table_closure(n, T, Gamma_T, L_m, N_gas, mu_iN, tab):
     """The fluid model's tabulated closure evaluated on a given state (the same
-    formulas as the fluid step): electron flux (eq. 11), field (eq. 17) and energy
+    formulas as the fluid step): electron flux (eq. 11), field (eqs. 10 + 12) and energy
     flux (eqs. 8-9) at cells as averages of their faces, and nu_i(T)."""
     dx = L_m / len(n)
     mu_e = tab.at("muN", T) / N_gas
@@ -179,9 +179,8 @@ def table_closure(n, T, Gamma_T, L_m, N_gas, mu_iN, tab):
     af = _face(a)
     nD = n * D_e
     G = -af * (np.roll(nD, -1) - nD) / dx - (1.0 - af) * Gamma_T
-    nDm = n * D_e / mu_e
     nf = _face(n)
-    E = -(np.roll(nDm, -1) - nDm) / (dx * nf) + Gamma_T / (nf * _face(mu_e + mu_i))
+    E = -(np.roll(nD, -1) - nD) / (dx * nf * _face(mu_e)) + Gamma_T / (nf * _face(mu_e + mu_i))
     nT = n * T
     H = -0.75 * _face(mu_eps) * E * (nT + np.roll(nT, -1)) - 1.5 * (np.roll(n * D_eps * T, -1) - n * D_eps * T) / dx
     cell = lambda f: 0.5 * (f + np.roll(f, 1))

@@ -1,9 +1,12 @@
-// Quasi-neutral three-moment fluid model (Sec. IV.A, eqs. 3-5, 8-9, 11, 17)
+// Quasi-neutral three-moment fluid model (Sec. IV.A, eqs. 3-5, 8-12, 17)
 // of many independent periodic columns: one thread block per column holds the
 // whole column in shared memory (state, coefficient and face arrays, the two
 // cyclic tridiagonal systems) and advances it through a chunk of steps with no
 // global-memory round trip; the spectral record and the closure features are
 // the only per-step outputs.  The step is written out in include/pic.h.
+// The state is kept as FP32 pairs (hi + lo) advanced by exact two-sums, so that
+// increments far below one FP32 ulp of n or Te still accumulate (slow growth at
+// a small time step); every coefficient and flux is evaluated from hi in FP32.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,7 +28,7 @@ constexpr int kRows = kMaxCells / kThreads;   // rows per thread at the largest 
 constexpr int kMaxModes = 64;
 constexpr int kMaxT = 256;
 constexpr int kNQ = 6;                          // muN, DN, mueN, DeN, nu_izN, lossN
-constexpr int kArrays = 13;                     // shared-memory arrays of n_cells floats
+constexpr int kArrays = 14;                     // shared-memory arrays of n_cells floats
 constexpr int kChunk = 2000;                    // steps per launch without a closure
 constexpr float kTd = 1e-21f;
 
@@ -39,7 +42,7 @@ struct ColK {
 
 struct FluidK {
   const ColK *cols;
-  float *n, *T;                 // state, all columns
+  double *n, *T;                // state, all columns
   const float *tab;             // kNQ x nT (per gas density)
   int nT;
   float T0, inv_dT, Tmax, dt;
@@ -57,7 +60,7 @@ struct FluidK {
 };
 
 struct Sm {
-  float *n, *T, *u, *D, *A, *B, *G, *E, *H, *pa, *pb, *pc, *pd, *tab;
+  float *n, *nl, *T, *Tl, *u, *D, *A, *B, *G, *E, *pa, *pb, *pc, *pd;
 };
 
 __device__ __forceinline__ void tpos(const FluidK &K, float T, int &i, float &f) {
@@ -67,9 +70,20 @@ __device__ __forceinline__ void tpos(const FluidK &K, float T, int &i, float &f)
   f = x - (float)i;
 }
 
-__device__ __forceinline__ float tq(const Sm &S, const FluidK &K, int q, int i, float f) {
-  const float a = S.tab[q * K.nT + i], b = S.tab[q * K.nT + i + 1];
+// table value q at position (i, f); the table (a few KB) is read through the L1 cache
+__device__ __forceinline__ float tq(const Sm &, const FluidK &K, int q, int i, float f) {
+  const float a = __ldg(K.tab + q * K.nT + i), b = __ldg(K.tab + q * K.nT + i + 1);
   return a + f * (b - a);
+}
+
+// (hi, lo) += d with an exact two-sum (no contraction: -fmad=false)
+__device__ __forceinline__ void add2(float &hi, float &lo, float d) {
+  const float s = hi + d;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (d - bp);
+  const float l = lo + e;
+  hi = s + l;
+  lo = l - (hi - s);
 }
 
 // periodic parallel cyclic reduction; N a power of two; row j: pa x_{j-1} + pb x_j + pc x_{j+1} = pd
@@ -122,15 +136,17 @@ __device__ void coeffs(const Sm &S, const FluidK &K, const ColK &c) {
   }
 }
 
-// E at faces (eq. 17) from the density in S.n into S.E; uses D, B (= mu_e)
+// E at faces from the density in S.n into S.E; uses D, B (= mu_e):
+// E = -d_x(n D_e) / (n mu_e) + Gamma_T / (n (mu_e + mu_i)), eq. 10 with the flux of eq. 12
 __device__ void field(const Sm &S, const ColK &c) {
   const int N = c.N;
   for (int j = threadIdx.x; j < N; j += kThreads) {
     const int jp = (j + 1) & (N - 1);
-    const float nDm0 = S.n[j] * S.D[j] / S.B[j], nDm1 = S.n[jp] * S.D[jp] / S.B[jp];
+    const float nD0 = S.n[j] * S.D[j], nD1 = S.n[jp] * S.D[jp];
     const float nf = 0.5f * (S.n[j] + S.n[jp]);
+    const float muf = 0.5f * (S.B[j] + S.B[jp]);
     const float mf = 0.5f * ((S.B[j] + c.mu_i) + (S.B[jp] + c.mu_i));
-    S.E[j] = -(nDm1 - nDm0) / (c.dx * nf) + c.GT / (nf * mf);
+    S.E[j] = -(nD1 - nD0) / (c.dx * nf * muf) + c.GT / (nf * mf);
   }
 }
 
@@ -168,7 +184,6 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
       corr_at(K, c.off + j, g0, h0, n0);
       corr_at(K, c.off + jp, g1, h1, n1);
       S.G[j] = 0.5f * (S.n[j] * g0 + S.n[jp] * g1);
-      S.H[j] = 0.5f * (S.n[j] * h0 + S.n[jp] * h1);
       if (K.netY && K.nu_bound > 0.0f) n0 = fminf(fmaxf(n0, -K.nu_bound * nu), K.nu_bound * nu);
       nu += n0;
     }
@@ -202,7 +217,7 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
   }
   __syncthreads();
   pcr(S, N);
-  for (int j = t; j < N; j += kThreads) S.n[j] = S.u[j] + S.pd[j] / (S.pa[j] + S.pb[j] + S.pc[j]);
+  for (int j = t; j < N; j += kThreads) add2(S.n[j], S.nl[j], S.pd[j] / (S.pa[j] + S.pb[j] + S.pc[j]));
   __syncthreads();
   // 3. flux and field at faces from n'; energy coefficients into pa (mu_eps), pb (D_eps)
   field(S, c);
@@ -219,14 +234,20 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
     S.pb[j] = tq(S, K, 3, i, f) * c.invNg;
   }
   __syncthreads();
-  // energy flux of the starting T with n' (plus the correction) on faces, into H
+  // energy flux of the starting T with n' (plus the correction, on the starting n kept in u)
+  // on faces, into A (free once the flux and field are formed)
   for (int j = t; j < N; j += kThreads) {
     const int jp = (j + 1) & (N - 1);
     const float mep = 0.5f * (S.pa[j] + S.pa[jp]);
     float h = -0.75f * mep * S.E[j] * (S.n[j] * S.T[j] + S.n[jp] * S.T[jp]) -
               c.k * (S.n[jp] * S.pb[jp] * S.T[jp] - S.n[j] * S.pb[j] * S.T[j]);
-    if (has_corr) h += S.H[j];
-    S.H[j] = h;
+    if (has_corr) {
+      float g0, h0, n0, g1, h1, n1;
+      corr_at(K, c.off + j, g0, h0, n0);
+      corr_at(K, c.off + jp, g1, h1, n1);
+      h += 0.5f * (S.u[j] * h0 + S.u[jp] * h1);
+    }
+    S.A[j] = h;
   }
   __syncthreads();
   // 4. energy: A dT = rhs - A T (built in registers: rows read the neighbours' pa, pb)
@@ -241,7 +262,7 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
         int i; float f;
         tpos(K, S.T[j], i, f);
         const float L = tq(S, K, 5, i, f) * c.Ng;
-        const float dL = (S.tab[5 * K.nT + i + 1] - S.tab[5 * K.nT + i]) * K.inv_dT * c.Ng;
+        const float dL = (__ldg(K.tab + 5 * K.nT + i + 1) - __ldg(K.tab + 5 * K.nT + i)) * K.inv_dT * c.Ng;
         const float mep = 0.5f * (S.pa[j] + S.pa[jp]), mem = 0.5f * (S.pa[jm] + S.pa[j]);
         const float Ep = S.E[j], Em = S.E[jm];
         const float n1 = S.n[j];
@@ -249,7 +270,7 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
                 2.0f * c.s * c.k * n1 * S.pb[j];
         rc[r] = c.s * (-0.75f * mep * Ep - c.k * S.pb[jp]) * S.n[jp];
         ra[r] = c.s * (0.75f * mem * Em - c.k * S.pb[jm]) * S.n[jm];
-        rd[r] = 1.5f * (S.u[j] - n1) * S.T[j] + K.dt * P - K.dt * n1 * L - c.s * (S.H[j] - S.H[jm]);
+        rd[r] = 1.5f * (S.u[j] - n1) * S.T[j] + K.dt * P - K.dt * n1 * L - c.s * (S.A[j] - S.A[jm]);
       }
     }
     __syncthreads();
@@ -262,8 +283,9 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
   }
   pcr(S, N);
   for (int j = t; j < N; j += kThreads) {
-    const float T1 = S.T[j] + S.pd[j] / (S.pa[j] + S.pb[j] + S.pc[j]);
-    S.T[j] = fminf(fmaxf(T1, K.T0), K.Tmax);
+    add2(S.T[j], S.Tl[j], S.pd[j] / (S.pa[j] + S.pb[j] + S.pc[j]));
+    if (S.T[j] < K.T0) { S.T[j] = K.T0; S.Tl[j] = 0.0f; }
+    if (S.T[j] > K.Tmax) { S.T[j] = K.Tmax; S.Tl[j] = 0.0f; }
   }
   __syncthreads();
 }
@@ -272,20 +294,24 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
 __device__ void record(const Sm &S, const FluidK &K, const ColK &c, int snap, float *red) {
   const int N = c.N, M = K.n_modes;
   float v = 0.0f;
-  for (int j = threadIdx.x; j < N; j += kThreads) v += S.n[j];
+  for (int j = threadIdx.x; j < N; j += kThreads) v += S.n[j] + S.nl[j];
   const float mean = block_sum(v, red) / (float)N;
   float2 *out = K.modes + ((size_t)snap * K.n_cols + blockIdx.x) * (M + 1);
   if (threadIdx.x == 0) out[0] = make_float2(mean, 0.0f);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   for (int m = 1 + w; m <= M; m += kThreads / 32) {
-    float re = 0.0f, im = 0.0f;
+    float re = 0.0f, im = 0.0f, rel = 0.0f, iml = 0.0f;   // hi and lo parts summed apart
     for (int j = l; j < N; j += 32) {
       const int ph = (m * j) & (N - 1);
       float sn, cs;
       sincospif(2.0f * (float)ph / (float)N, &sn, &cs);
       re += S.n[j] * cs;
       im -= S.n[j] * sn;
+      rel += S.nl[j] * cs;
+      iml -= S.nl[j] * sn;
     }
+    re += rel;
+    im += iml;
     for (int o = 16; o > 0; o >>= 1) {
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
@@ -324,15 +350,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_fluid(FluidK K, int n_steps, in
   const ColK c = K.cols[blockIdx.x];
   const int N = c.N;
   Sm S;
-  S.n = base;          S.T = base + N;      S.u = base + 2 * N;  S.D = base + 3 * N;
-  S.A = base + 4 * N;  S.B = base + 5 * N;  S.G = base + 6 * N;  S.E = base + 7 * N;
-  S.H = base + 8 * N;  S.pa = base + 9 * N; S.pb = base + 10 * N; S.pc = base + 11 * N;
-  S.pd = base + 12 * N;
-  S.tab = base + (size_t)kArrays * N;
-  for (int q = threadIdx.x; q < kNQ * K.nT; q += kThreads) S.tab[q] = K.tab[q];
+  S.n = base;           S.nl = base + N;      S.T = base + 2 * N;   S.Tl = base + 3 * N;
+  S.u = base + 4 * N;   S.D = base + 5 * N;   S.A = base + 6 * N;   S.B = base + 7 * N;
+  S.G = base + 8 * N;   S.E = base + 9 * N;   S.pa = base + 10 * N; S.pb = base + 11 * N;
+  S.pc = base + 12 * N; S.pd = base + 13 * N;
   for (int j = threadIdx.x; j < N; j += kThreads) {
-    S.n[j] = K.n[c.off + j];
-    S.T[j] = K.T[c.off + j];
+    const double n = K.n[c.off + j], T = K.T[c.off + j];
+    S.n[j] = (float)n;
+    S.nl[j] = (float)(n - (double)S.n[j]);
+    S.T[j] = (float)T;
+    S.Tl[j] = (float)(T - (double)S.T[j]);
   }
   __syncthreads();
   if (!feat_only) {
@@ -344,14 +371,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_fluid(FluidK K, int n_steps, in
         record(S, K, c, K.snap_base + (int)((g + 1) / K.diag_every - 1 - first), red);
     }
     for (int j = threadIdx.x; j < N; j += kThreads) {
-      K.n[c.off + j] = S.n[j];
-      K.T[c.off + j] = S.T[j];
+      K.n[c.off + j] = (double)S.n[j] + (double)S.nl[j];
+      K.T[c.off + j] = (double)S.T[j] + (double)S.Tl[j];
     }
   }
   if (K.feat) features(S, K, c, red);
 }
 
-size_t smem_bytes(int N, int nT) { return ((size_t)kArrays * N + (size_t)kNQ * nT) * sizeof(float); }
+size_t smem_bytes(int N) { return (size_t)kArrays * N * sizeof(float); }
 
 bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
@@ -363,7 +390,8 @@ struct pic_fluid {
   double dt = 0.0, T0 = 0.0, dT = 0.0;
   std::vector<ColK> hcols;
   ColK *cols = nullptr;
-  float *n = nullptr, *T = nullptr, *tab = nullptr;
+  double *n = nullptr, *T = nullptr;
+  float *tab = nullptr;
   float2 *modes = nullptr;
   int snap_cap = 0, snap_count = 0;
   const float *corr = nullptr;
@@ -407,7 +435,7 @@ FluidK make_k(pic_fluid *f) {
 }
 
 int launch(pic_fluid *f, FluidK K, int n_steps, int feat_only) {
-  const size_t sm = smem_bytes(f->maxN, f->nT);
+  const size_t sm = smem_bytes(f->maxN);
   if (cudaFuncSetAttribute(k_fluid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return PIC_ECUDA;
   k_fluid<<<f->n_cols, kThreads, sm, f->st>>>(K, n_steps, feat_only);
@@ -537,14 +565,14 @@ int pic_fluid_init(const pic_fluid_column *cols, int n_cols, const pic_transport
   bool ok = cudaStreamCreateWithFlags(&f->st, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreate(&f->e0) == cudaSuccess && cudaEventCreate(&f->e1) == cudaSuccess &&
             cudaMalloc(&f->cols, sizeof(ColK) * n_cols) == cudaSuccess &&
-            cudaMalloc(&f->n, sizeof(float) * off) == cudaSuccess &&
-            cudaMalloc(&f->T, sizeof(float) * off) == cudaSuccess &&
+            cudaMalloc(&f->n, sizeof(double) * off) == cudaSuccess &&
+            cudaMalloc(&f->T, sizeof(double) * off) == cudaSuccess &&
             cudaMalloc(&f->tab, sizeof(float) * tab.size()) == cudaSuccess;
   if (ok)
     ok = cudaMemcpy(f->cols, f->hcols.data(), sizeof(ColK) * n_cols, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(f->tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemset(f->n, 0, sizeof(float) * off) == cudaSuccess &&
-         cudaMemset(f->T, 0, sizeof(float) * off) == cudaSuccess;
+         cudaMemset(f->n, 0, sizeof(double) * off) == cudaSuccess &&
+         cudaMemset(f->T, 0, sizeof(double) * off) == cudaSuccess;
   if (!ok) {
     pic_fluid_free(f);
     return PIC_ENOMEM;
@@ -556,14 +584,10 @@ int pic_fluid_init(const pic_fluid_column *cols, int n_cols, const pic_transport
 int pic_fluid_set_state(pic_fluid *f, int col, const double *n_m3, const double *Te_eV) {
   if (!f || col < 0 || col >= f->n_cols || !n_m3 || !Te_eV) return PIC_EINVAL;
   const ColK &c = f->hcols[col];
-  std::vector<float> a(c.N), b(c.N);
-  for (int j = 0; j < c.N; ++j) {
-    if (!(n_m3[j] > 0.0) || !std::isfinite(Te_eV[j])) return PIC_EINVAL;
-    a[j] = (float)n_m3[j];
-    b[j] = (float)Te_eV[j];
-  }
-  if (cudaMemcpyAsync(f->n + c.off, a.data(), 4 * c.N, cudaMemcpyHostToDevice, f->st) != cudaSuccess ||
-      cudaMemcpyAsync(f->T + c.off, b.data(), 4 * c.N, cudaMemcpyHostToDevice, f->st) != cudaSuccess ||
+  for (int j = 0; j < c.N; ++j)
+    if (!(n_m3[j] > 0.0) || !std::isfinite(n_m3[j]) || !std::isfinite(Te_eV[j])) return PIC_EINVAL;
+  if (cudaMemcpyAsync(f->n + c.off, n_m3, 8 * c.N, cudaMemcpyHostToDevice, f->st) != cudaSuccess ||
+      cudaMemcpyAsync(f->T + c.off, Te_eV, 8 * c.N, cudaMemcpyHostToDevice, f->st) != cudaSuccess ||
       cudaStreamSynchronize(f->st) != cudaSuccess)
     return PIC_ECUDA;
   f->y_valid = false;
@@ -573,15 +597,10 @@ int pic_fluid_set_state(pic_fluid *f, int col, const double *n_m3, const double 
 int pic_fluid_get_state(pic_fluid *f, int col, double *n_m3, double *Te_eV) {
   if (!f || col < 0 || col >= f->n_cols || !n_m3 || !Te_eV) return PIC_EINVAL;
   const ColK &c = f->hcols[col];
-  std::vector<float> a(c.N), b(c.N);
-  if (cudaMemcpyAsync(a.data(), f->n + c.off, 4 * c.N, cudaMemcpyDeviceToHost, f->st) != cudaSuccess ||
-      cudaMemcpyAsync(b.data(), f->T + c.off, 4 * c.N, cudaMemcpyDeviceToHost, f->st) != cudaSuccess ||
+  if (cudaMemcpyAsync(n_m3, f->n + c.off, 8 * c.N, cudaMemcpyDeviceToHost, f->st) != cudaSuccess ||
+      cudaMemcpyAsync(Te_eV, f->T + c.off, 8 * c.N, cudaMemcpyDeviceToHost, f->st) != cudaSuccess ||
       cudaStreamSynchronize(f->st) != cudaSuccess)
     return PIC_ECUDA;
-  for (int j = 0; j < c.N; ++j) {
-    n_m3[j] = a[j];
-    Te_eV[j] = b[j];
-  }
   return 0;
 }
 

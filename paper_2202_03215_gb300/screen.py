@@ -52,10 +52,10 @@ def n_gas(p_torr: float, T_gas: float = 300.0) -> float:
     return p_torr * TORR / (KB * T_gas)
 
 
-def transport(gas: str = "neon", EN_Td: Sequence[float] | None = None, eps_max_eV: float = 250.0,
-              n_grid: int = 1000) -> List[dict]:
-    """Two-term transport records on a log grid of reduced fields (increasing Te)."""
-    ens = np.geomspace(2.0, 300.0, 64) if EN_Td is None else np.asarray(EN_Td, float)
+def transport(gas: str = "neon", EN_Td: Sequence[float] | None = None, eps_max_eV: float = 400.0,
+              n_grid: int = 1200) -> List[dict]:
+    """Two-term transport records on a log grid of reduced fields, 2-1000 Td (increasing Te)."""
+    ens = np.geomspace(2.0, 1000.0, 80) if EN_Td is None else np.asarray(EN_Td, float)
     xs = w.neon_xsecs() if gas == "neon" else w.argon_xsecs()
     mass = w.AMU_NE if gas == "neon" else w.AMU_AR
     recs = two_term(xs, mass, ens, eps_max_eV, n_grid)
@@ -70,6 +70,20 @@ class Table:
     def __init__(self, records):
         self.Te = np.array([2.0 / 3.0 * r["mean_eps_eV"] for r in records])
         self.q = {k: np.array([r[k] for r in records]) for k in records[0]}
+
+    @classmethod
+    def uniform(cls, records, n_T: int) -> "Table":
+        """The records resampled (linear in Te) onto n_T uniform Te points: the table the fluid
+        kernel interpolates (pic_fluid_init), so that derivatives match its slopes."""
+        Te = np.array([2.0 / 3.0 * r["mean_eps_eV"] for r in records])
+        grid = np.linspace(Te[0], Te[-1], n_T)
+        keys = [k for k in records[0] if k != "mean_eps_eV"]
+        out = [dict(mean_eps_eV=1.5 * x) for x in grid]
+        for k in keys:
+            v = np.interp(grid, Te, np.array([r[k] for r in records]))
+            for d, x in zip(out, v):
+                d[k] = float(x)
+        return cls(out)
 
     def at(self, key, T):
         return np.interp(T, self.Te, self.q[key])
@@ -197,6 +211,68 @@ def gamma_k(tab: Table, h: Homogeneous, k: float) -> tuple[float, float]:
     return g, om
 
 
+def dispersion(tab: Table, h: Homogeneous, k: float, vector: bool = False):
+    """(gamma, omega) of wave number k from the full linearisation of the fluid model as it is
+    integrated (eqs. 3-5 with the flux of eq. 11, the field of eqs. 10 + 12 and the energy flux
+    of eqs. 8-9 read as beta = 3/2 Te mu_eps, G = 3/2 Te D_eps; fixed nu_w = nu_i(T0)), keeping
+    what eq. (18) drops: the time
+    derivative of the energy equation, the temperature terms of the field and of the fluxes.
+    Perturbations (dn, dT) exp(i k x - i Omega t) solve -i Omega M v = A v with
+    M = [[1, 0], [3/2 T0, 3/2 n0]]; the root with the largest growth rate is returned, and with
+    vector=True also its eigenvector (dn, dT)."""
+    N, T0, n0, GT = h.N_gas, h.T0, h.n0, h.Gamma_T
+    d = 1e-4
+    mu = lambda T: tab.at("muN", T) / N
+    D = lambda T: tab.at("DN", T) / N
+    mue = lambda T: tab.at("mueN", T) / N
+    De = lambda T: tab.at("DeN", T) / N
+    der = lambda F: (F(T0 + d) - F(T0 - d)) / (2 * d)
+    mui = h.mu_i
+    a = lambda T: mui / (mu(T) + mui)
+    a0, ap = a(T0), der(a)
+    D0, Dp = D(T0), der(D)
+    mu0, mup = mu(T0), der(mu)
+
+    E0 = GT / (n0 * (mu0 + mui))
+    Gam0 = -(1.0 - a0) * GT
+    me0, mep, De0, Dep = mue(T0), der(mue), De(T0), der(De)
+    L0 = tab.at("lossN", T0) * N
+    Lp = tab.slope("lossN", T0) * N
+    nup = tab.slope("nu_izN", T0) * N
+    ik = 1j * k
+    # continuity: Gamma = -a d_x(n D) - (1 - a) Gamma_T, source n (nu_i - nu_w)
+    A11 = -a0 * k * k * D0
+    A12 = -a0 * k * k * n0 * Dp - ik * ap * GT + n0 * nup
+    # field (eq. 17) and fluxes
+    # E = -d_x(n D)/(n mu) + Gamma_T/(n (mu + mu_i))
+    dE_dn = -ik * D0 / (n0 * mu0) - E0 / n0
+    dE_dT = -ik * Dp / mu0 - E0 * mup / (mu0 + mui)
+    dG_dn = -a0 * ik * D0
+    dG_dT = -a0 * ik * n0 * Dp + ap * GT
+    dH_dn = -1.5 * (me0 * dE_dn * n0 * T0 + me0 * E0 * T0) - 1.5 * ik * De0 * T0
+    dH_dT = -1.5 * (mep * E0 * n0 * T0 + me0 * dE_dT * n0 * T0 + me0 * E0 * n0) - 1.5 * ik * n0 * (De0 + Dep * T0)
+    dP_dn = -(dG_dn * E0 + Gam0 * dE_dn)
+    dP_dT = -(dG_dT * E0 + Gam0 * dE_dT)
+    B1 = -ik * dH_dn + dP_dn - L0
+    B2 = -ik * dH_dT + dP_dT - n0 * Lp
+    M = np.array([[1.0, 0.0], [1.5 * T0, 1.5 * n0]], complex)
+    A = np.array([[A11, A12], [B1, B2]], complex)
+    lam, vec = np.linalg.eig(np.linalg.solve(M, A))
+    W = lam / (-1j)
+    i = int(np.argmax(W.imag))
+    if vector:
+        return float(W[i].imag), float(W[i].real), vec[:, i]
+    return float(W[i].imag), float(W[i].real)
+
+
+def dispersion_max(tab: Table, h: Homogeneous, L: float, m_max: int = 256) -> dict:
+    """Fastest-growing mode m = 1..m_max of a periodic column of length L (full linearisation)."""
+    best = max(range(1, m_max + 1), key=lambda m: dispersion(tab, h, 2 * math.pi * m / L)[0])
+    k = 2 * math.pi * best / L
+    g, om = dispersion(tab, h, k)
+    return dict(m=best, lam=L / best, gamma=g, v_ph=om / k)
+
+
 def observables(t: np.ndarray, modes: np.ndarray, L: float) -> dict:
     """Striation observables from a record of modes: t (snapshot times, increasing),
     modes [snap, 1 + M] complex with entry 0 the mean density."""
@@ -229,20 +305,18 @@ def initial_state(N: int, h: Homogeneous, seed: int, amp: float = 1e-3):
     return n, T
 
 
-def fluid_columns(states: Sequence[Homogeneous], L_m: float, n_cells: int, pair: bool | None = None) -> List[dict]:
-    """Fluid columns of the homogeneous states: pair losses for imposed-field states (the
-    particle model's pair-loss column), the wall loss of eq. 2 for tube states (pair=None)."""
+def fluid_columns(states: Sequence[Homogeneous], L_m: float, n_cells: int, pair: bool = True) -> List[dict]:
+    """Fluid columns of the homogeneous states.  pair=True (default): losses equal to the
+    ionization of the column at every step (the particle model's pair removal; a fixed nu_w
+    lets the mean density run away once striations change the mean ionization); pair=False:
+    nu_w fixed at the homogeneous value (eq. 3 as written; used for the linear phase)."""
     from . import FLUID_LOSS_FIXED, FLUID_LOSS_PAIR
-    out = []
-    for h in states:
-        pr = (math.isnan(h.R_m)) if pair is None else pair
-        out.append(dict(L_m=L_m, N_gas_m3=h.N_gas, mu_iN=h.mu_i * h.N_gas, Gamma_T=h.Gamma_T, nu_w=h.nu_w,
-                        n_cells=n_cells, loss=FLUID_LOSS_PAIR if pr else FLUID_LOSS_FIXED))
-    return out
+    return [dict(L_m=L_m, N_gas_m3=h.N_gas, mu_iN=h.mu_i * h.N_gas, Gamma_T=h.Gamma_T, nu_w=h.nu_w,
+                 n_cells=n_cells, loss=FLUID_LOSS_PAIR if pair else FLUID_LOSS_FIXED) for h in states]
 
 
 def fluid_screen(records, states: Sequence[Homogeneous], L_m: float = 0.30, n_cells: int = 4096,
-                 dt: float = 2e-8, steps: int = 20000, diag_every: int = 100, n_modes: int = 64,
+                 dt: float = 2e-9, steps: int = 20000, diag_every: int = 100, n_modes: int = 64,
                  seed: int = 11, n_T: int = 128, closure=None) -> dict:
     """Advance one fluid column per state for `steps` steps; return the observables per
     column, the device time and the number of kernel launches."""
@@ -334,7 +408,7 @@ def _cathode_v(v_ph: float, frame: str) -> float:
 
 def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 1.0, L_m: float = 0.10,
           n_cells: int = 2048, particles: int = 1_000_000, windows: int = 200, window: int = 4000,
-          early: int = 100, early_window: int = 1000, agg: int = 4, fluid_dt: float = 2e-8, fluid_diag: int = 2,
+          early: int = 100, early_window: int = 1000, agg: int = 4, fluid_dt: float = 2e-9, fluid_diag: int = 20,
           train_steps: int = 3000, batch: int = 8192, lr: float = 1e-3, period: int = 10,
           components=(0.0, 0.0, 1.0), nu_bound: float = 1.0, seed: int = 7, log=print) -> dict:
     """Particle model (one GPU batch: comparison and training fields), closure training on
@@ -435,8 +509,7 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
     mask = np.asarray(components, np.float32)
     out = {}
     clo_args = (net, period, fs, ts * mask, nu_bound)
-    variants = (("fluid", True, None), ("fluid_closure", True, clo_args),
-                ("fluid_fixed", False, None), ("fluid_fixed_closure", False, clo_args))
+    variants = (("fluid", True, None), ("fluid_closure", True, clo_args))
     for name, pair, clo in variants:
         f = Fluid(fluid_columns(states, L_m, n_cells, pair=pair), records, n_T=128, dt_s=fluid_dt,
                   diag_every=diag, n_modes=M)
@@ -458,10 +531,11 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
     for o in pic_obs:
         o["v_ph"] = _cathode_v(o["v_ph"], "pic")
     lin = [linear(tab, h) for h in states]
+    full = [dispersion_max(tab, h, L_m) for h in states]
     pic_per_col = pic_run / len(Es)
     return dict(E_compare=list(E_compare), E_train=list(E_train), mu_iN=mu, pic=pic_obs,
-                fluid=out["fluid"]["obs"], fluid_closure=out["fluid_closure"]["obs"],
-                fluid_fixed=out["fluid_fixed"]["obs"], fluid_fixed_closure=out["fluid_fixed_closure"]["obs"], linear=lin,
+                fluid=out["fluid"]["obs"], fluid_closure=out["fluid_closure"]["obs"], linear=lin,
+                dispersion=full,
                 pic_seconds_per_column=pic_per_col,
                 fluid_seconds_per_column=out["fluid"]["ms"] / 1e3 / ncmp,
                 fluid_closure_seconds_per_column=out["fluid_closure"]["ms"] / 1e3 / ncmp,
@@ -491,17 +565,30 @@ def main(argv=None) -> int:
     import argparse
     import json
     ap = argparse.ArgumentParser(prog="python -m paper_2202_03215_gb300.screen")
-    ap.add_argument("what", choices=["study"])
+    ap.add_argument("what", choices=["study", "fluid"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--nu-bound", type=float, default=0.5)
+    ap.add_argument("--columns", type=int, default=152)
+    ap.add_argument("--cells", type=int, default=4096)
+    ap.add_argument("--steps", type=int, default=200)
     a = ap.parse_args(argv)
+    if a.what == "fluid":
+        # a fluid screen of imposed fields 6..20 V/cm/Torr (neon, 1 Torr, L = 10 cm): time per step
+        recs = transport()
+        tab = Table(recs)
+        states = [homogeneous_E0(tab, e, 1.0) for e in np.linspace(6.0, 20.0, a.columns)]
+        r = fluid_screen(recs, states, L_m=0.10, n_cells=a.cells, steps=a.steps, diag_every=50)
+        print(f"fluid: {a.columns} columns x {a.cells} cells, {a.steps} steps in {r['ms']:.2f} ms "
+              f"({r['launches']} launches)", flush=True)
+        return 0
     r = study([6, 8, 10, 12, 14, 16, 18, 20], [7, 9, 11, 13, 15, 17, 19, 21], nu_bound=a.nu_bound,
               log=lambda s: print(s, flush=True))
     for k, e in enumerate(r["E_compare"]):
-        p, f, g = r["pic"][k], r["fluid_fixed"][k], r["fluid_fixed_closure"][k]
+        p, f, g, l, d = r["pic"][k], r["fluid"][k], r["fluid_closure"][k], r["linear"][k], r["dispersion"][k]
         print(f"E0/p={e}: PIC lam={p['lam'] * 100:.3g} cm v={p['v_ph']:.3g} m/s g={p['gamma']:.3g}/s | "
-              f"fluid lam={f['lam'] * 100:.3g} v={f['v_ph']:.3g} | fluid+closure lam={g['lam'] * 100:.3g} "
-              f"v={g['v_ph']:.3g}", flush=True)
+              f"fluid lam={f['lam'] * 100:.3g} v={f['v_ph']:.3g} g={f['gamma']:.3g} | fluid+closure "
+              f"lam={g['lam'] * 100:.3g} v={g['v_ph']:.3g} | eq.22 lam={l['lam'] * 100:.3g} v={l['v_ph']:.3g} "
+              f"g={l['gamma_max']:.3g} | full linear lam={d['lam'] * 100:.3g} g={d['gamma']:.3g}", flush=True)
     print("speed ratio (particle / fluid per column):",
           r["pic_seconds_per_column"] / r["fluid_seconds_per_column"], flush=True)
     if a.out:

@@ -155,7 +155,7 @@ def config_neon_column(seed: int = 1, precision: int = MIXED, n_per_species: int
     p = Params(gas_mass_amu=AMU_NE, L_m=0.30, R_m=0.01, drive=DRIVE_E0, E0_Vpm=E0_Vpm,
                V_applied=0.0, xsec=neon_xsecs(), n_cells=16384, dt_s=4e-11,
                n_e0=n_per_species, n_i0=n_per_species, precision=precision, seed=seed,
-               eps_max_e_eV=200.0, sort_every=1000, diag_every=0)
+               eps_max_e_eV=200.0, sort_every=250, diag_every=0)
     return p.with_(**kw) if kw else p
 
 
