@@ -19,6 +19,7 @@
 #include "pic.h"
 
 int mlp_forward_async(pic_mlp *h, const float *X, int n, float *Y, cudaStream_t st);
+int mlp_take_status(pic_mlp *h);
 
 namespace {
 
@@ -35,7 +36,7 @@ constexpr float kTd = 1e-21f;
 struct ColK {
   int N, logN;
   long long off;       // first cell in the state arrays
-  float dx, r, s, k;   // dx, dt/dx^2, dt/dx, 3/(2 dx)
+  float dx, inv_dx, r, s, k;   // dx, 1/dx, dt/dx^2, dt/dx, 3/(2 dx)
   float GT, nu_w, mu_i, Ng, invNg;
   int pair;            // nu_w = <n nu>/<n> every step
 };
@@ -87,6 +88,7 @@ __device__ __forceinline__ void add2(float &hi, float &lo, float d) {
 }
 
 // periodic parallel cyclic reduction; N a power of two; row j: pa x_{j-1} + pb x_j + pc x_{j+1} = pd
+// (fast divisions, a few ulp: the systems are diagonally dominant and well conditioned)
 __device__ void pcr(const Sm &S, int N) {
   const int t = threadIdx.x;
   for (int s = 1; s < N; s <<= 1) {
@@ -96,7 +98,7 @@ __device__ void pcr(const Sm &S, int N) {
       const int j = t + r * kThreads;
       if (j < N) {
         const int jm = (j - s) & (N - 1), jp = (j + s) & (N - 1);
-        const float al = -S.pa[j] / S.pb[jm], be = -S.pc[j] / S.pb[jp];
+        const float al = -__fdividef(S.pa[j], S.pb[jm]), be = -__fdividef(S.pc[j], S.pb[jp]);
         na[r] = al * S.pa[jm];
         nc[r] = be * S.pc[jp];
         nb[r] = S.pb[j] + al * S.pc[jm] + be * S.pa[jp];
@@ -131,7 +133,7 @@ __device__ void coeffs(const Sm &S, const FluidK &K, const ColK &c) {
     tpos(K, S.T[j], i, f);
     const float mu_e = tq(S, K, 0, i, f) * c.invNg;
     S.D[j] = tq(S, K, 1, i, f) * c.invNg;
-    S.A[j] = c.mu_i / (mu_e + c.mu_i);
+    S.A[j] = __fdividef(c.mu_i, mu_e + c.mu_i);
     S.B[j] = mu_e;
   }
 }
@@ -146,7 +148,7 @@ __device__ void field(const Sm &S, const ColK &c) {
     const float nf = 0.5f * (S.n[j] + S.n[jp]);
     const float muf = 0.5f * (S.B[j] + S.B[jp]);
     const float mf = 0.5f * ((S.B[j] + c.mu_i) + (S.B[jp] + c.mu_i));
-    S.E[j] = -(nD1 - nD0) / (c.dx * nf * muf) + c.GT / (nf * mf);
+    S.E[j] = -__fdividef(nD1 - nD0, c.dx * nf * muf) + __fdividef(c.GT, nf * mf);
   }
 }
 
@@ -217,7 +219,7 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
   }
   __syncthreads();
   pcr(S, N);
-  for (int j = t; j < N; j += kThreads) add2(S.n[j], S.nl[j], S.pd[j] / (S.pa[j] + S.pb[j] + S.pc[j]));
+  for (int j = t; j < N; j += kThreads) add2(S.n[j], S.nl[j], __fdividef(S.pd[j], S.pa[j] + S.pb[j] + S.pc[j]));
   __syncthreads();
   // 3. flux and field at faces from n'; energy coefficients into pa (mu_eps), pb (D_eps)
   field(S, c);
@@ -225,7 +227,7 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
     const int jp = (j + 1) & (N - 1);
     const float af = 0.5f * (S.A[j] + S.A[jp]);
     const float bf = 1.0f - af;
-    float g = -af * (S.n[jp] * S.D[jp] - S.n[j] * S.D[j]) / c.dx - bf * c.GT;
+    float g = -af * (S.n[jp] * S.D[jp] - S.n[j] * S.D[j]) * c.inv_dx - bf * c.GT;
     if (has_corr) g += S.G[j];
     S.G[j] = g;
     int i; float f;
@@ -283,7 +285,7 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
   }
   pcr(S, N);
   for (int j = t; j < N; j += kThreads) {
-    add2(S.T[j], S.Tl[j], S.pd[j] / (S.pa[j] + S.pb[j] + S.pc[j]));
+    add2(S.T[j], S.Tl[j], __fdividef(S.pd[j], S.pa[j] + S.pb[j] + S.pc[j]));
     if (S.T[j] < K.T0) { S.T[j] = K.T0; S.Tl[j] = 0.0f; }
     if (S.T[j] > K.Tmax) { S.T[j] = K.Tmax; S.Tl[j] = 0.0f; }
   }
@@ -547,6 +549,7 @@ int pic_fluid_init(const pic_fluid_column *cols, int n_cols, const pic_transport
     k.off = off;
     const double dx = p.L_m / p.n_cells;
     k.dx = (float)dx;
+    k.inv_dx = (float)(1.0 / dx);
     k.r = (float)(dt_s / (dx * dx));
     k.s = (float)(dt_s / dx);
     k.k = (float)(1.5 / dx);
@@ -614,7 +617,7 @@ int pic_fluid_step(pic_fluid *f, int64_t n_steps) {
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, f->e0, f->e1);
   f->last_ms = ms;
-  return 0;
+  return f->net ? mlp_take_status(f->net) : 0;
 }
 
 int pic_fluid_modes(pic_fluid *f, float *out, int max_snaps, int *n_snaps) {

@@ -293,127 +293,6 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
   }
 }
 
-// ---------------------------------------------------------------------------
-// Inference: persistent warps, each taking 16 samples at a time.  The weights sit
-// in shared memory as BF16 once per block (rows padded by 8 elements so that the
-// 8 rows a fragment load touches fall in distinct banks); inputs go from global
-// memory straight into A fragments; each layer's accumulators, after bias and
-// GELU, are repacked in registers as the next layer's A fragments (the m16n8k16
-// C layout of two adjacent 8-column tiles is the A layout of one 16-wide k slice),
-// so activations never touch shared memory.
-constexpr int FW1 = NIP + 8, FW2 = NH + 8;   // padded row strides (bf16 elements)
-constexpr int FWD_WARPS = 8;
-
-struct FwdSmem {
-  bf W1[NH][FW1];
-  bf W2[NH][FW2];
-  bf W3[8][FW2];
-  float b1[NH], b2[NH], b3[8];
-};
-
-// gelu(z) = z / (1 + exp(-2u)), u = sqrt(2/pi) (z + 0.044715 z^3): the tanh form
-// rewritten with 1 + tanh(u) = 2 / (1 + exp(-2u))
-__device__ __forceinline__ float gelu_fast(float z) {
-  const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
-  return __fdividef(z, 1.0f + __expf(-2.0f * u));   // a few ulp: far below one BF16 ulp
-}
-
-__device__ __forceinline__ unsigned pack2(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x = lo (low half), .y = hi
-  return *reinterpret_cast<const unsigned *>(&v);
-}
-
-__device__ __forceinline__ unsigned ld2(const bf *p) { return *reinterpret_cast<const unsigned *>(p); }
-
-__global__ void __launch_bounds__(FWD_WARPS * 32) k_mlp_fwd(const float *__restrict__ P, const float *__restrict__ X,
-                                                           int n, float *__restrict__ Y) {
-  __shared__ __align__(16) FwdSmem sm;
-  const int tid = threadIdx.x, lane = tid & 31, g = lane >> 2, t = lane & 3;
-  for (int q = tid; q < NH * FW1; q += blockDim.x) {
-    const int h = q / FW1, i = q % FW1;
-    sm.W1[h][i] = __float2bfloat16_rn(i < NI ? P[oW1 + h * NI + i] : 0.0f);
-  }
-  for (int q = tid; q < NH * FW2; q += blockDim.x) {
-    const int h = q / FW2, k = q % FW2;
-    sm.W2[h][k] = __float2bfloat16_rn(k < NH ? P[oW2 + h * NH + k] : 0.0f);
-  }
-  for (int q = tid; q < 8 * FW2; q += blockDim.x) {
-    const int o = q / FW2, k = q % FW2;
-    sm.W3[o][k] = __float2bfloat16_rn(o < NO && k < NH ? P[oW3 + o * NH + k] : 0.0f);
-  }
-  for (int q = tid; q < NH; q += blockDim.x) { sm.b1[q] = P[ob1 + q]; sm.b2[q] = P[ob2 + q]; }
-  if (tid < 8) sm.b3[tid] = tid < NO ? P[ob3 + tid] : 0.0f;
-  __syncthreads();
-  const int chunks = (n + 15) / 16;
-  const int wstride = gridDim.x * (blockDim.x >> 5);
-  for (int ch = blockIdx.x * (blockDim.x >> 5) + (tid >> 5); ch < chunks; ch += wstride) {
-    const int s0 = ch * 16, sa = s0 + g, sb = s0 + g + 8;
-    // layer 1: A fragment straight from the inputs (column 15 is the zero pad)
-    auto xin = [&](int s, int i) -> float { return (s < n && i < NI) ? X[(size_t)s * NI + i] : 0.0f; };
-    unsigned a1[4];
-    a1[0] = pack2(xin(sa, 2 * t), xin(sa, 2 * t + 1));
-    a1[1] = pack2(xin(sb, 2 * t), xin(sb, 2 * t + 1));
-    a1[2] = pack2(xin(sa, 2 * t + 8), xin(sa, 2 * t + 9));
-    a1[3] = pack2(xin(sb, 2 * t + 8), xin(sb, 2 * t + 9));
-    float c[16][4];
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      const float bl = sm.b1[8 * nt + 2 * t], bh = sm.b1[8 * nt + 2 * t + 1];
-      c[nt][0] = bl; c[nt][1] = bh; c[nt][2] = bl; c[nt][3] = bh;
-      unsigned b[2];
-      b[0] = ld2(&sm.W1[8 * nt + g][2 * t]);
-      b[1] = ld2(&sm.W1[8 * nt + g][2 * t + 8]);
-      mma(c[nt], a1, b);
-    }
-    unsigned a[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      a[j][0] = pack2(gelu_fast(c[2 * j][0]), gelu_fast(c[2 * j][1]));
-      a[j][1] = pack2(gelu_fast(c[2 * j][2]), gelu_fast(c[2 * j][3]));
-      a[j][2] = pack2(gelu_fast(c[2 * j + 1][0]), gelu_fast(c[2 * j + 1][1]));
-      a[j][3] = pack2(gelu_fast(c[2 * j + 1][2]), gelu_fast(c[2 * j + 1][3]));
-    }
-    // layer 2
-#pragma unroll
-    for (int nt = 0; nt < 16; ++nt) {
-      const float bl = sm.b2[8 * nt + 2 * t], bh = sm.b2[8 * nt + 2 * t + 1];
-      c[nt][0] = bl; c[nt][1] = bh; c[nt][2] = bl; c[nt][3] = bh;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-#pragma unroll
-      for (int nt = 0; nt < 16; ++nt) {
-        unsigned b[2];
-        b[0] = ld2(&sm.W2[8 * nt + g][16 * j + 2 * t]);
-        b[1] = ld2(&sm.W2[8 * nt + g][16 * j + 2 * t + 8]);
-        mma(c[nt], a[j], b);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      a[j][0] = pack2(gelu_fast(c[2 * j][0]), gelu_fast(c[2 * j][1]));
-      a[j][1] = pack2(gelu_fast(c[2 * j][2]), gelu_fast(c[2 * j][3]));
-      a[j][2] = pack2(gelu_fast(c[2 * j + 1][0]), gelu_fast(c[2 * j + 1][1]));
-      a[j][3] = pack2(gelu_fast(c[2 * j + 1][2]), gelu_fast(c[2 * j + 1][3]));
-    }
-    // layer 3: one 8-column tile (outputs 0..2)
-    float y[4];
-    y[0] = sm.b3[2 * t]; y[1] = sm.b3[2 * t + 1]; y[2] = y[0]; y[3] = y[1];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      unsigned b[2];
-      b[0] = ld2(&sm.W3[g][16 * j + 2 * t]);
-      b[1] = ld2(&sm.W3[g][16 * j + 2 * t + 8]);
-      mma(y, a[j], b);
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int o = 2 * t + (e & 1), s = (e < 2) ? sa : sb;
-      if (o < NO && s < n) Y[(size_t)s * NO + o] = y[e];
-    }
-  }
-}
-
 // g[p] = sum over tiles of the partials, in tile order; loss likewise (block 0)
 __global__ void k_mlp_reduce(const float *__restrict__ gpart, const float *__restrict__ lpart, int ntiles,
                              float *__restrict__ grad, double *__restrict__ loss, float inv_n3) {
@@ -445,10 +324,13 @@ __global__ void k_mlp_adam(float *__restrict__ P, const float *__restrict__ grad
 
 }  // namespace
 
+int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status, cudaStream_t st);
+
 struct pic_mlp {
   float *P = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
   float *gpart = nullptr, *lpart = nullptr;
   double *loss = nullptr;
+  int *status = nullptr;   // device: 1 once a bounded wait of the tensor-core forward gave up
   int cap_tiles = 0;
   int t = 0;   // Adam steps taken
 };
@@ -470,18 +352,7 @@ int ensure(pic_mlp *h, int n) {
 }
 
 int run_forward(pic_mlp *h, const float *X, int n, float *Y, cudaStream_t st) {
-  if (n <= 0) return PIC_EINVAL;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  const int chunks = (n + 15) / 16;
-  const int blocks = std::max(1, std::min((chunks + FWD_WARPS - 1) / FWD_WARPS, 4 * sms));
-  k_mlp_fwd<<<blocks, FWD_WARPS * 32, 0, st>>>(h->P, X, n, Y);
-  return cudaGetLastError() == cudaSuccess ? 0 : PIC_ECUDA;
+  return mlp_forward_tc(h->P, X, n, Y, h->status, st);
 }
 
 int run_tiles(pic_mlp *h, const float *X, const float *T, int n, float *Y, int mode, cudaStream_t st) {
@@ -508,6 +379,16 @@ uint64_t splitmix(uint64_t &x) {
 
 }  // namespace
 
+// PIC_ETIMEOUT (and the flag cleared) if a bounded wait of a forward pass gave up since the
+// last call; synchronous (the handle's work must have completed)
+int mlp_take_status(pic_mlp *h) {
+  int st = 0;
+  if (cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+  if (!st) return 0;
+  cudaMemset(h->status, 0, sizeof(int));
+  return PIC_ETIMEOUT;
+}
+
 // forward pass enqueued on st without synchronising (used by the fluid closure)
 int mlp_forward_async(pic_mlp *h, const float *X, int n, float *Y, cudaStream_t st) {
   if (!h || !X || !Y) return PIC_EINVAL;
@@ -525,7 +406,7 @@ int pic_mlp_create(uint64_t seed, pic_mlp **out) {
   if (!h) return PIC_ENOMEM;
   if (cudaMalloc(&h->P, NPARAM * 4) != cudaSuccess || cudaMalloc(&h->m, NPARAM * 4) != cudaSuccess ||
       cudaMalloc(&h->v, NPARAM * 4) != cudaSuccess || cudaMalloc(&h->grad, NPARAM * 4) != cudaSuccess ||
-      cudaMalloc(&h->loss, 8) != cudaSuccess) {
+      cudaMalloc(&h->loss, 8) != cudaSuccess || cudaMalloc(&h->status, sizeof(int)) != cudaSuccess) {
     pic_mlp_free(h);
     return PIC_ENOMEM;
   }
@@ -541,6 +422,7 @@ int pic_mlp_create(uint64_t seed, pic_mlp **out) {
   cudaMemcpy(h->P, P.data(), NPARAM * 4, cudaMemcpyHostToDevice);
   cudaMemset(h->m, 0, NPARAM * 4);
   cudaMemset(h->v, 0, NPARAM * 4);
+  cudaMemset(h->status, 0, sizeof(int));
   *out = h;
   return 0;
 }
@@ -549,6 +431,7 @@ void pic_mlp_free(pic_mlp *h) {
   if (!h) return;
   cudaFree(h->P); cudaFree(h->m); cudaFree(h->v); cudaFree(h->grad); cudaFree(h->gpart); cudaFree(h->lpart);
   cudaFree(h->loss);
+  cudaFree(h->status);
   delete h;
 }
 
@@ -571,7 +454,8 @@ int pic_mlp_forward(pic_mlp *h, const float *X, int n, float *Y, void *stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int rc = run_forward(h, X, n, Y, st);
   if (rc) return rc;
-  return cudaStreamSynchronize(st) == cudaSuccess ? 0 : PIC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PIC_ECUDA;
+  return mlp_take_status(h);
 }
 
 int pic_mlp_grad(pic_mlp *h, const float *X, const float *T, int n, float *grad_host, double *loss, void *stream) {
