@@ -60,6 +60,8 @@ extern "C" {
 #define PIC_DRIVE_CIRCUIT 2  /* Sec. V: external circuit, E0 = (U_src - R_ext J) / L after every step,
                                 J = e w (sum v_x,ions - sum v_x,electrons) / L over the pushed particles
                                 (ions at their last push; velocities summed as round(256 v_x), exact) */
+#define PIC_DRIVE_RI 3       /* tube radius R_m and current I_A (eq. 2): E0 and n0 from pic_drive_ri at
+                                pic_init, then run as PIC_DRIVE_E0 (E0_Vpm and n0_m3 are ignored) */
 
 /* field: self-consistent (Sec. II) or the applied field alone (uniform-field swarm) */
 #define PIC_FIELD_POISSON 0
@@ -418,6 +420,18 @@ int pic_fluid_features(pic_fluid *f, float *X_dev);
 int pic_fluid_elapsed(pic_fluid *f, double *ms, int64_t *launches);
 void *pic_fluid_stream(pic_fluid *f);
 void pic_fluid_free(pic_fluid *f);
+
+/* The (R, I) drive (Sec. II, eq. 2; the paper imposes E0 and recovers R from eq. 2): the field E0
+ * of a homogeneous column of radius R whose ionization balances ambipolar diffusion to the wall,
+ * nu_iz(E0/N) = D_a (2.405/R)^2 with D_a = mu_i D_e/mu_e, and the density carrying the current
+ * I: J = I/(pi R^2) = e n0 (mu_e + mu_i) E0.  Electron transport from pic_two_term on the
+ * params' electron cross sections (energy grid up to eps_max_e_eV); ion mobility from the ion
+ * cross sections in the low-field Chapman-Enskog first approximation,
+ * mu_i = 3e/(16 N Omega) sqrt(2 pi/(mu_r k T_gas)), mu_r = M/2, Omega = 2 sigma_cx + sigma_iso at
+ * the mean thermal relative energy 8 k T_gas/(pi e) (charge exchange reverses the relative
+ * velocity).  out: E0 (V/m), n0 (1/m^3), Te0 = 2/3 of the mean energy (eV), mu_i N (1/(V m s)).
+ * Host code.  Errors: PIC_EINVAL (bad arguments, no ion process, no root in 1..2000 Td). */
+int pic_drive_ri(const pic_params *p, double out[4]);
 
 /* Self-test hook: int128 -> double conversion used by the field solve, run
  * on the device: v_k = hi[k] 2^64 + lo[k]; out[k] = double nearest to v_k

@@ -144,6 +144,7 @@ def lib() -> C.CDLL:
         L.pic_fluid_stream.restype = C.c_void_p
         L.pic_fluid_free.argtypes = [C.c_void_p]
         L.pic_fluid_free.restype = None
+        L.pic_drive_ri.argtypes = [C.POINTER(Params), _D]
         L.pic_set_timing.argtypes = [C.c_void_p, C.c_int]
         L.pic_kernel_times.argtypes = [C.c_void_p, _D, _I64]
         _lib = L
@@ -206,6 +207,14 @@ def make_params(p):
     st.n_xsec = len(p.xsec)
     st.xsec = C.cast(xs, C.POINTER(Xsec))
     return st, keep
+
+
+def drive_ri(p) -> dict:
+    """pic_drive_ri: E0, n0, Te0 and the ion mobility x N of the (R, I) drive of params p."""
+    st, keep = make_params(p)
+    out = np.zeros(4)
+    _check(lib().pic_drive_ri(C.byref(st), _ptr(out, _D)))
+    return dict(E0_Vpm=out[0], n0_m3=out[1], Te0_eV=out[2], mu_iN=out[3])
 
 
 def i128_to_double(values) -> np.ndarray:

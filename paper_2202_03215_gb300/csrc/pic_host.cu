@@ -423,6 +423,18 @@ void free_all(pic_handle *h) {
   if (h->stream) cudaStreamDestroy(h->stream);
 }
 
+// (R, I) drive: the E0-drive parameters of the same column (E0 and n0 from pic_drive_ri)
+int resolve_ri(const pic_params *p, pic_params *q) {
+  double v[4];
+  const int rc = pic_drive_ri(p, v);
+  if (rc) return rc;
+  *q = *p;
+  q->drive = PIC_DRIVE_E0;
+  q->E0_Vpm = v[0];
+  q->n0_m3 = v[1];
+  return 0;
+}
+
 int validate(const pic_params *p) {
   if (!p) return set_err(nullptr, PIC_EINVAL, "params is NULL");
   if (p->n_cells < 3 || p->n_cells > 65536) return set_err(nullptr, PIC_EINVAL, "n_cells must be in [3, 65536]");
@@ -690,6 +702,11 @@ const char *pic_last_error(pic_handle *h) { return h ? h->err.c_str() : g_err.c_
 int pic_init(const pic_params *params, pic_handle **out) {
   if (!out) return set_err(nullptr, PIC_EINVAL, "out is NULL");
   *out = nullptr;
+  pic_params ri;
+  if (params && params->drive == PIC_DRIVE_RI) {   // resolve (R, I) -> (E0, n0), then run as the E0 drive
+    if (resolve_ri(params, &ri)) return set_err(nullptr, PIC_EINVAL, "the (R, I) drive has no solution");
+    params = &ri;
+  }
   int rc = validate(params);
   if (rc) return rc;
   pic_handle *h = new (std::nothrow) pic_handle();
@@ -820,6 +837,16 @@ int pic_kernel_times(pic_handle *h, double *ms, int64_t *launches) {
 int pic_init_batch(const pic_params *params, int n, pic_handle **out) {
   if (!out || !params || n < 1 || n > 4096) return set_err(nullptr, PIC_EINVAL, "bad arguments");
   *out = nullptr;
+  std::vector<pic_params> resolved;
+  for (int i = 0; i < n; ++i)
+    if (params[i].drive == PIC_DRIVE_RI) {
+      resolved.assign(params, params + n);
+      for (int k = 0; k < n; ++k)
+        if (resolved[k].drive == PIC_DRIVE_RI && resolve_ri(&params[k], &resolved[k]))
+          return set_err(nullptr, PIC_EINVAL, "the (R, I) drive of column %d has no solution", k);
+      params = resolved.data();
+      break;
+    }
   for (int i = 0; i < n; ++i) {
     const int rc = validate(&params[i]);
     if (rc) return rc;

@@ -234,3 +234,61 @@ extern "C" int pic_two_term(const pic_xsec *xs, int n_xsec, double gas_mass_amu,
   }
   return 0;
 }
+
+namespace {
+
+constexpr double kKb = 1.380649e-23;
+constexpr double kTorr = 133.32236842105263;
+constexpr double kPi = 3.14159265358979323846;
+
+}  // namespace
+
+extern "C" int pic_drive_ri(const pic_params *p, double out[4]) {
+  if (!p || !out || !(p->R_m > 0.0) || !(p->I_A > 0.0) || !(p->pressure_torr > 0.0) || !(p->T_gas_K > 0.0) ||
+      !(p->gas_mass_amu > 0.0) || !(p->eps_max_e_eV > 0.0) || p->n_xsec <= 0 || !p->xsec)
+    return PIC_EINVAL;
+  const double N = p->pressure_torr * kTorr / (kKb * p->T_gas_K);
+  const double M = p->gas_mass_amu * kAmu;
+  // ion mobility: momentum-transfer cross section at the mean thermal relative energy
+  const double eps_th = 8.0 * kKb * p->T_gas_K / (kPi * kQe);
+  double omega = 0.0;
+  for (int k = 0; k < p->n_xsec; ++k) {
+    const pic_xsec &x = p->xsec[k];
+    if (x.n < 1 || !x.energy_eV || !x.sigma_m2) return PIC_EINVAL;
+    if (x.kind == PIC_ION_CX) omega += 2.0 * sigma_lin(x, eps_th);
+    if (x.kind == PIC_ION_ISO) omega += sigma_lin(x, eps_th);
+  }
+  if (!(omega > 0.0)) return PIC_EINVAL;
+  const double mu_i = 3.0 * kQe / (16.0 * N * omega) * std::sqrt(2.0 * kPi / (0.5 * M * kKb * p->T_gas_K));
+  const double g2 = (2.405 / p->R_m) * (2.405 / p->R_m);
+  pic_transport tr;
+  // balance f(E/N) = N nu_izN - (mu_i N / N)(DN / muN)(2.405/R)^2: negative below, positive above
+  auto f = [&](double EN, int &rc) {
+    rc = pic_two_term(p->xsec, p->n_xsec, p->gas_mass_amu, &EN, 1, p->eps_max_e_eV, 800, &tr);
+    return N * tr.nu_izN - mu_i * (tr.DN / tr.muN) * g2;
+  };
+  int rc = 0;
+  double lo = std::log(1.0), hi = std::log(2000.0);
+  const double flo = f(std::exp(lo), rc);
+  if (rc) return rc;
+  const double fhi = f(std::exp(hi), rc);
+  if (rc) return rc;
+  if (!(flo < 0.0 && fhi > 0.0)) return PIC_EINVAL;
+  for (int it = 0; it < 40; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    const double fm = f(std::exp(mid), rc);
+    if (rc) return rc;
+    if (fm < 0.0) lo = mid; else hi = mid;
+  }
+  const double EN = std::exp(0.5 * (lo + hi));
+  f(EN, rc);
+  if (rc) return rc;
+  const double E0 = EN * kTd * N;
+  const double mu_e = tr.muN / N;
+  const double J = p->I_A / (kPi * p->R_m * p->R_m);
+  out[0] = E0;
+  out[1] = J / (kQe * (mu_e + mu_i) * E0);
+  out[2] = 2.0 / 3.0 * tr.mean_eps_eV;
+  out[3] = mu_i * N;
+  return 0;
+}

@@ -31,7 +31,7 @@ import numpy as np
 # process kinds (same numbering in include/pic.h and the oracle's header)
 ELASTIC, EXCITATION, IONIZATION, ION_CX, ION_ISO = 0, 1, 2, 3, 4
 # drive modes
-DRIVE_E0, DRIVE_V, DRIVE_CIRCUIT = 0, 1, 2
+DRIVE_E0, DRIVE_V, DRIVE_CIRCUIT, DRIVE_RI = 0, 1, 2, 3
 # field modes
 FIELD_POISSON, FIELD_APPLIED = 0, 1
 # loss modes
