@@ -242,6 +242,24 @@ def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: 
             "forward": {"samples": n, "samples_per_s": n / sf, "tflops": MLP_FWD_FLOP * n / sf / 1e12}}
 
 
+def replica_params(w, rank: int, n_per_species: int):
+    """The column of rank `rank` in a multi-GPU run: an independent replica of the neon column
+    (its own seed and RNG column index), no data shared between ranks."""
+    return w.config_neon_column(n_per_species=n_per_species, seed=1 + rank, column=rank)
+
+
+def aggregate(dist, torch, seconds: float, units: int, device: str = "cuda"):
+    """Whole-job figures of a timed region: the slowest rank's time and the units of all ranks
+    (identity without a process group)."""
+    if dist is None:
+        return seconds, units
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -304,7 +322,7 @@ def main():
                "sample": f"{steps_s} oracle steps (FP32-storage build) of {n_s} electrons + {n_s} ions on the "
                          f"same column, {dt:.1f} s of single-thread CPU"}
 
-    p = w.config_neon_column(n_per_species=args.n, seed=1 + rank, column=rank)
+    p = replica_params(w, rank, args.n)
     col = pb.Column(p)
     col.step(args.warmup)
     st0 = col.stats()
@@ -330,12 +348,7 @@ def main():
     units = pushed_steps(st0["step"], args.steps, st0["n_e"], st0["n_i"], p.ion_subcycle)
     assert st1["n_e"] == st0["n_e"] and st1["step"] == st0["step"] + args.steps
     launches = sum(v[1] for v in kt.values())
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        u = torch.tensor([float(units)], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        ms, units = float(t.item()), int(u.item())
+    ms, units = aggregate(dist, torch, ms, units)
     value = units / (ms / 1e3)
 
     # roofline of the dominant kernel (electron step), live from the timed region
@@ -376,12 +389,7 @@ def main():
         t1 = time.perf_counter()
         d2h = sum(v.nbytes for v in mom.values() if isinstance(v, np.ndarray)) + 8 * 40
         secs = t1 - t0
-        if dist:
-            t = torch.tensor([secs], device="cuda")
-            u = torch.tensor([float(local_units)], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(u, op=dist.ReduceOp.SUM)
-            secs, local_units = float(t.item()), int(u.item())
+        secs, local_units = aggregate(dist, torch, secs, local_units)
         e2e = {"value": local_units / secs, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "seconds": secs, "api": "pic_set_state (host arrays) + pic_step(K) + pic_moments + pic_get_stats"}
