@@ -1,7 +1,9 @@
 // Closure-network inference on the 5th-generation tensor cores (tcgen05).
 //
-// One block of 128 threads takes 128 samples at a time (a persistent loop over
-// tiles); thread t owns sample row t.  Each layer is one or eight
+// A block runs G = 4 independent groups of 128 threads; a group takes 128 samples
+// at a time (a persistent loop over tiles) and its thread t owns sample row t.
+// The groups share the weights (loaded once per block) and overlap: while one
+// waits for its MMAs, the others run their epilogues.  Each layer is one or eight
 // tcgen05.mma (kind::f16: BF16 operands, FP32 accumulation) of M = 128 rows,
 // issued by thread 0, with A (activations) and B (weights, [out][in] = N x K,
 // K-major) in shared memory and the accumulator D in tensor memory (128
@@ -13,9 +15,9 @@
 // of D (tcgen05.ld, one lane per row), adds the bias, applies GELU and writes
 // the BF16 activations back as the next layer's A operand.
 //
-// Only thread 0 polls the mbarrier; a block barrier then hands completion to the
-// other threads (which order their tensor-memory reads after it with
-// tcgen05.fence::after_thread_sync), so the waiting threads issue nothing.
+// One thread of each group waits on its mbarrier (a suspending try_wait with a
+// back-off); a named barrier of the group then hands completion to the other threads (which
+// order their tensor-memory reads after it with tcgen05.fence::after_thread_sync).
 // Every wait is bounded: a wait that gives up sets *status and the block
 // stops after freeing its tensor memory.
 #include <cuda_bf16.h>
@@ -32,8 +34,9 @@ constexpr int oW1 = 0, ob1 = NH * NI, oW2 = ob1 + NH, ob2 = oW2 + NH * NH, oW3 =
 constexpr int TM = 128;            // samples per tile = MMA rows = threads per block
 constexpr int K1 = 16;             // input width padded to one MMA K step
 constexpr int N3 = 16;             // output width padded to the smallest N of an M = 128 MMA
-constexpr uint32_t kCols = 128;    // tensor-memory columns of a block
-constexpr int kSpin = 1 << 20;     // polls of an mbarrier before giving up
+constexpr int G = 4;               // groups of TM threads per block
+constexpr uint32_t kCols = 128 * G;   // tensor-memory columns of a block: 128 per group
+constexpr int kSpin = 200000;      // polls of an mbarrier (each suspends up to 10 us, then sleeps) before giving up
 
 using bf = __nv_bfloat16;
 
@@ -42,14 +45,19 @@ __host__ __device__ constexpr int cm_off(int r, int k, int K) {
   return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-struct __align__(1024) TcSmem {
+struct TcGroup {
+  bf X[TM * K1];    // A of layer 1
+  bf H[TM * NH];    // A of layers 2 and 3
+};
+
+struct __align__(128) TcSmem {
   bf W1[NH * K1];   // N = 128 x K = 16
   bf W2[NH * NH];   // 128 x 128
   bf W3[N3 * NH];   // 16 x 128 (rows 3..15 zero)
-  bf X[TM * K1];    // A of layer 1
-  bf H[TM * NH];    // A of layers 2 and 3
+  TcGroup g[G];
   float b1[NH], b2[NH], b3[N3];
-  unsigned long long mbar;
+  unsigned long long mbar[G];
+  int ok[G];
   uint32_t tmem_slot;
 };
 
@@ -84,11 +92,12 @@ __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
   for (int it = 0; it < kSpin; ++it) {
     uint32_t done;
     asm volatile(
-        "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.b32 %0, 1, 0, P;\n}\n"
+        "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, 10000;\nselp.b32 %0, 1, 0, P;\n}\n"
         : "=r"(done)
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
+    __nanosleep(64);
   }
   return false;
 }
@@ -110,10 +119,14 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// gelu(z) = z / (1 + exp(-2u)), u = sqrt(2/pi) (z + 0.044715 z^3): the tanh form
+// gelu(z) = z/2 (1 + tanh u), u = sqrt(2/pi) z (1 + 0.044715 z^2), with the hardware tanh
+// (tanh.approx.f32, relative error about 2^-11: below half a BF16 ulp of the stored activation)
 __device__ __forceinline__ float gelu(float z) {
-  const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
-  return __fdividef(z, 1.0f + __expf(-2.0f * u));
+  const float u = 0.7978845608028654f * z * (1.0f + 0.044715f * z * z);
+  float th;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(u));
+  const float h = 0.5f * z;
+  return h + h * th;
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -122,8 +135,8 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
 }
 
 // D row t (128 columns) + bias -> GELU -> BF16 -> row t of H (canonical layout)
-__device__ __forceinline__ void epilogue(TcSmem &S, uint32_t taddr, const float *b, int t) {
-  unsigned char *H = reinterpret_cast<unsigned char *>(S.H);
+__device__ __forceinline__ void epilogue(bf *Hs, uint32_t taddr, const float *b, int t) {
+  unsigned char *H = reinterpret_cast<unsigned char *>(Hs);
 #pragma unroll 1
   for (int c = 0; c < NH; c += 16) {
     float v[16];
@@ -142,42 +155,51 @@ __device__ __forceinline__ void epilogue(TcSmem &S, uint32_t taddr, const float 
   }
 }
 
-// all threads: operands written by this block become visible to the tensor core, and tensor
-// memory reads before the barrier are ordered before MMAs after it
-__device__ __forceinline__ void block_handoff() {
+__device__ __forceinline__ void group_bar(int g) { asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(TM) : "memory"); }
+
+// the threads of group g: operands written by the group become visible to the tensor core, and
+// tensor-memory reads before the barrier are ordered before MMAs after it
+__device__ __forceinline__ void group_handoff(int g) {
   fence_async_smem();
   tc_before_sync();
-  __syncthreads();
+  group_bar(g);
   tc_after_sync();
 }
 
-__global__ void __launch_bounds__(TM) k_mlp_fwd_tc(const float *__restrict__ P, const float *__restrict__ X, int n,
-                                                   float *__restrict__ Y, int *status) {
-  extern __shared__ __align__(1024) unsigned char raw[];
-  TcSmem &S = *reinterpret_cast<TcSmem *>(raw + ((1024u - (smem_u32(raw) & 1023u)) & 1023u));
-  const int t = threadIdx.x, w = t >> 5;
+// one thread of the group waits for the group's MMAs (thread 32 (g % 4): the four groups' waiters
+// sit in warps of four different schedulers); the barrier passes the outcome to the group
+__device__ __forceinline__ bool group_wait(TcSmem &S, int g, int lt, uint32_t mbar, uint32_t parity) {
+  if (lt == 32 * (g & 3)) S.ok[g] = wait_phase(mbar, parity) ? 1 : 0;
+  group_bar(g);
+  const bool ok = S.ok[g] != 0;
+  group_bar(g);   // the flag is read before thread 0 can rewrite it
+  return ok;
+}
+
+__global__ void __launch_bounds__(TM * G) k_mlp_fwd_tc(const float *__restrict__ P, const float *__restrict__ X,
+                                                       int n, float *__restrict__ Y, int *status) {
+  extern __shared__ __align__(128) unsigned char raw[];
+  TcSmem &S = *reinterpret_cast<TcSmem *>(raw);
+  const int tid = threadIdx.x, w = tid >> 5, g = tid / TM, lt = tid % TM;
   unsigned char *W1 = reinterpret_cast<unsigned char *>(S.W1);
   unsigned char *W2 = reinterpret_cast<unsigned char *>(S.W2);
   unsigned char *W3 = reinterpret_cast<unsigned char *>(S.W3);
-  unsigned char *Xs = reinterpret_cast<unsigned char *>(S.X);
-  for (int q = t; q < NH * K1; q += TM) {
+  for (int q = tid; q < NH * K1; q += TM * G) {
     const int h = q / K1, i = q % K1;
     *reinterpret_cast<bf *>(W1 + cm_off(h, i, K1)) = __float2bfloat16_rn(i < NI ? P[oW1 + h * NI + i] : 0.0f);
   }
-  for (int q = t; q < NH * NH; q += TM) {
+  for (int q = tid; q < NH * NH; q += TM * G) {
     const int h = q / NH, k = q % NH;
     *reinterpret_cast<bf *>(W2 + cm_off(h, k, NH)) = __float2bfloat16_rn(P[oW2 + q]);
   }
-  for (int q = t; q < N3 * NH; q += TM) {
+  for (int q = tid; q < N3 * NH; q += TM * G) {
     const int o = q / NH, k = q % NH;
     *reinterpret_cast<bf *>(W3 + cm_off(o, k, NH)) = __float2bfloat16_rn(o < NO ? P[oW3 + o * NH + k] : 0.0f);
   }
-  S.b1[t] = P[ob1 + t];
-  S.b2[t] = P[ob2 + t];
-  if (t < N3) S.b3[t] = t < NO ? P[ob3 + t] : 0.0f;
-  const uint32_t mbar = smem_u32(&S.mbar);
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+  if (tid < NH) { S.b1[tid] = P[ob1 + tid]; S.b2[tid] = P[ob2 + tid]; }
+  if (tid < N3) S.b3[tid] = tid < NO ? P[ob3 + tid] : 0.0f;
+  if (lt == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar[g])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (w == 0) {
@@ -186,50 +208,57 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd_tc(const float *__restrict__ P, 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  block_handoff();
-  const uint32_t tmem = S.tmem_slot;
-  const uint32_t row = tmem + ((uint32_t)(w * 32) << 16);   // this warp's 32 lanes
+  fence_async_smem();
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  // group g: tensor-memory columns [128 g, 128 g + 128); warp w reads lanes 32 (w % 4) .. + 31
+  const uint32_t tmem = S.tmem_slot + (uint32_t)(128 * g);
+  const uint32_t row = tmem + ((uint32_t)((w & 3) * 32) << 16);
+  const uint32_t mbar = smem_u32(&S.mbar[g]);
+  TcGroup &Gs = S.g[g];
+  unsigned char *Xs = reinterpret_cast<unsigned char *>(Gs.X);
   const uint64_t dW1 = sdesc(S.W1, 128, K1 * 16), dW2 = sdesc(S.W2, 128, NH * 16), dW3 = sdesc(S.W3, 128, NH * 16);
-  const uint64_t dX = sdesc(S.X, 128, K1 * 16), dH = sdesc(S.H, 128, NH * 16);
+  const uint64_t dX = sdesc(Gs.X, 128, K1 * 16), dH = sdesc(Gs.H, 128, NH * 16);
   constexpr uint32_t id12 = idesc(TM, NH), id3 = idesc(TM, N3);
   uint32_t parity = 0;
-  int ok = 1;
+  bool ok = true;
   const int tiles = (n + TM - 1) / TM;
-  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int s = tile * TM + t;
-    // layer 1: A = the inputs of the tile, row t (column 15 is the zero pad)
+  for (int tile = blockIdx.x * G + g; tile < tiles; tile += gridDim.x * G) {
+    const int s = tile * TM + lt;
+    // layer 1: A = the inputs of the tile, row lt (column 15 is the zero pad)
 #pragma unroll
     for (int i = 0; i < K1; ++i)
-      *reinterpret_cast<bf *>(Xs + cm_off(t, i, K1)) =
+      *reinterpret_cast<bf *>(Xs + cm_off(lt, i, K1)) =
           __float2bfloat16_rn((s < n && i < NI) ? X[(size_t)s * NI + i] : 0.0f);
-    block_handoff();
-    if (t == 0) {
+    group_handoff(g);
+    if (lt == 0) {
       mma(tmem, dX, dW1, id12, 0u);
       commit(mbar);
     }
-    ok = __syncthreads_and(ok && (t != 0 || wait_phase(mbar, parity)));   // thread 0 waits, the barrier tells the rest
+    ok = group_wait(S, g, lt, mbar, parity);
     parity ^= 1u;
     if (!ok) break;
     tc_after_sync();
-    epilogue(S, row, S.b1, t);
-    block_handoff();
+    epilogue(Gs.H, row, S.b1, lt);
+    group_handoff(g);
     // layer 2: eight K = 16 slices (descriptor start + 256 B each)
-    if (t == 0) {
+    if (lt == 0) {
       for (uint32_t kk = 0; kk < NH / 16; ++kk) mma(tmem, dH + kk * 16u, dW2 + kk * 16u, id12, kk);
       commit(mbar);
     }
-    ok = __syncthreads_and(ok && (t != 0 || wait_phase(mbar, parity)));   // thread 0 waits, the barrier tells the rest
+    ok = group_wait(S, g, lt, mbar, parity);
     parity ^= 1u;
     if (!ok) break;
     tc_after_sync();
-    epilogue(S, row, S.b2, t);
-    block_handoff();
+    epilogue(Gs.H, row, S.b2, lt);
+    group_handoff(g);
     // layer 3: N = 16 (outputs 0..2)
-    if (t == 0) {
+    if (lt == 0) {
       for (uint32_t kk = 0; kk < NH / 16; ++kk) mma(tmem, dH + kk * 16u, dW3 + kk * 16u, id3, kk);
       commit(mbar);
     }
-    ok = __syncthreads_and(ok && (t != 0 || wait_phase(mbar, parity)));   // thread 0 waits, the barrier tells the rest
+    ok = group_wait(S, g, lt, mbar, parity);
     parity ^= 1u;
     if (!ok) break;
     tc_after_sync();
@@ -240,14 +269,14 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd_tc(const float *__restrict__ P, 
       for (int o = 0; o < NO; ++o) Y[(size_t)s * NO + o] = v[o] + S.b3[o];
     }
     tc_before_sync();
-    __syncthreads();   // D, X and H are rewritten by the next tile
+    group_bar(g);   // D, X and H are rewritten by the group's next tile
     tc_after_sync();
   }
-  if (!ok && t == 0) atomicExch(status, 1);
+  if (!ok && lt == 0) atomicExch(status, 1);
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
-  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+  if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_slot), "r"(kCols) : "memory");
 }
 
 }  // namespace
@@ -264,10 +293,11 @@ int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status,
     if (sms <= 0) sms = 1;
   }
   const int tiles = (n + TM - 1) / TM;
-  const int blocks = tiles < 2 * sms ? tiles : 2 * sms;
-  const int smem = (int)sizeof(TcSmem) + 1024;   // room to align the dynamic base to 1 KB
+  const int groups = (tiles + G - 1) / G;
+  const int blocks = groups < sms ? groups : sms;   // one block (all of tensor memory) per SM
+  const int smem = (int)sizeof(TcSmem);
   if (cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return PIC_ECUDA;
-  k_mlp_fwd_tc<<<blocks, TM, smem, st>>>(P, X, n, Y, status);
+  k_mlp_fwd_tc<<<blocks, TM * G, smem, st>>>(P, X, n, Y, status);
   return cudaGetLastError() == cudaSuccess ? 0 : PIC_ECUDA;
 }
