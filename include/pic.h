@@ -402,19 +402,21 @@ int pic_fluid_step(pic_fluid *f, int64_t n_steps);
  * *n_snaps receives the number written (PIC_ECAPACITY if more were recorded) */
 int pic_fluid_modes(pic_fluid *f, float *out, int max_snaps, int *n_snaps);
 /* attach (net != NULL) or detach the closure network: every `period` steps the
- * features of every cell (15: 5-point stencils of n/<n>, 3/2 Te in eV and
- * E/N in Td with E at cells the mean of its faces; each divided by
- * feat_scale[k]) go through the network, whose 3 outputs times targ_scale
+ * features of every cell j (15: n/<n>, 3/2 Te in eV and E/N in Td, with E at
+ * cells the mean of its faces, at cells j + d stencil, d = -2..2; each divided
+ * by feat_scale[k]) go through the network, whose 3 outputs times targ_scale
  * become dG, dH, dnu for the next `period` steps (a zero scale switches a
  * correction off).  nu_bound > 0 limits the learned ionization correction to
  * |dnu| <= nu_bound nu_i(Te) of the cell (a trust region for states unlike
- * the training data); <= 0: unbounded.  The network is not owned. */
+ * the training data); <= 0: unbounded.  stencil: spacing of the stencil points in
+ * cells, 1 <= 4 stencil <= n_cells of every column.  The network is not owned. */
 int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *feat_scale, const float *targ_scale,
-                          float nu_bound);
+                          float nu_bound, int stencil);
 /* fixed corrections (device array, total cells x 3, already scaled to SI; NULL clears) */
 int pic_fluid_set_corrections(pic_fluid *f, const float *corr_dev);
-/* features of the current state (device array, total cells x 15, divided by feat_scale of
- * the attached closure, or unscaled without one); cells are numbered column after column */
+/* features of the current state (device array, total cells x 15, divided by feat_scale and
+ * spaced by the stencil of the attached closure, or unscaled at spacing 1 without one); cells are
+ * numbered column after column */
 int pic_fluid_features(pic_fluid *f, float *X_dev);
 /* device time of the last pic_fluid_step and the kernels it launched */
 int pic_fluid_elapsed(pic_fluid *f, double *ms, int64_t *launches);

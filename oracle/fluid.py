@@ -171,11 +171,11 @@ def modes(n, M):
     return np.fft.fft(n)[1:M + 1] / len(n)
 
 
-def features(col, tab, n, T):
-    """Closure-network inputs per cell (unnormalised): 5-point stencils of n/<n>,
-    mean energy 3/2 T [eV] and E/N [Td] with E at cells the average of its faces."""
+def features(col, tab, n, T, step=1):
+    """Closure-network inputs per cell j (unnormalised): n/<n>, mean energy 3/2 T [eV] and
+    E/N [Td] (E at cells the average of its faces) at cells j + d step, d = -2..2."""
     c = coefficients(col, tab, T)
     _, E = flux_and_field(col, c, n)
     Ec = 0.5 * (E + np.roll(E, 1))
     q = (n / n.mean(), 1.5 * T, Ec / (col["N_gas"] * TD))
-    return np.stack([np.roll(v, -d) for v in q for d in (-2, -1, 0, 1, 2)], 1)
+    return np.stack([np.roll(v, -d * step) for v in q for d in (-2, -1, 0, 1, 2)], 1)

@@ -136,7 +136,7 @@ def lib() -> C.CDLL:
         L.pic_fluid_step.argtypes = [C.c_void_p, C.c_int64]
         L.pic_fluid_modes.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
         L.pic_fluid_set_closure.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_float),
-                                            C.POINTER(C.c_float), C.c_float]
+                                            C.POINTER(C.c_float), C.c_float, C.c_int]
         L.pic_fluid_set_corrections.argtypes = [C.c_void_p, C.c_void_p]
         L.pic_fluid_features.argtypes = [C.c_void_p, C.c_void_p]
         L.pic_fluid_elapsed.argtypes = [C.c_void_p, _D, _I64]
@@ -502,12 +502,12 @@ class Fluid:
         o = out[:k.value].astype(np.float64)
         return o[..., 0] + 1j * o[..., 1]
 
-    def set_closure(self, net, period: int, feat_scale, targ_scale, nu_bound: float = 0.0) -> None:
+    def set_closure(self, net, period: int, feat_scale, targ_scale, nu_bound: float = 0.0, stencil: int = 1) -> None:
         fs = np.ascontiguousarray(feat_scale, dtype=np.float32)
         ts = np.ascontiguousarray(targ_scale, dtype=np.float32)
         _check(self.L.pic_fluid_set_closure(self.h, net.h if net is not None else None, period,
                                             fs.ctypes.data_as(C.POINTER(C.c_float)),
-                                            ts.ctypes.data_as(C.POINTER(C.c_float)), nu_bound))
+                                            ts.ctypes.data_as(C.POINTER(C.c_float)), nu_bound, stencil))
         self._net = net
 
     def set_corrections(self, corr) -> None:

@@ -97,9 +97,9 @@ def swarm_table(EN_Td: Sequence[float], gas: str = "neon", n: int = 100_000, rel
     return table, ps, mom
 
 
-def _stencil(a: np.ndarray, j: np.ndarray) -> np.ndarray:
+def _stencil(a: np.ndarray, j: np.ndarray, step: int = 1) -> np.ndarray:
     N = len(a)
-    return np.stack([a[(j + d) % N] for d in (-2, -1, 0, 1, 2)], 1)
+    return np.stack([a[(j + d * step) % N] for d in (-2, -1, 0, 1, 2)], 1)
 
 
 def samples_from_moments(m: dict, p: w.Params) -> tuple[np.ndarray, np.ndarray]:
@@ -187,9 +187,10 @@ def table_closure(n, T, Gamma_T, L_m, N_gas, mu_iN, tab):
     return cell(G), cell(H), tab.at("nu_izN", T) * N_gas, cell(E)
 
 
-def residual_samples(m: dict, p: w.Params, tab, mu_iN: float, T_range=None):
+def residual_samples(m: dict, p: w.Params, tab, mu_iN: float, T_range=None, step: int = 1):
     """(features, residual targets) of every cell of one particle-model window, in the
-    fluid frame: features as the fluid screen computes them (n/<n>, mean energy, E/N
+    fluid frame: features as the fluid screen computes them at stencil spacing `step`
+    (n/<n>, mean energy, E/N
     from eq. 17), targets = (Gamma_e - Gamma_tab)/n, (H_e - H_tab)/n, nu_iz - nu_tab."""
     f = mirror(m)
     N_gas = n_gas(p)
@@ -200,6 +201,7 @@ def residual_samples(m: dict, p: w.Params, tab, mu_iN: float, T_range=None):
     Gamma_T = float(np.mean(f["gamma_i"] - f["gamma_e"]))
     G, H, nu, E = table_closure(n, T, Gamma_T, p.L_m, N_gas, mu_iN, tab)
     j = np.arange(len(n))
-    X = np.concatenate([_stencil(n / n.mean(), j), _stencil(1.5 * T, j), _stencil(E / (N_gas * TD), j)], 1)
+    X = np.concatenate([_stencil(n / n.mean(), j, step), _stencil(1.5 * T, j, step),
+                        _stencil(E / (N_gas * TD), j, step)], 1)
     Y = np.stack([(f["gamma_e"] - G) / n, (f["heat_e"] - H) / n, f["iz_rate"] / n - nu], 1)
     return X.astype(np.float32), Y.astype(np.float32)

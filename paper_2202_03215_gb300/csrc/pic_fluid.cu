@@ -58,6 +58,7 @@ struct FluidK {
   float nu_bound;               // |dnu| <= nu_bound nu_i (network corrections; <= 0: unbounded)
   float *feat;                  // cells x 15 or null: written after the last step
   float fs[15];                 // feature scales (divisors)
+  int step;                     // stencil spacing of the features, cells
 };
 
 struct Sm {
@@ -336,7 +337,7 @@ __device__ void features(const Sm &S, const FluidK &K, const ColK &c, float *red
     float *x = K.feat + (c.off + j) * 15;
 #pragma unroll
     for (int d = -2; d <= 2; ++d) {
-      const int q = (j + d) & (N - 1), qm = (q - 1) & (N - 1);
+      const int q = (j + d * K.step) & (N - 1), qm = (q - 1) & (N - 1);
       x[d + 2] = S.n[q] / mean / K.fs[d + 2];
       x[d + 7] = 1.5f * S.T[q] / K.fs[d + 7];
       x[d + 12] = 0.5f * (S.E[q] + S.E[qm]) / (c.Ng * kTd) / K.fs[d + 12];
@@ -401,6 +402,7 @@ struct pic_fluid {
   int period = 0;
   float fs[15], cs[3];
   float nu_bound = 0.0f;
+  int stencil = 1;
   float *X = nullptr, *Y = nullptr;
   bool y_valid = false;
   cudaStream_t st = nullptr;
@@ -431,6 +433,7 @@ FluidK make_k(pic_fluid *f) {
   K.n_cols = f->n_cols;
   K.corr = f->corr;
   for (int k = 0; k < 15; ++k) K.fs[k] = f->fs[k];
+  K.step = f->stencil;
   K.cs0 = f->cs[0]; K.cs1 = f->cs[1]; K.cs2 = f->cs[2];
   K.nu_bound = f->nu_bound;
   return K;
@@ -634,14 +637,17 @@ int pic_fluid_modes(pic_fluid *f, float *out, int max_snaps, int *n_snaps) {
 }
 
 int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *feat_scale, const float *targ_scale,
-                          float nu_bound) {
+                          float nu_bound, int stencil) {
   if (!f) return PIC_EINVAL;
   if (!net) {
     f->net = nullptr;
     f->y_valid = false;
+    f->stencil = 1;
     return 0;
   }
-  if (period <= 0 || !feat_scale || !targ_scale) return PIC_EINVAL;
+  if (period <= 0 || !feat_scale || !targ_scale || stencil < 1) return PIC_EINVAL;
+  for (const ColK &c : f->hcols)
+    if (4 * stencil > c.N) return PIC_EINVAL;
   for (int k = 0; k < 15; ++k)
     if (!(feat_scale[k] != 0.0f)) return PIC_EINVAL;
   if (!f->X && (cudaMalloc(&f->X, sizeof(float) * 15 * f->cells) != cudaSuccess ||
@@ -652,6 +658,7 @@ int pic_fluid_set_closure(pic_fluid *f, pic_mlp *net, int period, const float *f
   f->net = net;
   f->period = period;
   f->nu_bound = nu_bound;
+  f->stencil = stencil;
   f->y_valid = false;
   return 0;
 }

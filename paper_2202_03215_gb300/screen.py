@@ -410,7 +410,8 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
           n_cells: int = 2048, particles: int = 1_000_000, windows: int = 200, window: int = 4000,
           early: int = 100, early_window: int = 1000, agg: int = 4, fluid_dt: float = 2e-9, fluid_diag: int = 20,
           train_steps: int = 3000, batch: int = 8192, lr: float = 1e-3, period: int = 10,
-          components=(0.0, 0.0, 1.0), nu_bound: float = 1.0, seed: int = 7, log=print) -> dict:
+          components=(0.0, 0.0, 1.0), nu_bound: float = 1.0, stencils=(1,), seed: int = 7,
+          log=print) -> dict:
     """Particle model (one GPU batch: comparison and training fields), closure training on
     its moment windows, fluid model with and without the trained closure at the comparison
     fields; striation observables, closure gain and times.  The particle record takes
@@ -470,37 +471,45 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
         # ion mobility of the uniform column: windows after the first 0.2 us, before striations
         sel = [s for s in range(nw) if t_pic[s] > 2e-7 and amp[s, k] < 0.05][:8] or [min(nw - 1, early)]
         mu.append(float(np.median(mob[sel, k])))
-    # closure data from the training columns: residuals of the tabulated closure
+    # closure data from the training columns: residuals of the tabulated closure, one network per
+    # stencil spacing (the first is the study's main closure)
     T_range = (tab.Te[0], tab.Te[-1])
-    Xs, Ys, col_of = [], [], []
-    for k in range(ncmp, len(Es)):
-        for m in train_windows[k][2:]:
-            X, Y = cl.residual_samples(m, params[k], tab, mu[k], T_range)
-            Xs.append(X)
-            Ys.append(Y)
-            col_of.append(np.full(len(X), k))
-    X = np.concatenate(Xs)
-    Y = np.concatenate(Ys)
-    col_of = np.concatenate(col_of)
-    fs = cl.FEATURE_SCALE
-    ts = np.maximum(np.std(Y, 0), 1e-30).astype(np.float32)
     held = ncmp + (len(E_train) // 2)                  # one training column held out (split by run)
-    tr, te = col_of != held, col_of == held
-    Xn, Yn = (X / fs).astype(np.float32), (Y / ts).astype(np.float32)
-    rng = np.random.default_rng(seed)
-    perm = rng.permutation(np.nonzero(tr)[0])
-    Xd = torch.from_numpy(Xn[perm]).cuda()
-    Yd = torch.from_numpy(Yn[perm]).cuda()
-    net = Mlp(seed=seed)
-    torch.cuda.synchronize()
-    ta = time.perf_counter()
-    last = net.train(Xd, Yd, batch=batch, steps=train_steps, lr=lr)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - ta
-    Yh = net.forward(torch.from_numpy(Xn[te]).cuda()).cpu().numpy()
-    mse_net = ((Yh - Yn[te]) ** 2).mean(0)
-    mse_tab = (Yn[te] ** 2).mean(0)             # the tabulated closure alone predicts zero residual
-    log(f"closure: {len(X)} samples, held-out column E0/p = {Es[held]}, mse net {mse_net} vs table {mse_tab}")
+    fs = cl.FEATURE_SCALE
+    nets = []
+    for st_k in stencils:
+        Xs, Ys, col_of = [], [], []
+        for k in range(ncmp, len(Es)):
+            for m in train_windows[k][2:]:
+                X, Y = cl.residual_samples(m, params[k], tab, mu[k], T_range, step=st_k)
+                Xs.append(X)
+                Ys.append(Y)
+                col_of.append(np.full(len(X), k))
+        X = np.concatenate(Xs)
+        Y = np.concatenate(Ys)
+        col_of = np.concatenate(col_of)
+        ts = np.maximum(np.std(Y, 0), 1e-30).astype(np.float32)
+        tr, te = col_of != held, col_of == held
+        Xn, Yn = (X / fs).astype(np.float32), (Y / ts).astype(np.float32)
+        rng = np.random.default_rng(seed)
+        perm = rng.permutation(np.nonzero(tr)[0])
+        Xd = torch.from_numpy(Xn[perm]).cuda()
+        Yd = torch.from_numpy(Yn[perm]).cuda()
+        net = Mlp(seed=seed)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        last = net.train(Xd, Yd, batch=batch, steps=train_steps, lr=lr)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - ta
+        Yh = net.forward(torch.from_numpy(Xn[te]).cuda()).cpu().numpy()
+        mse_net = ((Yh - Yn[te]) ** 2).mean(0)
+        mse_tab = (Yn[te] ** 2).mean(0)             # the tabulated closure alone predicts zero residual
+        log(f"closure (stencil {st_k}): {len(X)} samples, held-out column E0/p = {Es[held]}, "
+            f"mse net {mse_net} vs table {mse_tab}")
+        nets.append(dict(stencil=st_k, net=net, ts=ts, mse_net=mse_net, mse_tab=mse_tab, train_s=train_s,
+                         last=last, n=len(X)))
+    net, ts, mse_net, mse_tab, train_s, last = (nets[0][k] for k in ("net", "ts", "mse_net", "mse_tab",
+                                                                    "train_s", "last"))
     # fluid model at the comparison fields, same simulated time, noise of the particle model
     states = [homogeneous_E0(tab, e, p_torr, mu_iN=mu[k]) for k, e in enumerate(E_compare)]
     steps = int(round(total_steps * dt_pic / fluid_dt))
@@ -508,8 +517,9 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
     noise = 1.0 / math.sqrt(particles / n_cells)
     mask = np.asarray(components, np.float32)
     out = {}
-    clo_args = (net, period, fs, ts * mask, nu_bound)
-    variants = (("fluid", True, None), ("fluid_closure", True, clo_args))
+    variants = [("fluid", True, None)] + [
+        ("fluid_closure" if i == 0 else f"fluid_closure_s{d['stencil']}", True,
+         (d["net"], period, fs, d["ts"] * mask, nu_bound, d["stencil"])) for i, d in enumerate(nets)]
     for name, pair, clo in variants:
         f = Fluid(fluid_columns(states, L_m, n_cells, pair=pair), records, n_T=128, dt_s=fluid_dt,
                   diag_every=diag, n_modes=M)
@@ -540,7 +550,12 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
                 fluid_seconds_per_column=out["fluid"]["ms"] / 1e3 / ncmp,
                 fluid_closure_seconds_per_column=out["fluid_closure"]["ms"] / 1e3 / ncmp,
                 simulated_s=total_steps * dt_pic, train_seconds=train_s, train_loss=last, components=list(components),
-                n_samples=int(len(X)), held_out_E=Es[held], mse_net=mse_net.tolist(), mse_table=mse_tab.tolist(),
+                stencils=list(stencils), nu_bound=nu_bound,
+                closures=[dict(stencil=d["stencil"], mse_net=d["mse_net"].tolist(), mse_table=d["mse_tab"].tolist(),
+                               lam=[o["lam"] for o in out["fluid_closure" if i == 0 else f"fluid_closure_s{d['stencil']}"]["obs"]],
+                               v_ph=[o["v_ph"] for o in out["fluid_closure" if i == 0 else f"fluid_closure_s{d['stencil']}"]["obs"]])
+                          for i, d in enumerate(nets)],
+                n_samples=int(nets[0]["n"]), held_out_E=Es[held], mse_net=mse_net.tolist(), mse_table=mse_tab.tolist(),
                 target_scale=ts.tolist(), pic_modes=rec, t_pic=t_pic,
                 fluid_modes=out["fluid"]["modes"], fluid_closure_modes=out["fluid_closure"]["modes"],
                 t_fluid=out["fluid"]["t"])
@@ -568,6 +583,7 @@ def main(argv=None) -> int:
     ap.add_argument("what", choices=["study", "fluid"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--nu-bound", type=float, default=0.5)
+    ap.add_argument("--stencils", type=int, nargs="+", default=[1], help="closure stencil spacings, cells")
     ap.add_argument("--columns", type=int, default=152)
     ap.add_argument("--cells", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=200)
@@ -581,7 +597,7 @@ def main(argv=None) -> int:
         print(f"fluid: {a.columns} columns x {a.cells} cells, {a.steps} steps in {r['ms']:.2f} ms "
               f"({r['launches']} launches)", flush=True)
         return 0
-    r = study([6, 8, 10, 12, 14, 16, 18, 20], [7, 9, 11, 13, 15, 17, 19, 21], nu_bound=a.nu_bound,
+    r = study([6, 8, 10, 12, 14, 16, 18, 20], [7, 9, 11, 13, 15, 17, 19, 21], nu_bound=a.nu_bound, stencils=tuple(a.stencils),
               log=lambda s: print(s, flush=True))
     for k, e in enumerate(r["E_compare"]):
         p, f, g, l, d = r["pic"][k], r["fluid"][k], r["fluid_closure"][k], r["linear"][k], r["dispersion"][k]
@@ -589,6 +605,9 @@ def main(argv=None) -> int:
               f"fluid lam={f['lam'] * 100:.3g} v={f['v_ph']:.3g} g={f['gamma']:.3g} | fluid+closure "
               f"lam={g['lam'] * 100:.3g} v={g['v_ph']:.3g} | eq.22 lam={l['lam'] * 100:.3g} v={l['v_ph']:.3g} "
               f"g={l['gamma_max']:.3g} | full linear lam={d['lam'] * 100:.3g} g={d['gamma']:.3g}", flush=True)
+    for c in r["closures"]:
+        print(f"closure stencil {c['stencil']}: held-out mse {c['mse_net']} (table {c['mse_table']}); lambda cm "
+              + " ".join(f"{x * 100:.3g}" for x in c["lam"]), flush=True)
     print("speed ratio (particle / fluid per column):",
           r["pic_seconds_per_column"] / r["fluid_seconds_per_column"], flush=True)
     if a.out:

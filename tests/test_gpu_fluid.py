@@ -129,7 +129,8 @@ def test_fluid_corrections_match_oracle(records):
     f.close()
 
 
-def test_fluid_network_closure_matches_oracle(records):
+@pytest.mark.parametrize("stencil", [1, 4])
+def test_fluid_network_closure_matches_oracle(records, stencil):
     import torch
     from oracle import mlp_forward_backward
     cols = columns()[:2] + columns()[3:]
@@ -139,7 +140,7 @@ def test_fluid_network_closure_matches_oracle(records):
     net = pb.Mlp(seed=5)
     f = pb.Fluid(cols, records, n_T=128, dt_s=dt)
     bound = 0.05                       # active: the random network's dnu exceeds 5% of nu_i in places
-    f.set_closure(net, period, fs, ts, nu_bound=bound)
+    f.set_closure(net, period, fs, ts, nu_bound=bound, stencil=stencil)
     for k, c in enumerate(cols):
         f.set_state(k, *initial(c["n_cells"], k + 30))
     f.step(2 * period)
@@ -148,7 +149,7 @@ def test_fluid_network_closure_matches_oracle(records):
     for k, c in enumerate(cols):
         n, T = initial(c["n_cells"], k + 30)
         for _ in range(2):
-            X = fl.features(oracle_col(c), tab, n, T) / fs
+            X = fl.features(oracle_col(c), tab, n, T, step=stencil) / fs
             Y = mlp_forward_backward(P, X, np.zeros((len(X), 3)), bf16=True, want_grad=False)[1]
             ck = (Y * ts).T
             for _ in range(period):
