@@ -1,11 +1,13 @@
 // Closure network of the quasi-neutral fluid screen: MLP 15 -> 128 -> 128 -> 3,
 // GELU (tanh form) on the hidden layers, mean-squared-error loss, Adam.
-// BF16 operands on the tensor cores (mma.sync m16n8k16, FP32 accumulation),
-// FP32 master weights and optimizer state.
+// Training: BF16 operands on the tensor cores (mma.sync m16n8k16 fed by
+// ldmatrix, FP32 accumulation), FP32 master weights and optimizer state.
+// The forward pass of the fluid closure runs on tcgen05 (pic_mlp_tc.cu).
 //
-// One CTA trains on a tile of 64 samples: forward, backward and the weight
-// gradients of its tile, written as a partial; a second kernel sums the
-// partials in a fixed order (deterministic gradients), a third applies Adam.
+// One CTA of 8 warps trains on a tile of 64 samples: forward, backward and the
+// weight gradients of its tile, written as a partial; a second kernel sums the
+// partials in a fixed order (deterministic gradients) and applies Adam, which
+// also refreshes the BF16 copy of the weights that the tile kernel stages.
 // Parameter layout (FP32, flat): W1[128][15], b1[128], W2[128][128], b2[128],
 // W3[3][128], b3[3]  (row = output unit).
 #include <cuda_bf16.h>
@@ -23,71 +25,103 @@
 namespace {
 
 constexpr int NI = 15, NIP = 16, NH = 128, NO = 3, NOP = 16;
+constexpr int LDI = NIP + 8, LDH = NH + 8, LDZ = NH + 8;   // padded rows: conflict-free ldmatrix
 constexpr int S = 64;                 // samples per tile
-constexpr int WARPS = S / 16;         // one warp per 16 samples in the row passes
+constexpr int WR = S / 16;            // row groups of 16 samples
+constexpr int WC = 2;                 // column halves of the hidden layers
+constexpr int WARPS = WR * WC;
 constexpr int THREADS = WARPS * 32;
 constexpr int oW1 = 0, ob1 = NH * NI, oW2 = ob1 + NH, ob2 = oW2 + NH * NH, oW3 = ob2 + NH, ob3 = oW3 + NO * NH;
 constexpr int NPARAM = ob3 + NO;      // 18947
 
 using bf = __nv_bfloat16;
 
+// BF16 weights exactly as the tile kernel holds them in shared memory (padding zero)
+struct WPack {
+  bf W1[NH][LDI];
+  bf W2[NH][LDH];
+  bf W3[NOP][LDH];
+};
+static_assert(sizeof(WPack) % 16 == 0, "16-byte copies");
+
 struct Smem {
-  bf W1[NH][NIP];
-  bf W2[NH][NH];
-  bf W3[NOP][NH];
-  bf X[S][NIP];
-  bf A1[S][NH];        // activations of layer 1, later dL/dz1
-  bf A2[S][NH];        // activations of layer 2, later dL/dz2
-  bf dY[S][NOP];
-  float Z1[S][NH];
-  float Z2[S][NH];
+  WPack w;
+  bf X[S][LDI];
+  bf A1[S][LDH];       // activations of layer 1
+  bf A2[S][LDH];       // activations of layer 2
+  bf D2[S][LDH];       // dL/dz2
+  bf D1[S][LDH];       // dL/dz1
+  bf dY[S][LDI];       // dL/dy (columns 3..15 zero)
+  float Z1[S][LDZ];
+  float Z2[S][LDZ];
   float b1[NH], b2[NH], b3[NOP];
-  float cs[WARPS][NH]; // per-warp column sums (bias gradients)
-  float loss[WARPS];
+  float cs1[WR][NH], cs2[WR][NH], cs3[WR][NOP];   // per-row-group column sums (bias gradients)
+  float loss[WR];
 };
 
-// a matrix in shared memory read element by element: (r, c) at p[r*ld + c], or p[c*ld + r] if tr
-struct Mat {
-  const bf *p;
-  int ld;
-  bool tr;
-};
-__device__ __forceinline__ unsigned short bits(bf x) { return *reinterpret_cast<unsigned short *>(&x); }
-__device__ __forceinline__ unsigned at2(Mat m, int r, int c, int r2, int c2) {
-  const bf lo = m.tr ? m.p[c * m.ld + r] : m.p[r * m.ld + c];
-  const bf hi = m.tr ? m.p[c2 * m.ld + r2] : m.p[r2 * m.ld + c2];
-  return (unsigned)bits(lo) | ((unsigned)bits(hi) << 16);
+// index of parameter p in WPack (in BF16 elements), -1 for biases
+__host__ __device__ __forceinline__ int wpack_index(int p) {
+  if (p < ob1) return (p / NI) * LDI + p % NI;
+  if (p >= oW2 && p < ob2) return NH * LDI + ((p - oW2) / NH) * LDH + (p - oW2) % NH;
+  if (p >= oW3 && p < ob3) return NH * LDI + NH * LDH + ((p - oW3) / NH) * LDH + (p - oW3) % NH;
+  return -1;
 }
 
-__device__ __forceinline__ void mma(float c[4], const unsigned a[4], const unsigned b[2]) {
+__device__ __forceinline__ unsigned saddr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// four 8x8 BF16 matrices; lanes 8i..8i+7 give the row addresses of matrix i. Lane l receives
+// row l/4, columns 2(l%4), 2(l%4)+1 of each (.trans: row 2(l%4), 2(l%4)+1 of column l/4)
+__device__ __forceinline__ void ldsm4(unsigned r[4], const bf *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(saddr(p)));
+}
+__device__ __forceinline__ void ldsm4t(unsigned r[4], const bf *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(saddr(p)));
+}
+
+__device__ __forceinline__ void mma(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// C[16 x 8 NT] (rows r0.., columns n0..) += A(16 x K) B(K x 8 NT), one warp.
+// C[16 x 8 NT] (rows r0.., columns n0..) += A(16 x K) B(K x 8 NT), one warp, operands in shared memory.
+// A(r, k) = A[r*lda + k], or A[k*lda + r] if AT; B(k, n) = B[n*ldb + k], or B[k*ldb + n] if BT.
 // Fragment layout of m16n8k16 (g = lane/4, t = lane%4): A rows g, g+8 and columns 2t, 2t+1,
 // 2t+8, 2t+9; B columns g and rows 2t, 2t+1, 2t+8, 2t+9; C rows g, g+8 and columns 2t, 2t+1.
-template <int NT>
-__device__ __forceinline__ void gemm(float c[NT][4], Mat A, int r0, Mat B, int n0, int K) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+template <int NT, bool AT, bool BT>
+__device__ __forceinline__ void gemm(float c[NT][4], const bf *A, int lda, int r0, const bf *B, int ldb, int n0,
+                                     int K) {
+  static_assert(NT % 2 == 0, "two column tiles per B load");
+  const int lane = threadIdx.x & 31, mi = lane >> 3, j = lane & 7;
   for (int k0 = 0; k0 < K; k0 += 16) {
     unsigned a[4];
-    a[0] = at2(A, r0 + g, k0 + 2 * t, r0 + g, k0 + 2 * t + 1);
-    a[1] = at2(A, r0 + g + 8, k0 + 2 * t, r0 + g + 8, k0 + 2 * t + 1);
-    a[2] = at2(A, r0 + g, k0 + 2 * t + 8, r0 + g, k0 + 2 * t + 9);
-    a[3] = at2(A, r0 + g + 8, k0 + 2 * t + 8, r0 + g + 8, k0 + 2 * t + 9);
+    if (AT) ldsm4t(a, A + (k0 + j + (mi >> 1) * 8) * lda + r0 + (mi & 1) * 8);
+    else    ldsm4(a, A + (r0 + j + (mi & 1) * 8) * lda + k0 + (mi >> 1) * 8);
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const int n = n0 + 8 * nt + g;
-      unsigned b[2];
-      b[0] = at2(B, k0 + 2 * t, n, k0 + 2 * t + 1, n);
-      b[1] = at2(B, k0 + 2 * t + 8, n, k0 + 2 * t + 9, n);
-      mma(c[nt], a, b);
+    for (int np = 0; np < NT / 2; ++np) {
+      const int n = n0 + 16 * np;
+      unsigned b[4];   // b[0], b[1]: column tile 2np; b[2], b[3]: tile 2np + 1
+      if (BT) ldsm4t(b, B + (k0 + j + (mi & 1) * 8) * ldb + n + (mi >> 1) * 8);
+      else    ldsm4(b, B + (n + j + (mi >> 1) * 8) * ldb + k0 + (mi & 1) * 8);
+      mma(c[2 * np], a, b[0], b[1]);
+      mma(c[2 * np + 1], a, b[2], b[3]);
     }
   }
+}
+
+template <int NT>
+__device__ __forceinline__ void zero(float c[NT][4]) {
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
+}
+
+__device__ __forceinline__ void st_bf2(bf *p, float x, float y) {
+  *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(x, y);
 }
 
 // GELU (tanh form) through s = (1 + tanh u)/2 = 1/(1 + exp(-2u)), u = sqrt(2/pi)(z + 0.044715 z^3):
@@ -111,215 +145,256 @@ __device__ __forceinline__ float colsum(float v) {
   return v;
 }
 
-// mode 0: forward + backward of the tile, partial gradients and loss; mode 1: forward only (Y)
-__global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ P, const float *__restrict__ X,
-                                                      const float *__restrict__ T, int n, float inv_n3,
-                                                      float *__restrict__ gpart, float *__restrict__ lpart,
-                                                      float *__restrict__ Y, int mode) {
+// hidden-layer epilogue of a row pass: z = c + b -> Z (FP32), gelu(z) -> H (BF16)
+template <int NT>
+__device__ __forceinline__ void act_epilogue(const float c[NT][4], const float *b, float (*Z)[LDZ], bf (*H)[LDH],
+                                             int r0, int n0) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int r = r0 + g + 8 * hr, col = n0 + 8 * nt + 2 * t;
+      const float z0 = c[nt][2 * hr] + b[col], z1 = c[nt][2 * hr + 1] + b[col + 1];
+      *reinterpret_cast<float2 *>(&Z[r][col]) = make_float2(z0, z1);
+      st_bf2(&H[r][col], gelu(z0), gelu(z1));
+    }
+}
+
+// backward epilogue of a row pass: dz = c * gelu'(z) -> D (BF16), column sums -> cs
+template <int NT>
+__device__ __forceinline__ void dz_epilogue(const float c[NT][4], const float (*Z)[LDZ], bf (*D)[LDH], float *cs,
+                                            int r0, int n0) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    float bs[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int r = r0 + g + 8 * hr, col = n0 + 8 * nt + 2 * t;
+      const float2 z = *reinterpret_cast<const float2 *>(&Z[r][col]);
+      const float d0 = c[nt][2 * hr] * gelu_d(z.x), d1 = c[nt][2 * hr + 1] * gelu_d(z.y);
+      bs[0] += d0;
+      bs[1] += d1;
+      st_bf2(&D[r][col], d0, d1);
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      const float v = colsum(bs[o]);
+      if (g == 0) cs[n0 + 8 * nt + 2 * t + o] = v;
+    }
+  }
+}
+
+// weight-gradient epilogue: 16 rows h0.. of a (rows x ncol) partial, columns n0.. (< ncol kept)
+template <int NT>
+__device__ __forceinline__ void wgrad_store(const float c[NT][4], float *gp, int h0, int n0, int ncol, int nrow) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int h = h0 + g + 8 * hr, col = n0 + 8 * nt + 2 * t;
+      if (h >= nrow) continue;
+      if (col < ncol) gp[h * ncol + col] = c[nt][2 * hr];
+      if (col + 1 < ncol) gp[h * ncol + col + 1] = c[nt][2 * hr + 1];
+    }
+}
+
+// forward + backward of one tile of S samples; partial gradients (NPARAM floats) and loss per tile
+__global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ P, const WPack *__restrict__ Wb,
+                                                      const float *__restrict__ X, const float *__restrict__ T, int n,
+                                                      float inv_n3, float *__restrict__ gpart,
+                                                      float *__restrict__ lpart) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane >> 2, t = lane & 3;
+  const int rg = w % WR, ch = w / WR;          // row group, column half
+  const int r0 = 16 * rg, c0 = (NH / WC) * ch;
+  constexpr int NTH = NH / WC / 8;             // column tiles of a hidden-layer row pass
   const int tile = blockIdx.x, s0 = tile * S;
-  // weights to BF16, biases FP32, the tile's inputs
-  for (int q = tid; q < NH * NIP; q += THREADS) {
-    const int h = q / NIP, i = q % NIP;
-    sm.W1[h][i] = __float2bfloat16_rn(i < NI ? P[oW1 + h * NI + i] : 0.0f);
-  }
-  for (int q = tid; q < NH * NH; q += THREADS) sm.W2[q / NH][q % NH] = __float2bfloat16_rn(P[oW2 + q]);
-  for (int q = tid; q < NOP * NH; q += THREADS) {
-    const int o = q / NH, k = q % NH;
-    sm.W3[o][k] = __float2bfloat16_rn(o < NO ? P[oW3 + o * NH + k] : 0.0f);
+  // stage the BF16 weights, the FP32 biases and the tile's inputs
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(Wb);
+    uint4 *dst = reinterpret_cast<uint4 *>(&sm.w);
+    constexpr int NV = (int)(sizeof(WPack) / 16);
+#pragma unroll 4
+    for (int q = tid; q < NV; q += THREADS) dst[q] = __ldg(src + q);
   }
   for (int q = tid; q < NH; q += THREADS) { sm.b1[q] = P[ob1 + q]; sm.b2[q] = P[ob2 + q]; }
   if (tid < NOP) sm.b3[tid] = tid < NO ? P[ob3 + tid] : 0.0f;
-  for (int q = tid; q < S * NIP; q += THREADS) {
-    const int r = q / NIP, i = q % NIP, s = s0 + r;
-    sm.X[r][i] = __float2bfloat16_rn((s < n && i < NI) ? X[(size_t)s * NI + i] : 0.0f);
+  {
+    const int rows = min(S, n - s0);
+    for (int q = tid; q < S * NI; q += THREADS) {
+      const int r = q / NI, i = q % NI;
+      sm.X[r][i] = __float2bfloat16_rn(r < rows ? X[(size_t)s0 * NI + q] : 0.0f);
+    }
+    for (int q = tid; q < S * (LDI - NI); q += THREADS) sm.X[q / (LDI - NI)][NI + q % (LDI - NI)] = __float2bfloat16_rn(0.0f);
   }
   __syncthreads();
-  const int r0 = 16 * w;
-  // layer 1 and layer 2 (rows of this warp)
+  // layer 1, then layer 2: rows r0.., columns c0..
   {
-    float c[16][4];
-    for (int nt = 0; nt < 16; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-    gemm<16>(c, Mat{&sm.X[0][0], NIP, false}, r0, Mat{&sm.W1[0][0], NIP, true}, 0, NIP);
-    for (int nt = 0; nt < 16; ++nt)
-      for (int e = 0; e < 4; ++e) {
-        const int r = r0 + g + (e >> 1) * 8, col = 8 * nt + 2 * t + (e & 1);
-        const float z = c[nt][e] + sm.b1[col];
-        sm.Z1[r][col] = z;
-        sm.A1[r][col] = __float2bfloat16_rn(gelu(z));
-      }
-    __syncwarp();
-    for (int nt = 0; nt < 16; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-    gemm<16>(c, Mat{&sm.A1[0][0], NH, false}, r0, Mat{&sm.W2[0][0], NH, true}, 0, NH);
-    for (int nt = 0; nt < 16; ++nt)
-      for (int e = 0; e < 4; ++e) {
-        const int r = r0 + g + (e >> 1) * 8, col = 8 * nt + 2 * t + (e & 1);
-        const float z = c[nt][e] + sm.b2[col];
-        sm.Z2[r][col] = z;
-        sm.A2[r][col] = __float2bfloat16_rn(gelu(z));
-      }
-    __syncwarp();
+    float c[NTH][4];
+    zero<NTH>(c);
+    gemm<NTH, false, false>(c, &sm.X[0][0], LDI, r0, &sm.w.W1[0][0], LDI, c0, NIP);
+    act_epilogue<NTH>(c, sm.b1, sm.Z1, sm.A1, r0, c0);
   }
-  // layer 3, outputs, dL/dy
+  __syncthreads();
   {
-    float c[1][4] = {{0.0f, 0.0f, 0.0f, 0.0f}};
-    gemm<1>(c, Mat{&sm.A2[0][0], NH, false}, r0, Mat{&sm.W3[0][0], NH, true}, 0, NH);
-    float lsum = 0.0f;
-    float bsum[2] = {0.0f, 0.0f};
-    for (int e = 0; e < 4; ++e) {
-      const int r = r0 + g + (e >> 1) * 8, o = 2 * t + (e & 1), s = s0 + r;
-      float dy = 0.0f;
-      if (o < NO && s < n) {
-        const float y = c[0][e] + sm.b3[o];
-        if (mode == 1) {
-          Y[(size_t)s * NO + o] = y;
-        } else {
-          const float d = y - T[(size_t)s * NO + o];
+    float c[NTH][4];
+    zero<NTH>(c);
+    gemm<NTH, false, false>(c, &sm.A1[0][0], LDH, r0, &sm.w.W2[0][0], LDH, c0, NH);
+    act_epilogue<NTH>(c, sm.b2, sm.Z2, sm.A2, r0, c0);
+  }
+  __syncthreads();
+  // layer 3, outputs, dL/dy, loss (one warp per row group)
+  if (ch == 0) {
+    float c[2][4];
+    zero<2>(c);
+    gemm<2, false, false>(c, &sm.A2[0][0], LDH, r0, &sm.w.W3[0][0], LDH, 0, NH);
+    float lsum = 0.0f, bsum[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int r = r0 + g + 8 * hr, s = s0 + r;
+      float dy[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int o = 2 * t + e;
+        dy[e] = 0.0f;
+        if (o < NO && s < n) {
+          const float d = c[0][2 * hr + e] + sm.b3[o] - T[(size_t)s * NO + o];
           lsum += d * d;
-          dy = 2.0f * d * inv_n3;
+          dy[e] = 2.0f * d * inv_n3;
         }
+        bsum[e] += dy[e];
       }
-      bsum[e & 1] += dy;
-      sm.dY[r][o] = __float2bfloat16_rn(dy);
+      st_bf2(&sm.dY[r][2 * t], dy[0], dy[1]);
+      st_bf2(&sm.dY[r][8 + 2 * t], 0.0f, 0.0f);
     }
-    // dY columns 8..15 are zero padding
-    for (int q = lane; q < 16 * 8; q += 32) sm.dY[r0 + q / 8][8 + q % 8] = __float2bfloat16_rn(0.0f);
-    for (int o = 0; o < 2; ++o) {
-      const float v = colsum(bsum[o]);
-      if (g == 0 && 2 * t + o < NO) sm.cs[w][2 * t + o] = v;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float v = colsum(bsum[e]);
+      if (g == 0) sm.cs3[rg][2 * t + e] = v;
     }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    if (lane == 0) sm.loss[w] = lsum;
+    if (lane == 0) sm.loss[rg] = lsum;
   }
-  if (mode == 1) return;
-  float *gp = gpart + (size_t)tile * NPARAM;
   __syncthreads();
+  float *gp = gpart + (size_t)tile * NPARAM;
   if (tid < NO) {
     float v = 0.0f;
-    for (int q = 0; q < WARPS; ++q) v += sm.cs[q][tid];
+    for (int q = 0; q < WR; ++q) v += sm.cs3[q][tid];
     gp[ob3 + tid] = v;
   }
-  if (tid == 0) {
+  if (tid == 32) {
     float v = 0.0f;
-    for (int q = 0; q < WARPS; ++q) v += sm.loss[q];
+    for (int q = 0; q < WR; ++q) v += sm.loss[q];
     lpart[tile] = v;
   }
-  // dL/dW3 = dY^T A2 (outputs x hidden, summed over the tile's samples); warp w: hidden columns 32w..32w+31
+  // dL/dW3 = dY^T A2 (outputs x hidden, summed over the tile): warp w, hidden columns 16w..
   {
-    float c[4][4];
-    for (int nt = 0; nt < 4; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-    gemm<4>(c, Mat{&sm.dY[0][0], NOP, true}, 0, Mat{&sm.A2[0][0], NH, false}, 32 * w, S);
-    for (int nt = 0; nt < 4; ++nt)
-      for (int e = 0; e < 2; ++e) {
-        const int o = g, col = 32 * w + 8 * nt + 2 * t + e;
-        if (o < NO) gp[oW3 + o * NH + col] = c[nt][e];
-      }
+    float c[2][4];
+    zero<2>(c);
+    gemm<2, true, true>(c, &sm.dY[0][0], LDI, 0, &sm.A2[0][0], LDH, 16 * w, S);
+    wgrad_store<2>(c, gp + oW3, 0, 16 * w, NH, NO);
   }
-  __syncthreads();   // A2 is read above: from here on it holds dL/dz2
-  // dL/dz2 = (dY W3) * gelu'(z2), rows of this warp
+  // dL/dz2 = (dY W3) * gelu'(z2): rows r0.., columns c0..
   {
-    float c[16][4];
-    for (int nt = 0; nt < 16; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-    gemm<16>(c, Mat{&sm.dY[0][0], NOP, false}, r0, Mat{&sm.W3[0][0], NH, false}, 0, NOP);
-    for (int nt = 0; nt < 16; ++nt) {
-      float bs[2] = {0.0f, 0.0f};
-      for (int e = 0; e < 4; ++e) {
-        const int r = r0 + g + (e >> 1) * 8, col = 8 * nt + 2 * t + (e & 1);
-        const float dz = c[nt][e] * gelu_d(sm.Z2[r][col]);
-        bs[e & 1] += dz;
-        sm.A2[r][col] = __float2bfloat16_rn(dz);
-      }
-      for (int o = 0; o < 2; ++o) {
-        const float v = colsum(bs[o]);
-        if (g == 0) sm.cs[w][8 * nt + 2 * t + o] = v;
-      }
-    }
+    float c[NTH][4];
+    zero<NTH>(c);
+    gemm<NTH, false, true>(c, &sm.dY[0][0], LDI, r0, &sm.w.W3[0][0], LDH, c0, NOP);
+    dz_epilogue<NTH>(c, sm.Z2, sm.D2, sm.cs2[rg], r0, c0);
   }
   __syncthreads();
   for (int q = tid; q < NH; q += THREADS) {
     float v = 0.0f;
-    for (int ww = 0; ww < WARPS; ++ww) v += sm.cs[ww][q];
+    for (int k = 0; k < WR; ++k) v += sm.cs2[k][q];
     gp[ob2 + q] = v;
   }
-  // dL/dW2 = dZ2^T A1; warp w: output rows 32w..32w+31 in two 16-row tiles
-  for (int mt = 0; mt < 2; ++mt) {
+  // dL/dW2 = dZ2^T A1: warp w, output rows 16w..
+  {
     float c[16][4];
-    for (int nt = 0; nt < 16; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-    const int h0 = 32 * w + 16 * mt;
-    gemm<16>(c, Mat{&sm.A2[0][0], NH, true}, h0, Mat{&sm.A1[0][0], NH, false}, 0, S);
-    for (int nt = 0; nt < 16; ++nt)
-      for (int e = 0; e < 4; ++e) {
-        const int h = h0 + g + (e >> 1) * 8, col = 8 * nt + 2 * t + (e & 1);
-        gp[oW2 + h * NH + col] = c[nt][e];
-      }
+    zero<16>(c);
+    gemm<16, true, true>(c, &sm.D2[0][0], LDH, 16 * w, &sm.A1[0][0], LDH, 0, S);
+    wgrad_store<16>(c, gp + oW2, 16 * w, 0, NH, NH);
   }
-  // dL/dz1 = (dZ2 W2) * gelu'(z1), rows of this warp, kept in registers until A1 is free
-  float d1[16][4];
-  for (int nt = 0; nt < 16; ++nt) d1[nt][0] = d1[nt][1] = d1[nt][2] = d1[nt][3] = 0.0f;
-  gemm<16>(d1, Mat{&sm.A2[0][0], NH, false}, r0, Mat{&sm.W2[0][0], NH, false}, 0, NH);
-  __syncthreads();   // A1 is read by dL/dW2 above: from here on it holds dL/dz1
-  for (int nt = 0; nt < 16; ++nt) {
-    float bs[2] = {0.0f, 0.0f};
-    for (int e = 0; e < 4; ++e) {
-      const int r = r0 + g + (e >> 1) * 8, col = 8 * nt + 2 * t + (e & 1);
-      const float dz = d1[nt][e] * gelu_d(sm.Z1[r][col]);
-      bs[e & 1] += dz;
-      sm.A1[r][col] = __float2bfloat16_rn(dz);
-    }
-    for (int o = 0; o < 2; ++o) {
-      const float v = colsum(bs[o]);
-      if (g == 0) sm.cs[w][8 * nt + 2 * t + o] = v;
-    }
+  // dL/dz1 = (dZ2 W2) * gelu'(z1): rows r0.., columns c0..
+  {
+    float c[NTH][4];
+    zero<NTH>(c);
+    gemm<NTH, false, true>(c, &sm.D2[0][0], LDH, r0, &sm.w.W2[0][0], LDH, c0, NH);
+    dz_epilogue<NTH>(c, sm.Z1, sm.D1, sm.cs1[rg], r0, c0);
   }
   __syncthreads();
   for (int q = tid; q < NH; q += THREADS) {
     float v = 0.0f;
-    for (int ww = 0; ww < WARPS; ++ww) v += sm.cs[ww][q];
+    for (int k = 0; k < WR; ++k) v += sm.cs1[k][q];
     gp[ob1 + q] = v;
   }
-  // dL/dW1 = dZ1^T X; warp w: rows 32w..32w+31
-  for (int mt = 0; mt < 2; ++mt) {
+  // dL/dW1 = dZ1^T X: warp w, output rows 16w..
+  {
     float c[2][4];
-    for (int nt = 0; nt < 2; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.0f;
-    const int h0 = 32 * w + 16 * mt;
-    gemm<2>(c, Mat{&sm.A1[0][0], NH, true}, h0, Mat{&sm.X[0][0], NIP, false}, 0, S);
-    for (int nt = 0; nt < 2; ++nt)
-      for (int e = 0; e < 4; ++e) {
-        const int h = h0 + g + (e >> 1) * 8, i = 8 * nt + 2 * t + (e & 1);
-        if (i < NI) gp[oW1 + h * NI + i] = c[nt][e];
-      }
+    zero<2>(c);
+    gemm<2, true, true>(c, &sm.D1[0][0], LDH, 16 * w, &sm.X[0][0], LDI, 0, S);
+    wgrad_store<2>(c, gp + oW1, 16 * w, 0, NI, NH);
   }
 }
 
-// g[p] = sum over tiles of the partials, in tile order; loss likewise (block 0)
-__global__ void k_mlp_reduce(const float *__restrict__ gpart, const float *__restrict__ lpart, int ntiles,
-                             float *__restrict__ grad, double *__restrict__ loss, float inv_n3) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+struct AdamArgs {
+  int on;
+  float lr, b1, b2, eps, c1, c2;
+};
+
+// g[p] = sum over tiles of the partials in a fixed order (tiles w, w+8, .. per warp, then the
+// warps in order); optionally Adam (Kingma & Ba) on the FP32 master weights, refreshing the
+// BF16 copy. Block 0 also sums the loss.
+constexpr int RW = 8;   // warps of the reduction
+__global__ void __launch_bounds__(RW * 32) k_mlp_reduce(const float *__restrict__ gpart, const float *__restrict__ lpart,
+                                                        int ntiles, float *__restrict__ grad, double *__restrict__ loss,
+                                                        float inv_n3, float *__restrict__ P, float *__restrict__ m,
+                                                        float *__restrict__ v, bf *__restrict__ Wb, AdamArgs a) {
+  __shared__ float part[RW][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
+  float s = 0.0f;
   if (p < NPARAM) {
-    float v = 0.0f;
-    for (int q = 0; q < ntiles; ++q) v += gpart[(size_t)q * NPARAM + p];
-    grad[p] = v;
+#pragma unroll 4
+    for (int q = w; q < ntiles; q += RW) s += gpart[(size_t)q * NPARAM + p];
   }
-  if (p == 0) {
+  part[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && p < NPARAM) {
+    float gr = 0.0f;
+#pragma unroll
+    for (int k = 0; k < RW; ++k) gr += part[k][lane];
+    grad[p] = gr;
+    if (a.on) {
+      const float mm = a.b1 * m[p] + (1.0f - a.b1) * gr;
+      const float vv = a.b2 * v[p] + (1.0f - a.b2) * gr * gr;
+      m[p] = mm;
+      v[p] = vv;
+      const float x = P[p] - a.lr * (mm / a.c1) / (sqrtf(vv / a.c2) + a.eps);
+      P[p] = x;
+      const int q = wpack_index(p);
+      if (q >= 0) Wb[q] = __float2bfloat16_rn(x);
+    }
+  }
+  if (blockIdx.x == 0 && w == 1) {
     double l = 0.0;
-    for (int q = 0; q < ntiles; ++q) l += (double)lpart[q];
-    *loss = l * (double)inv_n3;
+    for (int q = lane; q < ntiles; q += 32) l += (double)lpart[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (lane == 0) *loss = l * (double)inv_n3;
   }
 }
 
-// Adam (Kingma & Ba) on the FP32 master weights
-__global__ void k_mlp_adam(float *__restrict__ P, const float *__restrict__ grad, float *__restrict__ m,
-                           float *__restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+// BF16 copy of the weights (the padding of the copy stays zero)
+__global__ void k_mlp_pack(const float *__restrict__ P, bf *__restrict__ Wb) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= NPARAM) return;
-  const float gr = grad[p];
-  const float mm = b1 * m[p] + (1.0f - b1) * gr;
-  const float vv = b2 * v[p] + (1.0f - b2) * gr * gr;
-  m[p] = mm;
-  v[p] = vv;
-  P[p] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+  const int q = wpack_index(p);
+  if (q >= 0) Wb[q] = __float2bfloat16_rn(P[p]);
 }
 
 }  // namespace
@@ -329,6 +404,7 @@ int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status,
 struct pic_mlp {
   float *P = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
   float *gpart = nullptr, *lpart = nullptr;
+  bf *Wb = nullptr;        // BF16 weights in the tile kernel's shared-memory layout
   double *loss = nullptr;
   int *status = nullptr;   // device: 1 once a bounded wait of the tensor-core forward gave up
   int cap_tiles = 0;
@@ -355,17 +431,26 @@ int run_forward(pic_mlp *h, const float *X, int n, float *Y, cudaStream_t st) {
   return mlp_forward_tc(h->P, X, n, Y, h->status, st);
 }
 
-int run_tiles(pic_mlp *h, const float *X, const float *T, int n, float *Y, int mode, cudaStream_t st) {
+int pack(pic_mlp *h) {
+  k_mlp_pack<<<(NPARAM + 255) / 256, 256>>>(h->P, h->Wb);
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : PIC_ECUDA;
+}
+
+// partial gradients of n samples, reduced into h->grad (and h->loss); Adam if a.on
+int run_tiles(pic_mlp *h, const float *X, const float *T, int n, const AdamArgs &a, cudaStream_t st) {
   if (n <= 0) return PIC_EINVAL;
-  if (mode == 0) {   // per-tile partial gradients only when training
-    const int rc = ensure(h, n);
-    if (rc) return rc;
-  }
+  const int rc = ensure(h, n);
+  if (rc) return rc;
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_mlp_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  });
   const int tiles = (n + S - 1) / S;
   const float inv_n3 = 1.0f / (3.0f * (float)n);
-  cudaFuncSetAttribute(k_mlp_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-  k_mlp_tile<<<tiles, THREADS, sizeof(Smem), st>>>(h->P, X, T, n, inv_n3, h->gpart, h->lpart, Y, mode);
-  if (mode == 0) k_mlp_reduce<<<(NPARAM + 255) / 256, 256, 0, st>>>(h->gpart, h->lpart, tiles, h->grad, h->loss, inv_n3);
+  k_mlp_tile<<<tiles, THREADS, sizeof(Smem), st>>>(h->P, reinterpret_cast<const WPack *>(h->Wb), X, T, n, inv_n3,
+                                                    h->gpart, h->lpart);
+  k_mlp_reduce<<<(NPARAM + 31) / 32, RW * 32, 0, st>>>(h->gpart, h->lpart, tiles, h->grad, h->loss, inv_n3, h->P,
+                                                       h->m, h->v, h->Wb, a);
   return cudaGetLastError() == cudaSuccess ? 0 : PIC_ECUDA;
 }
 
@@ -406,7 +491,8 @@ int pic_mlp_create(uint64_t seed, pic_mlp **out) {
   if (!h) return PIC_ENOMEM;
   if (cudaMalloc(&h->P, NPARAM * 4) != cudaSuccess || cudaMalloc(&h->m, NPARAM * 4) != cudaSuccess ||
       cudaMalloc(&h->v, NPARAM * 4) != cudaSuccess || cudaMalloc(&h->grad, NPARAM * 4) != cudaSuccess ||
-      cudaMalloc(&h->loss, 8) != cudaSuccess || cudaMalloc(&h->status, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&h->loss, 8) != cudaSuccess || cudaMalloc(&h->status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->Wb, sizeof(WPack)) != cudaSuccess) {
     pic_mlp_free(h);
     return PIC_ENOMEM;
   }
@@ -423,6 +509,11 @@ int pic_mlp_create(uint64_t seed, pic_mlp **out) {
   cudaMemset(h->m, 0, NPARAM * 4);
   cudaMemset(h->v, 0, NPARAM * 4);
   cudaMemset(h->status, 0, sizeof(int));
+  cudaMemset(h->Wb, 0, sizeof(WPack));
+  if (pack(h)) {
+    pic_mlp_free(h);
+    return PIC_ECUDA;
+  }
   *out = h;
   return 0;
 }
@@ -432,6 +523,7 @@ void pic_mlp_free(pic_mlp *h) {
   cudaFree(h->P); cudaFree(h->m); cudaFree(h->v); cudaFree(h->grad); cudaFree(h->gpart); cudaFree(h->lpart);
   cudaFree(h->loss);
   cudaFree(h->status);
+  cudaFree(h->Wb);
   delete h;
 }
 
@@ -441,7 +533,7 @@ int pic_mlp_set_params(pic_mlp *h, const float *host, int n) {
   cudaMemset(h->m, 0, NPARAM * 4);
   cudaMemset(h->v, 0, NPARAM * 4);
   h->t = 0;
-  return 0;
+  return pack(h);
 }
 
 int pic_mlp_get_params(pic_mlp *h, float *host, int n) {
@@ -461,7 +553,7 @@ int pic_mlp_forward(pic_mlp *h, const float *X, int n, float *Y, void *stream) {
 int pic_mlp_grad(pic_mlp *h, const float *X, const float *T, int n, float *grad_host, double *loss, void *stream) {
   if (!h || !X || !T) return PIC_EINVAL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int rc = run_tiles(h, X, T, n, nullptr, 0, st);
+  const int rc = run_tiles(h, X, T, n, AdamArgs{0, 0, 0, 0, 0, 0, 0}, st);
   if (rc) return rc;
   if (grad_host && cudaMemcpyAsync(grad_host, h->grad, NPARAM * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PIC_ECUDA;
@@ -477,11 +569,10 @@ int pic_mlp_train(pic_mlp *h, const float *X, const float *T, int n, int batch, 
   for (int k = 0; k < steps; ++k) {
     const long long off = ((long long)k * batch) % n;
     const int nb = (int)((off + batch <= n) ? batch : n - off);
-    int rc = run_tiles(h, X + off * NI, T + off * NO, nb, nullptr, 0, st);
-    if (rc) return rc;
     h->t += 1;
     const float c1 = 1.0f - powf(b1, (float)h->t), c2 = 1.0f - powf(b2, (float)h->t);
-    k_mlp_adam<<<(NPARAM + 255) / 256, 256, 0, st>>>(h->P, h->grad, h->m, h->v, lr, b1, b2, eps, c1, c2);
+    const int rc = run_tiles(h, X + off * NI, T + off * NO, nb, AdamArgs{1, lr, b1, b2, eps, c1, c2}, st);
+    if (rc) return rc;
   }
   if (last_loss && cudaMemcpyAsync(last_loss, h->loss, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PIC_ECUDA;
