@@ -4,10 +4,11 @@
 // ldmatrix, FP32 accumulation), FP32 master weights and optimizer state.
 // The forward pass of the fluid closure runs on tcgen05 (pic_mlp_tc.cu).
 //
-// One CTA of 8 warps trains on a tile of 64 samples: forward, backward and the
+// One CTA of 16 warps trains on a tile of 64 samples: forward, backward and the
 // weight gradients of its tile, written as a partial; a second kernel sums the
 // partials in a fixed order (deterministic gradients) and applies Adam, which
-// also refreshes the BF16 copy of the weights that the tile kernel stages.
+// also refreshes the BF16 copy of the weights that the tile kernel stages with
+// one bulk copy (TMA engine, completion on an mbarrier, bounded wait).
 // Parameter layout (FP32, flat): W1[128][15], b1[128], W2[128][128], b2[128],
 // W3[3][128], b3[3]  (row = output unit).
 #include <cuda_bf16.h>
@@ -28,11 +29,12 @@ constexpr int NI = 15, NIP = 16, NH = 128, NO = 3, NOP = 16;
 constexpr int LDI = NIP + 8, LDH = NH + 8, LDZ = NH + 8;   // padded rows: conflict-free ldmatrix
 constexpr int S = 64;                 // samples per tile
 constexpr int WR = S / 16;            // row groups of 16 samples
-constexpr int WC = 2;                 // column halves of the hidden layers
+constexpr int WC = 4;                 // column quarters of the hidden layers
 constexpr int WARPS = WR * WC;
 constexpr int THREADS = WARPS * 32;
 constexpr int oW1 = 0, ob1 = NH * NI, oW2 = ob1 + NH, ob2 = oW2 + NH * NH, oW3 = ob2 + NH, ob3 = oW3 + NO * NH;
 constexpr int NPARAM = ob3 + NO;      // 18947
+constexpr int kSpin = 200000;         // polls of an mbarrier (each suspends up to 10 us) before giving up
 
 using bf = __nv_bfloat16;
 
@@ -52,11 +54,13 @@ struct Smem {
   bf D2[S][LDH];       // dL/dz2
   bf D1[S][LDH];       // dL/dz1
   bf dY[S][LDI];       // dL/dy (columns 3..15 zero)
-  float Z1[S][LDZ];
-  float Z2[S][LDZ];
+  float G1[S][LDZ];    // gelu'(z1)
+  float G2[S][LDZ];    // gelu'(z2)
   float b1[NH], b2[NH], b3[NOP];
   float cs1[WR][NH], cs2[WR][NH], cs3[WR][NOP];   // per-row-group column sums (bias gradients)
   float loss[WR];
+  unsigned long long mbar;   // completion of the weight copy
+  int ok;
 };
 
 // index of parameter p in WPack (in BF16 elements), -1 for biases
@@ -79,6 +83,34 @@ __device__ __forceinline__ void ldsm4(unsigned r[4], const bf *p) {
 __device__ __forceinline__ void ldsm4t(unsigned r[4], const bf *p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(saddr(p)));
+}
+
+// one bulk copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte aligned),
+// completing on the mbarrier at mbar (initialised for one arrival by the calling thread)
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *mbar) {
+  const unsigned mb = saddr(mbar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(mb), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(mb)
+               : "memory");
+}
+__device__ __forceinline__ bool wait_phase(unsigned long long *mbar, unsigned parity) {
+  const unsigned mb = saddr(mbar);
+  for (int it = 0; it < kSpin; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, 10000;\nselp.b32 %0, 1, 0, P;\n}\n"
+        : "=r"(done)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    if (done) return true;
+    __nanosleep(64);
+  }
+  return false;
 }
 
 __device__ __forceinline__ void mma(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
@@ -124,17 +156,15 @@ __device__ __forceinline__ void st_bf2(bf *p, float x, float y) {
   *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(x, y);
 }
 
-// GELU (tanh form) through s = (1 + tanh u)/2 = 1/(1 + exp(-2u)), u = sqrt(2/pi)(z + 0.044715 z^3):
-// gelu = z s, gelu' = s + 2 z s (1 - s) du/dz
-__device__ __forceinline__ float gelu(float z) {
-  const float u = 0.7978845608028654f * (z + 0.044715f * z * z * z);
-  return __fdividef(z, 1.0f + __expf(-2.0f * u));
-}
-__device__ __forceinline__ float gelu_d(float z) {
-  const float c = 0.7978845608028654f;
-  const float u = c * (z + 0.044715f * z * z * z);
-  const float s = __fdividef(1.0f, 1.0f + __expf(-2.0f * u));
-  return s + 2.0f * z * s * (1.0f - s) * c * (1.0f + 3.0f * 0.044715f * z * z);
+// GELU (tanh form) and its derivative from th = tanh u, u = sqrt(2/pi)(z + 0.044715 z^3) (hardware
+// tanh): gelu = z (1 + th)/2, gelu' = (1 + th)/2 + z (1 - th^2) du/dz / 2
+__device__ __forceinline__ void gelu2(float z, float &y, float &dy) {
+  const float c = 0.7978845608028654f, z2 = z * z;
+  float th;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(c * z * (1.0f + 0.044715f * z2)));
+  const float h = 0.5f * (1.0f + th);
+  y = z * h;
+  dy = h + 0.5f * z * (1.0f - th * th) * c * (1.0f + 3.0f * 0.044715f * z2);
 }
 
 // sum of the two row values of a C fragment column over the 8 row groups (lanes t, t+4, ..)
@@ -145,9 +175,9 @@ __device__ __forceinline__ float colsum(float v) {
   return v;
 }
 
-// hidden-layer epilogue of a row pass: z = c + b -> Z (FP32), gelu(z) -> H (BF16)
+// hidden-layer epilogue of a row pass: z = c + b; gelu(z) -> H (BF16), gelu'(z) -> G (FP32)
 template <int NT>
-__device__ __forceinline__ void act_epilogue(const float c[NT][4], const float *b, float (*Z)[LDZ], bf (*H)[LDH],
+__device__ __forceinline__ void act_epilogue(const float c[NT][4], const float *b, float (*G)[LDZ], bf (*H)[LDH],
                                              int r0, int n0) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
@@ -155,15 +185,17 @@ __device__ __forceinline__ void act_epilogue(const float c[NT][4], const float *
 #pragma unroll
     for (int hr = 0; hr < 2; ++hr) {
       const int r = r0 + g + 8 * hr, col = n0 + 8 * nt + 2 * t;
-      const float z0 = c[nt][2 * hr] + b[col], z1 = c[nt][2 * hr + 1] + b[col + 1];
-      *reinterpret_cast<float2 *>(&Z[r][col]) = make_float2(z0, z1);
-      st_bf2(&H[r][col], gelu(z0), gelu(z1));
+      float y0, d0, y1, d1;
+      gelu2(c[nt][2 * hr] + b[col], y0, d0);
+      gelu2(c[nt][2 * hr + 1] + b[col + 1], y1, d1);
+      *reinterpret_cast<float2 *>(&G[r][col]) = make_float2(d0, d1);
+      st_bf2(&H[r][col], y0, y1);
     }
 }
 
 // backward epilogue of a row pass: dz = c * gelu'(z) -> D (BF16), column sums -> cs
 template <int NT>
-__device__ __forceinline__ void dz_epilogue(const float c[NT][4], const float (*Z)[LDZ], bf (*D)[LDH], float *cs,
+__device__ __forceinline__ void dz_epilogue(const float c[NT][4], const float (*G)[LDZ], bf (*D)[LDH], float *cs,
                                             int r0, int n0) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
@@ -172,8 +204,8 @@ __device__ __forceinline__ void dz_epilogue(const float c[NT][4], const float (*
 #pragma unroll
     for (int hr = 0; hr < 2; ++hr) {
       const int r = r0 + g + 8 * hr, col = n0 + 8 * nt + 2 * t;
-      const float2 z = *reinterpret_cast<const float2 *>(&Z[r][col]);
-      const float d0 = c[nt][2 * hr] * gelu_d(z.x), d1 = c[nt][2 * hr + 1] * gelu_d(z.y);
+      const float2 gd = *reinterpret_cast<const float2 *>(&G[r][col]);
+      const float d0 = c[nt][2 * hr] * gd.x, d1 = c[nt][2 * hr + 1] * gd.y;
       bs[0] += d0;
       bs[1] += d1;
       st_bf2(&D[r][col], d0, d1);
@@ -205,7 +237,7 @@ __device__ __forceinline__ void wgrad_store(const float c[NT][4], float *gp, int
 __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ P, const WPack *__restrict__ Wb,
                                                       const float *__restrict__ X, const float *__restrict__ T, int n,
                                                       float inv_n3, float *__restrict__ gpart,
-                                                      float *__restrict__ lpart) {
+                                                      float *__restrict__ lpart, int *__restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane >> 2, t = lane & 3;
@@ -213,14 +245,8 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
   const int r0 = 16 * rg, c0 = (NH / WC) * ch;
   constexpr int NTH = NH / WC / 8;             // column tiles of a hidden-layer row pass
   const int tile = blockIdx.x, s0 = tile * S;
-  // stage the BF16 weights, the FP32 biases and the tile's inputs
-  {
-    const uint4 *src = reinterpret_cast<const uint4 *>(Wb);
-    uint4 *dst = reinterpret_cast<uint4 *>(&sm.w);
-    constexpr int NV = (int)(sizeof(WPack) / 16);
-#pragma unroll 4
-    for (int q = tid; q < NV; q += THREADS) dst[q] = __ldg(src + q);
-  }
+  // stage the BF16 weights (one bulk copy), the FP32 biases and the tile's inputs
+  if (tid == 0) bulk_load(&sm.w, Wb, (unsigned)sizeof(WPack), &sm.mbar);
   for (int q = tid; q < NH; q += THREADS) { sm.b1[q] = P[ob1 + q]; sm.b2[q] = P[ob2 + q]; }
   if (tid < NOP) sm.b3[tid] = tid < NO ? P[ob3 + tid] : 0.0f;
   {
@@ -231,20 +257,29 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
     }
     for (int q = tid; q < S * (LDI - NI); q += THREADS) sm.X[q / (LDI - NI)][NI + q % (LDI - NI)] = __float2bfloat16_rn(0.0f);
   }
+  if (tid == 0) {
+    bool ok = wait_phase(&sm.mbar, 0);
+    if (!ok) {            // report, let the copy in flight land (bounded), skip the tile
+      atomicExch(status, 1);
+      wait_phase(&sm.mbar, 0);
+    }
+    sm.ok = ok;
+  }
   __syncthreads();
+  if (!sm.ok) return;
   // layer 1, then layer 2: rows r0.., columns c0..
   {
     float c[NTH][4];
     zero<NTH>(c);
     gemm<NTH, false, false>(c, &sm.X[0][0], LDI, r0, &sm.w.W1[0][0], LDI, c0, NIP);
-    act_epilogue<NTH>(c, sm.b1, sm.Z1, sm.A1, r0, c0);
+    act_epilogue<NTH>(c, sm.b1, sm.G1, sm.A1, r0, c0);
   }
   __syncthreads();
   {
     float c[NTH][4];
     zero<NTH>(c);
     gemm<NTH, false, false>(c, &sm.A1[0][0], LDH, r0, &sm.w.W2[0][0], LDH, c0, NH);
-    act_epilogue<NTH>(c, sm.b2, sm.Z2, sm.A2, r0, c0);
+    act_epilogue<NTH>(c, sm.b2, sm.G2, sm.A2, r0, c0);
   }
   __syncthreads();
   // layer 3, outputs, dL/dy, loss (one warp per row group)
@@ -292,8 +327,8 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
     for (int q = 0; q < WR; ++q) v += sm.loss[q];
     lpart[tile] = v;
   }
-  // dL/dW3 = dY^T A2 (outputs x hidden, summed over the tile): warp w, hidden columns 16w..
-  {
+  // dL/dW3 = dY^T A2 (outputs x hidden, summed over the tile): warp w < 8, hidden columns 16w..
+  if (w < NH / 16) {
     float c[2][4];
     zero<2>(c);
     gemm<2, true, true>(c, &sm.dY[0][0], LDI, 0, &sm.A2[0][0], LDH, 16 * w, S);
@@ -304,7 +339,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
     float c[NTH][4];
     zero<NTH>(c);
     gemm<NTH, false, true>(c, &sm.dY[0][0], LDI, r0, &sm.w.W3[0][0], LDH, c0, NOP);
-    dz_epilogue<NTH>(c, sm.Z2, sm.D2, sm.cs2[rg], r0, c0);
+    dz_epilogue<NTH>(c, sm.G2, sm.D2, sm.cs2[rg], r0, c0);
   }
   __syncthreads();
   for (int q = tid; q < NH; q += THREADS) {
@@ -312,19 +347,21 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
     for (int k = 0; k < WR; ++k) v += sm.cs2[k][q];
     gp[ob2 + q] = v;
   }
-  // dL/dW2 = dZ2^T A1: warp w, output rows 16w..
+  // dL/dW2 = dZ2^T A1: output rows 16 (w % 8).., columns 128 / (WARPS / 8) per warp
   {
-    float c[16][4];
-    zero<16>(c);
-    gemm<16, true, true>(c, &sm.D2[0][0], LDH, 16 * w, &sm.A1[0][0], LDH, 0, S);
-    wgrad_store<16>(c, gp + oW2, 16 * w, 0, NH, NH);
+    constexpr int NTW = NH / 8 / (WARPS / 8);
+    const int h0 = 16 * (w % 8), n0 = NTW * 8 * (w / 8);
+    float c[NTW][4];
+    zero<NTW>(c);
+    gemm<NTW, true, true>(c, &sm.D2[0][0], LDH, h0, &sm.A1[0][0], LDH, n0, S);
+    wgrad_store<NTW>(c, gp + oW2, h0, n0, NH, NH);
   }
   // dL/dz1 = (dZ2 W2) * gelu'(z1): rows r0.., columns c0..
   {
     float c[NTH][4];
     zero<NTH>(c);
     gemm<NTH, false, true>(c, &sm.D2[0][0], LDH, r0, &sm.w.W2[0][0], LDH, c0, NH);
-    dz_epilogue<NTH>(c, sm.Z1, sm.D1, sm.cs1[rg], r0, c0);
+    dz_epilogue<NTH>(c, sm.G1, sm.D1, sm.cs1[rg], r0, c0);
   }
   __syncthreads();
   for (int q = tid; q < NH; q += THREADS) {
@@ -332,8 +369,8 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
     for (int k = 0; k < WR; ++k) v += sm.cs1[k][q];
     gp[ob1 + q] = v;
   }
-  // dL/dW1 = dZ1^T X: warp w, output rows 16w..
-  {
+  // dL/dW1 = dZ1^T X: warp w < 8, output rows 16w..
+  if (w < NH / 16) {
     float c[2][4];
     zero<2>(c);
     gemm<2, true, true>(c, &sm.D1[0][0], LDH, 16 * w, &sm.X[0][0], LDI, 0, S);
@@ -349,7 +386,7 @@ struct AdamArgs {
 // g[p] = sum over tiles of the partials in a fixed order (tiles w, w+8, .. per warp, then the
 // warps in order); optionally Adam (Kingma & Ba) on the FP32 master weights, refreshing the
 // BF16 copy. Block 0 also sums the loss.
-constexpr int RW = 8;   // warps of the reduction
+constexpr int RW = 16;  // warps of the reduction
 __global__ void __launch_bounds__(RW * 32) k_mlp_reduce(const float *__restrict__ gpart, const float *__restrict__ lpart,
                                                         int ntiles, float *__restrict__ grad, double *__restrict__ loss,
                                                         float inv_n3, float *__restrict__ P, float *__restrict__ m,
@@ -359,7 +396,7 @@ __global__ void __launch_bounds__(RW * 32) k_mlp_reduce(const float *__restrict_
   const int p = blockIdx.x * 32 + lane;
   float s = 0.0f;
   if (p < NPARAM) {
-#pragma unroll 4
+#pragma unroll 8
     for (int q = w; q < ntiles; q += RW) s += gpart[(size_t)q * NPARAM + p];
   }
   part[w][lane] = s;
@@ -448,7 +485,7 @@ int run_tiles(pic_mlp *h, const float *X, const float *T, int n, const AdamArgs 
   const int tiles = (n + S - 1) / S;
   const float inv_n3 = 1.0f / (3.0f * (float)n);
   k_mlp_tile<<<tiles, THREADS, sizeof(Smem), st>>>(h->P, reinterpret_cast<const WPack *>(h->Wb), X, T, n, inv_n3,
-                                                    h->gpart, h->lpart);
+                                                    h->gpart, h->lpart, h->status);
   k_mlp_reduce<<<(NPARAM + 31) / 32, RW * 32, 0, st>>>(h->gpart, h->lpart, tiles, h->grad, h->loss, inv_n3, h->P,
                                                        h->m, h->v, h->Wb, a);
   return cudaGetLastError() == cudaSuccess ? 0 : PIC_ECUDA;
@@ -558,7 +595,8 @@ int pic_mlp_grad(pic_mlp *h, const float *X, const float *T, int n, float *grad_
   if (grad_host && cudaMemcpyAsync(grad_host, h->grad, NPARAM * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PIC_ECUDA;
   if (loss && cudaMemcpyAsync(loss, h->loss, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return PIC_ECUDA;
-  return cudaStreamSynchronize(st) == cudaSuccess ? 0 : PIC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PIC_ECUDA;
+  return mlp_take_status(h);
 }
 
 int pic_mlp_train(pic_mlp *h, const float *X, const float *T, int n, int batch, int steps, float lr,
@@ -576,7 +614,8 @@ int pic_mlp_train(pic_mlp *h, const float *X, const float *T, int n, int batch, 
   }
   if (last_loss && cudaMemcpyAsync(last_loss, h->loss, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PIC_ECUDA;
-  return cudaStreamSynchronize(st) == cudaSuccess ? 0 : PIC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PIC_ECUDA;
+  return mlp_take_status(h);
 }
 
 }  // extern "C"
