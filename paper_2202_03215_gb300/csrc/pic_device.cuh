@@ -26,6 +26,19 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
   return c;
 }
 
+// the same function with its ten round keys given (rk[r] = key + r Weyl constants), so that
+// a kernel whose key is a launch parameter reads them as constant operands
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t (&rk)[10][2]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[r][0], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk[r][1],
+                   (uint32_t)p0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ uint2 seed_key(uint64_t seed) {
   return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
 }

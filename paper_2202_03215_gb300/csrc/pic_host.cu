@@ -229,6 +229,10 @@ template <class R> int setup_tables(pic_handle *h) {
   k.sub = p.ion_subcycle;
   k.column = (uint32_t)p.column;
   k.seed = p.seed;
+  for (int r = 0; r < 10; ++r) {
+    k.rk[r][0] = (uint32_t)p.seed + (uint32_t)r * 0x9E3779B9u;
+    k.rk[r][1] = (uint32_t)(p.seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+  }
   const double M = h->M;
   k.V_e = (R)(2.0 * kQe / kMe);
   k.em = (R)(2.0 * kMe / M);

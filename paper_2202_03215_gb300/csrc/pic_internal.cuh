@@ -76,6 +76,7 @@ template <class R> struct StepK {
   int diag_every, sub;
   uint32_t column;
   uint64_t seed;
+  uint32_t rk[10][2];             // Philox round keys of seed: key + r (0x9E3779B9, 0xBB67AE85)
   R V_e, em, sig_n;               // 2e/m, 2m/M, sqrt(kT_g/M)
   const float *gauss;             // kGaussN+1 entries
   SpecK<R> sp[2];

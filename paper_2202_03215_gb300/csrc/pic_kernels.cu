@@ -84,8 +84,8 @@ __device__ void bitonic_sort(unsigned long long *a, int n2) {
 // tiles of blockDim particles.
 //   phase A (every particle): gather, leapfrog push, wrap, the Philox block
 //     that decides collision candidacy (u0 < P_null) and radial loss, the
-//     cloud-in-cell deposit (warp-aggregated over equal cells into 64-bit
-//     fixed-point bins in shared memory over a cell window), and the store of
+//     cloud-in-cell deposit (into 64-bit fixed-point bins in shared memory
+//     over a cell window, one atomic update per particle), and the store of
 //     every non-candidate; candidates go to a shared-memory queue;
 //   phase B (whenever a warp has queued 32 candidates, and at the end): the
 //     collision path for 32 queued candidates, one per lane, so that a warp
@@ -286,46 +286,18 @@ __device__ __forceinline__ void cell_add(const CellBins &b, int N, int32_t cell,
   }
 }
 
-// Deposit of one warp.  Sorted particles come in runs of neighbouring lanes
-// in one cell: those are summed by a segmented warp scan and added once by
-// the run's last lane; when no two neighbouring lanes share a cell every
-// lane adds its own particle.  Lanes with in == false contribute nothing.
-// All 32 lanes must call it.
-__device__ __forceinline__ void deposit_runs(bool in, int lane, int32_t cell, unsigned long long kk, int N,
-                                             const CellBins &b, unsigned long long *Q) {
-  const unsigned mask = __ballot_sync(kFull, in);
-  const int32_t pc = __shfl_up_sync(kFull, cell, 1);
-  const bool pin = lane > 0 && ((mask >> (lane - 1)) & 1u);
-  const bool head = !in || !pin || pc != cell;
-  if (__ballot_sync(kFull, !head) == 0) {
-    if (in) cell_add(b, N, cell, 1u, kk, Q);
-    return;
-  }
-  const int32_t nc = __shfl_down_sync(kFull, cell, 1);
-  const bool nin = lane < 31 && ((mask >> (lane + 1)) & 1u);
-  const bool tail = in && (!nin || nc != cell);
-  int start = head ? lane : 0;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(kFull, start, o);
-    if (lane >= o) start = max(start, t);
-  }
-  // low 16 bits of k plus a count in bits 21..; high 16 bits separately (no overflow over 32 lanes)
-  unsigned a = in ? (((unsigned)kk & 0xffffu) | (1u << 21)) : 0u;
-  unsigned c = in ? (unsigned)(kk >> 16) : 0u;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned ta = __shfl_up_sync(kFull, a, o), tc = __shfl_up_sync(kFull, c, o);
-    if (lane - o >= start) { a += ta; c += tc; }
-  }
-  if (tail) {
-    const unsigned long long sk = ((unsigned long long)c << 16) + (unsigned long long)(a & 0x1fffffu);
-    cell_add(b, N, cell, a >> 21, sk, Q);
-  }
+// Deposit of one particle into the CTA's shared-memory bins (lanes with in == false contribute
+// nothing).  Lanes of a warp that share a cell are serialised by the shared-memory atomics;
+// that costs less than summing runs of equal cells with warp shuffles first, even right after
+// a sort, when most lanes of a warp share a cell.
+__device__ __forceinline__ void deposit(bool in, int32_t cell, unsigned long long kk, int N, const CellBins &b,
+                                        unsigned long long *Q) {
+  if (in) cell_add(b, N, cell, 1u, kk, Q);
 }
 
-// one CTA's share (cta of ncta) of the particle step of one column
-template <class R, int SP>
+// one CTA's share (cta of ncta) of the particle step of one column; PK: k is a launch
+// parameter (the Philox round keys are read from it as constants)
+template <class R, int SP, bool PK>
 __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef,
                                           BirthBuf<R> bb, Moments m, int W, int smemE, int cta, int ncta,
                                           unsigned char *smem) {
@@ -424,7 +396,8 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     if (valid) {
       const R Ep = gather(E, cell, off);
       push<R>(N, sp.a, sp.d, Ep, cell, off, vx);
-      const uint4 w0 = philox10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, c3), key);
+      const uint4 ctr = make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, c3);
+      const uint4 w0 = PK ? philox10_rk(ctr, k.rk) : philox10(ctr, key);
       dead = radial && (w0.z < sp.Pw);
       if (!dead) {
         u1 = u_dec<R>(w0.y);
@@ -460,8 +433,8 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
       Qd.slot[qi] = p; Qd.cell[qi] = cell;
     }
     wq += __popc(bal);
-    // charge deposit, summed over runs of lanes in the same cell
-    deposit_runs(valid && !dead, lane, cell, wfix(off), N, bins, s.Q);
+    // charge deposit into the window bins
+    deposit(valid && !dead, cell, wfix(off), N, bins, s.Q);
     __syncwarp();
     if (wq >= 32) {
       flush(32);
@@ -505,7 +478,7 @@ __global__ void __launch_bounds__(kStepThreads, 1)
 k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef, BirthBuf<R> bb,
        Moments m, int W, int smemE) {
   extern __shared__ __align__(16) unsigned char smem[];
-  push_body<R, SP>(k, s, ctl, Ef, bb, m, W, smemE, blockIdx.x, gridDim.x, smem);
+  push_body<R, SP, true>(k, s, ctl, Ef, bb, m, W, smemE, blockIdx.x, gridDim.x, smem);
 }
 
 // batched columns: CTA b runs share sched[b].y of sched[b].z of column sched[b].x
@@ -521,7 +494,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_push_batch(const ColDev<R> 
     for (int q = threadIdx.x; q < (int)(sizeof(StepK<R>) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
   }
   __syncthreads();
-  push_body<R, SP>(sk, cd->sp[SP], cd->ctl, reinterpret_cast<const R *>(cd->Ef), cd->bb, cd->m, cd->W, cd->smemE,
+  push_body<R, SP, false>(sk, cd->sp[SP], cd->ctl, reinterpret_cast<const R *>(cd->Ef), cd->bb, cd->m, cd->W, cd->smemE,
                    sc.y, sc.z, smem);
 }
 

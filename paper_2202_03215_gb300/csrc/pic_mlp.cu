@@ -34,6 +34,7 @@ constexpr int WARPS = WR * WC;
 constexpr int THREADS = WARPS * 32;
 constexpr int oW1 = 0, ob1 = NH * NI, oW2 = ob1 + NH, ob2 = oW2 + NH * NH, oW3 = ob2 + NH, ob3 = oW3 + NO * NH;
 constexpr int NPARAM = ob3 + NO;      // 18947
+constexpr int GSTRIDE = (NPARAM + 3) & ~3;   // floats between the partials of two tiles (8-byte pairs stay aligned)
 constexpr int kSpin = 200000;         // polls of an mbarrier (each suspends up to 10 us) before giving up
 
 using bf = __nv_bfloat16;
@@ -45,6 +46,7 @@ struct WPack {
   bf W3[NOP][LDH];
 };
 static_assert(sizeof(WPack) % 16 == 0, "16-byte copies");
+static_assert(oW2 % 2 == 0 && oW3 % 2 == 0 && GSTRIDE % 2 == 0, "8-byte pairs of partial gradients");
 
 struct Smem {
   WPack w;
@@ -112,6 +114,11 @@ __device__ __forceinline__ bool wait_phase(unsigned long long *mbar, unsigned pa
   }
   return false;
 }
+
+// programmatic dependent launch: let the next kernel of the stream start its launch now; wait
+// for the previous kernel of the stream to complete (no-op without a programmatic dependency)
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ void mma(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
   asm volatile(
@@ -228,12 +235,17 @@ __device__ __forceinline__ void wgrad_store(const float c[NT][4], float *gp, int
     for (int hr = 0; hr < 2; ++hr) {
       const int h = h0 + g + 8 * hr, col = n0 + 8 * nt + 2 * t;
       if (h >= nrow) continue;
-      if (col < ncol) gp[h * ncol + col] = c[nt][2 * hr];
-      if (col + 1 < ncol) gp[h * ncol + col + 1] = c[nt][2 * hr + 1];
+      if (ncol % 2 == 0) {   // the pair is 8-byte aligned: partial and matrix offsets are even
+        *reinterpret_cast<float2 *>(&gp[h * ncol + col]) = make_float2(c[nt][2 * hr], c[nt][2 * hr + 1]);
+      } else {
+        if (col < ncol) gp[h * ncol + col] = c[nt][2 * hr];
+        if (col + 1 < ncol) gp[h * ncol + col + 1] = c[nt][2 * hr + 1];
+      }
     }
 }
 
-// forward + backward of one tile of S samples; partial gradients (NPARAM floats) and loss per tile
+// forward + backward of one tile of S samples; partial gradients (NPARAM floats at a stride of
+// GSTRIDE) and loss per tile
 __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ P, const WPack *__restrict__ Wb,
                                                       const float *__restrict__ X, const float *__restrict__ T, int n,
                                                       float inv_n3, float *__restrict__ gpart,
@@ -245,7 +257,11 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
   const int r0 = 16 * rg, c0 = (NH / WC) * ch;
   constexpr int NTH = NH / WC / 8;             // column tiles of a hidden-layer row pass
   const int tile = blockIdx.x, s0 = tile * S;
-  // stage the BF16 weights (one bulk copy), the FP32 biases and the tile's inputs
+  // everything this kernel reads may come from the previous kernel of the stream (the inputs
+  // from the caller's producer, the weights from the previous step's Adam update)
+  pdl_launch_next();
+  pdl_wait_prev();
+  // the BF16 weights by one bulk copy, the FP32 biases and the tile's inputs
   if (tid == 0) bulk_load(&sm.w, Wb, (unsigned)sizeof(WPack), &sm.mbar);
   for (int q = tid; q < NH; q += THREADS) { sm.b1[q] = P[ob1 + q]; sm.b2[q] = P[ob2 + q]; }
   if (tid < NOP) sm.b3[tid] = tid < NO ? P[ob3 + tid] : 0.0f;
@@ -316,7 +332,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
     if (lane == 0) sm.loss[rg] = lsum;
   }
   __syncthreads();
-  float *gp = gpart + (size_t)tile * NPARAM;
+  float *gp = gpart + (size_t)tile * GSTRIDE;
   if (tid < NO) {
     float v = 0.0f;
     for (int q = 0; q < WR; ++q) v += sm.cs3[q][tid];
@@ -392,12 +408,14 @@ __global__ void __launch_bounds__(RW * 32) k_mlp_reduce(const float *__restrict_
                                                         float inv_n3, float *__restrict__ P, float *__restrict__ m,
                                                         float *__restrict__ v, bf *__restrict__ Wb, AdamArgs a) {
   __shared__ float part[RW][32];
+  pdl_launch_next();
+  pdl_wait_prev();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + lane;
   float s = 0.0f;
   if (p < NPARAM) {
 #pragma unroll 8
-    for (int q = w; q < ntiles; q += RW) s += gpart[(size_t)q * NPARAM + p];
+    for (int q = w; q < ntiles; q += RW) s += gpart[(size_t)q * GSTRIDE + p];
   }
   part[w][lane] = s;
   __syncthreads();
@@ -457,7 +475,7 @@ int ensure(pic_mlp *h, int n) {
   cudaFree(h->lpart);
   h->gpart = nullptr;
   h->lpart = nullptr;
-  if (cudaMalloc(&h->gpart, (size_t)tiles * NPARAM * 4) != cudaSuccess ||
+  if (cudaMalloc(&h->gpart, (size_t)tiles * GSTRIDE * 4) != cudaSuccess ||
       cudaMalloc(&h->lpart, (size_t)tiles * 4) != cudaSuccess)
     return PIC_ENOMEM;
   h->cap_tiles = tiles;
@@ -484,11 +502,29 @@ int run_tiles(pic_mlp *h, const float *X, const float *T, int n, const AdamArgs 
   });
   const int tiles = (n + S - 1) / S;
   const float inv_n3 = 1.0f / (3.0f * (float)n);
-  k_mlp_tile<<<tiles, THREADS, sizeof(Smem), st>>>(h->P, reinterpret_cast<const WPack *>(h->Wb), X, T, n, inv_n3,
-                                                    h->gpart, h->lpart, h->status);
-  k_mlp_reduce<<<(NPARAM + 31) / 32, RW * 32, 0, st>>>(h->gpart, h->lpart, tiles, h->grad, h->loss, inv_n3, h->P,
-                                                       h->m, h->v, h->Wb, a);
-  return cudaGetLastError() == cudaSuccess ? 0 : PIC_ECUDA;
+  // both kernels with programmatic stream serialization: each may be scheduled while the
+  // previous kernel of the stream drains and waits for it (griddepcontrol.wait) before it
+  // reads that kernel's results
+  cudaLaunchAttribute pdl;
+  pdl.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.stream = st;
+  cfg.attrs = &pdl;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(tiles);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = sizeof(Smem);
+  if (cudaLaunchKernelEx(&cfg, k_mlp_tile, (const float *)h->P, (const WPack *)h->Wb, X, T, n, inv_n3, h->gpart,
+                         h->lpart, h->status) != cudaSuccess)
+    return PIC_ECUDA;
+  cfg.gridDim = dim3((NPARAM + 31) / 32);
+  cfg.blockDim = dim3(RW * 32);
+  cfg.dynamicSmemBytes = 0;
+  if (cudaLaunchKernelEx(&cfg, k_mlp_reduce, (const float *)h->gpart, (const float *)h->lpart, tiles, h->grad, h->loss,
+                         inv_n3, h->P, h->m, h->v, h->Wb, a) != cudaSuccess)
+    return PIC_ECUDA;
+  return 0;
 }
 
 // splitmix64 (Steele, Lea, Flood 2014): seeds the initial weights
