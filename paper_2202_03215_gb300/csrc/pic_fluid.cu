@@ -88,32 +88,131 @@ __device__ __forceinline__ void add2(float &hi, float &lo, float d) {
   lo = l - (hi - s);
 }
 
-// periodic parallel cyclic reduction; N a power of two; row j: pa x_{j-1} + pb x_j + pc x_{j+1} = pd
-// (fast divisions, a few ulp: the systems are diagonally dominant and well conditioned)
-__device__ void pcr(const Sm &S, int N) {
+// periodic parallel cyclic reduction; N a power of two, N <= RP kThreads; row j:
+// pa x_{j-1} + pb x_j + pc x_{j+1} = pd (fast divisions, a few ulp: the systems are
+// diagonally dominant and well conditioned)
+template <int RP>
+__device__ void pcr(float *pa, float *pb, float *pc, float *pd, int N) {
   const int t = threadIdx.x;
   for (int s = 1; s < N; s <<= 1) {
-    float na[kRows], nb[kRows], nc[kRows], nd[kRows];
+    float na[RP], nb[RP], nc[RP], nd[RP];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
+    for (int r = 0; r < RP; ++r) {
       const int j = t + r * kThreads;
       if (j < N) {
         const int jm = (j - s) & (N - 1), jp = (j + s) & (N - 1);
-        const float al = -__fdividef(S.pa[j], S.pb[jm]), be = -__fdividef(S.pc[j], S.pb[jp]);
-        na[r] = al * S.pa[jm];
-        nc[r] = be * S.pc[jp];
-        nb[r] = S.pb[j] + al * S.pc[jm] + be * S.pa[jp];
-        nd[r] = S.pd[j] + al * S.pd[jm] + be * S.pd[jp];
+        const float al = -__fdividef(pa[j], pb[jm]), be = -__fdividef(pc[j], pb[jp]);
+        na[r] = al * pa[jm];
+        nc[r] = be * pc[jp];
+        nb[r] = pb[j] + al * pc[jm] + be * pa[jp];
+        nd[r] = pd[j] + al * pd[jm] + be * pd[jp];
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
+    for (int r = 0; r < RP; ++r) {
       const int j = t + r * kThreads;
-      if (j < N) { S.pa[j] = na[r]; S.pb[j] = nb[r]; S.pc[j] = nc[r]; S.pd[j] = nd[r]; }
+      if (j < N) { pa[j] = na[r]; pb[j] = nb[r]; pc[j] = nc[r]; pd[j] = nd[r]; }
     }
     __syncthreads();
   }
+}
+
+// m (2, 4 or 8) consecutive floats at p (m-float aligned) into x[0..m), by vector loads
+__device__ __forceinline__ void ld_rows(const float *p, int m, float (&x)[kRows]) {
+  if (m == 8) {
+    const float4 u = *reinterpret_cast<const float4 *>(p), v = *reinterpret_cast<const float4 *>(p + 4);
+    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w; x[4] = v.x; x[5] = v.y; x[6] = v.z; x[7] = v.w;
+  } else if (m == 4) {
+    const float4 u = *reinterpret_cast<const float4 *>(p);
+    x[0] = u.x; x[1] = u.y; x[2] = u.z; x[3] = u.w;
+  } else {
+    const float2 u = *reinterpret_cast<const float2 *>(p);
+    x[0] = u.x; x[1] = u.y;
+  }
+}
+__device__ __forceinline__ void st_rows(float *p, int m, const float (&x)[kRows]) {
+  if (m == 8) {
+    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    *reinterpret_cast<float4 *>(p + 4) = make_float4(x[4], x[5], x[6], x[7]);
+  } else if (m == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  } else {
+    *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+  }
+}
+
+// Periodic tridiagonal solve, N a power of two in [64, kMaxCells]; row j:
+// pa x_{j-1} + pb x_j + pc x_{j+1} = pd; the solution is left in pd (pa, pb, pc are
+// overwritten).  Partition method: thread p takes the m = max(2, N / kThreads) rows
+// [p m, p m + m) into registers and eliminates them (a forward and a backward sweep)
+// until every row couples only to the partition's own first and last unknowns; the
+// first row then couples to the previous partition's last unknown and the last row to
+// the next partition's first, so the first and last rows of all partitions form a
+// periodic tridiagonal system of 2N/m rows, solved by parallel cyclic reduction; the
+// interior unknowns follow by substitution.  The systems are diagonally dominant: no
+// pivoting, fast reciprocals.
+__device__ void solve(float *pa, float *pb, float *pc, float *pd, int N) {
+  const int m = max(2, N / kThreads), P = N / m, t = threadIdx.x, j0 = t * m;
+  float a[kRows], b[kRows], c[kRows], d[kRows];
+  if (t < P) {
+    ld_rows(pa + j0, m, a);
+    ld_rows(pb + j0, m, b);
+    ld_rows(pc + j0, m, c);
+    ld_rows(pd + j0, m, d);
+    // forward: rows 0 and 1 normalised; row i >= 2 loses x_{i-1} and gains x_0 (coefficient in a)
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float r = __fdividef(1.0f, b[i]);
+      a[i] *= r; c[i] *= r; d[i] *= r;
+    }
+#pragma unroll
+    for (int i = 2; i < kRows; ++i)
+      if (i < m) {
+        const float r = __fdividef(1.0f, b[i] - a[i] * c[i - 1]);
+        d[i] = (d[i] - a[i] * d[i - 1]) * r;
+        a[i] = -a[i] * a[i - 1] * r;
+        c[i] *= r;
+      }
+    // backward: row i in [1, m - 3] loses x_{i+1} and gains x_{m-1} (coefficient in c)
+#pragma unroll
+    for (int i = kRows - 3; i >= 1; --i)
+      if (i <= m - 3) {
+        const float q = c[i];
+        a[i] -= q * a[i + 1];
+        d[i] -= q * d[i + 1];
+        c[i] = -q * c[i + 1];
+      }
+    // row 0 loses x_1 (for m >= 3; for m == 2, x_1 is the last unknown already)
+    if (m >= 3) {
+      const float q = c[0], r = __fdividef(1.0f, 1.0f - q * a[1]);
+      a[0] *= r;
+      d[0] = (d[0] - q * d[1]) * r;
+      c[0] = -q * c[1] * r;
+    }
+  }
+  __syncthreads();   // every partition is in registers: the arrays take the reduced system
+  if (t < P) {
+    // the last row, m - 1 (selected explicitly: an index computed from m would put the rows in
+    // local memory)
+    const float aL = m == 8 ? a[7] : m == 4 ? a[3] : a[1];
+    const float cL = m == 8 ? c[7] : m == 4 ? c[3] : c[1];
+    const float dL = m == 8 ? d[7] : m == 4 ? d[3] : d[1];
+    pa[2 * t] = a[0]; pb[2 * t] = 1.0f; pc[2 * t] = c[0]; pd[2 * t] = d[0];
+    pa[2 * t + 1] = aL; pb[2 * t + 1] = 1.0f; pc[2 * t + 1] = cL; pd[2 * t + 1] = dL;
+  }
+  __syncthreads();
+  pcr<2>(pa, pb, pc, pd, 2 * P);   // 2P = 2N/m <= 2 kThreads
+  float x[kRows];
+  if (t < P) {
+    const float F = __fdividef(pd[2 * t], pa[2 * t] + pb[2 * t] + pc[2 * t]);
+    const float L = __fdividef(pd[2 * t + 1], pa[2 * t + 1] + pb[2 * t + 1] + pc[2 * t + 1]);
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) x[i] = (i == 0) ? F : (i == m - 1) ? L : d[i] - a[i] * F - c[i] * L;
+  }
+  __syncthreads();   // the reduced solution is read: pd takes the solution
+  if (t < P) st_rows(pd + j0, m, x);
+  __syncthreads();
 }
 
 // correction of cell j: scaled network outputs, or fixed corrections, or none
@@ -219,8 +318,8 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
               c.s * (af - am) * c.GT + K.dt * S.n[j] * (nu - nu_w) - c.s * (dGf - dGm);
   }
   __syncthreads();
-  pcr(S, N);
-  for (int j = t; j < N; j += kThreads) add2(S.n[j], S.nl[j], __fdividef(S.pd[j], S.pa[j] + S.pb[j] + S.pc[j]));
+  solve(S.pa, S.pb, S.pc, S.pd, N);
+  for (int j = t; j < N; j += kThreads) add2(S.n[j], S.nl[j], S.pd[j]);
   __syncthreads();
   // 3. flux and field at faces from n'; energy coefficients into pa (mu_eps), pb (D_eps)
   field(S, c);
@@ -253,13 +352,11 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
     S.A[j] = h;
   }
   __syncthreads();
-  // 4. energy: A dT = rhs - A T (built in registers: rows read the neighbours' pa, pb)
+  // 4. energy: A dT = rhs - A T, into D, B, pc, pd (rows read the neighbours' pa, pb; D and B
+  //    are free once the field is formed)
   {
-    float ra[kRows], rb[kRows], rc[kRows], rd[kRows];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-      const int j = t + r * kThreads;
-      if (j < N) {
+    for (int j = t; j < N; j += kThreads) {
+      {
         const int jm = (j - 1) & (N - 1), jp = (j + 1) & (N - 1);
         const float P = -0.5f * (S.G[j] * S.E[j] + S.G[jm] * S.E[jm]);
         int i; float f;
@@ -269,24 +366,18 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
         const float mep = 0.5f * (S.pa[j] + S.pa[jp]), mem = 0.5f * (S.pa[jm] + S.pa[j]);
         const float Ep = S.E[j], Em = S.E[jm];
         const float n1 = S.n[j];
-        rb[r] = 1.5f * n1 + K.dt * n1 * dL + c.s * (-0.75f * mep * Ep + 0.75f * mem * Em) * n1 +
-                2.0f * c.s * c.k * n1 * S.pb[j];
-        rc[r] = c.s * (-0.75f * mep * Ep - c.k * S.pb[jp]) * S.n[jp];
-        ra[r] = c.s * (0.75f * mem * Em - c.k * S.pb[jm]) * S.n[jm];
-        rd[r] = 1.5f * (S.u[j] - n1) * S.T[j] + K.dt * P - K.dt * n1 * L - c.s * (S.A[j] - S.A[jm]);
+        S.B[j] = 1.5f * n1 + K.dt * n1 * dL + c.s * (-0.75f * mep * Ep + 0.75f * mem * Em) * n1 +
+                 2.0f * c.s * c.k * n1 * S.pb[j];
+        S.pc[j] = c.s * (-0.75f * mep * Ep - c.k * S.pb[jp]) * S.n[jp];
+        S.D[j] = c.s * (0.75f * mem * Em - c.k * S.pb[jm]) * S.n[jm];
+        S.pd[j] = 1.5f * (S.u[j] - n1) * S.T[j] + K.dt * P - K.dt * n1 * L - c.s * (S.A[j] - S.A[jm]);
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-      const int j = t + r * kThreads;
-      if (j < N) { S.pa[j] = ra[r]; S.pb[j] = rb[r]; S.pc[j] = rc[r]; S.pd[j] = rd[r]; }
-    }
-    __syncthreads();
   }
-  pcr(S, N);
+  solve(S.D, S.B, S.pc, S.pd, N);
   for (int j = t; j < N; j += kThreads) {
-    add2(S.T[j], S.Tl[j], __fdividef(S.pd[j], S.pa[j] + S.pb[j] + S.pc[j]));
+    add2(S.T[j], S.Tl[j], S.pd[j]);
     if (S.T[j] < K.T0) { S.T[j] = K.T0; S.Tl[j] = 0.0f; }
     if (S.T[j] > K.Tmax) { S.T[j] = K.Tmax; S.Tl[j] = 0.0f; }
   }

@@ -38,7 +38,8 @@ def columns():
     return [dict(L_m=0.05, N_gas_m3=N_GAS, mu_iN=1.1e22, Gamma_T=1.5e20, nu_w=2e4, n_cells=64),
             dict(L_m=0.30, N_gas_m3=0.5 * N_GAS, mu_iN=1.1e22, Gamma_T=3e20, nu_w=5e4, n_cells=512),
             dict(L_m=0.30, N_gas_m3=2 * N_GAS, mu_iN=1.1e22, Gamma_T=2e20, nu_w=1e4, n_cells=4096),
-            dict(L_m=0.10, N_gas_m3=N_GAS, mu_iN=1.3e22, Gamma_T=2e20, nu_w=0.0, n_cells=1024, loss=pb.FLUID_LOSS_PAIR)]
+            dict(L_m=0.10, N_gas_m3=N_GAS, mu_iN=1.3e22, Gamma_T=2e20, nu_w=0.0, n_cells=1024, loss=pb.FLUID_LOSS_PAIR),
+            dict(L_m=0.20, N_gas_m3=N_GAS, mu_iN=1.2e22, Gamma_T=2.5e20, nu_w=3e4, n_cells=2048)]
 
 
 def initial(N, seed):
