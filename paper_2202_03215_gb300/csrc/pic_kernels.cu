@@ -115,7 +115,29 @@ template <class R> __device__ __forceinline__ Queue<R> queue_at(unsigned char *q
   Q.cell = Q.slot + kQcap;
   return Q;
 }
-template <class R> constexpr size_t queue_bytes() { return (size_t)kQcap * (8 + 5 * sizeof(R) + 8); }
+template <class R> __host__ __device__ constexpr size_t queue_bytes() { return (size_t)kQcap * (8 + 5 * sizeof(R) + 8); }
+
+// MIXED form: every thread stages its particles of the next kStages tiles (cell, float4 record,
+// id) in shared memory with asynchronous copies, so that two tiles per thread are in flight
+// without holding registers; each thread reads back only what it copied itself
+constexpr int kStages = 2;
+template <class R> __host__ __device__ constexpr size_t stage_bytes() {
+  return std::is_same<R, float>::value ? (size_t)kStages * kStepThreads * (4 + 16 + 8) : 0;
+}
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int G> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory");
+}
 
 // round(256 vx) to nearest even, as an integer (exact, order independent sums)
 __device__ __forceinline__ long long vfix(float v) { return __float2ll_rn(v * 256.0f); }
@@ -312,6 +334,11 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
   bins.khi = bins.klo + W;
   bins.W = W;
   const Queue<R> Qd = queue_at<R>(smem + eb + bins_bytes(W));
+  constexpr bool kStg = std::is_same<R, float>::value;
+  unsigned char *stg = smem + eb + bins_bytes(W) + queue_bytes<R>();
+  int32_t *g_cell = reinterpret_cast<int32_t *>(stg);                                  // [kStages][threads]
+  float4 *g_rec = reinterpret_cast<float4 *>(stg + (size_t)kStages * kStepThreads * 4);
+  uint64_t *g_id = reinterpret_cast<uint64_t *>(stg + (size_t)kStages * kStepThreads * 20);
   const long long n = ctl->n[SP];
   const long long stepll = ctl->step;
   const uint32_t step = (uint32_t)stepll;
@@ -366,11 +393,26 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     __syncwarp();
   };
 
-  // software pipeline: the next tile's particle is loaded while this one is processed
+  // software pipeline.  MIXED form: the particles of the next two tiles are in flight as
+  // asynchronous copies into shared memory (one commit group per tile and thread); FP64 form:
+  // the next tile's particle is loaded into registers while this one is processed
+  auto stage_in = [&](int base, int sidx) {
+    const int p = base + threadIdx.x;
+    if (p < (int)p1) {
+      const int q = sidx * kStepThreads + threadIdx.x;
+      cp_async4(g_cell + q, s.cell + p);
+      cp_async16(g_rec + q, reinterpret_cast<const float4 *>(s.rec) + p);
+      cp_async8(g_id + q, s.id + p);
+    }
+    cp_async_commit();
+  };
   int32_t n_cell = 0;
   R n_off = 0, n_vx = 0, n_vy = 0, n_vz = 0;
   uint64_t n_id = 0;
-  {
+  if constexpr (kStg) {
+    stage_in((int)p0, 0);
+    stage_in((int)p0 + blockDim.x, 1);
+  } else {
     const int p = (int)p0 + threadIdx.x;
     if (p < (int)p1) {
       n_cell = s.cell[p];
@@ -378,6 +420,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
       n_id = s.id[p];
     }
   }
+  int sidx = 0;   // stage of this tile (MIXED form)
   for (int base = (int)p0; base < (int)p1; base += blockDim.x) {
     const int p = base + threadIdx.x;
     const bool valid = p < (int)p1;
@@ -385,7 +428,16 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     int32_t cell = n_cell;
     R off = n_off, vx = n_vx, vy = n_vy, vz = n_vz, u1 = 0;
     uint64_t id = n_id;
-    {
+    if constexpr (kStg) {
+      cp_async_wait<kStages - 1>();   // this tile's group has landed
+      if (valid) {
+        const int q = sidx * kStepThreads + threadIdx.x;
+        cell = g_cell[q];
+        const float4 r = g_rec[q];
+        off = r.x; vx = r.y; vy = r.z; vz = r.w;
+        id = g_id[q];
+      }
+    } else {
       const int pn = p + blockDim.x;
       if (pn < (int)p1) {
         n_cell = s.cell[pn];
@@ -425,6 +477,10 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
         else atomicOr(&ctl->status, kStDeadOverflow);
       }
     }
+    if constexpr (kStg) {   // the slot is consumed (its values were used above): refill it
+      stage_in(base + kStages * blockDim.x, sidx);
+      sidx ^= 1;
+    }
     // queue the candidates in this warp's slice
     const unsigned bal = __ballot_sync(kFull, cand);
     if (cand) {
@@ -450,6 +506,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     }
   }
   if (wq > 0) flush(wq);
+  if constexpr (kStg) cp_async_wait<0>();
   if (circuit) {
     unsigned long long u = (unsigned long long)vsum;
 #pragma unroll
@@ -504,11 +561,11 @@ template <class R> int push_smem_bytes(int N) {
 }
 
 template <class R> size_t push_layout(int n_cells, int &W, int &smemE) {
-  const size_t budget = 220 * 1024;
-  const size_t qb = queue_bytes<R>();
+  const size_t budget = 226 * 1024;   // of 227 KB: room for the batched kernel's static StepK
+  const size_t qb = queue_bytes<R>() + stage_bytes<R>();
   size_t eb = (((size_t)n_cells + 1) * sizeof(R) + 15) & ~(size_t)15;
-  // the node field goes to shared memory when it leaves room for a 4096-cell bin window
-  smemE = eb + qb + bins_bytes(4096) <= budget ? 1 : 0;
+  // the node field goes to shared memory when it leaves room for a 2048-cell bin window
+  smemE = eb + qb + bins_bytes(2048) <= budget ? 1 : 0;
   if (!smemE) eb = 0;
   const size_t wmax = (budget - eb - qb) / 12;
   W = (int)((size_t)n_cells < wmax ? (size_t)n_cells : wmax);
