@@ -35,9 +35,16 @@ sys.path.insert(0, str(ROOT))
 METRIC = "particle-steps/s and % HBM roofline on 1 GB300 vs CPU oracle; batched vs serial"
 UNIT = "particle-steps/s"
 BYTES_PER_PUSH = 48  # float4 state read + write (32 B) + id read (8 B) + int32 cell read + write (8 B)
-WORKLOAD = ("neon periodic column, 1 Torr 300 K, L=0.30 m, R=0.01 m, 16384 cells, 2e7 electrons + 2e7 ions, "
-            "dt=4e-11 s, ions subcycled x10, E0=600 V/m, PAIR losses, int32 cell + FP32 offset/velocity, "
-            "FP64 Poisson")
+WORKLOAD = ("neon periodic column, 1 Torr 300 K, L=0.30 m, R=0.01 m, I=1 mA (field and density from eq. 2), "
+            "16384 cells, 2e7 electrons + 2e7 ions, dt=4e-11 s, ions subcycled x10, PAIR losses, int32 cell + "
+            "FP32 offset/velocity, FP64 Poisson")
+
+
+def column_params(w, n_per_species: int, seed: int = 1, column: int = 0):
+    """The neon column of the throughput workload: R = 1 cm carrying I = 1 mA; pic_init
+    resolves the homogeneous field E0 and density n0 of eq. 2."""
+    return w.config_neon_column(n_per_species=n_per_species, seed=seed, column=column, drive=w.DRIVE_RI,
+                                I_A=1e-3)
 
 
 def peaks():
@@ -111,8 +118,8 @@ def oracle_rate(n_per_species: int, steps: int, warmup: int = 1):
     """The CPU oracle as it stands (FP32-storage build, one thread) on a sample of the workload."""
     import oracle
     from paper_2202_03215_gb300 import workloads as w
-    p = w.config_neon_column(n_per_species=n_per_species)
-    o = oracle.Oracle(p)
+    p = column_params(w, n_per_species)
+    o = oracle.Oracle(p)                       # resolves eq. 2 with the oracle's own two-term solve
     o.step(warmup)
     s0 = o.stats()["step"]
     t = time.perf_counter()
@@ -245,7 +252,7 @@ def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: 
 def replica_params(w, rank: int, n_per_species: int):
     """The column of rank `rank` in a multi-GPU run: an independent replica of the neon column
     (its own seed and RNG column index), no data shared between ranks."""
-    return w.config_neon_column(n_per_species=n_per_species, seed=1 + rank, column=rank)
+    return column_params(w, n_per_species, seed=1 + rank, column=rank)
 
 
 def aggregate(dist, torch, seconds: float, units: int, device: str = "cuda"):
@@ -425,6 +432,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "particles_per_species": args.n, "n_cells": p.n_cells,
+                           "eq2": {k: float(v) for k, v in pb.drive_ri(p).items()},
                            "l2": "inputs larger than L2 (state 1.1 GB)", "parallelism": f"replicas x{world}",
                            "pushed_particle_steps": units},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_vs_serial": batch,

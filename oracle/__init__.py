@@ -195,6 +195,14 @@ class Oracle:
         from_params_f32 = params.precision == 1
         self.f32 = from_params_f32 if f32 is None else f32
         self.L = lib(self.f32)
+        if params.drive == 3:
+            # (R, I) drive: the homogeneous field and density of eq. 2 from this package's own
+            # two-term solve, then the column runs at that field
+            from . import two_term
+            xs = [(x.kind, x.threshold_eV, x.energy_eV, x.sigma_m2) for x in params.xsec]
+            E0, n0, _ = two_term.ri_drive(xs, params.gas_mass_amu, params.pressure_torr, params.T_gas_K,
+                                          params.R_m, params.I_A, params.eps_max_e_eV)
+            params = params.with_(drive=0, E0_Vpm=float(E0), n0_m3=float(n0))
         self.params = params
         st, self._keep = make_params(params)
         h = C.c_void_p()

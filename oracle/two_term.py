@@ -151,3 +151,64 @@ def solve(xsecs, mass_amu, EN_Td, eps_max=100.0, n=2000):
                 nuN=nuN, nu_izN=nu_iz, drift=w, alphaN=nu_iz / w if w > 0 else 0.0,
                 loss_elN=loss_el, loss_N=loss_el + loss_inel,
                 power_N=muN * EN * EN, swarm_loss_N=loss_el + loss_inel + loss_swarm_iz)
+
+
+KB = 1.380649e-23
+TORR = 133.32236842105263
+ION_CX, ION_ISO = 3, 4
+J0_ZERO = 2.405            # first zero of J_0: the "2.4" of eq. 2
+
+
+def ion_mobility_N(ion_xsecs, mass_amu, T_K):
+    """mu_i N of ions in their parent gas at low field, the ion mobility of eq. 2 (the
+    paper takes measured values; the synthetic gases here have a cross section only).
+    First Chapman-Enskog approximation for a constant momentum-transfer cross section Q:
+    mu_i = 3 e / (16 N Q) (2 pi / (m_r k T))^(1/2), m_r = M/2 for an ion in its own gas.
+    Q is read at the mean relative energy of a thermal pair, 8 k T / pi: a charge
+    exchange reverses the ion's velocity in the centre-of-mass frame (2 sigma_cx), an
+    isotropic collision transfers sigma_iso on average."""
+    eps = 8.0 * KB * T_K / (np.pi * QE)
+    Q = 0.0
+    for kind, thr, e, s in ion_xsecs:
+        if kind == ION_CX:
+            Q += 2.0 * float(np.interp(eps, np.asarray(e, float), np.asarray(s, float)))
+        elif kind == ION_ISO:
+            Q += float(np.interp(eps, np.asarray(e, float), np.asarray(s, float)))
+    return 3.0 * QE / (16.0 * Q) * np.sqrt(2.0 * np.pi / (0.5 * mass_amu * AMU * KB * T_K))
+
+
+def ri_drive(xsecs, mass_amu, p_torr, T_K, R_m, I_A, eps_max, n=800, iters=40):
+    """Field and density of a column of radius R carrying the current I (Sec. II, eq. 2).
+
+    Ionization balances ambipolar loss to the wall, nu_i = (2.405/R)^2 D_a with
+    D_a = D_e mu_i / mu_e, all at the homogeneous field E0; the electron terms come from
+    this module's two-term solve at E0/N, mu_i from ion_mobility_N.  The balance
+    N nu_izN - mu_i (D N / mu N) (2.405/R)^2 rises with E/N through zero; bisection on
+    log(E/N) over [5, 300] Td (the central differences need some field at the grid's
+    resolution; columns of the paper's range sit well inside).  The density follows from J = I / (pi R^2) =
+    e n0 (mu_e + mu_i) E0.  Returns (E0 in V/m, n0 in m^-3, mu_i N)."""
+    N = p_torr * TORR / (KB * T_K)
+    el = [x for x in xsecs if x[0] in (ELASTIC, EXCITATION, IONIZATION)]
+    ions = [x for x in xsecs if x[0] in (ION_CX, ION_ISO)]
+    mu_i = ion_mobility_N(ions, mass_amu, T_K) / N
+    g2 = (J0_ZERO / R_m) ** 2
+
+    def balance(EN):
+        s = solve(el, mass_amu, EN, eps_max=eps_max, n=n)
+        return N * s["nu_izN"] - mu_i * (s["DN"] / s["muN"]) * g2, s
+
+    lo, hi = np.log(5.0), np.log(300.0)
+    if not (balance(np.exp(lo))[0] < 0.0 < balance(np.exp(hi))[0]):
+        raise ValueError("no root of eq. 2 in [5, 300] Td")
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if balance(np.exp(mid))[0] < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    EN = np.exp(0.5 * (lo + hi))
+    _, s = balance(EN)
+    E0 = EN * TD * N
+    J = I_A / (np.pi * R_m ** 2)
+    n0 = J / (QE * (s["muN"] / N + mu_i) * E0)
+    return E0, n0, mu_i * N
