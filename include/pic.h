@@ -192,7 +192,12 @@ int pic_step(pic_handle *h, int64_t n);
 int pic_moments(pic_handle *h, pic_moments_out *out);
 
 int pic_get_state(pic_handle *h, pic_state *out);
-/* Replace the state; the next step uses state->step as its counter. */
+/* Replace the state; the next step uses state->step as its counter.  The arrays are
+ * uploaded as given (pinned host memory copies at full link speed) and checked on the
+ * device: a particle outside the grid (cell not in [0, n_cells), offset not in [0, 1),
+ * or, for PIC_MIXED, an offset that rounds to 1 in FP32) returns PIC_EINVAL naming the
+ * lowest such particle and leaves the particles undefined until the next successful
+ * call.  The first call allocates 32 bytes of device memory per particle of capacity. */
 int pic_set_state(pic_handle *h, const pic_state *in);
 int pic_get_stats(pic_handle *h, pic_stats *out);
 

@@ -54,6 +54,8 @@ struct pic_handle {
   uint32_t *k3_mem = nullptr;
   double *mom = nullptr;              // 8 * N doubles
   unsigned long long *mom_iz = nullptr;
+  double *stage = nullptr;            // pic_set_state: offsets and velocities uploaded as given (4 x cap doubles)
+  unsigned long long *stage_bad = nullptr;   // first particle outside the grid (or ~0)
   // kernel parameter blocks
   pic::StepK<double> kd{};
   pic::StepK<float> kf{};
@@ -89,6 +91,26 @@ struct pic_handle {
 };
 
 namespace {
+
+// pic_set_state: the uploaded offsets and velocities (FP64, as given) into the particle records,
+// rounded once to the storage precision; *bad = the lowest index outside the grid
+// (cell not in [0, N), offset not in [0, 1), or an offset that rounds to 1 in FP32 storage)
+template <class R>
+__global__ void k_set_rec(const int32_t *__restrict__ cell, const double *__restrict__ st, long long n, int N,
+                          void *rec, unsigned long long *bad) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+    const double o = st[p], vx = st[n + p], vy = st[2 * n + p], vz = st[3 * n + p];
+    const int32_t c = cell[p];
+    bool ok = c >= 0 && c < N && o >= 0.0 && o < 1.0;
+    if constexpr (std::is_same<R, float>::value) {
+      ok = ok && (float)o < 1.0f;
+      reinterpret_cast<float4 *>(rec)[p] = make_float4((float)o, (float)vx, (float)vy, (float)vz);
+    } else {
+      reinterpret_cast<pic::D4 *>(rec)[p] = pic::D4{o, vx, vy, vz};
+    }
+    if (!ok) atomicMin(bad, (unsigned long long)p);
+  }
+}
 
 int set_err(pic_handle *h, int code, const char *fmt, ...) {
   char buf[512];
@@ -423,6 +445,7 @@ void free_all(pic_handle *h) {
   cudaFree(h->tabb);
   cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->Dg); cudaFree(h->fs); cudaFree(h->Ef); cudaFree(h->gauss);
   cudaFree(h->bb_mem); cudaFree(h->k3_mem); cudaFree(h->mom); cudaFree(h->mom_iz);
+  cudaFree(h->stage); cudaFree(h->stage_bad);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
 }
@@ -997,29 +1020,46 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
                *vzs[2] = {in->vz_e, in->vz_i};
   const uint64_t *ids[2] = {in->id_e, in->id_i};
   const int64_t ns[2] = {in->n_e, in->n_i};
+  // the arrays go to the device as given (cells and ids to their places, offsets and velocities
+  // to a staging area), then one kernel per species checks the grid and writes the records
+  for (int q = 0; q < 2; ++q)
+    if (ns[q] > 0 && (!cells[q] || !offs[q] || !vxs[q] || !vys[q] || !vzs[q] || !ids[q]))
+      return set_err(h, PIC_EINVAL, "missing state array");
+  if (!h->stage && (ns[0] > 0 || ns[1] > 0)) {
+    const int64_t cap = std::max(h->sp[0].cap, h->sp[1].cap);
+    if (cudaMalloc(&h->stage, (size_t)cap * 4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->stage_bad, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaFree(h->stage);
+      h->stage = nullptr;
+      return set_err(h, PIC_ENOMEM, "no device memory for the state upload");
+    }
+  }
+  unsigned long long bad[2] = {~0ull, ~0ull};
   for (int q = 0; q < 2; ++q) {
     const int64_t n = ns[q];
     if (n == 0) continue;
-    if (!cells[q] || !offs[q] || !vxs[q] || !vys[q] || !vzs[q] || !ids[q])
-      return set_err(h, PIC_EINVAL, "missing state array");
-    for (int64_t p = 0; p < n; ++p) {
-      const double o = offs[q][p];
-      if (cells[q][p] < 0 || cells[q][p] >= h->N || !(o >= 0.0 && o < 1.0) || (h->mixed && !((float)o < 1.0f)))
-        return set_err(h, PIC_EINVAL, "particle %lld of species %d outside the grid", (long long)p, q);
-    }
-    CU(h, cudaMemcpy(h->sp[q].cell, cells[q], (size_t)n * 4, cudaMemcpyHostToDevice));
-    CU(h, cudaMemcpy(h->sp[q].id, ids[q], (size_t)n * 8, cudaMemcpyHostToDevice));
-    if (h->mixed) {
-      std::vector<float4> r((size_t)n);
-      for (int64_t p = 0; p < n; ++p)
-        r[p] = make_float4((float)offs[q][p], (float)vxs[q][p], (float)vys[q][p], (float)vzs[q][p]);
-      CU(h, cudaMemcpy(h->sp[q].rec, r.data(), (size_t)n * 16, cudaMemcpyHostToDevice));
-    } else {
-      std::vector<pic::D4> r((size_t)n);
-      for (int64_t p = 0; p < n; ++p) r[p] = pic::D4{offs[q][p], vxs[q][p], vys[q][p], vzs[q][p]};
-      CU(h, cudaMemcpy(h->sp[q].rec, r.data(), (size_t)n * 32, cudaMemcpyHostToDevice));
-    }
+    const size_t b8 = (size_t)n * 8;
+    CU(h, cudaMemcpyAsync(h->sp[q].cell, cells[q], (size_t)n * 4, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->sp[q].id, ids[q], b8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->stage, offs[q], b8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->stage + n, vxs[q], b8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->stage + 2 * n, vys[q], b8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->stage + 3 * n, vzs[q], b8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->stage_bad + q, &bad[q], 8, cudaMemcpyHostToDevice, h->stream));
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)h->nsm * 8);
+    if (h->mixed)
+      k_set_rec<float><<<blocks, 256, 0, h->stream>>>(h->sp[q].cell, h->stage, n, h->N, h->sp[q].rec,
+                                                       h->stage_bad + q);
+    else
+      k_set_rec<double><<<blocks, 256, 0, h->stream>>>(h->sp[q].cell, h->stage, n, h->N, h->sp[q].rec,
+                                                        h->stage_bad + q);
+    CU(h, cudaGetLastError());
+    CU(h, cudaMemcpyAsync(&bad[q], h->stage_bad + q, 8, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));   // the staging area is reused by the next species
   }
+  for (int q = 0; q < 2; ++q)
+    if (bad[q] != ~0ull)
+      return set_err(h, PIC_EINVAL, "particle %lld of species %d outside the grid", (long long)bad[q], q);
   pic::Ctl c;
   CU(h, cudaMemcpy(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost));
   c.n[0] = in->n_e; c.n[1] = in->n_i; c.step = in->step; c.next_id = in->next_id; c.E0 = in->E0;

@@ -164,10 +164,35 @@ def test_int128_conversion_on_device():
     assert np.array_equal(got, want)
 
 
+def test_set_state_rejects_particles_outside_the_grid():
+    p = w.config_argon_small(n_e0=5000, n_i0=5000, precision=w.MIXED)
+    g = pb.Column(p)
+    good = g.get_state()
+    for key, k, val in (("off_e", 123, 1.0), ("off_i", 7, -1e-300), ("cell_e", 4000, p.n_cells),
+                        ("off_e", 9, np.nextafter(1.0, 0.0))):   # the last one rounds to 1 in FP32
+        bad = {kk: (v.copy() if isinstance(v, np.ndarray) else v) for kk, v in good.items()}
+        bad[key][k] = val
+        with pytest.raises(pb.PicError, match=f"particle {k} of species {0 if key.endswith('_e') else 1}"):
+            g.set_state(bad)
+    g.set_state(good)
+    o = oracle.Oracle(p)
+    o.set_state(good)
+    g.step(2)
+    o.step(2)
+    assert_same(g.get_state(), o.get_state(), "after a rejected state")
+    g.close()
+
+
 def test_full_size_neon_column_first_step():
-    """The 2e7-per-species neon column in the benchmark's launch configuration:
-    initial state and first step (an ion step) bit-exact against the oracle."""
-    p = w.config_neon_column()
+    """The benchmark's neon column (2e7 per species, R = 1 cm carrying I = 1 mA) in its
+    launch configuration: the field and density of eq. 2 come from the oracle's own
+    two-term solve and are given to both sides; initial state and first step (an ion
+    step) bit-exact against the oracle."""
+    from oracle import two_term as tt
+    p = w.config_neon_column(drive=w.DRIVE_RI, I_A=1e-3)
+    xs = [(x.kind, x.threshold_eV, x.energy_eV, x.sigma_m2) for x in p.xsec]
+    E0, n0, _ = tt.ri_drive(xs, p.gas_mass_amu, p.pressure_torr, p.T_gas_K, p.R_m, p.I_A, p.eps_max_e_eV)
+    p = p.with_(drive=w.DRIVE_E0, E0_Vpm=float(E0), n0_m3=float(n0))
     g = pb.Column(p)
     o = oracle.Oracle(p)
     assert_same(g.get_state(), o.get_state(), "init")
