@@ -184,12 +184,30 @@ int pic_init(const pic_params *params, pic_handle **out);
 
 /* Advance n >= 0 steps.  Each step: electron gather/push/collisions/deposit,
  * ion step on every ion_subcycle-th step, births and removals, periodic sort
- * every sort_every steps, field solve.  Stream-ordered; synchronises once at
- * the end to read the device status word. */
+ * every sort_every steps, field solve.  A plain ion cycle (ion_subcycle steps
+ * with no sort and no diagnostic sample) is replayed from a CUDA graph captured
+ * on first use (PIC_FLAG_NO_GRAPH or kernel timing: launched one by one); the
+ * results are the same.  Stream-ordered; synchronises once at the end to read
+ * the device status word. */
 int pic_step(pic_handle *h, int64_t n);
 
 /* Copy the moment window (host arrays of n_cells, NULL to skip). */
 int pic_moments(pic_handle *h, pic_moments_out *out);
+
+/* Electron energy probability function F(x, eps) (Sec. III.C, Fig. 8), sampled as a
+ * histogram.  With n_x > 0, on every diagnostic step (diag_every) each live electron
+ * adds 1 to bin (floor(cell n_x / n_cells), floor(eps n_eps / eps_max)) after its push
+ * and collision; column n_eps collects the energies at or above eps_max (and non-finite
+ * ones), so each sample adds exactly n_e counts.  eps = K (vx^2 + vy^2 + vz^2) and its
+ * bin are computed in the storage precision, as in the collision test.  The host
+ * normalises: F = counts / (sum eps^(1/2) counts deps) per spatial bin, so that
+ * int eps^(1/2) F deps = 1.  pic_eepf_config allocates and clears the histogram
+ * (n_x = 0 frees it); 1 <= n_x <= n_cells, 1 <= n_eps <= 65536, eps_max > 0.  Single
+ * columns only: PIC_EINVAL on a batch or a column of one. */
+int pic_eepf_config(pic_handle *h, int32_t n_x, int32_t n_eps, double eps_max_eV);
+/* Copy the n_x (n_eps + 1) counts (x-major, host array) and the number of diagnostic
+ * samples they hold; reset = 1 clears both afterwards. */
+int pic_eepf_get(pic_handle *h, uint64_t *counts, int64_t *n_samples, int32_t reset);
 
 int pic_get_state(pic_handle *h, pic_state *out);
 /* Replace the state; the next step uses state->step as its counter.  The arrays are

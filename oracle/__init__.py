@@ -104,6 +104,8 @@ def lib(f32: bool = False) -> C.CDLL:
         L.ora_set_state.argtypes = [C.c_void_p, C.POINTER(OraState)]
         L.ora_stats_get.argtypes = [C.c_void_p, C.POINTER(OraStats)]
         L.ora_moments_get.argtypes = [C.c_void_p, C.POINTER(OraMoments)]
+        L.ora_eepf_config.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double]
+        L.ora_eepf_get.argtypes = [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int64), C.c_int]
         L.ora_last_codes.argtypes = [C.c_void_p, C.c_int, _I32, C.c_int64]
         L.ora_derived.argtypes = [C.c_void_p, _D]
         L.ora_nu_table.argtypes = [C.c_void_p, C.c_int, C.c_int, _D, C.c_int]
@@ -301,6 +303,18 @@ class Oracle:
         self.L.ora_moments_get(self.h, C.byref(m))
         d["n_samples"], d["n_steps"] = m.n_samples, m.n_steps
         return d
+
+    def eepf_config(self, n_x: int, n_eps: int, eps_max_eV: float) -> None:
+        if self.L.ora_eepf_config(self.h, n_x, n_eps, eps_max_eV):
+            raise ValueError("bad EEPF histogram shape")
+        self._eepf_shape = (n_x, n_eps + 1)
+
+    def eepf(self, reset: bool = False):
+        c = np.zeros(self._eepf_shape, np.uint64)
+        ns = C.c_int64()
+        if self.L.ora_eepf_get(self.h, c.ctypes.data_as(C.POINTER(C.c_uint64)), C.byref(ns), int(reset)):
+            raise ValueError("no EEPF histogram")
+        return c, ns.value
 
 
 _mlp = None

@@ -278,6 +278,8 @@ struct ora_t {
   double *m_ne, *m_ni, *m_ge, *m_ee, *m_he, *m_gi, *m_E, *m_phi;
   int64_t *m_iz;
   int64_t m_samples, m_steps;
+  /* electron energy histogram: eepf_nx x (eepf_ne + 1) counts */
+  uint64_t *eepf; int eepf_nx, eepf_ne; real eepf_scale; int64_t eepf_samples;
   int err;
 };
 
@@ -520,7 +522,14 @@ static void electron_step(ora_t *h, int64_t p, int diag) {
   deposit(s->Q, h->N, cell, off, +1);
   if (h->p.drive == ORA_DRIVE_CIRCUIT) h->sumv[0] += (int64_t)llrint((double)(vx * (real)256));
   if (diag) {
-    double eps = (double)(h->K_e * (vx * vx + vy * vy + vz * vz));
+    real er = h->K_e * (vx * vx + vy * vy + vz * vz);
+    double eps = (double)er;
+    if (h->eepf) {   /* Sec. III.C: the electron's energy bin at its cell, after push and collision */
+      real x = er * h->eepf_scale;
+      int b = x < (real)h->eepf_ne ? (int)x : h->eepf_ne;
+      int bx = (int)(((int64_t)cell * h->eepf_nx) / h->N);
+      h->eepf[(size_t)bx * (size_t)(h->eepf_ne + 1) + (size_t)b] += 1;
+    }
     moment_add(h->m_ge, h->N, cell, off, (double)vx);
     moment_add(h->m_ee, h->N, cell, off, eps);
     moment_add(h->m_he, h->N, cell, off, eps * (double)vx);
@@ -798,6 +807,7 @@ static int step_once(ora_t *h) {
     }
     h->m_samples++;
     h->st.n_diag++;
+    if (h->eepf) h->eepf_samples++;
   }
   return h->err;
 }
@@ -975,7 +985,28 @@ void ora_destroy(ora_t *h) {
   species_free(&h->e); species_free(&h->i);
   free(h->E); free(h->Eh); free(h->Ef); free(h->births); free(h->dead_e); free(h->dead_i);
   moments_free(h);
+  free(h->eepf);
   free(h);
+}
+
+int ora_eepf_config(ora_t *h, int n_x, int n_eps, double eps_max_eV) {
+  if (n_x < 0 || n_x > h->N || (n_x > 0 && (n_eps < 1 || n_eps > 65536 || !(eps_max_eV > 0.0)))) return ORA_EINVAL;
+  free(h->eepf);
+  h->eepf = NULL; h->eepf_nx = 0; h->eepf_ne = 0; h->eepf_samples = 0;
+  if (n_x == 0) return 0;
+  h->eepf = (uint64_t *)xcalloc((size_t)n_x * (size_t)(n_eps + 1), 8);
+  h->eepf_nx = n_x; h->eepf_ne = n_eps;
+  h->eepf_scale = (real)((double)n_eps / eps_max_eV);
+  return 0;
+}
+
+int ora_eepf_get(ora_t *h, uint64_t *counts, int64_t *n_samples, int reset) {
+  if (!h->eepf) return ORA_EINVAL;
+  size_t n = (size_t)h->eepf_nx * (size_t)(h->eepf_ne + 1);
+  if (counts) memcpy(counts, h->eepf, n * 8);
+  if (n_samples) *n_samples = h->eepf_samples;
+  if (reset) { memset(h->eepf, 0, n * 8); h->eepf_samples = 0; }
+  return 0;
 }
 
 int ora_get_state(ora_t *h, ora_state *s) {

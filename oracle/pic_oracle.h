@@ -87,6 +87,11 @@ int  ora_get_state(ora_t *h, ora_state *s);
 int  ora_set_state(ora_t *h, const ora_state *s);
 int  ora_stats_get(ora_t *h, ora_stats *s);
 int  ora_moments_get(ora_t *h, ora_moments *m);
+/* electron energy histogram (Sec. III.C, the EEPF F(x, eps)): on each diagnostic step every
+   live electron adds 1 to bin (cell n_x / n_cells, eps n_eps / eps_max), energies at or above
+   eps_max in column n_eps; n_x = 0 switches it off */
+int  ora_eepf_config(ora_t *h, int n_x, int n_eps, double eps_max_eV);
+int  ora_eepf_get(ora_t *h, uint64_t *counts, int64_t *n_samples, int reset);
 /* per-particle process code of the last step (-1 none, else xsec index), length n */
 int  ora_last_codes(ora_t *h, int species, int32_t *out, int64_t n);
 /* derived scalars: [n_g, nu_star_e, P_null_e, nu_star_i, P_null_i, w, dx] */

@@ -94,6 +94,8 @@ def lib() -> C.CDLL:
         L.pic_init.argtypes = [C.POINTER(Params), C.POINTER(C.c_void_p)]
         L.pic_step.argtypes = [C.c_void_p, C.c_int64]
         L.pic_moments.argtypes = [C.c_void_p, C.POINTER(MomentsOut)]
+        L.pic_eepf_config.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double]
+        L.pic_eepf_get.argtypes = [C.c_void_p, _U64, C.POINTER(C.c_int64), C.c_int32]
         L.pic_get_state.argtypes = [C.c_void_p, C.POINTER(State)]
         L.pic_set_state.argtypes = [C.c_void_p, C.POINTER(State)]
         L.pic_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
@@ -353,6 +355,31 @@ class Column:
         _check(self.L.pic_moments(self.h, C.byref(m)), self.h)
         d["n_samples"], d["n_steps"] = m.n_samples, m.n_steps
         return d
+
+    def eepf_config(self, n_x: int, n_eps: int, eps_max_eV: float) -> None:
+        """Sample the electron energy histogram on every diagnostic step (pic_eepf_config)."""
+        _check(self.L.pic_eepf_config(self.h, n_x, n_eps, eps_max_eV), self.h)
+        self._eepf_shape = (n_x, n_eps + 1)
+
+    def eepf(self, reset: bool = False):
+        """(counts[n_x, n_eps + 1], diagnostic samples) of the energy histogram."""
+        c = np.zeros(self._eepf_shape, np.uint64)
+        ns = C.c_int64()
+        _check(self.L.pic_eepf_get(self.h, _ptr(c, _U64), C.byref(ns), int(reset)), self.h)
+        return c, ns.value
+
+
+def eepf_normalized(counts, eps_max_eV: float):
+    """F(x, eps) from an energy histogram (Sec. III.C): per spatial bin, counts / (deps eps^(1/2))
+    scaled so that sum eps^(1/2) F deps = 1 over the bins below eps_max (bin centres eps).
+    Returns (eps centres, F[n_x, n_eps])."""
+    c = np.asarray(counts, float)[:, :-1]
+    n_eps = c.shape[1]
+    de = eps_max_eV / n_eps
+    eps = (np.arange(n_eps) + 0.5) * de
+    F = c / (de * np.sqrt(eps))[None, :]
+    norm = (F * np.sqrt(eps)[None, :] * de).sum(axis=1, keepdims=True)
+    return eps, F / np.where(norm > 0, norm, 1.0)
 
 
 class Batch:

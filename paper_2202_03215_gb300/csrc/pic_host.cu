@@ -54,6 +54,7 @@ struct pic_handle {
   uint32_t *k3_mem = nullptr;
   double *mom = nullptr;              // 8 * N doubles
   unsigned long long *mom_iz = nullptr;
+  long long eepf_base = 0;            // diagnostic samples (ctl n_diag) when the EEPF histogram was cleared
   double *stage = nullptr;            // pic_set_state: offsets and velocities uploaded as given (4 x cap doubles)
   unsigned long long *stage_bad = nullptr;   // first particle outside the grid (or ~0)
   // kernel parameter blocks
@@ -445,7 +446,7 @@ void free_all(pic_handle *h) {
   cudaFree(h->tabb);
   cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->Dg); cudaFree(h->fs); cudaFree(h->Ef); cudaFree(h->gauss);
   cudaFree(h->bb_mem); cudaFree(h->k3_mem); cudaFree(h->mom); cudaFree(h->mom_iz);
-  cudaFree(h->stage); cudaFree(h->stage_bad);
+  cudaFree(h->stage); cudaFree(h->stage_bad); cudaFree(h->m.eepf);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
 }
@@ -821,14 +822,55 @@ int pic_init(const pic_params *params, pic_handle **out) {
   return 0;
 }
 
+// steps s .. s+sub-1 of a column hold no sort and no diagnostic sample
+static bool plain_steps(const pic_params &p, long long s, int sub) {
+  for (long long q = s; q < s + sub; ++q) {
+    if (p.sort_every > 0 && q % p.sort_every == 0) return false;
+    if (p.diag_every > 0 && q % p.diag_every == 0) return false;
+  }
+  return true;
+}
+
 int pic_step(pic_handle *h, int64_t n) {
   if (!h || n < 0) return set_err(h, PIC_EINVAL, "bad arguments");
   if (h->is_batch) return pic_step_batch(h, n);
   if (h->owner) return set_err(h, PIC_EINVAL, "a column of a batch advances with pic_step_batch");
   if (h->latched) return h->latched;
-  for (int64_t s = 0; s < n; ++s) {
+  const int sub = h->p.ion_subcycle > 0 ? h->p.ion_subcycle : 1;
+  const bool graphs = !(h->p.flags & PIC_FLAG_NO_GRAPH) && !h->timing;
+  int64_t done = 0;
+  while (done < n) {
+    if (graphs && n - done >= sub && h->host_step % sub == 0 && plain_steps(h->p, h->host_step, sub)) {
+      if (!h->cycle) {
+        // capture one ion cycle; the kernels read the step counter on the device, so it replays
+        const long long s0 = h->host_step;
+        int64_t before[PIC_K_CLASSES];
+        for (int q = 0; q < PIC_K_CLASSES; ++q) before[q] = h->klaunch[q];
+        cudaGraph_t g;
+        CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = 0;
+        for (int q = 0; q < sub && !rc; ++q) rc = h->mixed ? enqueue_step<float>(h) : enqueue_step<double>(h);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        h->host_step = s0;
+        if (rc) return rc;
+        if (e != cudaSuccess) return set_err(h, PIC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->cycle, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_err(h, PIC_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
+        for (int q = 0; q < PIC_K_CLASSES; ++q) {   // the capture only recorded the launches
+          h->cycle_launch[q] = h->klaunch[q] - before[q];
+          h->klaunch[q] = before[q];
+        }
+      }
+      CU(h, cudaGraphLaunch(h->cycle, h->stream));
+      for (int q = 0; q < PIC_K_CLASSES; ++q) h->klaunch[q] += h->cycle_launch[q];
+      h->host_step += sub;
+      done += sub;
+      continue;
+    }
     const int rc = h->mixed ? enqueue_step<float>(h) : enqueue_step<double>(h);
     if (rc) return rc;
+    ++done;
     // keep the event pool bounded: fold recorded pairs every 256 steps
     if (h->timing && h->ev_cls.size() > 1024) {
       CU(h, cudaStreamSynchronize(h->stream));
@@ -1108,6 +1150,51 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
   CU(h, cudaStreamSynchronize(h->stream));
   CU(h, cudaGetLastError());
   return check_status(h);
+}
+
+int pic_eepf_config(pic_handle *h, int32_t n_x, int32_t n_eps, double eps_max_eV) {
+  if (!h) return set_err(h, PIC_EINVAL, "bad arguments");
+  if (h->is_batch || h->owner) return set_err(h, PIC_EINVAL, "the EEPF histogram is for single columns");
+  if (n_x < 0 || n_x > h->N || (n_x > 0 && (n_eps < 1 || n_eps > 65536 || !(eps_max_eV > 0.0))))
+    return set_err(h, PIC_EINVAL, "bad EEPF histogram shape");
+  CU(h, cudaStreamSynchronize(h->stream));
+  cudaFree(h->m.eepf);
+  h->m.eepf = nullptr;
+  h->m.eepf_nx = 0;
+  h->m.eepf_ne = 0;
+  if (n_x == 0) return 0;
+  const size_t bytes = (size_t)n_x * (size_t)(n_eps + 1) * 8;
+  if (cudaMalloc(&h->m.eepf, bytes) != cudaSuccess) {
+    h->m.eepf = nullptr;
+    return set_err(h, PIC_ENOMEM, "no device memory for the EEPF histogram");
+  }
+  CU(h, cudaMemset(h->m.eepf, 0, bytes));
+  h->m.eepf_nx = n_x;
+  h->m.eepf_ne = n_eps;
+  h->m.eepf_scale = (double)n_eps / eps_max_eV;
+  pic::Ctl c;
+  CU(h, cudaMemcpy(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost));
+  h->eepf_base = c.n_diag;
+  if (h->cycle) {   // the captured ion cycle holds the old kernel parameters (it takes no samples)
+    cudaGraphExecDestroy(h->cycle);
+    h->cycle = nullptr;
+  }
+  return 0;
+}
+
+int pic_eepf_get(pic_handle *h, uint64_t *counts, int64_t *n_samples, int32_t reset) {
+  if (!h || !h->m.eepf) return set_err(h, PIC_EINVAL, "no EEPF histogram (pic_eepf_config)");
+  const size_t n = (size_t)h->m.eepf_nx * (size_t)(h->m.eepf_ne + 1);
+  pic::Ctl c;
+  CU(h, cudaMemcpyAsync(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+  if (counts) CU(h, cudaMemcpyAsync(counts, h->m.eepf, n * 8, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (n_samples) *n_samples = c.n_diag - h->eepf_base;
+  if (reset) {
+    CU(h, cudaMemset(h->m.eepf, 0, n * 8));
+    h->eepf_base = c.n_diag;
+  }
+  return 0;
 }
 
 int pic_moments(pic_handle *h, pic_moments_out *o) {

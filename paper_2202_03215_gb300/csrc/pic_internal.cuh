@@ -90,6 +90,9 @@ template <class R> struct BirthBuf {
 struct Moments {
   double *ge, *ee, *he, *gi, *ne, *ni, *E, *phi;
   unsigned long long *iz;
+  unsigned long long *eepf;   // electron energy histogram, eepf_nx x (eepf_ne + 1), or null
+  int eepf_nx, eepf_ne;
+  double eepf_scale;          // eepf_ne / eps_max (rounded to the storage precision at the use)
 };
 
 struct K3Scratch {

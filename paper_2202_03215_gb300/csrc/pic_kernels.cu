@@ -152,7 +152,14 @@ __device__ __forceinline__ void add_moments(const SpecK<R> &sp, const Moments &m
   const double w1 = (double)kk * (1.0 / 4294967296.0), w0 = 1.0 - w1;
   const double vxd = (double)vx;
   if constexpr (SP == 0) {
-    const double eps = (double)(sp.K * (vx * vx + vy * vy + vz * vz));
+    const R epsr = sp.K * (vx * vx + vy * vy + vz * vz);
+    const double eps = (double)epsr;
+    if (m.eepf) {   // energy histogram (Sec. III.C): bin decided in the storage precision
+      const R x = epsr * (R)m.eepf_scale;
+      const int b = x < (R)m.eepf_ne ? (int)x : m.eepf_ne;
+      const int bx = (int)(((long long)cell * m.eepf_nx) / N);
+      atomicAdd(m.eepf + (size_t)bx * (m.eepf_ne + 1) + b, 1ull);
+    }
     atomicAdd(m.ge + cell, w0 * vxd); atomicAdd(m.ge + c1, w1 * vxd);
     atomicAdd(m.ee + cell, w0 * eps); atomicAdd(m.ee + c1, w1 * eps);
     const double h = eps * vxd;
