@@ -179,6 +179,34 @@ def bf16_peak():
 MLP_FWD_FLOP = 2 * (15 * 128 + 128 * 128 + 128 * 3)   # 37,376 per sample
 
 
+def eepf_leg(pb, w, torch, n: int = 20_000_000, steps: int = 200, diag_every: int = 10):
+    """Cost of the EEPF histogram (Sec. III.C) on the throughput column: the same diagnostic steps
+    (moments every diag_every steps) with and without the 64 x 200 energy histogram."""
+    p = column_params(w, n).with_(diag_every=diag_every)
+    col = pb.Column(p)
+    col.step(diag_every)
+    ext = torch.cuda.ExternalStream(col.stream())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    snap = col.get_state()
+    for on in (False, True):
+        col.set_state(snap)
+        if on:
+            col.eepf_config(64, 200, 50.0)
+        torch.cuda.synchronize()
+        e0.record(ext)
+        col.step(steps)
+        e1.record(ext)
+        torch.cuda.synchronize()
+        out["ms_per_step_eepf" if on else "ms_per_step"] = e0.elapsed_time(e1) / steps
+    c, ns = col.eepf()
+    col.close()
+    extra = (out["ms_per_step_eepf"] - out["ms_per_step"]) * diag_every
+    return {"particles_per_species": n, "steps": steps, "diag_every": diag_every, "bins": [64, 201],
+            "samples": ns, "counted": int(c.sum()), **out, "ms_per_sample_extra": extra,
+            "binned_per_s": (c.sum() / ns) / (extra / 1e3) if extra > 0 else None}
+
+
 def fluid_screen_leg(pb, torch, steps: int = 1000, warmup: int = 20, closure_steps: int = 200):
     """The fluid screen of a 32 x 32 grid of (pR, I/R) for neon columns (R = 1 cm, L = 0.30 m,
     4096 cells, FP32): homogeneous states from eq. 2 with seeded 1e-3 noise, pair losses, one batch.
@@ -303,6 +331,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-screen", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-eepf", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -424,6 +453,9 @@ def main():
     screen = train = None
     if rank == 0 and world == 1 and not args.no_screen:
         screen = fluid_screen_leg(pb, torch)
+    eepf = None
+    if rank == 0 and world == 1 and not args.no_eepf:
+        eepf = eepf_leg(pb, w, torch, n=args.n)
     if rank == 0 and world == 1 and not args.no_train:
         train = closure_training_leg(pb, torch)
 
@@ -436,7 +468,7 @@ def main():
                            "l2": "inputs larger than L2 (state 1.1 GB)", "parallelism": f"replicas x{world}",
                            "pushed_particle_steps": units},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_vs_serial": batch,
-                "fluid_screen": screen, "closure_training": train,
+                "fluid_screen": screen, "closure_training": train, "eepf": eepf,
                 "gpu_launches": launches, "ms_per_step_instrumented": ms_inst / args.steps,
                 "kernel_ms": {k: v[0] for k, v in kt.items()}, "clocks": clocks}
         print(json.dumps(line), flush=True)
