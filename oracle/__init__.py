@@ -58,7 +58,8 @@ class OraParams(C.Structure):
                 ("diag_every", C.c_int32), ("sort_every", C.c_int32), ("n_table", C.c_int32),
                 ("flags", C.c_int32),
                 ("eps_max_e_eV", C.c_double), ("eps_max_i_eV", C.c_double),
-                ("column", C.c_int32), ("pad1", C.c_int32)]
+                ("column", C.c_int32), ("pad1", C.c_int32),
+                ("J_emit_Am2", C.c_double), ("T_emit_eV", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -80,7 +81,8 @@ class OraStats(C.Structure):
                 ("n_coll_e", C.c_int64 * 8), ("n_coll_i", C.c_int64 * 8),
                 ("births", C.c_int64), ("losses_e", C.c_int64), ("losses_i", C.c_int64),
                 ("overflow_e", C.c_int64), ("overflow_i", C.c_int64),
-                ("E0", C.c_double), ("n_diag", C.c_int64)]
+                ("E0", C.c_double), ("n_diag", C.c_int64),
+                ("absorbed_e", C.c_int64 * 2), ("absorbed_i", C.c_int64 * 2), ("emitted", C.c_int64)]
 
 
 class OraMoments(C.Structure):
@@ -116,6 +118,7 @@ def lib(f32: bool = False) -> C.CDLL:
         L.ora_i128_to_double.argtypes = [C.c_int64, C.c_uint64]
         L.ora_i128_to_double.restype = C.c_double
         L.ora_field_exact.argtypes = [C.c_int, _I64, _I64, C.c_double, _D]
+        L.ora_field_exact_bounded.argtypes = [C.c_int, _I64, _I64, C.c_double, _D]
         L.ora_poisson_thomas.argtypes = [C.c_int, C.c_double, _D, _D]
         _libs[f32] = L
     return _libs[f32]
@@ -154,6 +157,16 @@ def field_exact(Q_i: np.ndarray, Q_e: np.ndarray, Cfield: float) -> np.ndarray:
     Q_e = np.ascontiguousarray(Q_e, dtype=np.int64)
     out = np.zeros(len(Q_i))
     lib().ora_field_exact(len(Q_i), _ptr(Q_i, _I64), _ptr(Q_e, _I64), Cfield, _ptr(out, _D))
+    return out
+
+
+def field_exact_bounded(Q_i: np.ndarray, Q_e: np.ndarray, Cfield: float) -> np.ndarray:
+    """Space-charge field at the n_cells faces between two electrodes (n_cells + 1 node charges)."""
+    Q_i = np.ascontiguousarray(Q_i, dtype=np.int64)
+    Q_e = np.ascontiguousarray(Q_e, dtype=np.int64)
+    n = len(Q_i) - 1
+    out = np.zeros(n)
+    lib().ora_field_exact_bounded(n, _ptr(Q_i, _I64), _ptr(Q_e, _I64), Cfield, _ptr(out, _D))
     return out
 
 
@@ -213,6 +226,7 @@ class Oracle:
             raise RuntimeError(f"ora_create failed: {rc}")
         self.h = h
         self.N = params.n_cells
+        self.nodes = params.n_nodes
         self.cap = params.capacity or (max(params.n_e0, params.n_i0) * 5 // 4 + 1024)
 
     def __del__(self):
@@ -232,6 +246,8 @@ class Oracle:
         d = {k: getattr(s, k) for k, _ in OraStats._fields_}
         d["n_coll_e"] = list(s.n_coll_e)
         d["n_coll_i"] = list(s.n_coll_i)
+        d["absorbed_e"] = list(s.absorbed_e)
+        d["absorbed_i"] = list(s.absorbed_i)
         return d
 
     def derived(self) -> dict:
@@ -254,7 +270,7 @@ class Oracle:
             "vy_e": np.zeros(ne), "vz_e": np.zeros(ne), "id_e": np.zeros(ne, np.uint64),
             "cell_i": np.zeros(ni, np.int32), "off_i": np.zeros(ni), "vx_i": np.zeros(ni),
             "vy_i": np.zeros(ni), "vz_i": np.zeros(ni), "id_i": np.zeros(ni, np.uint64),
-            "E": np.zeros(self.N), "Q_e": np.zeros(self.N, np.int64), "Q_i": np.zeros(self.N, np.int64),
+            "E": np.zeros(self.nodes), "Q_e": np.zeros(self.nodes, np.int64), "Q_i": np.zeros(self.nodes, np.int64),
         }
         s = OraState()
         for k, t in (("cell", _I32), ("off", _D), ("vx", _D), ("vy", _D), ("vz", _D), ("id", _U64)):
@@ -295,7 +311,7 @@ class Oracle:
 
     def moments(self, reset: bool = False) -> dict:
         names = ("n_e", "n_i", "gamma_e", "mean_eps_e", "heat_e", "iz_rate", "gamma_i", "E", "phi")
-        d = {k: np.zeros(self.N) for k in names}
+        d = {k: np.zeros(self.nodes) for k in names}
         m = OraMoments()
         for k in names:
             setattr(m, k, _ptr(d[k], _D))

@@ -74,7 +74,7 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 }
 
 /* Counter layout: (id_lo, id_hi, step, stream<<28 | column<<16 | block). */
-enum { ST_E = 0, ST_I = 1, ST_INIT_E = 2, ST_INIT_I = 3, ST_VIC_E = 4, ST_VIC_I = 5 };
+enum { ST_E = 0, ST_I = 1, ST_INIT_E = 2, ST_INIT_I = 3, ST_VIC_E = 4, ST_VIC_I = 5, ST_EMIT = 6 };
 
 static void rng_block(uint64_t seed, uint64_t id, uint32_t step, uint32_t stream, uint32_t column,
                       uint32_t block, uint32_t w[4]) {
@@ -208,6 +208,30 @@ void ora_field_exact(int N, const int64_t *Qi, const int64_t *Qe, double C, doub
   free(Sp);
 }
 
+/* Bounded column (Sec. V): Gauss's law between the electrodes,
+ * E_{j+1/2} - E_{j-1/2} = dx rho_j / eps0 for the interior nodes j = 1..N-1 (the
+ * electrode nodes 0 and N hold surface charge), with the potential equal at both
+ * electrodes (the applied voltage is added by the caller as -V/L).  With
+ * P_j = sum_{k=1..j} D_k (P_0 = 0) and U = sum_{j<N} P_j:
+ *   E_{j+1/2} = C (N P_j - U) / N  (zero mean over the N faces),
+ * written as the periodic route's C (N S'_j - M) / N^2 with S'_j = N P_j, M = N U:
+ * no uniform background, D_0 = 0. */
+void ora_field_exact_bounded(int N, const int64_t *Qi, const int64_t *Qe, double C, double *Eh) {
+  __int128 *Sp = (__int128 *)malloc(sizeof(__int128) * (size_t)N);
+  __int128 run = 0, M = 0;
+  for (int j = 0; j < N; ++j) {
+    if (j > 0) run += (__int128)(Qi[j] - Qe[j]);
+    Sp[j] = (__int128)N * run;
+    M += Sp[j];
+  }
+  double Cf = C / ((double)N * (double)N);
+  for (int j = 0; j < N; ++j) {
+    __int128 num = (__int128)N * Sp[j] - M;
+    Eh[j] = (double)num * Cf;
+  }
+  free(Sp);
+}
+
 /* The paper's route (Sec. II, Thomas algorithm): -phi_{j-1} + 2 phi_j - phi_{j+1}
  * = dx^2 rho_j / eps0 for j = 1..N-1 with the gauge phi_0 = 0 (periodic wrap
  * phi_N = phi_0); the j = 0 row is implied by neutrality (sum rho = 0). */
@@ -280,6 +304,10 @@ struct ora_t {
   int64_t m_samples, m_steps;
   /* electron energy histogram: eepf_nx x (eepf_ne + 1) counts */
   uint64_t *eepf; int eepf_nx, eepf_ne; real eepf_scale; int64_t eepf_samples;
+  /* bounded column (Sec. V) */
+  int bounded, Nw;          /* Nw: nodes of the charge arrays = N (periodic, node N is node 0) or N + 1 */
+  double emit_per_step, emit_acc;
+  real sig_emit, emit_dtdx;
   int err;
 };
 
@@ -311,10 +339,11 @@ static double build_table(const ora_xsec *x, double ng, double eps_max, int n, d
   return de;
 }
 
-static void deposit(int64_t *Q, int N, int32_t cell, real off, int sign) {
+/* cloud-in-cell charge of one particle; Nw = nodes (a periodic column wraps node N to 0) */
+static void deposit(int64_t *Q, int Nw, int32_t cell, real off, int sign) {
   uint64_t k = (uint64_t)(off * (real)TWO32);
   int64_t a = (int64_t)(((uint64_t)1 << 32) - k), b = (int64_t)k;
-  int c1 = (cell + 1 == N) ? 0 : cell + 1;
+  int c1 = (cell + 1 == Nw) ? 0 : cell + 1;
   Q[cell] += sign * a;
   Q[c1] += sign * b;
 }
@@ -346,7 +375,16 @@ static void copy_particle(species *s, int64_t dst, int64_t src) {
 static void solve_field(ora_t *h) {
   int N = h->N;
   if (h->p.field_mode == ORA_FIELD_APPLIED) {
-    for (int j = 0; j < N; ++j) { h->Eh[j] = 0.0; h->E[j] = -h->E0; }
+    for (int j = 0; j < h->Nw; ++j) { h->Eh[j < N ? j : N - 1] = 0.0; h->E[j] = -h->E0; }
+  } else if (h->bounded) {
+    /* Sec. V: E_0 = E_{1/2}, E_N = E_{N-1/2} at the electrodes; the applied -E0 = -V_D / L */
+    ora_field_exact_bounded(N, h->i.Q, h->e.Q, h->C_field, h->Eh);
+    double Eapp = -h->E0;
+    h->E[0] = h->Eh[0] + Eapp;
+    for (int j = 1; j < N; ++j) h->E[j] = 0.5 * (h->Eh[j - 1] + h->Eh[j]) + Eapp;
+    h->E[N] = h->Eh[N - 1] + Eapp;
+    for (int j = 0; j <= N; ++j)
+      if (!isfinite(h->E[j])) h->err = ORA_ENONFINITE;
   } else {
     ora_field_exact(N, h->i.Q, h->e.Q, h->C_field, h->Eh);
     double Eapp = -h->E0;
@@ -357,7 +395,7 @@ static void solve_field(ora_t *h) {
     }
   }
   for (int j = 0; j < N; ++j) h->Ef[j] = (real)h->E[j];
-  h->Ef[N] = h->Ef[0];
+  h->Ef[N] = h->bounded ? (real)h->E[N] : h->Ef[0];
 }
 
 static real gather(const ora_t *h, int32_t cell, real off) {
@@ -366,17 +404,26 @@ static real gather(const ora_t *h, int32_t cell, real off) {
 }
 
 /* leapfrog kick + drift with periodic re-injection (Sec. II: particles leaving
- * one end re-enter at the other with the same velocity). */
-static void push(const ora_t *h, real a, real d, real E, int32_t *cell, real *off, real *vx) {
+ * one end re-enter at the other with the same velocity).  Bounded column
+ * (Sec. V): a particle leaving [0, L) is taken by the electrode it crossed;
+ * returns -1 (cathode, x < 0) or +1 (anode, x >= L), else 0. */
+static int push(const ora_t *h, real a, real d, real E, int32_t *cell, real *off, real *vx) {
   *vx = *vx + a * E;
   real f = *off + *vx * d;
   real c = R_FLOOR(f);
   f = f - c;
   int32_t cl = *cell + (int32_t)c;
   if (f >= (real)1) { f = (real)0; cl += 1; }
+  if (h->bounded) {
+    if (cl < 0) { *cell = 0; *off = 0; return -1; }
+    if (cl >= h->N) { *cell = h->N - 1; *off = 0; return 1; }
+    *cell = cl; *off = f;
+    return 0;
+  }
   cl %= h->N;
   if (cl < 0) cl += h->N;
   *cell = cl; *off = f;
+  return 0;
 }
 
 /* table position of eps: i, fraction fr; above the table the last value is held */
@@ -390,7 +437,7 @@ static int tab_pos(real eps, real inv_de, int ntab, real *fr, int *ovf) {
 }
 
 static void moments_alloc(ora_t *h) {
-  int N = h->N;
+  int N = h->N + 1;
   h->m_ne = (double *)xcalloc(N, 8); h->m_ni = (double *)xcalloc(N, 8);
   h->m_ge = (double *)xcalloc(N, 8); h->m_ee = (double *)xcalloc(N, 8);
   h->m_he = (double *)xcalloc(N, 8); h->m_gi = (double *)xcalloc(N, 8);
@@ -398,7 +445,7 @@ static void moments_alloc(ora_t *h) {
   h->m_iz = (int64_t *)xcalloc(N, 8);
 }
 static void moments_reset(ora_t *h) {
-  size_t b = (size_t)h->N * 8;
+  size_t b = (size_t)(h->N + 1) * 8;
   memset(h->m_ne, 0, b); memset(h->m_ni, 0, b); memset(h->m_ge, 0, b); memset(h->m_ee, 0, b);
   memset(h->m_he, 0, b); memset(h->m_gi, 0, b); memset(h->m_E, 0, b); memset(h->m_phi, 0, b);
   memset(h->m_iz, 0, b);
@@ -441,13 +488,14 @@ static void electron_step(ora_t *h, int64_t p, int diag) {
   uint64_t id = s->id[p];
   uint32_t stp = (uint32_t)h->step, col = (uint32_t)h->p.column;
   real Ep = gather(h, cell, off);
-  push(h, h->a_e, h->d_e, Ep, &cell, &off, &vx);
+  int side = push(h, h->a_e, h->d_e, Ep, &cell, &off, &vx);
   uint32_t w[4];
   rng_block(h->p.seed, id, stp, ST_E, col, 0, w);
   ustream us; us_init(&us, h->p.seed, id, stp, ST_E, col);
   int32_t code = -1;
   int dead = 0;
-  if (h->p.loss_mode == ORA_LOSS_RADIAL && w[2] < h->Pw_e) dead = 1;
+  if (side) { dead = 1; h->st.absorbed_e[side > 0] += 1; }
+  else if (h->p.loss_mode == ORA_LOSS_RADIAL && w[2] < h->Pw_e) dead = 1;
   if (!dead) {
     real u0 = u_dec(w[0]), u1 = u_dec(w[1]);
     real eps = h->K_e * (vx * vx + vy * vy + vz * vz);
@@ -506,7 +554,7 @@ static void electron_step(ora_t *h, int64_t p, int diag) {
           }
           if (h->m_iz) {
             uint64_t kk = (uint64_t)(off * (real)TWO32);
-            int c1 = (cell + 1 == h->N) ? 0 : cell + 1;
+            int c1 = (cell + 1 == h->Nw) ? 0 : cell + 1;
             h->m_iz[cell] += (int64_t)(((uint64_t)1 << 32) - kk);
             h->m_iz[c1] += (int64_t)kk;
           }
@@ -519,7 +567,7 @@ static void electron_step(ora_t *h, int64_t p, int diag) {
   s->cell[p] = cell; s->off[p] = off; s->vx[p] = vx; s->vy[p] = vy; s->vz[p] = vz;
   s->code[p] = code;
   if (dead) { h->dead_e[h->nde++] = p; return; }
-  deposit(s->Q, h->N, cell, off, +1);
+  deposit(s->Q, h->Nw, cell, off, +1);
   if (h->p.drive == ORA_DRIVE_CIRCUIT) h->sumv[0] += (int64_t)llrint((double)(vx * (real)256));
   if (diag) {
     real er = h->K_e * (vx * vx + vy * vy + vz * vz);
@@ -530,9 +578,9 @@ static void electron_step(ora_t *h, int64_t p, int diag) {
       int bx = (int)(((int64_t)cell * h->eepf_nx) / h->N);
       h->eepf[(size_t)bx * (size_t)(h->eepf_ne + 1) + (size_t)b] += 1;
     }
-    moment_add(h->m_ge, h->N, cell, off, (double)vx);
-    moment_add(h->m_ee, h->N, cell, off, eps);
-    moment_add(h->m_he, h->N, cell, off, eps * (double)vx);
+    moment_add(h->m_ge, h->Nw, cell, off, (double)vx);
+    moment_add(h->m_ee, h->Nw, cell, off, eps);
+    moment_add(h->m_he, h->Nw, cell, off, eps * (double)vx);
   }
 }
 
@@ -548,13 +596,14 @@ static void ion_step(ora_t *h, int64_t p, int diag) {
   uint64_t id = s->id[p];
   uint32_t stp = (uint32_t)h->step, col = (uint32_t)h->p.column;
   real Ep = gather(h, cell, off);
-  push(h, h->a_i, h->d_i, Ep, &cell, &off, &vx);
+  int side = push(h, h->a_i, h->d_i, Ep, &cell, &off, &vx);
   uint32_t w[4];
   rng_block(h->p.seed, id, stp, ST_I, col, 0, w);
   ustream us; us_init(&us, h->p.seed, id, stp, ST_I, col);
   int32_t code = -1;
   int dead = 0;
-  if (h->p.loss_mode == ORA_LOSS_RADIAL && w[2] < h->Pw_i) dead = 1;
+  if (side) { dead = 1; h->st.absorbed_i[side > 0] += 1; }
+  else if (h->p.loss_mode == ORA_LOSS_RADIAL && w[2] < h->Pw_i) dead = 1;
   if (!dead) {
     real u0 = u_dec(w[0]), u1 = u_dec(w[1]);
     if (u0 < h->P_i) {
@@ -596,9 +645,9 @@ static void ion_step(ora_t *h, int64_t p, int diag) {
   s->cell[p] = cell; s->off[p] = off; s->vx[p] = vx; s->vy[p] = vy; s->vz[p] = vz;
   s->code[p] = code;
   if (dead) { h->dead_i[h->ndi++] = p; return; }
-  deposit(s->Q, h->N, cell, off, +1);
+  deposit(s->Q, h->Nw, cell, off, +1);
   if (h->p.drive == ORA_DRIVE_CIRCUIT) h->sumv[1] += (int64_t)llrint((double)(vx * (real)256));
-  if (diag) moment_add(h->m_gi, h->N, cell, off, (double)vx);
+  if (diag) moment_add(h->m_gi, h->Nw, cell, off, (double)vx);
 }
 
 /* uniform slot in [0, n) from a 64-bit word: floor(r n / 2^64) */
@@ -665,7 +714,7 @@ static int fill_and_compact(ora_t *h, species *s, const int64_t *dead, int64_t n
     const birth *b = &h->births[k];
     uint64_t id = (uint64_t)h->next_id + 2 * (uint64_t)k + (uint64_t)is_ion;
     write_newborn(s, dead[k], b->cell, b->off, is_ion ? b->vi : b->ve, id);
-    deposit(s->Q, h->N, b->cell, b->off, +1);
+    deposit(s->Q, h->Nw, b->cell, b->off, +1);
   }
   if (nb > nd) {
     if (N + (nb - nd) > s->cap) return ORA_ECAPACITY;
@@ -673,7 +722,7 @@ static int fill_and_compact(ora_t *h, species *s, const int64_t *dead, int64_t n
       const birth *b = &h->births[k];
       uint64_t id = (uint64_t)h->next_id + 2 * (uint64_t)k + (uint64_t)is_ion;
       write_newborn(s, N + (k - m), b->cell, b->off, is_ion ? b->vi : b->ve, id);
-      deposit(s->Q, h->N, b->cell, b->off, +1);
+      deposit(s->Q, h->Nw, b->cell, b->off, +1);
     }
     s->n = N + (nb - nd);
   } else if (nd > nb) {
@@ -703,17 +752,19 @@ static int births_and_losses(ora_t *h, int ion_pushed) {
       if (rc) { free(ve); free(vi); return rc; }
       for (int64_t k = 0; k < nb; ++k) {
         const birth *b = &h->births[k];
-        deposit(h->e.Q, h->N, h->e.cell[ve[k]], h->e.off[ve[k]], -1);
+        deposit(h->e.Q, h->Nw, h->e.cell[ve[k]], h->e.off[ve[k]], -1);
         write_newborn(&h->e, ve[k], b->cell, b->off, b->ve, (uint64_t)h->next_id + 2 * (uint64_t)k);
-        deposit(h->e.Q, h->N, b->cell, b->off, +1);
-        deposit(h->i.Q, h->N, h->i.cell[vi[k]], h->i.off[vi[k]], -1);
+        deposit(h->e.Q, h->Nw, b->cell, b->off, +1);
+        deposit(h->i.Q, h->Nw, h->i.cell[vi[k]], h->i.off[vi[k]], -1);
         write_newborn(&h->i, vi[k], b->cell, b->off, b->vi, (uint64_t)h->next_id + 2 * (uint64_t)k + 1);
-        deposit(h->i.Q, h->N, b->cell, b->off, +1);
+        deposit(h->i.Q, h->Nw, b->cell, b->off, +1);
       }
       free(ve); free(vi);
       h->st.losses_e += nb; h->st.losses_i += nb;
     }
-  } else if (lm == ORA_LOSS_RADIAL) {
+  } else if (lm == ORA_LOSS_RADIAL || h->bounded) {
+    /* removed particles (radial losses; in a bounded column also those the electrodes took) leave
+       holes that the births fill, the rest compacted */
     int rc = fill_and_compact(h, &h->e, h->dead_e, h->nde, 0);
     if (!rc) rc = fill_and_compact(h, &h->i, h->dead_i, ion_pushed ? h->ndi : 0, 1);
     if (rc) return rc;
@@ -723,9 +774,9 @@ static int births_and_losses(ora_t *h, int ion_pushed) {
     for (int64_t k = 0; k < nb; ++k) {
       const birth *b = &h->births[k];
       write_newborn(&h->e, h->e.n + k, b->cell, b->off, b->ve, (uint64_t)h->next_id + 2 * (uint64_t)k);
-      deposit(h->e.Q, h->N, b->cell, b->off, +1);
+      deposit(h->e.Q, h->Nw, b->cell, b->off, +1);
       write_newborn(&h->i, h->i.n + k, b->cell, b->off, b->vi, (uint64_t)h->next_id + 2 * (uint64_t)k + 1);
-      deposit(h->i.Q, h->N, b->cell, b->off, +1);
+      deposit(h->i.Q, h->Nw, b->cell, b->off, +1);
     }
     h->e.n += nb; h->i.n += nb;
   }
@@ -734,6 +785,38 @@ static int births_and_losses(ora_t *h, int ion_pushed) {
     h->next_id += 2 * nb;
   }
   h->nb = 0;
+  if (h->bounded && h->emit_per_step > 0.0) {
+    /* Sec. V: the cathode emits the current density J_emit: J_emit dt / (e w) macro-electrons per
+       step (the fraction carried over).  Emitted electron k of step s draws (Philox counter k, s,
+       emission stream) a half-Maxwellian velocity at T_emit, v_x = sig |g0|, v_y = sig g1,
+       v_z = sig g2, and starts at x = u v_x dt (the part of the step it has already flown). */
+    h->emit_acc += h->emit_per_step;
+    int64_t ne = (int64_t)floor(h->emit_acc);
+    h->emit_acc -= (double)ne;
+    species *s = &h->e;
+    if (s->n + ne > s->cap) return ORA_ECAPACITY;
+    uint32_t stp = (uint32_t)h->step, col = (uint32_t)h->p.column;
+    for (int64_t k = 0; k < ne; ++k) {
+      ustream us; us_init(&us, h->p.seed, (uint64_t)k, stp, ST_EMIT, col);
+      real g0 = gauss_sample(h->gauss, us_next(&us));
+      real g1 = gauss_sample(h->gauss, us_next(&us));
+      real g2 = gauss_sample(h->gauss, us_next(&us));
+      real u = us_next(&us);
+      real v[3];
+      v[0] = h->sig_emit * (g0 < (real)0 ? -g0 : g0);
+      v[1] = h->sig_emit * g1;
+      v[2] = h->sig_emit * g2;
+      real x = u * v[0] * h->emit_dtdx;
+      int32_t cell = (int32_t)x;
+      real off = x - (real)cell;
+      if (cell >= h->N) { cell = h->N - 1; off = (real)0; }
+      write_newborn(s, s->n + k, cell, off, v, (uint64_t)h->next_id + (uint64_t)k);
+      deposit(s->Q, h->Nw, cell, off, +1);
+    }
+    s->n += ne;
+    h->next_id += ne;
+    h->st.emitted += ne;
+  }
   return 0;
 }
 
@@ -774,11 +857,11 @@ static int step_once(ora_t *h) {
     int64_t pi = (int64_t)h->p.sort_every * (sub > 0 ? sub : 1);
     if (h->step % pi == 0) sort_species(h, &h->i);
   }
-  memset(h->e.Q, 0, sizeof(int64_t) * (size_t)h->N);
+  memset(h->e.Q, 0, sizeof(int64_t) * (size_t)h->Nw);
   h->sumv[0] = 0;
   for (int64_t p = 0; p < h->e.n; ++p) electron_step(h, p, diag);
   if (ion_push) {
-    memset(h->i.Q, 0, sizeof(int64_t) * (size_t)h->N);
+    memset(h->i.Q, 0, sizeof(int64_t) * (size_t)h->Nw);
     h->sumv[1] = 0;
     for (int64_t p = 0; p < h->i.n; ++p) ion_step(h, p, diag);
   }
@@ -798,12 +881,12 @@ static int step_once(ora_t *h) {
   solve_field(h);
   if (diag) {
     double phi = 0.0;
-    for (int j = 0; j < h->N; ++j) {
+    for (int j = 0; j < h->Nw; ++j) {
       h->m_ne[j] += (double)h->e.Q[j] * (1.0 / TWO32);
       h->m_ni[j] += (double)h->i.Q[j] * (1.0 / TWO32);
       h->m_E[j] += h->E[j];
       h->m_phi[j] += phi;
-      phi = phi - h->dx * h->Eh[j];
+      if (j < h->N) phi = phi - h->dx * h->Eh[j];
     }
     h->m_samples++;
     h->st.n_diag++;
@@ -830,8 +913,8 @@ static void half_step_back(ora_t *h, species *s, real a) {
 }
 
 static void redeposit(ora_t *h, species *s) {
-  memset(s->Q, 0, sizeof(int64_t) * (size_t)h->N);
-  for (int64_t p = 0; p < s->n; ++p) deposit(s->Q, h->N, s->cell[p], s->off[p], +1);
+  memset(s->Q, 0, sizeof(int64_t) * (size_t)h->Nw);
+  for (int64_t p = 0; p < s->n; ++p) deposit(s->Q, h->Nw, s->cell[p], s->off[p], +1);
 }
 
 /* Initial state (Sec. II: uniform, equal electron and ion densities;
@@ -871,6 +954,13 @@ int ora_create(const ora_params *pp, ora_t **out) {
   if (!h) return ORA_ENOMEM;
   h->p = *pp;
   h->N = pp->n_cells;
+  h->bounded = (pp->flags & ORA_FLAG_BOUNDED) != 0;
+  h->Nw = h->N + h->bounded;
+  if (h->bounded && ((pp->loss_mode != ORA_LOSS_RADIAL && pp->loss_mode != ORA_LOSS_NONE) ||
+                     !(pp->J_emit_Am2 >= 0.0) || !(pp->T_emit_eV >= 0.0))) {
+    free(h);
+    return ORA_EINVAL;
+  }
   h->ntab = pp->n_table;
   double M = pp->gas_mass_amu * AMU;
   h->M = M;
@@ -894,6 +984,9 @@ int ora_create(const ora_params *pp, ora_t **out) {
   h->sig_n = (real)sqrt(KB * pp->T_gas_K / M);
   h->sig_e0 = (real)sqrt(QE * pp->Te0_eV / ME);
   h->sig_i0 = (real)sqrt(QE * pp->Ti0_eV / M);
+  h->sig_emit = (real)sqrt(QE * pp->T_emit_eV / ME);
+  h->emit_dtdx = (real)(pp->dt_s / h->dx);
+  h->emit_per_step = (h->bounded && h->w > 0.0) ? pp->J_emit_Am2 * pp->dt_s / (QE * h->w) : 0.0;
   /* collision-frequency tables */
   int n = h->ntab;
   double sum_e_max = 0.0, sum_i_max = 0.0;
@@ -959,8 +1052,8 @@ int ora_create(const ora_params *pp, ora_t **out) {
   int64_t nmax = pp->n_e0 > pp->n_i0 ? pp->n_e0 : pp->n_i0;
   if (cap <= 0) cap = nmax + nmax / 4 + 1024;
   if (cap < nmax) { ora_destroy(h); return ORA_EINVAL; }
-  if (species_alloc(&h->e, cap, h->N) || species_alloc(&h->i, cap, h->N)) { ora_destroy(h); return ORA_ENOMEM; }
-  h->E = (double *)xcalloc((size_t)h->N, 8);
+  if (species_alloc(&h->e, cap, h->N + 1) || species_alloc(&h->i, cap, h->N + 1)) { ora_destroy(h); return ORA_ENOMEM; }
+  h->E = (double *)xcalloc((size_t)h->N + 1, 8);
   h->Eh = (double *)xcalloc((size_t)h->N, 8);
   h->Ef = (real *)xcalloc((size_t)h->N + 1, sizeof(real));
   moments_alloc(h);
@@ -1026,9 +1119,10 @@ int ora_get_state(ora_t *h, ora_state *s) {
       if (ids[q]) ids[q][p] = sp[q]->id[p];
     }
   }
-  if (s->E) memcpy(s->E, h->E, sizeof(double) * (size_t)h->N);
-  if (s->Q_e) memcpy(s->Q_e, h->e.Q, sizeof(int64_t) * (size_t)h->N);
-  if (s->Q_i) memcpy(s->Q_i, h->i.Q, sizeof(int64_t) * (size_t)h->N);
+  /* node arrays: n_cells entries, n_cells + 1 in a bounded column */
+  if (s->E) memcpy(s->E, h->E, sizeof(double) * (size_t)h->Nw);
+  if (s->Q_e) memcpy(s->Q_e, h->e.Q, sizeof(int64_t) * (size_t)h->Nw);
+  if (s->Q_i) memcpy(s->Q_i, h->i.Q, sizeof(int64_t) * (size_t)h->Nw);
   return 0;
 }
 
@@ -1055,15 +1149,16 @@ int ora_set_state(ora_t *h, const ora_state *s) {
     sp[q]->n = ns[q];
   }
   h->step = s->step; h->next_id = s->next_id; h->E0 = s->E0;
+  h->emit_acc = 0.0;
   h->sumv[1] = 0;
   for (int64_t p = 0; p < h->i.n; ++p) h->sumv[1] += (int64_t)llrint((double)(h->i.vx[p] * (real)256));
   redeposit(h, &h->e);
-  if (s->Q_i) memcpy(h->i.Q, s->Q_i, sizeof(int64_t) * (size_t)h->N);
+  if (s->Q_i) memcpy(h->i.Q, s->Q_i, sizeof(int64_t) * (size_t)h->Nw);
   else redeposit(h, &h->i);
   if (s->E) {
-    memcpy(h->E, s->E, sizeof(double) * (size_t)h->N);
+    memcpy(h->E, s->E, sizeof(double) * (size_t)h->Nw);
     for (int j = 0; j < h->N; ++j) h->Ef[j] = (real)h->E[j];
-    h->Ef[h->N] = h->Ef[0];
+    h->Ef[h->N] = h->bounded ? (real)h->E[h->N] : h->Ef[0];
   } else {
     solve_field(h);
   }
@@ -1077,7 +1172,7 @@ int ora_stats_get(ora_t *h, ora_stats *s) {
 }
 
 int ora_moments_get(ora_t *h, ora_moments *m) {
-  int N = h->N;
+  int N = h->Nw;
   double ns = h->m_samples > 0 ? (double)h->m_samples : 1.0;
   double dens = h->w / h->dx;
   double tsteps = (double)(h->m_steps > 0 ? h->m_steps : 1) * h->p.dt_s;

@@ -23,6 +23,9 @@ enum { ORA_ELASTIC = 0, ORA_EXCITATION = 1, ORA_IONIZATION = 2, ORA_ION_CX = 3, 
 enum { ORA_DRIVE_E0 = 0, ORA_DRIVE_V = 1, ORA_DRIVE_CIRCUIT = 2 };
 enum { ORA_FIELD_POISSON = 0, ORA_FIELD_APPLIED = 1 };
 enum { ORA_LOSS_PAIR = 0, ORA_LOSS_RADIAL = 1, ORA_LOSS_NONE = 2, ORA_LOSS_SWARM = 3 };
+/* flags: ORA_FLAG_BOUNDED = the bounded column of Sec. V (absorbing electrodes at x = 0, the
+   cathode, and x = L, the anode; Dirichlet field; electron emission at the cathode) */
+enum { ORA_FLAG_BOUNDED = 8 };
 enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_ENOMEM = -2, ORA_ECAPACITY = -4, ORA_ENONFINITE = -5,
        ORA_EPARAM = -7 };
 
@@ -51,6 +54,7 @@ typedef struct ora_params {
   int32_t diag_every, sort_every, n_table, flags;
   double eps_max_e_eV, eps_max_i_eV;
   int32_t column, pad1;
+  double J_emit_Am2, T_emit_eV;   /* bounded column: cathode emission current density, emission temperature */
 } ora_params;
 
 typedef struct ora_state {
@@ -70,6 +74,8 @@ typedef struct ora_stats {
   int64_t overflow_e, overflow_i;
   double E0;
   int64_t n_diag;
+  int64_t absorbed_e[2], absorbed_i[2];   /* bounded column: particles taken by [cathode, anode] */
+  int64_t emitted;                        /* electrons emitted by the cathode */
 } ora_stats;
 
 typedef struct ora_moments {
@@ -107,6 +113,9 @@ double ora_i128_to_double(int64_t hi, uint64_t lo);
 /* E at half-nodes from node charges by the exact integer route (Gauss's law,
  * zero-mean field, uniform background removed); C = e w / (eps0 2^32) */
 void ora_field_exact(int n_cells, const int64_t *Q_i, const int64_t *Q_e, double C, double *E_half);
+/* bounded column: space-charge field at the n_cells faces from the charges of nodes 1..n_cells-1
+   (the electrode nodes 0 and n_cells carry surface charge), with phi equal at both electrodes */
+void ora_field_exact_bounded(int n_cells, const int64_t *Q_i, const int64_t *Q_e, double C, double *E_half);
 /* phi at nodes (phi_0 = 0) from node charge density rho (C/m^3) by Thomas on the
  * gauge-pinned tridiagonal system; returns 0 or ORA_EINVAL */
 int ora_poisson_thomas(int n_cells, double dx, const double *rho, double *phi);

@@ -36,6 +36,7 @@ DRIVE_E0, DRIVE_V, DRIVE_CIRCUIT, DRIVE_RI = 0, 1, 2, 3
 FIELD_POISSON, FIELD_APPLIED = 0, 1
 # loss modes
 LOSS_PAIR, LOSS_RADIAL, LOSS_NONE, LOSS_SWARM = 0, 1, 2, 3
+FLAG_RECORD_CODES, FLAG_NO_GRAPH, FLAG_ALLOW_LARGE_NULL, FLAG_BOUNDED = 1, 2, 4, 8
 # particle storage forms
 FP64, MIXED = 0, 1
 
@@ -135,6 +136,13 @@ class Params:
     eps_max_e_eV: float = 500.0
     eps_max_i_eV: float = 50.0
     column: int = 0
+    J_emit_Am2: float = 0.0       # bounded column (FLAG_BOUNDED): cathode emission current density
+    T_emit_eV: float = 0.0        # and its emission temperature
+
+    @property
+    def n_nodes(self) -> int:
+        """Entries of the node arrays: n_cells, or n_cells + 1 between two electrodes."""
+        return self.n_cells + (1 if self.flags & FLAG_BOUNDED else 0)
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)
