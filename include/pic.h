@@ -81,6 +81,15 @@ extern "C" {
 #define PIC_FLAG_RECORD_CODES 1u        /* keep each particle's process code of the last step */
 #define PIC_FLAG_NO_GRAPH 2u            /* launch kernels one by one instead of CUDA graphs */
 #define PIC_FLAG_ALLOW_LARGE_NULL 4u    /* accept nu* dt > 0.3 */
+#define PIC_FLAG_BOUNDED 8u             /* Sec. V: the bounded column instead of the periodic one.  The
+                                           cathode (x = 0) and anode (x = L) take every particle that
+                                           crosses them; the field solves Gauss's law between them
+                                           with the potential V_D = E0 L across the gap (E0 from the
+                                           drive: V_applied / L, E0_Vpm, or the circuit's
+                                           (U_src - R_ext J) / L); the cathode emits J_emit_Am2 at
+                                           T_emit_eV.  Node arrays get n_cells + 1 entries.  Needs
+                                           PIC_LOSS_RADIAL (the fixed loss frequency nu_w of Sec. V)
+                                           or PIC_LOSS_NONE; single columns only. */
 
 /* One collision process (Sec. II, "scattering cross-sections"): sigma(eps)
  * on an ascending energy grid.  Electron processes use the electron energy;
@@ -129,10 +138,15 @@ typedef struct pic_params {
   double eps_max_e_eV;     /* electron table range [0, eps_max_e]; higher energies hold the last value */
   double eps_max_i_eV;     /* ion table range */
   int32_t column, pad1;    /* column index mixed into the random-number counters (batched runs) */
+  double J_emit_Am2;       /* PIC_FLAG_BOUNDED: electron current density emitted by the cathode: J dt / (e w)
+                              macro-electrons per step (fraction carried over), velocities (s |g0|, s g1, s g2)
+                              with s = (e T_emit / m)^(1/2), starting at x = u v_x dt */
+  double T_emit_eV;        /* emission temperature */
 } pic_params;
 
 /* Particle state and field, host arrays.  pic_get_state fills the non-NULL
- * arrays (lengths >= n_e, n_i, n_cells); pic_set_state reads them.  For
+ * arrays (lengths >= n_e, n_i, and the node count: n_cells, or n_cells + 1 in a
+ * bounded column); pic_set_state reads them.  For
  * PIC_MIXED the offsets/velocities are rounded to FP32 on set and widened on get.
  * Offsets lie in [0, 1): position x = (cell + off) L / n_cells. */
 typedef struct pic_state {
@@ -142,7 +156,7 @@ typedef struct pic_state {
   double E0;               /* current |applied field| */
   int32_t *cell_e; double *off_e, *vx_e, *vy_e, *vz_e; uint64_t *id_e;
   int32_t *cell_i; double *off_i, *vx_i, *vy_i, *vz_i; uint64_t *id_i;
-  double *E;               /* node field E^n (V/m), n_cells; set: NULL = recompute from the charges */
+  double *E;               /* node field E^n (V/m), one per node; set: NULL = recompute from the charges */
   int64_t *Q_e;            /* electron node charge, fixed point 2^32 per particle (get only) */
   int64_t *Q_i;            /* ion node charge, fixed point (set: NULL = re-deposit the ions) */
 } pic_state;
@@ -157,10 +171,13 @@ typedef struct pic_stats {
   int64_t overflow_e, overflow_i;  /* collisions evaluated above the table range */
   double E0;
   int64_t n_diag;          /* diagnostic samples taken */
+  int64_t absorbed_e[2], absorbed_i[2];   /* PIC_FLAG_BOUNDED: particles taken by [cathode, anode] */
+  int64_t emitted;         /* electrons emitted by the cathode */
 } pic_stats;
 
 /* Time-averaged moments over the current window (the profiles of Fig. 4).
- * Every non-NULL array has n_cells entries (node values). */
+ * Every non-NULL array has one entry per node (n_cells, or n_cells + 1 in a bounded
+ * column). */
 typedef struct pic_moments_out {
   int64_t n_samples, n_steps;   /* diagnostic samples / steps in the window (out) */
   double *n_e, *n_i;            /* densities (m^-3) */
@@ -191,7 +208,7 @@ int pic_init(const pic_params *params, pic_handle **out);
  * the device status word. */
 int pic_step(pic_handle *h, int64_t n);
 
-/* Copy the moment window (host arrays of n_cells, NULL to skip). */
+/* Copy the moment window (host arrays of one entry per node, NULL to skip). */
 int pic_moments(pic_handle *h, pic_moments_out *out);
 
 /* Electron energy probability function F(x, eps) (Sec. III.C, Fig. 8), sampled as a

@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("diag_every", C.c_int32), ("sort_every", C.c_int32), ("n_table", C.c_int32),
                 ("flags", C.c_uint32),
                 ("eps_max_e_eV", C.c_double), ("eps_max_i_eV", C.c_double),
-                ("column", C.c_int32), ("pad1", C.c_int32)]
+                ("column", C.c_int32), ("pad1", C.c_int32),
+                ("J_emit_Am2", C.c_double), ("T_emit_eV", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -70,7 +71,8 @@ class Stats(C.Structure):
                 ("n_coll_e", C.c_int64 * 8), ("n_coll_i", C.c_int64 * 8),
                 ("births", C.c_int64), ("losses_e", C.c_int64), ("losses_i", C.c_int64),
                 ("overflow_e", C.c_int64), ("overflow_i", C.c_int64),
-                ("E0", C.c_double), ("n_diag", C.c_int64)]
+                ("E0", C.c_double), ("n_diag", C.c_int64),
+                ("absorbed_e", C.c_int64 * 2), ("absorbed_i", C.c_int64 * 2), ("emitted", C.c_int64)]
 
 
 MOMENT_NAMES = ("n_e", "n_i", "gamma_e", "mean_eps_e", "heat_e", "iz_rate", "gamma_i", "E", "phi")
@@ -257,6 +259,7 @@ class Column:
         self.L = lib()
         self.params = params
         self.N = params.n_cells
+        self.nodes = params.n_nodes          # node arrays: n_cells, or n_cells + 1 between electrodes
         self.cap = params.capacity or (max(params.n_e0, params.n_i0) * 5 // 4 + 1024)
         self._owned = _handle is None
         if _handle is not None:
@@ -286,6 +289,7 @@ class Column:
         _check(self.L.pic_get_stats(self.h, C.byref(s)), self.h)
         d = {k: getattr(s, k) for k, _ in Stats._fields_}
         d["n_coll_e"], d["n_coll_i"] = list(s.n_coll_e), list(s.n_coll_i)
+        d["absorbed_e"], d["absorbed_i"] = list(s.absorbed_e), list(s.absorbed_i)
         return d
 
     def derived(self) -> dict:
@@ -303,7 +307,7 @@ class Column:
              "vy_e": np.zeros(ne), "vz_e": np.zeros(ne), "id_e": np.zeros(ne, np.uint64),
              "cell_i": np.zeros(ni, np.int32), "off_i": np.zeros(ni), "vx_i": np.zeros(ni),
              "vy_i": np.zeros(ni), "vz_i": np.zeros(ni), "id_i": np.zeros(ni, np.uint64),
-             "E": np.zeros(self.N), "Q_e": np.zeros(self.N, np.int64), "Q_i": np.zeros(self.N, np.int64)}
+             "E": np.zeros(self.nodes), "Q_e": np.zeros(self.nodes, np.int64), "Q_i": np.zeros(self.nodes, np.int64)}
         s = State()
         for k, t in (("cell", _I32), ("off", _D), ("vx", _D), ("vy", _D), ("vz", _D), ("id", _U64)):
             for sp in ("e", "i"):
@@ -347,7 +351,7 @@ class Column:
         return out
 
     def moments(self, reset: bool = False) -> dict:
-        d = {k: np.zeros(self.N) for k in MOMENT_NAMES}
+        d = {k: np.zeros(self.nodes) for k in MOMENT_NAMES}
         m = MomentsOut()
         for k in MOMENT_NAMES:
             setattr(m, k, _ptr(d[k], _D))

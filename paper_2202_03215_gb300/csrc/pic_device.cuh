@@ -108,15 +108,24 @@ template <class R> __device__ __forceinline__ void iso_dir(UStream<R> &us, R &nx
   nx = a * t2; ny = b * t2; nz = (R)1 - (R)2 * q;
 }
 
-// leapfrog kick + drift in cell units with periodic re-injection
+// leapfrog kick + drift in cell units with periodic re-injection; in a bounded column (Sec. V) a
+// particle leaving [0, L) is taken by the electrode it crossed: returns -1 (cathode, x < 0, the
+// record left at cell 0) or +1 (anode, x >= L, at cell N - 1), else 0
 template <class R>
-__device__ __forceinline__ void push(int N, R a, R d, R E, int32_t &cell, R &off, R &vx) {
+__device__ __forceinline__ int push(int N, bool bounded, R a, R d, R E, int32_t &cell, R &off, R &vx) {
   vx = vx + a * E;
   R f = off + vx * d;
   const R c = floor(f);
   f = f - c;
   int32_t cl = cell + (int32_t)c;
   if (f >= (R)1) { f = (R)0; cl += 1; }
+  if (bounded) {
+    if (cl < 0) { cell = 0; off = (R)0; return -1; }
+    if (cl >= N) { cell = N - 1; off = (R)0; return 1; }
+    cell = cl;
+    off = f;
+    return 0;
+  }
   // cl mod N, without a division when the particle moved less than a column length
   if (cl >= N) cl = cl < 2 * N ? cl - N : cl % N;
   else if (cl < 0) {
@@ -125,6 +134,7 @@ __device__ __forceinline__ void push(int N, R a, R d, R E, int32_t &cell, R &off
   }
   cell = cl;
   off = f;
+  return 0;
 }
 
 template <class R> __device__ __forceinline__ R gather(const R *E, int32_t cell, R off) {

@@ -32,6 +32,7 @@ thread_local std::string g_err;
 struct pic_handle {
   pic_params p{};
   int N = 0;
+  int Nn = 0;                         // node-array entries: N, or N + 1 in a bounded column
   int ntab = 0;
   int nsm = 0;
   bool mixed = false;
@@ -243,6 +244,11 @@ template <class R> int setup_tables(pic_handle *h) {
   const pic_params &p = h->p;
   const int n = h->ntab;
   k.N = h->N;
+  k.bounded = (p.flags & PIC_FLAG_BOUNDED) ? 1 : 0;
+  k.Nw = h->N + k.bounded;
+  k.emit_per_step = (k.bounded && h->w > 0.0) ? p.J_emit_Am2 * p.dt_s / (kQe * h->w) : 0.0;
+  k.sig_emit = (R)std::sqrt(kQe * p.T_emit_eV / kMe);
+  k.emit_dtdx = (R)(p.dt_s / h->dx);
   k.ntab = n;
   k.loss_mode = p.loss_mode;
   k.field_mode = p.field_mode;
@@ -332,9 +338,9 @@ template <class R> int alloc_species(pic_handle *h) {
     CU(h, cudaMalloc(&s.cell, (size_t)cap * 4));
     CU(h, cudaMalloc(&s.rec, (size_t)cap * sizeof(typename pic::Rec<R>::T)));
     CU(h, cudaMalloc(&s.id, (size_t)cap * 8));
-    CU(h, cudaMalloc(&s.Q, (size_t)h->N * 8));
+    CU(h, cudaMalloc(&s.Q, (size_t)(h->N + 1) * 8));
     CU(h, cudaMalloc(&s.dead, (size_t)pic::kStageCap * 4));
-    CU(h, cudaMemset(s.Q, 0, (size_t)h->N * 8));
+    CU(h, cudaMemset(s.Q, 0, (size_t)(h->N + 1) * 8));
     if (h->p.flags & PIC_FLAG_RECORD_CODES) {
       CU(h, cudaMalloc(&s.code, (size_t)cap * 4));
       CU(h, cudaMemset(s.code, 0xff, (size_t)cap * 4));
@@ -402,12 +408,12 @@ template <class R> int enqueue_step(pic_handle *h) {
   }
   const bool circuit = h->p.drive == PIC_DRIVE_CIRCUIT;
   if (circuit) CU(h, cudaMemsetAsync(&h->ctl->sumv[0], 0, 8, h->stream));
-  CU(h, cudaMemsetAsync(h->sp[0].Q, 0, (size_t)h->N * 8, h->stream));
+  CU(h, cudaMemsetAsync(h->sp[0].Q, 0, (size_t)h->Nn * 8, h->stream));
   t_begin(h);
   pic::launch_push<R>(k, h->sp[0], h->ctl, Ef, bbuf<R>(h), h->m, 0, h->nsm, h->stream);
   t_end(h, PIC_K_PUSH_E);
   if (ion_push) {
-    CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->N * 8, h->stream));
+    CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->Nn * 8, h->stream));
     if (circuit) CU(h, cudaMemsetAsync(&h->ctl->sumv[1], 0, 8, h->stream));
     t_begin(h);
     pic::launch_push<R>(k, h->sp[1], h->ctl, Ef, bbuf<R>(h), h->m, 1, h->nsm, h->stream);
@@ -478,6 +484,12 @@ int validate(const pic_params *p) {
   if (p->field_mode != PIC_FIELD_POISSON && p->field_mode != PIC_FIELD_APPLIED)
     return set_err(nullptr, PIC_EINVAL, "bad field mode");
   if (p->ion_subcycle < 0) return set_err(nullptr, PIC_EINVAL, "ion_subcycle < 0");
+  if (p->flags & PIC_FLAG_BOUNDED) {
+    if (p->loss_mode != PIC_LOSS_RADIAL && p->loss_mode != PIC_LOSS_NONE)
+      return set_err(nullptr, PIC_EINVAL, "a bounded column needs PIC_LOSS_RADIAL or PIC_LOSS_NONE");
+    if (!(p->J_emit_Am2 >= 0.0) || !(p->T_emit_eV >= 0.0))
+      return set_err(nullptr, PIC_EINVAL, "emission current and temperature must be >= 0");
+  }
   if (p->diag_every < 0) return set_err(nullptr, PIC_EINVAL, "diag_every < 0");
   if (p->diag_every > 0 && p->ion_subcycle > 0 && p->diag_every % p->ion_subcycle != 0)
     return set_err(nullptr, PIC_EINVAL, "diag_every must be a multiple of ion_subcycle");
@@ -504,8 +516,9 @@ template <class R> int init_typed(pic_handle *h) {
   if (rc) return rc;
   rc = alloc_species<R>(h);
   if (rc) return rc;
-  h->m.ge = h->mom; h->m.ee = h->mom + h->N; h->m.he = h->mom + 2 * h->N; h->m.gi = h->mom + 3 * h->N;
-  h->m.ne = h->mom + 4 * h->N; h->m.ni = h->mom + 5 * h->N; h->m.E = h->mom + 6 * h->N; h->m.phi = h->mom + 7 * h->N;
+  const size_t ms = (size_t)h->N + 1;   // moment arrays: one entry per node (N + 1 in a bounded column)
+  h->m.ge = h->mom; h->m.ee = h->mom + ms; h->m.he = h->mom + 2 * ms; h->m.gi = h->mom + 3 * ms;
+  h->m.ne = h->mom + 4 * ms; h->m.ni = h->mom + 5 * ms; h->m.E = h->mom + 6 * ms; h->m.phi = h->mom + 7 * ms;
   h->m.iz = h->mom_iz;
   return run_init<R>(h);
 }
@@ -742,6 +755,7 @@ int pic_init(const pic_params *params, pic_handle **out) {
   h->p = *params;  // p.xsec is caller-owned: used during pic_init only, cleared below
   const pic_params &p = *params;
   h->N = p.n_cells;
+  h->Nn = p.n_cells + ((p.flags & PIC_FLAG_BOUNDED) ? 1 : 0);
   h->ntab = p.n_table;
   h->mixed = p.precision == PIC_MIXED;
   h->M = p.gas_mass_amu * kAmu;
@@ -770,17 +784,17 @@ int pic_init(const pic_params *params, pic_handle **out) {
     return fail(set_err(h, PIC_ECUDA, "device query failed"));
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(set_err(h, PIC_ECUDA, "stream creation failed"));
-  if (cudaMalloc(&h->ctl, sizeof(pic::Ctl)) != cudaSuccess || cudaMalloc(&h->E, (size_t)h->N * 8) != cudaSuccess ||
+  if (cudaMalloc(&h->ctl, sizeof(pic::Ctl)) != cudaSuccess || cudaMalloc(&h->E, (size_t)(h->N + 1) * 8) != cudaSuccess ||
       cudaMalloc(&h->Eh, (size_t)h->N * 8) != cudaSuccess || cudaMalloc(&h->Dg, ((size_t)h->N + h->N / 16 + 1) * 8) != cudaSuccess ||
       cudaMalloc(&h->fs, sizeof(pic::FieldScan)) != cudaSuccess ||
       cudaMalloc(&h->gauss, (pic::kGaussN + 1) * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&h->k3_mem, (size_t)pic::kStageCap * 7 * 4) != cudaSuccess ||
-      cudaMalloc(&h->mom, (size_t)h->N * 8 * 8) != cudaSuccess ||
-      cudaMalloc(&h->mom_iz, (size_t)h->N * 8) != cudaSuccess)
+      cudaMalloc(&h->mom, (size_t)(h->N + 1) * 8 * 8) != cudaSuccess ||
+      cudaMalloc(&h->mom_iz, (size_t)(h->N + 1) * 8) != cudaSuccess)
     return fail(set_err(h, PIC_ENOMEM, "device allocation failed"));
-  cudaMemset(h->mom, 0, (size_t)h->N * 8 * 8);
+  cudaMemset(h->mom, 0, (size_t)(h->N + 1) * 8 * 8);
   cudaMemset(h->fs, 0, sizeof(pic::FieldScan));
-  cudaMemset(h->mom_iz, 0, (size_t)h->N * 8);
+  cudaMemset(h->mom_iz, 0, (size_t)(h->N + 1) * 8);
   h->sc.order = h->k3_mem;
   h->sc.cand = h->k3_mem + pic::kStageCap;
   h->sc.att = h->k3_mem + 2 * pic::kStageCap;
@@ -799,6 +813,7 @@ int pic_init(const pic_params *params, pic_handle **out) {
   if (cudaMemcpy(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(set_err(h, PIC_ECUDA, "control block upload failed"));
   h->fk.N = h->N;
+  h->fk.bounded = (p.flags & PIC_FLAG_BOUNDED) ? 1 : 0;
   h->fk.field_mode = p.field_mode;
   h->fk.sub = p.ion_subcycle;
   h->fk.diag_every = 0;  // the initial solve takes no diagnostic sample
@@ -906,6 +921,9 @@ int pic_kernel_times(pic_handle *h, double *ms, int64_t *launches) {
 int pic_init_batch(const pic_params *params, int n, pic_handle **out) {
   if (!out || !params || n < 1 || n > 4096) return set_err(nullptr, PIC_EINVAL, "bad arguments");
   *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (params[i].flags & PIC_FLAG_BOUNDED)
+      return set_err(nullptr, PIC_EINVAL, "bounded columns run alone (column %d)", i);
   std::vector<pic_params> resolved;
   for (int i = 0; i < n; ++i)
     if (params[i].drive == PIC_DRIVE_RI) {
@@ -1002,6 +1020,11 @@ int pic_get_stats(pic_handle *h, pic_stats *out) {
   out->overflow_e = (int64_t)c.overflow[0]; out->overflow_i = (int64_t)c.overflow[1];
   out->E0 = c.E0;
   out->n_diag = c.n_diag;
+  for (int q = 0; q < 2; ++q) {
+    out->absorbed_e[q] = (int64_t)c.absorbed[0][q];
+    out->absorbed_i[q] = (int64_t)c.absorbed[1][q];
+  }
+  out->emitted = (int64_t)c.emitted;
   return 0;
 }
 
@@ -1042,9 +1065,9 @@ int pic_get_state(pic_handle *h, pic_state *o) {
       }
     }
   }
-  if (o->E) CU(h, cudaMemcpy(o->E, h->E, (size_t)h->N * 8, cudaMemcpyDeviceToHost));
-  if (o->Q_e) CU(h, cudaMemcpy(o->Q_e, h->sp[0].Q, (size_t)h->N * 8, cudaMemcpyDeviceToHost));
-  if (o->Q_i) CU(h, cudaMemcpy(o->Q_i, h->sp[1].Q, (size_t)h->N * 8, cudaMemcpyDeviceToHost));
+  if (o->E) CU(h, cudaMemcpy(o->E, h->E, (size_t)h->Nn * 8, cudaMemcpyDeviceToHost));
+  if (o->Q_e) CU(h, cudaMemcpy(o->Q_e, h->sp[0].Q, (size_t)h->Nn * 8, cudaMemcpyDeviceToHost));
+  if (o->Q_i) CU(h, cudaMemcpy(o->Q_i, h->sp[1].Q, (size_t)h->Nn * 8, cudaMemcpyDeviceToHost));
   return 0;
 }
 
@@ -1105,6 +1128,7 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
   pic::Ctl c;
   CU(h, cudaMemcpy(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost));
   c.n[0] = in->n_e; c.n[1] = in->n_i; c.step = in->step; c.next_id = in->next_id; c.E0 = in->E0;
+  c.emit_acc = 0.0;
   c.status = 0; c.n_birth = 0; c.n_dead[0] = c.n_dead[1] = 0;
   c.sumv[0] = c.sumv[1] = 0;
   CU(h, cudaMemcpy(h->ctl, &c, sizeof c, cudaMemcpyHostToDevice));
@@ -1114,28 +1138,29 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
   }
   h->latched = 0;
   h->host_step = in->step;
-  CU(h, cudaMemset(h->sp[0].Q, 0, (size_t)h->N * 8));
+  CU(h, cudaMemset(h->sp[0].Q, 0, (size_t)h->Nn * 8));
   if (h->mixed) pic::launch_deposit<float>(h->kf, h->sp[0], h->ctl, 0, h->stream);
   else pic::launch_deposit<double>(h->kd, h->sp[0], h->ctl, 0, h->stream);
   if (in->Q_i) {
-    CU(h, cudaMemcpyAsync(h->sp[1].Q, in->Q_i, (size_t)h->N * 8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->sp[1].Q, in->Q_i, (size_t)h->Nn * 8, cudaMemcpyHostToDevice, h->stream));
   } else {
-    CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->N * 8, h->stream));
+    CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->Nn * 8, h->stream));
     if (h->mixed) pic::launch_deposit<float>(h->kf, h->sp[1], h->ctl, 1, h->stream);
     else pic::launch_deposit<double>(h->kd, h->sp[1], h->ctl, 1, h->stream);
   }
   if (in->E) {
-    CU(h, cudaMemcpyAsync(h->E, in->E, (size_t)h->N * 8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->E, in->E, (size_t)h->Nn * 8, cudaMemcpyHostToDevice, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
+    const bool bounded = h->Nn > h->N;   // the gather copy's node N: the anode node, or node 0 again
     if (h->mixed) {
       std::vector<float> f((size_t)h->N + 1);
       for (int j = 0; j < h->N; ++j) f[j] = (float)in->E[j];
-      f[h->N] = f[0];
+      f[h->N] = bounded ? (float)in->E[h->N] : f[0];
       CU(h, cudaMemcpy(h->Ef, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
     } else {
       std::vector<double> f((size_t)h->N + 1);
       for (int j = 0; j < h->N; ++j) f[j] = in->E[j];
-      f[h->N] = f[0];
+      f[h->N] = bounded ? in->E[h->N] : f[0];
       CU(h, cudaMemcpy(h->Ef, f.data(), f.size() * 8, cudaMemcpyHostToDevice));
     }
   } else {
@@ -1199,16 +1224,17 @@ int pic_eepf_get(pic_handle *h, uint64_t *counts, int64_t *n_samples, int32_t re
 
 int pic_moments(pic_handle *h, pic_moments_out *o) {
   if (!h || !o) return set_err(h, PIC_EINVAL, "bad arguments");
-  const int N = h->N;
-  std::vector<double> acc((size_t)N * 8);
-  std::vector<unsigned long long> iz((size_t)N);
+  const int N = h->Nn;                       // nodes
+  const size_t ms = (size_t)h->N + 1;        // stride of the device moment arrays
+  std::vector<double> acc(ms * 8);
+  std::vector<unsigned long long> iz(ms);
   pic::Ctl c;
   CU(h, cudaMemcpyAsync(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaMemcpyAsync(acc.data(), h->mom, acc.size() * 8, cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaMemcpyAsync(iz.data(), h->mom_iz, iz.size() * 8, cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
-  const double *ge = acc.data(), *ee = ge + N, *he = ge + 2 * N, *gi = ge + 3 * N, *ne = ge + 4 * N, *ni = ge + 5 * N,
-               *E = ge + 6 * N, *phi = ge + 7 * N;
+  const double *ge = acc.data(), *ee = ge + ms, *he = ge + 2 * ms, *gi = ge + 3 * ms, *ne = ge + 4 * ms,
+               *ni = ge + 5 * ms, *E = ge + 6 * ms, *phi = ge + 7 * ms;
   const double ns = c.m_samples > 0 ? (double)c.m_samples : 1.0;
   const double dens = h->w / h->dx;
   const double tsteps = (double)(c.m_steps > 0 ? c.m_steps : 1) * h->p.dt_s;
@@ -1226,8 +1252,8 @@ int pic_moments(pic_handle *h, pic_moments_out *o) {
     if (o->phi) o->phi[j] = phi[j] / ns;
   }
   if (o->reset) {
-    CU(h, cudaMemsetAsync(h->mom, 0, (size_t)N * 8 * 8, h->stream));
-    CU(h, cudaMemsetAsync(h->mom_iz, 0, (size_t)N * 8, h->stream));
+    CU(h, cudaMemsetAsync(h->mom, 0, ms * 8 * 8, h->stream));
+    CU(h, cudaMemsetAsync(h->mom_iz, 0, ms * 8, h->stream));
     long long z[3] = {0, 0, 0};  // m_samples, m_steps (n_diag kept)
     CU(h, cudaMemcpyAsync(&h->ctl->m_samples, &z[0], 8, cudaMemcpyHostToDevice, h->stream));
     CU(h, cudaMemcpyAsync(&h->ctl->m_steps, &z[1], 8, cudaMemcpyHostToDevice, h->stream));

@@ -23,7 +23,7 @@ constexpr unsigned kStDeadOverflow = 8u;
 constexpr unsigned kStVictim = 16u;
 
 // random-number streams (counter word 3 = stream<<28 | column<<16 | block)
-enum Stream : uint32_t { kStE = 0, kStI = 1, kStInitE = 2, kStInitI = 3, kStVicE = 4, kStVicI = 5 };
+enum Stream : uint32_t { kStE = 0, kStI = 1, kStInitE = 2, kStInitI = 3, kStVicE = 4, kStVicI = 5, kStEmit = 6 };
 
 // FP64 particle record (offset in cell, velocity); MIXED uses float4 with the same order
 struct alignas(32) D4 { double off, vx, vy, vz; };
@@ -46,6 +46,9 @@ struct Ctl {
   unsigned long long births, losses[2], overflow[2];
   long long n_diag, m_samples, m_steps;
   long long sumv[2];       // circuit drive: sum of round(256 vx), electrons of this step, ions of their last push
+  unsigned long long absorbed[2][2];   // bounded column: particles taken by [species][cathode, anode]
+  unsigned long long emitted;          // bounded column: electrons emitted by the cathode
+  double emit_acc;                     // bounded column: fraction of a macro-electron carried to the next step
 };
 
 struct SpeciesDev {
@@ -77,6 +80,9 @@ template <class R> struct StepK {
   uint32_t column;
   uint64_t seed;
   uint32_t rk[10][2];             // Philox round keys of seed: key + r (0x9E3779B9, 0xBB67AE85)
+  int bounded, Nw;                // bounded column (Sec. V); nodes of the charge arrays (N, or N + 1)
+  double emit_per_step;           // bounded column: J_emit dt / (e w) macro-electrons per step
+  R sig_emit, emit_dtdx;          // (e T_emit / m)^(1/2); dt / dx
   R V_e, em, sig_n;               // 2e/m, 2m/M, sqrt(kT_g/M)
   const float *gauss;             // kGaussN+1 entries
   SpecK<R> sp[2];
@@ -114,6 +120,7 @@ struct FieldScan {
 
 struct FieldK {
   int N, field_mode, sub, diag_every;
+  int bounded, pad_;  // bounded column (Sec. V): Dirichlet field, node arrays of N + 1
   int smem;           // node arrays staged in shared memory (N <= kFieldSmemMax)
   int seg;            // nodes per thread segment: ceil(N / kFieldThreads)
   int circuit;        // E0 = (U - R_ext J) / L after every step (Sec. V)

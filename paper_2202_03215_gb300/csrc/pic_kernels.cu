@@ -47,6 +47,7 @@ template <class R> __device__ __forceinline__ R rec_get_off(const void *base, lo
 // signed fixed-point deposit straight to global memory (births, removals, init)
 template <class R>
 __device__ __forceinline__ void dep_global(unsigned long long *Q, int N, int32_t cell, R off, bool add) {
+  // N: nodes of Q (node N wraps to 0 in a periodic column; a bounded column passes N + 1)
   const unsigned long long k = wfix(off);
   unsigned long long a = (1ull << 32) - k, b = k;
   if (!add) { a = 0ull - a; b = 0ull - b; }
@@ -145,10 +146,10 @@ __device__ __forceinline__ long long vfix(double v) { return __double2ll_rn(v * 
 
 // diagnostic moments of one particle (FP64, cloud-in-cell weights)
 template <class R, int SP>
-__device__ __forceinline__ void add_moments(const SpecK<R> &sp, const Moments &m, int N, int32_t cell, R off, R vx,
-                                            R vy, R vz) {
+__device__ __forceinline__ void add_moments(const SpecK<R> &sp, const Moments &m, int N, int Nw, int32_t cell, R off,
+                                            R vx, R vy, R vz) {
   const unsigned long long kk = wfix(off);
-  const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+  const int c1 = (cell + 1 == Nw) ? 0 : cell + 1;
   const double w1 = (double)kk * (1.0 / 4294967296.0), w0 = 1.0 - w1;
   const double vxd = (double)vx;
   if constexpr (SP == 0) {
@@ -237,7 +238,7 @@ __device__ __forceinline__ int collide(const StepK<R> &k, const SpecK<R> &sp, Ct
           atomicAdd(&ctl->births, 1ull);
         }
         const unsigned long long kk = wfix(off);
-        const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+        const int c1 = (cell + 1 == k.Nw) ? 0 : cell + 1;
         atomicAdd(m.iz + cell, (1ull << 32) - kk);
         atomicAdd(m.iz + c1, kk);
       }
@@ -298,8 +299,8 @@ struct CellBins {
 };
 
 // n particles of cell `cell` with summed weight sk
-__device__ __forceinline__ void cell_add(const CellBins &b, int N, int32_t cell, unsigned n, unsigned long long sk,
-                                         unsigned long long *Q) {
+__device__ __forceinline__ void cell_add(const CellBins &b, int N, int Nw, int32_t cell, unsigned n,
+                                         unsigned long long sk, unsigned long long *Q) {
   int li = cell;
   if (b.W < N) {
     li = cell - b.c0;
@@ -309,7 +310,7 @@ __device__ __forceinline__ void cell_add(const CellBins &b, int N, int32_t cell,
     atomicAdd(b.cnt + li, n);
     add64(b.klo + li, b.khi + li, sk);
   } else {
-    const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+    const int c1 = (cell + 1 == Nw) ? 0 : cell + 1;
     atomicAdd(Q + cell, ((unsigned long long)n << 32) - sk);
     atomicAdd(Q + c1, sk);
   }
@@ -319,9 +320,9 @@ __device__ __forceinline__ void cell_add(const CellBins &b, int N, int32_t cell,
 // nothing).  Lanes of a warp that share a cell are serialised by the shared-memory atomics;
 // that costs less than summing runs of equal cells with warp shuffles first, even right after
 // a sort, when most lanes of a warp share a cell.
-__device__ __forceinline__ void deposit(bool in, int32_t cell, unsigned long long kk, int N, const CellBins &b,
+__device__ __forceinline__ void deposit(bool in, int32_t cell, unsigned long long kk, int N, int Nw, const CellBins &b,
                                         unsigned long long *Q) {
-  if (in) cell_add(b, N, cell, 1u, kk, Q);
+  if (in) cell_add(b, N, Nw, cell, 1u, kk, Q);
 }
 
 // one CTA's share (cta of ncta) of the particle step of one column; PK: k is a launch
@@ -331,7 +332,8 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
                                           BirthBuf<R> bb, Moments m, int W, int smemE, int cta, int ncta,
                                           unsigned char *smem) {
   __shared__ unsigned int s_cnt[kMaxProc + 1];
-  const int N = k.N;
+  const int N = k.N, Nw = k.Nw;
+  const bool bounded = k.bounded != 0;
   const SpecK<R> &sp = k.sp[SP];
   const size_t eb = smemE ? ((((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15) : 0;
   R *sE = reinterpret_cast<R *>(smem);
@@ -388,7 +390,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
       sel = collide<R, SP>(k, sp, ctl, bb, m, Qd.id[i], step, c3, qp, qcell, qoff_, Qd.u1[i], qx, qy, qz, ovf);
       rec_store<R>(s.rec, qp, qoff_, qx, qy, qz);
       if (record) s.code[qp] = sel >= 0 ? sp.xs[sel] : -1;
-      if (diag) add_moments<R, SP>(sp, m, N, qcell, qoff_, qx, qy, qz);
+      if (diag) add_moments<R, SP>(sp, m, N, Nw, qcell, qoff_, qx, qy, qz);
       if (circuit) vsum += vfix(qx);
     }
     for (int q = 0; q < sp.np; ++q) {
@@ -454,10 +456,11 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     }
     if (valid) {
       const R Ep = gather(E, cell, off);
-      push<R>(N, sp.a, sp.d, Ep, cell, off, vx);
+      const int side = push<R>(N, bounded, sp.a, sp.d, Ep, cell, off, vx);
       const uint4 ctr = make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, c3);
       const uint4 w0 = PK ? philox10_rk(ctr, k.rk) : philox10(ctr, key);
-      dead = radial && (w0.z < sp.Pw);
+      dead = side != 0 || (radial && (w0.z < sp.Pw));
+      if (side != 0) atomicAdd(&ctl->absorbed[SP][side > 0 ? 1 : 0], 1ull);
       if (!dead) {
         u1 = u_dec<R>(w0.y);
         if constexpr (SP == 0) {
@@ -475,7 +478,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
       if (!cand) {
         rec_store<R>(s.rec, p, off, vx, vy, vz);
         if (record) s.code[p] = dead ? -2 : -1;
-        if (!dead && diag) add_moments<R, SP>(sp, m, N, cell, off, vx, vy, vz);
+        if (!dead && diag) add_moments<R, SP>(sp, m, N, Nw, cell, off, vx, vy, vz);
         if (!dead && circuit) vsum += vfix(vx);
       }
       if (dead) {
@@ -497,7 +500,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     }
     wq += __popc(bal);
     // charge deposit into the window bins
-    deposit(valid && !dead, cell, wfix(off), N, bins, s.Q);
+    deposit(valid && !dead, cell, wfix(off), N, Nw, bins, s.Q);
     __syncwarp();
     if (wq >= 32) {
       flush(32);
@@ -527,7 +530,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     if (nq || sk) {
       int cell = j;
       if (W < N) { cell = c0 + j; if (cell >= N) cell -= N; }
-      const int c1 = (cell + 1 == N) ? 0 : cell + 1;
+      const int c1 = (cell + 1 == Nw) ? 0 : cell + 1;
       atomicAdd(s.Q + cell, ((unsigned long long)nq << 32) - sk);
       atomicAdd(s.Q + c1, sk);
     }
@@ -721,7 +724,7 @@ __device__ void fill_compact(const StepK<R> &k, SpeciesDev s, Ctl *ctl, int SP, 
   for (int t = threadIdx.x; t < m; t += blockDim.x) {
     const uint32_t b = sc.order[t];
     write_newborn<R>(s, (long long)keys[t], bb.cell[b], bb.off[b], bv[b], bv[kStageCap + b], bv[2 * kStageCap + b],
-                     (uint64_t)next_id + 2ull * (uint64_t)t + (uint64_t)SP, N);
+                     (uint64_t)next_id + 2ull * (uint64_t)t + (uint64_t)SP, k.Nw);
   }
   long long Nnew = Nold;
   if (nb > nd) {
@@ -733,7 +736,7 @@ __device__ void fill_compact(const StepK<R> &k, SpeciesDev s, Ctl *ctl, int SP, 
       for (int t = m + threadIdx.x; t < nb; t += blockDim.x) {
         const uint32_t b = sc.order[t];
         write_newborn<R>(s, Nold + (t - m), bb.cell[b], bb.off[b], bv[b], bv[kStageCap + b], bv[2 * kStageCap + b],
-                         (uint64_t)next_id + 2ull * (uint64_t)t + (uint64_t)SP, N);
+                         (uint64_t)next_id + 2ull * (uint64_t)t + (uint64_t)SP, k.Nw);
       }
     }
   } else if (nd > nb) {
@@ -840,17 +843,19 @@ __device__ __forceinline__ void births_body(const StepK<R> &k, SpeciesDev e, Spe
         for (int t = threadIdx.x; t < nb; t += blockDim.x) {
           const uint32_t b = sc.order[t];
           const long long ve = sc.vic[t], vi = sc.vic[vstride + t];
-          dep_global<R>(e.Q, N, e.cell[ve], rec_get_off<R>(e.rec, ve), false);
+          dep_global<R>(e.Q, k.Nw, e.cell[ve], rec_get_off<R>(e.rec, ve), false);
           write_newborn<R>(e, ve, bb.cell[b], bb.off[b], bb.ve[b], bb.ve[kStageCap + b], bb.ve[2 * kStageCap + b],
-                           (uint64_t)next_id + 2ull * (uint64_t)t, N);
-          dep_global<R>(ion.Q, N, ion.cell[vi], rec_get_off<R>(ion.rec, vi), false);
+                           (uint64_t)next_id + 2ull * (uint64_t)t, k.Nw);
+          dep_global<R>(ion.Q, k.Nw, ion.cell[vi], rec_get_off<R>(ion.rec, vi), false);
           write_newborn<R>(ion, vi, bb.cell[b], bb.off[b], bb.vi[b], bb.vi[kStageCap + b], bb.vi[2 * kStageCap + b],
-                           (uint64_t)next_id + 2ull * (uint64_t)t + 1ull, N);
+                           (uint64_t)next_id + 2ull * (uint64_t)t + 1ull, k.Nw);
         }
         if (threadIdx.x == 0) { ctl->losses[0] += nb; ctl->losses[1] += nb; }
       }
     }
-  } else if (k.loss_mode == PIC_LOSS_RADIAL) {
+  } else if (k.loss_mode == PIC_LOSS_RADIAL || k.bounded) {
+    // removed particles (radial losses; in a bounded column also those the electrodes took)
+    // leave holes that the births fill, the rest compacted
     fill_compact<R>(k, e, ctl, 0, bb, sc, nb, nde, next_id, keys, s_scan);
     __syncthreads();
     fill_compact<R>(k, ion, ctl, 1, bb, sc, nb, ndi, next_id, keys, s_scan);
@@ -863,9 +868,9 @@ __device__ __forceinline__ void births_body(const StepK<R> &k, SpeciesDev e, Spe
       for (int t = threadIdx.x; t < nb; t += blockDim.x) {
         const uint32_t b = sc.order[t];
         write_newborn<R>(e, ne + t, bb.cell[b], bb.off[b], bb.ve[b], bb.ve[kStageCap + b], bb.ve[2 * kStageCap + b],
-                         (uint64_t)next_id + 2ull * (uint64_t)t, N);
+                         (uint64_t)next_id + 2ull * (uint64_t)t, k.Nw);
         write_newborn<R>(ion, ni + t, bb.cell[b], bb.off[b], bb.vi[b], bb.vi[kStageCap + b], bb.vi[2 * kStageCap + b],
-                         (uint64_t)next_id + 2ull * (uint64_t)t + 1ull, N);
+                         (uint64_t)next_id + 2ull * (uint64_t)t + 1ull, k.Nw);
       }
       __syncthreads();
       if (threadIdx.x == 0) { ctl->n[0] = ne + nb; ctl->n[1] = ni + nb; }
@@ -880,6 +885,46 @@ __device__ __forceinline__ void births_body(const StepK<R> &k, SpeciesDev e, Spe
     ctl->n_birth = 0;
     ctl->n_dead[0] = 0;
     ctl->n_dead[1] = 0;
+  }
+  if (k.bounded && k.emit_per_step > 0.0) {
+    // Sec. V: the cathode emits J_emit dt / (e w) macro-electrons per step (the fraction carried
+    // over).  Emitted electron q of step s draws (Philox counter q, s, emission stream) a
+    // half-Maxwellian velocity at T_emit, (s |g0|, s g1, s g2), and starts at x = u v_x dt.
+    __shared__ long long s_em[3];   // count, first slot, first id
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double acc = ctl->emit_acc + k.emit_per_step;
+      long long ne = (long long)floor(acc);
+      acc -= (double)ne;
+      const long long n0 = ctl->n[0];
+      if (n0 + ne > e.cap) {
+        atomicOr(&ctl->status, kStCapacity);
+        ne = 0;
+      }
+      ctl->emit_acc = acc;
+      s_em[0] = ne;
+      s_em[1] = n0;
+      s_em[2] = ctl->next_id;
+      ctl->n[0] = n0 + ne;
+      ctl->next_id += ne;
+      ctl->emitted += (unsigned long long)ne;
+    }
+    __syncthreads();
+    const long long ne = s_em[0], n0 = s_em[1], id0 = s_em[2];
+    const uint32_t c3 = ((uint32_t)kStEmit << 28) | (k.column << 16);
+    for (long long q = threadIdx.x; q < ne; q += blockDim.x) {
+      UStream<R> us(key, (uint64_t)q, step, c3);
+      const R g0 = gauss<R>(k.gauss, us.next());
+      const R g1 = gauss<R>(k.gauss, us.next());
+      const R g2 = gauss<R>(k.gauss, us.next());
+      const R u = us.next();
+      const R vx = k.sig_emit * (g0 < (R)0 ? -g0 : g0), vy = k.sig_emit * g1, vz = k.sig_emit * g2;
+      const R x = u * vx * k.emit_dtdx;
+      int32_t cell = (int32_t)x;
+      R off = x - (R)cell;
+      if (cell >= N) { cell = N - 1; off = (R)0; }
+      write_newborn<R>(e, n0 + q, cell, off, vx, vy, vz, (uint64_t)(id0 + q), k.Nw);
+    }
   }
 }
 
@@ -1036,7 +1081,7 @@ __device__ __forceinline__ void field_reduce_body(const FieldK &f, const unsigne
   const int j = blk * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __int128 r = 0, u = 0;
-  if (j < N) {
+  if (j < N && !(f.bounded && j == 0)) {   // bounded column: node 0 is the cathode (surface charge)
     const long long d = (long long)__ldcg(Qi + j) - (long long)__ldcg(Qe + j);
     r = (__int128)d;
     u = mul_u32(r, (uint32_t)(N - j));
@@ -1072,6 +1117,7 @@ __device__ __forceinline__ void field_reduce_body(const FieldK &f, const unsigne
   __int128 T, U;
   const __int128 run = block_excl_scan_i128(Rb, sh, T);    // sum of D before this thread's block
   (void)block_excl_scan_i128(Ub, sh, U);
+  if (f.bounded) T = 0;   // between electrodes: no uniform background, the electrodes hold the image charge
   if ((int)threadIdx.x < nblk) fs->Sp0[threadIdx.x] = mul_u32(run, Nu) - (__int128)(threadIdx.x * blockDim.x) * T;
   if (threadIdx.x == 0) {
     const __int128 half = (__int128)((unsigned long long)N * (unsigned long long)(N + 1) / 2ull);
@@ -1122,7 +1168,7 @@ __device__ __forceinline__ void field_eval_body(const FieldK &f, const unsigned 
     const uint32_t Nu = (uint32_t)N;
     const __int128 T = fs->T, M = fs->M;
     __int128 v = 0;
-    if (j < N) v = mul_u32((__int128)((long long)Qi[j] - (long long)Qe[j]), Nu) - T;
+    if (j < N && !(f.bounded && j == 0)) v = mul_u32((__int128)((long long)Qi[j] - (long long)Qe[j]), Nu) - T;
     __int128 tot;
     const __int128 ex = block_excl_scan_i128(v, sh, tot);
     const __int128 Sp0 = fs->Sp0[blk];
@@ -1137,14 +1183,24 @@ __device__ __forceinline__ void field_eval_body(const FieldK &f, const unsigned 
     double e;
     if (poisson) {
       Eh[j] = eh;
-      e = 0.5 * (sEh[threadIdx.x] + eh) + (-E0);
+      // bounded column: the cathode node takes the field of the first half cell
+      e = (f.bounded && j == 0) ? eh + (-E0) : 0.5 * (sEh[threadIdx.x] + eh) + (-E0);
     } else {
       Eh[j] = 0.0;
       e = -E0;
     }
     E[j] = e;
     Ef[j] = (R)e;
-    if (j == 0) Ef[N] = (R)e;
+    if (f.bounded) {
+      if (j == N - 1) {   // the anode node: the field of the last half cell
+        const double ea = poisson ? eh + (-E0) : -E0;
+        E[N] = ea;
+        Ef[N] = (R)ea;
+        if (!isfinite(ea)) bad = true;
+      }
+    } else if (j == 0) {
+      Ef[N] = (R)e;
+    }
     if (!isfinite(e)) bad = true;
   }
   if (bad) atomicOr(&ctl->status, kStNonFinite);
@@ -1190,11 +1246,13 @@ __device__ __forceinline__ void field_diag_body(const FieldK &f, const unsigned 
     m.phi[j] += -f.dx * run;
     run += Eh[j];
   }
-  for (int j = t; j < N; j += blockDim.x) {
+  const int nodes = N + (f.bounded ? 1 : 0);   // a bounded column's anode node N
+  for (int j = t; j < nodes; j += blockDim.x) {
     m.ne[j] += (double)(long long)Qe[j] * (1.0 / 4294967296.0);
     m.ni[j] += (double)(long long)Qi[j] * (1.0 / 4294967296.0);
     m.E[j] += E[j];
   }
+  if (f.bounded && t == 0) m.phi[N] += -f.dx * tot;
   __syncthreads();
   if (t == 0) {
     ctl->m_samples += 1;
@@ -1296,7 +1354,7 @@ __global__ void k_deposit(SpeciesDev s, const Ctl *ctl, int species, int N) {
 
 template <class R>
 void launch_deposit(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, int species, cudaStream_t st) {
-  k_deposit<R><<<152 * 8, 256, 0, st>>>(s, ctl, species, k.N);
+  k_deposit<R><<<152 * 8, 256, 0, st>>>(s, ctl, species, k.Nw);
 }
 
 // leapfrog start: v^{-1/2} = v^0 - (q dt / 2m) E^0(x^0)
