@@ -179,6 +179,39 @@ def bf16_peak():
 MLP_FWD_FLOP = 2 * (15 * 128 + 128 * 128 + 128 * 3)   # 37,376 per sample
 
 
+def bounded_leg(pb, w, torch, steps: int = 1000, warmup: int = 200):
+    """The bounded column of Sec. V (Fig. 18 conditions): neon 1 Torr, cathode-anode gap 15 cm,
+    1000 cells, 5000 particles per cell and species, 270 V through 10 Ohm m^2, cathode emission
+    10 A/m^2, loss frequency 1e6 s^-1."""
+    p = w.Params(gas_mass_amu=w.AMU_NE, L_m=0.15, n_cells=1000, xsec=w.neon_xsecs(), dt_s=4e-11,
+                 n_e0=5_000_000, n_i0=5_000_000, n0_m3=1e15, Te0_eV=2.0, drive=w.DRIVE_CIRCUIT, U_src=270.0,
+                 E0_Vpm=1400.0,
+                 R_ext_ohm_m2=10.0, loss_mode=w.LOSS_RADIAL, nu_w=1e6, flags=w.FLAG_BOUNDED, J_emit_Am2=10.0,
+                 T_emit_eV=0.2, precision=w.MIXED, sort_every=250, eps_max_e_eV=200.0, capacity=8_000_000)
+    col = pb.Column(p)
+    col.step(warmup)
+    st0 = col.stats()
+    ext = torch.cuda.ExternalStream(col.stream())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ext)
+    col.step(steps)
+    e1.record(ext)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = col.stats()
+    col.close()
+    units = pushed_steps(st0["step"], steps, (st0["n_e"] + st["n_e"]) // 2, (st0["n_i"] + st["n_i"]) // 2,
+                         p.ion_subcycle)
+    return {"workload": "bounded neon column, 1 Torr, gap 0.15 m, 1000 cells, 5e6 + 5e6 particles, U = 270 V, "
+                        "R = 10 Ohm m^2, J_emit = 10 A/m^2, nu_w = 1e6 s^-1, dt = 4e-11 s, MIXED",
+            "steps": steps, "ms_per_step": ms / steps, "value": units / (ms / 1e3), "unit": UNIT,
+            "n_e": st["n_e"], "n_i": st["n_i"], "V_D": st["E0"] * p.L_m,
+            "absorbed_e": [a - b for a, b in zip(st["absorbed_e"], st0["absorbed_e"])],
+            "absorbed_i": [a - b for a, b in zip(st["absorbed_i"], st0["absorbed_i"])],
+            "emitted": st["emitted"] - st0["emitted"]}
+
+
 def eepf_leg(pb, w, torch, n: int = 20_000_000, steps: int = 200, diag_every: int = 10):
     """Cost of the EEPF histogram (Sec. III.C) on the throughput column: the same diagnostic steps
     (moments every diag_every steps) with and without the 64 x 200 energy histogram."""
@@ -332,6 +365,7 @@ def main():
     ap.add_argument("--no-screen", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-eepf", action="store_true")
+    ap.add_argument("--no-bounded", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -456,6 +490,9 @@ def main():
     eepf = None
     if rank == 0 and world == 1 and not args.no_eepf:
         eepf = eepf_leg(pb, w, torch, n=args.n)
+    bnd = None
+    if rank == 0 and world == 1 and not args.no_bounded:
+        bnd = bounded_leg(pb, w, torch)
     if rank == 0 and world == 1 and not args.no_train:
         train = closure_training_leg(pb, torch)
 
@@ -468,7 +505,7 @@ def main():
                            "l2": "inputs larger than L2 (state 1.1 GB)", "parallelism": f"replicas x{world}",
                            "pushed_particle_steps": units},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_vs_serial": batch,
-                "fluid_screen": screen, "closure_training": train, "eepf": eepf,
+                "fluid_screen": screen, "closure_training": train, "eepf": eepf, "bounded_column": bnd,
                 "gpu_launches": launches, "ms_per_step_instrumented": ms_inst / args.steps,
                 "kernel_ms": {k: v[0] for k, v in kt.items()}, "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -57,9 +57,11 @@ extern "C" {
 /* how the applied field E0 is set */
 #define PIC_DRIVE_E0 0       /* E0 = E0_Vpm (the paper's control parameter) */
 #define PIC_DRIVE_V 1        /* E0 = V_applied / L */
-#define PIC_DRIVE_CIRCUIT 2  /* Sec. V: external circuit, E0 = (U_src - R_ext J) / L after every step,
-                                J = e w (sum v_x,ions - sum v_x,electrons) / L over the pushed particles
-                                (ions at their last push; velocities summed as round(256 v_x), exact) */
+#define PIC_DRIVE_CIRCUIT 2  /* Sec. V: external circuit U_src = R_ext J + E0 L: E0 = (U_src - R_ext J) / L
+                                after every step, J = e w (sum v_x,electrons - sum v_x,ions) / L the
+                                discharge current density over the pushed particles (positive when the
+                                electrons drift against the applied field -E0; ions at their last push;
+                                velocities summed as round(256 v_x), exact) */
 #define PIC_DRIVE_RI 3       /* tube radius R_m and current I_A (eq. 2): E0 and n0 from pic_drive_ri at
                                 pic_init, then run as PIC_DRIVE_E0 (E0_Vpm and n0_m3 are ignored) */
 

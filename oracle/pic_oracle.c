@@ -871,11 +871,13 @@ static int step_once(ora_t *h) {
   h->step++;
   h->m_steps++;
   /* Sec. V: an external circuit with a resistor sets the applied field,
-   * E0 = (U - R_ext J) / L, J = e w (sum v_i - sum v_e) / L over the pushed
-   * particles (ions at their last push) -- build reading of "adding an
-   * external circuit with a resistor to adjust the applied field E0". */
+   * U = R_ext J + V_D with V_D = E0 L, so E0 = (U - R_ext J) / L, where J is the
+   * discharge current density e w (sum v_e - sum v_i) / L over the pushed particles
+   * (ions at their last push): positive when the electrons drift against the
+   * applied field -E0 -- build reading of "adding an external circuit with a
+   * resistor to adjust the applied field E0". */
   if (h->p.drive == ORA_DRIVE_CIRCUIT) {
-    double J = h->Cj * (double)(h->sumv[1] - h->sumv[0]);
+    double J = h->Cj * (double)(h->sumv[0] - h->sumv[1]);
     h->E0 = (h->p.U_src - h->p.R_ext_ohm_m2 * J) / h->p.L_m;
   }
   solve_field(h);

@@ -327,13 +327,13 @@ __device__ __forceinline__ void deposit(bool in, int32_t cell, unsigned long lon
 
 // one CTA's share (cta of ncta) of the particle step of one column; PK: k is a launch
 // parameter (the Philox round keys are read from it as constants)
-template <class R, int SP, bool PK>
+template <class R, int SP, bool PK, bool BD>
 __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef,
                                           BirthBuf<R> bb, Moments m, int W, int smemE, int cta, int ncta,
                                           unsigned char *smem) {
   __shared__ unsigned int s_cnt[kMaxProc + 1];
-  const int N = k.N, Nw = k.Nw;
-  const bool bounded = k.bounded != 0;
+  const int N = k.N, Nw = BD ? k.N + 1 : k.N;
+  constexpr bool bounded = BD;   // a bounded column (Sec. V), a separate instantiation
   const SpecK<R> &sp = k.sp[SP];
   const size_t eb = smemE ? ((((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15) : 0;
   R *sE = reinterpret_cast<R *>(smem);
@@ -540,12 +540,12 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
   if (threadIdx.x == 0 && s_cnt[kMaxProc]) atomicAdd(&ctl->overflow[SP], (unsigned long long)s_cnt[kMaxProc]);
 }
 
-template <class R, int SP>
+template <class R, int SP, bool BD>
 __global__ void __launch_bounds__(kStepThreads, 1)
 k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef, BirthBuf<R> bb,
        Moments m, int W, int smemE) {
   extern __shared__ __align__(16) unsigned char smem[];
-  push_body<R, SP, true>(k, s, ctl, Ef, bb, m, W, smemE, blockIdx.x, gridDim.x, smem);
+  push_body<R, SP, true, BD>(k, s, ctl, Ef, bb, m, W, smemE, blockIdx.x, gridDim.x, smem);
 }
 
 // batched columns: CTA b runs share sched[b].y of sched[b].z of column sched[b].x
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_push_batch(const ColDev<R> 
     for (int q = threadIdx.x; q < (int)(sizeof(StepK<R>) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
   }
   __syncthreads();
-  push_body<R, SP, false>(sk, cd->sp[SP], cd->ctl, reinterpret_cast<const R *>(cd->Ef), cd->bb, cd->m, cd->W, cd->smemE,
+  push_body<R, SP, false, false>(sk, cd->sp[SP], cd->ctl, reinterpret_cast<const R *>(cd->Ef), cd->bb, cd->m, cd->W, cd->smemE,
                    sc.y, sc.z, smem);
 }
 
@@ -588,12 +588,14 @@ void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBu
                  int nsm, cudaStream_t st) {
   int W = 0, smemE = 0;
   const size_t bytes = push_layout<R>(k.N, W, smemE);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    kern<<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
+  };
   if (species == 0) {
-    cudaFuncSetAttribute(k_push<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_push<R, 0><<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
+    if (k.bounded) go(k_push<R, 0, true>); else go(k_push<R, 0, false>);
   } else {
-    cudaFuncSetAttribute(k_push<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    k_push<R, 1><<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
+    if (k.bounded) go(k_push<R, 1, true>); else go(k_push<R, 1, false>);
   }
 }
 
@@ -1126,7 +1128,7 @@ __device__ __forceinline__ void field_reduce_body(const FieldK &f, const unsigne
     fs->ticket = 0u;
     if (f.circuit && advance) {
       // Sec. V: the external circuit sets the applied field for the next step
-      const double J = f.Cj * (double)(ctl->sumv[1] - ctl->sumv[0]);
+      const double J = f.Cj * (double)(ctl->sumv[0] - ctl->sumv[1]);   // discharge current density
       ctl->E0 = (f.U - f.Rext * J) / f.L;
     }
   }

@@ -169,18 +169,23 @@ def test_sorting_does_not_change_any_particle():
 
 
 def test_circuit_drive_sets_E0_from_the_current():
-    """Sec. V: the applied field is set by an external circuit, E0 = (U - R J)/L with
-    J = e w (sum v_i - sum v_e)/L; J recomputed here from the particles."""
+    """Sec. V: the applied field is set by an external circuit, U = R J + E0 L, with the
+    discharge current density J = e w (sum v_e - sum v_i)/L (electrons drift against the
+    applied field -E0, so J > 0 and a larger current lowers the field); J recomputed here
+    from the particles."""
     U, Rext = 150.0, 2.0
     p = _small(seed=4, drive=w.DRIVE_CIRCUIT, U_src=U, R_ext_ohm_m2=Rext, E0_Vpm=1000.0,
                loss_mode=w.LOSS_SWARM, ion_subcycle=1)
     o = oracle.Oracle(p)
     wgt = o.derived()["w"]
-    for _ in range(5):
+    Js = []
+    for _ in range(60):
         o.step(1)
         s = o.get_state()
         si = np.round(s["vx_i"] * 256.0).astype(np.int64).sum()
         se = np.round(s["vx_e"] * 256.0).astype(np.int64).sum()
-        J = QE * wgt / (p.L_m * 256.0) * float(si - se)
+        J = QE * wgt / (p.L_m * 256.0) * float(se - si)
         assert s["E0"] == pytest.approx((U - Rext * J) / p.L_m, rel=1e-12, abs=1e-9)
+        Js.append(J)
+    assert np.mean(Js[30:]) > 0          # the electrons' drift against the applied field: J > 0
     assert s["E0"] != 1000.0
