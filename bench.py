@@ -236,8 +236,7 @@ def eepf_leg(pb, w, torch, n: int = 20_000_000, steps: int = 200, diag_every: in
     col.close()
     extra = (out["ms_per_step_eepf"] - out["ms_per_step"]) * diag_every
     return {"particles_per_species": n, "steps": steps, "diag_every": diag_every, "bins": [64, 201],
-            "samples": ns, "counted": int(c.sum()), **out, "ms_per_sample_extra": extra,
-            "binned_per_s": (c.sum() / ns) / (extra / 1e3) if extra > 0 else None}
+            "samples": ns, "counted": int(c.sum()), **out, "ms_per_sample_extra": extra}
 
 
 def fluid_screen_leg(pb, torch, steps: int = 1000, warmup: int = 20, closure_steps: int = 200):
