@@ -173,7 +173,7 @@ __device__ __forceinline__ void add_moments(const SpecK<R> &sp, const Moments &m
 // Collision of one candidate (u0 < P_null already drawn): process choice by
 // u1 nu* against the cumulative collision frequencies, then the scattering.
 // Returns the process index within the species, or -1 for a null collision.
-template <class R, int SP>
+template <class R, int SP, bool BD>
 __device__ __forceinline__ int collide(const StepK<R> &k, const SpecK<R> &sp, Ctl *ctl, const BirthBuf<R> &bb,
                                        const Moments &m, uint64_t id, uint32_t step, uint32_t c3, int32_t p,
                                        int32_t cell, R off, R u1, R &vx, R &vy, R &vz, bool &ovf) {
@@ -238,7 +238,7 @@ __device__ __forceinline__ int collide(const StepK<R> &k, const SpecK<R> &sp, Ct
           atomicAdd(&ctl->births, 1ull);
         }
         const unsigned long long kk = wfix(off);
-        const int c1 = (cell + 1 == k.Nw) ? 0 : cell + 1;
+        const int c1 = (cell + 1 == N + (BD ? 1 : 0)) ? 0 : cell + 1;   // nodes: N, or N + 1 bounded
         atomicAdd(m.iz + cell, (1ull << 32) - kk);
         atomicAdd(m.iz + c1, kk);
       }
@@ -332,7 +332,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
                                           BirthBuf<R> bb, Moments m, int W, int smemE, int cta, int ncta,
                                           unsigned char *smem) {
   __shared__ unsigned int s_cnt[kMaxProc + 1];
-  const int N = k.N, Nw = BD ? k.N + 1 : k.N;
+  const int N = k.N, Nw = N + (BD ? 1 : 0);
   constexpr bool bounded = BD;   // a bounded column (Sec. V), a separate instantiation
   const SpecK<R> &sp = k.sp[SP];
   const size_t eb = smemE ? ((((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15) : 0;
@@ -387,7 +387,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
       const int32_t qp = Qd.slot[i], qcell = Qd.cell[i];
       const R qoff_ = Qd.off[i];
       R qx = Qd.vx[i], qy = Qd.vy[i], qz = Qd.vz[i];
-      sel = collide<R, SP>(k, sp, ctl, bb, m, Qd.id[i], step, c3, qp, qcell, qoff_, Qd.u1[i], qx, qy, qz, ovf);
+      sel = collide<R, SP, BD>(k, sp, ctl, bb, m, Qd.id[i], step, c3, qp, qcell, qoff_, Qd.u1[i], qx, qy, qz, ovf);
       rec_store<R>(s.rec, qp, qoff_, qx, qy, qz);
       if (record) s.code[qp] = sel >= 0 ? sp.xs[sel] : -1;
       if (diag) add_moments<R, SP>(sp, m, N, Nw, qcell, qoff_, qx, qy, qz);
