@@ -1,12 +1,16 @@
 // CUDA kernels of the 1D3V electrostatic PIC-MCC positive-column step
-// (Boeuf, Sec. II), written for sm_103a.
+// (Boeuf, Sec. II; the bounded column of Sec. V), written for sm_103a.
 //
-//   k_push      field gather, leapfrog push, periodic wrap, null-collision MCC,
-//               radial-loss flag, birth staging, cloud-in-cell deposit into
-//               shared-memory 64-bit fixed-point bins (one persistent CTA per SM)
+//   k_push      field gather, leapfrog push, periodic wrap (or absorption at the
+//               electrodes of a bounded column), null-collision MCC, radial-loss
+//               flag, birth staging, cloud-in-cell deposit into shared-memory
+//               64-bit fixed-point bins (one persistent CTA per SM)
 //   k_births    ionization births and the paired random removal (or radial
-//               losses with compaction); one CTA
-//   k_field     periodic Poisson solve by the exact integer route; one CTA
+//               losses and absorbed particles with compaction; cathode emission
+//               of a bounded column); one CTA
+//   k_field_reduce / k_field_eval   Poisson solve by the exact integer route
+//               (periodic, or Dirichlet between two electrodes), blocks of
+//               nodes, the last block to finish forms the totals
 //   k_init / k_deposit / k_halfstep   initial state
 #include <cstdint>
 
