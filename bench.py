@@ -56,9 +56,15 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the particle-step sources with comments and blank space removed (a comment edit
+    does not change the kernel the traffic figure was taken on)."""
+    import re
     h = hashlib.sha256()
     for f in ("pic_kernels.cu", "pic_device.cuh", "pic_internal.cuh"):
-        h.update((ROOT / "paper_2202_03215_gb300" / "csrc" / f).read_bytes())
+        src = (ROOT / "paper_2202_03215_gb300" / "csrc" / f).read_text()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
