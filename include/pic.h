@@ -120,7 +120,7 @@ typedef struct pic_params {
   double I_A, U_src, R_ext_ohm_m2;  /* discharge current (workload label); circuit source voltage (V) and
                                        resistor (Ohm m^2) of PIC_DRIVE_CIRCUIT */
   int32_t n_xsec, pad0;
-  const pic_xsec *xsec;    /* n_xsec processes; at most 8 per species */
+  const pic_xsec *xsec;    /* n_xsec processes; at most 16 per species */
   int32_t n_cells;         /* grid cells = nodes (periodic), 3 <= n_cells <= 65536 */
   int32_t ion_subcycle;    /* ions advance every ion_subcycle steps with dt_i = ion_subcycle dt; 0 = frozen */
   double dt_s;             /* electron time step dt (Sec. II: dt < 0.2/w_pe) */
@@ -166,8 +166,8 @@ typedef struct pic_state {
 /* Counters since pic_init. */
 typedef struct pic_stats {
   int64_t step, n_e, n_i, next_id;
-  int64_t n_coll_e[8];     /* real electron collisions per electron process (in xsec order) */
-  int64_t n_coll_i[8];     /* real ion collisions per ion process */
+  int64_t n_coll_e[16];    /* real electron collisions per electron process (in xsec order) */
+  int64_t n_coll_i[16];    /* real ion collisions per ion process */
   int64_t births;          /* ionization events (pairs created) */
   int64_t losses_e, losses_i;
   int64_t overflow_e, overflow_i;  /* collisions evaluated above the table range */

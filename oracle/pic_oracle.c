@@ -50,7 +50,7 @@ typedef double real;
 
 #define TWO32 4294967296.0
 #define NGAUSS 4096
-#define MAXPROC 8
+#define MAXPROC 16
 
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its published

@@ -69,7 +69,7 @@ typedef struct ora_state {
 
 typedef struct ora_stats {
   int64_t step, n_e, n_i, next_id;
-  int64_t n_coll_e[8], n_coll_i[8];
+  int64_t n_coll_e[16], n_coll_i[16];
   int64_t births, losses_e, losses_i;
   int64_t overflow_e, overflow_i;
   double E0;

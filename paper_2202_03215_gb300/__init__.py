@@ -68,7 +68,7 @@ class State(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("n_e", C.c_int64), ("n_i", C.c_int64), ("next_id", C.c_int64),
-                ("n_coll_e", C.c_int64 * 8), ("n_coll_i", C.c_int64 * 8),
+                ("n_coll_e", C.c_int64 * 16), ("n_coll_i", C.c_int64 * 16),
                 ("births", C.c_int64), ("losses_e", C.c_int64), ("losses_i", C.c_int64),
                 ("overflow_e", C.c_int64), ("overflow_i", C.c_int64),
                 ("E0", C.c_double), ("n_diag", C.c_int64),

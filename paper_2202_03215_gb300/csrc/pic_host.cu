@@ -503,7 +503,7 @@ int validate(const pic_params *p) {
       if (!(xs.energy_eV[i] >= xs.energy_eV[i - 1])) return set_err(nullptr, PIC_EINVAL, "xsec %d not ascending", x);
     (is_e_kind(xs.kind) ? ne : ni)++;
   }
-  if (ne > pic::kMaxProc || ni > pic::kMaxProc) return set_err(nullptr, PIC_EINVAL, "at most 8 processes per species");
+  if (ne > pic::kMaxProc || ni > pic::kMaxProc) return set_err(nullptr, PIC_EINVAL, "at most %d processes per species", pic::kMaxProc);
   if (p->n_e0 > 0 && !(p->n0_m3 > 0) && p->field_mode == PIC_FIELD_POISSON)
     return set_err(nullptr, PIC_EINVAL, "n0 must be > 0");
   if (!(p->eps_max_e_eV > 0) || !(p->eps_max_i_eV > 0)) return set_err(nullptr, PIC_EINVAL, "eps_max must be > 0");

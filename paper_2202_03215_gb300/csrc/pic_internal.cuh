@@ -8,7 +8,7 @@
 
 namespace pic {
 
-constexpr int kMaxProc = 8;
+constexpr int kMaxProc = 16;   // collision processes per species
 constexpr int kGaussN = 4096;          // Gaussian inverse-CDF intervals
 constexpr int kStageCap = 8192;        // births / radial losses staged per step and species
 constexpr int kFieldThreads = 1024;

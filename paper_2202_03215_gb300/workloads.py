@@ -100,6 +100,24 @@ def neon_xsecs(eps_max_e: float = 200.0, eps_max_i: float = 50.0,
     return out
 
 
+def neon_multilevel_xsecs(eps_max_e: float = 200.0, eps_max_i: float = 50.0) -> List[XSec]:
+    """Synthetic neon with the excitation split over seven levels (the lumped level of
+    neon_xsecs spread over thresholds 16.6 .. 20.0 eV, Lotz forms whose peaks sum to its 4e-21 m^2),
+    for the multi-level machinery; elastic, ionization and charge exchange as in neon_xsecs."""
+    g = _energy_grid(eps_max_e)
+    gi = _energy_grid(eps_max_e, threshold=21.56)
+    out = [XSec(ELASTIC, g, np.full_like(g, 2e-20))]
+    thr = [16.6, 16.7, 16.85, 18.4, 18.7, 19.0, 20.0]
+    peak = [1.0e-21, 0.5e-21, 0.5e-21, 0.8e-21, 0.5e-21, 0.4e-21, 0.3e-21]
+    for t, s in zip(thr, peak):
+        gx = _energy_grid(eps_max_e, threshold=t)
+        out.append(XSec(EXCITATION, gx, _lotz(gx, t, s), t))
+    out.append(XSec(IONIZATION, gi, _lotz(gi, 21.56, 7e-21), 21.56))
+    ge = np.array([0.0, eps_max_i])
+    out.append(XSec(ION_CX, ge, np.array([3e-19, 3e-19])))
+    return out
+
+
 @dataclass
 class Params:
     """Problem statement of one periodic positive column (Sec. II)."""

@@ -55,3 +55,15 @@ def test_two_term_rejects_bad_arguments():
         pb.two_term(w.neon_xsecs(), w.AMU_NE, [-1.0])
     with pytest.raises(pb.PicError):
         pb.two_term(w.neon_xsecs(), w.AMU_NE, [10.0], n_grid=10)
+
+
+def test_multilevel_transport_matches_the_oracle():
+    from paper_2202_03215_gb300 import workloads as w
+    xs = [x for x in w.neon_multilevel_xsecs() if x.kind <= 2]
+    xo = [(x.kind, x.threshold_eV, x.energy_eV, x.sigma_m2) for x in xs]
+    for en in (30.0, 80.0):
+        g = pb.two_term(xs, w.AMU_NE, [en], eps_max_eV=200.0, n_grid=1000)[0]
+        o = tt.solve(xo, w.AMU_NE, en, eps_max=200.0, n=1000)
+        for kg, ko in (("mean_eps_eV", "mean_eps"), ("muN", "muN"), ("nu_izN", "nu_izN")):
+            assert g[kg] == pytest.approx(o[ko], rel=1e-4), (en, kg)
+
