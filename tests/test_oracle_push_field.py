@@ -5,7 +5,7 @@ import numpy as np
 
 import oracle
 from paper_2202_03215_gb300 import workloads as w
-from tests.helpers import QE, ME, EPS0
+from tests.helpers import AMU, QE, ME, EPS0
 
 
 def test_constant_field_positions_are_exact_quadratics():
@@ -65,3 +65,30 @@ def test_cold_plasma_oscillation_leapfrog_dispersion():
     w_leap = 2 / dt * np.arcsin(wpe_dt / 2)
     assert abs(w_meas / w_leap - 1) < 1.5e-3
     assert abs(w_meas / wpe - 1) > 5e-3   # the leapfrog correction is resolved
+
+
+def test_subcycled_ions_move_on_their_push_steps_only():
+    """Ion subcycling: ions are pushed on steps 0, sub, 2 sub, ... with dt_i = sub dt and stay put
+    in between; over m pushes the leapfrog is exact for a constant field (x quadratic in m dt_i)."""
+    N, L, dt, E0, sub = 100, 0.01, 2e-11, 5e6, 10
+    p = w.Params(L_m=L, n_cells=N, dt_s=dt, xsec=[], field_mode=w.FIELD_APPLIED, drive=w.DRIVE_E0,
+                 E0_Vpm=E0, n_e0=0, n_i0=2000, ion_subcycle=sub, loss_mode=w.LOSS_NONE, Ti0_eV=0.5)
+    o = oracle.Oracle(p)
+    s0 = o.get_state()
+    dx, dti = L / N, sub * dt
+    x0 = s0["cell_i"] + s0["off_i"]
+    v_half = s0["vx_i"]
+    a = -QE * E0 / (p.gas_mass_amu * AMU)   # E = -E0, ion charge +e
+    prev = None
+    for n in (1, 5, 10, 11, 20, 35):
+        o.step(n - o.stats()["step"])
+        s = o.get_state()
+        m = -(-n // sub)   # pushes on steps 0, sub, ... below n
+        disp = (m * dti * v_half + a * dti * dti * m * (m + 1) / 2) / dx
+        d = (s["cell_i"] + s["off_i"]) - (x0 + disp)
+        d = (d + N / 2) % N - N / 2
+        assert np.abs(d).max() < 1e-7, n
+        assert np.allclose(s["vx_i"], v_half + m * a * dti, rtol=1e-12, atol=1e-9)
+        if prev is not None and prev[0] == m:
+            assert np.array_equal(s["cell_i"], prev[1]) and np.array_equal(s["off_i"], prev[2])
+        prev = (m, s["cell_i"], s["off_i"])
