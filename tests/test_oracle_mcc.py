@@ -149,3 +149,36 @@ def test_ion_charge_exchange_takes_the_neutral_velocity():
     assert abs(cx.sum() - n * P) < 4.5 * np.sqrt(n * P)
     vi = np.concatenate([s["vx_i"][cx], s["vy_i"][cx], s["vz_i"][cx]]) / vt
     assert stats.kstest(vi, "norm").pvalue > 1e-4
+
+
+def test_ion_isotropic_scattering_in_the_centre_of_mass_frame():
+    """Isotropic elastic ion-atom scattering (Sec. II) between equal masses: in a nearly cold gas
+    (T_g = 3e-4 K, the gas density of 1 Torr at 300 K) a beam ion of speed g0 leaves with
+    v' = v/2 + (g0/2) n, n uniform on the sphere, so |v' - v/2| = g0/2, the x-component of n is
+    uniform on [-1, 1] (Archimedes) and its azimuth uniform; the count of scatterings is binomial
+    with P_null nu_iso(g0)/nu*."""
+    n, g0, s_iso = 200_000, 3000.0, 2e-19
+    ge = np.array([0.0, 50.0])
+    p = _beam_params(0, n_i0=n, ion_subcycle=1, capacity=n + 10, dt_s=5e-9, T_gas_K=3e-4,
+                     pressure_torr=1e-6, xsec=[w.XSec(w.ION_ISO, ge, np.array([s_iso, s_iso]))])
+    o = oracle.Oracle(p)
+    st = beam_state(0, p.n_cells, 0.0, np.random.default_rng(6), n_i=n, ion_speed=g0)
+    o.set_state(st)
+    o.step(1)
+    codes = o.codes(1, n)
+    s = o.get_state()
+    hit = codes == 0
+    d = o.derived()
+    assert d["n_g"] == pytest.approx(n_gas(1.0, 300.0), rel=1e-12)
+    M = p.gas_mass_amu * AMU
+    nu_iso = d["n_g"] * s_iso * g0
+    P = d["P_null_i"] * nu_iso / d["nu_star_i"]
+    assert abs(hit.sum() - n * P) < 4.5 * np.sqrt(n * P)
+    assert hit.sum() > 5000
+    # ions that did not scatter keep their velocity
+    assert np.all(s["vx_i"][~hit] == g0) and not s["vy_i"][~hit].any()
+    ux, uy, uz = s["vx_i"][hit] - g0 / 2, s["vy_i"][hit], s["vz_i"][hit]
+    vt = np.sqrt(KB * p.T_gas_K / M)   # the neutrals' thermal speed, 0.25 m/s
+    assert np.allclose(np.sqrt(ux**2 + uy**2 + uz**2), g0 / 2, rtol=0, atol=10 * vt)
+    assert stats.kstest(ux / (g0 / 2), "uniform", args=(-1.0, 2.0)).pvalue > 1e-4
+    assert stats.kstest(np.arctan2(uz, uy), "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-4
