@@ -93,7 +93,7 @@ extern "C" {
                                            PIC_LOSS_RADIAL (the fixed loss frequency nu_w of Sec. V)
                                            or PIC_LOSS_NONE; single columns only. */
 
-/* One collision process (Sec. II, "scattering cross-sections"): sigma(eps)
+/* One collision process (Sec. II: one member of a gas's cross-section set): sigma(eps)
  * on an ascending energy grid.  Electron processes use the electron energy;
  * ion processes use 0.5 M g^2 / e, g the ion-neutral relative speed.  Linear
  * interpolation between points, end values held outside; excitation and
@@ -290,8 +290,8 @@ void pic_free(pic_handle *h);
 const char *pic_last_error(pic_handle *h);
 
 /* Periodic Poisson solve of Sec. II on caller device memory: the field step
- * that pic_step runs every step ("two tridiagonal systems" in the paper; here
- * the algebraically identical exact route).  From fixed-point node charges
+ * that pic_step runs every step (the paper solves a pair of tridiagonal
+ * systems; here the algebraically identical exact route).  From fixed-point node charges
  * (2^32 per particle) it computes the half-node space-charge field
  *   E_{j+1/2} = C (N S'_j - M) / N^2,  S'_j = N sum_{k<=j} D_k - (j+1) T,
  *   D = Q_i - Q_e, T = sum D, M = sum S'   (zero-mean field, uniform

@@ -121,7 +121,7 @@ static real us_next(ustream *s) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Gaussian inverse-CDF table (build reading: neutral and Maxwellian
+/* Gaussian inverse-CDF table (reading: neutral and Maxwellian
  * velocities are sampled by table so that the step holds no
  * transcendental).  T[k] = Phi^-1(k/4096) for 1 <= k <= 4095, rounded to
  * FP32; the end entries are set so that the linear piece over the first
@@ -661,8 +661,9 @@ static int64_t slot_draw(uint64_t seed, int64_t k, uint32_t attempt, uint32_t st
   return (int64_t)(((unsigned __int128)r * (unsigned __int128)(uint64_t)n) >> 64);
 }
 
-/* Paired random removal (Sec. II: for each ionization another electron and
- * ion are "chosen randomly and separately over the simulation length").
+/* Paired random removal (Sec. II: each ionization is balanced by removing one
+ * electron and one ion, each picked at random anywhere in the column,
+ * independently of each other).
  * Reading: victims are uniform over the pre-step slots, drawn without
  * replacement in rounds: every unsettled event k holds a candidate drawn
  * with its attempt counter; in one round an event settles iff no settled
@@ -820,7 +821,7 @@ static int births_and_losses(ora_t *h, int ion_pushed) {
   return 0;
 }
 
-/* Stable counting sort of one species by cell (build reading: particles are
+/* Stable counting sort of one species by cell (reading: particles are
  * reordered periodically so that each GPU thread block works on a narrow
  * cell window; slots, and hence victim draws, depend on the order, so the
  * sort is part of the step's definition).  Equal cells keep slot order. */
@@ -870,12 +871,12 @@ static int step_once(ora_t *h) {
   if (rc) return rc;
   h->step++;
   h->m_steps++;
-  /* Sec. V: an external circuit with a resistor sets the applied field,
+  /* Sec. V: a source in series with a resistor sets the applied field,
    * U = R_ext J + V_D with V_D = E0 L, so E0 = (U - R_ext J) / L, where J is the
    * discharge current density e w (sum v_e - sum v_i) / L over the pushed particles
    * (ions at their last push): positive when the electrons drift against the
-   * applied field -E0 -- build reading of "adding an external circuit with a
-   * resistor to adjust the applied field E0". */
+   * applied field -E0 -- a reading of the Sec. V circuit, whose resistor
+   * adjusts E0. */
   if (h->p.drive == ORA_DRIVE_CIRCUIT) {
     double J = h->Cj * (double)(h->sumv[0] - h->sumv[1]);
     h->E0 = (h->p.U_src - h->p.R_ext_ohm_m2 * J) / h->p.L_m;
@@ -1018,7 +1019,7 @@ int ora_create(const ora_params *pp, ora_t **out) {
     if (sum_i[i] > sum_i_max) sum_i_max = sum_i[i];
   }
   /* Electron majorant per energy bin [eps_i, eps_i+1]: the interpolated frequencies in a bin never
-   * exceed the larger of the summed frequencies at its two ends (build reading: an energy-binned
+   * exceed the larger of the summed frequencies at its two ends (reading: an energy-binned
    * null-collision majorant; the electron energy is known before the collision test). */
   h->nub_e = (real *)xcalloc((size_t)n, sizeof(real));
   h->Pb_e = (real *)xcalloc((size_t)n, sizeof(real));
