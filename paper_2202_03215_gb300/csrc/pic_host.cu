@@ -469,8 +469,28 @@ int resolve_ri(const pic_params *p, pic_params *q) {
   return 0;
 }
 
+// every floating-point input finite (a non-finite field or rate would reach the particle step)
+static int check_finite(const pic_params *p) {
+  const struct {
+    const char *name;
+    double v;
+  } f[] = {{"gas_mass_amu", p->gas_mass_amu}, {"pressure_torr", p->pressure_torr}, {"T_gas_K", p->T_gas_K},
+           {"L_m", p->L_m}, {"R_m", p->R_m}, {"E0_Vpm", p->E0_Vpm}, {"V_applied", p->V_applied}, {"I_A", p->I_A},
+           {"U_src", p->U_src}, {"R_ext_ohm_m2", p->R_ext_ohm_m2}, {"dt_s", p->dt_s}, {"n0_m3", p->n0_m3},
+           {"Te0_eV", p->Te0_eV}, {"Ti0_eV", p->Ti0_eV}, {"nu_w", p->nu_w}, {"eps_max_e_eV", p->eps_max_e_eV},
+           {"eps_max_i_eV", p->eps_max_i_eV}, {"J_emit_Am2", p->J_emit_Am2}, {"T_emit_eV", p->T_emit_eV}};
+  for (const auto &x : f)
+    if (!std::isfinite(x.v)) return set_err(nullptr, PIC_EINVAL, "%s is not finite", x.name);
+  return 0;
+}
+
 int validate(const pic_params *p) {
   if (!p) return set_err(nullptr, PIC_EINVAL, "params is NULL");
+  if (int rc = check_finite(p)) return rc;
+  if (!(p->gas_mass_amu > 0) || !(p->T_gas_K > 0)) return set_err(nullptr, PIC_EINVAL, "gas mass and temperature must be > 0");
+  if (p->pressure_torr < 0) return set_err(nullptr, PIC_EINVAL, "pressure must be >= 0");
+  if (p->Te0_eV < 0 || p->Ti0_eV < 0) return set_err(nullptr, PIC_EINVAL, "initial temperatures must be >= 0");
+  if (p->nu_w < 0) return set_err(nullptr, PIC_EINVAL, "nu_w must be >= 0");
   if (p->n_cells < 3 || p->n_cells > 65536) return set_err(nullptr, PIC_EINVAL, "n_cells must be in [3, 65536]");
   if (!(p->dt_s > 0) || !(p->L_m > 0)) return set_err(nullptr, PIC_EINVAL, "dt and L must be > 0");
   if (p->n_e0 < 0 || p->n_i0 < 0) return set_err(nullptr, PIC_EINVAL, "negative particle count");
@@ -501,6 +521,11 @@ int validate(const pic_params *p) {
       return set_err(nullptr, PIC_EINVAL, "bad cross section %d", x);
     for (int i = 1; i < xs.n; ++i)
       if (!(xs.energy_eV[i] >= xs.energy_eV[i - 1])) return set_err(nullptr, PIC_EINVAL, "xsec %d not ascending", x);
+    if (!std::isfinite(xs.threshold_eV) || xs.threshold_eV < 0)
+      return set_err(nullptr, PIC_EINVAL, "xsec %d: bad threshold", x);
+    for (int i = 0; i < xs.n; ++i)
+      if (!std::isfinite(xs.energy_eV[i]) || !std::isfinite(xs.sigma_m2[i]) || xs.sigma_m2[i] < 0)
+        return set_err(nullptr, PIC_EINVAL, "xsec %d has a negative or non-finite value", x);
     (is_e_kind(xs.kind) ? ne : ni)++;
   }
   if (ne > pic::kMaxProc || ni > pic::kMaxProc) return set_err(nullptr, PIC_EINVAL, "at most %d processes per species", pic::kMaxProc);
@@ -745,6 +770,7 @@ int pic_init(const pic_params *params, pic_handle **out) {
   *out = nullptr;
   pic_params ri;
   if (params && params->drive == PIC_DRIVE_RI) {   // resolve (R, I) -> (E0, n0), then run as the E0 drive
+    if (int rc = check_finite(params)) return rc;
     if (resolve_ri(params, &ri)) return set_err(nullptr, PIC_EINVAL, "the (R, I) drive has no solution");
     params = &ri;
   }

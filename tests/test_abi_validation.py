@@ -46,6 +46,18 @@ CASES = {
     "energy range": (_ok(eps_max_e_eV=0.0), "eps_max"),
     "column index": (_ok(column=5000), "column"),
     "capacity below the count": (_ok(capacity=10), "capacity"),
+    "infinite field": (_ok(drive=w.DRIVE_E0, E0_Vpm=float("inf")), "E0_Vpm is not finite"),
+    "NaN pressure": (_ok(pressure_torr=float("nan")), "pressure_torr is not finite"),
+    "NaN radius, (R, I) drive": (_ok(drive=w.DRIVE_RI, I_A=1e-3, R_m=float("nan")), "R_m is not finite"),
+    "gas temperature": (_ok(T_gas_K=0.0), "gas mass and temperature"),
+    "gas mass": (_ok(gas_mass_amu=-4.0), "gas mass and temperature"),
+    "negative pressure": (_ok(pressure_torr=-1.0), "pressure"),
+    "negative initial temperature": (_ok(Te0_eV=-1.0), "initial temperatures"),
+    "negative loss frequency": (_ok(loss_mode=w.LOSS_RADIAL, nu_w=-1.0), "nu_w"),
+    "NaN cross section": (_ok(xsec=[_bad_xsec(sigmas=(1e-19, float("nan")))]), "non-finite value"),
+    "negative cross section": (_ok(xsec=[_bad_xsec(sigmas=(1e-19, -1e-20))]), "negative"),
+    "negative threshold": (_ok(xsec=[w.XSec(w.EXCITATION, np.array([0.0, 20.0]), np.array([0.0, 1e-20]), -5.0)]),
+                           "threshold"),
 }
 
 
