@@ -437,7 +437,7 @@ static int tab_pos(real eps, real inv_de, int ntab, real *fr, int *ovf) {
 }
 
 static void moments_alloc(ora_t *h) {
-  int N = h->N + 1;
+  size_t N = (size_t)h->N + 1;
   h->m_ne = (double *)xcalloc(N, 8); h->m_ni = (double *)xcalloc(N, 8);
   h->m_ge = (double *)xcalloc(N, 8); h->m_ee = (double *)xcalloc(N, 8);
   h->m_he = (double *)xcalloc(N, 8); h->m_gi = (double *)xcalloc(N, 8);
