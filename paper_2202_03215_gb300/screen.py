@@ -189,7 +189,7 @@ def linear(tab: Table, h: Homogeneous) -> dict:
     al, be, de = chi * nup / (Da * K), Lp / K, 2 * L0 * nup / (Da * K)
     disc = de - al * be
     out = dict(chi=chi, K=K, nu_p=nup, L0=L0, L_p=Lp, D_a=Da,
-               chi_crit=-(Da * Lp + math.sqrt(max(8 * Da * K * L0 * nup, 0.0))) / nup)
+               chi_crit=(-(Da * Lp + math.sqrt(max(8 * Da * K * L0 * nup, 0.0))) / nup) if nup != 0 else math.nan)
     if disc <= 0 or -be + math.sqrt(disc) <= 0:
         out.update(gamma_max=math.nan, k_max=math.nan, lam=math.nan, v_ph=math.nan, unstable=False)
         return out
