@@ -62,3 +62,31 @@ def test_eq19_growth_rate_reduces_to_ambipolar_diffusion():
         assert om == 0.0
     lin = screen.linear(tab, h)
     assert lin["nu_p"] == 0.0 and not lin["unstable"]
+
+
+def test_closed_form_maximum_is_the_maximum_of_eq19():
+    """eqs. (21)-(22) give the fastest-growing wave number and its growth rate in closed form;
+    a direct search of eq. (19)'s gamma(k) over k must find the same maximum, and the phase
+    velocity is omega(k_max)/k_max."""
+    from scipy.optimize import minimize_scalar
+    tab = screen.Table(screen.transport())
+    found = 0
+    for E0p in (6.0, 8.0, 12.0, 16.0):
+        h = screen.homogeneous_E0(tab, E0p, 1.0)
+        lin = screen.linear(tab, h)
+        if not lin["unstable"]:
+            continue
+        found += 1
+        ks = np.geomspace(lin["k_max"] / 30, lin["k_max"] * 30, 400)
+        g = np.array([screen.gamma_k(tab, h, k)[0] for k in ks])
+        i = int(np.argmax(g))
+        assert 0 < i < len(ks) - 1                       # an interior maximum
+        r = minimize_scalar(lambda lk: -screen.gamma_k(tab, h, math.exp(lk))[0],
+                            bracket=(math.log(ks[i - 1]), math.log(ks[i]), math.log(ks[i + 1])), tol=1e-10)
+        k_best = math.exp(r.x)
+        assert k_best == pytest.approx(lin["k_max"], rel=1e-4)
+        assert -r.fun == pytest.approx(lin["gamma_max"], rel=1e-8)
+        g_at, om_at = screen.gamma_k(tab, h, lin["k_max"])
+        assert om_at / lin["k_max"] == pytest.approx(lin["v_ph"], rel=1e-12)
+        assert lin["lam"] == pytest.approx(2 * math.pi / lin["k_max"], rel=1e-12)
+    assert found >= 2
