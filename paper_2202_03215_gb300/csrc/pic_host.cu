@@ -710,7 +710,10 @@ template <class R> int step_batch(pic_handle *b, int64_t n) {
         cudaError_t e = cudaStreamEndCapture(b->stream, &g);
         b->host_step = s0;
         for (pic_handle *c : b->cols) c->host_step = s0;
-        if (rc) return rc;
+        if (rc) {
+          if (e == cudaSuccess) cudaGraphDestroy(g);
+          return rc;
+        }
         if (e != cudaSuccess) return set_err(b, PIC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&b->cycle, g, 0);
         cudaGraphDestroy(g);
@@ -893,7 +896,10 @@ int pic_step(pic_handle *h, int64_t n) {
         for (int q = 0; q < sub && !rc; ++q) rc = h->mixed ? enqueue_step<float>(h) : enqueue_step<double>(h);
         cudaError_t e = cudaStreamEndCapture(h->stream, &g);
         h->host_step = s0;
-        if (rc) return rc;
+        if (rc) {
+          if (e == cudaSuccess) cudaGraphDestroy(g);
+          return rc;
+        }
         if (e != cudaSuccess) return set_err(h, PIC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&h->cycle, g, 0);
         cudaGraphDestroy(g);
