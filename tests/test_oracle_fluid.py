@@ -144,3 +144,28 @@ def test_cyclic_solve_against_dense():
         A[j, (j - 1) % N] += lo[j]
         A[j, (j + 1) % N] += up[j]
     assert np.allclose(fl.cyclic_solve(lo, dg, up, rhs), np.linalg.solve(A, rhs), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("pair", [False, True])
+def test_the_model_is_linear_in_the_density(pair):
+    """The fluid model, like the particle model (Sec. II), is linear in the plasma density: four
+    times the density and the current (an exact power of two) give four times the density and
+    the same temperature, bit for bit, through both tridiagonal solves and the field."""
+    tab = const_table(dloss=4e-15)
+    rng = np.random.default_rng(12)
+    n = 1e16 * (1 + 0.05 * rng.standard_normal(512))
+    T = 4.0 + 0.2 * rng.standard_normal(512)
+    c = fl.coefficients(column(tab=tab), tab, np.array([4.0]))   # the current of the steady state at 4 eV
+    GT = 1e16 * (c["mu_e"][0] + c["mu_i"]) * np.sqrt(c["L"][0] / c["mu_e"][0])
+    c1 = column(Gamma_T=GT, tab=tab)
+    c4 = dict(c1, Gamma_T=4 * c1["Gamma_T"])
+    if pair:
+        c1["pair"] = c4["pair"] = True
+    n1, T1, n4, T4 = n.copy(), T.copy(), 4 * n, T.copy()
+    lo, hi = tab["T0"], tab["T0"] + (tab["nT"] - 1) * tab["dT"]
+    for _ in range(30):
+        n1, T1 = fl.step(c1, tab, n1, T1, 2e-8)
+        n4, T4 = fl.step(c4, tab, n4, T4, 2e-8)
+        assert np.array_equal(n4, 4 * n1) and np.array_equal(T4, T1)
+        assert np.all((T1 > lo) & (T1 < hi))          # no clipping at the table ends masks a difference
+    assert np.std(n1) > 0 and not np.array_equal(n1, n)
