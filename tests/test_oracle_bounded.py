@@ -75,3 +75,27 @@ def test_vacuum_diode_child_langmuir():
     # velocities at 0.05 eV raise it by a few per cent), the rest returns to the cathode
     assert J == pytest.approx(Jcl, rel=0.08)
     assert o.stats()["absorbed_e"][0] > 0
+
+
+def test_emitted_electrons_are_a_half_maxwellian_at_the_cathode():
+    """Cathode emission (Sec. V) at T_emit: the newborns of one step have v_x half-normal and
+    v_y, v_z normal with sigma = (e T_emit / m)^(1/2), and start at x = u v_x dt with u uniform
+    (the part of the step already flown)."""
+    from scipy import stats
+    T_emit = 2.0
+    p = diode(1e4, 0.0, T_emit=T_emit)
+    o = oracle.Oracle(p)
+    id0 = o.get_state()["next_id"]
+    o.step(1)
+    s = o.get_state()
+    new = s["id_e"] >= id0
+    per_step = p.J_emit_Am2 * p.dt_s / (QE * p.n0_m3 * p.L_m / p.n_e0)
+    assert new.sum() == int(np.floor(per_step)) > 2000
+    sig = np.sqrt(QE * T_emit / ME)
+    vx, vy, vz = s["vx_e"][new] / sig, s["vy_e"][new] / sig, s["vz_e"][new] / sig
+    assert np.all(vx >= 0)
+    assert stats.kstest(vx, "halfnorm").pvalue > 1e-4
+    assert stats.kstest(np.concatenate([vy, vz]), "norm").pvalue > 1e-4
+    dx = p.L_m / p.n_cells
+    u = (s["cell_e"][new] + s["off_e"][new]) * dx / (s["vx_e"][new] * p.dt_s)
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
