@@ -189,3 +189,24 @@ def test_circuit_drive_sets_E0_from_the_current():
         Js.append(J)
     assert np.mean(Js[30:]) > 0          # the electrons' drift against the applied field: J > 0
     assert s["E0"] != 1000.0
+
+
+def test_radial_losses_of_subcycled_ions_use_the_ion_step():
+    """With ions pushed every 10th step, an ion is removed only on its push steps, with
+    probability 1 - exp(-nu_w dt_i), dt_i = 10 dt; electrons every step with 1 - exp(-nu_w dt)."""
+    n, nu_w, dt, sub = 100_000, 2e8, 2e-11, 10
+    p = w.Params(L_m=0.05, n_cells=100, dt_s=dt, xsec=[], field_mode=w.FIELD_APPLIED, drive=w.DRIVE_E0,
+                 E0_Vpm=0.0, n_e0=n, n_i0=n, ion_subcycle=sub, loss_mode=w.LOSS_RADIAL, nu_w=nu_w)
+    o = oracle.Oracle(p)
+    o.step(1)                                    # step 0: electrons and ions
+    s = o.stats()
+    Pi = 1 - np.exp(-nu_w * sub * dt)
+    assert abs(s["n_i"] - n * (1 - Pi)) < 4.5 * np.sqrt(n * Pi * (1 - Pi))
+    ni1, ne1 = s["n_i"], s["n_e"]
+    o.step(sub - 1)                              # steps 1..9: electrons only
+    s = o.stats()
+    assert s["n_i"] == ni1
+    Pe9 = 1 - np.exp(-nu_w * dt * (sub - 1))
+    assert abs(s["n_e"] - ne1 * (1 - Pe9)) < 4.5 * np.sqrt(ne1 * Pe9 * (1 - Pe9))
+    o.step(1)                                    # step 10: the ions' next push
+    assert o.stats()["n_i"] < ni1
