@@ -182,3 +182,32 @@ def test_ion_isotropic_scattering_in_the_centre_of_mass_frame():
     assert np.allclose(np.sqrt(ux**2 + uy**2 + uz**2), g0 / 2, rtol=0, atol=10 * vt)
     assert stats.kstest(ux / (g0 / 2), "uniform", args=(-1.0, 2.0)).pvalue > 1e-4
     assert stats.kstest(np.arctan2(uz, uy), "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-4
+
+
+def test_energies_above_the_table_hold_its_last_value_and_are_counted():
+    """Electrons above the table's range (eps_max_e) collide with the frequencies of the table's
+    end and the last bin's majorant, and every collision candidate among them is counted as an
+    overflow; below the range nothing is counted."""
+    n, eps0 = 200_000, 600.0
+    p = _beam_params(n, eps_max_e_eV=500.0)
+    o = oracle.Oracle(p)
+    o.set_state(beam_state(n, p.n_cells, np.sqrt(2 * QE * eps0 / ME), np.random.default_rng(8)))
+    o.step(1)
+    codes, st = o.codes(0, n), o.stats()
+    ng = n_gas()
+    de = p.eps_max_e_eV / (p.n_table - 1)
+    ends = [(p.n_table - 2) * de, (p.n_table - 1) * de]
+    S = [sum(_sigma(x, e) for x in p.xsec[:3]) * ng * np.sqrt(2 * QE * e / ME) for e in ends]
+    Pn = 1 - np.exp(-max(S) * p.dt_s)
+    cand = st["overflow_e"]
+    assert abs(cand - n * Pn) < 4.5 * np.sqrt(n * Pn * (1 - Pn))
+    v_end = np.sqrt(2 * QE * p.eps_max_e_eV / ME)     # the frequency held is the one at eps_max
+    for k, x in enumerate(p.xsec[:3]):
+        pk = Pn * ng * _sigma(x, p.eps_max_e_eV) * v_end / max(S)
+        cnt = np.count_nonzero(codes == k)
+        assert abs(cnt - n * pk) < 4.5 * np.sqrt(n * pk * (1 - pk)) + 1, (k, cnt, n * pk)
+    # the same beam inside the range: no overflow
+    o2 = oracle.Oracle(_beam_params(n, eps_max_e_eV=700.0))
+    o2.set_state(beam_state(n, p.n_cells, np.sqrt(2 * QE * eps0 / ME), np.random.default_rng(8)))
+    o2.step(1)
+    assert o2.stats()["overflow_e"] == 0
