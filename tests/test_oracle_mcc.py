@@ -211,3 +211,24 @@ def test_energies_above_the_table_hold_its_last_value_and_are_counted():
     o2.set_state(beam_state(n, p.n_cells, np.sqrt(2 * QE * eps0 / ME), np.random.default_rng(8)))
     o2.step(1)
     assert o2.stats()["overflow_e"] == 0
+
+
+def test_ions_above_the_table_are_counted():
+    """Ions whose relative energy 0.5 M g^2/e exceeds eps_max_i (a nearly cold gas, 60 eV against a
+    50 eV table): every candidate, drawn with the global P_null of the ions, is an overflow, and
+    charge exchange keeps the table's end frequency."""
+    n, eps_g = 200_000, 60.0
+    p = _beam_params(0, n_i0=n, ion_subcycle=1, capacity=n + 10, T_gas_K=3e-4, pressure_torr=1e-6,
+                     eps_max_i_eV=50.0, xsec=w.argon_xsecs(sigma_iso=0.0))
+    o = oracle.Oracle(p)
+    g = np.sqrt(2 * QE * eps_g / (p.gas_mass_amu * AMU))
+    o.set_state(beam_state(0, p.n_cells, 0.0, np.random.default_rng(10), n_i=n, ion_speed=g))
+    o.step(1)
+    d, st, codes = o.derived(), o.stats(), o.codes(1, n)
+    P = d["P_null_i"]
+    assert abs(st["overflow_i"] - n * P) < 4.5 * np.sqrt(n * P * (1 - P))
+    # CX (5e-19 m^2, constant) at the end of the table: nu = n_g sigma g_max with 0.5 M g_max^2 = e eps_max_i
+    g_end = np.sqrt(2 * QE * p.eps_max_i_eV / (p.gas_mass_amu * AMU))
+    pcx = P * d["n_g"] * 5e-19 * g_end / d["nu_star_i"]
+    cnt = np.count_nonzero(codes == 3)
+    assert abs(cnt - n * pcx) < 4.5 * np.sqrt(n * pcx * (1 - pcx))
