@@ -195,10 +195,16 @@ typedef struct pic_moments_out {
 
 typedef struct pic_handle pic_handle;
 
-/* Validate params, build the collision tables, allocate device memory,
- * place n_e0 electrons and n_i0 ions uniformly with Maxwellian velocities,
- * solve the initial field and pull velocities back half a step (leapfrog).
- * *out receives the handle (owned by the caller until pic_free). */
+/* Create one column (Sec. II).  Validates params, builds the collision tables, allocates
+ * device memory, places n_e0 electrons and n_i0 ions uniformly in x with Maxwellian
+ * velocities at Te0 / Ti0, solves the initial field, and pulls the velocities back half a
+ * step (the leapfrog start).  PIC_DRIVE_RI is first resolved into E0 and n0 by eq. 2
+ * (pic_drive_ri).
+ * params and its xsec arrays are read during the call only.  On success *out is a handle
+ * owned by the caller until pic_free.  On failure *out = NULL and nothing stays allocated:
+ * PIC_EINVAL for an invalid problem statement (checked before any device call; the message
+ * names the offending field; also a capacity below the initial count), PIC_ENOMEM,
+ * PIC_ECUDA (no device, or a failed launch). */
 int pic_init(const pic_params *params, pic_handle **out);
 
 /* Advance n >= 0 steps.  Each step: electron gather/push/collisions/deposit,
@@ -207,10 +213,19 @@ int pic_init(const pic_params *params, pic_handle **out);
  * with no sort and no diagnostic sample) is replayed from a CUDA graph captured
  * on first use (PIC_FLAG_NO_GRAPH or kernel timing: launched one by one); the
  * results are the same.  Stream-ordered; synchronises once at the end to read
- * the device status word. */
+ * the device status word.
+ * Errors: PIC_EINVAL (n < 0, or a column of a batch); a device-side error of the step
+ * (PIC_ECAPACITY: more births than free slots, or than particles to remove; PIC_ENONFINITE:
+ * a non-finite field) is returned after the step and latched: every later call on the handle
+ * returns it until pic_set_state installs a new state.  The births of the failing step are
+ * not written. */
 int pic_step(pic_handle *h, int64_t n);
 
-/* Copy the moment window (host arrays of one entry per node, NULL to skip). */
+/* Copy the moment window (Sec. III, the profiles of Fig. 4): time averages over the
+ * diagnostic samples since the last reset (see pic_moments_out for units).  Every non-NULL
+ * array is caller-owned host memory of one entry per node (n_cells, or n_cells + 1 in a
+ * bounded column); NULL skips it.  Synchronises the handle's stream.  PIC_EINVAL for a NULL
+ * argument. */
 int pic_moments(pic_handle *h, pic_moments_out *out);
 
 /* Electron energy probability function F(x, eps) (Sec. III.C, Fig. 8), sampled as a
@@ -228,6 +243,11 @@ int pic_eepf_config(pic_handle *h, int32_t n_x, int32_t n_eps, double eps_max_eV
  * samples they hold; reset = 1 clears both afterwards. */
 int pic_eepf_get(pic_handle *h, uint64_t *counts, int64_t *n_samples, int32_t reset);
 
+/* Copy the state: counts, step counter, next id and E0 always; then every non-NULL array,
+ * caller-owned host memory of at least n_e (electron arrays) or n_i (ion arrays) entries,
+ * which pic_get_stats gives, or of the capacity; E, Q_e and Q_i hold one entry per node.  The
+ * MIXED form's FP32 offsets and velocities are widened exactly to double.  Synchronises the
+ * handle's stream; PIC_EINVAL for a NULL argument. */
 int pic_get_state(pic_handle *h, pic_state *out);
 /* Replace the state; the next step uses state->step as its counter.  The arrays are
  * uploaded as given (pinned host memory copies at full link speed) and checked on the
@@ -236,6 +256,8 @@ int pic_get_state(pic_handle *h, pic_state *out);
  * lowest such particle and leaves the particles undefined until the next successful
  * call.  The first call allocates 32 bytes of device memory per particle of capacity. */
 int pic_set_state(pic_handle *h, const pic_state *in);
+/* Copy the counters (pic_stats) into *out.  Synchronises the handle's stream; PIC_EINVAL for a
+ * NULL argument. */
 int pic_get_stats(pic_handle *h, pic_stats *out);
 
 /* Batched columns: n independent periodic columns (uneven lengths, cell counts,
@@ -254,6 +276,7 @@ int pic_step_batch(pic_handle *batch, int64_t n);
 /* Column i of a batch (owned by the batch: use it for get_state, stats,
  * moments; it cannot be stepped or freed on its own).  NULL if out of range. */
 pic_handle *pic_batch_column(pic_handle *batch, int i);
+/* Number of columns of a batch; 0 for NULL or a single column. */
 int pic_batch_size(pic_handle *batch);
 
 /* Per-particle process code of the last step (needs PIC_FLAG_RECORD_CODES):
@@ -284,6 +307,8 @@ int pic_kernel_times(pic_handle *h, double *ms, int64_t *launches);
 /* The CUDA stream the handle launches on (a cudaStream_t). */
 void *pic_stream(pic_handle *h);
 
+/* Release a column or a batch: waits for its stream, frees its device memory, graphs, events
+ * and stream.  NULL is ignored, and so is a column of a batch (freed with its batch). */
 void pic_free(pic_handle *h);
 
 /* Message of the last error on this handle (NULL: the last global error). */
