@@ -361,11 +361,18 @@ int pic_field_periodic_noalloc(const int64_t *Q_i, const int64_t *Q_e, int n_cel
  * Inputs: 15 features per sample (5-point stencil of density, mean energy and
  * field, normalised by the caller); outputs: 3 (electron flux, energy flux,
  * ionization rate, normalised).  Parameter layout (FP32, flat, 18947 values):
- * W1[128][15], b1[128], W2[128][128], b2[128], W3[3][128], b3[3]. */
+ * W1[128][15], b1[128], W2[128][128], b2[128], W3[3][128], b3[3].
+ * Sample arrays are row-major (n x 15, n x 3) FP32 in caller-owned device memory, read (or,
+ * for Y, written) on the given stream (NULL: the default stream); nothing is retained after a
+ * call.  Errors are returned as codes only (pic_last_error does not see them): PIC_EINVAL for
+ * a NULL handle or array, n <= 0, or a parameter count other than pic_mlp_nparam();
+ * PIC_ENOMEM; PIC_ECUDA; PIC_ETIMEOUT when a bounded wait on a weight copy gave up (the
+ * kernels then return without writing and the status is cleared). */
 typedef struct pic_mlp pic_mlp;
 int pic_mlp_nparam(void);
 /* weights and biases uniform in +-1/sqrt(fan_in) from a seeded generator */
 int pic_mlp_create(uint64_t seed, pic_mlp **out);
+/* release the network's device memory (NULL is ignored) */
 void pic_mlp_free(pic_mlp *m);
 /* host arrays of pic_mlp_nparam() floats; set resets the Adam state */
 int pic_mlp_set_params(pic_mlp *m, const float *host, int n);
@@ -459,8 +466,12 @@ typedef struct pic_fluid pic_fluid;
  * Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
 int pic_fluid_init(const pic_fluid_column *cols, int n_cols, const pic_transport *tr, int n_tr, int n_T,
                    double dt_s, int diag_every, int n_modes, pic_fluid **out);
-/* host arrays of the column's n_cells values (FP64 in, stored as FP32) */
+/* host arrays of the column's n_cells values, n > 0 and finite (PIC_EINVAL otherwise, and for
+ * a NULL handle or array or col out of range).  The state is kept in FP64 between launches; a
+ * launch holds it in shared memory as FP32 (hi, lo) pairs */
 int pic_fluid_set_state(pic_fluid *f, int col, const double *n_m3, const double *Te_eV);
+/* the column's FP64 state into host arrays of n_cells; PIC_EINVAL for a NULL handle or array
+ * or col out of range */
 int pic_fluid_get_state(pic_fluid *f, int col, double *n_m3, double *Te_eV);
 /* advance every column by n_steps; synchronises the handle's stream */
 int pic_fluid_step(pic_fluid *f, int64_t n_steps);
@@ -487,7 +498,9 @@ int pic_fluid_set_corrections(pic_fluid *f, const float *corr_dev);
 int pic_fluid_features(pic_fluid *f, float *X_dev);
 /* device time of the last pic_fluid_step and the kernels it launched */
 int pic_fluid_elapsed(pic_fluid *f, double *ms, int64_t *launches);
+/* the CUDA stream the screen launches on (a cudaStream_t) */
 void *pic_fluid_stream(pic_fluid *f);
+/* release the screen's device memory and stream (NULL is ignored) */
 void pic_fluid_free(pic_fluid *f);
 
 /* The (R, I) drive (Sec. II, eq. 2; the paper imposes E0 and recovers R from eq. 2): the field E0
@@ -507,6 +520,8 @@ int pic_drive_ri(const pic_params *p, double out[4]);
  * (ties to even).  Host arrays of n. */
 int pic_test_i128_to_double(const int64_t *hi, const uint64_t *lo, double *out, int n);
 
+/* Version of this interface: changes whenever a declaration or a struct layout in this header
+ * changes, so a binding can refuse a library built from another header. */
 int pic_abi_version(void);
 
 #ifdef __cplusplus
