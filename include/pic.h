@@ -311,7 +311,8 @@ void *pic_stream(pic_handle *h);
  * and stream.  NULL is ignored, and so is a column of a batch (freed with its batch). */
 void pic_free(pic_handle *h);
 
-/* Message of the last error on this handle (NULL: the last global error). */
+/* Message of the last error on this handle; with NULL, of the last error this thread met outside
+ * a handle (pic_init, pic_init_batch, the standalone field solve).  Valid until the next call. */
 const char *pic_last_error(pic_handle *h);
 
 /* Periodic Poisson solve of Sec. II on caller device memory: the field step
