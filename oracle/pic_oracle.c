@@ -22,7 +22,29 @@
  * Readings where the paper is silent are listed beside each function.
  *
  * Parity pins live in tests/ (closed forms and invariants); see each
- * function's comment for which one pins it.
+ * function's comment for which one pins it.  In brief:
+ *   Philox, Gaussian table     known-answer vectors, quantiles, moments, KS
+ *   push, subcycling           exact constant-field quadratics (electrons and
+ *                              subcycled ions), the leapfrog plasma frequency
+ *   deposit, field             Gauss's law, sinusoidal and uniform charge closed
+ *                              forms, the paper's Thomas route (periodic and
+ *                              Dirichlet), charge = N 2^32 exactly
+ *   collisions                 counts against n_g sigma v, the majorant, the
+ *                              table's end values with overflow counts,
+ *                              elastic / inelastic / ionization kinematics,
+ *                              charge exchange, centre-of-mass isotropic
+ *                              scattering, the Maxwell-model swarm
+ *   births, losses             pair counts and uniform victims, radial
+ *                              binomials (electrons, subcycled ions),
+ *                              compaction order, cathode emission
+ *                              (half-Maxwellian, Child-Langmuir)
+ *   moments, EEPF              column integrals, Poisson for the sampled
+ *                              potential, mono-energetic and Maxwellian EEPFs
+ *   the whole step             determinism, checkpoint/resume, the discharge
+ *                              similarity laws bit for bit
+ * Every function here has a pin.  What long runs produce (striation
+ * wavelength and phase velocity under the synthetic cross sections) has no
+ * value to compare against: parity unpinned there, compared statistically.
  */
 #include "pic_oracle.h"
 
