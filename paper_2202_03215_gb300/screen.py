@@ -273,6 +273,14 @@ def dispersion_max(tab: Table, h: Homogeneous, L: float, m_max: int = 256) -> di
     return dict(m=best, lam=L / best, gamma=g, v_ph=om / k)
 
 
+def potential_drop(E_nodes: np.ndarray, dx: float, cells: int, start: int = 0) -> float:
+    """Potential drop over `cells` consecutive cells of a periodic column from the total node
+    field E = -E0 + E_sp (eq. 1: over one striation it equals E0 lambda, the space-charge field
+    averaging to zero over a period): |-sum_j E_j dx| over nodes start .. start + cells - 1."""
+    idx = (start + np.arange(cells)) % len(E_nodes)
+    return float(abs(-np.sum(E_nodes[idx]) * dx))
+
+
 def observables(t: np.ndarray, modes: np.ndarray, L: float) -> dict:
     """Striation observables from a record of modes: t (snapshot times, increasing),
     modes [snap, 1 + M] complex with entry 0 the mean density."""
