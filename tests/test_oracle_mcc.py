@@ -232,3 +232,29 @@ def test_ions_above_the_table_are_counted():
     pcx = P * d["n_g"] * 5e-19 * g_end / d["nu_star_i"]
     cnt = np.count_nonzero(codes == 3)
     assert abs(cnt - n * pcx) < 4.5 * np.sqrt(n * pcx * (1 - pcx))
+
+
+@pytest.mark.parametrize("gas", ["argon", "neon_multilevel"])
+def test_collision_frequency_tables_on_the_uniform_grid(gas):
+    """The tables hold nu_k(eps_i) = n_g sigma_k(eps_i) v(eps_i) at eps_i = i eps_max/(n-1), with
+    sigma linear between the given points, end values held, zero below an inelastic threshold;
+    v = (2 e eps/m) for electrons and the relative speed (2 e eps/M) for ions."""
+    xs = w.argon_xsecs(sigma_iso=1e-19) if gas == "argon" else w.neon_multilevel_xsecs()
+    mass = w.AMU_AR if gas == "argon" else w.AMU_NE
+    p = _beam_params(10, gas_mass_amu=mass, xsec=xs, n_table=4097)
+    o = oracle.Oracle(p)
+    ng = o.derived()["n_g"]
+    assert ng == pytest.approx(n_gas(), rel=1e-12)
+    e_proc = [x for x in xs if x.kind in (w.ELASTIC, w.EXCITATION, w.IONIZATION)]
+    i_proc = [x for x in xs if x.kind in (w.ION_CX, w.ION_ISO)]
+    for sp, procs, emax, m in ((0, e_proc, p.eps_max_e_eV, ME), (1, i_proc, p.eps_max_i_eV, mass * AMU)):
+        eps = np.arange(p.n_table) * (emax / (p.n_table - 1))
+        v = np.sqrt(2 * QE * eps / m)
+        for j, x in enumerate(procs):
+            s = np.interp(eps, x.energy_eV, x.sigma_m2)
+            if x.kind in (w.EXCITATION, w.IONIZATION):
+                s = np.where(eps < x.threshold_eV, 0.0, s)
+            got = o.nu_table(sp, j)
+            assert np.allclose(got, ng * s * v, rtol=1e-12, atol=0), (sp, j)
+            if x.kind in (w.EXCITATION, w.IONIZATION):
+                assert not got[eps < x.threshold_eV].any() and got[eps > x.threshold_eV + 1].all()
