@@ -258,3 +258,38 @@ def test_collision_frequency_tables_on_the_uniform_grid(gas):
             assert np.allclose(got, ng * s * v, rtol=1e-12, atol=0), (sp, j)
             if x.kind in (w.EXCITATION, w.IONIZATION):
                 assert not got[eps < x.threshold_eV].any() and got[eps > x.threshold_eV + 1].all()
+
+
+def test_real_collision_probability_is_the_continuous_time_one():
+    """Null-collision method (Sec. II): with a majorant nu_b >= nu the per-step probability of a real
+    collision, P(nu_b dt) nu/nu_b with P(x) = 1 - exp(-x), differs from the exact probability
+    1 - exp(-nu dt) of the continuous-time process by at most (nu_b dt)^2/8 (from (1 - e^-x)/x,
+    decreasing with slope above -1/2), and never exceeds it.  Measured from mono-energetic beams
+    across the whole table, each energy's nu = n_g sum_k sigma_k(eps) v(eps) taken from the cross
+    sections as given, not from the oracle's tables; nu_b is bounded by the global maximum nu*, so
+    the bound does not assume the binned construction.  A candidate probability taken as nu_b dt,
+    or a majorant below the frequency somewhere in a bin, fails it."""
+    n = 400_000
+    p = _beam_params(n, dt_s=2e-11)
+    ng = n_gas()
+    d0 = oracle.Oracle(p.with_(n_e0=10, capacity=20)).derived()
+    x_star = d0["nu_star_e"] * p.dt_s
+    assert 0.2 < x_star <= 0.3           # large enough to make the O(x^2) term visible
+    rng = np.random.default_rng(31)
+    worst = 0.0
+    for eps0 in np.geomspace(0.05, 480.0, 23):
+        o = oracle.Oracle(p)
+        speed = np.sqrt(2 * QE * eps0 / ME)
+        o.set_state(beam_state(n, p.n_cells, speed, rng))
+        o.step(1)
+        real = np.count_nonzero(o.codes(0, n) >= 0)
+        nu = sum(_sigma(x, eps0) for x in p.xsec[:3]) * ng * speed
+        exact = -np.expm1(-nu * p.dt_s)
+        got = real / n
+        sd = np.sqrt(max(exact, 1.0 / n) * (1 - exact) / n)
+        # the table interpolates n_g sigma v linearly between grid points 0.06 eV apart
+        slack = 2e-3 * exact
+        assert got <= exact + 4.5 * sd + slack, (eps0, got, exact)
+        assert exact - got <= x_star ** 2 / 8 + 4.5 * sd + slack, (eps0, got, exact, x_star)
+        worst = max(worst, (exact - got) / (x_star ** 2 / 8))
+    assert worst < 1.0
