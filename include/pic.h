@@ -207,6 +207,18 @@ typedef struct pic_handle pic_handle;
  * PIC_ECUDA (no device, or a failed launch). */
 int pic_init(const pic_params *params, pic_handle **out);
 
+/* Resolution limits of the explicit particle scheme (Sec. II): the time step must resolve the
+ * electron plasma frequency, dt < 0.2 / w_pe, and the cell size the electron Debye length,
+ * dx < lambda_De, with w_pe = (n0 e^2 / (eps0 m_e))^(1/2) and lambda_De = (eps0 Te0 / (n0 e))^(1/2)
+ * (Te0 in eV) at the initial density and temperature (PIC_DRIVE_RI: the n0 of eq. 2).  Host
+ * only: no device call.  These are warnings, not errors: pic_init does not enforce them.
+ *   out    (may be NULL) out[0] = w_pe dt, out[1] = dx / lambda_De (HUGE_VAL when Te0 = 0)
+ * Returns the PIC_WARN_* bits of the limits that fail (0 when both hold), or PIC_EINVAL for a
+ * NULL, non-finite or non-positive statement. */
+#define PIC_WARN_PLASMA_FREQ 1   /* w_pe dt >= 0.2 */
+#define PIC_WARN_DEBYE 2         /* dx >= lambda_De */
+int pic_check_stability(const pic_params *params, double out[2]);
+
 /* Advance n >= 0 steps.  Each step: electron gather/push/collisions/deposit,
  * ion step on every ion_subcycle-th step, births and removals, periodic sort
  * every sort_every steps, field solve.  A plain ion cycle (ion_subcycle steps
@@ -341,11 +353,12 @@ int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, doub
  * caller's other streams; callers that manage device memory through their own
  * pool may not allocate behind it at all.  This variant takes the same
  * arguments and computes the same result (bit for bit), but keeps its scratch
- * in a fixed array built into the library: about 1.1 MB that every GPU which
+ * in a fixed array built into the library: 525 KiB that every GPU which
  * loads the library holds until the process exits.  It calls no allocator.
  *   n_cells    3 <= n_cells <= 65536; larger sizes return PIC_EINVAL
- *   the first call on a device looks up the array's device address (once per
- *   device, with that device current): make it before any stream capture
+ *   every call looks up the array's device address on the current device (no
+ *   allocation); the first call on a device also loads the library's device
+ *   code there: make it before any stream capture
  *   every call shares and overwrites the one array: calls that overlap on the
  *   GPU (other streams, other host threads on the same device) race; order them
  * Synchronises the stream before returning.  Errors are returned as codes only

@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
             raise ImportError(f"{LIBPATH} is missing: run paper_2202_03215_gb300.build.build() (nvcc, sm_103a)")
         L = C.CDLL(str(LIBPATH))
         L.pic_init.argtypes = [C.POINTER(Params), C.POINTER(C.c_void_p)]
+        L.pic_check_stability.argtypes = [C.POINTER(Params), _D]
         L.pic_step.argtypes = [C.c_void_p, C.c_int64]
         L.pic_moments.argtypes = [C.c_void_p, C.POINTER(MomentsOut)]
         L.pic_eepf_config.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_double]
@@ -221,6 +222,20 @@ def drive_ri(p) -> dict:
     return dict(E0_Vpm=out[0], n0_m3=out[1], Te0_eV=out[2], mu_iN=out[3])
 
 
+WARN_PLASMA_FREQ, WARN_DEBYE = 1, 2
+
+
+def check_stability(p) -> dict:
+    """pic_check_stability (host only): the resolution limits of Sec. II at the initial state,
+    w_pe dt < 0.2 and dx < lambda_De.  Returns the ratios and the PIC_WARN_* bits that fail."""
+    st, keep = make_params(p)
+    out = np.zeros(2)
+    rc = lib().pic_check_stability(C.byref(st), _ptr(out, _D))
+    if rc < 0:
+        _check(rc)
+    return {"wpe_dt": float(out[0]), "dx_over_lambda_De": float(out[1]), "warnings": int(rc)}
+
+
 def i128_to_double(values) -> np.ndarray:
     """Run the device int128 -> double conversion of the field solve on a list of Python ints."""
     vals = [int(v) for v in values]
@@ -235,7 +250,7 @@ def field_periodic(Q_i, Q_e, C_unit: float, E0: float, stream: int = 0):
     """Periodic Poisson solve on device tensors (int64 node charges, 2^32 per particle).
     Returns (E, E_half) as float64 device tensors of the same length."""
     import torch
-    n = Q_i.numel()
+    n = _check_field_tensors(Q_i, Q_e)
     E = torch.empty(n, dtype=torch.float64, device=Q_i.device)
     Eh = torch.empty_like(E)
     _check(lib().pic_field_periodic(Q_i.data_ptr(), Q_e.data_ptr(), n, C_unit, E0, E.data_ptr(), Eh.data_ptr(),
@@ -243,9 +258,32 @@ def field_periodic(Q_i, Q_e, C_unit: float, E0: float, stream: int = 0):
     return E, Eh
 
 
+def _check_field_tensors(Q_i, Q_e, E=None, E_half=None) -> int:
+    """Argument checks of the field solves: int64 node charges and float64 outputs, all
+    contiguous CUDA tensors on one device, each holding at least n = Q_i.numel() entries.
+    Raises ValueError before any device call; returns n."""
+    import torch
+    n = Q_i.numel()
+    dev = Q_i.device
+    for name, t, dt in (("Q_i", Q_i, torch.int64), ("Q_e", Q_e, torch.int64), ("E", E, torch.float64),
+                        ("E_half", E_half, torch.float64)):
+        if t is None:
+            continue
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_cuda or t.device != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on {dev}, got {t.device}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < n:
+            raise ValueError(f"{name} holds {t.numel()} entries, fewer than the {n} nodes")
+    return n
+
+
 def field_periodic_noalloc(Q_i, Q_e, C_unit: float, E0: float, E, E_half, stream: int = 0) -> None:
     """pic_field_periodic_noalloc: the same solve with caller-provided outputs E, E_half
     (float64 device tensors) and no device allocation inside the call."""
+    _check_field_tensors(Q_i, Q_e, E, E_half)
     rc = lib().pic_field_periodic_noalloc(Q_i.data_ptr(), Q_e.data_ptr(), Q_i.numel(), C_unit, E0,
                                           E.data_ptr(), E_half.data_ptr(), stream or None)
     if rc:
@@ -271,6 +309,12 @@ class Column:
         rc = self.L.pic_init(C.byref(st), C.byref(h))
         _check(rc)
         self.h = h
+        self.stability = check_stability(params)
+        if self.stability["warnings"]:
+            import warnings
+            warnings.warn(f"resolution limits of the explicit scheme not met: w_pe dt = "
+                          f"{self.stability['wpe_dt']:.3g} (< 0.2), dx / lambda_De = "
+                          f"{self.stability['dx_over_lambda_De']:.3g} (< 1)", stacklevel=2)
 
     def close(self) -> None:
         if getattr(self, "h", None):

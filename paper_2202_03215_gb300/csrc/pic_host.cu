@@ -44,7 +44,6 @@ struct pic_handle {
   pic::Ctl *ctl = nullptr;
   pic::SpeciesDev sp[2]{};
   double *E = nullptr, *Eh = nullptr;
-  long long *Dg = nullptr;            // field scratch when the nodes exceed shared memory
   pic::FieldScan *fs = nullptr;       // exact prefix data between the two field kernels
   pic::SortBuf sb[2]{};               // sort buffers per species (sort_every > 0)
   void *Ef = nullptr;                 // R[N+1]
@@ -379,7 +378,7 @@ template <class R> int run_init(pic_handle *h) {
   pic::launch_deposit<R>(k, h->sp[0], h->ctl, 0, h->stream);
   pic::launch_deposit<R>(k, h->sp[1], h->ctl, 1, h->stream);
   pic::launch_field<R>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<R *>(h->Ef), h->m,
-                       h->Dg, h->fs, false, false, h->stream);
+                       h->fs, false, false, h->stream);
   pic::launch_halfstep<R>(k, h->sp[0], h->ctl, reinterpret_cast<R *>(h->Ef), 0, h->stream);
   pic::launch_halfstep<R>(k, h->sp[1], h->ctl, reinterpret_cast<R *>(h->Ef), 1, h->stream);
   if (p.drive == PIC_DRIVE_CIRCUIT) pic::launch_sumv<R>(h->sp[1], h->ctl, 1, h->stream);
@@ -425,7 +424,7 @@ template <class R> int enqueue_step(pic_handle *h) {
   const bool diag = h->p.diag_every > 0 && (h->host_step % h->p.diag_every) == 0;
   t_begin(h);
   pic::launch_field<R>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<R *>(h->Ef), h->m,
-                       h->Dg, h->fs, diag, true, h->stream);
+                       h->fs, diag, true, h->stream);
   t_end(h, PIC_K_FIELD, (h->p.field_mode == PIC_FIELD_POISSON ? 2 : 1) + (diag ? 1 : 0));
   CU(h, cudaGetLastError());
   h->host_step++;
@@ -450,7 +449,7 @@ void free_all(pic_handle *h) {
     cudaFree(h->sb[q].cell); cudaFree(h->sb[q].rec); cudaFree(h->sb[q].id); cudaFree(h->sb[q].hist);
   }
   cudaFree(h->tabb);
-  cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->Dg); cudaFree(h->fs); cudaFree(h->Ef); cudaFree(h->gauss);
+  cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->fs); cudaFree(h->Ef); cudaFree(h->gauss);
   cudaFree(h->bb_mem); cudaFree(h->k3_mem); cudaFree(h->mom); cudaFree(h->mom_iz);
   cudaFree(h->stage); cudaFree(h->stage_bad); cudaFree(h->m.eepf);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -565,7 +564,6 @@ template <class R> pic::ColDev<R> coldev_of(pic_handle *c) {
   d.m = c->m;
   d.fk = c->fk;
   d.fs = c->fs;
-  d.Dg = c->Dg;
   d.N = c->N;
   pic::push_layout<R>(c->N, d.W, d.smemE);
   return d;
@@ -768,6 +766,26 @@ int pic_abi_version(void) { return PIC_ABI_VERSION; }
 
 const char *pic_last_error(pic_handle *h) { return h ? h->err.c_str() : g_err.c_str(); }
 
+int pic_check_stability(const pic_params *params, double out[2]) {
+  if (!params) return set_err(nullptr, PIC_EINVAL, "params is NULL");
+  if (int rc = check_finite(params)) return rc;
+  pic_params ri;
+  if (params->drive == PIC_DRIVE_RI) {   // the density of the column is the one eq. 2 gives
+    if (resolve_ri(params, &ri)) return set_err(nullptr, PIC_EINVAL, "the (R, I) drive has no solution");
+    params = &ri;
+  }
+  const pic_params &p = *params;
+  if (!(p.dt_s > 0) || !(p.L_m > 0) || p.n_cells < 1 || !(p.n0_m3 >= 0) || !(p.Te0_eV >= 0))
+    return set_err(nullptr, PIC_EINVAL, "dt, L, n_cells, n0 and Te0 must be positive");
+  // Sec. II: dt < 0.2 / w_pe and dx < lambda_De at the initial density and electron temperature
+  const double wpe = std::sqrt(p.n0_m3 * kQe * kQe / (kEps0 * kMe));
+  const double lde = p.n0_m3 > 0 ? std::sqrt(kEps0 * p.Te0_eV / (p.n0_m3 * kQe)) : HUGE_VAL;
+  const double dx = p.L_m / (double)p.n_cells;
+  const double r0 = wpe * p.dt_s, r1 = lde > 0 ? dx / lde : HUGE_VAL;
+  if (out) { out[0] = r0; out[1] = r1; }
+  return (r0 < 0.2 ? 0 : (int)PIC_WARN_PLASMA_FREQ) | (r1 < 1.0 ? 0 : (int)PIC_WARN_DEBYE);
+}
+
 int pic_init(const pic_params *params, pic_handle **out) {
   if (!out) return set_err(nullptr, PIC_EINVAL, "out is NULL");
   *out = nullptr;
@@ -814,7 +832,7 @@ int pic_init(const pic_params *params, pic_handle **out) {
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(set_err(h, PIC_ECUDA, "stream creation failed"));
   if (cudaMalloc(&h->ctl, sizeof(pic::Ctl)) != cudaSuccess || cudaMalloc(&h->E, (size_t)(h->N + 1) * 8) != cudaSuccess ||
-      cudaMalloc(&h->Eh, (size_t)h->N * 8) != cudaSuccess || cudaMalloc(&h->Dg, ((size_t)h->N + h->N / 16 + 1) * 8) != cudaSuccess ||
+      cudaMalloc(&h->Eh, (size_t)h->N * 8) != cudaSuccess ||
       cudaMalloc(&h->fs, sizeof(pic::FieldScan)) != cudaSuccess ||
       cudaMalloc(&h->gauss, (pic::kGaussN + 1) * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&h->k3_mem, (size_t)pic::kStageCap * 7 * 4) != cudaSuccess ||
@@ -1199,10 +1217,10 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
     // solve the field of the new charges without advancing the step counter
     if (h->mixed)
       pic::launch_field<float>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<float *>(h->Ef),
-                               h->m, h->Dg, h->fs, false, false, h->stream);
+                               h->m, h->fs, false, false, h->stream);
     else
       pic::launch_field<double>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh,
-                                reinterpret_cast<double *>(h->Ef), h->m, h->Dg, h->fs, false, false, h->stream);
+                                reinterpret_cast<double *>(h->Ef), h->m, h->fs, false, false, h->stream);
   }
   CU(h, cudaStreamSynchronize(h->stream));
   CU(h, cudaGetLastError());
@@ -1326,11 +1344,9 @@ int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, doub
   const int N = n_cells;
   pic::Ctl *ctl = nullptr;
   pic::FieldScan *fs = nullptr;
-  long long *Dg = nullptr;
   double *Ef = nullptr;
   int rc = 0;
   if (cudaMalloc(&ctl, sizeof(pic::Ctl)) != cudaSuccess || cudaMalloc(&fs, sizeof(pic::FieldScan)) != cudaSuccess ||
-      cudaMalloc(&Dg, ((size_t)N + N / 16 + 1) * 8) != cudaSuccess ||
       cudaMalloc(&Ef, ((size_t)N + 1) * 8) != cudaSuccess) {
     rc = set_err(nullptr, PIC_ENOMEM, "device allocation failed");
   } else {
@@ -1348,7 +1364,7 @@ int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, doub
     } else {
       pic::launch_field<double>(f, reinterpret_cast<const unsigned long long *>(Q_e),
                                 reinterpret_cast<const unsigned long long *>(Q_i), ctl, E, E_half, Ef, pic::Moments{},
-                                Dg, fs, false, false, st);
+                                fs, false, false, st);
       cudaError_t e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaMemcpyAsync(&c, ctl, sizeof c, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1356,7 +1372,7 @@ int pic_field_periodic(const int64_t *Q_i, const int64_t *Q_e, int n_cells, doub
       else if (c.status & pic::kStNonFinite) rc = set_err(nullptr, PIC_ENONFINITE, "the field became non-finite");
     }
   }
-  cudaFree(ctl); cudaFree(fs); cudaFree(Dg); cudaFree(Ef);
+  cudaFree(ctl); cudaFree(fs); cudaFree(Ef);
   return rc;
 }
 

@@ -141,7 +141,6 @@ template <class R> struct ColDev {
   Moments m;
   FieldK fk;
   FieldScan *fs;
-  long long *Dg;
   int W, smemE;   // shared-memory layout of the particle step for this column
   int N;
 };
@@ -179,8 +178,7 @@ void launch_births(const StepK<R> &k, SpeciesDev e, SpeciesDev i, Ctl *ctl, Birt
 // field solve; diag: take a diagnostic sample; advance: count the step
 template <class R>
 void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned long long *Qi, Ctl *ctl,
-                  double *E, double *Eh, R *Ef, Moments m, long long *Dg, FieldScan *fs, bool diag, bool advance,
-                  cudaStream_t st);
+                  double *E, double *Eh, R *Ef, Moments m, FieldScan *fs, bool diag, bool advance, cudaStream_t st);
 void launch_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n, cudaStream_t st);
 template <class R> int push_smem_bytes(int N);
 // shared-memory layout of the particle step for n_cells: bin window W, node field in shared memory

@@ -1282,9 +1282,7 @@ __global__ void __launch_bounds__(kFieldThreads, 1) k_field_diag_batch(const Col
 
 template <class R>
 void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned long long *Qi, Ctl *ctl, double *E,
-                  double *Eh, R *Ef, Moments m, long long *Dg, FieldScan *fs, bool diag, bool advance,
-                  cudaStream_t st) {
-  (void)Dg;
+                  double *Eh, R *Ef, Moments m, FieldScan *fs, bool diag, bool advance, cudaStream_t st) {
   const int nblk = (f.N + kEvalThreads - 1) / kEvalThreads;
   if (f.field_mode == PIC_FIELD_POISSON)
     k_field_reduce<R><<<nblk, kEvalThreads, 0, st>>>(f, Qe, Qi, fs, ctl, advance ? 1 : 0);
@@ -1412,8 +1410,7 @@ template <class R> void launch_sumv(SpeciesDev s, Ctl *ctl, int species, cudaStr
   template void launch_births<R>(const StepK<R> &, SpeciesDev, SpeciesDev, Ctl *, BirthBuf<R>, K3Scratch, int,      \
                                  cudaStream_t);                                                                      \
   template void launch_field<R>(const FieldK &, const unsigned long long *, const unsigned long long *, Ctl *,       \
-                                double *, double *, R *, Moments, long long *, FieldScan *, bool, bool,             \
-                                cudaStream_t);                                                                      \
+                                double *, double *, R *, Moments, FieldScan *, bool, bool, cudaStream_t);            \
   template int push_smem_bytes<R>(int);                                                                             \
   template void launch_sumv<R>(SpeciesDev, Ctl *, int, cudaStream_t);                                               \
   template size_t push_layout<R>(int, int &, int &);                                                                \

@@ -11,15 +11,13 @@
 // fixed array compiled into the library instead.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (about 1.1 MB) until the process exits.  Host code cannot
-// use the array's name as a device address, so the first call on each device
-// looks the address up with cudaGetSymbolAddress (with that device current)
-// and caches it; make that first call before any stream capture.  Every call
-// shares the one array and overwrites it, so calls that overlap on the GPU
-// (two streams, or two host threads on one device) race and must be ordered
-// by the caller.
-#include <mutex>
-
+// library holds it (525 KiB) until the process exits.  Host code cannot
+// use the array's name as a device address, so every call looks the address
+// up with cudaGetSymbolAddress on the current device (a lookup, no
+// allocation); the first call on a device also loads the library's device
+// code there, so make it before any stream capture.  Every call shares the
+// one array and overwrites it, so calls that overlap on the GPU (two streams,
+// or two host threads on one device) race and must be ordered by the caller.
 #include "pic_internal.cuh"
 
 namespace {
@@ -28,32 +26,20 @@ constexpr int kNoAllocMaxCells = 65536;
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffCtl = 0;
 constexpr size_t kOffScan = align256(sizeof(pic::Ctl));
-constexpr size_t kOffD = kOffScan + align256(sizeof(pic::FieldScan));
-constexpr size_t kOffEf = kOffD + align256(((size_t)kNoAllocMaxCells + kNoAllocMaxCells / 16 + 1) * 8);
+constexpr size_t kOffEf = kOffScan + align256(sizeof(pic::FieldScan));
 constexpr size_t kScratchBytes = kOffEf + align256(((size_t)kNoAllocMaxCells + 1) * 8);
 
-// scratch of the no-allocation field solve: control block, exact prefix data,
-// padded net-charge array, field copy; see the file comment for its rules
+// scratch of the no-allocation field solve: control block, block partials of
+// the exact prefix sums, field copy; see the file comment for its rules
 static __device__ __align__(256) unsigned char g_field_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_addr[kMaxDevices] = {};
-
-// device address of the scratch on the current device (looked up once per device)
+// device address of the scratch on the current device, looked up on every call
+// (a cached address would outlive a cudaDeviceReset, which reloads the module)
 cudaError_t scratch_address(unsigned char **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_field_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_field_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<unsigned char *>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<unsigned char *>(p);
   return cudaSuccess;
 }
 
@@ -71,7 +57,6 @@ int pic_field_periodic_noalloc(const int64_t *Q_i, const int64_t *Q_e, int n_cel
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   pic::Ctl *ctl = reinterpret_cast<pic::Ctl *>(base + kOffCtl);
   pic::FieldScan *fs = reinterpret_cast<pic::FieldScan *>(base + kOffScan);
-  long long *Dg = reinterpret_cast<long long *>(base + kOffD);
   double *Ef = reinterpret_cast<double *>(base + kOffEf);
   // the control block keeps the previous call's status: start it from zero
   pic::Ctl c{};
@@ -88,8 +73,8 @@ int pic_field_periodic_noalloc(const int64_t *Q_i, const int64_t *Q_e, int n_cel
   f.seg = (n_cells + pic::kFieldThreads - 1) / pic::kFieldThreads;
   f.Cf = C / ((double)n_cells * (double)n_cells);
   pic::launch_field<double>(f, reinterpret_cast<const unsigned long long *>(Q_e),
-                            reinterpret_cast<const unsigned long long *>(Q_i), ctl, E, E_half, Ef, pic::Moments{}, Dg,
-                            fs, false, false, st);
+                            reinterpret_cast<const unsigned long long *>(Q_i), ctl, E, E_half, Ef, pic::Moments{}, fs,
+                            false, false, st);
   e = cudaGetLastError();
   unsigned int status = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, &ctl->status, sizeof status, cudaMemcpyDeviceToHost, st);

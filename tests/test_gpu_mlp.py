@@ -33,20 +33,60 @@ def _data(n, seed):
     return X, T.astype(np.float32)
 
 
-def test_gradients_match_the_oracle():
+def _gelu_d(z):
+    c = np.sqrt(2 / np.pi)
+    th = np.tanh(c * (z + 0.044715 * z ** 3))
+    return 0.5 * (1 + th) + 0.5 * z * (1 - th * th) * c * (1 + 3 * 0.044715 * z * z)
+
+
+def _gradient_magnitudes(P, X, T):
+    """Per parameter, the sum over samples of the magnitudes of the terms its gradient adds up,
+    with magnitudes carried through the backward chain (|dy| |W3| |gelu'| ... ): the scale of
+    the rounding error each gradient element can collect (a running error bound)."""
+    W1, b1 = P[:1920].reshape(128, 15), P[1920:2048]
+    W2, b2 = P[2048:18432].reshape(128, 128), P[18432:18560]
+    W3, b3 = P[18560:18944].reshape(3, 128), P[18944:]
+    z1 = X @ W1.T + b1
+    c = np.sqrt(2 / np.pi)
+    a1 = 0.5 * z1 * (1 + np.tanh(c * (z1 + 0.044715 * z1 ** 3)))
+    z2 = a1 @ W2.T + b2
+    a2 = 0.5 * z2 * (1 + np.tanh(c * (z2 + 0.044715 * z2 ** 3)))
+    y = a2 @ W3.T + b3
+    dy = np.abs(2 * (y - T) / y.size)
+    m3 = dy.T @ np.abs(a2)
+    d2 = (dy @ np.abs(W3)) * np.abs(_gelu_d(z2))
+    m2 = d2.T @ np.abs(a1)
+    d1 = (d2 @ np.abs(W2)) * np.abs(_gelu_d(z1))
+    m1 = d1.T @ np.abs(X)
+    return np.concatenate([m1.ravel(), d1.sum(0), m2.ravel(), d2.sum(0), m3.ravel(), dy.sum(0)])
+
+
+# Element-wise bound of the GPU gradient against the oracle's (which rounds the same operands to
+# BF16): |g - g_oracle| <= C_BF16 * 2^-8 * (sum of the magnitudes of the gradient's terms).
+# 2^-8 is one BF16 unit in the last place relative to the value; the GPU's FP32 sums and its
+# hardware tanh can move a BF16 rounding to the neighbouring value on either factor of a term,
+# and the errors of the layers above propagate into the lower layers' terms.
+C_BF16 = 0.25   # measured worst 0.09 (W2) on a GB300
+
+
+def test_gradients_match_the_oracle_element_by_element():
     import torch
     P = _params(11)
     X, T = _data(300, 12)          # 5 tiles of 64, the last one ragged
     m = pb.Mlp()
     m.set_params(P)
     loss, g = m.grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
-    lo, _, go = oracle.mlp_forward_backward(P, X.astype(np.float64), T.astype(np.float64), bf16=True)
+    X64, T64 = X.astype(np.float64), T.astype(np.float64)
+    lo, _, go = oracle.mlp_forward_backward(P, X64, T64, bf16=True)
     assert abs(loss / lo - 1) < 1e-4
+    mag = _gradient_magnitudes(P, X64, T64)
+    ratio = np.abs(g - go) / (2.0 ** -8 * mag + 1e-30)
+    worst = {k: float(ratio[a:b].max()) for k, (a, b) in GROUPS.items()}
+    print("gradient error / (2^-8 sum|terms|), worst per group:", worst)
     for k, (a, b) in GROUPS.items():
-        err = np.linalg.norm(g[a:b] - go[a:b]) / np.linalg.norm(go[a:b])
-        assert err < 1e-2, (k, err)
+        assert worst[k] <= C_BF16, (k, worst[k], int(np.argmax(ratio[a:b])))
     # and against the unrounded FP64 network: the BF16 rounding error
-    _, _, g64 = oracle.mlp_forward_backward(P, X.astype(np.float64), T.astype(np.float64))
+    _, _, g64 = oracle.mlp_forward_backward(P, X64, T64)
     assert np.linalg.norm(g - g64) < 5e-2 * np.linalg.norm(g64)
 
 

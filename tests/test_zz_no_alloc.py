@@ -48,3 +48,18 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     out = torch.empty(65537, dtype=torch.float64, device="cuda")
     with pytest.raises(pb.PicError):
         pb.field_periodic_noalloc(q, q, C_UNIT, 0.0, out, out)
+
+
+def test_noalloc_binding_rejects_outputs_the_kernel_would_overrun():
+    import torch
+    qi, qe = _charges(1000, 4)
+    good = torch.empty(1000, dtype=torch.float64, device="cuda")
+    for bad in (torch.empty(1000, dtype=torch.float32, device="cuda"),
+                torch.empty(999, dtype=torch.float64, device="cuda"),
+                torch.empty(2000, dtype=torch.float64, device="cuda")[::2]):
+        with pytest.raises(ValueError):
+            pb.field_periodic_noalloc(qi, qe, C_UNIT, 0.0, bad, good)
+        with pytest.raises(ValueError):
+            pb.field_periodic_noalloc(qi, qe, C_UNIT, 0.0, good, bad)
+    with pytest.raises(ValueError):
+        pb.field_periodic_noalloc(qi, qe[:999], C_UNIT, 0.0, good, good)
