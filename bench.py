@@ -81,13 +81,28 @@ def ncu_traffic(n_e: int):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clock and throttle reasons during the timed region, by read-only NVML queries from a
+    sampling thread (every millisecond, plus one sample as it starts and one as it stops, so
+    that even a few-millisecond window has samples); nvidia-smi sampling where NVML cannot be
+    loaded."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
+        self.rows = []
+        self.p = None
+        self.nvml = self._nvml_handle(index)
+        if self.nvml is not None:
+            import threading
+            self.stop_ev = threading.Event()
+            self._sample()
+            self.th = threading.Thread(target=self._loop, daemon=True)
+            self.th.start()
+            return
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
@@ -96,7 +111,67 @@ class Clocks:
         except (OSError, FileNotFoundError):
             self.p = None
 
+    def _nvml_handle(self, index: int):
+        import ctypes as C
+        try:
+            L = C.CDLL("libnvidia-ml.so.1")
+            if L.nvmlInit_v2() != 0:
+                return None
+            cnt = C.c_uint(0)
+            if L.nvmlDeviceGetCount_v2(C.byref(cnt)) != 0 or cnt.value == 0:
+                return None
+            want = None
+            try:
+                import torch
+                want = str(torch.cuda.get_device_properties(index).uuid).lower()
+            except Exception:
+                pass
+            pick = None
+            for i in range(cnt.value):
+                h = C.c_void_p()
+                if L.nvmlDeviceGetHandleByIndex_v2(i, C.byref(h)) != 0:
+                    continue
+                buf = C.create_string_buffer(96)
+                if L.nvmlDeviceGetUUID(h, buf, 96) == 0 and want and want in buf.value.decode().lower():
+                    pick = h
+                    break
+            if pick is None:
+                h = C.c_void_p()
+                if L.nvmlDeviceGetHandleByIndex_v2(index if cnt.value > index else 0, C.byref(h)) != 0:
+                    return None
+                pick = h
+            reasons = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                L.nvmlDeviceGetCurrentClocksThrottleReasons
+            self._L, self._reasons = L, reasons
+            mx = C.c_uint(0)
+            self.max_mhz = float(mx.value) if L.nvmlDeviceGetMaxClockInfo(pick, 1, C.byref(mx)) == 0 else None
+            return pick
+        except (OSError, AttributeError):
+            return None
+
+    def _sample(self):
+        import ctypes as C
+        mhz, r, mw = C.c_uint(0), C.c_ulonglong(0), C.c_uint(0)
+        ok = self._L.nvmlDeviceGetClockInfo(self.nvml, 1, C.byref(mhz)) == 0
+        self._reasons(self.nvml, C.byref(r))
+        self._L.nvmlDeviceGetPowerUsage(self.nvml, C.byref(mw))
+        if ok:
+            self.rows.append((float(mhz.value), int(r.value), mw.value / 1e3))
+
+    def _loop(self):
+        while not self.stop_ev.wait(0.001):
+            self._sample()
+
     def stop(self):
+        if self.nvml is not None:
+            self.stop_ev.set()
+            self.th.join(5)
+            self._sample()
+            sm = [r[0] for r in self.rows]
+            reasons = sorted({name for r in self.rows for bit, name in self.REASONS.items() if r[1] & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(self.rows), "source": "nvml",
+                    "power_w_max": max(r[2] for r in self.rows) if self.rows else None}
         if self.p is None:
             return None
         self.p.terminate()
@@ -112,7 +187,7 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi"}
 
 
 def pushed_steps(s0: int, k: int, n_e: int, n_i: int, sub: int) -> int:
@@ -120,18 +195,50 @@ def pushed_steps(s0: int, k: int, n_e: int, n_i: int, sub: int) -> int:
     return k * n_e + ion_steps * n_i
 
 
-def oracle_rate(n_per_species: int, steps: int, warmup: int = 1):
-    """The CPU oracle as it stands (FP32-storage build, one thread) on a sample of the workload."""
+def oracle_rate(n_per_species: int, steps: int, warmup: int = 1, seed: int = 1):
+    """The CPU oracle as it stands (FP32-storage build, one thread) on a sample of the workload:
+    (pushed particle-steps, seconds) of `steps` timed steps."""
     import oracle
     from paper_2202_03215_gb300 import workloads as w
-    p = column_params(w, n_per_species)
+    p = column_params(w, n_per_species, seed=seed)
     o = oracle.Oracle(p)                       # resolves eq. 2 with the oracle's own two-term solve
     o.step(warmup)
     s0 = o.stats()["step"]
     t = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t
-    return pushed_steps(s0, steps, n_per_species, n_per_species, p.ion_subcycle) / dt, dt
+    return pushed_steps(s0, steps, n_per_species, n_per_species, p.ion_subcycle), dt
+
+
+def _oracle_worker(a):
+    return oracle_rate(*a)
+
+
+def oracle_rate_cores(n_per_species: int, steps: int, warmup: int = 1, procs: int | None = None):
+    """The oracle on every host core: one process per core (spawned, so that no process is forked
+    from one that has touched the GPU), each stepping its own sample of the column with its own
+    seed.  Rate = the units of all processes / the longest process's timed seconds."""
+    import multiprocessing as mp
+    procs = procs or len(os.sched_getaffinity(0)) or 1
+    if procs == 1:
+        units, dt = oracle_rate(n_per_species, steps, warmup)
+        return units / dt, dt, 1
+    # one thread per process: the numerical libraries of each child stay single-threaded
+    threads = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in threads}
+    os.environ.update({k: "1" for k in threads})
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [(n_per_species, steps, warmup, 1 + k) for k in range(procs)])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    units = sum(u for u, _ in res)
+    secs = max(d for _, d in res)
+    return units / secs, secs, procs
 
 
 def batched_vs_serial(pb, w, torch, steps: int, warmup: int, n_columns: int = 64):
@@ -153,6 +260,7 @@ def batched_vs_serial(pb, w, torch, steps: int, warmup: int, n_columns: int = 64
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3
     b.set_timing(True)
+    b.kernel_times()                        # the counts so far (all steps since the batch was made)
     b.step(sub)
     launches = sum(v[1] for v in b.kernel_times().values())
     b.set_timing(False)
@@ -315,6 +423,57 @@ def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: 
             "forward": {"samples": n, "samples_per_s": n / sf, "tflops": MLP_FWD_FLOP * n / sf / 1e12}}
 
 
+def timed_steps(col, torch, steps: int):
+    """Device milliseconds of `steps` steps on the column's stream (CUDA events)."""
+    ext = torch.cuda.ExternalStream(col.stream())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ext)
+    col.step(steps)
+    e1.record(ext)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def fp64_form_leg(pb, w, torch, n: int, steps: int = 300, warmup: int = 10):
+    """The throughput column in the plain FP64 form (32-byte double records): the same steps as
+    the precision form, and the electron step's fraction of the HBM bandwidth at 80 B per
+    electron (double record read + write, int32 cell read + write, id read)."""
+    p = column_params(w, n).with_(precision=w.FP64)
+    col = pb.Column(p)
+    col.step(warmup)
+    st0 = col.stats()
+    ms = timed_steps(col, torch, steps)
+    col.set_timing(True)
+    col.kernel_times()
+    timed_steps(col, torch, steps)
+    kt = col.kernel_times()
+    col.close()
+    units = pushed_steps(st0["step"], steps, st0["n_e"], st0["n_i"], p.ion_subcycle)
+    push_ms, push_n = kt["push_e"]
+    avg = push_ms / max(1, push_n) / 1e3
+    peak, kind = peaks()
+    return {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "electron_step_us": avg * 1e6, "bytes_per_electron": 80,
+            "electron_step_frac_of_hbm": 80 * st0["n_e"] / avg / 1e9 / peak, "peak_kind": kind,
+            "workload": "the throughput column with FP64 particle records"}
+
+
+def small_column_leg(pb, w, torch, steps: int = 2000, warmup: int = 20):
+    """The argon parity column (1 Torr, L = 5 cm, 500 cells, 1e5 + 1e5 particles, FP64, 20 V,
+    dt = 2e-11 s): microseconds per step with the ion cycles replayed as CUDA graphs.  8.8 MB
+    of state stay in L2, so the step is bound by launch latency, not by HBM."""
+    p = w.config_argon_small()
+    col = pb.Column(p)
+    col.step(warmup)
+    st0 = col.stats()
+    ms = timed_steps(col, torch, steps)
+    col.close()
+    units = pushed_steps(st0["step"], steps, st0["n_e"], st0["n_i"], p.ion_subcycle)
+    return {"us_per_step": ms * 1e3 / steps, "steps": steps, "value": units / (ms / 1e3), "unit": UNIT,
+            "workload": "argon 1 Torr, L=0.05 m, 500 cells, 1e5 + 1e5 particles, FP64, V=20 V, dt=2e-11 s"}
+
+
 def replica_params(w, rank: int, n_per_species: int):
     """The column of rank `rank` in a multi-GPU run: an independent replica of the neon column
     (its own seed and RNG column index), no data shared between ranks."""
@@ -342,16 +501,19 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    # each step one oracle step of a sample of the workload, sized so K steps take about two minutes
+    # each step one oracle step of a sample of the workload on every host core, sized so that K
+    # steps take about two minutes
     n = int(min(2_000_000, max(100_000, 120.0 * 2.5e7 / max(1, args.steps) / 1.1)))
-    rate, dt = oracle_rate(n, args.steps, warmup=min(args.warmup, 3))
-    cores = 1
+    rate, dt, cores = oracle_rate_cores(n, args.steps, warmup=min(args.warmup, 3))
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{n} electrons + {n} ions per step (same cells, dt, gas)"},
+            "config": {"workload": WORKLOAD,
+                       "sample": f"{n} electrons + {n} ions per step and process (same cells, dt, gas), "
+                                 f"{cores} processes"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle steps of {n}+{n} particles, {dt:.1f} s"},
+                             "sample": f"{args.steps} oracle steps of {n}+{n} particles in each of {cores} "
+                                       f"processes (one per core), {dt:.1f} s"},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -371,6 +533,8 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-eepf", action="store_true")
     ap.add_argument("--no-bounded", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -391,11 +555,12 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_s = 2_000_000
-        steps_s = 60
-        rate, dt = oracle_rate(n_s, steps_s)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        steps_s = 40
+        rate, dt, cores = oracle_rate_cores(n_s, steps_s)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{steps_s} oracle steps (FP32-storage build) of {n_s} electrons + {n_s} ions on the "
-                         f"same column, {dt:.1f} s of single-thread CPU"}
+                         f"same column in each of {cores} processes (one per core, own seeds), "
+                         f"{dt:.1f} s per process"}
 
     p = replica_params(w, rank, args.n)
     col = pb.Column(p)
@@ -437,6 +602,16 @@ def main():
     col.set_timing(False)
     assert col.stats()["step"] == st1["step"]
     launches = sum(v[1] for v in kt.values())
+    # the step amortised over a whole sort cycle: sort_every x ion_subcycle steps hold every
+    # electron sort and ion sort of the cycle in their proportion
+    cyc = p.sort_every * p.ion_subcycle
+    torch.cuda.synchronize()
+    e0.record(ext)
+    col.step(cyc)
+    e1.record(ext)
+    torch.cuda.synchronize()
+    amort = {"ms_per_step": e0.elapsed_time(e1) / cyc, "steps": cyc,
+             "sorts": {"electrons": cyc // p.sort_every, "ions": 1}}
     ms, units = aggregate(dist, torch, ms, units)
     value = units / (ms / 1e3)
 
@@ -500,6 +675,11 @@ def main():
         bnd = bounded_leg(pb, w, torch)
     if rank == 0 and world == 1 and not args.no_train:
         train = closure_training_leg(pb, torch)
+    fp64 = small = None
+    if rank == 0 and world == 1 and not args.no_fp64:
+        fp64 = fp64_form_leg(pb, w, torch, n=args.n)
+    if rank == 0 and world == 1 and not args.no_small:
+        small = small_column_leg(pb, w, torch)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -510,6 +690,7 @@ def main():
                            "l2": "inputs larger than L2 (state 1.1 GB)", "parallelism": f"replicas x{world}",
                            "pushed_particle_steps": units},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_vs_serial": batch,
+                "ms_per_step_amortized": amort, "fp64_form": fp64, "argon_small_column": small,
                 "fluid_screen": screen, "closure_training": train, "eepf": eepf, "bounded_column": bnd,
                 "gpu_launches": launches, "ms_per_step_instrumented": ms_inst / args.steps,
                 "kernel_ms": {k: v[0] for k, v in kt.items()}, "clocks": clocks}

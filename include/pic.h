@@ -380,8 +380,9 @@ int pic_field_periodic_noalloc(const int64_t *Q_i, const int64_t *Q_e, int n_cel
  * for Y, written) on the given stream (NULL: the default stream); nothing is retained after a
  * call.  Errors are returned as codes only (pic_last_error does not see them): PIC_EINVAL for
  * a NULL handle or array, n <= 0, or a parameter count other than pic_mlp_nparam();
- * PIC_ENOMEM; PIC_ECUDA; PIC_ETIMEOUT when a bounded wait on a weight copy gave up (the
- * kernels then return without writing and the status is cleared). */
+ * PIC_ENOMEM; PIC_ECUDA; PIC_ETIMEOUT when a bounded wait of the kernels gave up (the
+ * kernels then return without writing; the error latches until pic_mlp_set_params, see
+ * pic_mlp_test_hook). */
 typedef struct pic_mlp pic_mlp;
 int pic_mlp_nparam(void);
 /* weights and biases uniform in +-1/sqrt(fan_in) from a seeded generator */
@@ -400,6 +401,21 @@ int pic_mlp_grad(pic_mlp *m, const float *X, const float *T, int n, float *grad_
  * last_loss receives the loss of the last batch (before its update) */
 int pic_mlp_train(pic_mlp *m, const float *X, const float *T, int n, int batch, int steps, float lr,
                   double *last_loss, void *stream);
+
+/* Test instrumentation of the bounded waits (not part of the method; the paper has no
+ * counterpart).  Every wait of the network's kernels on an mbarrier gives up after `spin` polls
+ * (each suspends for at most 10 us); a wait that gives up makes the call return PIC_ETIMEOUT,
+ * leaves the parameters, the Adam state and the outputs unwritten, and latches: every later
+ * call on the handle returns PIC_ETIMEOUT until pic_mlp_set_params.  hook selects waits that
+ * are made to give up, with nothing ever arriving on their barrier (no copy or MMA is issued for
+ * them, so nothing is left in flight):
+ *   PIC_MLP_HOOK_NO_WEIGHT_COPY   the training kernel's copy of the BF16 weights
+ *   PIC_MLP_HOOK_NO_FORWARD_MMA   the first layer-1 MMA of one group of the forward kernel
+ * spin = 0 restores the default limit (200000 polls); hook = 0 ends the instrumentation.
+ * Synchronises the device.  PIC_EINVAL for a NULL handle, spin < 0 or unknown hook bits. */
+#define PIC_MLP_HOOK_NO_WEIGHT_COPY 1u
+#define PIC_MLP_HOOK_NO_FORWARD_MMA 2u
+int pic_mlp_test_hook(pic_mlp *m, unsigned hook, int spin);
 
 /* ------------------------------------------------------------------------
  * Electron transport of a uniform-field swarm from the two-term Boltzmann

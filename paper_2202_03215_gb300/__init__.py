@@ -223,6 +223,7 @@ def drive_ri(p) -> dict:
 
 
 WARN_PLASMA_FREQ, WARN_DEBYE = 1, 2
+MLP_HOOK_NO_WEIGHT_COPY, MLP_HOOK_NO_FORWARD_MMA = 1, 2
 
 
 def check_stability(p) -> dict:
@@ -503,6 +504,10 @@ class Mlp:
     def set_params(self, P) -> None:
         P = np.ascontiguousarray(P, dtype=np.float32)
         _check(self.L.pic_mlp_set_params(self.h, P.ctypes.data_as(C.POINTER(C.c_float)), len(P)))
+
+    def test_hook(self, hook: int, spin: int = 0) -> None:
+        """pic_mlp_test_hook: make the selected bounded waits give up after `spin` polls."""
+        _check(self.L.pic_mlp_test_hook(self.h, C.c_uint(hook), spin))
 
     def forward(self, X):
         import torch

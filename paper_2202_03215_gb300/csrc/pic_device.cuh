@@ -147,6 +147,9 @@ template <class R> __device__ __forceinline__ unsigned long long wfix(R off) {
   return (unsigned long long)(off * (R)4294967296.0);
 }
 
+// the same weight as a 32-bit integer: off < 1, so off 2^32 < 2^32 (exact in both precisions)
+template <class R> __device__ __forceinline__ uint32_t wfix32(R off) { return (uint32_t)(off * (R)4294967296.0); }
+
 // collision-table position; above the table the last value is held
 template <class R>
 __device__ __forceinline__ int tab_pos(R eps, R inv_de, int ntab, R &fr, bool &ovf) {

@@ -49,6 +49,7 @@ struct pic_handle {
   void *Ef = nullptr;                 // R[N+1]
   void *tab[2] = {nullptr, nullptr};  // R[np * ntab]
   void *tabb = nullptr;               // electron per-bin majorant and null-collision probability, R[2 ntab]
+  uint32_t *tabi = nullptr;           // FP32 form: the per-bin probabilities as 24-bit integer thresholds
   float *gauss = nullptr;
   void *bb_mem = nullptr;
   uint32_t *k3_mem = nullptr;
@@ -233,6 +234,7 @@ int check_status(pic_handle *h) {
   if (c.status) {
     if (c.status & pic::kStNonFinite) h->latched = set_err(h, PIC_ENONFINITE, "the field became non-finite");
     else if (c.status & pic::kStVictim) h->latched = set_err(h, PIC_ECAPACITY, "more births than particles to remove");
+    else if (c.status & pic::kStTimeout) h->latched = set_err(h, PIC_ETIMEOUT, "a bounded wait of the particle step gave up");
     else h->latched = set_err(h, PIC_ECAPACITY, "capacity exceeded (status 0x%x)", c.status);
   }
   return h->latched;
@@ -300,11 +302,20 @@ template <class R> int setup_tables(pic_handle *h) {
       CU(h, cudaMemcpy(h->tabb, bins.data(), bins.size() * sizeof(R), cudaMemcpyHostToDevice));
       k.sp[0].nub = reinterpret_cast<const R *>(h->tabb);
       k.sp[0].Pb = reinterpret_cast<const R *>(h->tabb) + n;
+      k.sp[0].Pbi = nullptr;
+      if (std::is_same<R, float>::value) {
+        std::vector<uint32_t> thr(n, 0u);
+        for (int i = 0; i < n; ++i) thr[i] = (uint32_t)std::ceil((double)bins[n + i] * 16777216.0);
+        CU(h, cudaMalloc(&h->tabi, thr.size() * 4));
+        CU(h, cudaMemcpy(h->tabi, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice));
+        k.sp[0].Pbi = h->tabi;
+      }
     }
     h->nustar[q] = mx;
     h->Pnull[q] = -std::expm1(-mx * dts[q]);
     pic::SpecK<R> &s = k.sp[q];
     s.P = (R)h->Pnull[q];
+    s.Pi = (uint32_t)std::ceil((double)s.P * 16777216.0);
     s.nus = (R)mx;
     s.inv_de = (R)((double)(n - 1) / emax[q]);
     s.K = (R)(0.5 * (q == 0 ? kMe : M) / kQe);
@@ -334,9 +345,9 @@ template <class R> int alloc_species(pic_handle *h) {
   const int64_t cap = h->sp[0].cap;
   for (int q = 0; q < 2; ++q) {
     pic::SpeciesDev &s = h->sp[q];
-    CU(h, cudaMalloc(&s.cell, (size_t)cap * 4));
-    CU(h, cudaMalloc(&s.rec, (size_t)cap * sizeof(typename pic::Rec<R>::T)));
-    CU(h, cudaMalloc(&s.id, (size_t)cap * 8));
+    CU(h, cudaMalloc(&s.cell, ((size_t)cap + pic::kPad) * 4));
+    CU(h, cudaMalloc(&s.rec, ((size_t)cap + pic::kPad) * sizeof(typename pic::Rec<R>::T)));
+    CU(h, cudaMalloc(&s.id, ((size_t)cap + pic::kPad) * 8));
     CU(h, cudaMalloc(&s.Q, (size_t)(h->N + 1) * 8));
     CU(h, cudaMalloc(&s.dead, (size_t)pic::kStageCap * 4));
     CU(h, cudaMemset(s.Q, 0, (size_t)(h->N + 1) * 8));
@@ -408,20 +419,20 @@ template <class R> int enqueue_step(pic_handle *h) {
   const bool circuit = h->p.drive == PIC_DRIVE_CIRCUIT;
   if (circuit) CU(h, cudaMemsetAsync(&h->ctl->sumv[0], 0, 8, h->stream));
   CU(h, cudaMemsetAsync(h->sp[0].Q, 0, (size_t)h->Nn * 8, h->stream));
+  const bool diag = h->p.diag_every > 0 && (h->host_step % h->p.diag_every) == 0;
   t_begin(h);
-  pic::launch_push<R>(k, h->sp[0], h->ctl, Ef, bbuf<R>(h), h->m, 0, h->nsm, h->stream);
+  pic::launch_push<R>(k, h->sp[0], h->ctl, Ef, bbuf<R>(h), h->m, 0, h->nsm, diag, h->stream);
   t_end(h, PIC_K_PUSH_E);
   if (ion_push) {
     CU(h, cudaMemsetAsync(h->sp[1].Q, 0, (size_t)h->Nn * 8, h->stream));
     if (circuit) CU(h, cudaMemsetAsync(&h->ctl->sumv[1], 0, 8, h->stream));
     t_begin(h);
-    pic::launch_push<R>(k, h->sp[1], h->ctl, Ef, bbuf<R>(h), h->m, 1, h->nsm, h->stream);
+    pic::launch_push<R>(k, h->sp[1], h->ctl, Ef, bbuf<R>(h), h->m, 1, h->nsm, diag, h->stream);
     t_end(h, PIC_K_PUSH_I);
   }
   t_begin(h);
   pic::launch_births<R>(k, h->sp[0], h->sp[1], h->ctl, bbuf<R>(h), h->sc, ion_push ? 1 : 0, h->stream);
   t_end(h, PIC_K_BIRTHS);
-  const bool diag = h->p.diag_every > 0 && (h->host_step % h->p.diag_every) == 0;
   t_begin(h);
   pic::launch_field<R>(h->fk, h->sp[0].Q, h->sp[1].Q, h->ctl, h->E, h->Eh, reinterpret_cast<R *>(h->Ef), h->m,
                        h->fs, diag, true, h->stream);
@@ -449,6 +460,7 @@ void free_all(pic_handle *h) {
     cudaFree(h->sb[q].cell); cudaFree(h->sb[q].rec); cudaFree(h->sb[q].id); cudaFree(h->sb[q].hist);
   }
   cudaFree(h->tabb);
+  cudaFree(h->tabi);
   cudaFree(h->ctl); cudaFree(h->E); cudaFree(h->Eh); cudaFree(h->fs); cudaFree(h->Ef); cudaFree(h->gauss);
   cudaFree(h->bb_mem); cudaFree(h->k3_mem); cudaFree(h->mom); cudaFree(h->mom_iz);
   cudaFree(h->stage); cudaFree(h->stage_bad); cudaFree(h->m.eepf);
@@ -628,20 +640,25 @@ template <class R> int enqueue_batch_step(pic_handle *b) {
     }
     t_end(b, PIC_K_SORT, nk);
   }
+  const bool diag = c0->p.diag_every > 0 && (b->host_step % c0->p.diag_every) == 0;
+  // the kernel without the optional work when no column needs it on this step
+  bool plain = !diag;
+  for (pic_handle *c : b->cols)
+    plain = plain && !(c->p.flags & PIC_FLAG_RECORD_CODES) && c->p.drive != PIC_DRIVE_CIRCUIT &&
+            c->p.loss_mode != PIC_LOSS_RADIAL;
   t_begin(b);
   pic::launch_zero_q_batch<R>(cd, ncol, 0, b->maxN, b->stream);
-  pic::launch_push_batch<R>(cd, b->sched, b->nsched[0], 0, b->push_smem, b->stream);
+  pic::launch_push_batch<R>(cd, b->sched, b->nsched[0], 0, b->push_smem, plain, b->stream);
   t_end(b, PIC_K_PUSH_E, 2);
   if (ion_push && b->nsched[1] > 0) {
     t_begin(b);
     pic::launch_zero_q_batch<R>(cd, ncol, 1, b->maxN, b->stream);
-    pic::launch_push_batch<R>(cd, b->sched + b->nsched[0], b->nsched[1], 1, b->push_smem, b->stream);
+    pic::launch_push_batch<R>(cd, b->sched + b->nsched[0], b->nsched[1], 1, b->push_smem, plain, b->stream);
     t_end(b, PIC_K_PUSH_I, 2);
   }
   t_begin(b);
   pic::launch_births_batch<R>(cd, ncol, ion_push ? 1 : 0, b->stream);
   t_end(b, PIC_K_BIRTHS);
-  const bool diag = c0->p.diag_every > 0 && (b->host_step % c0->p.diag_every) == 0;
   t_begin(b);
   pic::launch_field_batch<R>(cd, ncol, b->maxN, c0->p.field_mode == PIC_FIELD_POISSON, diag, b->stream);
   t_end(b, PIC_K_FIELD, (c0->p.field_mode == PIC_FIELD_POISSON ? 2 : 1) + (diag ? 1 : 0));

@@ -21,6 +21,10 @@ constexpr unsigned kStCapacity = 2u;
 constexpr unsigned kStNonFinite = 4u;
 constexpr unsigned kStDeadOverflow = 8u;
 constexpr unsigned kStVictim = 16u;
+constexpr unsigned kStTimeout = 32u;    // a bounded wait of the particle step gave up
+// particle arrays hold this many slots past their capacity: the bulk copies of a tile round its
+// length up to a multiple of 4 slots
+constexpr int kPad = 64;
 
 // random-number streams (counter word 3 = stream<<28 | column<<16 | block)
 enum Stream : uint32_t { kStE = 0, kStI = 1, kStInitE = 2, kStInitI = 3, kStVicE = 4, kStVicI = 5, kStEmit = 6 };
@@ -70,6 +74,10 @@ template <class R> struct SpecK {
   R thr[kMaxProc];
   const R *tab;                   // np x ntab collision frequencies
   const R *nub, *Pb;              // electrons: per energy bin majorant and its null-collision probability
+  // FP32 form: the null-collision tests as integer compares on the top 24 bits of the decision
+  // word, (w >> 8) < ceil(P 2^24), the same decision as the FP32 compare (w >> 8) 2^-24 < P
+  const uint32_t *Pbi;            // electrons, per energy bin
+  uint32_t Pi;                    // the species' global P_null
 };
 
 template <class R> struct StepK {
@@ -171,7 +179,7 @@ void launch_halfstep(const StepK<R> &k, SpeciesDev s, const Ctl *ctl, const R *E
 template <class R> void launch_sumv(SpeciesDev s, Ctl *ctl, int species, cudaStream_t st);
 template <class R>
 void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBuf<R> bb, Moments m,
-                 int species, int nsm, cudaStream_t st);
+                 int species, int nsm, bool diag_step, cudaStream_t st);
 template <class R>
 void launch_births(const StepK<R> &k, SpeciesDev e, SpeciesDev i, Ctl *ctl, BirthBuf<R> bb, K3Scratch sc,
                    int ion_pushed, cudaStream_t st);
@@ -187,7 +195,7 @@ template <class R> size_t push_layout(int n_cells, int &W, int &smemE);
 // batched columns (one launch per phase for all columns)
 template <class R> void launch_zero_q_batch(const ColDev<R> *cols, int ncol, int species, int maxN, cudaStream_t st);
 template <class R>
-void launch_push_batch(const ColDev<R> *cols, const int4 *sched, int nblocks, int species, size_t smem,
+void launch_push_batch(const ColDev<R> *cols, const int4 *sched, int nblocks, int species, size_t smem, bool plain,
                        cudaStream_t st);
 template <class R> void launch_births_batch(const ColDev<R> *cols, int ncol, int ion_pushed, cudaStream_t st);
 template <class R>

@@ -43,6 +43,17 @@ template <class R> __device__ __forceinline__ void rec_store(void *base, long lo
     __stcs(q + 1, make_double2(vy, vz));
   }
 }
+// a record written earlier in the same kernel, read from L2 (not through L1)
+template <class R> __device__ __forceinline__ void rec_load_l2(const void *base, long long p, R &off, R &vx, R &vy, R &vz) {
+  if constexpr (std::is_same<R, float>::value) {
+    const float4 r = __ldcg(reinterpret_cast<const float4 *>(base) + p);
+    off = r.x; vx = r.y; vy = r.z; vz = r.w;
+  } else {
+    const double2 *q = reinterpret_cast<const double2 *>(reinterpret_cast<const D4 *>(base) + p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    off = a.x; vx = a.y; vy = b.x; vz = b.y;
+  }
+}
 template <class R> __device__ __forceinline__ R rec_get_off(const void *base, long long p) {
   if constexpr (std::is_same<R, float>::value) return reinterpret_cast<const float4 *>(base)[p].x;
   else return reinterpret_cast<const D4 *>(base)[p].off;
@@ -86,48 +97,70 @@ __device__ void bitonic_sort(unsigned long long *a, int n2) {
 
 // ---------------------------------------------------------------------------
 // Particle step.  One persistent CTA per SM walks a contiguous slot range in
-// tiles of blockDim particles.
+// tiles of particles.
 //   phase A (every particle): gather, leapfrog push, wrap, the Philox block
 //     that decides collision candidacy (u0 < P_null) and radial loss, the
-//     cloud-in-cell deposit (into 64-bit fixed-point bins in shared memory
-//     over a cell window, one atomic update per particle), and the store of
-//     every non-candidate; candidates go to a shared-memory queue;
+//     cloud-in-cell deposit (into fixed-point bins in shared memory over a
+//     cell window: three 32-bit additions per particle whose results are not
+//     read), and the store of every non-candidate; candidates go to a
+//     shared-memory queue;
 //   phase B (whenever a warp has queued 32 candidates, and at the end): the
 //     collision path for 32 queued candidates, one per lane, so that a warp
 //     runs it densely instead of whenever any of its lanes collides.
-// Every warp owns its queue (64 entries): no block-wide barrier in the loop,
-// so the warps' memory latencies overlap freely.  Collisions change
-// velocities only, so the deposit in phase A is final.
+// Every compute warp owns its queue (64 entries).  The only block-wide
+// barriers of the loop are the rare bin flushes (every flush_tiles tiles), so
+// the warps' memory latencies overlap freely.  Collisions change velocities
+// only, so the deposit in phase A is final.
+//
+// MIXED form: the particles of the next kStages tiles are staged in shared
+// memory while a tile is processed.  Two ways are built (PIC_STAGING):
+//   1  every thread copies its own particle of each tile with asynchronous
+//      copies (cp.async of 4, 16 and 8 bytes, one commit group per tile and
+//      thread) and reads back only what it copied, so no warp waits for another;
+//   2  the last warp of the CTA is a copy warp: one of its threads stages each
+//      tile as three contiguous ranges (int32 cells, float4 records, ids) with
+//      bulk asynchronous copies (the TMA engine) that complete on the stage's
+//      "full" mbarrier; the compute warps wait on it, read their particle and
+//      release the stage through its "empty" mbarrier.
+// FP64 form: every warp computes and the next tile's particle is prefetched in
+// registers.
+#ifndef PIC_STAGING
+#define PIC_STAGING 1
+#endif
+#ifndef PIC_STAGES
+#define PIC_STAGES 2
+#endif
 
-constexpr int kWarpQ = 64;                               // queue entries per warp
-constexpr int kQcap = (kStepThreads / 32) * kWarpQ;      // queue entries per CTA
+constexpr int kWarpQ = 64;           // queue entries per compute warp
+constexpr int kStages = PIC_STAGES;  // tiles in flight (MIXED form)
+constexpr int kStageSpin = 1 << 18;  // polls of a stage barrier (each suspends up to 10 us) before giving up
 
-template <class R> struct Queue {
-  uint64_t *id;
-  R *off, *vx, *vy, *vz, *u1;
-  int32_t *slot, *cell;
-};
-
-template <class R> __device__ __forceinline__ Queue<R> queue_at(unsigned char *q) {
-  Queue<R> Q;
-  Q.id = reinterpret_cast<uint64_t *>(q);
-  Q.off = reinterpret_cast<R *>(Q.id + kQcap);
-  Q.vx = Q.off + kQcap;
-  Q.vy = Q.vx + kQcap;
-  Q.vz = Q.vy + kQcap;
-  Q.u1 = Q.vz + kQcap;
-  Q.slot = reinterpret_cast<int32_t *>(Q.u1 + kQcap);
-  Q.cell = Q.slot + kQcap;
-  return Q;
+template <class R> __host__ __device__ constexpr bool staged() { return std::is_same<R, float>::value; }
+// 0: register prefetch (FP64 form), 1: per-thread asynchronous copies, 2: copy warp + bulk copies
+template <class R> __host__ __device__ constexpr int stage_mode() { return staged<R>() ? PIC_STAGING : 0; }
+template <class R> __host__ __device__ constexpr int compute_warps() {
+  return kStepThreads / 32 - (stage_mode<R>() == 2 ? 1 : 0);
 }
-template <class R> __host__ __device__ constexpr size_t queue_bytes() { return (size_t)kQcap * (8 + 5 * sizeof(R) + 8); }
+template <class R> __host__ __device__ constexpr int tile_of() { return compute_warps<R>() * 32; }
+// tiles between two flushes of the shared-memory bins: a cell of the window then receives fewer
+// than 2^16 particles in between, so the 16-bit halves of the weights sum without overflow
+template <class R> __host__ __device__ constexpr int flush_tiles() { return 65535 / tile_of<R>(); }
 
-// MIXED form: every thread stages its particles of the next kStages tiles (cell, float4 record,
-// id) in shared memory with asynchronous copies, so that two tiles per thread are in flight
-// without holding registers; each thread reads back only what it copied itself
-constexpr int kStages = 2;
+// queued candidates: the slot and the raw 32-bit word of the process-choice uniform, 8 bytes; the
+// candidate's cell, record and id were written to (or stay in) the particle arrays in phase A and
+// are read back from L2 when its warp runs the collision path
+template <class R> __host__ __device__ constexpr int queue_cap() { return compute_warps<R>() * kWarpQ; }
+template <class R> __host__ __device__ constexpr size_t queue_bytes() { return (size_t)queue_cap<R>() * 8; }
+
+// MIXED form: the first kPbHot per-bin null-collision thresholds of the electrons (the energies
+// where nearly every electron is: 50 eV on a 200 eV table of 8193 points) are read from shared
+// memory, the rest through L1
+constexpr int kPbHot = 2048;
+template <class R> __host__ __device__ constexpr size_t pbhot_bytes() { return staged<R>() ? (size_t)kPbHot * 4 : 0; }
+
+// MIXED form: kStages stages of one tile each: int32 cells, float4 records, ids
 template <class R> __host__ __device__ constexpr size_t stage_bytes() {
-  return std::is_same<R, float>::value ? (size_t)kStages * kStepThreads * (4 + 16 + 8) : 0;
+  return staged<R>() ? (size_t)kStages * tile_of<R>() * (4 + 16 + 8) : 0;
 }
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
@@ -142,6 +175,40 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int G> __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, unsigned bytes) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+// bounded wait for the completion of the barrier's phase of the given parity: false if the polls ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, int limit) {
+  for (int i = 0; i < limit; ++i) {
+    unsigned ok;
+    asm volatile("{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, 10000;\nselp.b32 %0, 1, 0, P;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(b)), "r"(parity)
+                 : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// bulk copy global -> shared (16-byte aligned addresses, a multiple of 16 bytes), completing on bar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
 // round(256 vx) to nearest even, as an integer (exact, order independent sums)
@@ -281,85 +348,94 @@ __device__ __forceinline__ int collide(const StepK<R> &k, const SpecK<R> &sp, Ct
   return sel;
 }
 
-// 64-bit fixed-point add into a shared-memory word pair: native 32-bit
-// atomics, the carry of the low word propagated exactly
-__device__ __forceinline__ void add64(unsigned *lo, unsigned *hi, unsigned long long v) {
-  const unsigned vlo = (unsigned)v;
-  const unsigned vhi = (unsigned)(v >> 32);
-  const unsigned old = atomicAdd(lo, vlo);
-  const unsigned c = vhi + ((old + vlo < old) ? 1u : 0u);
-  if (c) atomicAdd(hi, c);
-}
-
 // bytes of the shared-memory bins of W cells, rounded so that what follows stays 16-byte aligned
 __host__ __device__ constexpr size_t bins_bytes(int W) { return ((size_t)W * 12 + 15) & ~(size_t)15; }
 
-// Shared-memory charge bins per cell of a window [c0, c0 + W): particle count
-// and the sum of the cloud-in-cell weights k (64-bit).  Cell c's particles
-// give node c: n 2^32 - sum k and node c+1: sum k, applied at the flush.
+// Shared-memory charge bins per cell of a window [c0, c0 + W): the particle count and the sums
+// of the low and high 16-bit halves of the cloud-in-cell weights k.  Cell c's n particles give
+// node c: n 2^32 - sum k and node c+1: sum k, added at a flush.  Between two flushes a cell
+// receives fewer than 2^16 particles, so no 32-bit sum overflows.
 struct CellBins {
   unsigned *cnt, *klo, *khi;
   int W, c0;
 };
 
-// n particles of cell `cell` with summed weight sk
-__device__ __forceinline__ void cell_add(const CellBins &b, int N, int Nw, int32_t cell, unsigned n,
-                                         unsigned long long sk, unsigned long long *Q) {
+// one particle of cell `cell` with weight k into the window's bins (three additions whose
+// results are not read), or, outside the window, straight into the node charges
+__device__ __forceinline__ void deposit_one(const CellBins &b, int N, int Nw, int32_t cell, uint32_t k,
+                                            unsigned long long *Q) {
   int li = cell;
   if (b.W < N) {
     li = cell - b.c0;
     if (li < 0) li += N;
   }
   if (li < b.W) {
-    atomicAdd(b.cnt + li, n);
-    add64(b.klo + li, b.khi + li, sk);
+    atomicAdd(b.cnt + li, 1u);
+    atomicAdd(b.klo + li, k & 0xffffu);
+    atomicAdd(b.khi + li, k >> 16);
   } else {
     const int c1 = (cell + 1 == Nw) ? 0 : cell + 1;
-    atomicAdd(Q + cell, ((unsigned long long)n << 32) - sk);
-    atomicAdd(Q + c1, sk);
+    atomicAdd(Q + cell, (1ull << 32) - (unsigned long long)k);
+    atomicAdd(Q + c1, (unsigned long long)k);
   }
 }
 
-// Deposit of one particle into the CTA's shared-memory bins (lanes with in == false contribute
-// nothing).  Lanes of a warp that share a cell are serialised by the shared-memory atomics;
-// that costs less than summing runs of equal cells with warp shuffles first, even right after
-// a sort, when most lanes of a warp share a cell.
-__device__ __forceinline__ void deposit(bool in, int32_t cell, unsigned long long kk, int N, int Nw, const CellBins &b,
-                                        unsigned long long *Q) {
-  if (in) cell_add(b, N, Nw, cell, 1u, kk, Q);
+// add the bins to the node charges and clear them (threads t0, t0 + nt, ... of the CTA)
+__device__ __forceinline__ void bins_flush(const CellBins &b, int N, int Nw, unsigned long long *Q, int t0, int nt) {
+  for (int j = t0; j < b.W; j += nt) {
+    const unsigned nq = b.cnt[j];
+    if (nq) {
+      const unsigned long long sk = ((unsigned long long)b.khi[j] << 16) + (unsigned long long)b.klo[j];
+      int cell = j;
+      if (b.W < N) { cell = b.c0 + j; if (cell >= N) cell -= N; }
+      const int c1 = (cell + 1 == Nw) ? 0 : cell + 1;
+      atomicAdd(Q + cell, ((unsigned long long)nq << 32) - sk);
+      if (sk) atomicAdd(Q + c1, sk);
+      b.cnt[j] = 0u;
+      b.klo[j] = 0u;
+      b.khi[j] = 0u;
+    }
+  }
 }
 
 // one CTA's share (cta of ncta) of the particle step of one column; PK: k is a launch
-// parameter (the Philox round keys are read from it as constants)
-template <class R, int SP, bool PK, bool BD>
+// parameter (the Philox round keys are read from it as constants); PL: a plain step (no
+// process codes, no diagnostic sample, no circuit sums, no radial losses), compiled without
+// those branches
+template <class R, int SP, bool PK, bool BD, bool PL = false>
 __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef,
                                           BirthBuf<R> bb, Moments m, int W, int smemE, int cta, int ncta,
                                           unsigned char *smem) {
   __shared__ unsigned int s_cnt[kMaxProc + 1];
+  __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages];
+  constexpr int kMode = stage_mode<R>();
+  constexpr bool kStg = kMode == 2;        // copy warp and bulk copies
+  constexpr int CW = compute_warps<R>();   // compute warps (with a copy warp: all but the last)
+  constexpr int TILE = tile_of<R>();
+  constexpr int FT = flush_tiles<R>();
   const int N = k.N, Nw = N + (BD ? 1 : 0);
   constexpr bool bounded = BD;   // a bounded column (Sec. V), a separate instantiation
   const SpecK<R> &sp = k.sp[SP];
-  const size_t eb = smemE ? ((((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15) : 0;
-  R *sE = reinterpret_cast<R *>(smem);
+  const size_t eb = (smemE ? ((((size_t)N + 1) * sizeof(R) + 15) & ~(size_t)15) : 0) + pbhot_bytes<R>();
+  R *sE = reinterpret_cast<R *>(smem + pbhot_bytes<R>());
+  uint32_t *sPb = reinterpret_cast<uint32_t *>(smem);   // MIXED form: hot null-collision thresholds
   CellBins bins;
   bins.cnt = reinterpret_cast<unsigned *>(smem + eb);
   bins.klo = bins.cnt + W;
   bins.khi = bins.klo + W;
   bins.W = W;
-  const Queue<R> Qd = queue_at<R>(smem + eb + bins_bytes(W));
-  constexpr bool kStg = std::is_same<R, float>::value;
+  uint2 *Qd = reinterpret_cast<uint2 *>(smem + eb + bins_bytes(W));
   unsigned char *stg = smem + eb + bins_bytes(W) + queue_bytes<R>();
-  int32_t *g_cell = reinterpret_cast<int32_t *>(stg);                                  // [kStages][threads]
-  float4 *g_rec = reinterpret_cast<float4 *>(stg + (size_t)kStages * kStepThreads * 4);
-  uint64_t *g_id = reinterpret_cast<uint64_t *>(stg + (size_t)kStages * kStepThreads * 20);
   const long long n = ctl->n[SP];
   const long long stepll = ctl->step;
   const uint32_t step = (uint32_t)stepll;
-  const bool diag = k.diag_every > 0 && (stepll % k.diag_every) == 0;
+  const bool diag = !PL && k.diag_every > 0 && (stepll % k.diag_every) == 0;
   const uint2 key = seed_key(k.seed);
   const uint32_t c3 = ((SP == 0 ? (uint32_t)kStE : (uint32_t)kStI) << 28) | (k.column << 16);
-  const long long chunk = (n + ncta - 1) / ncta;
-  const long long p0 = (long long)cta * chunk;
+  // slot range of this CTA; the chunk is a multiple of 4 slots, so that every tile starts on a
+  // 16-byte boundary of the int32 and uint64 arrays
+  const long long chunk = (((n + ncta - 1) / ncta) + 3) & ~3ll;
+  const long long p0 = min(n, (long long)cta * chunk);
   const long long p1 = min(n, p0 + chunk);
   int c0 = 0;
   if (W < N && p0 < p1) {
@@ -367,193 +443,260 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     if (c0 < 0) c0 += N;
   }
   bins.c0 = c0;
+  // slots fit in 32 bits (the capacity is at most INT32_MAX)
+  const int ip0 = (int)p0, ip1 = (int)p1;
+  const int ntiles = ip1 > ip0 ? (ip1 - ip0 + TILE - 1) / TILE : 0;
+  // per-thread asynchronous copies: this thread's particle of tile tt into stage tt % kStages
+  auto stage_in = [&](int tt) {
+    const int p = ip0 + tt * TILE + (int)threadIdx.x;
+    if (tt < ntiles && p < ip1) {
+      unsigned char *sb = stg + (size_t)(tt % kStages) * TILE * 28;
+      cp_async4(reinterpret_cast<int32_t *>(sb) + threadIdx.x, s.cell + p);
+      cp_async16(reinterpret_cast<float4 *>(sb + (size_t)TILE * 4) + threadIdx.x,
+                 reinterpret_cast<const float4 *>(s.rec) + p);
+      cp_async8(reinterpret_cast<uint64_t *>(sb + (size_t)TILE * 20) + threadIdx.x, s.id + p);
+    }
+    cp_async_commit();
+  };
+  // the first tiles are in flight while the field and the tables are staged
+  if constexpr (kMode == 1)
+    for (int tt = 0; tt < kStages; ++tt) stage_in(tt);
+  if constexpr (staged<R>() && SP == 0)
+    for (int j = threadIdx.x; j < kPbHot && j < k.ntab; j += blockDim.x) sPb[j] = __ldg(sp.Pbi + j);
   if (smemE)
     for (int j = threadIdx.x; j <= N; j += blockDim.x) sE[j] = Ef[j];
   for (int j = threadIdx.x; j < W; j += blockDim.x) { bins.cnt[j] = 0u; bins.klo[j] = 0u; bins.khi[j] = 0u; }
   if (threadIdx.x <= kMaxProc) s_cnt[threadIdx.x] = 0u;
+  if (kStg && threadIdx.x == 0) {
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&s_full[q], 1);
+      mbar_init(&s_empty[q], CW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
   const R *E = smemE ? sE : Ef;
   const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const bool radial = k.loss_mode == PIC_LOSS_RADIAL;
-  const bool record = (k.flags & PIC_FLAG_RECORD_CODES) != 0;
-  const int qoff = (threadIdx.x >> 5) * kWarpQ;   // this warp's queue slice
-  int wq = 0;                                     // its length (warp-uniform)
-  const bool circuit = k.drive == PIC_DRIVE_CIRCUIT;
-  long long vsum = 0;                             // circuit drive: this thread's sum of round(256 vx)
+  const int warp = threadIdx.x >> 5;
 
-  // collision path for the warp's first nq (<= 32) queued candidates, one per lane
-  auto flush = [&](int nq) {
-    int sel = -1;
-    bool ovf = false;
-    if (lane < nq) {
-      const int i = qoff + lane;
-      const int32_t qp = Qd.slot[i], qcell = Qd.cell[i];
-      const R qoff_ = Qd.off[i];
-      R qx = Qd.vx[i], qy = Qd.vy[i], qz = Qd.vz[i];
-      sel = collide<R, SP, BD>(k, sp, ctl, bb, m, Qd.id[i], step, c3, qp, qcell, qoff_, Qd.u1[i], qx, qy, qz, ovf);
-      rec_store<R>(s.rec, qp, qoff_, qx, qy, qz);
-      if (record) s.code[qp] = sel >= 0 ? sp.xs[sel] : -1;
-      if (diag) add_moments<R, SP>(sp, m, N, Nw, qcell, qoff_, qx, qy, qz);
-      if (circuit) vsum += vfix(qx);
+  if (kStg && warp == CW) {
+    // copy warp: one thread stages tile t in stage t % kStages once the compute warps have
+    // released that stage's previous tile
+    if (lane == 0) {
+      int t = 0;
+      for (; t < ntiles; ++t) {
+        const int st = t % kStages;
+        if (t >= kStages && !mbar_wait(&s_empty[st], (unsigned)((t / kStages - 1) & 1), kStageSpin)) {
+          atomicOr(&ctl->status, kStTimeout);
+          break;
+        }
+        const int base = ip0 + t * TILE;
+        const int cnt = min(TILE, ip1 - base);
+        const unsigned c4 = (unsigned)((cnt + 3) & ~3);   // the arrays are padded past the capacity
+        unsigned char *sb = stg + (size_t)st * TILE * 28;
+        mbar_expect_tx(&s_full[st], c4 * 28u);
+        bulk_g2s(sb, s.cell + base, c4 * 4u, &s_full[st]);
+        bulk_g2s(sb + (size_t)TILE * 4, reinterpret_cast<const float4 *>(s.rec) + base, c4 * 16u, &s_full[st]);
+        bulk_g2s(sb + (size_t)TILE * 20, s.id + base, c4 * 8u, &s_full[st]);
+      }
+      // no copy may still be landing when the CTA exits: wait for the last tiles issued (they
+      // have landed already unless a compute warp gave up)
+      for (int u = t - kStages; u < t; ++u)
+        if (u >= 0 && !mbar_wait(&s_full[u % kStages], (unsigned)((u / kStages) & 1), kStageSpin))
+          atomicOr(&ctl->status, kStTimeout);
     }
-    for (int q = 0; q < sp.np; ++q) {
-      const unsigned b = __ballot_sync(kFull, sel == q);
-      if (lane == 0 && b) atomicAdd(&s_cnt[q], (unsigned)__popc(b));
-    }
-    const unsigned bo = __ballot_sync(kFull, ovf);
-    if (lane == 0 && bo) atomicAdd(&s_cnt[kMaxProc], (unsigned)__popc(bo));
-    __syncwarp();
-  };
-
-  // software pipeline.  MIXED form: the particles of the next two tiles are in flight as
-  // asynchronous copies into shared memory (one commit group per tile and thread); FP64 form:
-  // the next tile's particle is loaded into registers while this one is processed
-  auto stage_in = [&](int base, int sidx) {
-    const int p = base + threadIdx.x;
-    if (p < (int)p1) {
-      const int q = sidx * kStepThreads + threadIdx.x;
-      cp_async4(g_cell + q, s.cell + p);
-      cp_async16(g_rec + q, reinterpret_cast<const float4 *>(s.rec) + p);
-      cp_async8(g_id + q, s.id + p);
-    }
-    cp_async_commit();
-  };
-  int32_t n_cell = 0;
-  R n_off = 0, n_vx = 0, n_vy = 0, n_vz = 0;
-  uint64_t n_id = 0;
-  if constexpr (kStg) {
-    stage_in((int)p0, 0);
-    stage_in((int)p0 + blockDim.x, 1);
   } else {
-    const int p = (int)p0 + threadIdx.x;
-    if (p < (int)p1) {
-      n_cell = s.cell[p];
-      rec_load<R>(s.rec, p, n_off, n_vx, n_vy, n_vz);
-      n_id = s.id[p];
-    }
-  }
-  int sidx = 0;   // stage of this tile (MIXED form)
-  for (int base = (int)p0; base < (int)p1; base += blockDim.x) {
-    const int p = base + threadIdx.x;
-    const bool valid = p < (int)p1;
-    bool cand = false, dead = false;
-    int32_t cell = n_cell;
-    R off = n_off, vx = n_vx, vy = n_vy, vz = n_vz, u1 = 0;
-    uint64_t id = n_id;
-    if constexpr (kStg) {
-      cp_async_wait<kStages - 1>();   // this tile's group has landed
-      if (valid) {
-        const int q = sidx * kStepThreads + threadIdx.x;
-        cell = g_cell[q];
-        const float4 r = g_rec[q];
-        off = r.x; vx = r.y; vy = r.z; vz = r.w;
-        id = g_id[q];
+    const unsigned lt = (1u << lane) - 1u;
+    const bool radial = !PL && k.loss_mode == PIC_LOSS_RADIAL;
+    const bool record = !PL && (k.flags & PIC_FLAG_RECORD_CODES) != 0;
+    const int qoff = warp * kWarpQ;   // this warp's queue slice
+    int wq = 0;                       // its length (warp-uniform)
+    const bool circuit = !PL && k.drive == PIC_DRIVE_CIRCUIT;
+    long long vsum = 0;               // circuit drive: this thread's sum of round(256 vx)
+
+    // collision path for the warp's first nq (<= 32) queued candidates, one per lane
+    auto flush = [&](int nq) {
+      int sel = -1;
+      bool ovf = false;
+      if (lane < nq) {
+        const uint2 e = Qd[qoff + lane];
+        const int32_t qp = (int32_t)e.x;
+        const R qu1 = u_dec<R>(e.y);
+        // the candidate as phase A stored it (L2 reads: written by this warp, not through L1)
+        const int32_t qcell = __ldcg(s.cell + qp);
+        const uint64_t qid = __ldcg(reinterpret_cast<const unsigned long long *>(s.id) + qp);
+        R qoff_, qx, qy, qz;
+        rec_load_l2<R>(s.rec, qp, qoff_, qx, qy, qz);
+        sel = collide<R, SP, BD>(k, sp, ctl, bb, m, qid, step, c3, qp, qcell, qoff_, qu1, qx, qy, qz, ovf);
+        rec_store<R>(s.rec, qp, qoff_, qx, qy, qz);
+        if (record) s.code[qp] = sel >= 0 ? sp.xs[sel] : -1;
+        if (diag) add_moments<R, SP>(sp, m, N, Nw, qcell, qoff_, qx, qy, qz);
+        if (circuit) vsum += vfix(qx);
       }
-    } else {
-      const int pn = p + blockDim.x;
-      if (pn < (int)p1) {
-        n_cell = s.cell[pn];
-        rec_load<R>(s.rec, pn, n_off, n_vx, n_vy, n_vz);
-        n_id = s.id[pn];
+      for (int q = 0; q < sp.np; ++q) {
+        const unsigned b = __ballot_sync(kFull, sel == q);
+        if (lane == 0 && b) atomicAdd(&s_cnt[q], (unsigned)__popc(b));
+      }
+      const unsigned bo = __ballot_sync(kFull, ovf);
+      if (lane == 0 && bo) atomicAdd(&s_cnt[kMaxProc], (unsigned)__popc(bo));
+      __syncwarp();
+    };
+
+    // FP64 form: the next tile's particle in registers while this one is processed
+    int32_t n_cell = 0;
+    R n_off = 0, n_vx = 0, n_vy = 0, n_vz = 0;
+    uint64_t n_id = 0;
+    if constexpr (kMode == 0) {
+      const int p = ip0 + (int)threadIdx.x;
+      if (p < ip1) {
+        n_cell = s.cell[p];
+        rec_load<R>(s.rec, p, n_off, n_vx, n_vy, n_vz);
+        n_id = s.id[p];
       }
     }
-    if (valid) {
-      const R Ep = gather(E, cell, off);
-      const int side = push<R>(N, bounded, sp.a, sp.d, Ep, cell, off, vx);
-      const uint4 ctr = make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, c3);
-      const uint4 w0 = PK ? philox10_rk(ctr, k.rk) : philox10(ctr, key);
-      dead = side != 0 || (radial && (w0.z < sp.Pw));
-      if (side != 0) atomicAdd(&ctl->absorbed[SP][side > 0 ? 1 : 0], 1ull);
-      if (!dead) {
-        u1 = u_dec<R>(w0.y);
-        if constexpr (SP == 0) {
-          // electrons: null-collision probability of the energy bin of the particle
-          const R eps = sp.K * (vx * vx + vy * vy + vz * vz);
-          R fr;
-          bool ovf;
-          const int it = tab_pos(eps, sp.inv_de, k.ntab, fr, ovf);
-          cand = u_dec<R>(w0.x) < __ldg(sp.Pb + it);
-        } else {
-          cand = u_dec<R>(w0.x) < sp.P;
+    bool live = true;   // warp-uniform: false once a stage wait gave up
+    for (int t = 0; t < ntiles; ++t) {
+      const int base = ip0 + t * TILE;
+      const int p = base + warp * 32 + lane;
+      const bool valid = p < ip1;
+      bool cand = false, dead = false;
+      int32_t cell = n_cell;
+      R off = n_off, vx = n_vx, vy = n_vy, vz = n_vz;
+      uint32_t w1 = 0;   // raw word of the process-choice uniform (converted for candidates only)
+      uint64_t id = n_id;
+      if constexpr (kStg) {
+        const int st = t % kStages;
+        if (live) {
+          live = __all_sync(kFull, mbar_wait(&s_full[st], (unsigned)((t / kStages) & 1), kStageSpin));
+          if (!live && lane == 0) atomicOr(&ctl->status, kStTimeout);
+        }
+        if (live) {
+          if (valid) {
+            const unsigned char *sb = stg + (size_t)st * TILE * 28;
+            const int q = warp * 32 + lane;
+            cell = reinterpret_cast<const int32_t *>(sb)[q];
+            const float4 r = reinterpret_cast<const float4 *>(sb + (size_t)TILE * 4)[q];
+            off = r.x; vx = r.y; vy = r.z; vz = r.w;
+            id = reinterpret_cast<const uint64_t *>(sb + (size_t)TILE * 20)[q];
+          }
+        }
+      } else if constexpr (kMode == 1) {
+        cp_async_wait<kStages - 1>();   // this thread's copies of the tile have landed
+        if (valid) {
+          const unsigned char *sb = stg + (size_t)(t % kStages) * TILE * 28;
+          cell = reinterpret_cast<const int32_t *>(sb)[threadIdx.x];
+          const float4 r = reinterpret_cast<const float4 *>(sb + (size_t)TILE * 4)[threadIdx.x];
+          off = r.x; vx = r.y; vy = r.z; vz = r.w;
+          id = reinterpret_cast<const uint64_t *>(sb + (size_t)TILE * 20)[threadIdx.x];
+        }
+      } else {
+        const int pn = p + TILE;
+        if (pn < ip1) {
+          n_cell = s.cell[pn];
+          rec_load<R>(s.rec, pn, n_off, n_vx, n_vy, n_vz);
+          n_id = s.id[pn];
         }
       }
-      s.cell[p] = cell;
-      if (!cand) {
-        rec_store<R>(s.rec, p, off, vx, vy, vz);
-        if (record) s.code[p] = dead ? -2 : -1;
-        if (!dead && diag) add_moments<R, SP>(sp, m, N, Nw, cell, off, vx, vy, vz);
-        if (!dead && circuit) vsum += vfix(vx);
+      if (valid && live) {
+        const R Ep = gather(E, cell, off);
+        const int side = push<R>(N, bounded, sp.a, sp.d, Ep, cell, off, vx);
+        const uint4 ctr = make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, c3);
+        const uint4 w0 = PK ? philox10_rk(ctr, k.rk) : philox10(ctr, key);
+        dead = side != 0 || (radial && (w0.z < sp.Pw));
+        if (side != 0) atomicAdd(&ctl->absorbed[SP][side > 0 ? 1 : 0], 1ull);
+        if (!dead) {
+          w1 = w0.y;
+          if constexpr (SP == 0) {
+            // electrons: null-collision probability of the energy bin of the particle
+            const R eps = sp.K * (vx * vx + vy * vy + vz * vz);
+            R fr;
+            bool ovf;
+            const int it = tab_pos(eps, sp.inv_de, k.ntab, fr, ovf);
+            if constexpr (std::is_same<R, float>::value) cand = (w0.x >> 8) < (it < kPbHot ? sPb[it] : __ldg(sp.Pbi + it));
+            else cand = u_dec<R>(w0.x) < __ldg(sp.Pb + it);
+          } else {
+            if constexpr (std::is_same<R, float>::value) cand = (w0.x >> 8) < sp.Pi;
+            else cand = u_dec<R>(w0.x) < sp.P;
+          }
+        }
+        s.cell[p] = cell;
+        rec_store<R>(s.rec, p, off, vx, vy, vz);   // a candidate's record is rewritten after its collision
+        if (!cand) {
+          if (record) s.code[p] = dead ? -2 : -1;
+          if (!dead && diag) add_moments<R, SP>(sp, m, N, Nw, cell, off, vx, vy, vz);
+          if (!dead && circuit) vsum += vfix(vx);
+        }
+        if (dead) {
+          const int idx = atomicAdd(&ctl->n_dead[SP], 1);
+          if (idx < kStageCap) s.dead[idx] = p;
+          else atomicOr(&ctl->status, kStDeadOverflow);
+        }
+        // charge deposit into the window bins
+        if (!dead) deposit_one(bins, N, Nw, cell, wfix32(off), s.Q);
       }
-      if (dead) {
-        const int idx = atomicAdd(&ctl->n_dead[SP], 1);
-        if (idx < kStageCap) s.dead[idx] = p;
-        else atomicOr(&ctl->status, kStDeadOverflow);
+      if constexpr (kStg) {
+        // this warp is done with the stage: every value it read from it has been used above (so
+        // the loads have returned) before the copy warp may refill it
+        if (live) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&s_empty[t % kStages]);
+        }
       }
-    }
-    if constexpr (kStg) {   // the slot is consumed (its values were used above): refill it
-      stage_in(base + kStages * blockDim.x, sidx);
-      sidx ^= 1;
-    }
-    // queue the candidates in this warp's slice
-    const unsigned bal = __ballot_sync(kFull, cand);
-    if (cand) {
-      const int qi = qoff + wq + __popc(bal & lt);
-      Qd.id[qi] = id; Qd.off[qi] = off; Qd.vx[qi] = vx; Qd.vy[qi] = vy; Qd.vz[qi] = vz; Qd.u1[qi] = u1;
-      Qd.slot[qi] = p; Qd.cell[qi] = cell;
-    }
-    wq += __popc(bal);
-    // charge deposit into the window bins
-    deposit(valid && !dead, cell, wfix(off), N, Nw, bins, s.Q);
-    __syncwarp();
-    if (wq >= 32) {
-      flush(32);
-      // move the remaining entries to the front of the slice
-      const int rest = wq - 32;
-      if (lane < rest) {
-        const int a = qoff + 32 + lane, b = qoff + lane;
-        Qd.id[b] = Qd.id[a]; Qd.off[b] = Qd.off[a]; Qd.vx[b] = Qd.vx[a]; Qd.vy[b] = Qd.vy[a];
-        Qd.vz[b] = Qd.vz[a]; Qd.u1[b] = Qd.u1[a]; Qd.slot[b] = Qd.slot[a]; Qd.cell[b] = Qd.cell[a];
-      }
+      if constexpr (kMode == 1) stage_in(t + kStages);   // this thread's slot of the stage is free again
+      // queue the candidates in this warp's slice
+      const unsigned bal = __ballot_sync(kFull, cand);
+      if (cand) Qd[qoff + wq + __popc(bal & lt)] = make_uint2((uint32_t)p, w1);
+      wq += __popc(bal);
       __syncwarp();
-      wq = rest;
+      if (wq >= 32) {
+        // the collision path reads the candidates' records back from L2: make this warp's
+        // stores of phase A (all tiles so far) visible to its lanes first
+        __threadfence_block();
+        __syncwarp();
+        flush(32);
+        // move the remaining entries to the front of the slice
+        const int rest = wq - 32;
+        if (lane < rest) Qd[qoff + lane] = Qd[qoff + 32 + lane];
+        __syncwarp();
+        wq = rest;
+      }
+      // keep every cell of the window below 2^16 particles between flushes
+      if ((t + 1) % FT == 0 && t + 1 < ntiles) {
+        named_sync(1, CW * 32);
+        bins_flush(bins, N, Nw, s.Q, threadIdx.x, CW * 32);
+        named_sync(1, CW * 32);
+      }
     }
-  }
-  if (wq > 0) flush(wq);
-  if constexpr (kStg) cp_async_wait<0>();
-  if (circuit) {
-    unsigned long long u = (unsigned long long)vsum;
+    if (wq > 0) {
+      __threadfence_block();
+      __syncwarp();
+      flush(wq);
+    }
+    if constexpr (kMode == 1) cp_async_wait<0>();
+    if (circuit) {
+      unsigned long long u = (unsigned long long)vsum;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(kFull, u, o);
-    if (lane == 0 && u) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->sumv[SP]), u);
+      for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(kFull, u, o);
+      if (lane == 0 && u) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->sumv[SP]), u);
+    }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < W; j += blockDim.x) {
-    const unsigned nq = bins.cnt[j];
-    const unsigned long long sk = ((unsigned long long)bins.khi[j] << 32) | (unsigned long long)bins.klo[j];
-    if (nq || sk) {
-      int cell = j;
-      if (W < N) { cell = c0 + j; if (cell >= N) cell -= N; }
-      const int c1 = (cell + 1 == Nw) ? 0 : cell + 1;
-      atomicAdd(s.Q + cell, ((unsigned long long)nq << 32) - sk);
-      atomicAdd(s.Q + c1, sk);
-    }
-  }
+  bins_flush(bins, N, Nw, s.Q, threadIdx.x, blockDim.x);
   if (threadIdx.x < sp.np && s_cnt[threadIdx.x])
     atomicAdd(&ctl->n_coll[SP][threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
   if (threadIdx.x == 0 && s_cnt[kMaxProc]) atomicAdd(&ctl->overflow[SP], (unsigned long long)s_cnt[kMaxProc]);
 }
 
-template <class R, int SP, bool BD>
+template <class R, int SP, bool BD, bool PL>
 __global__ void __launch_bounds__(kStepThreads, 1)
 k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef, BirthBuf<R> bb,
        Moments m, int W, int smemE) {
   extern __shared__ __align__(16) unsigned char smem[];
-  push_body<R, SP, true, BD>(k, s, ctl, Ef, bb, m, W, smemE, blockIdx.x, gridDim.x, smem);
+  push_body<R, SP, true, BD, PL>(k, s, ctl, Ef, bb, m, W, smemE, blockIdx.x, gridDim.x, smem);
 }
 
 // batched columns: CTA b runs share sched[b].y of sched[b].z of column sched[b].x
-template <class R, int SP>
+template <class R, int SP, bool PL>
 __global__ void __launch_bounds__(kStepThreads, 1) k_push_batch(const ColDev<R> *cols, const int4 *sched) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) StepK<R> sk;
@@ -565,7 +708,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_push_batch(const ColDev<R> 
     for (int q = threadIdx.x; q < (int)(sizeof(StepK<R>) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
   }
   __syncthreads();
-  push_body<R, SP, false, false>(sk, cd->sp[SP], cd->ctl, reinterpret_cast<const R *>(cd->Ef), cd->bb, cd->m, cd->W, cd->smemE,
+  push_body<R, SP, false, false, PL>(sk, cd->sp[SP], cd->ctl, reinterpret_cast<const R *>(cd->Ef), cd->bb, cd->m, cd->W, cd->smemE,
                    sc.y, sc.z, smem);
 }
 
@@ -576,7 +719,7 @@ template <class R> int push_smem_bytes(int N) {
 
 template <class R> size_t push_layout(int n_cells, int &W, int &smemE) {
   const size_t budget = 226 * 1024;   // of 227 KB: room for the batched kernel's static StepK
-  const size_t qb = queue_bytes<R>() + stage_bytes<R>();
+  const size_t qb = queue_bytes<R>() + stage_bytes<R>() + pbhot_bytes<R>();
   size_t eb = (((size_t)n_cells + 1) * sizeof(R) + 15) & ~(size_t)15;
   // the node field goes to shared memory when it leaves room for a 2048-cell bin window
   smemE = eb + qb + bins_bytes(2048) <= budget ? 1 : 0;
@@ -589,29 +732,38 @@ template <class R> size_t push_layout(int n_cells, int &W, int &smemE) {
 
 template <class R>
 void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBuf<R> bb, Moments m, int species,
-                 int nsm, cudaStream_t st) {
+                 int nsm, bool diag_step, cudaStream_t st) {
   int W = 0, smemE = 0;
+  // a step with none of the optional work runs the kernel compiled without it
+  const bool plain = !diag_step && !(k.flags & PIC_FLAG_RECORD_CODES) && k.drive != PIC_DRIVE_CIRCUIT &&
+                     k.loss_mode != PIC_LOSS_RADIAL;
   const size_t bytes = push_layout<R>(k.N, W, smemE);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     kern<<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
   };
   if (species == 0) {
-    if (k.bounded) go(k_push<R, 0, true>); else go(k_push<R, 0, false>);
+    if (k.bounded) go(k_push<R, 0, true, false>);
+    else if (plain) go(k_push<R, 0, false, true>);
+    else go(k_push<R, 0, false, false>);
   } else {
-    if (k.bounded) go(k_push<R, 1, true>); else go(k_push<R, 1, false>);
+    if (k.bounded) go(k_push<R, 1, true, false>);
+    else if (plain) go(k_push<R, 1, false, true>);
+    else go(k_push<R, 1, false, false>);
   }
 }
 
 template <class R>
-void launch_push_batch(const ColDev<R> *cols, const int4 *sched, int nblocks, int species, size_t smem,
+void launch_push_batch(const ColDev<R> *cols, const int4 *sched, int nblocks, int species, size_t smem, bool plain,
                        cudaStream_t st) {
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<nblocks, kStepThreads, smem, st>>>(cols, sched);
+  };
   if (species == 0) {
-    cudaFuncSetAttribute(k_push_batch<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_push_batch<R, 0><<<nblocks, kStepThreads, smem, st>>>(cols, sched);
+    if (plain) go(k_push_batch<R, 0, true>); else go(k_push_batch<R, 0, false>);
   } else {
-    cudaFuncSetAttribute(k_push_batch<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_push_batch<R, 1><<<nblocks, kStepThreads, smem, st>>>(cols, sched);
+    if (plain) go(k_push_batch<R, 1, true>); else go(k_push_batch<R, 1, false>);
   }
 }
 
@@ -1405,7 +1557,7 @@ template <class R> void launch_sumv(SpeciesDev s, Ctl *ctl, int species, cudaStr
   template void launch_init<R>(const StepK<R> &, SpeciesDev, int, int64_t, uint64_t, R, cudaStream_t);              \
   template void launch_deposit<R>(const StepK<R> &, SpeciesDev, const Ctl *, int, cudaStream_t);                    \
   template void launch_halfstep<R>(const StepK<R> &, SpeciesDev, const Ctl *, const R *, int, cudaStream_t);        \
-  template void launch_push<R>(const StepK<R> &, SpeciesDev, Ctl *, const R *, BirthBuf<R>, Moments, int, int,      \
+  template void launch_push<R>(const StepK<R> &, SpeciesDev, Ctl *, const R *, BirthBuf<R>, Moments, int, int, bool, \
                                cudaStream_t);                                                                        \
   template void launch_births<R>(const StepK<R> &, SpeciesDev, SpeciesDev, Ctl *, BirthBuf<R>, K3Scratch, int,      \
                                  cudaStream_t);                                                                      \
@@ -1415,7 +1567,7 @@ template <class R> void launch_sumv(SpeciesDev s, Ctl *ctl, int species, cudaStr
   template void launch_sumv<R>(SpeciesDev, Ctl *, int, cudaStream_t);                                               \
   template size_t push_layout<R>(int, int &, int &);                                                                \
   template void launch_zero_q_batch<R>(const ColDev<R> *, int, int, int, cudaStream_t);                             \
-  template void launch_push_batch<R>(const ColDev<R> *, const int4 *, int, int, size_t, cudaStream_t);              \
+  template void launch_push_batch<R>(const ColDev<R> *, const int4 *, int, int, size_t, bool, cudaStream_t);              \
   template void launch_births_batch<R>(const ColDev<R> *, int, int, cudaStream_t);                                  \
   template void launch_field_batch<R>(const ColDev<R> *, int, int, bool, bool, cudaStream_t);
 PIC_INST(double)

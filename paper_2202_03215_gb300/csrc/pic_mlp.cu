@@ -100,9 +100,9 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                "l"(src), "r"(bytes), "r"(mb)
                : "memory");
 }
-__device__ __forceinline__ bool wait_phase(unsigned long long *mbar, unsigned parity) {
+__device__ __forceinline__ bool wait_phase(unsigned long long *mbar, unsigned parity, int spin) {
   const unsigned mb = saddr(mbar);
-  for (int it = 0; it < kSpin; ++it) {
+  for (int it = 0; it < spin; ++it) {
     unsigned done;
     asm volatile(
         "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, 10000;\nselp.b32 %0, 1, 0, P;\n}\n"
@@ -249,7 +249,8 @@ __device__ __forceinline__ void wgrad_store(const float c[NT][4], float *gp, int
 __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ P, const WPack *__restrict__ Wb,
                                                       const float *__restrict__ X, const float *__restrict__ T, int n,
                                                       float inv_n3, float *__restrict__ gpart,
-                                                      float *__restrict__ lpart, int *__restrict__ status) {
+                                                      float *__restrict__ lpart, int *__restrict__ status, int spin,
+                                                      unsigned hook) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, g = lane >> 2, t = lane & 3;
@@ -262,7 +263,14 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
   pdl_launch_next();
   pdl_wait_prev();
   // the BF16 weights by one bulk copy, the FP32 biases and the tile's inputs
-  if (tid == 0) bulk_load(&sm.w, Wb, (unsigned)sizeof(WPack), &sm.mbar);
+  if (tid == 0) {
+    if (!(hook & PIC_MLP_HOOK_NO_WEIGHT_COPY)) {
+      bulk_load(&sm.w, Wb, (unsigned)sizeof(WPack), &sm.mbar);
+    } else {   // test hook: the barrier is armed but no copy will ever arrive on it
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&sm.mbar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   for (int q = tid; q < NH; q += THREADS) { sm.b1[q] = P[ob1 + q]; sm.b2[q] = P[ob2 + q]; }
   if (tid < NOP) sm.b3[tid] = tid < NO ? P[ob3 + tid] : 0.0f;
   {
@@ -274,10 +282,10 @@ __global__ void __launch_bounds__(THREADS) k_mlp_tile(const float *__restrict__ 
     for (int q = tid; q < S * (LDI - NI); q += THREADS) sm.X[q / (LDI - NI)][NI + q % (LDI - NI)] = __float2bfloat16_rn(0.0f);
   }
   if (tid == 0) {
-    bool ok = wait_phase(&sm.mbar, 0);
+    bool ok = wait_phase(&sm.mbar, 0, spin);
     if (!ok) {            // report, let the copy in flight land (bounded), skip the tile
       atomicExch(status, 1);
-      wait_phase(&sm.mbar, 0);
+      wait_phase(&sm.mbar, 0, spin);
     }
     sm.ok = ok;
   }
@@ -406,10 +414,13 @@ constexpr int RW = 16;  // warps of the reduction
 __global__ void __launch_bounds__(RW * 32) k_mlp_reduce(const float *__restrict__ gpart, const float *__restrict__ lpart,
                                                         int ntiles, float *__restrict__ grad, double *__restrict__ loss,
                                                         float inv_n3, float *__restrict__ P, float *__restrict__ m,
-                                                        float *__restrict__ v, bf *__restrict__ Wb, AdamArgs a) {
+                                                        float *__restrict__ v, bf *__restrict__ Wb, AdamArgs a,
+                                                        const int *__restrict__ status) {
   __shared__ float part[RW][32];
   pdl_launch_next();
   pdl_wait_prev();
+  // a tile whose wait gave up wrote no partial: leave gradient, loss, weights and moments as they are
+  if (*status) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + lane;
   float s = 0.0f;
@@ -454,7 +465,8 @@ __global__ void k_mlp_pack(const float *__restrict__ P, bf *__restrict__ Wb) {
 
 }  // namespace
 
-int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status, cudaStream_t st);
+int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status, int spin, unsigned hook,
+                   cudaStream_t st);
 
 struct pic_mlp {
   float *P = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
@@ -464,6 +476,9 @@ struct pic_mlp {
   int *status = nullptr;   // device: 1 once a bounded wait of the tensor-core forward gave up
   int cap_tiles = 0;
   int t = 0;   // Adam steps taken
+  int spin = kSpin;        // polls of a bounded wait (pic_mlp_test_hook)
+  unsigned hook = 0;       // PIC_MLP_HOOK_* (pic_mlp_test_hook)
+  int latched = 0;         // PIC_ETIMEOUT once a wait gave up, until pic_mlp_set_params
 };
 
 namespace {
@@ -483,7 +498,7 @@ int ensure(pic_mlp *h, int n) {
 }
 
 int run_forward(pic_mlp *h, const float *X, int n, float *Y, cudaStream_t st) {
-  return mlp_forward_tc(h->P, X, n, Y, h->status, st);
+  return mlp_forward_tc(h->P, X, n, Y, h->status, h->spin, h->hook, st);
 }
 
 int pack(pic_mlp *h) {
@@ -516,13 +531,13 @@ int run_tiles(pic_mlp *h, const float *X, const float *T, int n, const AdamArgs 
   cfg.blockDim = dim3(THREADS);
   cfg.dynamicSmemBytes = sizeof(Smem);
   if (cudaLaunchKernelEx(&cfg, k_mlp_tile, (const float *)h->P, (const WPack *)h->Wb, X, T, n, inv_n3, h->gpart,
-                         h->lpart, h->status) != cudaSuccess)
+                         h->lpart, h->status, h->spin, h->hook) != cudaSuccess)
     return PIC_ECUDA;
   cfg.gridDim = dim3((NPARAM + 31) / 32);
   cfg.blockDim = dim3(RW * 32);
   cfg.dynamicSmemBytes = 0;
   if (cudaLaunchKernelEx(&cfg, k_mlp_reduce, (const float *)h->gpart, (const float *)h->lpart, tiles, h->grad, h->loss,
-                         inv_n3, h->P, h->m, h->v, h->Wb, a) != cudaSuccess)
+                         inv_n3, h->P, h->m, h->v, h->Wb, a, (const int *)h->status) != cudaSuccess)
     return PIC_ECUDA;
   return 0;
 }
@@ -537,19 +552,23 @@ uint64_t splitmix(uint64_t &x) {
 
 }  // namespace
 
-// PIC_ETIMEOUT (and the flag cleared) if a bounded wait of a forward pass gave up since the
-// last call; synchronous (the handle's work must have completed)
+// PIC_ETIMEOUT if a bounded wait of the handle's kernels gave up since the last call: the error
+// latches on the handle (device flag cleared) until pic_mlp_set_params; synchronous (the
+// handle's work must have completed)
 int mlp_take_status(pic_mlp *h) {
   int st = 0;
   if (cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
-  if (!st) return 0;
-  cudaMemset(h->status, 0, sizeof(int));
-  return PIC_ETIMEOUT;
+  if (st) {
+    cudaMemset(h->status, 0, sizeof(int));
+    h->latched = PIC_ETIMEOUT;
+  }
+  return h->latched;
 }
 
 // forward pass enqueued on st without synchronising (used by the fluid closure)
 int mlp_forward_async(pic_mlp *h, const float *X, int n, float *Y, cudaStream_t st) {
   if (!h || !X || !Y) return PIC_EINVAL;
+  if (h->latched) return h->latched;
   return run_forward(h, X, n, Y, st);
 }
 
@@ -606,7 +625,16 @@ int pic_mlp_set_params(pic_mlp *h, const float *host, int n) {
   cudaMemset(h->m, 0, NPARAM * 4);
   cudaMemset(h->v, 0, NPARAM * 4);
   h->t = 0;
+  h->latched = 0;
   return pack(h);
+}
+
+int pic_mlp_test_hook(pic_mlp *h, unsigned hook, int spin) {
+  if (!h || spin < 0 || (hook & ~(unsigned)(PIC_MLP_HOOK_NO_WEIGHT_COPY | PIC_MLP_HOOK_NO_FORWARD_MMA))) return PIC_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PIC_ECUDA;
+  h->hook = hook;
+  h->spin = spin > 0 ? spin : kSpin;
+  return 0;
 }
 
 int pic_mlp_get_params(pic_mlp *h, float *host, int n) {
@@ -616,6 +644,7 @@ int pic_mlp_get_params(pic_mlp *h, float *host, int n) {
 
 int pic_mlp_forward(pic_mlp *h, const float *X, int n, float *Y, void *stream) {
   if (!h || !X || !Y) return PIC_EINVAL;
+  if (h->latched) return h->latched;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int rc = run_forward(h, X, n, Y, st);
   if (rc) return rc;
@@ -625,6 +654,7 @@ int pic_mlp_forward(pic_mlp *h, const float *X, int n, float *Y, void *stream) {
 
 int pic_mlp_grad(pic_mlp *h, const float *X, const float *T, int n, float *grad_host, double *loss, void *stream) {
   if (!h || !X || !T) return PIC_EINVAL;
+  if (h->latched) return h->latched;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int rc = run_tiles(h, X, T, n, AdamArgs{0, 0, 0, 0, 0, 0, 0}, st);
   if (rc) return rc;
@@ -638,6 +668,7 @@ int pic_mlp_grad(pic_mlp *h, const float *X, const float *T, int n, float *grad_
 int pic_mlp_train(pic_mlp *h, const float *X, const float *T, int n, int batch, int steps, float lr,
                   double *last_loss, void *stream) {
   if (!h || !X || !T || n <= 0 || batch <= 0 || steps < 0) return PIC_EINVAL;
+  if (h->latched) return h->latched;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   for (int k = 0; k < steps; ++k) {

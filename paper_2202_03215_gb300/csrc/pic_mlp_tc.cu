@@ -36,7 +36,6 @@ constexpr int K1 = 16;             // input width padded to one MMA K step
 constexpr int N3 = 16;             // output width padded to the smallest N of an M = 128 MMA
 constexpr int G = 4;               // groups of TM threads per block
 constexpr uint32_t kCols = 128 * G;   // tensor-memory columns of a block: 128 per group
-constexpr int kSpin = 200000;      // polls of an mbarrier (each suspends up to 10 us, then sleeps) before giving up
 
 using bf = __nv_bfloat16;
 
@@ -88,8 +87,8 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < kSpin; ++it) {
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity, int spin) {
+  for (int it = 0; it < spin; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, 10000;\nselp.b32 %0, 1, 0, P;\n}\n"
@@ -168,8 +167,8 @@ __device__ __forceinline__ void group_handoff(int g) {
 
 // one thread of the group waits for the group's MMAs (thread 32 (g % 4): the four groups' waiters
 // sit in warps of four different schedulers); the barrier passes the outcome to the group
-__device__ __forceinline__ bool group_wait(TcSmem &S, int g, int lt, uint32_t mbar, uint32_t parity) {
-  if (lt == 32 * (g & 3)) S.ok[g] = wait_phase(mbar, parity) ? 1 : 0;
+__device__ __forceinline__ bool group_wait(TcSmem &S, int g, int lt, uint32_t mbar, uint32_t parity, int spin) {
+  if (lt == 32 * (g & 3)) S.ok[g] = wait_phase(mbar, parity, spin) ? 1 : 0;
   group_bar(g);
   const bool ok = S.ok[g] != 0;
   group_bar(g);   // the flag is read before thread 0 can rewrite it
@@ -177,7 +176,8 @@ __device__ __forceinline__ bool group_wait(TcSmem &S, int g, int lt, uint32_t mb
 }
 
 __global__ void __launch_bounds__(TM * G) k_mlp_fwd_tc(const float *__restrict__ P, const float *__restrict__ X,
-                                                       int n, float *__restrict__ Y, int *status) {
+                                                       int n, float *__restrict__ Y, int *status, int spin,
+                                                       unsigned hook) {
   extern __shared__ __align__(128) unsigned char raw[];
   TcSmem &S = *reinterpret_cast<TcSmem *>(raw);
   const int tid = threadIdx.x, w = tid >> 5, g = tid / TM, lt = tid % TM;
@@ -223,6 +223,9 @@ __global__ void __launch_bounds__(TM * G) k_mlp_fwd_tc(const float *__restrict__
   constexpr uint32_t id12 = idesc(TM, NH), id3 = idesc(TM, N3);
   uint32_t parity = 0;
   bool ok = true;
+  bool pending = false;   // an MMA was committed whose completion the group has not seen
+  // test hook: block 0's group 0 issues no MMA for its first tile, so its wait runs out
+  bool skip = (hook & PIC_MLP_HOOK_NO_FORWARD_MMA) && blockIdx.x == 0 && g == 0;
   const int tiles = (n + TM - 1) / TM;
   for (int tile = blockIdx.x * G + g; tile < tiles; tile += gridDim.x * G) {
     const int s = tile * TM + lt;
@@ -232,11 +235,13 @@ __global__ void __launch_bounds__(TM * G) k_mlp_fwd_tc(const float *__restrict__
       *reinterpret_cast<bf *>(Xs + cm_off(lt, i, K1)) =
           __float2bfloat16_rn((s < n && i < NI) ? X[(size_t)s * NI + i] : 0.0f);
     group_handoff(g);
-    if (lt == 0) {
+    if (lt == 0 && !skip) {
       mma(tmem, dX, dW1, id12, 0u);
       commit(mbar);
     }
-    ok = group_wait(S, g, lt, mbar, parity);
+    pending = !skip;
+    skip = false;
+    ok = group_wait(S, g, lt, mbar, parity, spin);
     parity ^= 1u;
     if (!ok) break;
     tc_after_sync();
@@ -247,7 +252,8 @@ __global__ void __launch_bounds__(TM * G) k_mlp_fwd_tc(const float *__restrict__
       for (uint32_t kk = 0; kk < NH / 16; ++kk) mma(tmem, dH + kk * 16u, dW2 + kk * 16u, id12, kk);
       commit(mbar);
     }
-    ok = group_wait(S, g, lt, mbar, parity);
+    pending = true;
+    ok = group_wait(S, g, lt, mbar, parity, spin);
     parity ^= 1u;
     if (!ok) break;
     tc_after_sync();
@@ -258,7 +264,8 @@ __global__ void __launch_bounds__(TM * G) k_mlp_fwd_tc(const float *__restrict__
       for (uint32_t kk = 0; kk < NH / 16; ++kk) mma(tmem, dH + kk * 16u, dW3 + kk * 16u, id3, kk);
       commit(mbar);
     }
-    ok = group_wait(S, g, lt, mbar, parity);
+    pending = true;
+    ok = group_wait(S, g, lt, mbar, parity, spin);
     parity ^= 1u;
     if (!ok) break;
     tc_after_sync();
@@ -273,6 +280,9 @@ __global__ void __launch_bounds__(TM * G) k_mlp_fwd_tc(const float *__restrict__
     tc_after_sync();
   }
   if (!ok && lt == 0) atomicExch(status, 1);
+  // a wait that gave up on a committed MMA: wait once more (bounded) for it to finish writing
+  // tensor memory before the memory is freed; the phase that ran out is the one before parity
+  if (!ok && pending && lt == 32 * (g & 3)) wait_phase(mbar, parity ^ 1u, spin);
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
@@ -283,7 +293,8 @@ __global__ void __launch_bounds__(TM * G) k_mlp_fwd_tc(const float *__restrict__
 
 // forward pass of the closure network on the tensor cores, enqueued on st; *status (device)
 // becomes 1 if a wait gave up
-int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status, cudaStream_t st) {
+int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status, int spin, unsigned hook,
+                   cudaStream_t st) {
   if (n <= 0) return PIC_EINVAL;
   static int sms = 0;
   if (!sms) {
@@ -298,6 +309,6 @@ int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status,
   const int smem = (int)sizeof(TcSmem);
   if (cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return PIC_ECUDA;
-  k_mlp_fwd_tc<<<blocks, TM * G, smem, st>>>(P, X, n, Y, status);
+  k_mlp_fwd_tc<<<blocks, TM * G, smem, st>>>(P, X, n, Y, status, spin, hook);
   return cudaGetLastError() == cudaSuccess ? 0 : PIC_ECUDA;
 }
