@@ -408,6 +408,22 @@ def compare(E0_over_p: Sequence[float], p_torr: float = 1.0, L_m: float = 0.10, 
                 pic_steps=windows * window, pic_modes=rec, fluid_modes=fl["modes"], t_pic=t_pic, t_fluid=fl["t"])
 
 
+def coarsen(m: dict, f: int) -> dict:
+    """A moment window averaged over blocks of f nodes: densities, fluxes, rates and the field as
+    block means, the mean energy weighted by the electron density."""
+    if f == 1:
+        return m
+    out = {}
+    for k, v in m.items():
+        if not isinstance(v, np.ndarray):
+            out[k] = v
+            continue
+        out[k] = v.reshape(-1, f).mean(1)
+    ne = m["n_e"].reshape(-1, f)
+    out["mean_eps_e"] = (m["mean_eps_e"].reshape(-1, f) * ne).sum(1) / np.maximum(ne.sum(1), 1e-300)
+    return out
+
+
 def _cathode_v(v_ph: float, frame: str) -> float:
     """Phase velocity counted positive towards the cathode: the particle model's field
     points along -x (cathode at -x), the fluid model's along +x."""
@@ -419,7 +435,7 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
           early: int = 100, early_window: int = 1000, agg: int = 4, fluid_dt: float = 2e-9, fluid_diag: int = 20,
           train_steps: int = 3000, batch: int = 8192, lr: float = 1e-3, period: int = 10,
           components=(0.0, 0.0, 1.0), nu_bound: float = 1.0, stencils=(1,), seed: int = 7,
-          log=print) -> dict:
+          fluid_cells: int | None = None, log=print) -> dict:
     """Particle model (one GPU batch: comparison and training fields), closure training on
     its moment windows, fluid model with and without the trained closure at the comparison
     fields; striation observables, closure gain and times.  The particle record takes
@@ -427,11 +443,18 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
     `window` steps; closure data come from the long windows, `agg` at a time.
     components: which network outputs the fluid screen applies (flux, energy flux,
     ionization); the flux corrections enter the step explicitly, so they are only
-    stable while dt |dGamma/n| / dx and the energy change they carry per step stay small."""
+    stable while dt |dGamma/n| / dx and the energy change they carry per step stay small.
+    fluid_cells: cells of the fluid columns (default: those of the particle columns); with fewer,
+    the particle model's moment windows are averaged onto the fluid grid (blocks of
+    n_cells / fluid_cells cells; the mean energy weighted by density) before the closure samples
+    are formed, so that the network sees the fluid model's resolution."""
     import time
     import torch
     from . import Batch, Mlp
     from . import closure as cl
+    fluid_cells = fluid_cells or n_cells
+    if n_cells % fluid_cells:
+        raise ValueError("the particle cells must be a multiple of the fluid cells")
     records = transport()
     tab = Table(records)
     Es = list(E_compare) + list(E_train)
@@ -489,7 +512,8 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
         Xs, Ys, col_of = [], [], []
         for k in range(ncmp, len(Es)):
             for m in train_windows[k][2:]:
-                X, Y = cl.residual_samples(m, params[k], tab, mu[k], T_range, step=st_k)
+                X, Y = cl.residual_samples(coarsen(m, n_cells // fluid_cells), params[k], tab, mu[k], T_range,
+                                           step=st_k)
                 Xs.append(X)
                 Ys.append(Y)
                 col_of.append(np.full(len(X), k))
@@ -522,19 +546,19 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
     states = [homogeneous_E0(tab, e, p_torr, mu_iN=mu[k]) for k, e in enumerate(E_compare)]
     steps = int(round(total_steps * dt_pic / fluid_dt))
     diag = fluid_diag
-    noise = 1.0 / math.sqrt(particles / n_cells)
+    noise = 1.0 / math.sqrt(particles / fluid_cells)
     mask = np.asarray(components, np.float32)
     out = {}
     variants = [("fluid", True, None)] + [
         ("fluid_closure" if i == 0 else f"fluid_closure_s{d['stencil']}", True,
          (d["net"], period, fs, d["ts"] * mask, nu_bound, d["stencil"])) for i, d in enumerate(nets)]
     for name, pair, clo in variants:
-        f = Fluid(fluid_columns(states, L_m, n_cells, pair=pair), records, n_T=128, dt_s=fluid_dt,
+        f = Fluid(fluid_columns(states, L_m, fluid_cells, pair=pair), records, n_T=128, dt_s=fluid_dt,
                   diag_every=diag, n_modes=M)
         if clo is not None:
             f.set_closure(*clo)
         for k, h in enumerate(states):
-            f.set_state(k, *initial_state(n_cells, h, seed + 100 + k, amp=noise))
+            f.set_state(k, *initial_state(fluid_cells, h, seed + 100 + k, amp=noise))
         f.step(steps)
         ms, launches = f.elapsed()
         r = f.modes()
@@ -595,6 +619,15 @@ def main(argv=None) -> int:
     ap.add_argument("--columns", type=int, default=152)
     ap.add_argument("--cells", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--L", type=float, default=0.10, help="study: column length, m")
+    ap.add_argument("--pic-cells", type=int, default=2048, help="study: cells of the particle and fluid columns")
+    ap.add_argument("--particles", type=int, default=1_000_000, help="study: particles per species and column")
+    ap.add_argument("--windows", type=int, default=200, help="study: long windows of the particle record")
+    ap.add_argument("--window", type=int, default=4000, help="study: steps per long window")
+    ap.add_argument("--agg", type=int, default=4, help="study: long windows averaged per closure sample window")
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--fluid-cells", type=int, default=None, help="study: cells of the fluid columns")
+    ap.add_argument("--early", type=int, default=100, help="study: growth-phase windows of 1000 steps")
     a = ap.parse_args(argv)
     if a.what == "fluid":
         # a fluid screen of imposed fields 6..20 V/cm/Torr (neon, 1 Torr, L = 10 cm): time per step
@@ -605,8 +638,10 @@ def main(argv=None) -> int:
         print(f"fluid: {a.columns} columns x {a.cells} cells, {a.steps} steps in {r['ms']:.2f} ms "
               f"({r['launches']} launches)", flush=True)
         return 0
-    r = study([6, 8, 10, 12, 14, 16, 18, 20], [7, 9, 11, 13, 15, 17, 19, 21], nu_bound=a.nu_bound, stencils=tuple(a.stencils),
-              log=lambda s: print(s, flush=True))
+    r = study([6, 8, 10, 12, 14, 16, 18, 20], [7, 9, 11, 13, 15, 17, 19, 21], L_m=a.L, n_cells=a.pic_cells,
+              particles=a.particles, windows=a.windows, window=a.window, agg=a.agg, train_steps=a.train_steps,
+              fluid_cells=a.fluid_cells, early=a.early,
+              nu_bound=a.nu_bound, stencils=tuple(a.stencils), log=lambda s: print(s, flush=True))
     for k, e in enumerate(r["E_compare"]):
         p, f, g, l, d = r["pic"][k], r["fluid"][k], r["fluid_closure"][k], r["linear"][k], r["dispersion"][k]
         print(f"E0/p={e}: PIC lam={p['lam'] * 100:.3g} cm v={p['v_ph']:.3g} m/s g={p['gamma']:.3g}/s | "
