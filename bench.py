@@ -392,7 +392,8 @@ def fluid_screen_leg(pb, torch, steps: int = 1000, warmup: int = 20, closure_ste
                         "spectral record every 50 steps"}
 
 
-def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: int = 300, warmup: int = 20):
+def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: int = 300, warmup: int = 20,
+                         big_steps: int = 100):
     """Adam training of the closure network on the GPU (BF16 operands, FP32 accumulation):
     forward + backward + deterministic gradient reduction + Adam per batch."""
     g = torch.Generator(device="cuda").manual_seed(5)
@@ -417,9 +418,21 @@ def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: 
     e1.record()
     torch.cuda.synchronize()
     sf = e0.elapsed_time(e1) / 1e3
+    # the same kernels with 16x the samples per Adam step: every SM holds several tiles
+    big = 16 * batch
+    net.train(X, T, batch=big, steps=5)
+    torch.cuda.synchronize()
+    e0.record()
+    net.train(X, T, batch=big, steps=big_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    sb = big * big_steps / (e0.elapsed_time(e1) / 1e3)
     return {"batch": batch, "steps": steps, "samples_per_s": sps, "tflops": tflops,
             "frac_of_bf16_peak": tflops / peak, "peak_tflops": peak, "peak_kind": kind,
             "flop_per_sample": 3 * MLP_FWD_FLOP,
+            "large_batch": {"batch": big, "steps": big_steps, "samples_per_s": sb,
+                            "tflops": 3 * MLP_FWD_FLOP * sb / 1e12,
+                            "frac_of_bf16_peak": 3 * MLP_FWD_FLOP * sb / 1e12 / peak},
             "forward": {"samples": n, "samples_per_s": n / sf, "tflops": MLP_FWD_FLOP * n / sf / 1e12}}
 
 

@@ -3,9 +3,10 @@
 // BF16 operands on the 5th-generation tensor cores (tcgen05, FP32 accumulation in
 // tensor memory), FP32 master weights and optimizer state.
 //
-// Training: one CTA per tile of 128 samples runs forward, backward and the weight
-// gradients of its tile (pic_mlp_train_tc.cu) and writes them as a partial; a
-// second kernel here sums the partials in a fixed order (deterministic gradients)
+// Training: persistent CTAs (at most one per SM) run forward, backward and the weight
+// gradients of their tiles of 128 samples (pic_mlp_train_tc.cu) and write them as one
+// partial per CTA; a second kernel here sums the partials in a fixed order (deterministic
+// gradients for a given SM count)
 // and applies Adam, which also refreshes the BF16 copy of the weights in the
 // tensor cores' operand layout that the tile kernel stages with one bulk copy.
 // The forward pass (inference) runs on tcgen05 too (pic_mlp_tc.cu).
@@ -41,12 +42,12 @@ struct AdamArgs {
   float lr, b1, b2, eps, c1, c2;
 };
 
-// g[p] = sum over tiles of the partials in a fixed order (tiles w, w+8, .. per warp, then the
+// g[p] = sum of the CTAs' partials in a fixed order (partials w, w+16, .. per warp, then the
 // warps in order); optionally Adam (Kingma & Ba) on the FP32 master weights, refreshing the
 // BF16 copy. Block 0 also sums the loss.
 constexpr int RW = 16;  // warps of the reduction
 __global__ void __launch_bounds__(RW * 32) k_mlp_reduce(const float *__restrict__ gpart, const float *__restrict__ lpart,
-                                                        int ntiles, float *__restrict__ grad, double *__restrict__ loss,
+                                                        int nparts, float *__restrict__ grad, double *__restrict__ loss,
                                                         float inv_n3, float *__restrict__ P, float *__restrict__ m,
                                                         float *__restrict__ v, bf *__restrict__ Wb, AdamArgs a,
                                                         const int *__restrict__ status) {
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(RW * 32) k_mlp_reduce(const float *__restrict_
   float s = 0.0f;
   if (p < NPARAM) {
 #pragma unroll 8
-    for (int q = w; q < ntiles; q += RW) s += gpart[(size_t)q * GSTRIDE + p];
+    for (int q = w; q < nparts; q += RW) s += gpart[(size_t)q * GSTRIDE + p];
   }
   part[w][lane] = s;
   __syncthreads();
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(RW * 32) k_mlp_reduce(const float *__restrict_
   }
   if (blockIdx.x == 0 && w == 1) {
     double l = 0.0;
-    for (int q = lane; q < ntiles; q += 32) l += (double)lpart[q];
+    for (int q = lane; q < nparts; q += 32) l += (double)lpart[q];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
     if (lane == 0) *loss = l * (double)inv_n3;
@@ -102,7 +103,7 @@ __global__ void k_mlp_pack(const float *__restrict__ P, bf *__restrict__ Wb) {
 int mlp_forward_tc(const float *P, const float *X, int n, float *Y, int *status, int spin, unsigned hook,
                    cudaStream_t st);
 int mlp_train_tiles_tc(const float *P, const void *Wb, const float *X, const float *T, int n, float inv_n3,
-                       float *gpart, float *lpart, int *status, int spin, unsigned hook, cudaStream_t st);
+                       float *gpart, float *lpart, int ctas, int *status, int spin, unsigned hook, cudaStream_t st);
 
 struct pic_mlp {
   float *P = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
@@ -110,7 +111,8 @@ struct pic_mlp {
   bf *Wb = nullptr;        // BF16 weights in the tensor cores' operand layout (TrainW)
   double *loss = nullptr;
   int *status = nullptr;   // device: 1 once a bounded wait of the tensor-core forward gave up
-  int cap_tiles = 0;
+  int cap_parts = 0;       // partials gpart / lpart hold
+  int nsm = 0;             // streaming multiprocessors: the training kernel's largest grid
   int t = 0;   // Adam steps taken
   int spin = kSpin;        // polls of a bounded wait (pic_mlp_test_hook)
   unsigned hook = 0;       // PIC_MLP_HOOK_* (pic_mlp_test_hook)
@@ -119,17 +121,21 @@ struct pic_mlp {
 
 namespace {
 
+// CTAs of the training kernel for n samples: one per tile, at most one per SM (each CTA then
+// loops over tiles b, b + ctas, ..)
+int train_ctas(const pic_mlp *h, int n) { return std::min((n + S - 1) / S, h->nsm); }
+
 int ensure(pic_mlp *h, int n) {
-  const int tiles = (n + S - 1) / S;
-  if (tiles <= h->cap_tiles) return 0;
+  const int parts = train_ctas(h, n);
+  if (parts <= h->cap_parts) return 0;
   cudaFree(h->gpart);
   cudaFree(h->lpart);
   h->gpart = nullptr;
   h->lpart = nullptr;
-  if (cudaMalloc(&h->gpart, (size_t)tiles * GSTRIDE * 4) != cudaSuccess ||
-      cudaMalloc(&h->lpart, (size_t)tiles * 4) != cudaSuccess)
+  if (cudaMalloc(&h->gpart, (size_t)parts * GSTRIDE * 4) != cudaSuccess ||
+      cudaMalloc(&h->lpart, (size_t)parts * 4) != cudaSuccess)
     return PIC_ENOMEM;
-  h->cap_tiles = tiles;
+  h->cap_parts = parts;
   return 0;
 }
 
@@ -147,9 +153,10 @@ int run_tiles(pic_mlp *h, const float *X, const float *T, int n, const AdamArgs 
   if (n <= 0) return PIC_EINVAL;
   const int rc = ensure(h, n);
   if (rc) return rc;
-  const int tiles = (n + S - 1) / S;
+  const int parts = train_ctas(h, n);
   const float inv_n3 = 1.0f / (3.0f * (float)n);
-  const int rc2 = mlp_train_tiles_tc(h->P, h->Wb, X, T, n, inv_n3, h->gpart, h->lpart, h->status, h->spin, h->hook, st);
+  const int rc2 =
+      mlp_train_tiles_tc(h->P, h->Wb, X, T, n, inv_n3, h->gpart, h->lpart, parts, h->status, h->spin, h->hook, st);
   if (rc2) return rc2;
   // the reduction with programmatic stream serialization: it may be scheduled while the tile
   // kernel drains and waits for it (griddepcontrol.wait) before it reads the partials
@@ -163,7 +170,7 @@ int run_tiles(pic_mlp *h, const float *X, const float *T, int n, const AdamArgs 
   cfg.gridDim = dim3((NPARAM + 31) / 32);
   cfg.blockDim = dim3(RW * 32);
   cfg.dynamicSmemBytes = 0;
-  if (cudaLaunchKernelEx(&cfg, k_mlp_reduce, (const float *)h->gpart, (const float *)h->lpart, tiles, h->grad, h->loss,
+  if (cudaLaunchKernelEx(&cfg, k_mlp_reduce, (const float *)h->gpart, (const float *)h->lpart, parts, h->grad, h->loss,
                          inv_n3, h->P, h->m, h->v, h->Wb, a, (const int *)h->status) != cudaSuccess)
     return PIC_ECUDA;
   return 0;
@@ -208,6 +215,12 @@ int pic_mlp_create(uint64_t seed, pic_mlp **out) {
   *out = nullptr;
   pic_mlp *h = new (std::nothrow) pic_mlp();
   if (!h) return PIC_ENOMEM;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || h->nsm <= 0) {
+    delete h;
+    return PIC_ECUDA;
+  }
   if (cudaMalloc(&h->P, NPARAM * 4) != cudaSuccess || cudaMalloc(&h->m, NPARAM * 4) != cudaSuccess ||
       cudaMalloc(&h->v, NPARAM * 4) != cudaSuccess || cudaMalloc(&h->grad, NPARAM * 4) != cudaSuccess ||
       cudaMalloc(&h->loss, 8) != cudaSuccess || cudaMalloc(&h->status, sizeof(int)) != cudaSuccess ||

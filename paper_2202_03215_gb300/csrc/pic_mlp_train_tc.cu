@@ -1,26 +1,32 @@
 // Closure-network training on the 5th-generation tensor cores (tcgen05): forward,
-// backward and weight gradients of one tile of 128 samples per CTA.
+// backward and weight gradients of tiles of 128 samples, one persistent CTA per SM.
 //
 // Every product is a tcgen05.mma of kind::f16 (BF16 operands in shared memory, FP32
 // accumulators in tensor memory), issued by one thread; the CTA's 512 threads run the
-// epilogues between them (tcgen05.ld of the accumulator rows, bias, GELU and its
-// derivative, BF16 conversion).  Operands use the canonical no-swizzle layouts: a tile
-// stored K-major for one product is read MN-major (transpose bit of the instruction
-// descriptor) by the next, so no transposed copy is made:
-//   forward   Z1 = X W1^T, A1 = gelu(Z1 + b1); Z2 = A1 W2^T, A2 = gelu(Z2 + b2);
-//             Y = A2 W3^T + b3
-//   backward  dY = 2 (Y - T) / (3 n); dA2 = dY W3; dZ2 = dA2 gelu'(Z2 + b2);
-//             dA1 = dZ2 W2; dZ1 = dA1 gelu'(Z1 + b1)
-//   gradients dW3^T = A2^T dY, dW2 = dZ2^T A1, dW1 = dZ1^T X; the bias gradients are the
-//             column sums of dZ (dZ^T times a tile of ones; dz is split into a BF16 high
-//             part and a BF16 low part so that the sums keep FP32 accuracy) and of dY
-//             (warp sums in FP32)
-// Tensor-memory columns: Z1 [0,128), Z2 [128,256) then dA1, Y [256,272), dA2 [272,400)
-// then dW2, dW3^T [400,416), gb2 [416,432), dW1 [432,448), gb1 [448,464).
-// The CTA writes its tile's partial gradient (the parameter layout, FP32) and its summed
-// squared error; the reduction kernel of pic_mlp.cu sums the tiles in a fixed order and
-// applies Adam.  Every wait is bounded: a wait that gives up sets *status, and the CTA
-// frees its tensor memory once no MMA it issued can still be running.
+// epilogues between them (tcgen05.ld of the accumulator rows, bias, GELU, BF16 conversion).
+// Operands use the canonical no-swizzle layouts: a tile stored K-major for one product is
+// read MN-major (transpose bit of the instruction descriptor) by the next, so no transposed
+// copy is made.  Per tile:
+//   R1  Z1 = X W1^T;          epilogue A1 = gelu(Z1 + b1), gelu'(Z1 + b1) stored over Z1
+//   R2  Z2 = A1 W2^T;         epilogue A2 = gelu(Z2 + b2), gelu'(Z2 + b2) stored over Z2, and
+//                             Y = A2 W3^T (three outputs: on the CUDA cores from the BF16 A2 and W3
+//                             an MMA would take); then dY = 2 (Y + b3 - T) / (3 n),
+//                             dA2 = dY W3 (CUDA cores, BF16-rounded dY and W3), dZ2 = dA2 gelu'
+//   R3  dW3^T += A2^T dY, gb2 += dZ2lo^T 1, dA1 = dZ2 W2 (waited for); dW2^T += A1^T dZ2 and
+//       gb2 += dZ2hi^T 1 run on under the epilogue dZ1 = dA1 gelu'
+//   R4  [dW1 | gb1] += dZ1^T [X 1] (X carries a column of ones, so column 15 is gb1); not waited
+//       for: the next tile's first commit covers it (and the unwaited half of R3)
+// dZ is stored as a BF16 high part and a BF16 low part: the weight gradients take the high
+// part (BF16 operands, like every product), the bias gradients (gb2, gb1) take both, so that
+// the sums keep FP32 accuracy.  gb3 and the squared error are warp sums in FP32.  The weight
+// gradients accumulate in tensor memory over the CTA's tiles (tiles b, b + G, b + 2G, .. of a
+// grid of G CTAs); the CTA writes them once as its partial, and the
+// reduction kernel of pic_mlp.cu sums the G partials in a fixed order and applies Adam.
+// Tensor-memory columns: Z1 then gelu'(Z1) [0,128), Z2 then gelu'(Z2) then dA1 [128,256),
+// dW2^T [272,400), dW3^T [400,416), gb2 [416,432), dW1 | gb1 [432,448), the low
+// part's [X 1] product (its column 15 completes gb1) [448,464).
+// Every wait is bounded: a wait that gives up sets *status, and the CTA frees its tensor
+// memory once no MMA it issued can still be running.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -36,13 +42,15 @@ using namespace mlpl;
 
 constexpr int TM = 128;              // samples per tile (MMA rows)
 constexpr int THREADS = 512;         // four threads per sample row in the epilogues (32 columns each)
+constexpr int ISSUER = 0;            // the thread that also issues, commits and waits for the MMAs
 constexpr int CW = NH / (THREADS / TM);   // columns per thread in the epilogues
+constexpr int XPT = (TM * NI + THREADS - 1) / THREADS;   // input values per thread per tile
 constexpr uint32_t kCols = 512;      // tensor-memory columns of the CTA
-constexpr uint32_t cZ1 = 0, cZ2 = 128, cY = 256, cA2d = 272, cW3t = 400, cGb2 = 416, cW1 = 432, cGb1 = 448;
+constexpr uint32_t cZ1 = 0, cZ2 = 128, cW2 = 272, cW3t = 400, cGb2 = 416, cW1 = 432, cW1lo = 448;
 
 struct __align__(1024) TrSmem {
   TrainW w;               // BF16 weights (canonical K-major)
-  bf X[TM * K1];          // inputs, K-major (K = 16 inputs, column 15 zero)
+  bf X[2][TM * K1];       // inputs of this tile and the next, K-major (K = 16: 15 inputs, then 1)
   bf dY[TM * N3];         // dL/dy, K-major (K = 16 outputs, columns 3..15 zero)
   bf ones[N3 * TM];       // B operand of the bias sums: N = 16, K = 128 samples, all ones
   bf A1[TM * NH];         // activations of layer 1 (K-major, K = hidden)
@@ -50,7 +58,9 @@ struct __align__(1024) TrSmem {
   bf dZ2[TM * NH];        // dL/dz2 (BF16 high part)
   bf dZlo[TM * NH];       // low BF16 parts of dz2, then of dz1
   float b1[NH], b2[NH], b3[N3];
-  float red[4][4];        // per-warp sums: dy of the three outputs, squared error
+  float W3[NO][NH];       // output weights rounded to BF16 (Y = A2 W3^T and dA2 = dY W3)
+  float yp[THREADS / TM][NO][TM];   // partial outputs of each column part
+  float red[4][4];        // per-warp sums over the CTA's tiles: dy of the three outputs, squared error
   unsigned long long mbar_w, mbar_mma;
   uint32_t tmem_slot;
   int ok;
@@ -125,63 +135,156 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// GELU (tanh form) and its derivative with the hardware tanh (relative error about 2^-11):
-// gelu = z (1 + th)/2, gelu' = (1 + th)/2 + z (1 - th^2) du/dz / 2, u = sqrt(2/pi)(z + 0.044715 z^3)
-__device__ __forceinline__ float gelu(float z) {
-  const float u = 0.7978845608028654f * z * (1.0f + 0.044715f * z * z);
-  float th;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(u));
-  const float h = 0.5f * z;
-  return h + h * th;
-}
-__device__ __forceinline__ float gelu_d(float z) {
-  const float c = 0.7978845608028654f, z2 = z * z;
-  float th;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(c * z * (1.0f + 0.044715f * z2)));
-  const float h = 0.5f * (1.0f + th);
-  return h + 0.5f * z * (1.0f - th * th) * c * (1.0f + 3.0f * 0.044715f * z2);
-}
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t *>(&v);
-}
-// eight values -> row r, columns c..c+7 of a K-major tile with K columns (16 bytes)
-__device__ __forceinline__ void put8(bf *tile, int r, int c, int K, const float *v) {
-  uint4 q;
-  q.x = pack2(v[0], v[1]); q.y = pack2(v[2], v[3]); q.z = pack2(v[4], v[5]); q.w = pack2(v[6], v[7]);
-  *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(tile) + cm_off(r, c, K)) = q;
+// 16 consecutive FP32 columns into this thread's tensor-memory lane
+__device__ __forceinline__ void st16(uint32_t taddr, const float v[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// forward epilogue: CW columns (c0..) of accumulator row r -> gelu(z + b) in BF16
-__device__ __forceinline__ void epi_act(bf *A, uint32_t tz, const float *b, int r, int c0) {
+// Pairs of FP32 values in one 64-bit register, operated on by the packed FP32 instructions
+// (.f32x2): half the instructions of the scalar form in the epilogues.
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f2 dup(float a) { return pk(a, a); }
+// the pair rounded to BF16, packed (first value in the low half: the lower address)
+__device__ __forceinline__ uint32_t bf2(f2 v) {
+  float a, b;
+  upk(v, a, b);
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+// the packed BF16 pair back to FP32 (exact)
+__device__ __forceinline__ f2 unbf2(uint32_t w) { return pk(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u)); }
+__device__ __forceinline__ f2 tanh2(f2 u) {
+  float a, b;
+  upk(u, a, b);
+  asm("tanh.approx.f32 %0, %0;" : "+f"(a));
+  asm("tanh.approx.f32 %0, %0;" : "+f"(b));
+  return pk(a, b);
+}
+
+// GELU (tanh form) and its derivative from one hardware tanh (relative error about 2^-11), on a
+// pair: u = sqrt(2/pi)(z + 0.044715 z^3), th = tanh u, h = (1 + th)/2,
+// gelu = z h, gelu' = h + z (1 - th^2) du/dz / 2
+__device__ __forceinline__ void gelu2(f2 z, f2 &g, f2 &d) {
+  const float c = 0.7978845608028654f, a = 0.044715f;
+  const f2 z2 = mul2(z, z);
+  const f2 th = tanh2(mul2(z, fma2(z2, dup(c * a), dup(c))));
+  const f2 h = fma2(th, dup(0.5f), dup(0.5f));
+  g = mul2(z, h);
+  const f2 q = mul2(z, fma2(z2, dup(1.5f * c * a), dup(0.5f * c)));
+  d = fma2(q, sub2(dup(1.0f), mul2(th, th)), h);
+}
+// four packed BF16 pairs -> row r, columns c..c+7 of a K-major tile with K columns (16 bytes)
+__device__ __forceinline__ void put8w(bf *tile, int r, int c, int K, uint32_t w0, uint32_t w1, uint32_t w2,
+                                      uint32_t w3) {
+  *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(tile) + cm_off(r, c, K)) = make_uint4(w0, w1, w2, w3);
+}
+__device__ __forceinline__ void put1(bf *tile, int r, int c, int K, float v) {
+  *reinterpret_cast<bf *>(reinterpret_cast<unsigned char *>(tile) + cm_off(r, c, K)) = __float2bfloat16_rn(v);
+}
+// 16 values (8 pairs) as BF16 high parts into H and the BF16-rounded rests into L, row r, columns c..c+15
+__device__ __forceinline__ void put16_split(bf *H, bf *L, int r, int c, const f2 v[8]) {
+  uint32_t hw[8], lw[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    hw[i] = bf2(v[i]);
+    lw[i] = bf2(sub2(v[i], unbf2(hw[i])));
+  }
+  put8w(H, r, c, NH, hw[0], hw[1], hw[2], hw[3]);
+  put8w(H, r, c + 8, NH, hw[4], hw[5], hw[6], hw[7]);
+  put8w(L, r, c, NH, lw[0], lw[1], lw[2], lw[3]);
+  put8w(L, r, c + 8, NH, lw[4], lw[5], lw[6], lw[7]);
+}
+
+// forward epilogue: CW columns (c0..) of accumulator row r -> gelu(z + b) in BF16 into A,
+// gelu'(z + b) in FP32 back into the accumulator's columns; with OUT, also this part's share
+// of the outputs y_o = sum_c a_c W3[o][c] (the BF16 a_c and W3 an MMA would take, FP32 sums)
+template <bool OUT>
+__device__ __forceinline__ void epi_act(bf *A, uint32_t tz, const float *b, int r, int c0, const float (*W3)[NH],
+                                        float (*yp)[TM]) {
+  f2 y0 = 0ull, y1 = 0ull, y2 = 0ull;   // (+0, +0) pairs
 #pragma unroll 1
   for (int c = c0; c < c0 + CW; c += 16) {
     float v[16];
+    uint32_t w[8];
     ld16(tz + (uint32_t)c, v);
+    const float2 *b2 = reinterpret_cast<const float2 *>(b + c);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + b[c + i]);
-    put8(A, r, c, NH, v);
-    put8(A, r, c + 8, NH, v + 8);
+    for (int i = 0; i < 8; ++i) {
+      const float2 bb = b2[i];
+      f2 g, d;
+      gelu2(add2(pk(v[2 * i], v[2 * i + 1]), pk(bb.x, bb.y)), g, d);
+      w[i] = bf2(g);
+      upk(d, v[2 * i], v[2 * i + 1]);
+      if (OUT) {
+        const f2 a = unbf2(w[i]);
+        y0 = fma2(a, reinterpret_cast<const f2 *>(&W3[0][c])[i], y0);
+        y1 = fma2(a, reinterpret_cast<const f2 *>(&W3[1][c])[i], y1);
+        y2 = fma2(a, reinterpret_cast<const f2 *>(&W3[2][c])[i], y2);
+      }
+    }
+    put8w(A, r, c, NH, w[0], w[1], w[2], w[3]);
+    put8w(A, r, c + 8, NH, w[4], w[5], w[6], w[7]);
+    st16(tz + (uint32_t)c, v);
+  }
+  if (OUT) {
+    float a, b2;
+    upk(y0, a, b2); yp[0][r] = a + b2;
+    upk(y1, a, b2); yp[1][r] = a + b2;
+    upk(y2, a, b2); yp[2][r] = a + b2;
   }
 }
-// backward epilogue: dz = dA gelu'(z + b), stored as BF16 high and low parts
-__device__ __forceinline__ void epi_dz(bf *D, bf *Dlo, uint32_t tda, uint32_t tz, const float *b, int r, int c0) {
-#pragma unroll 1
-  for (int c = c0; c < c0 + CW; c += 16) {
-    float a[16], z[16], hi[16], lo[16];
-    ld16(tda + (uint32_t)c, a);
-    ld16(tz + (uint32_t)c, z);
+
+// the tile's inputs: XPT values per thread (row-major X, NI per sample), in registers until stored
+__device__ __forceinline__ void load_x(const float *__restrict__ X, int s0, int rows, int tid, float xv[XPT]) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float dz = a[i] * gelu_d(z[i] + b[c + i]);
-      hi[i] = __bfloat162float(__float2bfloat16_rn(dz));
-      lo[i] = dz - hi[i];
-    }
-    put8(D, r, c, NH, hi);
-    put8(D, r, c + 8, NH, hi + 8);
-    put8(Dlo, r, c, NH, lo);
-    put8(Dlo, r, c + 8, NH, lo + 8);
+  for (int j = 0; j < XPT; ++j) {
+    const int e = tid + THREADS * j;
+    xv[j] = (e < rows * NI) ? __ldg(X + (size_t)s0 * NI + e) : 0.0f;
   }
+}
+__device__ __forceinline__ void put_x(bf *Xt, int rows, int tid, const float xv[XPT]) {
+#pragma unroll
+  for (int j = 0; j < XPT; ++j) {
+    const int e = tid + THREADS * j;
+    if (e < TM * NI) put1(Xt, e / NI, e % NI, K1, xv[j]);
+  }
+  if (tid < TM) put1(Xt, tid, NI, K1, tid < rows ? 1.0f : 0.0f);   // the ones column (W1's is zero)
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -194,7 +297,7 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
   const int q = w & 3, part = w >> 2;            // lane quadrant of the warp, column part
   const int r = 32 * q + lane;                   // accumulator row (sample, or hidden unit)
   const int c0 = CW * part;
-  const int tile = blockIdx.x, s0 = tile * TM;
+  const int ntiles = (n + TM - 1) / TM, G = gridDim.x;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (w == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su(&S.tmem_slot)),
@@ -202,18 +305,21 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // the tile's inputs (the caller's, ready before the launch) while the previous kernel of the
-  // stream may still run; the weights come from its Adam update: wait for it before reading them
-  const int rows = min(TM, n - s0);
-  for (int e = tid; e < TM * K1; e += THREADS) {
-    const int rr = e / K1, i = e % K1;
-    *reinterpret_cast<bf *>(reinterpret_cast<unsigned char *>(S.X) + cm_off(rr, i, K1)) =
-        __float2bfloat16_rn((rr < rows && i < NI) ? X[(size_t)(s0 + rr) * NI + i] : 0.0f);
-    *reinterpret_cast<bf *>(reinterpret_cast<unsigned char *>(S.dY) + cm_off(rr, i, N3)) = __float2bfloat16_rn(0.0f);
-    S.ones[e] = __float2bfloat16_rn(1.0f);
+  // the first tile's inputs (the caller's, ready before the launch) while the previous kernel of
+  // the stream may still run; the weights come from its Adam update: wait for it before reading them
+  float xv[XPT];
+  {
+    const int s0 = blockIdx.x * TM;
+    load_x(X, s0, min(TM, n - s0), tid, xv);
+    put_x(S.X[0], min(TM, n - s0), tid, xv);
   }
+  for (int e = tid; e < TM * N3; e += THREADS) {
+    S.ones[e] = __float2bfloat16_rn(1.0f);
+    S.dY[e] = __float2bfloat16_rn(0.0f);
+  }
+  if (tid < 16) S.red[tid >> 2][tid & 3] = 0.0f;
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (tid == 0) {
+  if (tid == ISSUER) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su(&S.mbar_w)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su(&S.mbar_mma)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -228,9 +334,13 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
                    : "memory");
     }
   }
-  for (int e = tid; e < NH; e += THREADS) { S.b1[e] = P[ob1 + e]; S.b2[e] = P[ob2 + e]; }
+  for (int e = tid; e < NH; e += THREADS) {
+    S.b1[e] = P[ob1 + e];
+    S.b2[e] = P[ob2 + e];
+  }
+  for (int e = tid; e < NO * NH; e += THREADS) S.W3[e / NH][e % NH] = __bfloat162float(__float2bfloat16_rn(P[oW3 + e]));
   if (tid < N3) S.b3[tid] = tid < NO ? P[ob3 + tid] : 0.0f;
-  if (tid == 0) {
+  if (tid == ISSUER) {
     const bool ok = wait_phase(&S.mbar_w, 0, spin);
     S.ok = ok ? 1 : 0;
     if (!ok) atomicExch(status, 1);   // nothing was issued on the barrier: nothing is in flight
@@ -240,9 +350,9 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
   const uint32_t trow = tm + ((uint32_t)(32 * q) << 16);   // this warp's lanes
   uint32_t ph = 0;
   bool pending = false;   // an MMA batch was committed whose completion was not seen
-  // thread 0 issues, commits and waits; the barrier passes the outcome on
+  // the issuing thread issues, commits and waits; the barrier passes the outcome on
   auto run = [&](auto issue) -> bool {
-    if (tid == 0) {
+    if (tid == ISSUER) {
       issue();
       commit(&S.mbar_mma);
       S.ok = wait_phase(&S.mbar_mma, ph, spin) ? 1 : 0;
@@ -256,107 +366,147 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
     return ok;
   };
   bool ok = S.ok != 0;
-  constexpr uint32_t kM = 4096, kX = 512;   // bytes per K step of 16 samples: 128-wide and 16-wide tiles
-  if (ok) ok = run([&] { mma(tm + cZ1, dk(S.X, K1), dk(S.w.W1, K1), idesc(TM, NH, 0, 0), 0u); });
-  if (ok) {
-    epi_act(S.A1, trow + cZ1, S.b1, r, c0);
+  constexpr uint32_t kM = 4096 >> 4, kX = 512 >> 4;   // descriptor steps of 16 samples: 128-wide, 16-wide tiles
+  int it = 0;
+  for (int tile = blockIdx.x; ok && tile < ntiles; tile += G, ++it) {
+    const int s0 = tile * TM, rows = min(TM, n - s0), buf = it & 1;
+    const uint32_t fresh = it == 0 ? 0u : 1u;   // accumulate into the gradients after the first tile
+    bf *Xt = S.X[buf];
+    // targets of this thread's row and the next tile's inputs, in flight during the products
+    float tg[NO];
+    const int nt = tile + G, ns0 = nt * TM, nrows = nt < ntiles ? min(TM, n - ns0) : 0;
+    {
+#pragma unroll
+      for (int o = 0; o < NO; ++o) tg[o] = r < rows ? __ldg(T + (size_t)(s0 + r) * NO + o) : 0.0f;
+      load_x(X, ns0, nrows, tid, xv);
+    }
+    // R1 (its commit also covers the previous tile's dW1 products)
+    ok = run([&] { mma(tm + cZ1, dk(Xt, K1), dk(S.w.W1, K1), idesc(TM, NH, 0, 0), 0u); });
+    if (!ok) break;
+    epi_act<false>(S.A1, trow + cZ1, S.b1, r, c0, S.W3, S.yp[part]);
     handoff();
     ok = run([&] {
       for (uint32_t k = 0; k < NH / 16; ++k)
         mma(tm + cZ2, dk(S.A1, NH) + k * 16u, dk(S.w.W2, NH) + k * 16u, idesc(TM, NH, 0, 0), k);
     });
-  }
-  if (ok) {
-    epi_act(S.A2, trow + cZ2, S.b2, r, c0);
+    if (!ok) break;
+    epi_act<true>(S.A2, trow + cZ2, S.b2, r, c0, S.W3, S.yp[part]);
     handoff();
-    ok = run([&] {
-      for (uint32_t k = 0; k < NH / 16; ++k)
-        mma(tm + cY, dk(S.A2, NH) + k * 16u, dk(S.w.W3, NH) + k * 16u, idesc(TM, N3, 0, 0), k);
-    });
-  }
-  if (ok) {
-    // outputs, loss and dL/dy (rows of samples past n contribute nothing)
-    if (part == 0) {
-      float v[16];
-      ld16(trow + cY, v);
-      const bool valid = r < rows;
+    {
+      // outputs (the column parts' shares summed in a fixed order), loss and dL/dy of row r
+      // (rows of samples past n contribute nothing); every thread of the row computes them, the
+      // first column part stores them
       float dy[NO], sq = 0.0f;
 #pragma unroll
       for (int o = 0; o < NO; ++o) {
-        const float d = valid ? v[o] + S.b3[o] - T[(size_t)(s0 + r) * NO + o] : 0.0f;
+        float y = S.yp[0][o][r];
+#pragma unroll
+        for (int p = 1; p < THREADS / TM; ++p) y += S.yp[p][o][r];
+        const float d = r < rows ? y + S.b3[o] - tg[o] : 0.0f;
         sq += d * d;
         dy[o] = 2.0f * d * inv_n3;
-        *reinterpret_cast<bf *>(reinterpret_cast<unsigned char *>(S.dY) + cm_off(r, o, N3)) = __float2bfloat16_rn(dy[o]);
       }
+      if (part == 0) {
+        put8w(S.dY, r, 0, N3, bf2(pk(dy[0], dy[1])), bf2(pk(dy[2], 0.0f)), 0u, 0u);
+        float s0v = dy[0], s1v = dy[1], s2v = dy[2];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dy[0] += __shfl_xor_sync(0xffffffffu, dy[0], o);
-        dy[1] += __shfl_xor_sync(0xffffffffu, dy[1], o);
-        dy[2] += __shfl_xor_sync(0xffffffffu, dy[2], o);
-        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        for (int o = 16; o > 0; o >>= 1) {
+          s0v += __shfl_xor_sync(0xffffffffu, s0v, o);
+          s1v += __shfl_xor_sync(0xffffffffu, s1v, o);
+          s2v += __shfl_xor_sync(0xffffffffu, s2v, o);
+          sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        }
+        if (lane == 0) { S.red[q][0] += s0v; S.red[q][1] += s1v; S.red[q][2] += s2v; S.red[q][3] += sq; }
       }
-      if (lane == 0) { S.red[q][0] = dy[0]; S.red[q][1] = dy[1]; S.red[q][2] = dy[2]; S.red[q][3] = sq; }
+      // dZ2 = (dY W3) gelu'(Z2 + b2), as BF16 high and low parts
+      const f2 dy0 = dup(__bfloat162float(__float2bfloat16_rn(dy[0]))),
+               dy1 = dup(__bfloat162float(__float2bfloat16_rn(dy[1]))),
+               dy2 = dup(__bfloat162float(__float2bfloat16_rn(dy[2])));
+#pragma unroll 1
+      for (int c = c0; c < c0 + CW; c += 16) {
+        float d[16];
+        f2 dz[8];
+        ld16(trow + cZ2 + (uint32_t)c, d);
+        const f2 *w0 = reinterpret_cast<const f2 *>(&S.W3[0][c]), *w1 = reinterpret_cast<const f2 *>(&S.W3[1][c]),
+                 *w2 = reinterpret_cast<const f2 *>(&S.W3[2][c]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          dz[i] = mul2(fma2(dy2, w2[i], fma2(dy1, w1[i], mul2(dy0, w0[i]))), pk(d[2 * i], d[2 * i + 1]));
+        put16_split(S.dZ2, S.dZlo, r, c, dz);
+      }
+      // the next tile's inputs: its buffer was last read by the previous tile's products
+      put_x(S.X[buf ^ 1], nrows, tid, xv);
     }
     handoff();
+    // R3, first the products whose operands the dZ1 epilogue overwrites (A2's buffer, dZlo) and
+    // dA1, which it reads; waited for
     ok = run([&] {
-      // dA2 = dY W3 (W3 read MN-major: N = hidden, K = outputs)
-      mma(tm + cA2d, dk(S.dY, N3), dmn(S.w.W3, 128, 2048), idesc(TM, NH, 0, 1), 0u);
-      // dW3^T = A2^T dY (both MN-major, K = samples)
+      // dW3^T += A2^T dY (both MN-major, K = samples)
       for (uint32_t k = 0; k < TM / 16; ++k)
-        mma(tm + cW3t, dmn(S.A2, 128, 2048) + k * (kM >> 4), dmn(S.dY, 128, 256) + k * (kX >> 4),
-            idesc(TM, N3, 1, 1), k);
-    });
-  }
-  if (ok) {
-    epi_dz(S.dZ2, S.dZlo, trow + cA2d, trow + cZ2, S.b2, r, c0);
-    handoff();
-    ok = run([&] {
-      // dA1 = dZ2 W2 (W2 read MN-major: N = hidden in, K = hidden out), into Z2's columns
+        mma(tm + cW3t, dmn(S.A2, 128, 2048) + k * kM, dmn(S.dY, 128, 256) + k * kX, idesc(TM, N3, 1, 1), k | fresh);
+      // gb2 += column sums of dz2 (low parts here, high parts below) against a tile of ones
+      for (uint32_t k = 0; k < TM / 16; ++k)
+        mma(tm + cGb2, dmn(S.dZlo, 128, 2048) + k * kM, dk(S.ones, TM) + k * 16u, idesc(NH, N3, 1, 0), k | fresh);
+      // dA1 = dZ2 W2 (W2 read MN-major: N = hidden in, K = hidden out), over gelu'(Z2)
       for (uint32_t k = 0; k < NH / 16; ++k)
-        mma(tm + cZ2, dk(S.dZ2, NH) + k * 16u, dmn(S.w.W2, 128, 2048) + k * (kM >> 4), idesc(TM, NH, 0, 1), k);
-      // dW2 = dZ2^T A1 (both MN-major, K = samples), into dA2's columns
-      for (uint32_t k = 0; k < TM / 16; ++k)
-        mma(tm + cA2d, dmn(S.dZ2, 128, 2048) + k * (kM >> 4), dmn(S.A1, 128, 2048) + k * (kM >> 4),
-            idesc(NH, NH, 1, 1), k);
-      // gb2 = column sums of dz2 (high and low parts) against a tile of ones
-      for (uint32_t k = 0; k < TM / 16; ++k)
-        mma(tm + cGb2, dmn(S.dZ2, 128, 2048) + k * (kM >> 4), dk(S.ones, TM) + k * 16u, idesc(NH, N3, 1, 0), k);
-      for (uint32_t k = 0; k < TM / 16; ++k)
-        mma(tm + cGb2, dmn(S.dZlo, 128, 2048) + k * (kM >> 4), dk(S.ones, TM) + k * 16u, idesc(NH, N3, 1, 0), 1u);
+        mma(tm + cZ2, dk(S.dZ2, NH) + k * 16u, dmn(S.w.W2, 128, 2048) + k * kM, idesc(TM, NH, 0, 1), k);
     });
-  }
-  if (ok) {
-    bf *dZ1 = S.A2;   // A2 was last read by the dW3 product, which has completed
-    epi_dz(dZ1, S.dZlo, trow + cZ2, trow + cZ1, S.b1, r, c0);
+    if (!ok) break;
+    // then the products that read only A1 and dZ2 (untouched until the next tile's epilogues,
+    // which follow the next commit): they run under the dZ1 epilogue
+    if (tid == ISSUER) {
+      // dW2^T += A1^T dZ2 (both MN-major, K = samples): accumulator row = hidden unit in, so that
+      // the partial's rows of W2 are written by consecutive lanes
+      for (uint32_t k = 0; k < TM / 16; ++k)
+        mma(tm + cW2, dmn(S.A1, 128, 2048) + k * kM, dmn(S.dZ2, 128, 2048) + k * kM, idesc(NH, NH, 1, 1), k | fresh);
+      for (uint32_t k = 0; k < TM / 16; ++k)
+        mma(tm + cGb2, dmn(S.dZ2, 128, 2048) + k * kM, dk(S.ones, TM) + k * 16u, idesc(NH, N3, 1, 0), 1u);
+    }
+    {
+      // dZ1 = dA1 gelu'(Z1 + b1) into A2's buffer (last read by the dW3 products, completed)
+      // and dZlo (last read by the gb2 products of the low parts, completed)
+      bf *dZ1 = S.A2;
+#pragma unroll 1
+      for (int c = c0; c < c0 + CW; c += 16) {
+        float a[16], d[16];
+        f2 dz[8];
+        ld16(trow + cZ2 + (uint32_t)c, a);
+        ld16(trow + cZ1 + (uint32_t)c, d);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dz[i] = mul2(pk(a[2 * i], a[2 * i + 1]), pk(d[2 * i], d[2 * i + 1]));
+        put16_split(dZ1, S.dZlo, r, c, dz);
+      }
+    }
     handoff();
-    ok = run([&] {
-      // dW1 = dZ1^T X (both MN-major, K = samples); gb1 as gb2
+    // R4: [dW1 | gb1] += dZ1^T [X 1] (both MN-major, K = samples), high and low parts apart
+    if (tid == ISSUER) {
       for (uint32_t k = 0; k < TM / 16; ++k)
-        mma(tm + cW1, dmn(dZ1, 128, 2048) + k * (kM >> 4), dmn(S.X, 128, 256) + k * (kX >> 4), idesc(NH, N3, 1, 1), k);
+        mma(tm + cW1, dmn(S.A2, 128, 2048) + k * kM, dmn(Xt, 128, 256) + k * kX, idesc(NH, N3, 1, 1), k | fresh);
       for (uint32_t k = 0; k < TM / 16; ++k)
-        mma(tm + cGb1, dmn(dZ1, 128, 2048) + k * (kM >> 4), dk(S.ones, TM) + k * 16u, idesc(NH, N3, 1, 0), k);
-      for (uint32_t k = 0; k < TM / 16; ++k)
-        mma(tm + cGb1, dmn(S.dZlo, 128, 2048) + k * (kM >> 4), dk(S.ones, TM) + k * 16u, idesc(NH, N3, 1, 0), 1u);
-    });
+        mma(tm + cW1lo, dmn(S.dZlo, 128, 2048) + k * kM, dmn(Xt, 128, 256) + k * kX, idesc(NH, N3, 1, 1),
+            k | fresh);
+    }
   }
+  // the last tile's dW1 products
+  if (ok) ok = run([] {});
   if (ok) {
-    // the tile's partial gradient: accumulator row r is hidden unit r
-    float *gp = gpart + (size_t)tile * GSTRIDE;
+    // the CTA's partial gradient: accumulator row r is hidden unit r (the input unit of W2)
+    float *gp = gpart + (size_t)blockIdx.x * GSTRIDE;
 #pragma unroll 1
     for (int c = c0; c < c0 + CW; c += 16) {
       float v[16];
-      ld16(trow + cA2d + (uint32_t)c, v);
-      float4 *dst = reinterpret_cast<float4 *>(gp + oW2 + r * NH + c);   // oW2 and the row stride are multiples of 4
+      ld16(trow + cW2 + (uint32_t)c, v);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      for (int i = 0; i < 16; ++i) gp[oW2 + (c + i) * NH + r] = v[i];
     }
     if (part == 0) {
       float v[16];
       ld16(trow + cW1, v);
 #pragma unroll
       for (int i = 0; i < NI; ++i) gp[oW1 + r * NI + i] = v[i];
-      ld16(trow + cGb1, v);
-      gp[ob1 + r] = v[0];
+      const float gb1 = v[NI];
+      ld16(trow + cW1lo, v);
+      gp[ob1 + r] = gb1 + v[NI];
       ld16(trow + cGb2, v);
       gp[ob2 + r] = v[0];
       ld16(trow + cW3t, v);
@@ -370,11 +520,11 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
         sq += S.red[k][3];
       }
       for (int o = 0; o < NO; ++o) gp[ob3 + o] = gb3[o];
-      lpart[tile] = sq;
+      lpart[blockIdx.x] = sq;
     }
   }
   // a batch whose wait gave up: wait once more (bounded) before the tensor memory is freed
-  if (pending && tid == 0) wait_phase(&S.mbar_mma, ph ^ 1u, spin);
+  if (pending && tid == ISSUER) wait_phase(&S.mbar_mma, ph ^ 1u, spin);
   tc_before();
   __syncthreads();
   tc_after();
@@ -383,10 +533,11 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
 
 }  // namespace
 
-// one training tile kernel per 128 samples, with programmatic stream serialization (the next
-// kernel of the stream may be scheduled while this one drains)
+// the training tiles of n samples on `ctas` persistent CTAs (each writes one partial), with
+// programmatic stream serialization (the next kernel of the stream may be scheduled while this
+// one drains)
 int mlp_train_tiles_tc(const float *P, const void *Wb, const float *X, const float *T, int n, float inv_n3,
-                       float *gpart, float *lpart, int *status, int spin, unsigned hook, cudaStream_t st) {
+                       float *gpart, float *lpart, int ctas, int *status, int spin, unsigned hook, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_mlp_tile_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrSmem)) !=
@@ -394,6 +545,7 @@ int mlp_train_tiles_tc(const float *P, const void *Wb, const float *X, const flo
       return PIC_ECUDA;
     attr = true;
   }
+  if (n <= 0 || ctas <= 0 || ctas > (n + TM - 1) / TM) return PIC_EINVAL;
   cudaLaunchAttribute pdl;
   pdl.id = cudaLaunchAttributeProgrammaticStreamSerialization;
   pdl.val.programmaticStreamSerializationAllowed = 1;
@@ -401,7 +553,7 @@ int mlp_train_tiles_tc(const float *P, const void *Wb, const float *X, const flo
   cfg.stream = st;
   cfg.attrs = &pdl;
   cfg.numAttrs = 1;
-  cfg.gridDim = dim3((n + TM - 1) / TM);
+  cfg.gridDim = dim3(ctas);
   cfg.blockDim = dim3(THREADS);
   cfg.dynamicSmemBytes = sizeof(TrSmem);
   return cudaLaunchKernelEx(&cfg, k_mlp_tile_tc, P, reinterpret_cast<const TrainW *>(Wb), X, T, n, inv_n3, gpart,

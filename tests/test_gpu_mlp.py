@@ -69,10 +69,10 @@ def _gradient_magnitudes(P, X, T):
 C_BF16 = 0.25   # measured worst 0.09 (W2) on a GB300
 
 
-def test_gradients_match_the_oracle_element_by_element():
+def _check_gradients(n, pseed, dseed):
     import torch
-    P = _params(11)
-    X, T = _data(300, 12)          # 5 tiles of 64, the last one ragged
+    P = _params(pseed)
+    X, T = _data(n, dseed)
     m = pb.Mlp()
     m.set_params(P)
     loss, g = m.grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
@@ -82,12 +82,22 @@ def test_gradients_match_the_oracle_element_by_element():
     mag = _gradient_magnitudes(P, X64, T64)
     ratio = np.abs(g - go) / (2.0 ** -8 * mag + 1e-30)
     worst = {k: float(ratio[a:b].max()) for k, (a, b) in GROUPS.items()}
-    print("gradient error / (2^-8 sum|terms|), worst per group:", worst)
+    print(f"n={n}: gradient error / (2^-8 sum|terms|), worst per group:", worst)
     for k, (a, b) in GROUPS.items():
         assert worst[k] <= C_BF16, (k, worst[k], int(np.argmax(ratio[a:b])))
     # and against the unrounded FP64 network: the BF16 rounding error
     _, _, g64 = oracle.mlp_forward_backward(P, X64, T64)
     assert np.linalg.norm(g - g64) < 5e-2 * np.linalg.norm(g64)
+
+
+def test_gradients_match_the_oracle_element_by_element():
+    _check_gradients(300, 11, 12)          # 3 tiles of 128, the last one ragged
+
+
+def test_gradients_accumulated_over_several_tiles_per_cta():
+    # 313 tiles of 128 (the last holds 64 samples) on at most one CTA per SM: every CTA
+    # accumulates the weight gradients of two or three tiles in tensor memory
+    _check_gradients(40000, 21, 22)
 
 
 def test_forward_matches_the_oracle():
