@@ -248,7 +248,9 @@ def batched_vs_serial(pb, w, torch, steps: int, warmup: int, n_columns: int = 64
     cols = w.config_batch_sweep(n_columns=n_columns)
     sub = cols[0].ion_subcycle
     b = pb.Batch(cols)
-    b.step(warmup + 3)                      # three autotuning steps, then warm-up
+    tuning = b.tune()                       # the autotuner's steps (it times candidate schedules)
+    _, mult_e, mult_i = b.schedule()
+    b.step(warmup)
     s0 = b.columns[0].stats()["step"]
     units = sum(pushed_steps(s0, steps, c.n_e0, c.n_i0, sub) for c in cols)
     ext = torch.cuda.ExternalStream(b.stream())
@@ -279,6 +281,7 @@ def batched_vs_serial(pb, w, torch, steps: int, warmup: int, n_columns: int = 64
     return {"columns": n_columns, "steps": steps, "pushed_particle_steps": units,
             "batched": units / t_batch, "serial": units / t_serial, "unit": UNIT,
             "speedup": t_serial / t_batch, "launches_per_ion_cycle": launches,
+            "schedule": {"tuning_steps": tuning, "ctas_per_sm_electrons": mult_e, "ctas_per_sm_ions": mult_i},
             "workload": "64 columns, seed 42: L 0.05-0.40 m, p 0.3-3 Torr, I 0.1-5 mA, 1e5-5e6 particles "
                         "per species, 2048-16384 cells, Ar/Ne alternating, dt 5e-12 s, MIXED"}
 

@@ -275,9 +275,14 @@ int pic_get_stats(pic_handle *h, pic_stats *out);
 /* Batched columns: n independent periodic columns (uneven lengths, cell counts,
  * pressures, particle counts, gases) advanced together, one kernel launch per
  * phase of the step for all columns, on a CTA schedule in proportion to each
- * column's particles (the first pic_step_batch steps time several schedules
- * and keep the fastest; the schedule never changes results), with the
- * plain ion cycles replayed from a captured CUDA graph.  Column i keys its
+ * column's particles, with the plain ion cycles replayed from a captured
+ * CUDA graph.  The schedule has mult x SMs CTAs per species; the first steps
+ * tune mult per species (1, 2, 3, 4, 6 or 8, each timed twice on that
+ * species' push kernel, electrons first, then ions on their steps; no graph
+ * replay meanwhile) and keep the fastest; the choice is cached for the life
+ * of the process by batch shape (SMs, precision, and per column the cells and
+ * particle counts rounded to powers of two).  The schedule never changes
+ * results.  Column i keys its
  * random numbers with column index i (params[i].column is overridden), so
  * column i of a batch evolves bit for bit like a lone handle created with
  * column = i.  All columns need equal dt, ion_subcycle, precision,
@@ -290,6 +295,11 @@ int pic_step_batch(pic_handle *batch, int64_t n);
 pic_handle *pic_batch_column(pic_handle *batch, int i);
 /* Number of columns of a batch; 0 for NULL or a single column. */
 int pic_batch_size(pic_handle *batch);
+/* The batch's CTA multipliers (electrons, ions; either pointer may be NULL):
+ * returns 1 once tuning has finished (or came from the cache), 0 while the
+ * next steps still tune (the values are those in use), PIC_EINVAL for a
+ * handle that is not a batch. */
+int pic_batch_schedule(pic_handle *batch, int *mult_e, int *mult_i);
 
 /* Per-particle process code of the last step (needs PIC_FLAG_RECORD_CODES):
  * -1 no collision, -2 removed by the radial loss, else the xsec index.
@@ -460,7 +470,7 @@ int pic_two_term(const pic_xsec *xs, int n_xsec, double gas_mass_amu, const doub
  *  0. nu_i + dnu at every cell; nu_w fixed, or <n (nu_i + dnu)>/<n> with pair losses;
  *  1. continuity, backward Euler in the ambipolar diffusion and the losses:
  *       n'_j (1 + dt nu_w) - dt/dx^2 [a_{j+1/2}((nD_e)'_{j+1} - (nD_e)'_j) - a_{j-1/2}((nD_e)'_j - (nD_e)'_{j-1})]
- *         = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i + dnu) - dt/dx (dG_{j+1/2} - dG_{j-1/2}),
+ *         + dt/dx (dG_{j+1/2} - dG_{j-1/2}) = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i + dnu),
  *     a = mu_i/(mu_e + mu_i), b = 1 - a (eq. 11);
  *  2. Gamma_{j+1/2} (eq. 11, plus dG) and E_{j+1/2} from n', with
  *     E = -d_x(n D_e)/(n mu_e) + Gamma_T/(n (mu_e + mu_i)) (eq. 10 combined with eq. 12,
@@ -470,9 +480,13 @@ int pic_two_term(const pic_xsec *xs, int n_xsec, double gas_mass_amu, const doub
  *     (eqs. 8-9 with beta = 3/2 Te mu_eps, G = 3/2 Te D_eps) and the heating
  *     P_j = -(Gamma E)_{j+1/2, j-1/2} averaged (eq. 5);
  *  4. Te' clamped to the table's range.
- * dG, dH, dnu: closure corrections (flux per electron, energy flux per
- * electron, ionization frequency) at cells, put on faces as
- * (n_j d_j + n_{j+1} d_{j+1})/2 with the step's starting n.
+ * g, h, dnu: closure corrections at cells (flux per electron, energy flux per
+ * electron, ionization frequency).  The flux corrections are implicit, as
+ * first-order upwind advection by the face velocities gf = (g_j + g_{j+1})/2
+ * and wf = (w_j + w_{j+1})/2, w = h/Te (the step's starting Te):
+ * dG_{j+1/2} = max(gf,0) n'_j + min(gf,0) n'_{j+1} in the continuity matrix
+ * and in Gamma, dH_{j+1/2} = max(wf,0) n'_j Te'_j + min(wf,0) n'_{j+1} Te'_{j+1}
+ * in the energy matrix: n' stays positive at any dt.
  * Each tridiagonal system is cyclic and is solved by parallel cyclic
  * reduction in shared memory (one thread block per column). */
 typedef struct pic_fluid_column {

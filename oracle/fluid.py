@@ -26,8 +26,8 @@ cells; coefficients from the table at the step's starting T):
  1. continuity, backward Euler in the diffusion and the losses, explicit in the
     rest (ionization explicit, losses implicit: n' stays positive):
       n'_j (1 + dt nu_w) - dt/dx^2 [a_{j+1/2} ((nD)'_{j+1} - (nD)'_j) - a_{j-1/2} ((nD)'_j - (nD)'_{j-1})]
+          + dt/dx (dG_{j+1/2} - dG_{j-1/2})
         = n_j + dt/dx (b_{j+1/2} - b_{j-1/2}) Gamma_T + dt n_j (nu_i,j + dnu_j)
-          - dt/dx (dG_{j+1/2} - dG_{j-1/2})
     a = mu_i/(mu_e + mu_i), b = mu_e/(mu_e + mu_i) at cells, D = D_e;
  2. Gamma_{j+1/2} from n' (eq. 11) plus dG_{j+1/2}; E_{j+1/2} from n' (eq. 17);
  3. energy, backward Euler in T' for the conduction, the energy drift and the
@@ -38,9 +38,16 @@ cells; coefficients from the table at the step's starting T):
                   - 3/2 ((n' D_eps T')_{j+1} - (n' D_eps T')_j)/dx + dH_{j+1/2},
       P_j = -(Gamma_{j+1/2} E_{j+1/2} + Gamma_{j-1/2} E_{j-1/2}) / 2;
  4. T' clamped to the table's range.
-dG, dH, dnu are optional closure corrections per cell (flux per electron,
-energy flux per electron, ionization frequency), put on faces as
-(n_j d_j + n_{j+1} d_{j+1}) / 2 with the step's starting n.
+g, h, dnu are optional closure corrections per cell (flux per electron,
+energy flux per electron, ionization frequency).  The two flux corrections
+enter implicitly, as first-order upwind advection by the face velocities
+gf = (g_j + g_{j+1}) / 2 and wf = (w_j + w_{j+1}) / 2, w = h / T (T of the
+step's start): dG_{j+1/2} = max(gf, 0) n'_j + min(gf, 0) n'_{j+1} is part of
+the continuity matrix (and of Gamma in step 2), dH_{j+1/2} =
+max(wf, 0) n'_j T'_j + min(wf, 0) n'_{j+1} T'_{j+1} part of the energy matrix.
+Backward-Euler upwind advection keeps the continuity matrix an M-matrix: n'
+stays positive at any time step, where central differences of a cell-to-cell
+varying g do not.
 With pair losses (col["pair"] true) nu_w = sum(n (nu_i + dnu)) / sum(n) at the
 step's start: the continuum form of the particle model's pair losses.
 Table lookup: x = (T - T0)/dT clamped to [0, nT - 1], i = min(floor x, nT - 2),
@@ -122,11 +129,11 @@ def step(col, tab, n, T, dt, corr=None):
     dx = col["L_m"] / N
     GT, nu_w = col["Gamma_T"], col["nu_w"]
     c = coefficients(col, tab, T)
-    dG = dH = None
+    g = w = None
     nu_i = c["nu_i"]
     if corr is not None:
-        dG = face(n * corr[0])
-        dH = face(n * corr[1])
+        g = corr[0]                # flux per electron: a velocity
+        w = corr[1] / T            # energy flux per electron over T: a velocity
         nu_i = nu_i + corr[2]
     if col.get("pair"):      # as many electrons leave as are created, uniformly per electron
         nu_w = np.sum(n * nu_i) / np.sum(n)
@@ -140,13 +147,16 @@ def step(col, tab, n, T, dt, corr=None):
     up = -r * af * np.roll(D, -1)
     bf = face(c["b"])
     rhs = n + dt / dx * (bf - np.roll(bf, 1)) * GT + dt * n * nu_i
-    if dG is not None:
-        rhs = rhs - dt / dx * (dG - np.roll(dG, 1))
+    if g is not None:             # + dt/dx (dG_{j+1/2} - dG_{j-1/2}) on the left, upwind
+        gp, gm = np.maximum(face(g), 0.0), np.minimum(face(g), 0.0)     # at faces j+1/2
+        lo = lo - dt / dx * np.roll(gp, 1)
+        dg = dg + dt / dx * (gp - np.roll(gm, 1))
+        up = up + dt / dx * gm
     n1 = cyclic_solve(lo, dg, up, rhs)
     # 2. flux and field from n'
     Gam, E = flux_and_field(col, c, n1)
-    if dG is not None:
-        Gam = Gam + dG
+    if g is not None:
+        Gam = Gam + gp * n1 + gm * np.roll(n1, -1)
     P = -0.5 * (Gam * E + np.roll(Gam * E, 1))
     # 3. energy
     s = dt / dx
@@ -159,8 +169,11 @@ def step(col, tab, n, T, dt, corr=None):
     up = s * (-0.75 * mep * Ep - k * np.roll(De, -1)) * np.roll(n1, -1)
     lo = s * (0.75 * mem * Em - k * np.roll(De, 1)) * np.roll(n1, 1)
     rhs = 1.5 * n * T + dt * P - dt * n1 * (c["L"] - c["dL"] * T)
-    if dH is not None:
-        rhs = rhs - s * (dH - np.roll(dH, 1))
+    if w is not None:             # + s (dH_{j+1/2} - dH_{j-1/2}) on the left, upwind
+        wp, wm = np.maximum(face(w), 0.0), np.minimum(face(w), 0.0)
+        lo = lo - s * np.roll(wp * n1, 1)
+        dg = dg + s * (wp - np.roll(wm, 1)) * n1
+        up = up + s * wm * np.roll(n1, -1)
     T1 = cyclic_solve(lo, dg, up, rhs)
     T1 = np.clip(T1, tab["T0"], tab["T0"] + (tab["nT"] - 1) * tab["dT"])
     return n1, T1

@@ -121,6 +121,7 @@ def lib() -> C.CDLL:
         L.pic_batch_column.argtypes = [C.c_void_p, C.c_int]
         L.pic_batch_column.restype = C.c_void_p
         L.pic_batch_size.argtypes = [C.c_void_p]
+        L.pic_batch_schedule.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.pic_mlp_nparam.restype = C.c_int
         L.pic_mlp_create.argtypes = [C.c_uint64, C.POINTER(C.c_void_p)]
         L.pic_mlp_free.argtypes = [C.c_void_p]
@@ -453,6 +454,22 @@ class Batch:
 
     def step(self, n: int = 1) -> None:
         _check(self.L.pic_step_batch(self.h, n), self.h)
+
+    def schedule(self) -> tuple:
+        """(tuned, CTA multiplier of the electrons, of the ions): tuned is False while the next
+        steps still time candidate schedules."""
+        me, mi = C.c_int(), C.c_int()
+        rc = self.L.pic_batch_schedule(self.h, C.byref(me), C.byref(mi))
+        _check(min(rc, 0), self.h)
+        return rc == 1, me.value, mi.value
+
+    def tune(self, max_steps: int = 1000) -> int:
+        """Step until the schedule is tuned (at most max_steps); returns the steps taken."""
+        k = 0
+        while not self.schedule()[0] and k < max_steps:
+            self.step(1)
+            k += 1
+        return k
 
     def stream(self) -> int:
         return self.L.pic_stream(self.h) or 0

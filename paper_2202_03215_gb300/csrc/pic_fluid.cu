@@ -285,7 +285,8 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
       float g0, h0, n0, g1, h1, n1;
       corr_at(K, c.off + j, g0, h0, n0);
       corr_at(K, c.off + jp, g1, h1, n1);
-      S.G[j] = 0.5f * (S.n[j] * g0 + S.n[jp] * g1);
+      const float gf = 0.5f * (g0 + g1);   // upwind correction flux at face j+1/2 (starting n)
+      S.G[j] = fmaxf(gf, 0.0f) * S.n[j] + fminf(gf, 0.0f) * S.n[jp];
       if (K.netY && K.nu_bound > 0.0f) n0 = fminf(fmaxf(n0, -K.nu_bound * nu), K.nu_bound * nu);
       nu += n0;
     }
@@ -299,20 +300,29 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
     nu_w = b / a;
   }
   __syncthreads();
-  // 2. continuity: A dn = rhs - A n
+  // 2. continuity: A dn = rhs - A n; the correction flux max(gf, 0) n'_j + min(gf, 0) n'_{j+1},
+  //    gf = (g_j + g_{j+1}) / 2, is implicit (upwind advection by gf: in A, which stays an
+  //    M-matrix), its value at the starting n in the residual
   for (int j = t; j < N; j += kThreads) {
     const int jm = (j - 1) & (N - 1), jp = (j + 1) & (N - 1);
     const float af = 0.5f * (S.A[j] + S.A[jp]), am = 0.5f * (S.A[jm] + S.A[j]);
     const float nu = S.E[j];
-    float dGf = 0.0f, dGm = 0.0f;
+    float dGf = 0.0f, dGm = 0.0f, up = 0.0f, um = 0.0f, dp = 0.0f, dm = 0.0f;
     if (has_corr) {
       dGf = S.G[j];
       dGm = S.G[jm];
+      float gm, g0, gp, h, q;
+      corr_at(K, c.off + jm, gm, h, q);
+      corr_at(K, c.off + j, g0, h, q);
+      corr_at(K, c.off + jp, gp, h, q);
+      const float gf = 0.5f * (g0 + gp), gb = 0.5f * (gm + g0);   // faces j+1/2, j-1/2
+      up = fmaxf(gf, 0.0f); dp = fminf(gf, 0.0f);
+      um = fmaxf(gb, 0.0f); dm = fminf(gb, 0.0f);
     }
     const float Dn = S.D[j] * S.n[j];
-    S.pa[j] = -c.r * am * S.D[jm];
-    S.pb[j] = 1.0f + c.r * (af + am) * S.D[j] + K.dt * nu_w;    // losses implicit: n' stays positive
-    S.pc[j] = -c.r * af * S.D[jp];
+    S.pa[j] = -c.r * am * S.D[jm] - c.s * um;
+    S.pb[j] = 1.0f + c.r * (af + am) * S.D[j] + K.dt * nu_w + c.s * (up - dm);   // losses implicit
+    S.pc[j] = -c.r * af * S.D[jp] + c.s * dp;
     // b_{j+1/2} - b_{j-1/2} = -(a_{j+1/2} - a_{j-1/2}): taken from a, which is small, to keep its digits
     S.pd[j] = c.r * (af * (S.D[jp] * S.n[jp] - Dn) - am * (Dn - S.D[jm] * S.n[jm])) -
               c.s * (af - am) * c.GT + K.dt * S.n[j] * (nu - nu_w) - c.s * (dGf - dGm);
@@ -321,14 +331,21 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
   solve(S.pa, S.pb, S.pc, S.pd, N);
   for (int j = t; j < N; j += kThreads) add2(S.n[j], S.nl[j], S.pd[j]);
   __syncthreads();
-  // 3. flux and field at faces from n'; energy coefficients into pa (mu_eps), pb (D_eps)
+  // 3. flux and field at faces from n' (the correction flux too); energy coefficients into
+  //    pa (mu_eps), pb (D_eps)
   field(S, c);
   for (int j = t; j < N; j += kThreads) {
     const int jp = (j + 1) & (N - 1);
     const float af = 0.5f * (S.A[j] + S.A[jp]);
     const float bf = 1.0f - af;
     float g = -af * (S.n[jp] * S.D[jp] - S.n[j] * S.D[j]) * c.inv_dx - bf * c.GT;
-    if (has_corr) g += S.G[j];
+    if (has_corr) {
+      float g0, h0, n0, g1, h1, n1;
+      corr_at(K, c.off + j, g0, h0, n0);
+      corr_at(K, c.off + jp, g1, h1, n1);
+      const float gf = 0.5f * (g0 + g1);
+      g += fmaxf(gf, 0.0f) * S.n[j] + fminf(gf, 0.0f) * S.n[jp];
+    }
     S.G[j] = g;
     int i; float f;
     tpos(K, S.T[j], i, f);
@@ -336,8 +353,9 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
     S.pb[j] = tq(S, K, 3, i, f) * c.invNg;
   }
   __syncthreads();
-  // energy flux of the starting T with n' (plus the correction, on the starting n kept in u)
-  // on faces, into A (free once the flux and field are formed)
+  // energy flux of the starting T with n' (the correction's too: max(wf, 0) n'_j T_j +
+  // min(wf, 0) n'_{j+1} T_{j+1}, wf = (h_j / T_j + h_{j+1} / T_{j+1}) / 2) on faces, into A (free
+  // once the flux and field are formed)
   for (int j = t; j < N; j += kThreads) {
     const int jp = (j + 1) & (N - 1);
     const float mep = 0.5f * (S.pa[j] + S.pa[jp]);
@@ -347,13 +365,15 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
       float g0, h0, n0, g1, h1, n1;
       corr_at(K, c.off + j, g0, h0, n0);
       corr_at(K, c.off + jp, g1, h1, n1);
-      h += 0.5f * (S.u[j] * h0 + S.u[jp] * h1);
+      const float wf = 0.5f * (__fdividef(h0, S.T[j]) + __fdividef(h1, S.T[jp]));
+      h += fmaxf(wf, 0.0f) * S.n[j] * S.T[j] + fminf(wf, 0.0f) * S.n[jp] * S.T[jp];
     }
     S.A[j] = h;
   }
   __syncthreads();
   // 4. energy: A dT = rhs - A T, into D, B, pc, pd (rows read the neighbours' pa, pb; D and B
-  //    are free once the field is formed)
+  //    are free once the field is formed); the correction flux is implicit in T' as upwind
+  //    advection of n' T' by wf, w = h / T (T of the step's start)
   {
     for (int j = t; j < N; j += kThreads) {
       {
@@ -366,10 +386,21 @@ __device__ void step(const Sm &S, const FluidK &K, const ColK &c, float *red) {
         const float mep = 0.5f * (S.pa[j] + S.pa[jp]), mem = 0.5f * (S.pa[jm] + S.pa[j]);
         const float Ep = S.E[j], Em = S.E[jm];
         const float n1 = S.n[j];
+        float up = 0.0f, um = 0.0f, dp = 0.0f, dm = 0.0f;
+        if (has_corr) {
+          float g, q, hm, h0, hp;
+          corr_at(K, c.off + jm, g, hm, q);
+          corr_at(K, c.off + j, g, h0, q);
+          corr_at(K, c.off + jp, g, hp, q);
+          const float w0 = __fdividef(h0, S.T[j]);
+          const float wf = 0.5f * (w0 + __fdividef(hp, S.T[jp])), wb = 0.5f * (__fdividef(hm, S.T[jm]) + w0);
+          up = fmaxf(wf, 0.0f); dp = fminf(wf, 0.0f);
+          um = fmaxf(wb, 0.0f); dm = fminf(wb, 0.0f);
+        }
         S.B[j] = 1.5f * n1 + K.dt * n1 * dL + c.s * (-0.75f * mep * Ep + 0.75f * mem * Em) * n1 +
-                 2.0f * c.s * c.k * n1 * S.pb[j];
-        S.pc[j] = c.s * (-0.75f * mep * Ep - c.k * S.pb[jp]) * S.n[jp];
-        S.D[j] = c.s * (0.75f * mem * Em - c.k * S.pb[jm]) * S.n[jm];
+                 2.0f * c.s * c.k * n1 * S.pb[j] + c.s * (up - dm) * n1;
+        S.pc[j] = c.s * (-0.75f * mep * Ep - c.k * S.pb[jp] + dp) * S.n[jp];
+        S.D[j] = c.s * (0.75f * mem * Em - c.k * S.pb[jm] - um) * S.n[jm];
         S.pd[j] = 1.5f * (S.u[j] - n1) * S.T[j] + K.dt * P - K.dt * n1 * L - c.s * (S.A[j] - S.A[jm]);
       }
     }

@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -82,10 +84,18 @@ struct pic_handle {
   std::vector<pic_handle *> cols;
   void *coldev = nullptr;             // ColDev<R>[ncol] on the device
   int4 *sched = nullptr;              // CTA schedules: electrons at [0, nsched[0]), ions after
+  pic::SortCol *scol[2] = {nullptr, nullptr};   // per species: the columns' sort table (sort_every > 0)
+  int stiles[2] = {0, 0};             // sort tiles of all columns per species
+  int spasses = 0;                    // radix passes of the largest column
   int nsched[2] = {0, 0};
-  std::vector<int> mults;             // CTAs per SM multipliers tried by the autotuner
-  std::vector<double> tune_ms;        // measured step time per multiplier
-  int tune_next = 0, mult = 1;
+  std::vector<int> mults;             // CTAs-per-SM multipliers the autotuner tries
+  int mult[2] = {1, 1};               // chosen multiplier per species
+  int tune_sp = 0;                    // species being tuned (2: done)
+  int tune_i = 0, tune_round = 0;     // candidate and round of the species being tuned
+  std::vector<float> tune_ms;         // best push time per candidate of that species
+  int tune_mark = -1;                 // species whose push the next step brackets with tune_ev
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+  std::string tune_key;               // shape of the batch (the autotuner's cache key)
   size_t push_smem = 0;
   int maxN = 0;
   cudaGraphExec_t cycle = nullptr;    // captured cycle of ion_subcycle steps (no sort, no diagnostics)
@@ -453,6 +463,10 @@ void free_all(pic_handle *h) {
   h->cols.clear();
   cudaFree(h->coldev);
   cudaFree(h->sched);
+  cudaFree(h->scol[0]);
+  cudaFree(h->scol[1]);
+  for (cudaEvent_t &e : h->tune_ev)
+    if (e) cudaEventDestroy(e);
   if (h->cycle) cudaGraphExecDestroy(h->cycle);
   for (int q = 0; q < 2; ++q) {
     cudaFree(h->sp[q].cell); cudaFree(h->sp[q].rec); cudaFree(h->sp[q].id); cudaFree(h->sp[q].code);
@@ -581,7 +595,8 @@ template <class R> pic::ColDev<R> coldev_of(pic_handle *c) {
   return d;
 }
 
-// CTA schedule of one species: CTAs in proportion to the live particles of each column (at least one)
+// CTA schedule of one species: mult x SMs CTAs, given to the columns in proportion to their
+// particles (at least one each, and at least 1024 particles per CTA)
 void build_schedule(pic_handle *b, int species, int mult, std::vector<int4> &out) {
   long long tot = 0;
   std::vector<long long> n(b->cols.size());
@@ -601,10 +616,10 @@ void build_schedule(pic_handle *b, int species, int mult, std::vector<int4> &out
   }
 }
 
-template <class R> int batch_schedules(pic_handle *b, int mult) {
+template <class R> int batch_schedules(pic_handle *b, int mult_e, int mult_i) {
   std::vector<int4> se, si;
-  build_schedule(b, 0, mult, se);
-  build_schedule(b, 1, mult, si);
+  build_schedule(b, 0, mult_e, se);
+  build_schedule(b, 1, mult_i, si);
   b->nsched[0] = (int)se.size();
   b->nsched[1] = (int)si.size();
   cudaFree(b->sched);
@@ -618,6 +633,34 @@ template <class R> int batch_schedules(pic_handle *b, int mult) {
   return 0;
 }
 
+constexpr int kTuneRounds = 2;
+
+// the autotuner's choices by batch shape, for the life of the process
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+// shape of a batch: SMs, precision, columns, and per column its cells and particle counts
+// rounded to powers of two
+std::string tune_key(const pic_handle *b) {
+  auto lg = [](long long v) { int k = 0; while ((1ll << k) < v) ++k; return k; };
+  std::string k = std::to_string(b->nsm) + (b->mixed ? "m" : "d") + std::to_string(b->cols.size());
+  for (const pic_handle *c : b->cols)
+    k += ":" + std::to_string(lg(c->N)) + "," + std::to_string(lg(c->p.n_e0)) + "," + std::to_string(lg(c->p.n_i0));
+  return k;
+}
+bool tune_lookup(pic_handle *b) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune_cache.find(b->tune_key);
+  if (it == g_tune_cache.end()) return false;
+  b->mult[0] = it->second.first;
+  b->mult[1] = it->second.second;
+  return true;
+}
+void tune_store(pic_handle *b) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_cache[b->tune_key] = {b->mult[0], b->mult[1]};
+}
+
 template <class R> int enqueue_batch_step(pic_handle *b) {
   pic_handle *c0 = b->cols[0];
   const int ncol = (int)b->cols.size();
@@ -628,15 +671,14 @@ template <class R> int enqueue_batch_step(pic_handle *b) {
   if (se > 0 && b->host_step % se == 0) {
     t_begin(b);
     const long long pi = (long long)se * (sub > 0 ? sub : 1);
+    // all columns of a species at once: one launch per phase of each radix pass
+    const int sk = 3 * b->spasses + (b->spasses & 1);
     int nk = 0;
-    for (pic_handle *c : b->cols) {
-      const int sk = 3 * pic::sort_passes(c->N) + (pic::sort_passes(c->N) & 1);
-      pic::launch_sort<R>(c->sp[0], c->sb[0], &c->ctl->n[0], c->sp[0].cap, c->N, b->nsm, b->stream);
+    for (int q = 0; q < 2; ++q) {
+      if (q == 1 && b->host_step % pi != 0) break;
+      if (b->stiles[q] == 0) continue;
+      pic::launch_sort_batch<R>(b->scol[q], ncol, b->stiles[q], b->spasses, b->nsm, b->stream);
       nk += sk;
-      if (b->host_step % pi == 0) {
-        pic::launch_sort<R>(c->sp[1], c->sb[1], &c->ctl->n[1], c->sp[1].cap, c->N, b->nsm, b->stream);
-        nk += sk;
-      }
     }
     t_end(b, PIC_K_SORT, nk);
   }
@@ -648,12 +690,16 @@ template <class R> int enqueue_batch_step(pic_handle *b) {
             c->p.loss_mode != PIC_LOSS_RADIAL;
   t_begin(b);
   pic::launch_zero_q_batch<R>(cd, ncol, 0, b->maxN, b->stream);
+  if (b->tune_mark == 0) cudaEventRecord(b->tune_ev[0], b->stream);
   pic::launch_push_batch<R>(cd, b->sched, b->nsched[0], 0, b->push_smem, plain, b->stream);
+  if (b->tune_mark == 0) cudaEventRecord(b->tune_ev[1], b->stream);
   t_end(b, PIC_K_PUSH_E, 2);
   if (ion_push && b->nsched[1] > 0) {
     t_begin(b);
     pic::launch_zero_q_batch<R>(cd, ncol, 1, b->maxN, b->stream);
+    if (b->tune_mark == 1) cudaEventRecord(b->tune_ev[0], b->stream);
     pic::launch_push_batch<R>(cd, b->sched + b->nsched[0], b->nsched[1], 1, b->push_smem, plain, b->stream);
+    if (b->tune_mark == 1) cudaEventRecord(b->tune_ev[1], b->stream);
     t_end(b, PIC_K_PUSH_I, 2);
   }
   t_begin(b);
@@ -683,30 +729,55 @@ template <class R> int step_batch(pic_handle *b, int64_t n) {
   const bool graphs = !(b->p.flags & PIC_FLAG_NO_GRAPH) && !b->timing;
   int64_t done = 0;
   while (done < n) {
-    // autotuner: the first steps try each CTA multiplier once (the schedule does not change results)
-    if (b->tune_next < (int)b->mults.size()) {
-      const int m = b->mults[b->tune_next];
-      int rc = batch_schedules<R>(b, m);
+    // autotuner (the schedule does not change results): each candidate multiplier of a species
+    // is timed on that species' push kernel, kRounds times (the shortest counts); electrons
+    // first, then ions on the steps that push them
+    if (b->tune_sp < 2) {
+      const int q = b->tune_sp;
+      const bool ion_step = sub > 0 && b->host_step % sub == 0;
+      if (b->nsched[q] == 0 || (q == 1 && b->cols[0]->p.ion_subcycle <= 0)) {
+        b->tune_sp = q + 1;   // nothing to tune for this species
+        if (b->tune_sp == 2) {
+          tune_store(b);
+          const int rc = batch_schedules<R>(b, b->mult[0], b->mult[1]);
+          if (rc) return rc;
+        }
+        continue;
+      }
+      if (q == 1 && !ion_step) {
+        const int rc = enqueue_batch_step<R>(b);
+        if (rc) return rc;
+        ++done;
+        continue;
+      }
+      int m[2] = {b->mult[0], b->mult[1]};
+      m[q] = b->mults[b->tune_i];
+      int rc = batch_schedules<R>(b, m[0], m[1]);
       if (rc) return rc;
-      cudaEvent_t e0, e1;
-      cudaEventCreate(&e0);
-      cudaEventCreate(&e1);
-      cudaEventRecord(e0, b->stream);
+      b->tune_mark = q;
       rc = enqueue_batch_step<R>(b);
-      cudaEventRecord(e1, b->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
+      b->tune_mark = -1;
       if (rc) return rc;
-      b->tune_ms.push_back(ms);
-      if (++b->tune_next == (int)b->mults.size()) {
-        size_t best = 0;
-        for (size_t i = 1; i < b->tune_ms.size(); ++i)
-          if (b->tune_ms[i] < b->tune_ms[best]) best = i;
-        b->mult = b->mults[best];
-        rc = batch_schedules<R>(b, b->mult);
+      CU(b, cudaEventSynchronize(b->tune_ev[1]));
+      float ms = 0.f;
+      CU(b, cudaEventElapsedTime(&ms, b->tune_ev[0], b->tune_ev[1]));
+      if (b->tune_round == 0) b->tune_ms.push_back(ms);
+      else b->tune_ms[b->tune_i] = std::min(b->tune_ms[b->tune_i], ms);
+      if (++b->tune_i == (int)b->mults.size()) {
+        b->tune_i = 0;
+        if (++b->tune_round == kTuneRounds) {
+          size_t best = 0;
+          for (size_t i = 1; i < b->tune_ms.size(); ++i)
+            if (b->tune_ms[i] < b->tune_ms[best]) best = i;
+          b->mult[q] = b->mults[best];
+          b->tune_ms.clear();
+          b->tune_round = 0;
+          b->tune_sp = q + 1;
+          if (b->tune_sp == 2) tune_store(b);
+        }
+      }
+      if (b->tune_sp == 2 || b->tune_sp != q) {
+        rc = batch_schedules<R>(b, b->mult[0], b->mult[1]);
         if (rc) return rc;
       }
       ++done;
@@ -772,7 +843,33 @@ template <class R> int init_batch_typed(pic_handle *b) {
     if (b->maxN > pic::kFieldSmemMax) x.fk.smem = 0;
   CU(b, cudaMalloc(&b->coldev, d.size() * sizeof(pic::ColDev<R>)));
   CU(b, cudaMemcpy(b->coldev, d.data(), d.size() * sizeof(pic::ColDev<R>), cudaMemcpyHostToDevice));
-  return batch_schedules<R>(b, b->mult);
+  if (b->cols[0]->p.sort_every > 0) {
+    // the batched sort's column tables (the arrays of a column do not move after pic_init)
+    for (pic_handle *c : b->cols) b->spasses = std::max(b->spasses, pic::sort_passes(c->N));
+    for (int q = 0; q < 2; ++q) {
+      std::vector<pic::SortCol> t;
+      int tile0 = 0;
+      for (pic_handle *c : b->cols) {
+        pic::SortCol e{};
+        e.cell[0] = c->sp[q].cell; e.rec[0] = c->sp[q].rec; e.id[0] = c->sp[q].id;
+        e.cell[1] = c->sb[q].cell; e.rec[1] = c->sb[q].rec; e.id[1] = c->sb[q].id;
+        e.hist = c->sb[q].hist;
+        e.n = &c->ctl->n[q];
+        e.tile0 = tile0;
+        e.ntiles = c->sp[q].cap > 0 && c->sb[q].hist ? pic::sort_tiles(c->sp[q].cap) : 0;
+        tile0 += e.ntiles;
+        t.push_back(e);
+      }
+      b->stiles[q] = tile0;
+      CU(b, cudaMalloc(&b->scol[q], t.size() * sizeof(pic::SortCol)));
+      CU(b, cudaMemcpy(b->scol[q], t.data(), t.size() * sizeof(pic::SortCol), cudaMemcpyHostToDevice));
+    }
+  }
+  b->tune_key = tune_key(b);
+  if (tune_lookup(b)) b->tune_sp = 2;
+  CU(b, cudaEventCreate(&b->tune_ev[0]));
+  CU(b, cudaEventCreate(&b->tune_ev[1]));
+  return batch_schedules<R>(b, b->mult[0], b->mult[1]);
 }
 
 }  // namespace
@@ -1038,7 +1135,7 @@ int pic_init_batch(const pic_params *params, int n, pic_handle **out) {
     c->owner = b;
     b->cols.push_back(c);
   }
-  b->mults = {1, 2, 4};
+  b->mults = {1, 2, 3, 4, 6, 8};
   const int rc = b->mixed ? init_batch_typed<float>(b) : init_batch_typed<double>(b);
   if (rc) {
     free_all(b);
@@ -1047,6 +1144,13 @@ int pic_init_batch(const pic_params *params, int n, pic_handle **out) {
   }
   *out = b;
   return 0;
+}
+
+int pic_batch_schedule(pic_handle *b, int *mult_e, int *mult_i) {
+  if (!b || !b->is_batch) return set_err(b, PIC_EINVAL, "not a batch handle");
+  if (mult_e) *mult_e = b->mult[0];
+  if (mult_i) *mult_i = b->mult[1];
+  return b->tune_sp >= 2 ? 1 : 0;
 }
 
 int pic_step_batch(pic_handle *b, int64_t n) {

@@ -161,9 +161,23 @@ struct SortBuf {
   unsigned *hist;
 };
 
+// one column's sort of one species in a batch: buffers 0 are the species arrays, buffers 1 the
+// sort buffers; hist holds ntiles * 128 + 128 words (sort_hist_words(cap))
+struct SortCol {
+  int32_t *cell[2];
+  void *rec[2];
+  uint64_t *id[2];
+  unsigned *hist;
+  const long long *n;   // live particles (device)
+  int tile0, ntiles;
+};
+
 // sort (pic_sort.cu)
 int sort_passes(int n_cells);
+int sort_tiles(int64_t cap);
 size_t sort_hist_words(int64_t cap);
+template <class R>
+void launch_sort_batch(const SortCol *cols, int ncols, int total_tiles, int passes, int nsm, cudaStream_t st);
 template <class R>
 void launch_sort(SpeciesDev s, SortBuf alt, const long long *n_dev, long long cap, int n_cells, int nsm,
                  cudaStream_t st);

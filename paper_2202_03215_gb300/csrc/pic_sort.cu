@@ -142,6 +142,153 @@ __global__ void k_sort_copy(const int32_t *cell, const T *rec, const uint64_t *i
   }
 }
 
+// ---- batches: one launch per phase for all columns of a batch (each global tile of
+// kTile particles belongs to one column; a column's tiles are [tile0, tile0 + ntiles))
+
+// the column of global tile t (columns in increasing tile0)
+__device__ __forceinline__ int col_of(const SortCol *c, int ncols, int t) {
+  int lo = 0, hi = ncols - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (c[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kWarps * 32)
+k_sort_hist_b(const SortCol *__restrict__ cols, int ncols, int total, int shift, int src) {
+  __shared__ unsigned h[kBins];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int gt = blockIdx.x; gt < total; gt += gridDim.x) {
+    const SortCol &c = cols[col_of(cols, ncols, gt)];
+    const int tile = gt - c.tile0;
+    const long long n = *c.n;
+    const int32_t *cell = c.cell[src];
+    for (int d = threadIdx.x; d < kBins; d += blockDim.x) h[d] = 0u;
+    __syncthreads();
+    const long long start = (long long)tile * kTile + (long long)w * kIters * 32;
+    for (int it = 0; it < kIters; ++it) {
+      const long long p = start + it * 32 + lane;
+      const int d = p < n ? digit_of(cell[p], shift) : kInvalid;
+      const unsigned grp = __match_any_sync(kFullMask, d);
+      if (d != kInvalid && lane == __ffs(grp) - 1) atomicAdd(&h[d], (unsigned)__popc(grp));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kBins; d += blockDim.x) c.hist[(size_t)d * c.ntiles + tile] = h[d];
+    __syncthreads();
+  }
+}
+
+// one warp per (column, digit): exclusive scan of the column's tile counts, digit totals
+__global__ void k_sort_scan_b(const SortCol *__restrict__ cols, int ncols) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= ncols * kBins) return;
+  const SortCol &c = cols[warp / kBins];
+  const int digit = warp % kBins;
+  unsigned *row = c.hist + (size_t)digit * c.ntiles;
+  unsigned carry = 0;
+  for (int base = 0; base < c.ntiles; base += 32) {
+    const int t = base + lane;
+    const unsigned v = t < c.ntiles ? row[t] : 0u;
+    unsigned incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned x = __shfl_up_sync(kFullMask, incl, o);
+      if (lane >= o) incl += x;
+    }
+    if (t < c.ntiles) row[t] = carry + incl - v;
+    carry += __shfl_sync(kFullMask, incl, 31);
+  }
+  if (lane == 0) c.hist[(size_t)kBins * c.ntiles + digit] = carry;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kWarps * 32)
+k_sort_scatter_b(const SortCol *__restrict__ cols, int ncols, int total, int shift, int src) {
+  __shared__ unsigned dbase[kBins];
+  __shared__ unsigned woff[kWarps][kBins];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int gt = blockIdx.x; gt < total; gt += gridDim.x) {
+    const SortCol &c = cols[col_of(cols, ncols, gt)];
+    const int tile = gt - c.tile0, ntiles = c.ntiles;
+    const long long n = *c.n;
+    const int32_t *cell = c.cell[src];
+    const T *rec = reinterpret_cast<const T *>(c.rec[src]);
+    const uint64_t *id = c.id[src];
+    int32_t *cell_o = c.cell[src ^ 1];
+    T *rec_o = reinterpret_cast<T *>(c.rec[src ^ 1]);
+    uint64_t *id_o = c.id[src ^ 1];
+    const unsigned *hist = c.hist, *tot = c.hist + (size_t)kBins * ntiles;
+    if (threadIdx.x < 32) {
+      // exclusive scan of the column's 128 digit totals by one warp (4 per lane)
+      unsigned v[4], s = 0;
+      for (int k = 0; k < 4; ++k) { v[k] = tot[lane * 4 + k]; s += v[k]; }
+      unsigned incl = s;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned x = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= o) incl += x;
+      }
+      unsigned run = incl - s;
+      for (int k = 0; k < 4; ++k) { dbase[lane * 4 + k] = run; run += v[k]; }
+    }
+    for (int d = lane; d < kBins; d += 32) woff[w][d] = 0u;
+    __syncthreads();
+    const long long start = (long long)tile * kTile + (long long)w * kIters * 32;
+    for (int it = 0; it < kIters; ++it) {
+      const long long p = start + it * 32 + lane;
+      const int d = p < n ? digit_of(cell[p], shift) : kInvalid;
+      const unsigned grp = __match_any_sync(kFullMask, d);
+      if (d != kInvalid && lane == __ffs(grp) - 1) woff[w][d] += (unsigned)__popc(grp);
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kBins; d += blockDim.x) {
+      unsigned run = dbase[d] + hist[(size_t)d * ntiles + tile];
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const unsigned cnt = woff[ww][d];
+        woff[ww][d] = run;
+        run += cnt;
+      }
+    }
+    __syncthreads();
+    for (int it = 0; it < kIters; ++it) {
+      const long long p = start + it * 32 + lane;
+      const bool valid = p < n;
+      const int32_t cv = valid ? cell[p] : 0;
+      const int d = valid ? digit_of(cv, shift) : kInvalid;
+      const unsigned grp = __match_any_sync(kFullMask, d);
+      unsigned pos = 0;
+      if (valid) pos = woff[w][d] + (unsigned)__popc(grp & lt);
+      __syncwarp();
+      if (valid && lane == __ffs(grp) - 1) woff[w][d] += (unsigned)__popc(grp);
+      __syncwarp();
+      if (valid) {
+        cell_o[pos] = cv;
+        rec_o[pos] = rec[p];
+        id_o[pos] = id[p];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// after an odd number of passes: buffers 1 back into buffers 0, every column
+template <class T>
+__global__ void k_sort_copy_b(const SortCol *__restrict__ cols, int ncols, int total) {
+  for (int gt = blockIdx.x; gt < total; gt += gridDim.x) {
+    const SortCol &c = cols[col_of(cols, ncols, gt)];
+    const long long n = *c.n, p0 = (long long)(gt - c.tile0) * kTile;
+    const T *rec = reinterpret_cast<const T *>(c.rec[1]);
+    T *rec_o = reinterpret_cast<T *>(c.rec[0]);
+    for (long long p = p0 + threadIdx.x; p < n && p < p0 + kTile; p += blockDim.x) {
+      c.cell[0][p] = c.cell[1][p];
+      rec_o[p] = rec[p];
+      c.id[0][p] = c.id[1][p];
+    }
+  }
+}
+
 }  // namespace
 
 int sort_passes(int n_cells) {
@@ -177,7 +324,28 @@ void launch_sort(SpeciesDev s, SortBuf alt, const long long *n_dev, long long ca
   if (passes & 1) k_sort_copy<T><<<nsm * 8, 256, 0, st>>>(ca, ra, ia, s.cell, reinterpret_cast<T *>(s.rec), s.id, n_dev);
 }
 
+int sort_tiles(int64_t cap) { return (int)((cap + kTile - 1) / kTile); }
+
+// Sort every column of a batch (one species) by cell: one launch per phase for all columns.
+// cols: device array of ncols columns in increasing tile0, tile0 = sum of the earlier columns'
+// ntiles (= sort_tiles(cap)); passes = sort_passes of the largest column (a pass on bits above a
+// column's cells keeps its order).  Same result, particle for particle, as launch_sort per column.
+template <class R>
+void launch_sort_batch(const SortCol *cols, int ncols, int total_tiles, int passes, int nsm, cudaStream_t st) {
+  using T = typename Rec<R>::T;
+  const int grid = total_tiles < nsm * 8 ? total_tiles : nsm * 8;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = pass * kBits, src = pass & 1;
+    k_sort_hist_b<<<grid, kWarps * 32, 0, st>>>(cols, ncols, total_tiles, shift, src);
+    k_sort_scan_b<<<(ncols * kBins * 32 + 255) / 256, 256, 0, st>>>(cols, ncols);
+    k_sort_scatter_b<T><<<grid, kWarps * 32, 0, st>>>(cols, ncols, total_tiles, shift, src);
+  }
+  if (passes & 1) k_sort_copy_b<T><<<grid, 256, 0, st>>>(cols, ncols, total_tiles);
+}
+
 template void launch_sort<double>(SpeciesDev, SortBuf, const long long *, long long, int, int, cudaStream_t);
 template void launch_sort<float>(SpeciesDev, SortBuf, const long long *, long long, int, int, cudaStream_t);
+template void launch_sort_batch<double>(const SortCol *, int, int, int, int, cudaStream_t);
+template void launch_sort_batch<float>(const SortCol *, int, int, int, int, cudaStream_t);
 
 }  // namespace pic

@@ -24,6 +24,7 @@ Every density is handled per unit density: the fluid model is linear in n
 """
 from __future__ import annotations
 
+import json
 import math
 from dataclasses import dataclass
 from typing import List, Sequence
@@ -434,16 +435,18 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
           n_cells: int = 2048, particles: int = 1_000_000, windows: int = 200, window: int = 4000,
           early: int = 100, early_window: int = 1000, agg: int = 4, fluid_dt: float = 2e-9, fluid_diag: int = 20,
           train_steps: int = 3000, batch: int = 8192, lr: float = 1e-3, period: int = 10,
-          components=(0.0, 0.0, 1.0), nu_bound: float = 1.0, stencils=(1,), seed: int = 7,
-          fluid_cells: int | None = None, log=print) -> dict:
+          components=((0.0, 1.0, 1.0), (0.0, 0.0, 1.0)), nu_bound: float = 1.0, stencils=(1,), seed: int = 7,
+          fluid_cells: int | None = None, save: str | None = None, load: str | None = None,
+          log=print) -> dict:
     """Particle model (one GPU batch: comparison and training fields), closure training on
     its moment windows, fluid model with and without the trained closure at the comparison
     fields; striation observables, closure gain and times.  The particle record takes
     `early` windows of `early_window` steps (growth phase), then `windows` windows of
     `window` steps; closure data come from the long windows, `agg` at a time.
     components: which network outputs the fluid screen applies (flux, energy flux,
-    ionization); the flux corrections enter the step explicitly, so they are only
-    stable while dt |dGamma/n| / dx and the energy change they carry per step stay small.
+    ionization), one triple or a list of triples (each closure is then run with each; the
+    first of the first stencil is the study's main closure); the flux corrections enter the
+    fluid step implicitly (upwind advection), positivity-preserving at any time step.
     fluid_cells: cells of the fluid columns (default: those of the particle columns); with fewer,
     the particle model's moment windows are averaged onto the fluid grid (blocks of
     n_cells / fluid_cells cells; the mean energy weighted by density) before the closure samples
@@ -460,86 +463,115 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
     Es = list(E_compare) + list(E_train)
     params = pic_columns(Es, p_torr, L_m, n_cells, particles)
     ncmp = len(E_compare)
-    b = Batch(params)
-    for c in b.columns:
-        c.moments(reset=True)
     M = 64
-    plan = [early_window] * early + [window] * windows
-    nw = len(plan)
-    rec = np.zeros((nw, len(Es), M + 1), complex)
-    mob = np.zeros((nw, len(Es)))
-    acc = [dict() for _ in Es]
-    train_windows = [[] for _ in Es]
-    keys = ("n_e", "mean_eps_e", "gamma_e", "heat_e", "iz_rate", "gamma_i", "E")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    pic_run = 0.0
-    for s, steps_s in enumerate(plan):
-        ta = time.perf_counter()
-        b.step(steps_s)
-        pic_run += time.perf_counter() - ta
-        for k, (c, p) in enumerate(zip(b.columns, params)):
-            m = c.moments(reset=True)
-            rec[s, k, 0] = m["n_e"].mean()
-            rec[s, k, 1:] = (np.fft.fft(m["n_e"]) / n_cells)[1:M + 1]
-            mob[s, k] = abs(m["gamma_i"].sum()) / max(m["n_i"].sum(), 1e-30) / p.E0_Vpm * n_gas(p_torr)
-            if k >= ncmp and s >= early:
-                for q in keys:
-                    acc[k][q] = acc[k].get(q, 0.0) + m[q] / agg
-                if (s - early + 1) % agg == 0:
-                    train_windows[k].append(acc[k])
-                    acc[k] = dict()
-    wall = time.perf_counter() - t0
-    b.close()
-    total_steps = int(sum(plan))
-    log(f"particle batch: {len(Es)} columns, {total_steps} steps, {pic_run:.1f} s stepping, {wall:.1f} s total")
-    dt_pic = params[0].dt_s
-    ends = np.cumsum(plan)
-    t_pic = (ends - 0.5 * np.array(plan)) * dt_pic
-    amp = np.abs(rec[:, :, 1:]).max(2) / rec[:, :, 0].real
-    mu = []
-    for k in range(len(Es)):
-        # ion mobility of the uniform column: windows after the first 0.2 us, before striations
-        sel = [s for s in range(nw) if t_pic[s] > 2e-7 and amp[s, k] < 0.05][:8] or [min(nw - 1, early)]
-        mu.append(float(np.median(mob[sel, k])))
-    # closure data from the training columns: residuals of the tabulated closure, one network per
-    # stencil spacing (the first is the study's main closure)
-    T_range = (tab.Te[0], tab.Te[-1])
-    held = ncmp + (len(E_train) // 2)                  # one training column held out (split by run)
     fs = cl.FEATURE_SCALE
-    nets = []
-    for st_k in stencils:
-        Xs, Ys, col_of = [], [], []
-        for k in range(ncmp, len(Es)):
-            for m in train_windows[k][2:]:
-                X, Y = cl.residual_samples(coarsen(m, n_cells // fluid_cells), params[k], tab, mu[k], T_range,
-                                           step=st_k)
-                Xs.append(X)
-                Ys.append(Y)
-                col_of.append(np.full(len(X), k))
-        X = np.concatenate(Xs)
-        Y = np.concatenate(Ys)
-        col_of = np.concatenate(col_of)
-        ts = np.maximum(np.std(Y, 0), 1e-30).astype(np.float32)
-        tr, te = col_of != held, col_of == held
-        Xn, Yn = (X / fs).astype(np.float32), (Y / ts).astype(np.float32)
-        rng = np.random.default_rng(seed)
-        perm = rng.permutation(np.nonzero(tr)[0])
-        Xd = torch.from_numpy(Xn[perm]).cuda()
-        Yd = torch.from_numpy(Yn[perm]).cuda()
-        net = Mlp(seed=seed)
+    if load is not None:
+        # the particle record and the trained closures of an earlier run of the same study
+        z = np.load(load)
+        meta = json.loads(str(z["meta"]))
+        mine = dict(E_compare=list(E_compare), E_train=list(E_train), p_torr=p_torr, L_m=L_m, n_cells=n_cells,
+                    fluid_cells=fluid_cells, particles=particles, stencils=list(stencils), seed=seed)
+        if any(meta[k] != v for k, v in mine.items()):
+            raise ValueError(f"{load} holds another study: {meta}")
+        rec, t_pic, mu = z["rec"], z["t_pic"], [float(v) for v in z["mu"]]
+        total_steps, dt_pic, pic_run, held = meta["total_steps"], meta["dt_pic"], meta["pic_run"], meta["held"]
+        nets = []
+        for k, st_k in enumerate(meta["stencils"]):
+            net = Mlp(seed=seed)
+            net.set_params(z["net_params"][k])
+            nets.append(dict(stencil=st_k, net=net, ts=z["net_ts"][k], mse_net=z["net_mse"][k],
+                             mse_tab=z["net_mse_tab"][k], train_s=float(z["net_train_s"][k]),
+                             last=float(z["net_last"][k]), n=int(z["net_n"][k])))
+        log(f"particle record and {len(nets)} closures from {load}")
+    else:
+        b = Batch(params)
+        for c in b.columns:
+            c.moments(reset=True)
+        plan = [early_window] * early + [window] * windows
+        nw = len(plan)
+        rec = np.zeros((nw, len(Es), M + 1), complex)
+        mob = np.zeros((nw, len(Es)))
+        acc = [dict() for _ in Es]
+        train_windows = [[] for _ in Es]
+        keys = ("n_e", "mean_eps_e", "gamma_e", "heat_e", "iz_rate", "gamma_i", "E")
         torch.cuda.synchronize()
-        ta = time.perf_counter()
-        last = net.train(Xd, Yd, batch=batch, steps=train_steps, lr=lr)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - ta
-        Yh = net.forward(torch.from_numpy(Xn[te]).cuda()).cpu().numpy()
-        mse_net = ((Yh - Yn[te]) ** 2).mean(0)
-        mse_tab = (Yn[te] ** 2).mean(0)             # the tabulated closure alone predicts zero residual
-        log(f"closure (stencil {st_k}): {len(X)} samples, held-out column E0/p = {Es[held]}, "
-            f"mse net {mse_net} vs table {mse_tab}")
-        nets.append(dict(stencil=st_k, net=net, ts=ts, mse_net=mse_net, mse_tab=mse_tab, train_s=train_s,
-                         last=last, n=len(X)))
+        t0 = time.perf_counter()
+        pic_run = 0.0
+        for s, steps_s in enumerate(plan):
+            ta = time.perf_counter()
+            b.step(steps_s)
+            pic_run += time.perf_counter() - ta
+            for k, (c, p) in enumerate(zip(b.columns, params)):
+                m = c.moments(reset=True)
+                rec[s, k, 0] = m["n_e"].mean()
+                rec[s, k, 1:] = (np.fft.fft(m["n_e"]) / n_cells)[1:M + 1]
+                mob[s, k] = abs(m["gamma_i"].sum()) / max(m["n_i"].sum(), 1e-30) / p.E0_Vpm * n_gas(p_torr)
+                if k >= ncmp and s >= early:
+                    for q in keys:
+                        acc[k][q] = acc[k].get(q, 0.0) + m[q] / agg
+                    if (s - early + 1) % agg == 0:
+                        train_windows[k].append(acc[k])
+                        acc[k] = dict()
+        wall = time.perf_counter() - t0
+        b.close()
+        total_steps = int(sum(plan))
+        log(f"particle batch: {len(Es)} columns, {total_steps} steps, {pic_run:.1f} s stepping, {wall:.1f} s total")
+        dt_pic = params[0].dt_s
+        ends = np.cumsum(plan)
+        t_pic = (ends - 0.5 * np.array(plan)) * dt_pic
+        amp = np.abs(rec[:, :, 1:]).max(2) / rec[:, :, 0].real
+        mu = []
+        for k in range(len(Es)):
+            # ion mobility of the uniform column: windows after the first 0.2 us, before striations
+            sel = [s for s in range(nw) if t_pic[s] > 2e-7 and amp[s, k] < 0.05][:8] or [min(nw - 1, early)]
+            mu.append(float(np.median(mob[sel, k])))
+        # closure data from the training columns: residuals of the tabulated closure, one network per
+        # stencil spacing (the first is the study's main closure)
+        T_range = (tab.Te[0], tab.Te[-1])
+        held = ncmp + (len(E_train) // 2)                  # one training column held out (split by run)
+        nets = []
+        for st_k in stencils:
+            Xs, Ys, col_of = [], [], []
+            for k in range(ncmp, len(Es)):
+                for m in train_windows[k][2:]:
+                    X, Y = cl.residual_samples(coarsen(m, n_cells // fluid_cells), params[k], tab, mu[k], T_range,
+                                               step=st_k)
+                    Xs.append(X)
+                    Ys.append(Y)
+                    col_of.append(np.full(len(X), k))
+            X = np.concatenate(Xs)
+            Y = np.concatenate(Ys)
+            col_of = np.concatenate(col_of)
+            ts = np.maximum(np.std(Y, 0), 1e-30).astype(np.float32)
+            tr, te = col_of != held, col_of == held
+            Xn, Yn = (X / fs).astype(np.float32), (Y / ts).astype(np.float32)
+            rng = np.random.default_rng(seed)
+            perm = rng.permutation(np.nonzero(tr)[0])
+            Xd = torch.from_numpy(Xn[perm]).cuda()
+            Yd = torch.from_numpy(Yn[perm]).cuda()
+            net = Mlp(seed=seed)
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            last = net.train(Xd, Yd, batch=batch, steps=train_steps, lr=lr)
+            torch.cuda.synchronize()
+            train_s = time.perf_counter() - ta
+            Yh = net.forward(torch.from_numpy(Xn[te]).cuda()).cpu().numpy()
+            mse_net = ((Yh - Yn[te]) ** 2).mean(0)
+            mse_tab = (Yn[te] ** 2).mean(0)             # the tabulated closure alone predicts zero residual
+            log(f"closure (stencil {st_k}): {len(X)} samples, held-out column E0/p = {Es[held]}, "
+                f"mse net {mse_net} vs table {mse_tab}")
+            nets.append(dict(stencil=st_k, net=net, ts=ts, mse_net=mse_net, mse_tab=mse_tab, train_s=train_s,
+                             last=last, n=len(X)))
+        if save is not None:
+            meta = dict(E_compare=list(E_compare), E_train=list(E_train), p_torr=p_torr, L_m=L_m, n_cells=n_cells,
+                        fluid_cells=fluid_cells, particles=particles, stencils=list(stencils), seed=seed,
+                        total_steps=total_steps, dt_pic=dt_pic, pic_run=pic_run, held=held)
+            np.savez(save, meta=json.dumps(meta), rec=rec, t_pic=t_pic, mu=np.array(mu),
+                     net_params=np.stack([d["net"].params() for d in nets]),
+                     net_ts=np.stack([d["ts"] for d in nets]), net_mse=np.stack([d["mse_net"] for d in nets]),
+                     net_mse_tab=np.stack([d["mse_tab"] for d in nets]),
+                     net_train_s=np.array([d["train_s"] for d in nets]),
+                     net_last=np.array([d["last"] for d in nets]), net_n=np.array([d["n"] for d in nets]))
     net, ts, mse_net, mse_tab, train_s, last = (nets[0][k] for k in ("net", "ts", "mse_net", "mse_tab",
                                                                     "train_s", "last"))
     # fluid model at the comparison fields, same simulated time, noise of the particle model
@@ -547,11 +579,13 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
     steps = int(round(total_steps * dt_pic / fluid_dt))
     diag = fluid_diag
     noise = 1.0 / math.sqrt(particles / fluid_cells)
-    mask = np.asarray(components, np.float32)
+    masks = np.atleast_2d(np.asarray(components, np.float32))
     out = {}
+    vname = lambda i, d, mi: ("fluid_closure" if i == 0 and mi == 0
+                              else f"fluid_closure_s{d['stencil']}_c{''.join(str(int(v)) for v in masks[mi])}")
     variants = [("fluid", True, None)] + [
-        ("fluid_closure" if i == 0 else f"fluid_closure_s{d['stencil']}", True,
-         (d["net"], period, fs, d["ts"] * mask, nu_bound, d["stencil"])) for i, d in enumerate(nets)]
+        (vname(i, d, mi), True, (d["net"], period, fs, d["ts"] * masks[mi], nu_bound, d["stencil"]))
+        for i, d in enumerate(nets) for mi in range(len(masks))]
     for name, pair, clo in variants:
         f = Fluid(fluid_columns(states, L_m, fluid_cells, pair=pair), records, n_T=128, dt_s=fluid_dt,
                   diag_every=diag, n_modes=M)
@@ -581,12 +615,16 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
                 pic_seconds_per_column=pic_per_col,
                 fluid_seconds_per_column=out["fluid"]["ms"] / 1e3 / ncmp,
                 fluid_closure_seconds_per_column=out["fluid_closure"]["ms"] / 1e3 / ncmp,
-                simulated_s=total_steps * dt_pic, train_seconds=train_s, train_loss=last, components=list(components),
+                simulated_s=total_steps * dt_pic, train_seconds=train_s, train_loss=last,
+                components=masks.tolist(),
                 stencils=list(stencils), nu_bound=nu_bound,
-                closures=[dict(stencil=d["stencil"], mse_net=d["mse_net"].tolist(), mse_table=d["mse_tab"].tolist(),
-                               lam=[o["lam"] for o in out["fluid_closure" if i == 0 else f"fluid_closure_s{d['stencil']}"]["obs"]],
-                               v_ph=[o["v_ph"] for o in out["fluid_closure" if i == 0 else f"fluid_closure_s{d['stencil']}"]["obs"]])
-                          for i, d in enumerate(nets)],
+                closures=[dict(stencil=d["stencil"], components=masks[mi].tolist(), mse_net=d["mse_net"].tolist(),
+                               mse_table=d["mse_tab"].tolist(),
+                               lam=[o["lam"] for o in out[vname(i, d, mi)]["obs"]],
+                               v_ph=[o["v_ph"] for o in out[vname(i, d, mi)]["obs"]],
+                               gamma=[o["gamma"] for o in out[vname(i, d, mi)]["obs"]],
+                               amp_sat=[o["amp_sat"] for o in out[vname(i, d, mi)]["obs"]])
+                          for i, d in enumerate(nets) for mi in range(len(masks))],
                 n_samples=int(nets[0]["n"]), held_out_E=Es[held], mse_net=mse_net.tolist(), mse_table=mse_tab.tolist(),
                 target_scale=ts.tolist(), pic_modes=rec, t_pic=t_pic,
                 fluid_modes=out["fluid"]["modes"], fluid_closure_modes=out["fluid_closure"]["modes"],
@@ -628,6 +666,10 @@ def main(argv=None) -> int:
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--fluid-cells", type=int, default=None, help="study: cells of the fluid columns")
     ap.add_argument("--early", type=int, default=100, help="study: growth-phase windows of 1000 steps")
+    ap.add_argument("--components", nargs="+", default=["0,1,1", "0,0,1"],
+                    help="study: closure outputs applied (flux,energy flux,ionization), one or more triples")
+    ap.add_argument("--save", default=None, help="study: write the particle record and closures to this .npz")
+    ap.add_argument("--load", default=None, help="study: take the particle record and closures from this .npz")
     a = ap.parse_args(argv)
     if a.what == "fluid":
         # a fluid screen of imposed fields 6..20 V/cm/Torr (neon, 1 Torr, L = 10 cm): time per step
@@ -640,7 +682,8 @@ def main(argv=None) -> int:
         return 0
     r = study([6, 8, 10, 12, 14, 16, 18, 20], [7, 9, 11, 13, 15, 17, 19, 21], L_m=a.L, n_cells=a.pic_cells,
               particles=a.particles, windows=a.windows, window=a.window, agg=a.agg, train_steps=a.train_steps,
-              fluid_cells=a.fluid_cells, early=a.early,
+              fluid_cells=a.fluid_cells, early=a.early, save=a.save, load=a.load,
+              components=[[float(v) for v in c.split(",")] for c in a.components],
               nu_bound=a.nu_bound, stencils=tuple(a.stencils), log=lambda s: print(s, flush=True))
     for k, e in enumerate(r["E_compare"]):
         p, f, g, l, d = r["pic"][k], r["fluid"][k], r["fluid_closure"][k], r["linear"][k], r["dispersion"][k]
@@ -649,7 +692,8 @@ def main(argv=None) -> int:
               f"lam={g['lam'] * 100:.3g} v={g['v_ph']:.3g} | eq.22 lam={l['lam'] * 100:.3g} v={l['v_ph']:.3g} "
               f"g={l['gamma_max']:.3g} | full linear lam={d['lam'] * 100:.3g} g={d['gamma']:.3g}", flush=True)
     for c in r["closures"]:
-        print(f"closure stencil {c['stencil']}: held-out mse {c['mse_net']} (table {c['mse_table']}); lambda cm "
+        print(f"closure stencil {c['stencil']} components {c['components']}: held-out mse {c['mse_net']} "
+              f"(table {c['mse_table']}); lambda cm "
               + " ".join(f"{x * 100:.3g}" for x in c["lam"]), flush=True)
     print("speed ratio (particle / fluid per column):",
           r["pic_seconds_per_column"] / r["fluid_seconds_per_column"], flush=True)

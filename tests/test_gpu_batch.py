@@ -39,17 +39,30 @@ def _columns(precision, sort_every):
 def test_batched_columns_equal_lone_columns(precision, sort_every):
     params = _columns(precision, sort_every)
     b = pb.Batch(params)
-    b.step(3)      # the autotuner's steps
+    t = b.tune()   # the autotuner's steps (none when an equal batch was tuned before)
+    tuned, me, mi = b.schedule()
+    assert tuned and me in (1, 2, 3, 4, 6, 8) and mi in (1, 2, 3, 4, 6, 8)
     b.step(30)     # graph cycles where no sort falls
     lone = [pb.Column(p) for p in params]
     for c in lone:
-        c.step(3)
-        c.step(30)
+        c.step(t + 30)
     for i, (bc, lc) in enumerate(zip(b.columns, lone)):
         assert_same(bc.get_state(), lc.get_state(), f"column {i}")
         assert bc.stats()["n_coll_e"] == lc.stats()["n_coll_e"]
-    assert all(c.stats()["step"] == 33 for c in b.columns)
+    assert all(c.stats()["step"] == t + 30 for c in b.columns)
     assert sum(c.stats()["births"] for c in b.columns) > 0   # the births path ran inside the batch
+
+
+def test_batched_sort_matches_oracle():
+    # the batched sort (one launch per radix phase for all columns) against the oracle's
+    # counting sort: columns of 97 (one pass) to 3001 cells, several 4096-particle tiles each
+    params = _columns(w.MIXED, 5)
+    b = pb.Batch(params)
+    b.step(16)
+    for k in (0, 3):
+        o = oracle.Oracle(params[k])
+        o.step(16)
+        assert_same(b.columns[k].get_state(), o.get_state(), f"column {k} vs oracle")
 
 
 def test_batched_column_matches_oracle():

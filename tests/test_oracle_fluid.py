@@ -169,3 +169,59 @@ def test_the_model_is_linear_in_the_density(pair):
         assert np.array_equal(n4, 4 * n1) and np.array_equal(T4, T1)
         assert np.all((T1 > lo) & (T1 < hi))          # no clipping at the table ends masks a difference
     assert np.std(n1) > 0 and not np.array_equal(n1, n)
+
+
+@pytest.mark.parametrize("m,v", [(2, 3e3), (17, -8e3), (60, 2e4)])
+def test_flux_correction_is_implicit_upwind_advection(m, v):
+    # no diffusion, drift, ionization or losses: the continuity step with a flux correction of
+    # g = v per electron is backward-Euler first-order upwind advection, which multiplies the mode
+    # exp(i theta j) by 1 / (1 + (dt |v| / dx)(1 - exp(-+ i theta))) (- for v > 0: the upwind
+    # cell is j - 1), conserving the particle number
+    tab = const_table(DN=0.0, nu_izN=0.0, lossN=0.0)
+    N, L, dt = 256, 0.1, 2e-8
+    col = column(L=L, tab=tab, nu_w=0.0)
+    dx = L / N
+    x = np.arange(N)
+    n = 1e16 * (1 + 1e-2 * np.cos(2 * np.pi * m * x / N))
+    corr = np.stack([np.full(N, v), np.zeros(N), np.zeros(N)])
+    n1, _ = fl.step(col, tab, n, np.full(N, 4.0), dt, corr=corr)
+    th = 2 * np.pi * m / N
+    g = 1.0 / (1.0 + dt * abs(v) / dx * (1 - np.exp(-np.sign(v) * 1j * th)))
+    c0, c1 = fl.modes(n, m)[-1], fl.modes(n1, m)[-1]
+    assert abs(c1 / c0 - g) < 1e-9 * abs(g)
+    assert n1.sum() == pytest.approx(n.sum(), rel=1e-13)
+
+
+def test_flux_correction_keeps_the_density_positive():
+    # a correction velocity that changes sign from cell to cell (converging and diverging faces)
+    # at a Courant number of 5: the upwind matrix is an M-matrix, n' > 0, the number conserved
+    tab = const_table(DN=0.0, nu_izN=0.0, lossN=0.0)
+    N, L, dt = 128, 0.1, 2e-8
+    col = column(L=L, tab=tab, nu_w=0.0)
+    rng = np.random.default_rng(8)
+    v = 5 * (L / N) / dt * rng.standard_normal(N)
+    n = 1e16 * (1 + 0.5 * rng.random(N))
+    n1, _ = fl.step(col, tab, n, np.full(N, 4.0), dt, corr=np.stack([v, np.zeros(N), np.zeros(N)]))
+    assert np.all(n1 > 0)
+    assert n1.sum() == pytest.approx(n.sum(), rel=1e-12)
+
+
+@pytest.mark.parametrize("m,w", [(3, 5e3), (31, -2e4)])
+def test_energy_flux_correction_is_implicit_upwind_advection(m, w):
+    # uniform n, no field, conduction, energy drift or loss: an energy-flux correction of
+    # h = w T per electron is backward-Euler upwind advection of (3/2) n T with velocity w,
+    # which multiplies a temperature mode by 1 / (1 + (2/3)(dt |w| / dx)(1 - exp(-+ i theta)))
+    tab = const_table(mueN=0.0, DeN=0.0, lossN=0.0, nu_izN=0.0)
+    N, L, dt, n0 = 256, 0.1, 1e-8, 1e16
+    col = column(L=L, tab=tab, nu_w=0.0)
+    dx = L / N
+    x = np.arange(N)
+    T = 4.0 + 1e-2 * np.cos(2 * np.pi * m * x / N)
+    corr = np.stack([np.zeros(N), w * T, np.zeros(N)])
+    n1, T1 = fl.step(col, tab, np.full(N, n0), T, dt, corr=corr)
+    assert np.allclose(n1, n0, rtol=1e-13)
+    th = 2 * np.pi * m / N
+    g = 1.0 / (1.0 + 2.0 / 3.0 * dt * abs(w) / dx * (1 - np.exp(-np.sign(w) * 1j * th)))
+    c0, c1 = fl.modes(T, m)[-1], fl.modes(T1, m)[-1]
+    assert abs(c1 / c0 - g) < 1e-9 * abs(g)
+    assert T1.mean() == pytest.approx(T.mean(), rel=1e-12)
