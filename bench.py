@@ -421,8 +421,9 @@ def closure_training_leg(pb, torch, n: int = 1 << 20, batch: int = 8192, steps: 
     e1.record()
     torch.cuda.synchronize()
     sf = e0.elapsed_time(e1) / 1e3
-    # the same kernels with 16x the samples per Adam step: every SM holds several tiles
-    big = 16 * batch
+    # the same kernels with 64x the samples per Adam step (at most the data set): every SM holds
+    # several tiles, and the step's fixed costs (partials, reduction, launches) are shared
+    big = min(64 * batch, n)
     net.train(X, T, batch=big, steps=5)
     torch.cuda.synchronize()
     e0.record()

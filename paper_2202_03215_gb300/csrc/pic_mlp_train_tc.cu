@@ -14,8 +14,9 @@
 //                             dA2 = dY W3 (CUDA cores, BF16-rounded dY and W3), dZ2 = dA2 gelu'
 //   R3  dW3^T += A2^T dY, gb2 += dZ2lo^T 1, dA1 = dZ2 W2 (waited for); dW2^T += A1^T dZ2 and
 //       gb2 += dZ2hi^T 1 run on under the epilogue dZ1 = dA1 gelu'
-//   R4  [dW1 | gb1] += dZ1^T [X 1] (X carries a column of ones, so column 15 is gb1); not waited
-//       for: the next tile's first commit covers it (and the unwaited half of R3)
+//   R4  [dW1 | gb1] += dZ1^T [X 1] (X carries a column of ones, so column 15 is gb1); issued after
+//       the next tile's R1 (committed on its own), so that it runs under that tile's layer-1
+//       epilogue; the next tile's R2 commit covers it (and the unwaited half of R3)
 // dZ is stored as a BF16 high part and a BF16 low part: the weight gradients take the high
 // part (BF16 operands, like every product), the bias gradients (gb2, gb1) take both, so that
 // the sums keep FP32 accuracy.  gb3 and the squared error are warp sums in FP32.  The weight
@@ -350,11 +351,16 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
   const uint32_t trow = tm + ((uint32_t)(32 * q) << 16);   // this warp's lanes
   uint32_t ph = 0;
   bool pending = false;   // an MMA batch was committed whose completion was not seen
-  // the issuing thread issues, commits and waits; the barrier passes the outcome on
-  auto run = [&](auto issue) -> bool {
+  // the issuing thread issues and commits (submit), then waits for that commit (await_); the
+  // barrier passes the outcome on
+  auto submit = [&](auto issue) {
     if (tid == ISSUER) {
       issue();
       commit(&S.mbar_mma);
+    }
+  };
+  auto await_ = [&]() -> bool {
+    if (tid == ISSUER) {
       S.ok = wait_phase(&S.mbar_mma, ph, spin) ? 1 : 0;
       if (!S.ok) atomicExch(status, 1);
     }
@@ -364,6 +370,10 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
     pending = !ok;
     tc_after();
     return ok;
+  };
+  auto run = [&](auto issue) -> bool {
+    submit(issue);
+    return await_();
   };
   bool ok = S.ok != 0;
   constexpr uint32_t kM = 4096 >> 4, kX = 512 >> 4;   // descriptor steps of 16 samples: 128-wide, 16-wide tiles
@@ -380,8 +390,10 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
       for (int o = 0; o < NO; ++o) tg[o] = r < rows ? __ldg(T + (size_t)(s0 + r) * NO + o) : 0.0f;
       load_x(X, ns0, nrows, tid, xv);
     }
-    // R1 (its commit also covers the previous tile's dW1 products)
-    ok = run([&] { mma(tm + cZ1, dk(Xt, K1), dk(S.w.W1, K1), idesc(TM, NH, 0, 0), 0u); });
+    // R1 (after the first tile it was submitted at the end of the previous tile, ahead of that
+    // tile's dW1 products)
+    if (it == 0) submit([&] { mma(tm + cZ1, dk(Xt, K1), dk(S.w.W1, K1), idesc(TM, NH, 0, 0), 0u); });
+    ok = await_();
     if (!ok) break;
     epi_act<false>(S.A1, trow + cZ1, S.b1, r, c0, S.W3, S.yp[part]);
     handoff();
@@ -478,7 +490,12 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
       }
     }
     handoff();
-    // R4: [dW1 | gb1] += dZ1^T [X 1] (both MN-major, K = samples), high and low parts apart
+    // the next tile's R1 first, committed on its own (its inputs were written in the dY/dZ2
+    // epilogue; Z1's columns were last read just above), so that its wait does not take in R4
+    if (nt < ntiles)
+      submit([&] { mma(tm + cZ1, dk(S.X[buf ^ 1], K1), dk(S.w.W1, K1), idesc(TM, NH, 0, 0), 0u); });
+    // R4: [dW1 | gb1] += dZ1^T [X 1] (both MN-major, K = samples), high and low parts apart; it
+    // runs under the next tile's layer-1 epilogue, and the next commit covers it
     if (tid == ISSUER) {
       for (uint32_t k = 0; k < TM / 16; ++k)
         mma(tm + cW1, dmn(S.A2, 128, 2048) + k * kM, dmn(Xt, 128, 256) + k * kX, idesc(NH, N3, 1, 1), k | fresh);
@@ -523,8 +540,13 @@ k_mlp_tile_tc(const float *__restrict__ P, const TrainW *__restrict__ Wb, const 
       lpart[blockIdx.x] = sq;
     }
   }
-  // a batch whose wait gave up: wait once more (bounded) before the tensor memory is freed
-  if (pending && tid == ISSUER) wait_phase(&S.mbar_mma, ph ^ 1u, spin);
+  // a batch whose wait gave up: wait once more (bounded), then commit whatever was issued after
+  // it (the dW1 products follow the next tile's R1 commit) and wait for that, before the tensor
+  // memory is freed
+  if (pending && tid == ISSUER && wait_phase(&S.mbar_mma, ph ^ 1u, spin)) {
+    commit(&S.mbar_mma);
+    wait_phase(&S.mbar_mma, ph, spin);
+  }
   tc_before();
   __syncthreads();
   tc_after();
