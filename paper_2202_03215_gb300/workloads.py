@@ -177,11 +177,13 @@ def config_argon_small(seed: int = 1, **kw) -> Params:
 def config_neon_column(seed: int = 1, precision: int = MIXED, n_per_species: int = 20_000_000,
                        E0_Vpm: float = 600.0, **kw) -> Params:
     """Neon 1 Torr 300 K, L = 30 cm, R = 1 cm, 16384 cells, 2e7 particles per species,
-    dt = 4e-11 s, ions subcycled x10, int32 cell + FP32 offset/velocity storage."""
+    dt = 4e-11 s, ions subcycled x10, int32 cell + FP32 offset/velocity storage, sorted by cell
+    every 100 steps (the fastest whole step measured: 0.250 ms, against 0.255 ms at 250 and
+    0.268 ms at 50)."""
     p = Params(gas_mass_amu=AMU_NE, L_m=0.30, R_m=0.01, drive=DRIVE_E0, E0_Vpm=E0_Vpm,
                V_applied=0.0, xsec=neon_xsecs(), n_cells=16384, dt_s=4e-11,
                n_e0=n_per_species, n_i0=n_per_species, precision=precision, seed=seed,
-               eps_max_e_eV=200.0, sort_every=250, diag_every=0)
+               eps_max_e_eV=200.0, sort_every=100, diag_every=0)
     return p.with_(**kw) if kw else p
 
 
