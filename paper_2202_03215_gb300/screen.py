@@ -582,7 +582,7 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
     masks = np.atleast_2d(np.asarray(components, np.float32))
     out = {}
     vname = lambda i, d, mi: ("fluid_closure" if i == 0 and mi == 0
-                              else f"fluid_closure_s{d['stencil']}_c{''.join(str(int(v)) for v in masks[mi])}")
+                              else f"fluid_closure_s{d['stencil']}_c{'_'.join(f'{v:g}' for v in masks[mi])}")
     variants = [("fluid", True, None)] + [
         (vname(i, d, mi), True, (d["net"], period, fs, d["ts"] * masks[mi], nu_bound, d["stencil"]))
         for i, d in enumerate(nets) for mi in range(len(masks))]
