@@ -53,6 +53,26 @@ def test_batched_columns_equal_lone_columns(precision, sort_every):
     assert sum(c.stats()["births"] for c in b.columns) > 0   # the births path ran inside the batch
 
 
+def test_tuned_schedule_is_cached_by_batch_shape():
+    # a batch of a shape tuned before in this process starts with that schedule (no tuning
+    # steps); a batch of another shape tunes; the schedule never changes the columns' evolution
+    params = _columns(w.MIXED, 0)
+    a = pb.Batch(params)
+    a.tune()
+    tuned = a.schedule()
+    a.close()
+    b = pb.Batch(params)
+    assert b.schedule() == tuned      # from the cache: tuned, the same multipliers
+    b.step(5)
+    c = pb.Batch(params[:3])          # another shape
+    assert c.schedule()[0] is False
+    c.close()
+    lone = pb.Column(params[1])
+    lone.step(5)
+    assert_same(b.columns[1].get_state(), lone.get_state(), "cached schedule")
+    b.close()
+
+
 def test_batched_sort_matches_oracle():
     # the batched sort (one launch per radix phase for all columns) against the oracle's
     # counting sort: columns of 97 (one pass) to 3001 cells, several 4096-particle tiles each
