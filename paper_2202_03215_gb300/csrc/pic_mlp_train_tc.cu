@@ -21,8 +21,8 @@
 // part (BF16 operands, like every product), the bias gradients (gb2, gb1) take both, so that
 // the sums keep FP32 accuracy.  gb3 and the squared error are warp sums in FP32.  The weight
 // gradients accumulate in tensor memory over the CTA's tiles (tiles b, b + G, b + 2G, .. of a
-// grid of G CTAs); the CTA writes them once as its partial, and the
-// reduction kernel of pic_mlp.cu sums the G partials in a fixed order and applies Adam.
+// grid of G CTAs); the CTA writes them once as its partial, and the reduction kernel of
+// pic_mlp.cu sums the G partials in a fixed order and applies Adam.
 // Tensor-memory columns: Z1 then gelu'(Z1) [0,128), Z2 then gelu'(Z2) then dA1 [128,256),
 // dW2^T [272,400), dW3^T [400,416), gb2 [416,432), dW1 | gb1 [432,448), the low
 // part's [X 1] product (its column 15 completes gb1) [448,464).
