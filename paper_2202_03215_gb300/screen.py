@@ -631,6 +631,131 @@ def study(E_compare: Sequence[float], E_train: Sequence[float], p_torr: float = 
                 t_fluid=out["fluid"]["t"])
 
 
+GRID_PR = np.geomspace(0.3, 3.0, 32)     # pR of the fluid screen, Torr cm
+GRID_IR = np.geomspace(0.01, 1.0, 32)    # I/R of the fluid screen, A/m
+
+
+def grid_points(idx: Sequence[int] = (4, 12, 20, 28)) -> list:
+    """Sampled points of the 32 x 32 (pR, I/R) screen: the sub-grid idx x idx (16 points)."""
+    return [(float(GRID_PR[i]), float(GRID_IR[j])) for i in idx for j in idx]
+
+
+def grid_study(points, load: str, R_m: float = 0.01, L_m: float = 0.30, n_cells: int = 16384,
+               fluid_cells: int = 4096, particles: int = 1_000_000, dt: float = 1.6e-11,
+               simulated_s: float = 3.6e-5, windows: int = 300, early: int = 100, early_frac: float = 0.1,
+               diag_every: int = 120, fluid_dt: float = 2e-9, fluid_diag: int = 20, period: int = 10,
+               components=((0.0, 1.0, 1.0), (0.0, 0.0, 1.0)), nu_bound: float = 0.5, seed: int = 7,
+               log=print) -> dict:
+    """The particle model at (pR, I/R) points of a tube of radius R (current drive: eq. 2 gives the
+    homogeneous field and density), one GPU batch, against the fluid screen at the same points
+    (homogeneous states of eq. 2, pair losses, each column with the ion mobility measured in its
+    particle column) with and without the closures of an earlier study (`load`: the .npz that
+    study(save=...) writes; networks trained on other columns), over the same simulated time.
+    dt is common to the batch and must keep nu* dt <= 0.3 at the highest pressure.  The record
+    takes `early` windows covering early_frac of the time (growth), then `windows` windows."""
+    import time
+    import torch
+    from . import Batch, Mlp
+    from . import closure as cl
+    records = transport()
+    tab = Table(records)
+    total = int(round(simulated_s / dt))
+    ew = max(1, int(total * early_frac / early) // diag_every * diag_every)
+    lw = max(1, int((total - early * ew) / windows) // diag_every * diag_every)
+    plan = [ew] * early + [lw] * windows
+    base = w.config_neon_column(n_per_species=particles)
+    params = [base.with_(pressure_torr=pr / (R_m * 100.0), R_m=R_m, I_A=ir * R_m, L_m=L_m, n_cells=n_cells,
+                         dt_s=dt, drive=w.DRIVE_RI, n_e0=particles, n_i0=particles, loss_mode=w.LOSS_PAIR,
+                         diag_every=diag_every, sort_every=1000, seed=seed + 40 + k, column=k)
+              for k, (pr, ir) in enumerate(points)]
+    from . import drive_ri
+    drives = [drive_ri(p) for p in params]   # eq. 2 as the library resolves it: E0, n0, Te0, mu_i N
+    b = Batch(params)
+    for c in b.columns:
+        c.moments(reset=True)
+    M = 64
+    nw = len(plan)
+    rec = np.zeros((nw, len(points), M + 1), complex)
+    mob = np.zeros((nw, len(points)))
+    torch.cuda.synchronize()
+    pic_run = 0.0
+    for s_, steps_s in enumerate(plan):
+        ta = time.perf_counter()
+        b.step(steps_s)
+        pic_run += time.perf_counter() - ta
+        for k, c in enumerate(b.columns):
+            m = c.moments(reset=True)
+            rec[s_, k, 0] = m["n_e"].mean()
+            rec[s_, k, 1:] = (np.fft.fft(m["n_e"]) / n_cells)[1:M + 1]
+            mob[s_, k] = abs(m["gamma_i"].sum()) / max(m["n_i"].sum(), 1e-30) / drives[k]["E0_Vpm"] * \
+                n_gas(params[k].pressure_torr)
+    b.close()
+    steps_total = int(sum(plan))
+    log(f"particle batch: {len(points)} columns, {steps_total} steps, {pic_run:.1f} s stepping")
+    ends = np.cumsum(plan)
+    t_pic = (ends - 0.5 * np.array(plan)) * dt
+    amp = np.abs(rec[:, :, 1:]).max(2) / rec[:, :, 0].real
+    mu = []
+    for k in range(len(points)):
+        # ion mobility of the uniform column: windows after the first 0.2 us, before striations
+        sel = [q for q in range(nw) if t_pic[q] > 2e-7 and amp[q, k] < 0.05][:8] or [min(nw - 1, early)]
+        mu.append(float(np.median(mob[sel, k])))
+    states = [homogeneous_R(tab, pr, ir, R_m=R_m, mu_iN=mu[k]) for k, (pr, ir) in enumerate(points)]
+    z = np.load(load)
+    meta = json.loads(str(z["meta"]))
+    fs = cl.FEATURE_SCALE
+    masks = np.atleast_2d(np.asarray(components, np.float32))
+    nets = []
+    for k, st_k in enumerate(meta["stencils"]):
+        net = Mlp(seed=seed)
+        net.set_params(z["net_params"][k])
+        nets.append((st_k, net, z["net_ts"][k]))
+    steps = int(round(steps_total * dt / fluid_dt))
+    noise = 1.0 / math.sqrt(particles / fluid_cells)
+    out = {}
+    variants = [("fluid", None)] + [(f"closure_s{st_k}_c{'_'.join(f'{v:g}' for v in masks[mi])}",
+                                     (net, period, fs, ts * masks[mi], nu_bound, st_k))
+                                    for st_k, net, ts in nets for mi in range(len(masks))]
+    ok = [math.isfinite(h.T0) for h in states]
+    for name, clo in variants:
+        f = Fluid(fluid_columns([h for h, g in zip(states, ok) if g], L_m, fluid_cells), records, n_T=128,
+                  dt_s=fluid_dt, diag_every=fluid_diag, n_modes=M)
+        if clo is not None:
+            f.set_closure(*clo)
+        for k, h in enumerate([h for h, g in zip(states, ok) if g]):
+            f.set_state(k, *initial_state(fluid_cells, h, seed + 100 + k, amp=noise))
+        f.step(steps)
+        ms, _ = f.elapsed()
+        r = f.modes()
+        f.close()
+        t = (np.arange(r.shape[0]) + 1) * fluid_diag * fluid_dt
+        obs, j = [], 0
+        for g in ok:
+            if g:
+                o = observables(t, r[:, j], L_m)
+                o["v_ph"] = _cathode_v(o["v_ph"], "fluid")
+                obs.append(o)
+                j += 1
+            else:
+                obs.append(None)
+        out[name] = dict(obs=obs, ms=ms)
+        log(f"{name}: {steps} steps of {sum(ok)} columns in {ms:.1f} ms")
+    pic_obs = []
+    for k in range(len(points)):
+        o = observables(t_pic, rec[:, k], L_m)
+        o["v_ph"] = _cathode_v(o["v_ph"], "pic")
+        pic_obs.append(o)
+    lin = [linear(tab, h) if g else None for h, g in zip(states, ok)]
+    return dict(points=[list(p) for p in points], dt=dt, steps=steps_total, simulated_s=steps_total * dt,
+                pic=pic_obs, pic_seconds_per_column=pic_run / len(points), mu_iN=mu,
+                pic_E0=[d["E0_Vpm"] for d in drives], pic_n0=[d["n0_m3"] for d in drives],
+                pic_Te0=[d["Te0_eV"] for d in drives],
+                fluid_T0=[h.T0 for h in states], fluid_E0=[h.E0 for h in states], fluid_n0=[h.n0 for h in states],
+                linear=lin, variants={k: v["obs"] for k, v in out.items()},
+                fluid_seconds_per_column={k: v["ms"] / 1e3 / max(1, sum(ok)) for k, v in out.items()},
+                closures_from=load, closure_meta=meta)
+
+
 def _jsonable(o):
     if isinstance(o, dict):
         return {k: _jsonable(v) for k, v in o.items() if not isinstance(v, np.ndarray)}
@@ -650,7 +775,7 @@ def main(argv=None) -> int:
     import argparse
     import json
     ap = argparse.ArgumentParser(prog="python -m paper_2202_03215_gb300.screen")
-    ap.add_argument("what", choices=["study", "fluid"])
+    ap.add_argument("what", choices=["study", "fluid", "grid"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--nu-bound", type=float, default=0.5)
     ap.add_argument("--stencils", type=int, nargs="+", default=[1], help="closure stencil spacings, cells")
@@ -679,6 +804,24 @@ def main(argv=None) -> int:
         r = fluid_screen(recs, states, L_m=0.10, n_cells=a.cells, steps=a.steps, diag_every=50)
         print(f"fluid: {a.columns} columns x {a.cells} cells, {a.steps} steps in {r['ms']:.2f} ms "
               f"({r['launches']} launches)", flush=True)
+        return 0
+    if a.what == "grid":
+        # the particle model at 16 points of the (pR, I/R) screen against the fluid screen with the
+        # closures of an earlier study (--load)
+        r = grid_study(grid_points(), a.load, L_m=a.L, n_cells=a.pic_cells, fluid_cells=a.fluid_cells or 4096,
+                       particles=a.particles, nu_bound=a.nu_bound,
+                       components=[[float(v) for v in c.split(",")] for c in a.components],
+                       log=lambda s: print(s, flush=True))
+        for k, (pr, ir) in enumerate(r["points"]):
+            line = (f"pR={pr:.3g} I/R={ir:.3g}: E0={r['pic_E0'][k]:.4g} V/m PIC lam={r['pic'][k]['lam'] * 100:.3g} cm "
+                    f"v={r['pic'][k]['v_ph']:.3g} g={r['pic'][k]['gamma']:.3g}")
+            for name, obs in r["variants"].items():
+                o = obs[k]
+                line += f" | {name} lam={o['lam'] * 100:.3g}" if o else f" | {name} -"
+            print(line, flush=True)
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(_jsonable(r), fh, indent=1)
         return 0
     r = study([6, 8, 10, 12, 14, 16, 18, 20], [7, 9, 11, 13, 15, 17, 19, 21], L_m=a.L, n_cells=a.pic_cells,
               particles=a.particles, windows=a.windows, window=a.window, agg=a.agg, train_steps=a.train_steps,
