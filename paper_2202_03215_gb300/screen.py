@@ -640,22 +640,27 @@ def grid_points(idx: Sequence[int] = (4, 12, 20, 28)) -> list:
     return [(float(GRID_PR[i]), float(GRID_IR[j])) for i in idx for j in idx]
 
 
-def grid_study(points, load: str, R_m: float = 0.01, L_m: float = 0.30, n_cells: int = 16384,
+def grid_study(points, load: str | None = None, R_m: float = 0.01, L_m: float = 0.30, n_cells: int = 16384,
                fluid_cells: int = 4096, particles: int = 1_000_000, dt: float = 1.6e-11,
                simulated_s: float = 3.6e-5, windows: int = 300, early: int = 100, early_frac: float = 0.1,
                diag_every: int = 120, fluid_dt: float = 2e-9, fluid_diag: int = 20, period: int = 10,
-               components=((0.0, 1.0, 1.0), (0.0, 0.0, 1.0)), nu_bound: float = 0.5, seed: int = 7,
+               components=((0.0, 1.0, 1.0), (0.0, 0.0, 1.0)), nu_bound: float = 0.5, stencils=(1, 16),
+               agg: int = 2, train_steps: int = 3000, batch: int = 8192, lr: float = 1e-3, seed: int = 7,
                log=print) -> dict:
     """The particle model at (pR, I/R) points of a tube of radius R (current drive: eq. 2 gives the
     homogeneous field and density), one GPU batch, against the fluid screen at the same points
     (homogeneous states of eq. 2, pair losses, each column with the ion mobility measured in its
-    particle column) with and without the closures of an earlier study (`load`: the .npz that
-    study(save=...) writes; networks trained on other columns), over the same simulated time.
+    particle column) with and without a learned closure, over the same simulated time.
+    Closures: with `load` (the .npz that study(save=...) writes) the networks of that study;
+    without it, two-fold cross-validation over the points: the points split by the parity of
+    their index sum on the 4 x 4 sub-grid (a checkerboard), one network per fold and stencil
+    trained on the moment windows of the other fold's columns and applied to this fold's.
     dt is common to the batch and must keep nu* dt <= 0.3 at the highest pressure.  The record
-    takes `early` windows covering early_frac of the time (growth), then `windows` windows."""
+    takes `early` windows covering early_frac of the time (growth), then `windows` windows; the
+    closure data come from the long windows, `agg` at a time."""
     import time
     import torch
-    from . import Batch, Mlp
+    from . import Batch, Mlp, drive_ri
     from . import closure as cl
     records = transport()
     tab = Table(records)
@@ -668,15 +673,18 @@ def grid_study(points, load: str, R_m: float = 0.01, L_m: float = 0.30, n_cells:
                          dt_s=dt, drive=w.DRIVE_RI, n_e0=particles, n_i0=particles, loss_mode=w.LOSS_PAIR,
                          diag_every=diag_every, sort_every=1000, seed=seed + 40 + k, column=k)
               for k, (pr, ir) in enumerate(points)]
-    from . import drive_ri
     drives = [drive_ri(p) for p in params]   # eq. 2 as the library resolves it: E0, n0, Te0, mu_i N
     b = Batch(params)
     for c in b.columns:
         c.moments(reset=True)
     M = 64
     nw = len(plan)
-    rec = np.zeros((nw, len(points), M + 1), complex)
-    mob = np.zeros((nw, len(points)))
+    npt = len(points)
+    rec = np.zeros((nw, npt, M + 1), complex)
+    mob = np.zeros((nw, npt))
+    keys = ("n_e", "mean_eps_e", "gamma_e", "heat_e", "iz_rate", "gamma_i", "E")
+    acc = [dict() for _ in points]
+    train_windows = [[] for _ in points]
     torch.cuda.synchronize()
     pic_run = 0.0
     for s_, steps_s in enumerate(plan):
@@ -689,71 +697,123 @@ def grid_study(points, load: str, R_m: float = 0.01, L_m: float = 0.30, n_cells:
             rec[s_, k, 1:] = (np.fft.fft(m["n_e"]) / n_cells)[1:M + 1]
             mob[s_, k] = abs(m["gamma_i"].sum()) / max(m["n_i"].sum(), 1e-30) / drives[k]["E0_Vpm"] * \
                 n_gas(params[k].pressure_torr)
+            if load is None and s_ >= early:
+                for q in keys:
+                    acc[k][q] = acc[k].get(q, 0.0) + m[q] / agg
+                if (s_ - early + 1) % agg == 0:
+                    train_windows[k].append(acc[k])
+                    acc[k] = dict()
     b.close()
     steps_total = int(sum(plan))
-    log(f"particle batch: {len(points)} columns, {steps_total} steps, {pic_run:.1f} s stepping")
+    log(f"particle batch: {npt} columns, {steps_total} steps, {pic_run:.1f} s stepping")
     ends = np.cumsum(plan)
     t_pic = (ends - 0.5 * np.array(plan)) * dt
     amp = np.abs(rec[:, :, 1:]).max(2) / rec[:, :, 0].real
     mu = []
-    for k in range(len(points)):
+    for k in range(npt):
         # ion mobility of the uniform column: windows after the first 0.2 us, before striations
         sel = [q for q in range(nw) if t_pic[q] > 2e-7 and amp[q, k] < 0.05][:8] or [min(nw - 1, early)]
         mu.append(float(np.median(mob[sel, k])))
     states = [homogeneous_R(tab, pr, ir, R_m=R_m, mu_iN=mu[k]) for k, (pr, ir) in enumerate(points)]
-    z = np.load(load)
-    meta = json.loads(str(z["meta"]))
     fs = cl.FEATURE_SCALE
-    masks = np.atleast_2d(np.asarray(components, np.float32))
-    nets = []
-    for k, st_k in enumerate(meta["stencils"]):
-        net = Mlp(seed=seed)
-        net.set_params(z["net_params"][k])
-        nets.append((st_k, net, z["net_ts"][k]))
+    # networks: nets[(fold, stencil)] = (net, target scale); fold of point k (its test fold)
+    side = int(round(math.sqrt(npt)))
+    fold = [((k // side) + (k % side)) % 2 for k in range(npt)] if load is None else [0] * npt
+    nets, mse = {}, {}
+    if load is not None:
+        z = np.load(load)
+        meta = json.loads(str(z["meta"]))
+        for j, st_k in enumerate(meta["stencils"]):
+            net = Mlp(seed=seed)
+            net.set_params(z["net_params"][j])
+            nets[(0, st_k)] = (net, z["net_ts"][j])
+        stencils = tuple(meta["stencils"])
+    else:
+        T_range = (tab.Te[0], tab.Te[-1])
+        for f_ in (0, 1):
+            for st_k in stencils:
+                Xs, Ys, test = [], [], []
+                for k in range(npt):
+                    for m in train_windows[k][2:]:
+                        X, Y = cl.residual_samples(coarsen(m, n_cells // fluid_cells), params[k], tab, mu[k],
+                                                   T_range, step=st_k)
+                        Xs.append(X)
+                        Ys.append(Y)
+                        test.append(np.full(len(X), fold[k] == f_))
+                X, Y, test = np.concatenate(Xs), np.concatenate(Ys), np.concatenate(test)
+                tr = ~test
+                ts = np.maximum(np.std(Y[tr], 0), 1e-30).astype(np.float32)
+                Xn, Yn = (X / fs).astype(np.float32), (Y / ts).astype(np.float32)
+                perm = np.random.default_rng(seed + f_).permutation(np.nonzero(tr)[0])
+                net = Mlp(seed=seed)
+                net.train(torch.from_numpy(Xn[perm]).cuda(), torch.from_numpy(Yn[perm]).cuda(), batch=batch,
+                          steps=train_steps, lr=lr)
+                Yh = net.forward(torch.from_numpy(Xn[test]).cuda()).cpu().numpy()
+                mse[(f_, st_k)] = (((Yh - Yn[test]) ** 2).mean(0).tolist(), (Yn[test] ** 2).mean(0).tolist(),
+                                   int(tr.sum()), int(test.sum()))
+                nets[(f_, st_k)] = (net, ts)
+                log(f"fold {f_} stencil {st_k}: {int(tr.sum())} training samples, held-out mse "
+                    f"{mse[(f_, st_k)][0]} vs table {mse[(f_, st_k)][1]}")
     steps = int(round(steps_total * dt / fluid_dt))
     noise = 1.0 / math.sqrt(particles / fluid_cells)
-    out = {}
-    variants = [("fluid", None)] + [(f"closure_s{st_k}_c{'_'.join(f'{v:g}' for v in masks[mi])}",
-                                     (net, period, fs, ts * masks[mi], nu_bound, st_k))
-                                    for st_k, net, ts in nets for mi in range(len(masks))]
+    masks = np.atleast_2d(np.asarray(components, np.float32))
     ok = [math.isfinite(h.T0) for h in states]
-    for name, clo in variants:
-        f = Fluid(fluid_columns([h for h, g in zip(states, ok) if g], L_m, fluid_cells), records, n_T=128,
-                  dt_s=fluid_dt, diag_every=fluid_diag, n_modes=M)
+
+    def fluid_obs(ks, clo):
+        """observables of the fluid columns of points ks (homogeneous start), closure clo or none"""
+        f = Fluid(fluid_columns([states[k] for k in ks], L_m, fluid_cells), records, n_T=128, dt_s=fluid_dt,
+                  diag_every=fluid_diag, n_modes=M)
         if clo is not None:
             f.set_closure(*clo)
-        for k, h in enumerate([h for h, g in zip(states, ok) if g]):
-            f.set_state(k, *initial_state(fluid_cells, h, seed + 100 + k, amp=noise))
+        for j, k in enumerate(ks):
+            f.set_state(j, *initial_state(fluid_cells, states[k], seed + 100 + k, amp=noise))
         f.step(steps)
         ms, _ = f.elapsed()
         r = f.modes()
         f.close()
         t = (np.arange(r.shape[0]) + 1) * fluid_diag * fluid_dt
-        obs, j = [], 0
-        for g in ok:
-            if g:
-                o = observables(t, r[:, j], L_m)
-                o["v_ph"] = _cathode_v(o["v_ph"], "fluid")
-                obs.append(o)
-                j += 1
-            else:
-                obs.append(None)
-        out[name] = dict(obs=obs, ms=ms)
-        log(f"{name}: {steps} steps of {sum(ok)} columns in {ms:.1f} ms")
+        obs = []
+        for j in range(len(ks)):
+            o = observables(t, r[:, j], L_m)
+            o["v_ph"] = _cathode_v(o["v_ph"], "fluid")
+            obs.append(o)
+        return obs, ms
+
+    variants, vms = {}, {}
+    names = [("fluid", None, None)] + [(f"closure_s{st_k}_c{'_'.join(f'{v:g}' for v in masks[mi])}", st_k, mi)
+                                      for st_k in stencils for mi in range(len(masks))]
+    for name, st_k, mi in names:
+        obs_all, ms_all = [None] * npt, 0.0
+        for f_ in sorted(set(fold)):
+            ks = [k for k in range(npt) if fold[k] == f_ and ok[k]]
+            if not ks:
+                continue
+            clo = None
+            if st_k is not None:
+                net, ts = nets[(f_, st_k)]
+                clo = (net, period, fs, ts * masks[mi], nu_bound, st_k)
+            obs, ms = fluid_obs(ks, clo)
+            for k, o in zip(ks, obs):
+                obs_all[k] = o
+            ms_all += ms
+        variants[name] = obs_all
+        vms[name] = ms_all
+        log(f"{name}: {steps} steps of {sum(ok)} columns in {ms_all:.1f} ms")
     pic_obs = []
-    for k in range(len(points)):
+    for k in range(npt):
         o = observables(t_pic, rec[:, k], L_m)
         o["v_ph"] = _cathode_v(o["v_ph"], "pic")
         pic_obs.append(o)
     lin = [linear(tab, h) if g else None for h, g in zip(states, ok)]
     return dict(points=[list(p) for p in points], dt=dt, steps=steps_total, simulated_s=steps_total * dt,
-                pic=pic_obs, pic_seconds_per_column=pic_run / len(points), mu_iN=mu,
+                pic=pic_obs, pic_seconds_per_column=pic_run / npt, mu_iN=mu,
                 pic_E0=[d["E0_Vpm"] for d in drives], pic_n0=[d["n0_m3"] for d in drives],
                 pic_Te0=[d["Te0_eV"] for d in drives],
                 fluid_T0=[h.T0 for h in states], fluid_E0=[h.E0 for h in states], fluid_n0=[h.n0 for h in states],
-                linear=lin, variants={k: v["obs"] for k, v in out.items()},
-                fluid_seconds_per_column={k: v["ms"] / 1e3 / max(1, sum(ok)) for k, v in out.items()},
-                closures_from=load, closure_meta=meta)
+                linear=lin, variants=variants,
+                fluid_seconds_per_column={k: v / 1e3 / max(1, sum(ok)) for k, v in vms.items()},
+                closures="loaded from " + load if load else "two-fold cross-validation over the points",
+                fold=fold, mse={f"fold{k[0]}_s{k[1]}": v for k, v in mse.items()})
 
 
 def _jsonable(o):
@@ -809,7 +869,8 @@ def main(argv=None) -> int:
         # the particle model at 16 points of the (pR, I/R) screen against the fluid screen with the
         # closures of an earlier study (--load)
         r = grid_study(grid_points(), a.load, L_m=a.L, n_cells=a.pic_cells, fluid_cells=a.fluid_cells or 4096,
-                       particles=a.particles, nu_bound=a.nu_bound,
+                       particles=a.particles, nu_bound=a.nu_bound, stencils=tuple(a.stencils), agg=a.agg,
+                       train_steps=a.train_steps,
                        components=[[float(v) for v in c.split(",")] for c in a.components],
                        log=lambda s: print(s, flush=True))
         for k, (pr, ir) in enumerate(r["points"]):
