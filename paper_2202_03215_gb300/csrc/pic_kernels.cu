@@ -804,14 +804,16 @@ __device__ bool draw_victims(uint2 key, uint32_t step, uint32_t c3, int nb, long
   const bool direct = nb <= kDirectMax;
   for (int round = 0; round < 64; ++round) {
     if (direct) {
-      // O(nb^2) conflict test: no sort for the usual few hundred events
+      // O(nb^2) conflict test: no sort for the usual few hundred events; the scan over the
+      // shared-memory candidates has no early exit, so its loads pipeline
       for (int t = threadIdx.x; t < nb; t += blockDim.x) {
         if (sc.settled[t]) continue;
         const uint32_t c = sc.cand[t];
-        uint32_t ok = 1u;
-        for (int j = 0; j < nb && ok; ++j)
-          if (j != t && sc.cand[j] == c && (sc.settled[j] || j < t)) ok = 0u;
-        sc.win[t] = ok;
+        uint32_t clash = 0u;
+#pragma unroll 8
+        for (int j = 0; j < nb; ++j)
+          clash |= (uint32_t)(sc.cand[j] == c) & (uint32_t)(j != t) & (uint32_t)((sc.settled[j] != 0u) | (j < t));
+        sc.win[t] = clash ? 0u : 1u;
       }
     } else {
       for (int t = threadIdx.x; t < n2; t += blockDim.x)
@@ -969,11 +971,16 @@ __device__ __forceinline__ void births_body(const StepK<R> &k, SpeciesDev e, Spe
   const uint2 key = seed_key(k.seed);
   // births in parent-slot order
   if (nb > 0 && nb <= kDirectMax) {
-    // rank of each birth by parent slot (parents are distinct)
+    // rank of each birth by parent slot (parents are distinct), from a shared-memory copy of the
+    // parents (the candidate array, unused until the victims are drawn)
+    int32_t *s_par = reinterpret_cast<int32_t *>(sc.cand);
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) s_par[t] = bb.parent[t];
+    __syncthreads();
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-      const int32_t pt = bb.parent[t];
+      const int32_t pt = s_par[t];
       int r = 0;
-      for (int j = 0; j < nb; ++j) r += bb.parent[j] < pt;
+#pragma unroll 8
+      for (int j = 0; j < nb; ++j) r += s_par[j] < pt;
       sc.order[r] = (uint32_t)t;
     }
     __syncthreads();
