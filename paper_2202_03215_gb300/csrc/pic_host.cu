@@ -100,6 +100,8 @@ struct pic_handle {
   int maxN = 0;
   cudaGraphExec_t cycle = nullptr;    // captured cycle of ion_subcycle steps (no sort, no diagnostics)
   int64_t cycle_launch[PIC_K_CLASSES] = {0};   // kernel launches per replay of the cycle
+  cudaGraphExec_t dcycle = nullptr;   // the same with a diagnostic sample on its first step
+  int64_t dcycle_launch[PIC_K_CLASSES] = {0};
 };
 
 namespace {
@@ -468,6 +470,7 @@ void free_all(pic_handle *h) {
   for (cudaEvent_t &e : h->tune_ev)
     if (e) cudaEventDestroy(e);
   if (h->cycle) cudaGraphExecDestroy(h->cycle);
+  if (h->dcycle) cudaGraphExecDestroy(h->dcycle);
   for (int q = 0; q < 2; ++q) {
     cudaFree(h->sp[q].cell); cudaFree(h->sp[q].rec); cudaFree(h->sp[q].id); cudaFree(h->sp[q].code);
     cudaFree(h->sp[q].Q); cudaFree(h->sp[q].dead); cudaFree(h->tab[q]);
@@ -591,7 +594,7 @@ template <class R> pic::ColDev<R> coldev_of(pic_handle *c) {
   d.fk = c->fk;
   d.fs = c->fs;
   d.N = c->N;
-  pic::push_layout<R>(c->N, d.W, d.smemE);
+  pic::push_layout<R>(c->N, d.W, d.smemE, d.mofs, d.Wm);
   return d;
 }
 
@@ -630,6 +633,7 @@ template <class R> int batch_schedules(pic_handle *b, int mult_e, int mult_i) {
   CU(b, cudaMalloc(&b->sched, all.size() * sizeof(int4)));
   CU(b, cudaMemcpy(b->sched, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
   if (b->cycle) { cudaGraphExecDestroy(b->cycle); b->cycle = nullptr; }
+  if (b->dcycle) { cudaGraphExecDestroy(b->dcycle); b->dcycle = nullptr; }
   return 0;
 }
 
@@ -714,14 +718,19 @@ template <class R> int enqueue_batch_step(pic_handle *b) {
   return 0;
 }
 
-// steps s .. s+sub-1 hold no sort and no diagnostic sample
-bool plain_cycle(pic_handle *b, long long s, int sub) {
-  const pic_params &p = b->cols[0]->p;
+// the ion cycle of steps s .. s+sub-1 as a captured graph replays it: 0 not replayed (it holds a
+// sort, or a diagnostic sample after its first step), 1 plain, 2 a diagnostic sample on its first
+// step only (diag_every is a multiple of ion_subcycle, so a sample falls on a cycle's first step)
+static int cycle_kind(const pic_params &p, long long s, int sub) {
+  int kind = 1;
   for (long long q = s; q < s + sub; ++q) {
-    if (p.sort_every > 0 && q % p.sort_every == 0) return false;
-    if (p.diag_every > 0 && q % p.diag_every == 0) return false;
+    if (p.sort_every > 0 && q % p.sort_every == 0) return 0;
+    if (p.diag_every > 0 && q % p.diag_every == 0) {
+      if (q != s) return 0;
+      kind = 2;
+    }
   }
-  return true;
+  return kind;
 }
 
 template <class R> int step_batch(pic_handle *b, int64_t n) {
@@ -783,8 +792,12 @@ template <class R> int step_batch(pic_handle *b, int64_t n) {
       ++done;
       continue;
     }
-    if (graphs && n - done >= sub && b->host_step % sub == 0 && plain_cycle(b, b->host_step, sub)) {
-      if (!b->cycle) {
+    const int kind =
+        graphs && n - done >= sub && b->host_step % sub == 0 ? cycle_kind(b->cols[0]->p, b->host_step, sub) : 0;
+    if (kind) {
+      cudaGraphExec_t &gx = kind == 1 ? b->cycle : b->dcycle;
+      int64_t *gl = kind == 1 ? b->cycle_launch : b->dcycle_launch;
+      if (!gx) {
         // capture one ion cycle; the kernels read the step counter on the device, so it replays
         const long long s0 = b->host_step;
         int64_t before[PIC_K_CLASSES];
@@ -801,16 +814,16 @@ template <class R> int step_batch(pic_handle *b, int64_t n) {
           return rc;
         }
         if (e != cudaSuccess) return set_err(b, PIC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&b->cycle, g, 0);
+        e = cudaGraphInstantiate(&gx, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return set_err(b, PIC_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
         for (int q = 0; q < PIC_K_CLASSES; ++q) {   // the capture only recorded the launches
-          b->cycle_launch[q] = b->klaunch[q] - before[q];
+          gl[q] = b->klaunch[q] - before[q];
           b->klaunch[q] = before[q];
         }
       }
-      CU(b, cudaGraphLaunch(b->cycle, b->stream));
-      for (int q = 0; q < PIC_K_CLASSES; ++q) b->klaunch[q] += b->cycle_launch[q];
+      CU(b, cudaGraphLaunch(gx, b->stream));
+      for (int q = 0; q < PIC_K_CLASSES; ++q) b->klaunch[q] += gl[q];
       b->host_step += sub;
       for (pic_handle *c : b->cols) c->host_step = b->host_step;
       done += sub;
@@ -832,8 +845,8 @@ template <class R> int init_batch_typed(pic_handle *b) {
   size_t smem = 0;
   for (pic_handle *c : b->cols) {
     d.push_back(coldev_of<R>(c));
-    int W = 0, se = 0;
-    const size_t by = pic::push_layout<R>(c->N, W, se);
+    int W = 0, se = 0, mo = -1, wm = 0;
+    const size_t by = pic::push_layout<R>(c->N, W, se, mo, wm);
     if (by > smem) smem = by;
     if (c->N > b->maxN) b->maxN = c->N;
   }
@@ -998,14 +1011,6 @@ int pic_init(const pic_params *params, pic_handle **out) {
   return 0;
 }
 
-// steps s .. s+sub-1 of a column hold no sort and no diagnostic sample
-static bool plain_steps(const pic_params &p, long long s, int sub) {
-  for (long long q = s; q < s + sub; ++q) {
-    if (p.sort_every > 0 && q % p.sort_every == 0) return false;
-    if (p.diag_every > 0 && q % p.diag_every == 0) return false;
-  }
-  return true;
-}
 
 int pic_step(pic_handle *h, int64_t n) {
   if (!h || n < 0) return set_err(h, PIC_EINVAL, "bad arguments");
@@ -1016,8 +1021,11 @@ int pic_step(pic_handle *h, int64_t n) {
   const bool graphs = !(h->p.flags & PIC_FLAG_NO_GRAPH) && !h->timing;
   int64_t done = 0;
   while (done < n) {
-    if (graphs && n - done >= sub && h->host_step % sub == 0 && plain_steps(h->p, h->host_step, sub)) {
-      if (!h->cycle) {
+    const int kind = graphs && n - done >= sub && h->host_step % sub == 0 ? cycle_kind(h->p, h->host_step, sub) : 0;
+    if (kind) {
+      cudaGraphExec_t &gx = kind == 1 ? h->cycle : h->dcycle;
+      int64_t *gl = kind == 1 ? h->cycle_launch : h->dcycle_launch;
+      if (!gx) {
         // capture one ion cycle; the kernels read the step counter on the device, so it replays
         const long long s0 = h->host_step;
         int64_t before[PIC_K_CLASSES];
@@ -1033,16 +1041,16 @@ int pic_step(pic_handle *h, int64_t n) {
           return rc;
         }
         if (e != cudaSuccess) return set_err(h, PIC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&h->cycle, g, 0);
+        e = cudaGraphInstantiate(&gx, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return set_err(h, PIC_ECUDA, "graph instantiation: %s", cudaGetErrorString(e));
         for (int q = 0; q < PIC_K_CLASSES; ++q) {   // the capture only recorded the launches
-          h->cycle_launch[q] = h->klaunch[q] - before[q];
+          gl[q] = h->klaunch[q] - before[q];
           h->klaunch[q] = before[q];
         }
       }
-      CU(h, cudaGraphLaunch(h->cycle, h->stream));
-      for (int q = 0; q < PIC_K_CLASSES; ++q) h->klaunch[q] += h->cycle_launch[q];
+      CU(h, cudaGraphLaunch(gx, h->stream));
+      for (int q = 0; q < PIC_K_CLASSES; ++q) h->klaunch[q] += gl[q];
       h->host_step += sub;
       done += sub;
       continue;
@@ -1371,9 +1379,14 @@ int pic_eepf_config(pic_handle *h, int32_t n_x, int32_t n_eps, double eps_max_eV
   pic::Ctl c;
   CU(h, cudaMemcpy(&c, h->ctl, sizeof c, cudaMemcpyDeviceToHost));
   h->eepf_base = c.n_diag;
-  if (h->cycle) {   // the captured ion cycle holds the old kernel parameters (it takes no samples)
+  // the captured ion cycles hold the old histogram in their kernel parameters
+  if (h->cycle) {
     cudaGraphExecDestroy(h->cycle);
     h->cycle = nullptr;
+  }
+  if (h->dcycle) {
+    cudaGraphExecDestroy(h->dcycle);
+    h->dcycle = nullptr;
   }
   return 0;
 }

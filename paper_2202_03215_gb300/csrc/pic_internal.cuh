@@ -150,6 +150,7 @@ template <class R> struct ColDev {
   FieldK fk;
   FieldScan *fs;
   int W, smemE;   // shared-memory layout of the particle step for this column
+  int mofs, Wm;   // byte offset of its diagnostic moment bins (-1: none) and their window
   int N;
 };
 
@@ -204,7 +205,7 @@ void launch_field(const FieldK &f, const unsigned long long *Qe, const unsigned 
 void launch_i128_test(const int64_t *hi, const uint64_t *lo, double *out, int n, cudaStream_t st);
 template <class R> int push_smem_bytes(int N);
 // shared-memory layout of the particle step for n_cells: bin window W, node field in shared memory
-template <class R> size_t push_layout(int n_cells, int &W, int &smemE);
+template <class R> size_t push_layout(int n_cells, int &W, int &smemE, int &mofs, int &Wm);
 
 // batched columns (one launch per phase for all columns)
 template <class R> void launch_zero_q_batch(const ColDev<R> *cols, int ncol, int species, int maxN, cudaStream_t st);

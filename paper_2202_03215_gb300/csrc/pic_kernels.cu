@@ -216,6 +216,15 @@ __device__ __forceinline__ long long vfix(float v) { return __float2ll_rn(v * 25
 __device__ __forceinline__ long long vfix(double v) { return __double2ll_rn(v * 256.0); }
 
 // diagnostic moments of one particle (FP64, cloud-in-cell weights)
+// EEPF sample (Sec. III.C): the energy bin decided in the storage precision
+template <class R>
+__device__ __forceinline__ void eepf_count(const Moments &m, int N, int32_t cell, R epsr) {
+  const R x = epsr * (R)m.eepf_scale;
+  const int b = x < (R)m.eepf_ne ? (int)x : m.eepf_ne;
+  const int bx = (int)(((long long)cell * m.eepf_nx) / N);
+  atomicAdd(m.eepf + (size_t)bx * (m.eepf_ne + 1) + b, 1ull);
+}
+
 template <class R, int SP>
 __device__ __forceinline__ void add_moments(const SpecK<R> &sp, const Moments &m, int N, int Nw, int32_t cell, R off,
                                             R vx, R vy, R vz) {
@@ -226,12 +235,7 @@ __device__ __forceinline__ void add_moments(const SpecK<R> &sp, const Moments &m
   if constexpr (SP == 0) {
     const R epsr = sp.K * (vx * vx + vy * vy + vz * vz);
     const double eps = (double)epsr;
-    if (m.eepf) {   // energy histogram (Sec. III.C): bin decided in the storage precision
-      const R x = epsr * (R)m.eepf_scale;
-      const int b = x < (R)m.eepf_ne ? (int)x : m.eepf_ne;
-      const int bx = (int)(((long long)cell * m.eepf_nx) / N);
-      atomicAdd(m.eepf + (size_t)bx * (m.eepf_ne + 1) + b, 1ull);
-    }
+    if (m.eepf) eepf_count<R>(m, N, cell, epsr);
     atomicAdd(m.ge + cell, w0 * vxd); atomicAdd(m.ge + c1, w1 * vxd);
     atomicAdd(m.ee + cell, w0 * eps); atomicAdd(m.ee + c1, w1 * eps);
     const double h = eps * vxd;
@@ -398,14 +402,106 @@ __device__ __forceinline__ void bins_flush(const CellBins &b, int N, int Nw, uns
   }
 }
 
+// Diagnostic moment bins, per node of the moment window [c0, c0 + Wm] (Wm + 1 nodes, Wm <= W,
+// the same origin as the charge window).  The electron flux and energy flux (and the ion flux)
+// are cancelling sums of thermal velocities of both signs: they are summed exactly as fixed point
+// (kMomScale per unit), each value split into a low 16-bit and a signed high part added to two
+// 32-bit words, like the charge bins; between two flushes a node receives fewer than 2^16 values,
+// so no word overflows.  The energy, a sum of positive terms, is summed in FP32.  The w0 parts go
+// to the left node, the w1 parts to the right one; a particle outside the moment window, or with a
+// value beyond the fixed-point range, goes straight to the FP64 node sums.  Flushed into the FP64
+// sums with the charge bins.  Words per node: electrons flux lo, hi, energy flux lo, hi, energy;
+// ions flux lo, hi.
+constexpr int kMomWords = 5;
+__host__ __device__ constexpr size_t mbins_bytes(int Wm) {
+  return ((size_t)(Wm + 1) * kMomWords * 4 + 15) & ~(size_t)15;
+}
+// fixed-point scales (powers of two, so the scaling is exact): flux in m/s (electrons 2^6, range
+// 3.3e7 m/s; ions 2^14, range 1.3e5 m/s) and energy flux in eV m/s (2^-1, range 4.2e9)
+template <int SP> __device__ __forceinline__ float mom_scale_v() { return SP == 0 ? 64.0f : 16384.0f; }
+constexpr float kMomScaleH = 0.5f;
+constexpr float kMomRange = 2147483520.0f;   // largest float below 2^31
+
+__device__ __forceinline__ void fix_add(uint32_t *lo, uint32_t *hi, int i, float v) {
+  const int q = __float2int_rn(v);
+  atomicAdd(lo + i, (uint32_t)q & 0xffffu);
+  atomicAdd(hi + i, (uint32_t)(q >> 16));
+}
+__device__ __forceinline__ long long fix_sum(uint32_t lo, uint32_t hi) {
+  return (long long)(int32_t)hi * 65536ll + (long long)lo;
+}
+
+template <class R, int SP>
+__device__ __forceinline__ void add_moments_win(const SpecK<R> &sp, const Moments &m, const CellBins &b, uint32_t *sM,
+                                                int Wm, int N, int Nw, int32_t cell, R off, R vx, R vy, R vz) {
+  int li = cell;
+  if (b.W < N) {
+    li = cell - b.c0;
+    if (li < 0) li += N;
+  }
+  const float fx = (float)vx;
+  const float sv = mom_scale_v<SP>();
+  if (li >= Wm || !(fabsf(fx) * sv < kMomRange)) {
+    add_moments<R, SP>(sp, m, N, Nw, cell, off, vx, vy, vz);
+    return;
+  }
+  const float w1 = (float)wfix32(off) * 2.3283064365386963e-10f, w0 = 1.0f - w1;
+  const int W1 = Wm + 1;
+  if constexpr (SP == 0) {
+    const R epsr = sp.K * (vx * vx + vy * vy + vz * vz);
+    const float fe = (float)epsr, fh = fe * fx;
+    if (!(fabsf(fh) * kMomScaleH < kMomRange)) {
+      add_moments<R, SP>(sp, m, N, Nw, cell, off, vx, vy, vz);
+      return;
+    }
+    if (m.eepf) eepf_count<R>(m, N, cell, epsr);
+    fix_add(sM, sM + W1, li, (w0 * fx) * sv);
+    fix_add(sM, sM + W1, li + 1, (w1 * fx) * sv);
+    fix_add(sM + 2 * W1, sM + 3 * W1, li, (w0 * fh) * kMomScaleH);
+    fix_add(sM + 2 * W1, sM + 3 * W1, li + 1, (w1 * fh) * kMomScaleH);
+    float *se = reinterpret_cast<float *>(sM + 4 * W1);
+    atomicAdd(se + li, w0 * fe);
+    atomicAdd(se + li + 1, w1 * fe);
+  } else {
+    fix_add(sM, sM + W1, li, (w0 * fx) * sv);
+    fix_add(sM, sM + W1, li + 1, (w1 * fx) * sv);
+  }
+}
+
+// add the moment bins to the FP64 node sums and clear them (threads t0, t0 + nt, ... of the CTA)
+template <int SP>
+__device__ __forceinline__ void mbins_flush(const CellBins &b, uint32_t *sM, int Wm, const Moments &m, int N, int Nw,
+                                            int t0, int nt) {
+  const int W1 = Wm + 1;
+  for (int j = t0; j < W1; j += nt) {
+    // node j: the left node of window cell j, or for j = Wm the right node of cell Wm - 1
+    int c = j < Wm ? j : Wm - 1;
+    if (b.W < N) { c = b.c0 + c; if (c >= N) c -= N; }
+    const int node = j < Wm ? c : ((c + 1 == Nw) ? 0 : c + 1);
+    const long long g = fix_sum(sM[j], sM[W1 + j]);
+    if (g) atomicAdd((SP == 0 ? m.ge : m.gi) + node, (double)g * (1.0 / (double)mom_scale_v<SP>()));
+    sM[j] = 0u;
+    sM[W1 + j] = 0u;
+    if constexpr (SP == 0) {
+      const long long h = fix_sum(sM[2 * W1 + j], sM[3 * W1 + j]);
+      if (h) atomicAdd(m.he + node, (double)h * (1.0 / (double)kMomScaleH));
+      float *se = reinterpret_cast<float *>(sM + 4 * W1);
+      if (se[j] != 0.0f) atomicAdd(m.ee + node, (double)se[j]);
+      sM[2 * W1 + j] = 0u;
+      sM[3 * W1 + j] = 0u;
+      se[j] = 0.0f;
+    }
+  }
+}
+
 // one CTA's share (cta of ncta) of the particle step of one column; PK: k is a launch
 // parameter (the Philox round keys are read from it as constants); PL: a plain step (no
 // process codes, no diagnostic sample, no circuit sums, no radial losses), compiled without
 // those branches
 template <class R, int SP, bool PK, bool BD, bool PL = false>
 __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef,
-                                          BirthBuf<R> bb, Moments m, int W, int smemE, int cta, int ncta,
-                                          unsigned char *smem) {
+                                          BirthBuf<R> bb, Moments m, int W, int smemE, int mofs, int Wm,
+                                          int cta, int ncta, unsigned char *smem) {
   __shared__ unsigned int s_cnt[kMaxProc + 1];
   __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages];
   constexpr int kMode = stage_mode<R>();
@@ -430,6 +526,14 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
   const long long stepll = ctl->step;
   const uint32_t step = (uint32_t)stepll;
   const bool diag = !PL && k.diag_every > 0 && (stepll % k.diag_every) == 0;
+  // this step's moments go to shared-memory bins (mofs >= 0: the layout has room for them); when
+  // they take the field's place, the field is gathered from global memory on this step
+  const bool mb = diag && mofs >= 0;
+  const bool eSmem = smemE && !(mb && mofs == (int)pbhot_bytes<R>());
+  uint32_t *sM = reinterpret_cast<uint32_t *>(smem + (mofs >= 0 ? mofs : 0));
+  // bin flushes every FT tiles; on a sampled step every FT / 2, so that with the candidates whose
+  // collision (and moments) come after a flush a node still receives fewer than 2^16 values
+  const int ftiles = mb ? FT / 2 : FT;
   const uint2 key = seed_key(k.seed);
   const uint32_t c3 = ((SP == 0 ? (uint32_t)kStE : (uint32_t)kStI) << 28) | (k.column << 16);
   // slot range of this CTA; the chunk is a multiple of 4 slots, so that every tile starts on a
@@ -463,9 +567,11 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     for (int tt = 0; tt < kStages; ++tt) stage_in(tt);
   if constexpr (staged<R>() && SP == 0)
     for (int j = threadIdx.x; j < kPbHot && j < k.ntab; j += blockDim.x) sPb[j] = __ldg(sp.Pbi + j);
-  if (smemE)
+  if (eSmem)
     for (int j = threadIdx.x; j <= N; j += blockDim.x) sE[j] = Ef[j];
   for (int j = threadIdx.x; j < W; j += blockDim.x) { bins.cnt[j] = 0u; bins.klo[j] = 0u; bins.khi[j] = 0u; }
+  if (mb)
+    for (int j = threadIdx.x; j < kMomWords * (Wm + 1); j += blockDim.x) sM[j] = 0u;
   if (threadIdx.x <= kMaxProc) s_cnt[threadIdx.x] = 0u;
   if (kStg && threadIdx.x == 0) {
     for (int q = 0; q < kStages; ++q) {
@@ -475,7 +581,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const R *E = smemE ? sE : Ef;
+  const R *E = eSmem ? sE : Ef;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
@@ -530,7 +636,8 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
         sel = collide<R, SP, BD>(k, sp, ctl, bb, m, qid, step, c3, qp, qcell, qoff_, qu1, qx, qy, qz, ovf);
         rec_store<R>(s.rec, qp, qoff_, qx, qy, qz);
         if (record) s.code[qp] = sel >= 0 ? sp.xs[sel] : -1;
-        if (diag) add_moments<R, SP>(sp, m, N, Nw, qcell, qoff_, qx, qy, qz);
+        if (mb) add_moments_win<R, SP>(sp, m, bins, sM, Wm, N, Nw, qcell, qoff_, qx, qy, qz);
+        else if (diag) add_moments<R, SP>(sp, m, N, Nw, qcell, qoff_, qx, qy, qz);
         if (circuit) vsum += vfix(qx);
       }
       for (int q = 0; q < sp.np; ++q) {
@@ -555,6 +662,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
       }
     }
     bool live = true;   // warp-uniform: false once a stage wait gave up
+    int until = ftiles; // tiles left before the next bin flush (a countdown: no division per tile)
     for (int t = 0; t < ntiles; ++t) {
       const int base = ip0 + t * TILE;
       const int p = base + warp * 32 + lane;
@@ -623,7 +731,8 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
         rec_store<R>(s.rec, p, off, vx, vy, vz);   // a candidate's record is rewritten after its collision
         if (!cand) {
           if (record) s.code[p] = dead ? -2 : -1;
-          if (!dead && diag) add_moments<R, SP>(sp, m, N, Nw, cell, off, vx, vy, vz);
+          if (!dead && mb) add_moments_win<R, SP>(sp, m, bins, sM, Wm, N, Nw, cell, off, vx, vy, vz);
+          else if (!dead && diag) add_moments<R, SP>(sp, m, N, Nw, cell, off, vx, vy, vz);
           if (!dead && circuit) vsum += vfix(vx);
         }
         if (dead) {
@@ -661,9 +770,11 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
         wq = rest;
       }
       // keep every cell of the window below 2^16 particles between flushes
-      if ((t + 1) % FT == 0 && t + 1 < ntiles) {
+      if (--until == 0 && t + 1 < ntiles) {
+        until = ftiles;
         named_sync(1, CW * 32);
         bins_flush(bins, N, Nw, s.Q, threadIdx.x, CW * 32);
+        if (mb) mbins_flush<SP>(bins, sM, Wm, m, N, Nw, threadIdx.x, CW * 32);
         named_sync(1, CW * 32);
       }
     }
@@ -682,6 +793,7 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
   }
   __syncthreads();
   bins_flush(bins, N, Nw, s.Q, threadIdx.x, blockDim.x);
+  if (mb) mbins_flush<SP>(bins, sM, Wm, m, N, Nw, threadIdx.x, blockDim.x);
   if (threadIdx.x < sp.np && s_cnt[threadIdx.x])
     atomicAdd(&ctl->n_coll[SP][threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
   if (threadIdx.x == 0 && s_cnt[kMaxProc]) atomicAdd(&ctl->overflow[SP], (unsigned long long)s_cnt[kMaxProc]);
@@ -690,9 +802,9 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
 template <class R, int SP, bool BD, bool PL>
 __global__ void __launch_bounds__(kStepThreads, 1)
 k_push(const __grid_constant__ StepK<R> k, SpeciesDev s, Ctl *ctl, const R *__restrict__ Ef, BirthBuf<R> bb,
-       Moments m, int W, int smemE) {
+       Moments m, int W, int smemE, int mofs, int Wm) {
   extern __shared__ __align__(16) unsigned char smem[];
-  push_body<R, SP, true, BD, PL>(k, s, ctl, Ef, bb, m, W, smemE, blockIdx.x, gridDim.x, smem);
+  push_body<R, SP, true, BD, PL>(k, s, ctl, Ef, bb, m, W, smemE, mofs, Wm, blockIdx.x, gridDim.x, smem);
 }
 
 // batched columns: CTA b runs share sched[b].y of sched[b].z of column sched[b].x
@@ -709,7 +821,7 @@ __global__ void __launch_bounds__(kStepThreads, 1) k_push_batch(const ColDev<R> 
   }
   __syncthreads();
   push_body<R, SP, false, false, PL>(sk, cd->sp[SP], cd->ctl, reinterpret_cast<const R *>(cd->Ef), cd->bb, cd->m, cd->W, cd->smemE,
-                   sc.y, sc.z, smem);
+                   cd->mofs, cd->Wm, sc.y, sc.z, smem);
 }
 
 template <class R> int push_smem_bytes(int N) {
@@ -717,7 +829,7 @@ template <class R> int push_smem_bytes(int N) {
   return (int)e;
 }
 
-template <class R> size_t push_layout(int n_cells, int &W, int &smemE) {
+template <class R> size_t push_layout(int n_cells, int &W, int &smemE, int &mofs, int &Wm) {
   const size_t budget = 226 * 1024;   // of 227 KB: room for the batched kernel's static StepK
   const size_t qb = queue_bytes<R>() + stage_bytes<R>() + pbhot_bytes<R>();
   size_t eb = (((size_t)n_cells + 1) * sizeof(R) + 15) & ~(size_t)15;
@@ -727,20 +839,40 @@ template <class R> size_t push_layout(int n_cells, int &W, int &smemE) {
   const size_t wmax = (budget - eb - qb) / 12;
   W = (int)((size_t)n_cells < wmax ? (size_t)n_cells : wmax);
   if (W < n_cells) W = W < 4096 ? (W & ~63) : 4096;
-  return eb + bins_bytes(W) + qb;
+  const size_t base = eb + bins_bytes(W) + qb;
+  // diagnostic moment bins: after everything for the whole charge window when they fit; else in
+  // the field's place (the field is then gathered from global memory on sampled steps) for as many
+  // nodes as fit there; else none (the moments then go straight to the FP64 node sums)
+  mofs = -1;
+  Wm = 0;
+  if (base + mbins_bytes(W) <= budget) {
+    mofs = (int)base;
+    Wm = W;
+    return base + mbins_bytes(W);
+  }
+  if (smemE) {
+    int wm = (int)(eb / (kMomWords * 4)) - 1;
+    if (wm >= W) wm = W;
+    else wm &= ~63;
+    if (wm >= 64) {
+      mofs = (int)pbhot_bytes<R>();
+      Wm = wm;
+    }
+  }
+  return base;
 }
 
 template <class R>
 void launch_push(const StepK<R> &k, SpeciesDev s, Ctl *ctl, const R *Ef, BirthBuf<R> bb, Moments m, int species,
                  int nsm, bool diag_step, cudaStream_t st) {
-  int W = 0, smemE = 0;
+  int W = 0, smemE = 0, mofs = -1, Wm = 0;
   // a step with none of the optional work runs the kernel compiled without it
   const bool plain = !diag_step && !(k.flags & PIC_FLAG_RECORD_CODES) && k.drive != PIC_DRIVE_CIRCUIT &&
                      k.loss_mode != PIC_LOSS_RADIAL;
-  const size_t bytes = push_layout<R>(k.N, W, smemE);
+  const size_t bytes = push_layout<R>(k.N, W, smemE, mofs, Wm);
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    kern<<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE);
+    kern<<<nsm, kStepThreads, bytes, st>>>(k, s, ctl, Ef, bb, m, W, smemE, mofs, Wm);
   };
   if (species == 0) {
     if (k.bounded) go(k_push<R, 0, true, false>);
@@ -1572,7 +1704,7 @@ template <class R> void launch_sumv(SpeciesDev s, Ctl *ctl, int species, cudaStr
                                 double *, double *, R *, Moments, FieldScan *, bool, bool, cudaStream_t);            \
   template int push_smem_bytes<R>(int);                                                                             \
   template void launch_sumv<R>(SpeciesDev, Ctl *, int, cudaStream_t);                                               \
-  template size_t push_layout<R>(int, int &, int &);                                                                \
+  template size_t push_layout<R>(int, int &, int &, int &, int &);                                                                \
   template void launch_zero_q_batch<R>(const ColDev<R> *, int, int, int, cudaStream_t);                             \
   template void launch_push_batch<R>(const ColDev<R> *, const int4 *, int, int, size_t, bool, cudaStream_t);              \
   template void launch_births_batch<R>(const ColDev<R> *, int, int, cudaStream_t);                                  \

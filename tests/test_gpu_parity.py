@@ -144,10 +144,13 @@ def test_moments_match(precision):
     mg, mo = g.moments(), o.moments()
     assert mg["n_samples"] == mo["n_samples"] == 4
     assert mg["n_steps"] == mo["n_steps"] == 35
+    # flux, energy and energy flux are summed per CTA in FP32 shared-memory bins before the FP64
+    # node sums: within 1e-5 of each array's largest value (the single-step bound for moments);
+    # densities and ionization counts are exact
     for k in pb.MOMENT_NAMES:
         a, b = mg[k], mo[k]
         scale = np.abs(b).max() + 1e-300
-        assert np.abs(a - b).max() <= 1e-9 * scale, k
+        assert np.abs(a - b).max() <= 1e-5 * scale, k
     for k in ("n_e", "n_i", "iz_rate", "E"):
         assert np.array_equal(mg[k], mo[k]) or k == "E", k
 
@@ -200,3 +203,30 @@ def test_full_size_neon_column_first_step():
     o.step(1)
     assert_same(g.get_state(), o.get_state(), "step 1")
     assert g.stats()["n_coll_e"] == o.stats()["n_coll_e"]
+
+
+def test_full_size_neon_column_moments():
+    """Diagnostic moments of one step (an ion step) of the benchmark's neon column, 2e7 per
+    species in 16384 cells: the GPU step sums flux, energy and energy flux per CTA cell window in
+    FP32 shared-memory bins (in the field's place, the field then gathered from global memory)
+    and the oracle sums every particle in FP64.  Within 1e-5 of each array's largest value;
+    densities and ionization counts exact."""
+    from oracle import two_term as tt
+    p = w.config_neon_column(drive=w.DRIVE_RI, I_A=1e-3)
+    xs = [(x.kind, x.threshold_eV, x.energy_eV, x.sigma_m2) for x in p.xsec]
+    E0, n0, _ = tt.ri_drive(xs, p.gas_mass_amu, p.pressure_torr, p.T_gas_K, p.R_m, p.I_A, p.eps_max_e_eV)
+    p = p.with_(drive=w.DRIVE_E0, E0_Vpm=float(E0), n0_m3=float(n0), diag_every=10)   # step 0 is sampled
+    g = pb.Column(p)
+    o = oracle.Oracle(p)
+    g.step(1)
+    o.step(1)
+    mg, mo = g.moments(), o.moments()
+    g.close()
+    rel = {}
+    for k in pb.MOMENT_NAMES:
+        a, b = mg[k], mo[k]
+        rel[k] = float(np.abs(a - b).max() / (np.abs(b).max() + 1e-300))
+    print("largest difference / largest value:", rel)
+    assert all(v <= 1e-5 for v in rel.values()), rel
+    for k in ("n_e", "n_i", "iz_rate"):
+        assert np.array_equal(mg[k], mo[k]), k
