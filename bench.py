@@ -552,6 +552,7 @@ def main():
     ap.add_argument("--no-bounded", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-steady", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -644,6 +645,37 @@ def main():
             "algorithmic_bytes_per_launch": BYTES_PER_PUSH * n_e, "avg_launch_us": avg_s * 1e6,
             "share_of_step": push_ms / ms_inst, "timed_with": "CUDA events around every kernel, second pass"}
 
+    # steady state: the column continued (untimed) to step 4000, by which its electrons have heated
+    # from the initial 2 eV to their steady mean energy (more collision candidates, more births
+    # than right after the start), then 1000 steps timed under graph replay, and the same steps
+    # again from a snapshot with a CUDA event around every kernel
+    steady = None
+    if not args.no_steady:
+        cur = col.stats()["step"]
+        if cur < 4000:
+            col.step(4000 - cur)
+        st_s = col.stats()
+        snap = col.get_state()
+        torch.cuda.synchronize()
+        e0.record(ext)
+        col.step(1000)
+        e1.record(ext)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1)
+        units_s = pushed_steps(st_s["step"], 1000, st_s["n_e"], st_s["n_i"], p.ion_subcycle)
+        col.set_state(snap)
+        del snap
+        col.set_timing(True)
+        col.kernel_times()
+        col.step(1000)
+        kt_s = col.kernel_times()
+        col.set_timing(False)
+        avg_e = kt_s["push_e"][0] / max(1, kt_s["push_e"][1]) / 1e3
+        steady = {"from_step": st_s["step"], "steps": 1000, "ms_per_step": ms_s / 1000,
+                  "value": units_s / (ms_s / 1e3), "unit": UNIT, "electron_step_us": avg_e * 1e6,
+                  "electron_step_frac": BYTES_PER_PUSH * st_s["n_e"] / avg_e / 1e9 / peak,
+                  "kernel_us_per_step": {k: v[0] / 1000 * 1e3 for k, v in kt_s.items()}}
+
     # end to end through the public API with host buffers: upload the state, step, read moments
     e2e = None
     if not args.no_e2e:
@@ -707,7 +739,7 @@ def main():
                            "l2": "inputs larger than L2 (state 1.1 GB)", "parallelism": f"replicas x{world}",
                            "pushed_particle_steps": units},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "batched_vs_serial": batch,
-                "ms_per_step_amortized": amort, "fp64_form": fp64, "argon_small_column": small,
+                "ms_per_step_amortized": amort, "steady_state": steady, "fp64_form": fp64, "argon_small_column": small,
                 "fluid_screen": screen, "closure_training": train, "eepf": eepf, "bounded_column": bnd,
                 "gpu_launches": launches, "ms_per_step_instrumented": ms_inst / args.steps,
                 "kernel_ms": {k: v[0] for k, v in kt.items()}, "clocks": clocks}
