@@ -543,7 +543,30 @@ __device__ __forceinline__ void push_body(const StepK<R> &k, SpeciesDev s, Ctl *
   const long long p1 = min(n, p0 + chunk);
   int c0 = 0;
   if (W < N && p0 < p1) {
-    c0 = s.cell[p0] - W / 8;
+    // the window is centred on the median of five cells in the middle of the slot range, taken as
+    // offsets on the periodic grid from the first of them: particles out of cell order (newborns
+    // in victims' slots since the last sort) cannot pull the window away from the rest
+    const long long pm = min(p1 - 5, max(p0, p0 + (p1 - p0) / 2 - 2));
+    int d[5];
+    const int ref = s.cell[max(p0, pm)];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const long long pq = min(p1 - 1, max(p0, pm + q));
+      int x = s.cell[pq] - ref;
+      if (x > N / 2) x -= N;
+      else if (x <= -(N / 2)) x += N;
+      d[q] = x;
+    }
+    int med = 0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      int below = 0;
+#pragma unroll
+      for (int r = 0; r < 5; ++r) below += (d[r] < d[q]) || (d[r] == d[q] && r < q);
+      if (below == 2) med = d[q];
+    }
+    c0 = ref + med - W / 2;
+    c0 %= N;
     if (c0 < 0) c0 += N;
   }
   bins.c0 = c0;
