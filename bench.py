@@ -680,6 +680,11 @@ def main():
     e2e = None
     if not args.no_e2e:
         host = col.get_state()
+        if p.precision == w.MIXED:
+            # the precision form's storage: FP32 offsets and velocities (pic_set_state_f32)
+            for k in ("off", "vx", "vy", "vz"):
+                for sp in ("e", "i"):
+                    host[f"{k}_{sp}"] = host[f"{k}_{sp}"].astype(np.float32)
         pinned = {}
         for k, v in host.items():
             if isinstance(v, np.ndarray):
@@ -705,7 +710,8 @@ def main():
         secs, local_units = aggregate(dist, torch, secs, local_units)
         e2e = {"value": local_units / secs, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "seconds": secs, "api": "pic_set_state (host arrays) + pic_step(K) + pic_moments + pic_get_stats"}
+               "seconds": secs, "api": ("pic_set_state_f32" if p.precision == w.MIXED else "pic_set_state")
+                      + " (host arrays) + pic_step(K) + pic_moments + pic_get_stats"}
         assert stx["step"] == host["step"] + args.steps
         col2.close()
 

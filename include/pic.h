@@ -163,6 +163,20 @@ typedef struct pic_state {
   int64_t *Q_i;            /* ion node charge, fixed point (set: NULL = re-deposit the ions) */
 } pic_state;
 
+/* The particle state with the offsets and velocities in FP32, the storage form of a PIC_MIXED
+ * column (Sec. II's particles: cell, offset in the cell, three velocity components, id), for
+ * pic_set_state_f32.  The other members mean what they mean in pic_state. */
+typedef struct pic_state_f32 {
+  int64_t n_e, n_i;
+  int64_t step;
+  int64_t next_id;
+  double E0;
+  int32_t *cell_e; float *off_e, *vx_e, *vy_e, *vz_e; uint64_t *id_e;
+  int32_t *cell_i; float *off_i, *vx_i, *vy_i, *vz_i; uint64_t *id_i;
+  double *E;               /* NULL = recompute from the charges */
+  int64_t *Q_i;            /* NULL = re-deposit the ions */
+} pic_state_f32;
+
 /* Counters since pic_init. */
 typedef struct pic_stats {
   int64_t step, n_e, n_i, next_id;
@@ -268,6 +282,11 @@ int pic_get_state(pic_handle *h, pic_state *out);
  * lowest such particle and leaves the particles undefined until the next successful
  * call.  The first call allocates 32 bytes of device memory per particle of capacity. */
 int pic_set_state(pic_handle *h, const pic_state *in);
+/* pic_set_state with FP32 offsets and velocities (pic_state_f32).  A PIC_MIXED column stores
+ * them as given, with no rounding on the way in, and the upload moves 28 bytes per particle
+ * instead of 44.  A PIC_FP64 column widens them exactly.  Checks, errors, ownership (nothing is
+ * kept after the call) and the first call's staging allocation are those of pic_set_state. */
+int pic_set_state_f32(pic_handle *h, const pic_state_f32 *in);
 /* Copy the counters (pic_stats) into *out.  Synchronises the handle's stream; PIC_EINVAL for a
  * NULL argument. */
 int pic_get_stats(pic_handle *h, pic_stats *out);

@@ -109,11 +109,11 @@ namespace {
 // pic_set_state: the uploaded offsets and velocities (FP64, as given) into the particle records,
 // rounded once to the storage precision; *bad = the lowest index outside the grid
 // (cell not in [0, N), offset not in [0, 1), or an offset that rounds to 1 in FP32 storage)
-template <class R>
-__global__ void k_set_rec(const int32_t *__restrict__ cell, const double *__restrict__ st, long long n, int N,
+template <class R, class In>
+__global__ void k_set_rec(const int32_t *__restrict__ cell, const In *__restrict__ st, long long n, int N,
                           void *rec, unsigned long long *bad) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
-    const double o = st[p], vx = st[n + p], vy = st[2 * n + p], vz = st[3 * n + p];
+    const double o = (double)st[p], vx = (double)st[n + p], vy = (double)st[2 * n + p], vz = (double)st[3 * n + p];
     const int32_t c = cell[p];
     bool ok = c >= 0 && c < N && o >= 0.0 && o < 1.0;
     if constexpr (std::is_same<R, float>::value) {
@@ -1250,8 +1250,21 @@ int pic_get_state(pic_handle *h, pic_state *o) {
   return 0;
 }
 
-int pic_set_state(pic_handle *h, const pic_state *in) {
-  if (!h || !in) return set_err(h, PIC_EINVAL, "bad arguments");
+}  // extern "C"
+
+// pic_set_state's arrays, with the offsets and velocities in FP64 or FP32 (In)
+template <class In> struct StateIn {
+  int64_t n_e, n_i, step, next_id;
+  double E0;
+  const int32_t *cell[2];
+  const In *off[2], *vx[2], *vy[2], *vz[2];
+  const uint64_t *id[2];
+  const double *E;
+  const int64_t *Q_i;
+};
+
+template <class In> static int set_state_in(pic_handle *h, const StateIn<In> &st) {
+  const StateIn<In> *in = &st;
   if (in->n_e < 0 || in->n_i < 0 || in->n_e > h->sp[0].cap || in->n_i > h->sp[1].cap)
     return set_err(h, PIC_EINVAL, "particle count out of range");
   if (in->step < 0) return set_err(h, PIC_EINVAL, "step < 0");
@@ -1259,10 +1272,9 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
   if (h->owner && in->step != h->owner->host_step)
     return set_err(h, PIC_EINVAL, "a column of a batch keeps the batch's step counter");
   CU(h, cudaStreamSynchronize(h->stream));
-  const int32_t *cells[2] = {in->cell_e, in->cell_i};
-  const double *offs[2] = {in->off_e, in->off_i}, *vxs[2] = {in->vx_e, in->vx_i}, *vys[2] = {in->vy_e, in->vy_i},
-               *vzs[2] = {in->vz_e, in->vz_i};
-  const uint64_t *ids[2] = {in->id_e, in->id_i};
+  const int32_t *const *cells = in->cell;
+  const In *const *offs = in->off, *const *vxs = in->vx, *const *vys = in->vy, *const *vzs = in->vz;
+  const uint64_t *const *ids = in->id;
   const int64_t ns[2] = {in->n_e, in->n_i};
   // the arrays go to the device as given (cells and ids to their places, offsets and velocities
   // to a staging area), then one kernel per species checks the grid and writes the records
@@ -1282,21 +1294,22 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
   for (int q = 0; q < 2; ++q) {
     const int64_t n = ns[q];
     if (n == 0) continue;
-    const size_t b8 = (size_t)n * 8;
+    const size_t b8 = (size_t)n * 8, bv = (size_t)n * sizeof(In);
+    In *stg = reinterpret_cast<In *>(h->stage);   // 4n values of In fit the 4 cap doubles
     CU(h, cudaMemcpyAsync(h->sp[q].cell, cells[q], (size_t)n * 4, cudaMemcpyHostToDevice, h->stream));
     CU(h, cudaMemcpyAsync(h->sp[q].id, ids[q], b8, cudaMemcpyHostToDevice, h->stream));
-    CU(h, cudaMemcpyAsync(h->stage, offs[q], b8, cudaMemcpyHostToDevice, h->stream));
-    CU(h, cudaMemcpyAsync(h->stage + n, vxs[q], b8, cudaMemcpyHostToDevice, h->stream));
-    CU(h, cudaMemcpyAsync(h->stage + 2 * n, vys[q], b8, cudaMemcpyHostToDevice, h->stream));
-    CU(h, cudaMemcpyAsync(h->stage + 3 * n, vzs[q], b8, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(stg, offs[q], bv, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(stg + n, vxs[q], bv, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(stg + 2 * n, vys[q], bv, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(stg + 3 * n, vzs[q], bv, cudaMemcpyHostToDevice, h->stream));
     CU(h, cudaMemcpyAsync(h->stage_bad + q, &bad[q], 8, cudaMemcpyHostToDevice, h->stream));
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)h->nsm * 8);
     if (h->mixed)
-      k_set_rec<float><<<blocks, 256, 0, h->stream>>>(h->sp[q].cell, h->stage, n, h->N, h->sp[q].rec,
-                                                       h->stage_bad + q);
+      k_set_rec<float, In><<<blocks, 256, 0, h->stream>>>(h->sp[q].cell, stg, n, h->N, h->sp[q].rec,
+                                                           h->stage_bad + q);
     else
-      k_set_rec<double><<<blocks, 256, 0, h->stream>>>(h->sp[q].cell, h->stage, n, h->N, h->sp[q].rec,
-                                                        h->stage_bad + q);
+      k_set_rec<double, In><<<blocks, 256, 0, h->stream>>>(h->sp[q].cell, stg, n, h->N, h->sp[q].rec,
+                                                            h->stage_bad + q);
     CU(h, cudaGetLastError());
     CU(h, cudaMemcpyAsync(&bad[q], h->stage_bad + q, 8, cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));   // the staging area is reused by the next species
@@ -1354,6 +1367,36 @@ int pic_set_state(pic_handle *h, const pic_state *in) {
   CU(h, cudaStreamSynchronize(h->stream));
   CU(h, cudaGetLastError());
   return check_status(h);
+}
+
+template <class In, class S> static StateIn<In> state_view(const S *in) {
+  StateIn<In> v;
+  v.n_e = in->n_e;
+  v.n_i = in->n_i;
+  v.step = in->step;
+  v.next_id = in->next_id;
+  v.E0 = in->E0;
+  v.cell[0] = in->cell_e; v.cell[1] = in->cell_i;
+  v.off[0] = in->off_e; v.off[1] = in->off_i;
+  v.vx[0] = in->vx_e; v.vx[1] = in->vx_i;
+  v.vy[0] = in->vy_e; v.vy[1] = in->vy_i;
+  v.vz[0] = in->vz_e; v.vz[1] = in->vz_i;
+  v.id[0] = in->id_e; v.id[1] = in->id_i;
+  v.E = in->E;
+  v.Q_i = in->Q_i;
+  return v;
+}
+
+extern "C" {
+
+int pic_set_state(pic_handle *h, const pic_state *in) {
+  if (!h || !in) return set_err(h, PIC_EINVAL, "bad arguments");
+  return set_state_in<double>(h, state_view<double>(in));
+}
+
+int pic_set_state_f32(pic_handle *h, const pic_state_f32 *in) {
+  if (!h || !in) return set_err(h, PIC_EINVAL, "bad arguments");
+  return set_state_in<float>(h, state_view<float>(in));
 }
 
 int pic_eepf_config(pic_handle *h, int32_t n_x, int32_t n_eps, double eps_max_eV) {

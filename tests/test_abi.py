@@ -41,7 +41,7 @@ def test_library_exports_every_declared_symbol(libpic):
 
 
 def test_binding_struct_layout_matches_header(tmp_path):
-    structs = {"pic_params": pb.Params, "pic_xsec": pb.Xsec, "pic_state": pb.State,
+    structs = {"pic_params": pb.Params, "pic_xsec": pb.Xsec, "pic_state": pb.State, "pic_state_f32": pb.StateF32,
                "pic_stats": pb.Stats, "pic_moments_out": pb.MomentsOut, "pic_transport": pb.Transport,
                "pic_fluid_column": pb.FluidColumn}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void) {']

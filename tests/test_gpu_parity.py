@@ -230,3 +230,33 @@ def test_full_size_neon_column_moments():
     assert all(v <= 1e-5 for v in rel.values()), rel
     for k in ("n_e", "n_i", "iz_rate"):
         assert np.array_equal(mg[k], mo[k]), k
+
+
+@pytest.mark.parametrize("precision", [w.FP64, w.MIXED])
+def test_set_state_f32_equals_set_state(precision):
+    """pic_set_state_f32 (FP32 offsets and velocities, the precision form's storage) installs
+    the state pic_set_state installs from the same values in FP64: particles, charges and field
+    bit for bit, and the same trajectory after it; an offset of 1 in FP32 is refused alike."""
+    p = small(precision)
+    g = pb.Column(p)
+    g.step(7)
+    st = g.get_state()
+    st32, st64 = dict(st), dict(st)
+    for k in ("off", "vx", "vy", "vz"):
+        for sp in ("e", "i"):
+            st32[f"{k}_{sp}"] = st[f"{k}_{sp}"].astype(np.float32)
+            st64[f"{k}_{sp}"] = st32[f"{k}_{sp}"].astype(np.float64)
+    a, b = pb.Column(p), pb.Column(p)
+    a.set_state(st64)
+    b.set_state(st32)
+    assert_same(a.get_state(), b.get_state(), "set")
+    a.step(12)
+    b.step(12)
+    assert_same(a.get_state(), b.get_state(), "12 steps after")
+    bad = dict(st32)
+    bad["off_e"] = st32["off_e"].copy()
+    bad["off_e"][5] = np.float32(1.0)
+    with pytest.raises(pb.PicError, match="particle 5 of species 0"):
+        b.set_state(bad)
+    for c in (g, a, b):
+        c.close()
