@@ -405,12 +405,12 @@ __device__ __forceinline__ void bins_flush(const CellBins &b, int N, int Nw, uns
 // Diagnostic moment bins, per node of the moment window [c0, c0 + Wm] (Wm + 1 nodes, Wm <= W,
 // the same origin as the charge window).  The electron flux and energy flux (and the ion flux)
 // are cancelling sums of thermal velocities of both signs: they are summed exactly as fixed point
-// (mom_scale_v, kMomScaleH per unit), each value split into a low 16-bit and a signed high part to two
-// 32-bit words, like the charge bins; between two flushes a node receives fewer than 2^16 values,
-// so no word overflows.  The energy, a sum of positive terms, is summed in FP32.  The w0 parts go
-// to the left node, the w1 parts to the right one; a particle outside the moment window, or with a
-// value beyond the fixed-point range, goes straight to the FP64 node sums.  Flushed into the FP64
-// sums with the charge bins.  Words per node: electrons flux lo, hi, energy flux lo, hi, energy;
+// (mom_scale_v, kMomScaleH per unit), each value split into a low 16-bit and a signed high part
+// added to two 32-bit words, like the charge bins; between two flushes a node receives fewer than
+// 2^16 values, so no word overflows.  The energy, a sum of positive terms, is summed in FP32.  The
+// w0 parts go to the left node, the w1 parts to the right one; a particle outside the moment
+// window, or with a value beyond the fixed-point range, goes straight to the FP64 node sums.
+// Flushed into the FP64 sums with the charge bins.  Words per node: electrons flux lo, hi, energy flux lo, hi, energy;
 // ions flux lo, hi.
 constexpr int kMomWords = 5;
 __host__ __device__ constexpr size_t mbins_bytes(int Wm) {
