@@ -410,8 +410,8 @@ __device__ __forceinline__ void bins_flush(const CellBins &b, int N, int Nw, uns
 // 2^16 values, so no word overflows.  The energy, a sum of positive terms, is summed in FP32.  The
 // w0 parts go to the left node, the w1 parts to the right one; a particle outside the moment
 // window, or with a value beyond the fixed-point range, goes straight to the FP64 node sums.
-// Flushed into the FP64 sums with the charge bins.  Words per node: electrons flux lo, hi, energy flux lo, hi, energy;
-// ions flux lo, hi.
+// Flushed into the FP64 sums with the charge bins.  Words per node: electrons flux lo, hi, energy
+// flux lo, hi, energy; ions flux lo, hi.
 constexpr int kMomWords = 5;
 __host__ __device__ constexpr size_t mbins_bytes(int Wm) {
   return ((size_t)(Wm + 1) * kMomWords * 4 + 15) & ~(size_t)15;
